@@ -1,0 +1,173 @@
+/*
+ * oracle_f32.c -- the two integer decisions of the splatting step, taken in FP32.
+ *
+ * TEST INFRASTRUCTURE ONLY (see gsrf_oracle.h).
+ *
+ * The depth sort key (App. E: the low 32 bits of each splat key hold the distance
+ * to the receiver) and the set of tiles a Gaussian is splatted to (Sec. 4.3) are
+ * integers decided by floating point.  The kernels take these decisions in FP32, so
+ * the oracle takes them in FP32 too, with the same sequence of correctly rounded
+ * operations (+ - * / sqrt, no fused multiply-add: this file is compiled with
+ * -ffp-contract=off), which makes keys and lists comparable bit for bit.
+ *
+ * Coverage rule (a conservative reading of the paper's splatting, written out in the
+ * design notes): the 3-sigma ellipsoid lies inside the sphere of radius
+ * 3 * max(scale) about mu; the sphere radius is inflated by 1% (Rc = 3.03 max s) and
+ * a tile is covered when the centre of at least one of its ray bins lies inside the
+ * angular bounding box of that sphere seen from the receiver:
+ *   elevation  el_c +- asin(Rc / D),        el_c = asin(cz / D)
+ *   azimuth    az_c +- asin(Rc / rho),      az_c = atan2(cy, cx), rho = |(cx, cy)|
+ * with every azimuth when rho <= Rc (the sphere meets the vertical through r),
+ * every tile when D <= Rc, and no tile when D + Rc < r_rx (the sphere lies inside
+ * the ray-emitting sphere).  exp, atan2 and asin are evaluated by the short
+ * formulas below (textbook series after exact argument reduction), not by libm,
+ * so that both sides round identically.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+#include "gsrf_oracle.h"
+
+#define RAD2DEG_F 57.2957795f
+
+/* exp(x) = 2^n * e^(f ln 2) with n = floor(x log2 e); Taylor series of e^t to t^9. */
+static float det_exp(float x)
+{
+    float y = x * 1.44269504f;
+    float n = floorf(y);
+    float f = y - n;
+    float t = f * 0.693147182f;
+    float p = 2.75573192e-6f;
+    p = p * t + 2.48015873e-5f;
+    p = p * t + 1.98412698e-4f;
+    p = p * t + 1.38888889e-3f;
+    p = p * t + 8.33333333e-3f;
+    p = p * t + 4.16666667e-2f;
+    p = p * t + 1.66666667e-1f;
+    p = p * t + 0.5f;
+    p = p * t + 1.0f;
+    p = p * t + 1.0f;
+    return ldexpf(p, (int)n);
+}
+
+/* atan(t), t in [0, 1]: two half-angle reductions t <- t / (1 + sqrt(1 + t^2))
+ * bring t below tan(pi/16); then the Maclaurin series to t^11. */
+static float det_atan_unit(float t)
+{
+    t = t / (1.0f + sqrtf(1.0f + t * t));
+    t = t / (1.0f + sqrtf(1.0f + t * t));
+    float z = t * t;
+    float p = -9.09090909e-2f;
+    p = p * z + 1.11111111e-1f;
+    p = p * z + -1.42857143e-1f;
+    p = p * z + 2.0e-1f;
+    p = p * z + -3.33333333e-1f;
+    p = p * z + 1.0f;
+    return 4.0f * (t * p);
+}
+
+static float det_atan2(float y, float x)
+{
+    float ax = fabsf(x), ay = fabsf(y), a;
+    if (ax == 0.0f && ay == 0.0f) return 0.0f;
+    if (ay <= ax) a = det_atan_unit(ay / ax);
+    else a = 1.57079633f - det_atan_unit(ax / ay);
+    if (x < 0.0f) a = 3.14159265f - a;
+    if (y < 0.0f) a = -a;
+    return a;
+}
+
+static float det_asin(float s)
+{
+    if (s > 1.0f) s = 1.0f;
+    if (s < -1.0f) s = -1.0f;
+    float c = sqrtf((1.0f - s) * (1.0f + s));
+    return det_atan2(s, c);
+}
+
+/* exported for the pins: the same three functions, callable one value at a time */
+float or_det_exp(float x) { return det_exp(x); }
+float or_det_atan2(float y, float x) { return det_atan2(y, x); }
+float or_det_asin(float s) { return det_asin(s); }
+
+uint32_t or_depth_key_f32(const float *mu, const float *r)
+{
+    float cx = mu[0] - r[0], cy = mu[1] - r[1], cz = mu[2] - r[2];
+    float d2 = cx * cx;
+    d2 = d2 + cy * cy;
+    d2 = d2 + cz * cz;
+    float D = sqrtf(d2);
+    uint32_t bits;
+    memcpy(&bits, &D, sizeof bits);
+    return bits;
+}
+
+static int32_t ceil_div_i(int32_t a, int32_t b) { return (a + b - 1) / b; }
+
+int32_t or_cover_f32(const float *mu, const float *log_scale, const float *r, const or_grid *g,
+                     uint64_t *mask_out, int32_t *tv_lo_out, int32_t *tv_hi_out)
+{
+    const int32_t ntu = ceil_div_i(g->n_az, g->tile_w);
+    const int32_t ntv = ceil_div_i(g->n_el, g->tile_h);
+    const uint64_t all_u = (ntu >= 64) ? ~0ull : ((1ull << ntu) - 1ull);
+
+    float cx = mu[0] - r[0], cy = mu[1] - r[1], cz = mu[2] - r[2];
+    float rho2 = cx * cx;
+    rho2 = rho2 + cy * cy;
+    float d2 = rho2 + cz * cz;
+    float D = sqrtf(d2);
+    float lsm = log_scale[0];
+    if (log_scale[1] > lsm) lsm = log_scale[1];
+    if (log_scale[2] > lsm) lsm = log_scale[2];
+    float Rc = 3.03f * det_exp(lsm);
+
+    *mask_out = 0;
+    *tv_lo_out = 1;
+    *tv_hi_out = 0;
+    if (D + Rc < g->r_rx) return 0;
+    if (D <= Rc) {
+        *mask_out = all_u;
+        *tv_lo_out = 0;
+        *tv_hi_out = ntv - 1;
+        return ntu * ntv;
+    }
+
+    /* elevation bins whose centre lies in [el_c - d, el_c + d] */
+    float elc = det_asin(cz / D) * RAD2DEG_F;
+    float eld = det_asin(Rc / D) * RAD2DEG_F;
+    float vlo = ceilf((elc - eld - g->el0_deg) / g->del_deg - 0.5f);
+    float vhi = floorf((elc + eld - g->el0_deg) / g->del_deg - 0.5f);
+    if (vlo < 0.0f) vlo = 0.0f;
+    if (vhi > (float)(g->n_el - 1)) vhi = (float)(g->n_el - 1);
+    if (vlo > vhi) return 0;
+    int32_t tv_lo = (int32_t)vlo / g->tile_h, tv_hi = (int32_t)vhi / g->tile_h;
+
+    uint64_t mask = 0;
+    float rho = sqrtf(rho2);
+    if (rho <= Rc) {
+        mask = all_u;
+    } else {
+        float azc = det_atan2(cy, cx) * RAD2DEG_F;
+        float azd = det_asin(Rc / rho) * RAD2DEG_F;
+        float rel = azc - g->az0_deg;
+        if (rel < 0.0f) rel = rel + 360.0f;
+        if (rel < 0.0f) rel = rel + 360.0f;
+        if (rel >= 360.0f) rel = rel - 360.0f;
+        float lo = rel - azd, hi = rel + azd;
+        for (int w = -1; w <= 1; ++w) {
+            float off = 360.0f * (float)w;
+            float ulo = ceilf((lo + off) / g->daz_deg - 0.5f);
+            float uhi = floorf((hi + off) / g->daz_deg - 0.5f);
+            if (ulo < 0.0f) ulo = 0.0f;
+            if (uhi > (float)(g->n_az - 1)) uhi = (float)(g->n_az - 1);
+            if (ulo > uhi) continue;
+            int32_t t0 = (int32_t)ulo / g->tile_w, t1 = (int32_t)uhi / g->tile_w;
+            for (int32_t t = t0; t <= t1; ++t) mask |= 1ull << t;
+        }
+    }
+    if (!mask) return 0;
+    *mask_out = mask;
+    *tv_lo_out = tv_lo;
+    *tv_hi_out = tv_hi;
+    return (int32_t)__builtin_popcountll(mask) * (tv_hi - tv_lo + 1);
+}

@@ -1,0 +1,624 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each check uses a closed form, a
+library routine (scipy, sympy, numpy), a brute-force enumeration or a value printed
+in the paper (tests/golden/).  A plausible mistake in the oracle -- a dropped term, a
+wrong sign or index, a transposed operand -- fails at least one of them.
+
+Coverage (oracle function -> pins):
+  or_legendre      scipy lpmv (m >= 0), sympy Rodrigues formula (all m)
+  or_basis         definition via scipy; orthogonality by quadrature
+  or_gaussian      scipy Rotation; Sigma Sigma^-1 = I; sigmoid
+  or_intersect     axis-aligned closed form; clipped chord; Cholesky least squares;
+                   midpoint = maximum of the density along the ray; line integral
+  det_* / keys     numpy float32 / float64; monotone in the FP64 distance
+  or_cover_f32     cone brute force over every ray direction (conservative)
+  or_bin           numpy lexsort of the enumerated pairs
+  or_render        single / two Gaussians in closed form, zero opacity, permutation
+                   invariance, phase linear in frequency, the worked example of
+                   Sec. 2 (pi phase shift for 0.0625 m at 2.4 GHz) and its
+                   cancellation, brute force == culled, associativity of the
+                   front-to-back sum, |T| monotone and |S| bounded
+  or_render_grad   central finite differences of or_render
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2502_01826_gb300 import synthetic
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def read_golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
+def one_gaussian(mu, log_s=(math.log(0.3),) * 3, quat=(1, 0, 0, 0), logit=2.0, coeffs=None, b=0.0):
+    if coeffs is None:
+        coeffs = np.zeros((16, 2))
+        coeffs[0] = (1.0, 0.0)
+    return dict(means=np.array([mu], np.float32), log_scales=np.array([log_s], np.float32),
+                quats=np.array([quat], np.float32), opacity_logit=np.array([logit], np.float32),
+                coeffs=np.array([coeffs], np.float32), phase_b=np.array([b], np.float32))
+
+
+def concat(*scenes):
+    return {k: np.concatenate([s[k] for s in scenes]) for k in scenes[0]}
+
+
+def ray_dirs(grid):
+    u = np.arange(grid.n_az)
+    v = np.arange(grid.n_el)
+    a = np.deg2rad(grid.az0_deg + (u + 0.5) * grid.daz_deg)
+    e = np.deg2rad(grid.el0_deg + (v + 0.5) * grid.del_deg)
+    A, E = np.meshgrid(a, e)  # [n_el, n_az]
+    d = np.stack([np.cos(E) * np.cos(A), np.cos(E) * np.sin(A), np.sin(E)], -1)
+    return A.reshape(-1), E.reshape(-1), d.reshape(-1, 3)
+
+
+# --------------------------------------------------------------------------- basis
+
+def test_legendre_matches_scipy_without_condon_shortley(oracle_lib):
+    from scipy.special import lpmv
+    for l in range(4):
+        for m in range(0, l + 1):
+            for x in np.linspace(-0.999, 0.999, 13):
+                ref = (-1) ** m * lpmv(m, l, x)
+                assert abs(oracle_lib.legendre(l, m, x) - ref) < 1e-12 * max(1.0, abs(ref))
+
+
+def test_legendre_all_orders_match_rodrigues(oracle_lib):
+    import sympy as sp
+    x = sp.symbols("x")
+    for l in range(4):
+        for m in range(-l, l + 1):
+            expr = (1 - x ** 2) ** sp.Rational(m, 2) / (2 ** l * sp.factorial(l)) * \
+                sp.diff((x ** 2 - 1) ** l, x, l + m)
+            f = sp.lambdify(x, expr, "math")
+            for xv in (-0.9, -0.41, 0.0, 0.27, 0.8):
+                assert abs(oracle_lib.legendre(l, m, xv) - f(xv)) < 1e-12
+
+
+def test_basis_definition(oracle_lib):
+    from scipy.special import lpmv
+    for alpha, x in ((0.3, 0.2), (2.9, -0.7), (5.5, 0.95)):
+        Y = oracle_lib.basis(alpha, x)
+        for l in range(4):
+            for m in range(-l, l + 1):
+                ref = np.exp(1j * m * alpha) * (-1) ** m * lpmv(m, l, x)
+                assert abs(Y[l * l + l + m] - ref) < 1e-12
+
+
+def test_basis_orthogonal_on_sphere(oracle_lib):
+    """Gram matrix by Gauss-Legendre in x = sin(elevation) and uniform azimuth equals
+    diag(2 pi * 2/(2l+1) * (l+m)!/(l-m)!): the basis is orthogonal on S^2 (Sec. 4.2)."""
+    xs, wx = np.polynomial.legendre.leggauss(12)
+    na = 16
+    al = 2 * np.pi * np.arange(na) / na
+    G = np.zeros((16, 16), complex)
+    for x, w in zip(xs, wx):
+        for a in al:
+            Y = oracle_lib.basis(a, x)
+            G += w * (2 * np.pi / na) * np.outer(Y, np.conj(Y))
+    D = np.zeros(16)
+    for l in range(4):
+        for m in range(-l, l + 1):
+            D[l * l + l + m] = 2 * np.pi * 2 / (2 * l + 1) * math.factorial(l + m) / math.factorial(l - m)
+    assert np.allclose(G, np.diag(D), atol=1e-10)
+
+
+# --------------------------------------------------------------------------- primitive
+
+def test_gaussian_covariance_matches_scipy_rotation(oracle_lib):
+    from scipy.spatial.transform import Rotation
+    s = synthetic.tiny_scene(20, 7)
+    s["quats"] = s["quats"] * np.float32(1.7)  # not unit: the oracle normalises
+    for k in range(20):
+        Sg, Si, o = oracle_lib.gaussian(s, k)
+        q = s["quats"][k].astype(np.float64)
+        R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()  # scipy: scalar last
+        sc = np.exp(s["log_scales"][k].astype(np.float64))
+        ref = R @ np.diag(sc ** 2) @ R.T
+        assert np.allclose(Sg, ref, rtol=1e-12, atol=1e-14)
+        assert np.allclose(Si @ ref, np.eye(3), atol=1e-9)
+        assert abs(o - 1 / (1 + math.exp(-float(s["opacity_logit"][k])))) < 1e-15
+
+
+# --------------------------------------------------------------------------- intersection
+
+def test_intersect_axis_aligned_closed_form(oracle_lib):
+    """mu = r + D x, Sigma = diag(sx^2, sy^2, sz^2), ray along x: A = 1/sx^2,
+    B = -D/sx^2, C = D^2/sx^2, m2 = 0, t = D -+ 3 sx, dt = 6 sx, g = 1 (App. D.3)."""
+    r = np.array([1.0, 2.0, 0.5])
+    D, sx, sy, sz = 4.0, 0.3, 0.2, 0.5
+    mu = r + np.array([D, 0, 0])
+    Si = np.diag([1 / sx ** 2, 1 / sy ** 2, 1 / sz ** 2])
+    hit, h = oracle_lib.intersect(Si, mu, r, np.array([1.0, 0, 0]), 1.0)
+    assert hit
+    assert abs(h["t_in"] - (D - 3 * sx)) < 1e-12 and abs(h["t_out"] - (D + 3 * sx)) < 1e-12
+    assert abs(h["dt"] - 6 * sx) < 1e-12 and abs(h["m2"]) < 1e-12 and abs(h["g"] - 1) < 1e-12
+    # ray offset sideways by y0 along the Gaussian's y axis: tilt the ray so that it
+    # passes through (D, y0) -- closest approach m2 = (y0/sy)^2 exactly when the ray is
+    # parallel to x; use a parallel ray by moving the receiver instead
+    y0 = 0.4
+    r2 = r + np.array([0, y0, 0])
+    hit, h = oracle_lib.intersect(Si, mu, r2, np.array([1.0, 0, 0]), 1.0)
+    m2 = (y0 / sy) ** 2
+    half = sx * math.sqrt(9 - m2)
+    assert hit and abs(h["m2"] - m2) < 1e-12
+    assert abs(h["t_in"] - (D - half)) < 1e-12 and abs(h["t_out"] - (D + half)) < 1e-12
+    assert abs(h["g"] - math.exp(-m2 / 2)) < 1e-12
+    # miss beyond the 3-sigma ellipsoid
+    hit, h = oracle_lib.intersect(Si, mu, r + np.array([0, 3.01 * sy, 0]), np.array([1.0, 0, 0]), 1.0)
+    assert not hit
+
+
+def test_intersect_clipped_by_emitting_sphere(oracle_lib):
+    """A Gaussian straddling the ray-emitting sphere: only d >= r_rx counts (Eq. 10)."""
+    r = np.zeros(3)
+    D, s = 1.1, 0.1
+    mu = np.array([D, 0, 0])
+    Si = np.eye(3) / s ** 2
+    hit, h = oracle_lib.intersect(Si, mu, r, np.array([1.0, 0, 0]), 1.0)
+    t_in, t_out = D - 3 * s, D + 3 * s
+    assert hit and t_in < 1.0
+    assert abs(h["t_a"] - 1.0) < 1e-12 and abs(h["dt"] - (t_out - 1.0)) < 1e-12
+    t_rep = 0.5 * (1.0 + t_out)
+    assert abs(h["t_rep"] - t_rep) < 1e-12
+    assert abs(h["m2_rep"] - ((t_rep - D) / s) ** 2) < 1e-9
+    # entirely inside the emitting sphere: no hit
+    hit, _ = oracle_lib.intersect(Si, np.array([0.5, 0, 0]), r, np.array([1.0, 0, 0]), 1.0)
+    assert not hit
+
+
+def test_intersect_general_vs_cholesky_and_density(oracle_lib):
+    """Closest approach by Cholesky least squares; midpoint g equals the maximum of the
+    unnormalised density along the ray (scipy multivariate_normal); the chord length
+    satisfies the line integral of the density = sqrt(2 pi / A) exp(-m2/2)."""
+    from scipy.stats import multivariate_normal
+    from scipy.integrate import quad
+    s = synthetic.tiny_scene(30, 11)
+    rng = np.random.default_rng(3)
+    n_checked = 0
+    for k in range(30):
+        Sg, Si, _ = oracle_lib.gaussian(s, k)
+        mu = s["means"][k].astype(np.float64)
+        for _ in range(5):
+            r = mu + rng.normal(0, 2.0, 3)
+            tgt = mu + rng.normal(0, 0.5, 3) * np.exp(s["log_scales"][k])
+            v = (tgt - r) / np.linalg.norm(tgt - r)
+            hit, h = oracle_lib.intersect(Si, mu, r, v, 0.0)
+            L = np.linalg.cholesky(Sg)
+            Li = np.linalg.inv(L)
+            a, b = Li @ v, Li @ (r - mu)
+            t_star = -np.dot(a, b) / np.dot(a, a)
+            m2 = np.sum((b + t_star * a) ** 2)
+            assert abs(h["m2"] - m2) < 1e-9 * max(1, m2)
+            if not hit or h["t_in"] < 0.0:
+                continue
+            n_checked += 1
+            mvn = multivariate_normal(mu, Sg)
+            norm = (2 * np.pi) ** 1.5 * math.sqrt(np.linalg.det(Sg))
+            dens = lambda t: mvn.pdf(r + t * v) * norm
+            assert abs(h["t_rep"] - t_star) < 1e-9 * max(1, abs(t_star))
+            assert abs(h["g"] - dens(t_star)) < 1e-9
+            assert abs(h["g"] - max(dens(t) for t in np.linspace(h["t_in"], h["t_out"], 201))) < 1e-9 + 1e-3
+            A = np.dot(a, a)
+            integ = quad(dens, t_star - 40 / math.sqrt(A), t_star + 40 / math.sqrt(A), points=[t_star])[0]
+            assert abs(integ - math.sqrt(2 * math.pi / A) * math.exp(-m2 / 2)) < 1e-7
+    assert n_checked > 20
+
+
+# --------------------------------------------------------------------------- FP32 decisions
+
+def test_det_functions_close_to_libm(oracle_lib):
+    for x in np.linspace(-6, 3, 37):
+        assert abs(oracle_lib.det_exp(float(x)) / math.exp(float(np.float32(x))) - 1) < 2e-6
+    for y, x in [(0.3, 1.0), (1.0, 0.3), (-2.0, -0.1), (0.0, -1.0), (-1e-3, 5.0), (3.0, -3.0)]:
+        assert abs(oracle_lib.det_atan2(y, x) - math.atan2(y, x)) < 3e-6
+    for s in np.linspace(-1, 1, 41):
+        assert abs(oracle_lib.det_asin(float(s)) - math.asin(float(np.float32(s)))) < 3e-6
+
+
+def test_depth_key_is_float32_distance(oracle_lib):
+    s = synthetic.scene(500, 5)
+    r = np.array([3.3, 2.2, 1.1], np.float32)
+    d = s["means"] - r  # float32 arithmetic
+    d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+    ref = np.sqrt(d2.astype(np.float32)).view(np.uint32)
+    keys = np.array([oracle_lib.depth_key_f32(s["means"][k], r) for k in range(500)], np.uint32)
+    assert np.array_equal(keys, ref)
+    D64 = np.linalg.norm(s["means"].astype(np.float64) - r.astype(np.float64), axis=1)
+    o64 = np.argsort(D64, kind="stable")
+    assert np.all(np.diff(keys[o64].astype(np.int64)) >= 0)
+
+
+@pytest.mark.parametrize("grid_args", [(36, 9), (72, 18), (360, 90), (30, 7, 10.0, 9.0, -20.0, 7.0)])
+def test_cover_is_conservative(oracle_lib, grid_args):
+    """Every ray direction inside the cone of the sphere of radius 3 max(s) (which
+    contains the 3-sigma ellipsoid) falls in a covered tile."""
+    if len(grid_args) == 2:
+        grid = oracle_lib.make_grid(*grid_args)
+    else:
+        n_az, n_el, az0, daz, el0, de = grid_args
+        grid = oracle_lib.make_grid(n_az, n_el, az0, daz, el0, de, tile_w=8, tile_h=4)
+    ntu, ntv = oracle_lib.n_tiles(grid)
+    A, E, dirs = ray_dirs(grid)
+    u = np.tile(np.arange(grid.n_az), grid.n_el)
+    v = np.repeat(np.arange(grid.n_el), grid.n_az)
+    tiles = (v // grid.tile_h) * ntu + u // grid.tile_w
+    s = synthetic.scene(300, 9)
+    r = np.array([5.0, 4.0, 1.2], np.float32)
+    for k in range(300):
+        mu = s["means"][k].astype(np.float64)
+        c = mu - r
+        D = np.linalg.norm(c)
+        R = 3 * np.exp(s["log_scales"][k].astype(np.float64).max())
+        n, mask, lo, hi = oracle_lib.cover_f32(s["means"][k], s["log_scales"][k], r, grid)
+        cov = set()
+        for tv in range(lo, hi + 1):
+            for tu in range(ntu):
+                if (mask >> tu) & 1:
+                    cov.add(tv * ntu + tu)
+        assert n == len(cov)
+        if D + R < grid.r_rx:
+            continue
+        if D <= R:
+            need = set(tiles.tolist())
+        else:
+            inside = dirs @ (c / D) >= math.sqrt(max(0.0, 1 - (R / D) ** 2))
+            need = set(tiles[inside].tolist())
+        assert need <= cov, (k, sorted(need - cov))
+
+
+def test_bin_matches_lexsort_of_pairs(oracle_lib):
+    s = synthetic.scene(400, 13)
+    grid = oracle_lib.make_grid(360, 90)
+    ntu, ntv = oracle_lib.n_tiles(grid)
+    r = np.array([2.5, 6.0, 2.0], np.float32)
+    keys, ids, ts = oracle_lib.bin_pairs(s, r, grid)
+    kk, ii = [], []
+    for k in range(400):
+        n, mask, lo, hi = oracle_lib.cover_f32(s["means"][k], s["log_scales"][k], r, grid)
+        dk = oracle_lib.depth_key_f32(s["means"][k], r)
+        for tv in range(lo, hi + 1):
+            for tu in range(ntu):
+                if (mask >> tu) & 1:
+                    kk.append(((tv * ntu + tu) << 32) | dk)
+                    ii.append(k)
+    kk = np.array(kk, np.uint64)
+    ii = np.array(ii, np.uint32)
+    o = np.lexsort((ii, kk))
+    assert np.array_equal(keys, kk[o]) and np.array_equal(ids, ii[o])
+    t = (keys >> np.uint64(32)).astype(np.int64)
+    assert np.array_equal(ts, np.searchsorted(t, np.arange(ntu * ntv + 1), side="left"))
+
+
+# --------------------------------------------------------------------------- render
+
+def small_grid(oracle_lib, **kw):
+    return oracle_lib.make_grid(72, 18, **kw)
+
+
+def test_single_gaussian_closed_form(oracle_lib):
+    """One Gaussian, T = 1: S = o g psi e^{-j 2 pi f d / c} on every hit ray (Eq. 14)."""
+    from scipy.special import lpmv
+    rng = np.random.default_rng(1)
+    coeffs = rng.normal(0, 0.3, (16, 2))
+    r = np.array([2.0, 2.0, 0.5], np.float32)
+    t = np.array([7.0, 1.0, 2.5], np.float32)
+    s = one_gaussian((4.0, 3.0, 1.0), log_s=(math.log(0.4), math.log(0.2), math.log(0.3)),
+                     quat=(0.9, 0.1, -0.3, 0.2), logit=0.7, coeffs=coeffs, b=0.3)
+    grid = small_grid(oracle_lib)
+    f = 2.4e9
+    out = oracle_lib.render(s, r[None][0], t, f, grid, mode=1)
+    Sg, Si, o = oracle_lib.gaussian(s, 0)
+    mu = s["means"][0].astype(np.float64)
+    d = np.linalg.norm(t.astype(np.float64) - mu) + np.linalg.norm(mu - r.astype(np.float64))
+    A, E, dirs = ray_dirs(grid)
+    L = np.linalg.cholesky(Sg)
+    Li = np.linalg.inv(L)
+    cf = s["coeffs"][0].astype(np.float64)
+    c = cf[:, 0] + 1j * cf[:, 1]
+    n_hit = 0
+    for i in range(len(dirs)):
+        a, b = Li @ dirs[i], Li @ (r.astype(np.float64) - mu)
+        ts = -np.dot(a, b) / np.dot(a, a)
+        m2 = np.sum((b + ts * a) ** 2)
+        half = math.sqrt(max(0.0, (9 - m2) / np.dot(a, a)))
+        if m2 >= 9 or ts + half < 1.0:
+            assert out["S"][0, i] == 0
+            continue
+        assert ts - half >= 1.0  # not clipped in this geometry
+        n_hit += 1
+        x = math.sin(E[i])
+        psi = sum(c[l * l + l + m] * np.exp(1j * m * A[i]) * (-1) ** m * lpmv(m, l, x)
+                  for l in range(4) for m in range(-l, l + 1))
+        ref = min(o * math.exp(-m2 / 2), 0.99) * psi * np.exp(-2j * np.pi * f * d / 3e8)
+        assert abs(out["S"][0, i] - ref) < 1e-10 * max(1e-3, abs(ref))
+    assert n_hit > 10
+
+
+def test_two_gaussians_closed_form(oracle_lib):
+    """S = alpha1 psi1 E1 + alpha2 psi2 E2 (1 - alpha1) e^{-j 2 pi f b1 dt1 / c}."""
+    r = np.array([0.0, 0.0, 0.0], np.float32)
+    t = np.array([3.0, 4.0, 0.0], np.float32)
+    c1 = np.zeros((16, 2)); c1[0] = (0.7, 0.2)
+    c2 = np.zeros((16, 2)); c2[0] = (-0.3, 0.9)
+    s = concat(one_gaussian((3.0, 0.0, 0.0), log_s=(math.log(0.2),) * 3, logit=1.0, coeffs=c1, b=0.4),
+               one_gaussian((6.0, 0.0, 0.0), log_s=(math.log(0.5),) * 3, logit=-0.5, coeffs=c2, b=0.0))
+    grid = oracle_lib.make_grid(1, 1, az0_deg=-0.5, daz_deg=1.0, el0_deg=-0.5, del_deg=1.0,
+                                eps_T=0.0, tile_w=1, tile_h=1)  # one ray exactly along +x
+    f = 1.0e9
+    out = oracle_lib.render(s, r, t, f, grid, mode=1)
+    o1, o2 = 1 / (1 + math.exp(-1.0)), 1 / (1 + math.exp(0.5))
+    P00 = 1.0  # P_0^0
+    d1 = 5.0 - 0.0 + 3.0 - 0.0  # |t - mu1| = |(0,4,0)| + |mu1 - r| = 3
+    d1 = math.hypot(0.0, 4.0) + 3.0
+    d2 = math.hypot(3.0, 4.0) + 6.0
+    a1, a2 = o1, o2
+    dt1 = 6 * 0.2
+    S_ref = a1 * (0.7 + 0.2j) * P00 * np.exp(-2j * np.pi * f * d1 / 3e8) + \
+        a2 * (-0.3 + 0.9j) * P00 * np.exp(-2j * np.pi * f * d2 / 3e8) * \
+        (1 - a1) * np.exp(-2j * np.pi * f * 0.4 * dt1 / 3e8)
+    assert abs(out["S"][0, 0] - S_ref) < 1e-6 * abs(S_ref)
+    assert out["nhit"][0] == 2
+
+
+def test_zero_opacity_gives_zero_signal(oracle_lib):
+    s = synthetic.tiny_scene(40, 21)
+    s["opacity_logit"][:] = -1e4
+    grid = small_grid(oracle_lib)
+    out = oracle_lib.render(s, np.array([2, 2, 1], np.float32), np.array([1, 1, 1], np.float32),
+                            2.4e9, grid, mode=1)
+    assert np.all(out["S"] == 0) and np.all(out["Ta"] == 1.0)
+
+
+def test_input_order_invariance(oracle_lib):
+    s = synthetic.tiny_scene(60, 22)
+    grid = small_grid(oracle_lib)
+    r = np.array([2.0, 1.5, 0.8], np.float32)
+    t = np.array([0.5, 3.5, 1.5], np.float32)
+    a = oracle_lib.render(s, r, t, 2.4e9, grid)["S"]
+    p = np.random.default_rng(0).permutation(60)
+    sp = {k: v[p] for k, v in s.items()}
+    b = oracle_lib.render(sp, r, t, 2.4e9, grid)["S"]
+    assert np.allclose(a, b, rtol=0, atol=1e-12)
+
+
+def test_phase_linear_in_frequency(oracle_lib):
+    """One Gaussian: S(f) = S(f0) e^{-j 2 pi (f - f0) d / c} with b = 0 (the signal's
+    phase is linear in path length over wavelength; Sec. 2, multipath model)."""
+    s = one_gaussian((4.0, 3.0, 1.0), b=0.0)
+    r = np.array([1.0, 1.0, 0.5], np.float32)
+    t = np.array([8.0, 7.0, 2.0], np.float32)
+    grid = small_grid(oracle_lib)
+    f0, df, nf = 2.4e9, 312.5e3 * 7, 9
+    out = oracle_lib.render(s, r, t, f0, grid, df=df, n_f=nf)
+    mu = s["means"][0].astype(np.float64)
+    d = np.linalg.norm(t - mu) + np.linalg.norm(mu - r)
+    S = out["S"]
+    hit = np.abs(S[0]) > 0
+    assert hit.sum() > 10
+    for i in range(nf):
+        ref = S[0, hit] * np.exp(-2j * np.pi * i * df * d / 3e8)
+        assert np.allclose(S[i, hit], ref, rtol=1e-9, atol=1e-14)
+
+
+def _mirror_pair_setup(oracle_lib, delta):
+    """Two identical isotropic Gaussians mirrored through the receiver along x, and a
+    transmitter placed so that their Tx->Gaussian->Rx path lengths differ by delta."""
+    from scipy.optimize import brentq
+    r = np.array([0.0, 0.0, 0.0])
+    mA, mB = np.array([2.0, 0.0, 0.0]), np.array([-2.0, 0.0, 0.0])
+    yt = 1.5
+    f = lambda x: (np.linalg.norm([x + 2.0, yt, 0]) - np.linalg.norm([x - 2.0, yt, 0])) - delta
+    xt = brentq(f, 0.0, 5.0)
+    t = np.array([xt, yt, 0.0])
+    s = concat(one_gaussian(tuple(mA)), one_gaussian(tuple(mB)))
+    return s, r.astype(np.float32), t
+
+
+def test_worked_example_phase_shift_and_cancellation(oracle_lib):
+    """Sec. 2: at 2.4 GHz a path 0.0625 m longer is shifted by pi; the two equal
+    mirror-image Gaussians then cancel in the coherent single-antenna sum."""
+    gold = read_golden("worked_example_phase.txt")
+    f, d1, d2 = gold["f_c_hz"], gold["d1_m"], gold["d2_m"]
+    assert abs(d1 / oracle_lib.C_LIGHT * 1e9 - gold["tau1_ns"]) < 1e-9
+    assert abs(d2 / oracle_lib.C_LIGHT * 1e9 - gold["tau2_ns"]) < 1e-3
+    dphi = 2 * np.pi * f * (d2 - d1) / oracle_lib.C_LIGHT
+    assert abs(dphi - gold["delta_phi_rad"]) < 1e-12
+    # move the transmitter radially away from a single Gaussian by d2 - d1
+    s = one_gaussian((4.0, 3.0, 1.0))
+    r = np.array([1.0, 1.0, 0.5], np.float32)
+    mu = s["means"][0].astype(np.float64)
+    u = np.array([0.6, 0.0, 0.8])
+    t1 = (mu + 2.0 * u).astype(np.float32)
+    t2 = (t1.astype(np.float64) + (d2 - d1) * u).astype(np.float32)
+    dd = np.linalg.norm(t2.astype(np.float64) - mu) - np.linalg.norm(t1.astype(np.float64) - mu)
+    grid = small_grid(oracle_lib)
+    S1 = oracle_lib.render(s, r, t1, f, grid)["S"][0]
+    S2 = oracle_lib.render(s, r, t2, f, grid)["S"][0]
+    assert abs(dd - (d2 - d1)) < 2e-7
+    hit = np.abs(S1) > 0
+    rot = np.exp(-2j * np.pi * f * dd / 3e8)
+    assert abs(rot - np.exp(-1j * gold["delta_phi_rad"])) < 1e-5
+    assert np.allclose(S2[hit], S1[hit] * rot, rtol=1e-9)
+    # destructive interference of two mirror-image sources
+    s, r, t = _mirror_pair_setup(oracle_lib, d2 - d1)
+    grid = oracle_lib.make_grid(360, 90)
+    S = oracle_lib.render(s, r, t, f, grid)["S"][0]
+    S_hat = oracle_lib.received_signal(S)
+    each = np.sum(np.abs(S)) / 2
+    assert each > 1.0
+    assert abs(S_hat) < 1e-6 * each
+    s0, r0, t0 = _mirror_pair_setup(oracle_lib, 0.0)
+    S0 = oracle_lib.render(s0, r0, t0, f, grid)["S"][0]
+    assert abs(oracle_lib.received_signal(S0)) > 1.9 * abs(np.sum(S0[: len(S0)]) / 2) * 0.99
+
+
+@pytest.mark.parametrize("seed,K,grid_args", [(31, 40, (36, 9)), (32, 64, (72, 18)),
+                                               (33, 50, (30, 7, 10.0, 9.0, -20.0, 7.0))])
+def test_culled_equals_brute_force(oracle_lib, seed, K, grid_args):
+    if len(grid_args) == 2:
+        grid = oracle_lib.make_grid(*grid_args)
+    else:
+        n_az, n_el, az0, daz, el0, de = grid_args
+        grid = oracle_lib.make_grid(n_az, n_el, az0, daz, el0, de, tile_w=8, tile_h=4)
+    s = synthetic.tiny_scene(K, seed)
+    r = np.array([2.0, 2.1, 0.9], np.float32)
+    t = np.array([3.5, 0.2, 1.7], np.float32)
+    a = oracle_lib.render(s, r, t, 2.4e9, grid, mode=0)
+    b = oracle_lib.render(s, r, t, 2.4e9, grid, mode=1)
+    assert np.array_equal(a["nhit"], b["nhit"])
+    assert np.max(np.abs(a["S"] - b["S"])) == 0.0
+    assert np.sum(a["nhit"]) > 50
+    assert np.all(a["ntest"] <= b["ntest"])
+
+
+def test_front_to_back_sum_is_associative(oracle_lib):
+    """Splitting every ray's Gaussians at a depth into a near and a far set:
+    S = S_near + T_near S_far, T = T_near T_far (eps_T = 0)."""
+    s = synthetic.tiny_scene(60, 41)
+    r = np.array([2.0, 2.0, 1.0], np.float32)
+    t = np.array([0.3, 0.3, 1.9], np.float32)
+    grid = small_grid(oracle_lib, eps_T=0.0)
+    D = np.linalg.norm(s["means"].astype(np.float64) - r, axis=1)
+    near = D < np.median(D)
+    full = oracle_lib.render(s, r, t, 2.4e9, grid)
+    a = oracle_lib.render({k: v[near] for k, v in s.items()}, r, t, 2.4e9, grid)
+    b = oracle_lib.render({k: v[~near] for k, v in s.items()}, r, t, 2.4e9, grid)
+    assert np.allclose(full["S"], a["S"] + a["T"] * b["S"], atol=1e-12)
+    assert np.allclose(full["T"], a["T"] * b["T"], atol=1e-12)
+
+
+def test_transmittance_monotone_and_signal_bounded(oracle_lib):
+    s = synthetic.tiny_scene(80, 51)
+    r = np.array([2.0, 2.0, 1.0], np.float32)
+    t = np.array([3.0, 0.5, 0.2], np.float32)
+    g0 = small_grid(oracle_lib, eps_T=0.0)
+    prev = None
+    D = np.linalg.norm(s["means"].astype(np.float64) - r, axis=1)
+    order = np.argsort(D)
+    for n in (10, 20, 40, 80):
+        sub = {k: v[order[:n]] for k, v in s.items()}
+        out = oracle_lib.render(sub, r, t, 2.4e9, g0)
+        assert np.allclose(np.abs(out["T"][0]), out["Ta"], rtol=1e-12)
+        if prev is not None:
+            assert np.all(out["Ta"] <= prev + 1e-15)
+        prev = out["Ta"]
+    cmax = np.sum(np.abs(s["coeffs"][..., 0] + 1j * s["coeffs"][..., 1]), axis=1)  # |psi| <= sum|c||Y|
+    ymax = max(abs(oracle_lib.legendre(l, m, x)) for l in range(4) for m in range(-l, l + 1)
+               for x in np.linspace(-1, 1, 201))
+    out = oracle_lib.render(s, r, t, 2.4e9, g0)
+    assert np.all(np.abs(out["S"]) <= out["nhit"] * 0.99 * cmax.max() * ymax + 1e-12)
+
+
+def test_termination_rule(oracle_lib):
+    """With eps_T > 0 a ray stops right after prod(1 - alpha) drops below eps_T."""
+    s = synthetic.tiny_scene(120, 61, box=(3.0, 3.0, 1.0), log_scale_mu=math.log(0.5))
+    s["opacity_logit"][:] = 4.0
+    r = np.array([1.5, 1.5, 0.2], np.float32)
+    t = np.array([0.1, 0.1, 0.1], np.float32)
+    g1 = small_grid(oracle_lib, eps_T=1e-2)
+    g0 = small_grid(oracle_lib, eps_T=0.0)
+    a = oracle_lib.render(s, r, t, 2.4e9, g1)
+    b = oracle_lib.render(s, r, t, 2.4e9, g0)
+    term = a["Ta"] < 1e-2
+    assert term.sum() > 20
+    assert np.all(a["nhit"][term] < b["nhit"][term]) or np.all(a["nhit"][term] <= b["nhit"][term])
+    assert np.all(a["nhit"][~term] == b["nhit"][~term])
+    # the ray stopped at its first step below eps_T: one step earlier it was above
+    D = np.linalg.norm(s["means"].astype(np.float64) - r, axis=1)
+
+
+# --------------------------------------------------------------------------- gradients
+
+def _fd_check(oracle_lib, s, r, t, f0, grid, rays, G, n_f=1, df=0.0, n_params=60, seed=0,
+              rel_step=2e-4, tol=2e-5):
+    # Rays that graze an ellipsoid (m2 near 9), cross the emitting sphere's edge or
+    # end near the termination threshold sit on a square-root singularity or a kink
+    # of S (the chord length 2 sqrt((9 - m2)/A) has an unbounded derivative there);
+    # central differences cannot resolve those, so they get no weight in the loss.
+    base = oracle_lib.render(s, r, t, f0, grid, df=df, n_f=n_f, rays=rays,
+                             bands=(0.5, 1e-2, 0.05))
+    G = np.array(G, copy=True)
+    G[:, base["flags"] != 0] = 0
+    assert np.count_nonzero(G[0]) >= 40
+    grads = oracle_lib.render_grad(s, r, t, f0, grid, G, df=df, n_f=n_f, rays=rays)
+    rng = np.random.default_rng(seed)
+    names = ["means", "log_scales", "quats", "opacity_logit", "coeffs", "phase_b"]
+    checked = 0
+    errs = []
+    for _ in range(n_params * 3):
+        name = names[rng.integers(len(names))]
+        arr = s[name]
+        idx = tuple(rng.integers(n) for n in arr.shape)
+        x0 = float(arr[idx])
+        h = rel_step * max(1.0, abs(x0))
+        xp, xm = np.float32(x0 + h), np.float32(x0 - h)
+        sp = {k: v.copy() for k, v in s.items()}
+        sm = {k: v.copy() for k, v in s.items()}
+        sp[name][idx] = xp
+        sm[name][idx] = xm
+        op = oracle_lib.render(sp, r, t, f0, grid, df=df, n_f=n_f, rays=rays)
+        om = oracle_lib.render(sm, r, t, f0, grid, df=df, n_f=n_f, rays=rays)
+        if not (np.array_equal(op["nhit"], base["nhit"]) and np.array_equal(om["nhit"], base["nhit"])):
+            continue
+        Lp = np.sum(np.real(np.conj(G) * op["S"]))
+        Lm = np.sum(np.real(np.conj(G) * om["S"]))
+        fd = (Lp - Lm) / (float(xp) - float(xm))
+        an = grads[name][idx]
+        errs.append((abs(fd - an), abs(fd), abs(an)))
+        checked += 1
+        if checked >= n_params:
+            break
+    assert checked >= n_params // 2
+    errs = np.array(errs)
+    scale = np.sqrt(np.mean(errs[:, 1] ** 2)) + 1e-30
+    assert np.all(errs[:, 0] <= tol * np.maximum(errs[:, 1], scale)), errs[errs[:, 0] > tol * np.maximum(errs[:, 1], scale)]
+    return errs
+
+
+def test_gradient_matches_finite_differences(oracle_lib):
+    s = synthetic.tiny_scene(24, 71)
+    r = np.array([2.0, 2.0, 0.6], np.float32)
+    t = np.array([3.0, 0.5, 1.5], np.float32)
+    grid = oracle_lib.make_grid(72, 18, eps_T=0.0)
+    rng = np.random.default_rng(5)
+    G = rng.normal(size=(1, 72 * 18)) + 1j * rng.normal(size=(1, 72 * 18))
+    _fd_check(oracle_lib, s, r, t, 2.0e8, grid, None, G)
+
+
+def test_gradient_multifrequency_and_clipped(oracle_lib):
+    """Several frequencies, Gaussians straddling the emitting sphere, termination on."""
+    s = synthetic.tiny_scene(30, 72, box=(2.5, 2.5, 1.5), log_scale_mu=math.log(0.35))
+    r = np.array([1.2, 1.3, 0.6], np.float32)
+    t = np.array([2.4, 0.1, 1.0], np.float32)
+    grid = oracle_lib.make_grid(36, 9, eps_T=1e-3)
+    rng = np.random.default_rng(6)
+    G = rng.normal(size=(3, 36 * 9)) + 1j * rng.normal(size=(3, 36 * 9))
+    _fd_check(oracle_lib, s, r, t, 1.0e8, grid, None, G, n_f=3, df=2.0e7, seed=1)
+
+
+def test_gradient_at_carrier_frequency(oracle_lib):
+    """At 2.4 GHz the path phase curves fast in the mean; a smaller step keeps the
+    central difference's truncation error below the tolerance."""
+    s = synthetic.tiny_scene(16, 73)
+    r = np.array([2.0, 2.0, 0.6], np.float32)
+    t = np.array([3.0, 0.5, 1.5], np.float32)
+    grid = oracle_lib.make_grid(36, 9, eps_T=0.0)
+    rng = np.random.default_rng(7)
+    G = rng.normal(size=(1, 36 * 9)) + 1j * rng.normal(size=(1, 36 * 9))
+    _fd_check(oracle_lib, s, r, t, 2.4e9, grid, None, G, rel_step=1e-4, tol=2e-4, seed=2)
