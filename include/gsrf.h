@@ -1,0 +1,172 @@
+/*
+ * gsrf.h -- C ABI of the GB300 (sm_103a) GSRF render library, libgsrf.so.
+ *
+ * GSRF (arXiv 2502.01826) renders the RF signal received at a receiver from a scene
+ * of complex-valued 3D Gaussians: orthographic splatting of the Gaussians onto the
+ * receiver's azimuth x elevation ray grid (Sec. 4.3), a Fourier-Legendre radiance per
+ * ray (Sec. 4.2, Eq. 9), and complex front-to-back accumulation along every ray
+ * (Sec. 4.4, Eq. 14; App. A), reduced to the received spectrum, RSSI or CSI.  The
+ * calls below follow the paper's statement of the problem (Sec. 4.1): given the
+ * transmitter position t, receiver positions r_i and the scene parameters theta,
+ * synthesise S_i.  They run as CUDA kernels on the caller's stream; nothing here
+ * falls back to the CPU.
+ *
+ * Conventions (all calls):
+ *   - Pointers marked [dev] are device pointers, [host] host pointers.  The caller
+ *     owns every buffer: inputs, outputs and one workspace.  The library allocates no
+ *     device memory and never synchronises the stream, except gsrf_read_status.
+ *   - Arrays are C-contiguous FP32 unless stated; complex values are interleaved
+ *     (re, im) pairs.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - Argument errors return synchronously (nothing is launched).  Conditions met on
+ *     the device (pair capacity exceeded, non-finite parameters, a bounded wait that
+ *     ran out) set the status word in the workspace; gsrf_read_status reads it.  No
+ *     call aborts, traps or throws.
+ *   - The workspace carries state from gsrf_project to gsrf_bin to gsrf_render_fwd /
+ *     gsrf_render_bwd: call them in that order with the same plan and workspace.
+ *
+ * Readings of the paper built into the arithmetic (each also listed in the
+ * repository's design notes): alpha_k = min(sigmoid(opacity_k) * exp(-m2_rep/2),
+ * alpha_max); the complex transmittance of a Gaussian is (1 - alpha_k)
+ * exp(-j 2 pi f b_k dt_k / c); every Gaussian re-radiates with the path phase
+ * exp(-j 2 pi f (|t - mu_k| + |mu_k - r|) / c); 3-sigma = Mahalanobis^2 9; the
+ * Fourier-Legendre basis is evaluated at each ray's (azimuth, sin elevation) without
+ * the Condon-Shortley phase; depth order is ascending FP32 |mu_k - r|, ties by index;
+ * a ray hits iff m2 < 9 and t_out >= r_rx, with t_in clipped to r_rx; c = 3e8 m/s.
+ */
+#ifndef GSRF_H
+#define GSRF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GSRF_OK = 0,
+    GSRF_ERR_INVALID_ARG = 1,  /* a size, pointer or grid field is out of range */
+    GSRF_ERR_CUDA = 2,         /* a CUDA launch or copy failed */
+    GSRF_ERR_CAPACITY = 3,     /* more (tile, Gaussian) pairs than plan.pair_capacity */
+    GSRF_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out */
+    GSRF_ERR_NONFINITE = 5,    /* a Gaussian parameter is NaN or infinite */
+    GSRF_ERR_UNSUPPORTED = 6   /* a configuration this build does not implement */
+} gsrf_status;
+
+/* The receiver's ray grid (Sec. 4.3, Eqs. 10-12): ray (u, v) points at azimuth
+ * az0 + (u + 1/2) daz and elevation el0 + (v + 1/2) del (degrees), i.e. at the
+ * centre of the one-bin cell that Eq. 12 maps it to. */
+typedef struct {
+    int32_t n_az, n_el;        /* rays along azimuth / elevation, >= 1 */
+    float az0_deg, daz_deg;    /* azimuth of the grid origin (|az0| <= 360), bin width > 0 */
+    float el0_deg, del_deg;    /* elevation of the grid origin, bin height > 0 */
+    float r_rx;                /* radius of the ray-emitting sphere (App. E table: 1.0 m) */
+    float eps_T;               /* stop a ray once prod(1 - alpha) < eps_T; 0 = never */
+    float alpha_max;           /* clamp on alpha, in (0, 1) (0.99 keeps 1/(1-alpha) finite) */
+    int32_t tile_w, tile_h;    /* rays per tile (App. E: 16 x 16); this build: 16 x 16 */
+} gsrf_grid;
+
+/* Scene parameters theta, [dev], structure-of-arrays, n Gaussians (Sec. 4.2). */
+typedef struct {
+    int64_t n;                 /* number of Gaussians, 0 <= n < 2^31 */
+    const float *means;        /* [n,3] mu_k, metres */
+    const float *log_scales;   /* [n,3] log of the diagonal of S_k */
+    const float *quats;        /* [n,4] rotation R_k as a quaternion (w,x,y,z), any non-zero norm */
+    const float *opacity_logit;/* [n]   opacity before the sigmoid */
+    const float *coeffs;       /* [n,16,2] Fourier-Legendre coefficients c_{l,m}, index l*l+l+m */
+    const float *phase_b;      /* [n] excess-phase coefficient b_k of the transmittance, or NULL (= 0) */
+} gsrf_gaussians;
+
+/* One render problem: n_rx receivers of one scene against one transmitter, at the
+ * n_f frequencies f0 + i*df (i < n_f). */
+typedef struct {
+    int64_t n_gauss;           /* Gaussians in the scene */
+    int32_t n_rx;              /* receivers, >= 1 */
+    int32_t n_f;               /* frequencies, 1 <= n_f <= 64 */
+    double f0_hz, df_hz;       /* first frequency and spacing (Hz), f0 > 0 */
+    gsrf_grid grid;
+    int64_t pair_capacity;     /* room for (tile, Gaussian) instances over all receivers */
+} gsrf_plan;
+
+/* Bytes of workspace a plan needs (256-byte aligned base required). [host] out. */
+gsrf_status gsrf_workspace_size(const gsrf_plan *plan, size_t *bytes);
+
+/* Byte offsets inside the workspace of the arrays tests and tools may inspect after
+ * gsrf_bin: sorted 64-bit splat keys (tile << 32 | FP32 depth bits) [uint64], their
+ * Gaussian ids [uint32], both over all receivers back to back; per receiver the first
+ * pair (int64, [n_rx + 1]); per receiver and tile the list start relative to the
+ * receiver's first pair (uint32, [n_rx][n_tiles + 1]). */
+typedef struct {
+    size_t pair_keys, pair_ids, rx_pair_base, tile_start;
+    size_t status;
+    int32_t n_tiles_u, n_tiles_v;
+} gsrf_layout;
+gsrf_status gsrf_workspace_layout(const gsrf_plan *plan, gsrf_layout *out);
+
+/* Step 1 -- Alg. 1 line 2 ("sphericalGaussian", Sec. 4.3): per Gaussian the
+ * whitening matrix diag(1/s) R^T and opacity; per (receiver, Gaussian) the whitened
+ * receiver offset, the FP32 depth |mu - r| (sort key), the set of tiles the Gaussian
+ * may touch (conservative: every ray that can hit it lies in one of them) and the
+ * path phase exp(-j 2 pi f0 d / c), d = |t - mu| + |mu - r|, range-reduced in FP64.
+ *   rx_pos [dev] [n_rx,3]; tx_pos [dev] [3].
+ * Clears the status word.  Non-finite parameters set GSRF_ERR_NONFINITE. */
+gsrf_status gsrf_project(const gsrf_plan *plan, const gsrf_gaussians *g, const float *rx_pos,
+                         const float *tx_pos, void *workspace, size_t ws_bytes, void *stream);
+
+/* Step 2 -- Alg. 1 lines 4-5 and App. E: one 64-bit key per (tile, Gaussian) pair,
+ * high 32 bits the tile index (tv * n_tiles_u + tu), low 32 bits the FP32 depth;
+ * all pairs of a receiver sorted by key, ties by Gaussian index (a stable radix sort
+ * written for this library), and each tile's [start, end) range.  If the pairs of all
+ * receivers exceed plan.pair_capacity the status word gets GSRF_ERR_CAPACITY and the
+ * required count; later steps then write zeros. */
+gsrf_status gsrf_bin(const gsrf_plan *plan, void *workspace, size_t ws_bytes, void *stream);
+
+/* Step 3 -- Alg. 1 lines 6-12, Eq. 14: every ray walks its tile's list front to back,
+ * intersects the 3-sigma ellipsoid (App. D.3), weights by the Gaussian at the midpoint
+ * of the chord beyond r_rx (App. A.2), evaluates the Fourier-Legendre radiance and
+ * accumulates S += alpha psi e^{-j phi} T, T *= (1 - alpha) e^{-j theta}.
+ *   out_rays  [dev] [n_rx][n_f][n_el][n_az][2]  per-ray received signal S.
+ *   ray_state [dev] NULL, or gsrf_ray_state_bytes(plan) bytes the backward needs. */
+gsrf_status gsrf_render_fwd(const gsrf_plan *plan, const gsrf_gaussians *g, void *workspace,
+                            size_t ws_bytes, float *out_rays, void *ray_state, void *stream);
+size_t gsrf_ray_state_bytes(const gsrf_plan *plan);
+
+/* Convenience: gsrf_project + gsrf_bin + gsrf_render_fwd in one call. */
+gsrf_status gsrf_render(const gsrf_plan *plan, const gsrf_gaussians *g, const float *rx_pos,
+                        const float *tx_pos, void *workspace, size_t ws_bytes, float *out_rays,
+                        void *ray_state, void *stream);
+
+/* Received signal from per-ray signals (Sec. 4.4, loss paragraph):
+ *   GSRF_SIG_COMPLEX_SUM  out [n_rx][n_f][2]  S_hat = sum over rays of S_{u,v}
+ *   GSRF_SIG_RSSI_DB      out [n_rx][n_f]     20 log10 |S_hat| (dB re unit amplitude)
+ *   GSRF_SIG_POWER_SUM    out [n_rx][n_f]     sum over rays of |S_{u,v}|^2
+ *   GSRF_SIG_SPECTRUM_MAG out [n_rx][n_f][n_el][n_az]  |S_{u,v}|, the spatial spectrum
+ * rays [dev] [n_rx][n_f][n_el][n_az][2]; out [dev].  Sums run in a fixed order with
+ * FP64 accumulation, so results are reproducible bit for bit. */
+typedef enum {
+    GSRF_SIG_COMPLEX_SUM = 0,
+    GSRF_SIG_RSSI_DB = 1,
+    GSRF_SIG_POWER_SUM = 2,
+    GSRF_SIG_SPECTRUM_MAG = 3
+} gsrf_sig_mode;
+gsrf_status gsrf_received_signal(const float *rays, int32_t n_rx, int32_t n_f, int32_t n_el,
+                                 int32_t n_az, int32_t mode, float *out, void *stream);
+
+/* Device-side status after the calls above (synchronises `stream`). */
+typedef struct {
+    int32_t code;              /* gsrf_status */
+    int32_t first_bad;         /* first offending Gaussian for GSRF_ERR_NONFINITE, else -1 */
+    int64_t required_pairs;    /* pairs the last gsrf_bin needed */
+    int64_t stats[4];          /* [0] candidate tests, [1] composited pairs (last render) */
+} gsrf_run_status;
+gsrf_status gsrf_read_status(const void *workspace, size_t ws_bytes, gsrf_run_status *out,
+                             void *stream);
+
+/* Library version string. */
+const char *gsrf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,102 @@
+"""ctypes binding of libgsrf.so: the C ABI of include/gsrf.h, name for name.
+
+Argument marshalling only; every step of the render runs in the library's CUDA
+kernels.  Loading fails loudly when the library is missing: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import _build
+
+GSRF_OK, GSRF_ERR_INVALID_ARG, GSRF_ERR_CUDA, GSRF_ERR_CAPACITY = 0, 1, 2, 3
+GSRF_ERR_TIMEOUT, GSRF_ERR_NONFINITE, GSRF_ERR_UNSUPPORTED = 4, 5, 6
+STATUS_NAMES = {0: "GSRF_OK", 1: "GSRF_ERR_INVALID_ARG", 2: "GSRF_ERR_CUDA", 3: "GSRF_ERR_CAPACITY",
+                4: "GSRF_ERR_TIMEOUT", 5: "GSRF_ERR_NONFINITE", 6: "GSRF_ERR_UNSUPPORTED"}
+SIG_COMPLEX_SUM, SIG_RSSI_DB, SIG_POWER_SUM, SIG_SPECTRUM_MAG = 0, 1, 2, 3
+
+# every exported symbol of include/gsrf.h
+EXPORTS = ["gsrf_workspace_size", "gsrf_workspace_layout", "gsrf_ray_state_bytes", "gsrf_project",
+           "gsrf_bin", "gsrf_render_fwd", "gsrf_render", "gsrf_received_signal", "gsrf_read_status",
+           "gsrf_version"]
+
+
+class GsrfError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__("%s returned %s" % (fn, STATUS_NAMES.get(code, code)))
+        self.code = code
+
+
+class gsrf_grid(C.Structure):
+    _fields_ = [("n_az", C.c_int32), ("n_el", C.c_int32), ("az0_deg", C.c_float), ("daz_deg", C.c_float),
+                ("el0_deg", C.c_float), ("del_deg", C.c_float), ("r_rx", C.c_float), ("eps_T", C.c_float),
+                ("alpha_max", C.c_float), ("tile_w", C.c_int32), ("tile_h", C.c_int32)]
+
+
+class gsrf_gaussians(C.Structure):
+    _fields_ = [("n", C.c_int64), ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logit", C.c_void_p), ("coeffs", C.c_void_p), ("phase_b", C.c_void_p)]
+
+
+class gsrf_plan(C.Structure):
+    _fields_ = [("n_gauss", C.c_int64), ("n_rx", C.c_int32), ("n_f", C.c_int32), ("f0_hz", C.c_double),
+                ("df_hz", C.c_double), ("grid", gsrf_grid), ("pair_capacity", C.c_int64)]
+
+
+class gsrf_layout(C.Structure):
+    _fields_ = [("pair_keys", C.c_size_t), ("pair_ids", C.c_size_t), ("rx_pair_base", C.c_size_t),
+                ("tile_start", C.c_size_t), ("status", C.c_size_t), ("n_tiles_u", C.c_int32),
+                ("n_tiles_v", C.c_int32)]
+
+
+class gsrf_run_status(C.Structure):
+    _fields_ = [("code", C.c_int32), ("first_bad", C.c_int32), ("required_pairs", C.c_int64),
+                ("stats", C.c_int64 * 4)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.SO
+
+
+def load(build_if_missing: bool = False):
+    """Load libgsrf.so.  Raises if it is absent (run __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.SO):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError("libgsrf.so not built (%s); call __graft_entry__.build()" % _build.SO)
+    L = C.CDLL(_build.SO)
+    vp, sz, st = C.c_void_p, C.c_size_t, C.c_int
+    P = C.POINTER
+    L.gsrf_workspace_size.argtypes = [P(gsrf_plan), P(C.c_size_t)]
+    L.gsrf_workspace_layout.argtypes = [P(gsrf_plan), P(gsrf_layout)]
+    L.gsrf_ray_state_bytes.argtypes = [P(gsrf_plan)]
+    L.gsrf_ray_state_bytes.restype = C.c_size_t
+    L.gsrf_project.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, vp, vp, sz, vp]
+    L.gsrf_bin.argtypes = [P(gsrf_plan), vp, sz, vp]
+    L.gsrf_render_fwd.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, sz, vp, vp, vp]
+    L.gsrf_render.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, vp, vp, sz, vp, vp, vp]
+    L.gsrf_received_signal.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, vp]
+    L.gsrf_read_status.argtypes = [vp, sz, P(gsrf_run_status), vp]
+    L.gsrf_version.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("gsrf_ray_state_bytes", "gsrf_version"):
+            getattr(L, name).restype = st
+    _lib = L
+    return L
+
+
+def check(fn: str, code: int):
+    if code != GSRF_OK:
+        raise GsrfError(fn, code)
+
+
+def call(fn: str, *args):
+    check(fn, getattr(load(), fn)(*args))

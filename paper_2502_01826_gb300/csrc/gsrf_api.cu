@@ -1,0 +1,193 @@
+// gsrf_api.cu -- the extern "C" boundary of libgsrf.so (declared in include/gsrf.h):
+// argument checks, workspace layout, and the launch sequences of each call.
+#include <stdio.h>
+#include <string.h>
+
+#include "gsrf_internal.cuh"
+
+namespace gsrf {
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool make_layout(const gsrf_plan* p, Layout* L) {
+    const gsrf_grid& g = p->grid;
+    L->ntu = (g.n_az + g.tile_w - 1) / g.tile_w;
+    L->ntv = (g.n_el + g.tile_h - 1) / g.tile_h;
+    L->n_tiles = L->ntu * L->ntv;
+    L->n_rx = p->n_rx;
+    L->n = p->n_gauss;
+    L->cap = p->pair_capacity;
+    L->dchunks = (int32_t)((p->n_gauss + kChunk - 1) / kChunk);
+    L->pchunks_max = (p->pair_capacity + kChunk - 1) / kChunk + p->n_rx;
+    const size_t n = (size_t)p->n_gauss, nr = (size_t)p->n_rx, cap = (size_t)p->pair_capacity;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    L->status = take(sizeof(DevStatus));
+    L->gshape = take(n * sizeof(GShape));
+    L->dpath = take(n * sizeof(double));
+    L->view = take(nr * n * sizeof(View));
+    L->cover = take(nr * n * sizeof(Cover));
+    L->dkey = take(nr * n * 4);
+    L->dkey2 = take(nr * n * 4);
+    L->dval = take(nr * n * 4);
+    L->dval2 = take(nr * n * 4);
+    L->dhist = take(nr * (size_t)L->dchunks * 256 * 4);
+    L->dchunk_sum = take(nr * (size_t)L->dchunks * 4);
+    L->rx_base = take((nr + 1) * 8);
+    L->rx_total = take(nr * 4);
+    L->pchunk_base = take((nr + 1) * 4);
+    L->pkeys = take(cap * 8);
+    L->pkeys2 = take(cap * 8);
+    L->pids = take(cap * 4);
+    L->pids2 = take(cap * 4);
+    L->tile_start = take(nr * (size_t)(L->n_tiles + 1) * 4);
+    L->thist = take((size_t)L->pchunks_max * L->n_tiles * 4);
+    L->total = off;
+    return true;
+}
+
+}  // namespace gsrf
+
+using namespace gsrf;
+
+static gsrf_status check_grid(const gsrf_grid* g) {
+    if (!g) return GSRF_ERR_INVALID_ARG;
+    if (g->n_az < 1 || g->n_el < 1 || g->n_az > 65536 || g->n_el > 65536) return GSRF_ERR_INVALID_ARG;
+    if (!(g->daz_deg > 0.0f) || !(g->del_deg > 0.0f)) return GSRF_ERR_INVALID_ARG;
+    if (!(g->az0_deg >= -360.0f && g->az0_deg <= 360.0f)) return GSRF_ERR_INVALID_ARG;
+    if (!(g->el0_deg >= -90.0f && g->el0_deg <= 90.0f)) return GSRF_ERR_INVALID_ARG;
+    if (!(g->r_rx >= 0.0f) || !(g->eps_T >= 0.0f && g->eps_T < 1.0f)) return GSRF_ERR_INVALID_ARG;
+    if (!(g->alpha_max > 0.0f && g->alpha_max < 1.0f)) return GSRF_ERR_INVALID_ARG;
+    if (g->tile_w != kTile || g->tile_h != kTile) return GSRF_ERR_UNSUPPORTED;
+    const int ntu = (g->n_az + g->tile_w - 1) / g->tile_w, ntv = (g->n_el + g->tile_h - 1) / g->tile_h;
+    if (ntu > 64 || ntu * ntv > kMaxTiles) return GSRF_ERR_UNSUPPORTED;
+    return GSRF_OK;
+}
+
+static gsrf_status check_plan(const gsrf_plan* p) {
+    if (!p) return GSRF_ERR_INVALID_ARG;
+    if (p->n_gauss < 0 || p->n_gauss >= (1ll << 31)) return GSRF_ERR_INVALID_ARG;
+    if (p->n_rx < 1 || p->n_rx > 65535) return GSRF_ERR_INVALID_ARG;
+    if (p->n_f < 1 || p->n_f > kMaxNf) return GSRF_ERR_INVALID_ARG;
+    if (!(p->f0_hz > 0.0) || !(p->df_hz >= 0.0)) return GSRF_ERR_INVALID_ARG;
+    if (p->pair_capacity < 0 || p->pair_capacity > (1ll << 40)) return GSRF_ERR_INVALID_ARG;
+    if ((size_t)p->n_gauss * (size_t)p->n_rx >= (1ull << 40)) return GSRF_ERR_INVALID_ARG;
+    return check_grid(&p->grid);
+}
+
+static gsrf_status check_ws(const gsrf_plan* p, const void* ws, size_t ws_bytes, Layout* L) {
+    gsrf_status s = check_plan(p);
+    if (s != GSRF_OK) return s;
+    make_layout(p, L);
+    if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < L->total) return GSRF_ERR_INVALID_ARG;
+    return GSRF_OK;
+}
+
+static gsrf_status check_gauss(const gsrf_plan* p, const gsrf_gaussians* g) {
+    if (!g || g->n != p->n_gauss) return GSRF_ERR_INVALID_ARG;
+    if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logit || !g->coeffs))
+        return GSRF_ERR_INVALID_ARG;
+    if (((uintptr_t)g->coeffs & 15) != 0) return GSRF_ERR_INVALID_ARG;  // staged as float4
+    return GSRF_OK;
+}
+
+static gsrf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GSRF_OK : GSRF_ERR_CUDA; }
+
+extern "C" {
+
+const char* gsrf_version(void) { return "gsrf-gb300 0.1 (sm_103a)"; }
+
+gsrf_status gsrf_workspace_size(const gsrf_plan* plan, size_t* bytes) {
+    gsrf_status s = check_plan(plan);
+    if (s != GSRF_OK) return s;
+    if (!bytes) return GSRF_ERR_INVALID_ARG;
+    Layout L;
+    make_layout(plan, &L);
+    *bytes = L.total;
+    return GSRF_OK;
+}
+
+gsrf_status gsrf_workspace_layout(const gsrf_plan* plan, gsrf_layout* out) {
+    gsrf_status s = check_plan(plan);
+    if (s != GSRF_OK) return s;
+    if (!out) return GSRF_ERR_INVALID_ARG;
+    Layout L;
+    make_layout(plan, &L);
+    out->pair_keys = L.pkeys;
+    out->pair_ids = L.pids;
+    out->rx_pair_base = L.rx_base;
+    out->tile_start = L.tile_start;
+    out->status = L.status;
+    out->n_tiles_u = L.ntu;
+    out->n_tiles_v = L.ntv;
+    return GSRF_OK;
+}
+
+size_t gsrf_ray_state_bytes(const gsrf_plan* plan) {
+    if (check_plan(plan) != GSRF_OK) return 0;
+    return (size_t)plan->n_rx * plan->grid.n_az * plan->grid.n_el * sizeof(RayState);
+}
+
+gsrf_status gsrf_project(const gsrf_plan* plan, const gsrf_gaussians* g, const float* rx_pos,
+                         const float* tx_pos, void* workspace, size_t ws_bytes, void* stream) {
+    Layout L;
+    gsrf_status s = check_ws(plan, workspace, ws_bytes, &L);
+    if (s != GSRF_OK) return s;
+    if ((s = check_gauss(plan, g)) != GSRF_OK) return s;
+    if (!rx_pos || !tx_pos) return GSRF_ERR_INVALID_ARG;
+    return cuda_status(launch_project(plan, L, g, rx_pos, tx_pos, workspace, (cudaStream_t)stream));
+}
+
+gsrf_status gsrf_bin(const gsrf_plan* plan, void* workspace, size_t ws_bytes, void* stream) {
+    Layout L;
+    gsrf_status s = check_ws(plan, workspace, ws_bytes, &L);
+    if (s != GSRF_OK) return s;
+    return cuda_status(launch_bin(plan, L, workspace, (cudaStream_t)stream));
+}
+
+gsrf_status gsrf_render_fwd(const gsrf_plan* plan, const gsrf_gaussians* g, void* workspace, size_t ws_bytes,
+                            float* out_rays, void* ray_state, void* stream) {
+    Layout L;
+    gsrf_status s = check_ws(plan, workspace, ws_bytes, &L);
+    if (s != GSRF_OK) return s;
+    if ((s = check_gauss(plan, g)) != GSRF_OK) return s;
+    if (!out_rays || ((uintptr_t)out_rays & 7) != 0 || ((uintptr_t)ray_state & 15) != 0)
+        return GSRF_ERR_INVALID_ARG;
+    if (plan->n_f != 1) return GSRF_ERR_UNSUPPORTED;
+    return cuda_status(launch_render_fwd(plan, L, g, workspace, out_rays, ray_state, (cudaStream_t)stream));
+}
+
+gsrf_status gsrf_render(const gsrf_plan* plan, const gsrf_gaussians* g, const float* rx_pos, const float* tx_pos,
+                        void* workspace, size_t ws_bytes, float* out_rays, void* ray_state, void* stream) {
+    gsrf_status s = gsrf_project(plan, g, rx_pos, tx_pos, workspace, ws_bytes, stream);
+    if (s != GSRF_OK) return s;
+    if ((s = gsrf_bin(plan, workspace, ws_bytes, stream)) != GSRF_OK) return s;
+    return gsrf_render_fwd(plan, g, workspace, ws_bytes, out_rays, ray_state, stream);
+}
+
+gsrf_status gsrf_received_signal(const float* rays, int32_t n_rx, int32_t n_f, int32_t n_el, int32_t n_az,
+                                 int32_t mode, float* out, void* stream) {
+    if (!rays || !out || n_rx < 1 || n_f < 1 || n_el < 1 || n_az < 1 || mode < 0 || mode > 3)
+        return GSRF_ERR_INVALID_ARG;
+    if ((size_t)n_rx * n_f > 0x7fffffffu || (size_t)n_el * n_az > 0x7fffffffu) return GSRF_ERR_INVALID_ARG;
+    return cuda_status(launch_signal(rays, n_rx, n_f, n_el, n_az, mode, out, (cudaStream_t)stream));
+}
+
+gsrf_status gsrf_read_status(const void* workspace, size_t ws_bytes, gsrf_run_status* out, void* stream) {
+    if (!workspace || !out || ws_bytes < sizeof(DevStatus)) return GSRF_ERR_INVALID_ARG;
+    DevStatus h;
+    cudaError_t e = cudaMemcpyAsync(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return GSRF_ERR_CUDA;
+    out->code = h.code;
+    out->first_bad = h.first_bad == 0x7fffffff ? -1 : h.first_bad;
+    out->required_pairs = h.required_pairs;
+    for (int i = 0; i < 4; ++i) out->stats[i] = (int64_t)h.stats[i];
+    return GSRF_OK;
+}
+
+}  // extern "C"

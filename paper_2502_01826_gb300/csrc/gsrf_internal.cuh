@@ -1,0 +1,156 @@
+// gsrf_internal.cuh -- device structures, workspace layout and shared device helpers
+// of the GB300 GSRF render (arXiv 2502.01826).  Internal to libgsrf.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gsrf.h"
+
+namespace gsrf {
+
+constexpr int kNB = 16;               // Fourier-Legendre coefficients, L = 3 (Sec. 4.2)
+constexpr double kC = 3.0e8;          // propagation speed (Sec. 2 worked example)
+constexpr int kTile = 16;             // rays per tile side (App. E)
+constexpr int kRenderThreads = kTile * kTile;
+constexpr int kChunk = 4096;          // items per block in the sort / emit passes
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kMaxTiles = 1024;       // bins of the tile counting sort
+constexpr int kMaxNf = 64;
+
+// Per-Gaussian shape record: whitening matrix W = diag(1/s) R^T (so that
+// (x-mu)^T Sigma^-1 (x-mu) = |W (x-mu)|^2), opacity, excess-phase coefficient.
+struct __align__(16) GShape {
+    float W[9];
+    float o;
+    float b;
+    float pad;
+};
+
+// Per-(receiver, Gaussian) view record: whitened receiver offset w = W (r - mu),
+// path phasor e^{-j 2 pi f0 d / c} and the per-subcarrier phase step 2 pi df d / c.
+struct __align__(16) View {
+    float w[3];
+    float er, ei;
+    float omd;
+    float pad0, pad1;
+};
+
+// Tile coverage of a Gaussian seen from a receiver: azimuth-tile bit mask,
+// elevation tile range packed lo | hi << 16, number of tiles.
+struct __align__(16) Cover {
+    unsigned long long mask;
+    uint32_t tv;
+    uint32_t count;
+};
+
+struct __align__(16) DevStatus {
+    int32_t code;
+    int32_t first_bad;
+    long long required_pairs;
+    unsigned long long stats[4];
+};
+
+// Per-ray state the backward replays from: list position (inside the tile's list) of
+// the last composited Gaussian (-1 = none), prod(1 - alpha) and the complex
+// transmittance at f0 after it.
+struct __align__(16) RayState {
+    int32_t last;
+    float Ta;
+    float Tr, Ti;
+};
+
+struct Layout {
+    // byte offsets
+    size_t status, gshape, dpath, view, cover, dkey, dkey2, dval, dval2, dhist, dchunk_sum,
+        rx_base, rx_total, pchunk_base, pkeys, pkeys2, pids, pids2, tile_start, thist, total;
+    int32_t ntu, ntv, n_tiles;
+    int32_t n_rx;
+    int64_t n;
+    int64_t cap;
+    int32_t dchunks;      // depth-sort chunks per receiver
+    int64_t pchunks_max;  // upper bound on pair chunks over all receivers
+};
+
+bool make_layout(const gsrf_plan* p, Layout* L);
+
+template <typename T>
+__host__ __device__ inline T* at(void* ws, size_t off) {
+    return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic FP32 arithmetic for the two integer decisions of the splatting
+// step (depth keys, tile coverage).  Only correctly rounded operations, written
+// with _rn intrinsics so that no multiply-add is fused: the result is the same
+// bit pattern on any IEEE-754 machine that evaluates the same sequence.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float dmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float dadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float dsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float ddiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float dsqrt(float a) { return __fsqrt_rn(a); }
+
+// exp(x) for the culling radius: 2^n * e^t with n = floor(x log2 e), t = frac * ln 2,
+// e^t by its Taylor series to t^9 (error ~1e-7, far inside the 1% radius margin).
+__device__ __forceinline__ float det_exp(float x) {
+    float y = dmul(x, 1.44269504f);
+    float n = floorf(y);
+    float t = dmul(dsub(y, n), 0.693147182f);
+    float p = 2.75573192e-6f;
+    p = dadd(dmul(p, t), 2.48015873e-5f);
+    p = dadd(dmul(p, t), 1.98412698e-4f);
+    p = dadd(dmul(p, t), 1.38888889e-3f);
+    p = dadd(dmul(p, t), 8.33333333e-3f);
+    p = dadd(dmul(p, t), 4.16666667e-2f);
+    p = dadd(dmul(p, t), 1.66666667e-1f);
+    p = dadd(dmul(p, t), 0.5f);
+    p = dadd(dmul(p, t), 1.0f);
+    p = dadd(dmul(p, t), 1.0f);
+    return ldexpf(p, (int)n);
+}
+
+// atan on [0, 1]: two half-angle steps t -> t / (1 + sqrt(1 + t^2)) reduce the
+// argument below tan(pi/16); the Maclaurin series to t^11 finishes it; times 4.
+__device__ __forceinline__ float det_atan_unit(float t) {
+    t = ddiv(t, dadd(1.0f, dsqrt(dadd(1.0f, dmul(t, t)))));
+    t = ddiv(t, dadd(1.0f, dsqrt(dadd(1.0f, dmul(t, t)))));
+    float z = dmul(t, t);
+    float p = -9.09090909e-2f;
+    p = dadd(dmul(p, z), 1.11111111e-1f);
+    p = dadd(dmul(p, z), -1.42857143e-1f);
+    p = dadd(dmul(p, z), 2.0e-1f);
+    p = dadd(dmul(p, z), -3.33333333e-1f);
+    p = dadd(dmul(p, z), 1.0f);
+    return dmul(4.0f, dmul(t, p));
+}
+
+__device__ __forceinline__ float det_atan2(float y, float x) {
+    float ax = fabsf(x), ay = fabsf(y), a;
+    if (ax == 0.0f && ay == 0.0f) return 0.0f;
+    if (ay <= ax) a = det_atan_unit(ddiv(ay, ax));
+    else a = dsub(1.57079633f, det_atan_unit(ddiv(ax, ay)));
+    if (x < 0.0f) a = dsub(3.14159265f, a);
+    if (y < 0.0f) a = -a;
+    return a;
+}
+
+__device__ __forceinline__ float det_asin(float s) {
+    s = fminf(fmaxf(s, -1.0f), 1.0f);
+    float c = dsqrt(dmul(dsub(1.0f, s), dadd(1.0f, s)));
+    return det_atan2(s, c);
+}
+
+// ---------------------------------------------------------------------------
+// launchers (one translation unit each)
+// ---------------------------------------------------------------------------
+cudaError_t launch_project(const gsrf_plan* p, const Layout& L, const gsrf_gaussians* g,
+                           const float* rx, const float* tx, void* ws, cudaStream_t st);
+cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream_t st);
+cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_gaussians* g,
+                              void* ws, float* out, void* ray_state, cudaStream_t st);
+cudaError_t launch_signal(const float* rays, int n_rx, int n_f, int n_el, int n_az, int mode,
+                          float* out, cudaStream_t st);
+
+}  // namespace gsrf

@@ -1,0 +1,373 @@
+// k_bin.cu -- Alg. 1 lines 4-5 and App. E: splat keys (tile << 32 | depth), one sort,
+// tile ranges.  The 64-bit sort is done as
+//   (1) a stable LSD radix sort of each receiver's n FP32 depth keys (4 x 8-bit digits);
+//   (2) emission of the (tile, Gaussian) pairs in that depth order;
+//   (3) a stable counting sort of each receiver's pairs by tile (the high 32 bits),
+// which leaves every tile's Gaussians in (depth, index) order: the same permutation as
+// one stable sort of the full 64-bit keys, with 4 passes over n keys and one pass over
+// the pairs instead of 8 passes over the pairs.
+//
+// Every pass is a (histogram, scan, scatter) triple over blocks of kChunk items.
+// Ranks inside a block come from __match_any_sync peer groups, so equal digits keep
+// their input order: the sort is stable and its output deterministic.
+#include "gsrf_internal.cuh"
+
+namespace gsrf {
+
+// Which items a block owns.  Segments are receivers; either all of length eq_len or
+// given by base[] with chunk_base[] = prefix of ceil(len / kChunk).
+struct Segs {
+    int n_seg;
+    long long eq_len;  // >= 0: equal segments
+    int eq_chunks;
+    const long long* base;
+    const uint32_t* chunk_base;
+};
+
+__device__ __forceinline__ bool block_items(const Segs& S, long long b, long long& lo, long long& hi,
+                                            long long& seg_lo, int& seg) {
+    if (S.eq_len >= 0) {
+        seg = (int)(b / S.eq_chunks);
+        const long long c = b % S.eq_chunks;
+        if (seg >= S.n_seg) return false;
+        seg_lo = (long long)seg * S.eq_len;
+        lo = seg_lo + c * kChunk;
+        hi = min(lo + (long long)kChunk, seg_lo + S.eq_len);
+        return lo < hi;
+    }
+    if (b >= (long long)S.chunk_base[S.n_seg]) return false;
+    int a = 0, z = S.n_seg - 1;
+    while (a < z) {
+        const int m = (a + z + 1) >> 1;
+        if ((long long)S.chunk_base[m] <= b) a = m;
+        else z = m - 1;
+    }
+    seg = a;
+    seg_lo = S.base[a];
+    lo = seg_lo + (b - (long long)S.chunk_base[a]) * kChunk;
+    hi = min(lo + (long long)kChunk, S.base[a + 1]);
+    return lo < hi;
+}
+
+__device__ __forceinline__ void chunk_range(const Segs& S, int seg, long long& c0, long long& c1) {
+    if (S.eq_len >= 0) {
+        c0 = (long long)seg * S.eq_chunks;
+        c1 = c0 + S.eq_chunks;
+    } else {
+        c0 = S.chunk_base[seg];
+        c1 = S.chunk_base[seg + 1];
+    }
+}
+
+template <typename K>
+__device__ __forceinline__ uint32_t digit_of(K key, int shift, uint32_t mask) {
+    return (uint32_t)(key >> shift) & mask;
+}
+
+__device__ __forceinline__ bool capacity_failed(const DevStatus* st) {
+    return st != nullptr && *(volatile const int32_t*)&st->code == (int32_t)GSRF_ERR_CAPACITY;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) k_hist(const K* __restrict__ keys, Segs S, int shift,
+                                                       uint32_t mask, int nbins, uint32_t* __restrict__ H,
+                                                       const DevStatus* st) {
+    if (capacity_failed(st)) return;
+    __shared__ uint32_t h[kMaxTiles];
+    long long lo, hi, seg_lo;
+    int seg;
+    if (!block_items(S, blockIdx.x, lo, hi, seg_lo, seg)) return;
+    for (int i = threadIdx.x; i < nbins; i += kSortThreads) h[i] = 0;
+    __syncthreads();
+    for (long long i = lo + threadIdx.x; i < hi; i += kSortThreads) atomicAdd(&h[digit_of(keys[i], shift, mask)], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nbins; i += kSortThreads) H[(size_t)blockIdx.x * nbins + i] = h[i];
+}
+
+// Block-wide exclusive scan of one value per thread (kSortThreads threads).
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T* total, T* sh /* [kSortWarps] */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    T wbase = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+        if (w < warp) wbase += sh[w];
+        tot += sh[w];
+    }
+    __syncthreads();
+    if (total) *total = tot;
+    return wbase + x - v;
+}
+
+// One block per segment: turn per-block digit counts H[block][digit] into absolute
+// destinations inside the segment; optionally record each digit's [start, end).
+__global__ void __launch_bounds__(kSortThreads) k_scan(Segs S, int nbins, uint32_t* __restrict__ H,
+                                                       uint32_t* __restrict__ bin_start,
+                                                       const DevStatus* st) {
+    if (capacity_failed(st)) return;
+    __shared__ uint32_t tot[kMaxTiles];
+    __shared__ uint32_t sh[kSortWarps];
+    const int seg = blockIdx.x;
+    long long c0, c1;
+    chunk_range(S, seg, c0, c1);
+    for (int d = threadIdx.x; d < nbins; d += kSortThreads) {
+        uint32_t run = 0;
+        for (long long c = c0; c < c1; ++c) {
+            const uint32_t v = H[(size_t)c * nbins + d];
+            H[(size_t)c * nbins + d] = run;
+            run += v;
+        }
+        tot[d] = run;
+    }
+    __syncthreads();
+    // exclusive scan over digits, kSortThreads at a time
+    uint32_t carry = 0;
+    for (int d0 = 0; d0 < nbins; d0 += kSortThreads) {
+        const int d = d0 + threadIdx.x;
+        const uint32_t v = d < nbins ? tot[d] : 0u;
+        uint32_t t;
+        const uint32_t ex = block_excl_scan<uint32_t>(v, &t, sh);
+        if (d < nbins) {
+            const uint32_t start = carry + ex;
+            for (long long c = c0; c < c1; ++c) H[(size_t)c * nbins + d] += start;
+            if (bin_start) bin_start[(size_t)seg * (nbins + 1) + d] = start;
+        }
+        carry += t;
+    }
+    if (bin_start && threadIdx.x == 0) bin_start[(size_t)seg * (nbins + 1) + nbins] = carry;
+}
+
+// Stable scatter.  vin == nullptr: the value is the item's index inside its segment.
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) k_scatter(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                          K* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                          Segs S, int shift, uint32_t mask, int nbins,
+                                                          const uint32_t* __restrict__ H, const DevStatus* st) {
+    if (capacity_failed(st)) return;
+    __shared__ uint32_t base[kMaxTiles];
+    __shared__ uint8_t cnt[kSortWarps][kMaxTiles];
+    long long lo, hi, seg_lo;
+    int seg;
+    if (!block_items(S, blockIdx.x, lo, hi, seg_lo, seg)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < nbins; d += kSortThreads) {
+        base[d] = H[(size_t)blockIdx.x * nbins + d];
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) cnt[w][d] = 0;
+    }
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+    for (long long r0 = lo; r0 < hi; r0 += kSortThreads) {
+        const long long i = r0 + threadIdx.x;
+        const bool valid = i < hi;
+        K key = 0;
+        uint32_t val = 0, d = 0xffffffffu;
+        if (valid) {
+            key = kin[i];
+            val = vin ? vin[i] : (uint32_t)(i - seg_lo);
+            d = digit_of(key, shift, mask);
+        }
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & lt);
+        if (valid && rank == 0) cnt[warp][d] = (uint8_t)__popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t off = base[d] + rank;
+            for (int w = 0; w < warp; ++w) off += cnt[w][d];
+            kout[seg_lo + off] = key;
+            vout[seg_lo + off] = val;
+        }
+        __syncthreads();
+        for (int dd = threadIdx.x; dd < nbins; dd += kSortThreads) {
+            uint32_t t = 0;
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) {
+                t += cnt[w][dd];
+                cnt[w][dd] = 0;
+            }
+            base[dd] += t;
+        }
+        __syncthreads();
+    }
+}
+
+// ---- emission -------------------------------------------------------------
+
+// Per (receiver, chunk of the depth-sorted Gaussians): number of pairs.
+__global__ void __launch_bounds__(kSortThreads) k_count_chunks(const uint32_t* __restrict__ dval,
+                                                               const Cover* __restrict__ cover, long long n,
+                                                               int dchunks, uint32_t* __restrict__ chunk_sum) {
+    __shared__ uint32_t sh[kSortWarps];
+    const int r = blockIdx.y, c = blockIdx.x;
+    const long long lo = (long long)c * kChunk, hi = min(lo + (long long)kChunk, n);
+    uint32_t s = 0;
+    for (long long i = lo + threadIdx.x; i < hi; i += kSortThreads)
+        s += cover[(size_t)r * n + dval[(size_t)r * n + i]].count;
+    uint32_t tot;
+    block_excl_scan<uint32_t>(s, &tot, sh);
+    if (threadIdx.x == 0) chunk_sum[(size_t)r * dchunks + c] = tot;
+}
+
+// One block: chunk offsets per receiver, receiver bases, capacity check, and the
+// chunk table of the tile sort.
+__global__ void __launch_bounds__(kSortThreads) k_scan_pairs(uint32_t* __restrict__ chunk_sum, int n_rx, int dchunks,
+                                                             long long cap, long long* __restrict__ rx_base,
+                                                             uint32_t* __restrict__ rx_total,
+                                                             uint32_t* __restrict__ pchunk_base, DevStatus* st) {
+    for (int r = threadIdx.x; r < n_rx; r += kSortThreads) {
+        uint32_t run = 0;
+        for (int c = 0; c < dchunks; ++c) {
+            const uint32_t v = chunk_sum[(size_t)r * dchunks + c];
+            chunk_sum[(size_t)r * dchunks + c] = run;
+            run += v;
+        }
+        rx_total[r] = run;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long b = 0;
+        uint32_t cb = 0;
+        for (int r = 0; r < n_rx; ++r) {
+            rx_base[r] = b;
+            pchunk_base[r] = cb;
+            b += rx_total[r];
+            cb += (rx_total[r] + kChunk - 1) / kChunk;
+        }
+        rx_base[n_rx] = b;
+        pchunk_base[n_rx] = cb;
+        st->required_pairs = b;
+        if (b > cap) {
+            atomicCAS(&st->code, (int)GSRF_OK, (int)GSRF_ERR_CAPACITY);
+            // a failed bin leaves no pairs: downstream kernels see empty lists
+            for (int r = 0; r <= n_rx; ++r) { rx_base[r] = 0; pchunk_base[r] = 0; }
+        }
+    }
+}
+
+// Expand each chunk of depth-sorted Gaussians into its (tile, Gaussian) pairs, written
+// contiguously in depth order (one thread per output pair).
+__global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restrict__ dval,
+                                                       const uint32_t* __restrict__ dkey_sorted,
+                                                       const Cover* __restrict__ cover, long long n, int dchunks,
+                                                       const uint32_t* __restrict__ chunk_off,
+                                                       const long long* __restrict__ rx_base,
+                                                       const uint32_t* __restrict__ rx_total, int ntu,
+                                                       unsigned long long* __restrict__ pkeys,
+                                                       uint32_t* __restrict__ pids, const DevStatus* st) {
+    if (capacity_failed(st)) return;
+    __shared__ uint32_t offs[kChunk + 1];
+    __shared__ uint32_t sh[kSortWarps];
+    const int r = blockIdx.y, c = blockIdx.x;
+    const long long lo = (long long)c * kChunk, hi = min(lo + (long long)kChunk, n);
+    const int m = (int)(hi - lo);
+    constexpr int per = kChunk / kSortThreads;
+    // blocked exclusive scan of the chunk's pair counts
+    uint32_t v[per];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < per; ++j) {
+        const int idx = threadIdx.x * per + j;
+        v[j] = idx < m ? cover[(size_t)r * n + dval[(size_t)r * n + lo + idx]].count : 0u;
+        s += v[j];
+    }
+    uint32_t tot;
+    uint32_t ex = block_excl_scan<uint32_t>(s, &tot, sh);
+#pragma unroll
+    for (int j = 0; j < per; ++j) {
+        offs[threadIdx.x * per + j] = ex;
+        ex += v[j];
+    }
+    if (threadIdx.x == 0) offs[kChunk] = tot;
+    __syncthreads();
+    const long long out0 = rx_base[r] + chunk_off[(size_t)r * dchunks + c];
+    for (uint32_t p = threadIdx.x; p < tot; p += kSortThreads) {
+        // item owning pair p: last idx with offs[idx] <= p
+        int a = 0, z = m - 1;
+        while (a < z) {
+            const int mid = (a + z + 1) >> 1;
+            if (offs[mid] <= p) a = mid;
+            else z = mid - 1;
+        }
+        const size_t gi = (size_t)r * n + lo + a;
+        const uint32_t gid = dval[gi];
+        const Cover cv = cover[(size_t)r * n + gid];
+        const uint32_t j = p - offs[a];
+        const int nb = __popcll(cv.mask);
+        const int tv = (int)(cv.tv & 0xffffu) + (int)(j / nb);
+        unsigned long long mk = cv.mask;
+        for (uint32_t q = j % nb; q > 0; --q) mk &= mk - 1ull;
+        const int tu = __ffsll((long long)mk) - 1;
+        const uint32_t tile = (uint32_t)(tv * ntu + tu);
+        pkeys[out0 + p] = ((unsigned long long)tile << 32) | dkey_sorted[gi];
+        pids[out0 + p] = gid;
+    }
+}
+
+__global__ void k_zero_tile_start(uint32_t* ts, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) ts[i] = 0;
+}
+
+cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream_t st) {
+    DevStatus* status = at<DevStatus>(ws, L.status);
+    const size_t nts = (size_t)L.n_rx * (L.n_tiles + 1);
+    k_zero_tile_start<<<(unsigned)((nts + 255) / 256), 256, 0, st>>>(at<uint32_t>(ws, L.tile_start), nts);
+    cudaError_t e = cudaMemsetAsync(at<long long>(ws, L.rx_base), 0, sizeof(long long) * (L.n_rx + 1), st);
+    if (e != cudaSuccess) return e;
+    if (L.n == 0) return cudaGetLastError();
+
+    // (1) depth sort, per receiver: keys dkey -> dkey2 -> dkey ..., values likewise
+    Segs ds{L.n_rx, L.n, L.dchunks, nullptr, nullptr};
+    const unsigned dblocks = (unsigned)(L.n_rx * L.dchunks);
+    uint32_t* k_in = at<uint32_t>(ws, L.dkey);
+    uint32_t* k_out = at<uint32_t>(ws, L.dkey2);
+    uint32_t* v_in = nullptr;
+    uint32_t* v_out = at<uint32_t>(ws, L.dval);
+    uint32_t* v_alt = at<uint32_t>(ws, L.dval2);
+    uint32_t* H = at<uint32_t>(ws, L.dhist);
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 8 * pass;
+        k_hist<uint32_t><<<dblocks, kSortThreads, 0, st>>>(k_in, ds, shift, 0xffu, 256, H, nullptr);
+        k_scan<<<L.n_rx, kSortThreads, 0, st>>>(ds, 256, H, nullptr, nullptr);
+        k_scatter<uint32_t><<<dblocks, kSortThreads, 0, st>>>(k_in, v_in, k_out, v_out, ds, shift, 0xffu, 256, H,
+                                                               nullptr);
+        uint32_t* t = k_in; k_in = k_out; k_out = t;
+        v_in = v_out;
+        v_out = (v_out == at<uint32_t>(ws, L.dval)) ? v_alt : at<uint32_t>(ws, L.dval);
+    }
+    // after 4 passes the sorted keys / values are back in dkey / dval2 ... track them:
+    const uint32_t* dkey_sorted = k_in;
+    const uint32_t* dval_sorted = v_in;
+
+    // (2) emission in depth order
+    uint32_t* chunk_sum = at<uint32_t>(ws, L.dchunk_sum);
+    k_count_chunks<<<dim3(L.dchunks, L.n_rx), kSortThreads, 0, st>>>(dval_sorted, at<Cover>(ws, L.cover), L.n,
+                                                                       L.dchunks, chunk_sum);
+    k_scan_pairs<<<1, kSortThreads, 0, st>>>(chunk_sum, L.n_rx, L.dchunks, L.cap, at<long long>(ws, L.rx_base),
+                                             at<uint32_t>(ws, L.rx_total), at<uint32_t>(ws, L.pchunk_base), status);
+    k_emit<<<dim3(L.dchunks, L.n_rx), kSortThreads, 0, st>>>(
+        dval_sorted, dkey_sorted, at<Cover>(ws, L.cover), L.n, L.dchunks, chunk_sum, at<long long>(ws, L.rx_base),
+        at<uint32_t>(ws, L.rx_total), L.ntu, at<unsigned long long>(ws, L.pkeys2), at<uint32_t>(ws, L.pids2), status);
+
+    // (3) stable counting sort of each receiver's pairs by tile: pkeys2 -> pkeys
+    Segs ps{L.n_rx, -1, 0, at<long long>(ws, L.rx_base), at<uint32_t>(ws, L.pchunk_base)};
+    const unsigned pblocks = (unsigned)L.pchunks_max;
+    uint32_t* TH = at<uint32_t>(ws, L.thist);
+    k_hist<unsigned long long><<<pblocks, kSortThreads, 0, st>>>(at<unsigned long long>(ws, L.pkeys2), ps, 32,
+                                                                 0xffffffffu, L.n_tiles, TH, status);
+    k_scan<<<L.n_rx, kSortThreads, 0, st>>>(ps, L.n_tiles, TH, at<uint32_t>(ws, L.tile_start), status);
+    k_scatter<unsigned long long><<<pblocks, kSortThreads, 0, st>>>(
+        at<unsigned long long>(ws, L.pkeys2), at<uint32_t>(ws, L.pids2), at<unsigned long long>(ws, L.pkeys),
+        at<uint32_t>(ws, L.pids), ps, 32, 0xffffffffu, L.n_tiles, TH, status);
+    (void)p;
+    return cudaGetLastError();
+}
+
+}  // namespace gsrf

@@ -1,0 +1,182 @@
+// k_project.cu -- Alg. 1 line 2 ("sphericalGaussian"): per-Gaussian shape records and
+// per-(receiver, Gaussian) view records, depth keys and tile coverage.
+#include <math.h>
+
+#include "gsrf_internal.cuh"
+
+namespace gsrf {
+
+// Clear the status word; first_bad holds INT_MAX until a non-finite Gaussian is seen.
+__global__ void k_status_init(DevStatus* st) {
+    if (threadIdx.x == 0) {
+        st->code = GSRF_OK;
+        st->first_bad = 0x7fffffff;
+        st->required_pairs = 0;
+        for (int i = 0; i < 4; ++i) st->stats[i] = 0ull;
+    }
+}
+
+// One thread per Gaussian: W = diag(1/s) R^T with R the rotation of the normalised
+// quaternion (Sec. 4.2, Sigma = R S S^T R^T, so Sigma^-1 = W^T W), opacity = sigmoid,
+// and |t - mu| in FP64 for the path phase.
+__global__ void __launch_bounds__(256) k_prepare(gsrf_gaussians g, const float* __restrict__ tx,
+                                                 GShape* __restrict__ shape, double* __restrict__ dpath_t,
+                                                 DevStatus* st) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n) return;
+    const float mx = g.means[3 * k], my = g.means[3 * k + 1], mz = g.means[3 * k + 2];
+    const float l0 = g.log_scales[3 * k], l1 = g.log_scales[3 * k + 1], l2 = g.log_scales[3 * k + 2];
+    float qw = g.quats[4 * k], qx = g.quats[4 * k + 1], qy = g.quats[4 * k + 2], qz = g.quats[4 * k + 3];
+    const float ol = g.opacity_logit[k];
+    const float b = g.phase_b ? g.phase_b[k] : 0.0f;
+    bool finite = isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(l0) && isfinite(l1) &&
+                  isfinite(l2) && isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) &&
+                  !isnan(ol) && isfinite(b);
+    const float* c = g.coeffs + (size_t)k * 2 * kNB;
+#pragma unroll
+    for (int i = 0; i < 2 * kNB; ++i) finite = finite && isfinite(c[i]);
+    if (!finite) {
+        atomicCAS(&st->code, (int)GSRF_OK, (int)GSRF_ERR_NONFINITE);
+        atomicMin(&st->first_bad, (int)k);
+    }
+    const float n2 = qw * qw + qx * qx + qy * qy + qz * qz;
+    if (n2 > 0.0f) {
+        const float inv = 1.0f / sqrtf(n2);
+        qw *= inv; qx *= inv; qy *= inv; qz *= inv;
+    } else {
+        qw = 1.0f; qx = qy = qz = 0.0f;
+    }
+    const float R[9] = {1.0f - 2.0f * (qy * qy + qz * qz), 2.0f * (qx * qy - qw * qz), 2.0f * (qx * qz + qw * qy),
+                        2.0f * (qx * qy + qw * qz), 1.0f - 2.0f * (qx * qx + qz * qz), 2.0f * (qy * qz - qw * qx),
+                        2.0f * (qx * qz - qw * qy), 2.0f * (qy * qz + qw * qx), 1.0f - 2.0f * (qx * qx + qy * qy)};
+    const float is[3] = {expf(-l0), expf(-l1), expf(-l2)};
+    GShape out;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) out.W[3 * i + j] = R[3 * j + i] * is[i];
+    out.o = 1.0f / (1.0f + expf(-ol));
+    out.b = b;
+    out.pad = 0.0f;
+    shape[k] = out;
+    const double dx = (double)tx[0] - mx, dy = (double)tx[1] - my, dz = (double)tx[2] - mz;
+    dpath_t[k] = sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+// Tile coverage: the bins of the receiving plane whose centre lies in the angular
+// bounding box of the sphere of radius 3.03 max(s) about mu (it contains the 3-sigma
+// ellipsoid with a 1% margin), in deterministic FP32.
+__device__ __forceinline__ Cover cover_of(float cx, float cy, float cz, float lsm, const gsrf_grid& gr,
+                                          int ntu, int ntv) {
+    const unsigned long long all_u = ntu >= 64 ? ~0ull : ((1ull << ntu) - 1ull);
+    Cover cv;
+    cv.mask = 0ull;
+    cv.tv = 1u;  // lo = 1 > hi = 0: empty
+    cv.count = 0u;
+    const float rho2 = dadd(dmul(cx, cx), dmul(cy, cy));
+    const float D = dsqrt(dadd(rho2, dmul(cz, cz)));
+    const float Rc = dmul(3.03f, det_exp(lsm));
+    if (dadd(D, Rc) < gr.r_rx) return cv;
+    if (D <= Rc) {
+        cv.mask = all_u;
+        cv.tv = (uint32_t)(ntv - 1) << 16;
+        cv.count = (uint32_t)(ntu * ntv);
+        return cv;
+    }
+    const float rad2deg = 57.2957795f;
+    const float elc = dmul(det_asin(ddiv(cz, D)), rad2deg);
+    const float eld = dmul(det_asin(ddiv(Rc, D)), rad2deg);
+    float vlo = ceilf(dsub(ddiv(dsub(dsub(elc, eld), gr.el0_deg), gr.del_deg), 0.5f));
+    float vhi = floorf(dsub(ddiv(dsub(dadd(elc, eld), gr.el0_deg), gr.del_deg), 0.5f));
+    vlo = fmaxf(vlo, 0.0f);
+    vhi = fminf(vhi, (float)(gr.n_el - 1));
+    if (vlo > vhi) return cv;
+    const int tv_lo = (int)vlo / gr.tile_h, tv_hi = (int)vhi / gr.tile_h;
+    unsigned long long mask = 0ull;
+    const float rho = dsqrt(rho2);
+    if (rho <= Rc) {
+        mask = all_u;
+    } else {
+        const float azc = dmul(det_atan2(cy, cx), rad2deg);
+        const float azd = dmul(det_asin(ddiv(Rc, rho)), rad2deg);
+        float rel = dsub(azc, gr.az0_deg);
+        if (rel < 0.0f) rel = dadd(rel, 360.0f);
+        if (rel < 0.0f) rel = dadd(rel, 360.0f);
+        if (rel >= 360.0f) rel = dsub(rel, 360.0f);
+        const float lo = dsub(rel, azd), hi = dadd(rel, azd);
+#pragma unroll
+        for (int w = -1; w <= 1; ++w) {
+            const float off = dmul(360.0f, (float)w);
+            float ulo = ceilf(dsub(ddiv(dadd(lo, off), gr.daz_deg), 0.5f));
+            float uhi = floorf(dsub(ddiv(dadd(hi, off), gr.daz_deg), 0.5f));
+            ulo = fmaxf(ulo, 0.0f);
+            uhi = fminf(uhi, (float)(gr.n_az - 1));
+            if (ulo > uhi) continue;
+            const int t0 = (int)ulo / gr.tile_w, t1 = (int)uhi / gr.tile_w;
+            const unsigned long long hi_bits = t1 >= 63 ? ~0ull : ((2ull << t1) - 1ull);
+            mask |= hi_bits & ~((1ull << t0) - 1ull);
+        }
+    }
+    if (!mask) return cv;
+    cv.mask = mask;
+    cv.tv = (uint32_t)tv_lo | ((uint32_t)tv_hi << 16);
+    cv.count = (uint32_t)(__popcll(mask) * (tv_hi - tv_lo + 1));
+    return cv;
+}
+
+// One thread per (receiver, Gaussian): whitened offset, depth key, coverage, phase.
+__global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __restrict__ rxp,
+                                              const GShape* __restrict__ shape,
+                                              const double* __restrict__ dpath_t, gsrf_grid gr,
+                                              int ntu, int ntv, double f0_over_c, float two_pi_df_over_c,
+                                              View* __restrict__ view, Cover* __restrict__ cover,
+                                              uint32_t* __restrict__ dkey) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (k >= g.n) return;
+    const size_t o = (size_t)r * g.n + k;
+    const float rx = rxp[3 * r], ry = rxp[3 * r + 1], rz = rxp[3 * r + 2];
+    const float mx = g.means[3 * k], my = g.means[3 * k + 1], mz = g.means[3 * k + 2];
+    const GShape sh = shape[k];
+    // whitened receiver offset (FP32, contraction allowed: not a decision)
+    const float ux = rx - mx, uy = ry - my, uz = rz - mz;
+    View v;
+    v.w[0] = sh.W[0] * ux + sh.W[1] * uy + sh.W[2] * uz;
+    v.w[1] = sh.W[3] * ux + sh.W[4] * uy + sh.W[5] * uz;
+    v.w[2] = sh.W[6] * ux + sh.W[7] * uy + sh.W[8] * uz;
+    // depth key and coverage: deterministic FP32 on c = mu - r
+    const float cx = dsub(mx, rx), cy = dsub(my, ry), cz = dsub(mz, rz);
+    const float D = dsqrt(dadd(dadd(dmul(cx, cx), dmul(cy, cy)), dmul(cz, cz)));
+    dkey[o] = __float_as_uint(D);
+    const float lsm = fmaxf(fmaxf(g.log_scales[3 * k], g.log_scales[3 * k + 1]), g.log_scales[3 * k + 2]);
+    cover[o] = cover_of(cx, cy, cz, lsm, gr, ntu, ntv);
+    // path phase: d = |t - mu| + |mu - r| and d f0 / c reduced to [0, 1) in FP64
+    const double ex = (double)mx - rx, ey = (double)my - ry, ez = (double)mz - rz;
+    const double d = dpath_t[k] + sqrt(ex * ex + ey * ey + ez * ez);
+    const double cyc = d * f0_over_c;
+    const float fr = (float)(cyc - floor(cyc));
+    float s, c;
+    sincospif(2.0f * fr, &s, &c);
+    v.er = c;
+    v.ei = -s;
+    v.omd = two_pi_df_over_c * (float)d;
+    v.pad0 = v.pad1 = 0.0f;
+    view[o] = v;
+}
+
+cudaError_t launch_project(const gsrf_plan* p, const Layout& L, const gsrf_gaussians* g, const float* rx,
+                           const float* tx, void* ws, cudaStream_t st) {
+    DevStatus* status = at<DevStatus>(ws, L.status);
+    k_status_init<<<1, 32, 0, st>>>(status);
+    if (L.n == 0) return cudaGetLastError();
+    const unsigned nb = (unsigned)((L.n + 255) / 256);
+    k_prepare<<<nb, 256, 0, st>>>(*g, tx, at<GShape>(ws, L.gshape), at<double>(ws, L.dpath), status);
+    k_view<<<dim3(nb, L.n_rx), 256, 0, st>>>(*g, rx, at<GShape>(ws, L.gshape), at<double>(ws, L.dpath),
+                                              p->grid, L.ntu, L.ntv, p->f0_hz / kC,
+                                              (float)(2.0 * 3.14159265358979323846 * p->df_hz / kC),
+                                              at<View>(ws, L.view), at<Cover>(ws, L.cover),
+                                              at<uint32_t>(ws, L.dkey));
+    return cudaGetLastError();
+}
+
+}  // namespace gsrf

@@ -1,0 +1,172 @@
+"""PyTorch-facing wrapper of libgsrf.so.
+
+PyTorch supplies device memory and the current stream; every computation runs in the
+library's kernels through the C ABI (``_lib``).  Parameters are the raw learnable
+tensors of Sec. 4.2: means [K,3], log_scales [K,3], quats [K,4] (w,x,y,z),
+opacity_logit [K], coeffs [K,16,2], phase_b [K].
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib as L
+
+PARAM_NAMES = ("means", "log_scales", "quats", "opacity_logit", "coeffs", "phase_b")
+
+
+def make_grid(n_az: int, n_el: int, az0_deg: float = 0.0, daz_deg: float | None = None,
+              el0_deg: float = 0.0, del_deg: float | None = None, r_rx: float = 1.0,
+              eps_T: float = 1e-4, alpha_max: float = 0.99, tile_w: int = 16, tile_h: int = 16) -> L.gsrf_grid:
+    """Receiving-plane grid; defaults span azimuth [0, 360) and elevation [0, 90)."""
+    if daz_deg is None:
+        daz_deg = 360.0 / n_az
+    if del_deg is None:
+        del_deg = 90.0 / n_el
+    return L.gsrf_grid(n_az, n_el, az0_deg, daz_deg, el0_deg, del_deg, r_rx, eps_T, alpha_max, tile_w, tile_h)
+
+
+def grid_from_spec(spec: dict, **kw) -> L.gsrf_grid:
+    args = dict(spec)
+    args.update(kw)
+    return make_grid(**args)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def gaussians_struct(p: dict) -> L.gsrf_gaussians:
+    for k in PARAM_NAMES[:5]:
+        t = p[k]
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise ValueError("%s must be a contiguous float32 CUDA tensor" % k)
+    pb = p.get("phase_b")
+    n = p["means"].shape[0]
+    return L.gsrf_gaussians(n, p["means"].data_ptr(), p["log_scales"].data_ptr(), p["quats"].data_ptr(),
+                            p["opacity_logit"].data_ptr(), p["coeffs"].data_ptr(),
+                            None if pb is None else pb.data_ptr())
+
+
+def to_device(params: dict, device="cuda") -> dict:
+    return {k: torch.as_tensor(params[k]).to(device=device, dtype=torch.float32).contiguous()
+            for k in PARAM_NAMES if k in params and params[k] is not None}
+
+
+class Renderer:
+    """One render problem (one scene, n_rx receivers, one transmitter) with its workspace.
+
+    The workspace holds every intermediate (records, sort buffers, pair lists); it is
+    sized once and reused.  ``pair_capacity`` grows on demand when a bin reports that
+    it needed more room (``ensure_capacity``)."""
+
+    def __init__(self, n_gauss: int, n_rx: int, grid: L.gsrf_grid, f0_hz: float, df_hz: float = 0.0,
+                 n_f: int = 1, pair_capacity: int | None = None, device="cuda"):
+        self.device = torch.device(device)
+        if pair_capacity is None:
+            pair_capacity = max(1024, 8 * n_gauss * n_rx)
+        self.plan = L.gsrf_plan(n_gauss, n_rx, n_f, f0_hz, df_hz, grid, int(pair_capacity))
+        self._alloc()
+
+    def _alloc(self):
+        nbytes = C.c_size_t()
+        L.call("gsrf_workspace_size", C.byref(self.plan), C.byref(nbytes))
+        self.ws_bytes = nbytes.value
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        assert self.ws.data_ptr() % 256 == 0
+
+    @property
+    def n_rx(self):
+        return self.plan.n_rx
+
+    def out_shape(self):
+        g = self.plan.grid
+        return (self.plan.n_rx, self.plan.n_f, g.n_el, g.n_az, 2)
+
+    def ray_state(self):
+        n = L.load().gsrf_ray_state_bytes(C.byref(self.plan))
+        return torch.empty(n, dtype=torch.uint8, device=self.device)
+
+    def project(self, params: dict, rx: torch.Tensor, tx: torch.Tensor, stream=None):
+        gs = gaussians_struct(params)
+        L.call("gsrf_project", C.byref(self.plan), C.byref(gs), _ptr(rx), _ptr(tx), _ptr(self.ws),
+               self.ws_bytes, _stream(stream))
+
+    def bin(self, stream=None):
+        L.call("gsrf_bin", C.byref(self.plan), _ptr(self.ws), self.ws_bytes, _stream(stream))
+
+    def render_fwd(self, params: dict, out: torch.Tensor | None = None, ray_state=None, stream=None):
+        if out is None:
+            out = torch.empty(self.out_shape(), dtype=torch.float32, device=self.device)
+        gs = gaussians_struct(params)
+        L.call("gsrf_render_fwd", C.byref(self.plan), C.byref(gs), _ptr(self.ws), self.ws_bytes,
+               _ptr(out), _ptr(ray_state), _stream(stream))
+        return out
+
+    def forward(self, params: dict, rx: torch.Tensor, tx: torch.Tensor, out=None, ray_state=None,
+                stream=None):
+        if out is None:
+            out = torch.empty(self.out_shape(), dtype=torch.float32, device=self.device)
+        gs = gaussians_struct(params)
+        L.call("gsrf_render", C.byref(self.plan), C.byref(gs), _ptr(rx), _ptr(tx), _ptr(self.ws),
+               self.ws_bytes, _ptr(out), _ptr(ray_state), _stream(stream))
+        return out
+
+    def status(self, stream=None) -> L.gsrf_run_status:
+        s = L.gsrf_run_status()
+        L.call("gsrf_read_status", _ptr(self.ws), self.ws_bytes, C.byref(s), _stream(stream))
+        return s
+
+    def ensure_capacity(self, params: dict, rx: torch.Tensor, tx: torch.Tensor, slack: float = 1.05):
+        """Run project + bin; if the pairs did not fit, grow the workspace and retry."""
+        for _ in range(3):
+            self.project(params, rx, tx)
+            self.bin()
+            s = self.status()
+            if s.code == L.GSRF_ERR_CAPACITY:
+                self.plan.pair_capacity = int(s.required_pairs * slack) + 1024
+                self._alloc()
+                continue
+            L.check("gsrf_bin (device status)", s.code)
+            return s.required_pairs
+        raise L.GsrfError("ensure_capacity", L.GSRF_ERR_CAPACITY)
+
+    def layout(self) -> L.gsrf_layout:
+        lay = L.gsrf_layout()
+        L.call("gsrf_workspace_layout", C.byref(self.plan), C.byref(lay))
+        return lay
+
+    def pairs(self):
+        """Views into the workspace after bin: (keys uint64 [total], ids int32 [total],
+        rx_base int64 [n_rx+1], tile_start int32 [n_rx, n_tiles+1])."""
+        lay = self.layout()
+        nt = lay.n_tiles_u * lay.n_tiles_v
+        nr = self.plan.n_rx
+        ws = self.ws
+        rb = ws[lay.rx_pair_base: lay.rx_pair_base + 8 * (nr + 1)].view(torch.int64)
+        total = int(rb[-1].item())
+        keys = ws[lay.pair_keys: lay.pair_keys + 8 * total].view(torch.int64)
+        ids = ws[lay.pair_ids: lay.pair_ids + 4 * total].view(torch.int32)
+        ts = ws[lay.tile_start: lay.tile_start + 4 * nr * (nt + 1)].view(torch.int32).view(nr, nt + 1)
+        return keys, ids, rb, ts
+
+
+def received_signal(rays: torch.Tensor, mode: int = L.SIG_COMPLEX_SUM, stream=None) -> torch.Tensor:
+    """rays [n_rx, n_f, n_el, n_az, 2] -> per mode (see include/gsrf.h)."""
+    if not (rays.is_cuda and rays.dtype == torch.float32 and rays.is_contiguous() and rays.dim() == 5):
+        raise ValueError("rays must be a contiguous float32 CUDA tensor [n_rx, n_f, n_el, n_az, 2]")
+    n_rx, n_f, n_el, n_az, _ = rays.shape
+    if mode == L.SIG_COMPLEX_SUM:
+        out = torch.empty((n_rx, n_f, 2), dtype=torch.float32, device=rays.device)
+    elif mode == L.SIG_SPECTRUM_MAG:
+        out = torch.empty((n_rx, n_f, n_el, n_az), dtype=torch.float32, device=rays.device)
+    else:
+        out = torch.empty((n_rx, n_f), dtype=torch.float32, device=rays.device)
+    L.call("gsrf_received_signal", _ptr(rays), n_rx, n_f, n_el, n_az, mode, _ptr(out), _stream(stream))
+    return out

@@ -1,0 +1,122 @@
+"""The C ABI without a GPU: the library loads, exports every call include/gsrf.h
+declares, its struct layouts match the ctypes mirrors, and its host-side argument
+checks and workspace sizing behave.  No kernel is launched here."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2502_01826_gb300 import _build, _lib as L
+from paper_2502_01826_gb300.render import make_grid
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gsrf.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return L.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gsrf_[a-z_]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree():
+    assert declared_functions() == sorted(L.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.SO], capture_output=True, text=True).stdout
+    for name in declared_functions():
+        assert re.search(r"\bT %s\b" % name, out), name
+    assert lib.gsrf_version().startswith(b"gsrf-gb300")
+
+
+def test_struct_layouts_match_header(tmp_path):
+    prog = tmp_path / "layout.c"
+    prog.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "gsrf.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(gsrf_grid), sizeof(gsrf_gaussians), sizeof(gsrf_plan),
+         sizeof(gsrf_layout), sizeof(gsrf_run_status));
+  printf("%zu %zu %zu %zu\\n", offsetof(gsrf_plan, f0_hz), offsetof(gsrf_plan, grid),
+         offsetof(gsrf_plan, pair_capacity), offsetof(gsrf_run_status, stats));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    sizes = [int(x) for x in lines[0].split()]
+    offs = [int(x) for x in lines[1].split()]
+    assert sizes == [C.sizeof(L.gsrf_grid), C.sizeof(L.gsrf_gaussians), C.sizeof(L.gsrf_plan),
+                     C.sizeof(L.gsrf_layout), C.sizeof(L.gsrf_run_status)]
+    assert offs == [L.gsrf_plan.f0_hz.offset, L.gsrf_plan.grid.offset, L.gsrf_plan.pair_capacity.offset,
+                    L.gsrf_run_status.stats.offset]
+
+
+def plan(n=1000, n_rx=4, n_az=360, n_el=90, cap=100000, **kw):
+    return L.gsrf_plan(n, n_rx, kw.get("n_f", 1), kw.get("f0", 2.4e9), kw.get("df", 0.0),
+                       make_grid(n_az, n_el, **kw.get("grid", {})), cap)
+
+
+def test_workspace_size_grows_with_problem(lib):
+    a, b = C.c_size_t(), C.c_size_t()
+    assert lib.gsrf_workspace_size(C.byref(plan()), C.byref(a)) == L.GSRF_OK
+    assert lib.gsrf_workspace_size(C.byref(plan(n=2000)), C.byref(b)) == L.GSRF_OK
+    assert b.value > a.value > 0
+    assert lib.gsrf_workspace_size(C.byref(plan(cap=200000)), C.byref(b)) == L.GSRF_OK
+    assert b.value >= a.value + 100000 * 24
+    lay = L.gsrf_layout()
+    assert lib.gsrf_workspace_layout(C.byref(plan()), C.byref(lay)) == L.GSRF_OK
+    assert (lay.n_tiles_u, lay.n_tiles_v) == (23, 6)
+    assert lay.status == 0 and lay.pair_keys % 256 == 0 and lay.tile_start % 256 == 0
+    assert lib.gsrf_ray_state_bytes(C.byref(plan())) == 4 * 360 * 90 * 16
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n=-1), dict(n_rx=0), dict(n_f=0), dict(n_f=65), dict(f0=0.0), dict(cap=-5),
+    dict(n_az=0, grid=dict(daz_deg=1.0)), dict(grid=dict(daz_deg=0.0)), dict(grid=dict(alpha_max=1.0)),
+    dict(grid=dict(eps_T=-1.0)), dict(grid=dict(az0_deg=400.0)),
+])
+def test_invalid_plans_rejected_synchronously(lib, bad):
+    kw = dict(bad)
+    p = plan(**{k: v for k, v in kw.items() if k in ("n", "n_rx", "n_az", "n_el", "cap")},
+             **{k: v for k, v in kw.items() if k in ("n_f", "f0", "grid")})
+    sz = C.c_size_t()
+    assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_ERR_INVALID_ARG
+
+
+def test_unsupported_configurations(lib):
+    sz = C.c_size_t()
+    p = plan(grid=dict(tile_w=8))
+    assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_ERR_UNSUPPORTED
+    p = plan(n_az=2000)  # more than 64 azimuth tiles
+    assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_ERR_UNSUPPORTED
+
+
+def test_calls_reject_bad_pointers_before_launch(lib):
+    p = plan()
+    g = L.gsrf_gaussians(1000, None, None, None, None, None, None)
+    sz = C.c_size_t()
+    lib.gsrf_workspace_size(C.byref(p), C.byref(sz))
+    # null workspace, misaligned workspace, short workspace, null Gaussians
+    assert lib.gsrf_project(C.byref(p), C.byref(g), C.c_void_p(256), C.c_void_p(256), None, sz.value,
+                            None) == L.GSRF_ERR_INVALID_ARG
+    assert lib.gsrf_bin(C.byref(p), C.c_void_p(4096 + 8), sz.value, None) == L.GSRF_ERR_INVALID_ARG
+    assert lib.gsrf_bin(C.byref(p), C.c_void_p(4096), sz.value - 1, None) == L.GSRF_ERR_INVALID_ARG
+    assert lib.gsrf_project(C.byref(p), C.byref(g), C.c_void_p(256), C.c_void_p(256), C.c_void_p(4096),
+                            sz.value, None) == L.GSRF_ERR_INVALID_ARG
+    assert lib.gsrf_received_signal(None, 1, 1, 1, 1, 0, None, None) == L.GSRF_ERR_INVALID_ARG
+    assert lib.gsrf_received_signal(C.c_void_p(256), 1, 1, 1, 1, 9, C.c_void_p(256), None) == \
+        L.GSRF_ERR_INVALID_ARG

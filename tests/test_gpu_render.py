@@ -1,0 +1,210 @@
+"""GPU parity of the forward path (project -> bin -> render -> received signal)
+against the FP64 oracle, through the C ABI.
+
+Bars: splat keys, per-tile id lists and tile ranges bit-exact; per-ray complex signal
+within 1e-4 (relative L2 and per ray, see gpu_util); RSSI within 0.01 dB.  Rays on
+which FP32 and FP64 may take a different discrete decision are flagged by the oracle
+and excluded from the per-ray comparison (counted, and bounded)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2502_01826_gb300 import _lib as L
+from paper_2502_01826_gb300 import synthetic
+from paper_2502_01826_gb300.render import Renderer, make_grid, received_signal, to_device
+
+from gpu_util import (BANDS, TOL_DB, compare, gpu_render, oracle_grid, require_gpu, rssi_db)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+    oracle.build()
+
+
+def oracle_render(scene, rx, tx, f0, spec, rays=None, **kw):
+    g = oracle_grid(spec, **kw)
+    return oracle.render(scene, rx, tx, f0, g, rays=rays, bands=BANDS)
+
+
+def check_bins(R: Renderer, scene, rx_all, spec, **kw):
+    """Keys, ids and tile ranges of every receiver equal the oracle's, bit for bit."""
+    keys, ids, rb, ts = R.pairs()
+    keys = keys.cpu().numpy().view(np.uint64)
+    ids = ids.cpu().numpy().view(np.uint32)
+    rb = rb.cpu().numpy()
+    ts = ts.cpu().numpy()
+    g = oracle_grid(spec, **kw)
+    for r in range(rx_all.shape[0]):
+        k_ref, i_ref, t_ref = oracle.bin_pairs(scene, rx_all[r], g)
+        assert rb[r + 1] - rb[r] == len(k_ref)
+        assert np.array_equal(keys[rb[r]:rb[r + 1]], k_ref), "keys differ for receiver %d" % r
+        assert np.array_equal(ids[rb[r]:rb[r + 1]], i_ref), "ids differ for receiver %d" % r
+        assert np.array_equal(ts[r].astype(np.int64), t_ref), "tile ranges differ for receiver %d" % r
+
+
+# --------------------------------------------------------------------------- C1
+
+def test_plain_forward_2k_matches_oracle():
+    cfg = synthetic.config_plain()
+    S, R, p, out = gpu_render(cfg["scene"], cfg["rx"], cfg["tx"], cfg["f0"], cfg["grid"])
+    ref = oracle_render(cfg["scene"], cfg["rx"][0], cfg["tx"], cfg["f0"], cfg["grid"])
+    res = compare(S[0], ref)
+    assert res["excluded"] <= 0.05 * S.shape[1]
+    check_bins(R, cfg["scene"], cfg["rx"], cfg["grid"])
+    # received signal through the library's reduction vs the oracle's coherent sum
+    db = received_signal(out, L.SIG_RSSI_DB).cpu().numpy()[0, 0]
+    assert abs(db - rssi_db(ref["S"][0])) <= TOL_DB
+    # statistics: candidate tests and composited pairs
+    st = R.status()
+    assert st.code == 0
+    assert abs(st.stats[0] - ref["ntest"].sum()) <= 0.01 * ref["ntest"].sum()
+    assert abs(st.stats[1] - ref["nhit"].sum()) <= 0.01 * ref["nhit"].sum()
+
+
+@pytest.mark.parametrize("eps_T", [0.0, 1e-2])
+def test_plain_forward_termination_settings(eps_T):
+    cfg = synthetic.config_plain()
+    S, R, p, out = gpu_render(cfg["scene"], cfg["rx"], cfg["tx"], cfg["f0"], cfg["grid"], eps_T=eps_T)
+    ref = oracle_render(cfg["scene"], cfg["rx"][0], cfg["tx"], cfg["f0"], cfg["grid"], eps_T=eps_T)
+    res = compare(S[0], ref)
+    assert res["excluded"] <= 0.05 * S.shape[1]
+
+
+# --------------------------------------------------------------------------- grids, receivers
+
+@pytest.mark.parametrize("spec", [
+    dict(n_az=30, n_el=7, az0_deg=10.0, daz_deg=9.0, el0_deg=-20.0, del_deg=7.0),  # ragged, offset
+    dict(n_az=100, n_el=37, az0_deg=-45.0, daz_deg=1.7, el0_deg=-30.0, del_deg=2.5),
+    dict(n_az=72, n_el=18),
+    dict(n_az=180, n_el=45),
+])
+def test_grids_and_receivers(spec):
+    scene = synthetic.tiny_scene(400, 101, box=(6.0, 5.0, 3.0), log_scale_mu=math.log(0.2))
+    rng = np.random.default_rng(3)
+    rx = (rng.uniform(0, 1, (3, 3)) * [6.0, 5.0, 3.0]).astype(np.float32)
+    tx = np.array([0.5, 4.5, 2.5], np.float32)
+    S, R, p, out = gpu_render(scene, rx, tx, 2.4e9, spec)
+    check_bins(R, scene, rx, spec)
+    for r in range(3):
+        ref = oracle_render(scene, rx[r], tx, 2.4e9, spec)
+        res = compare(S[r], ref)
+        assert res["excluded"] <= 0.05 * S.shape[1]
+
+
+def test_gaussians_around_the_receiver():
+    """Gaussians enclosing the receiver, straddling the emitting sphere, inside it."""
+    scene = synthetic.tiny_scene(300, 102, box=(3.0, 3.0, 2.0), log_scale_mu=math.log(0.4))
+    rx = np.array([[1.5, 1.5, 1.0]], np.float32)
+    scene["means"][:5] = rx[0] + np.array([[0, 0, 0], [0.3, 0, 0], [0, 0.9, 0.1], [1.0, 0, 0.2],
+                                           [0, 0, 0.5]], np.float32)
+    tx = np.array([0.2, 2.8, 0.3], np.float32)
+    spec = dict(n_az=72, n_el=18)
+    S, R, p, out = gpu_render(scene, rx, tx, 915e6, spec)
+    check_bins(R, scene, rx, spec)
+    ref = oracle_render(scene, rx[0], tx, 915e6, spec)
+    compare(S[0], ref)
+
+
+# --------------------------------------------------------------------------- edge cases
+
+def test_empty_scene_gives_zero():
+    scene = synthetic.tiny_scene(0, 1)
+    S, R, p, out = gpu_render(scene, [[1, 1, 1]], [2, 2, 2], 2.4e9, dict(n_az=36, n_el=9), cap=0)
+    assert np.all(S == 0)
+    assert R.status().code == 0
+
+
+def test_zero_opacity_gives_zero():
+    scene = synthetic.tiny_scene(200, 103)
+    scene["opacity_logit"][:] = -1e4
+    S, R, p, out = gpu_render(scene, [[2, 2, 1]], [1, 1, 1], 2.4e9, dict(n_az=72, n_el=18))
+    assert np.all(S == 0)
+
+
+def test_single_gaussian():
+    scene = synthetic.tiny_scene(1, 104)
+    scene["means"][0] = [3.0, 2.0, 1.5]
+    rx = np.array([[1.0, 1.0, 1.0]], np.float32)
+    S, R, p, out = gpu_render(scene, rx, [0.5, 0.5, 0.5], 2.4e9, dict(n_az=360, n_el=90))
+    ref = oracle_render(scene, rx[0], np.array([0.5, 0.5, 0.5], np.float32), 2.4e9, dict(n_az=360, n_el=90))
+    assert np.count_nonzero(ref["S"][0]) > 20
+    compare(S[0], ref)
+
+
+def test_capacity_overflow_reports_required_pairs():
+    cfg = synthetic.config_plain()
+    g = oracle_grid(cfg["grid"])
+    total = len(oracle.bin_pairs(cfg["scene"], cfg["rx"][0], g)[0])
+    S, R, p, out = gpu_render(cfg["scene"], cfg["rx"], cfg["tx"], cfg["f0"], cfg["grid"], cap=total - 1)
+    st = R.status()
+    assert st.code == L.GSRF_ERR_CAPACITY and st.required_pairs == total
+    assert np.all(S == 0)
+    S2, R2, _, _ = gpu_render(cfg["scene"], cfg["rx"], cfg["tx"], cfg["f0"], cfg["grid"], cap=total)
+    assert R2.status().code == 0 and np.count_nonzero(S2) > 0
+
+
+def test_nonfinite_parameter_is_reported():
+    scene = synthetic.tiny_scene(100, 105)
+    scene["means"][37, 1] = np.nan
+    scene["coeffs"][60, 3, 1] = np.inf
+    S, R, p, out = gpu_render(scene, [[2, 2, 1]], [1, 1, 1], 2.4e9, dict(n_az=36, n_el=9), cap=100000)
+    st = R.status()
+    assert st.code == L.GSRF_ERR_NONFINITE and st.first_bad == 37
+
+
+def test_render_is_deterministic():
+    cfg = synthetic.config_plain()
+    a = gpu_render(cfg["scene"], cfg["rx"], cfg["tx"], cfg["f0"], cfg["grid"])[0]
+    b = gpu_render(cfg["scene"], cfg["rx"], cfg["tx"], cfg["f0"], cfg["grid"])[0]
+    assert np.array_equal(a, b)
+
+
+def test_received_signal_modes_match_fp64_sums():
+    cfg = synthetic.config_plain()
+    S, R, p, out = gpu_render(cfg["scene"], np.repeat(cfg["rx"], 3, 0) + np.float32([[0, 0, 0], [0.5, 0, 0],
+                                                                                      [0, 0.5, 0.2]]),
+                              cfg["tx"], cfg["f0"], cfg["grid"])
+    Sd = S.astype(np.complex128)
+    cs = received_signal(out, L.SIG_COMPLEX_SUM).cpu().numpy()
+    assert np.allclose(cs[:, 0, 0] + 1j * cs[:, 0, 1], Sd.sum(1), rtol=1e-6, atol=1e-7)
+    db = received_signal(out, L.SIG_RSSI_DB).cpu().numpy()[:, 0]
+    assert np.allclose(db, 20 * np.log10(np.abs(Sd.sum(1))), atol=1e-4)
+    pw = received_signal(out, L.SIG_POWER_SUM).cpu().numpy()[:, 0]
+    assert np.allclose(pw, (np.abs(Sd) ** 2).sum(1), rtol=1e-6)
+    mg = received_signal(out, L.SIG_SPECTRUM_MAG).cpu().numpy()
+    assert np.allclose(mg.reshape(3, -1), np.abs(S), rtol=1e-6, atol=1e-9)
+
+
+# --------------------------------------------------------------------------- full size
+
+def test_ble_50k_64rx_full_size_sampled():
+    """The benchmark's workload in its launch configuration: all 64 receivers in one
+    call; bins of two receivers bit-exact, 400 sampled rays of four receivers and the
+    RSSI of two receivers against the oracle."""
+    cfg = synthetic.config_ble()
+    S, R, p, out = gpu_render(cfg["scene"], cfg["rx"], cfg["tx"], cfg["f0"], cfg["grid"])
+    n_rays = S.shape[1]
+    rng = np.random.default_rng(7)
+    keys, ids, rb, ts = R.pairs()
+    rb = rb.cpu().numpy()
+    g = oracle_grid(cfg["grid"])
+    for r in (0, 63):
+        k_ref, i_ref, t_ref = oracle.bin_pairs(cfg["scene"], cfg["rx"][r], g)
+        assert np.array_equal(keys[rb[r]:rb[r + 1]].cpu().numpy().view(np.uint64), k_ref)
+        assert np.array_equal(ids[rb[r]:rb[r + 1]].cpu().numpy().view(np.uint32), i_ref)
+        assert np.array_equal(ts[r].cpu().numpy().astype(np.int64), t_ref)
+    for r in (1, 17, 40, 62):
+        rays = np.sort(rng.choice(n_rays, 400, replace=False)).astype(np.int32)
+        ref = oracle.render(cfg["scene"], cfg["rx"][r], cfg["tx"], cfg["f0"], g, rays=rays, bands=BANDS)
+        res = compare(S[r, rays], ref)
+        assert res["excluded"] <= 0.05 * len(rays)
+    db = received_signal(out, L.SIG_RSSI_DB).cpu().numpy()[:, 0]
+    for r in (5, 33):
+        ref = oracle.render(cfg["scene"], cfg["rx"][r], cfg["tx"], cfg["f0"], g)
+        assert abs(db[r] - rssi_db(ref["S"][0])) <= TOL_DB
