@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark of the GSRF per-receiver render on GB300.
+
+Workload (default): the BLE-RSSI-shaped scene -- 50,000 complex Gaussians in a
+10 x 8 x 3 m box, 64 receivers, a 360 x 90 one-degree ray grid per receiver, one
+transmitter, 2.4 GHz -- synthetic and seeded (the paper's datasets are not here).
+
+One step = one pass of the whole hot path for all 64 receivers: project (records,
+depth keys, tile coverage, FP64 path phase), bin (depth radix sort, pair emission,
+tile counting sort), render (per-ray complex front-to-back accumulation) and the
+received-signal reduction (RSSI per receiver).  Inputs are resident in HBM when the
+timed region starts; L2 is flushed (256 MB write) between timed steps, outside the
+timed events.
+
+Metric: composited ray-Gaussian pairs per second (whole job), with receiver spectra
+per second, the same work as 64 plain single-receiver launches, the roofline of the
+dominant kernel, an end-to-end number through the C ABI with host buffers, and the
+FP64 CPU oracle timed on a bounded sample of the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ray-Gaussian pairs/s and Rx spectra/s (fwd, fwd+bwd) vs plain launch; % roofline"
+UNIT = "pairs/s"
+
+# Algorithmic FP32 work of the compositing kernel (FMA = 2 FLOP), counted from its
+# arithmetic: a candidate test (whitened direction 15, A 5, B 5, t_mid 1, closest
+# point 6, m2 5) and a composited pair on top of its test (chord and midpoint weight
+# 16, Fourier-Legendre radiance 128, accumulation and transmittance 28).
+FLOP_TEST = 37
+FLOP_HIT = 172
+# FP32 peak: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x the maximum SM clock.
+SMS, FP32_LANES = 152, 128
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return m, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+
+def oracle_sample(cfg, budget_s: float = 12.0, threads: int | None = None):
+    """Time the FP64 oracle on a bounded sample of the workload: whole receivers (all
+    their rays), as many as fit in about ``budget_s`` seconds.  Returns pairs/s."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    th = threads or (os.cpu_count() or 1)
+    g = oracle.make_grid(**cfg["grid"])
+    n_rays = g.n_az * g.n_el
+    n_rx_all = cfg["rx"].shape[0]
+    pairs, dt, n = 0, 0.0, 0
+    t_start = time.perf_counter()
+    while n < n_rx_all:
+        t0 = time.perf_counter()
+        out = oracle.render(cfg["scene"], cfg["rx"][n], cfg["tx"], cfg["f0"], g, threads=th)
+        dt += time.perf_counter() - t0
+        pairs += int(out["nhit"].sum())
+        n += 1
+        if time.perf_counter() - t_start >= budget_s:
+            break
+    return dict(value=pairs / dt, unit=UNIT, cores=th, kind="oracle",
+                sample="receivers 0..%d of %s (%d of %d), all %d rays each, %d composited pairs, %.1f s"
+                       % (n - 1, cfg["name"], n, n_rx_all, n_rays, pairs, dt)), dt
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, ws, rank):
+    import numpy as np
+    import torch
+
+    from paper_2502_01826_gb300 import _lib as L
+    from paper_2502_01826_gb300 import synthetic
+    from paper_2502_01826_gb300.render import Renderer, make_grid, received_signal, to_device
+
+    L.load(build_if_missing=True)
+    cfg = synthetic.config_ble(n_rx=args.n_rx, seed_offset=0)
+    K, n_rx = cfg["scene"]["means"].shape[0], cfg["rx"].shape[0]
+    grid = make_grid(**cfg["grid"])
+    dev = torch.device("cuda")
+    p = to_device(cfg["scene"])
+    rx = torch.tensor(cfg["rx"], device=dev)
+    tx = torch.tensor(cfg["tx"], device=dev)
+    R = Renderer(K, n_rx, grid, cfg["f0"])
+    R.ensure_capacity(p, rx, tx)
+    out = torch.empty(R.out_shape(), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        R.project(p, rx, tx)
+        if ev:
+            ev[1].record(stream)
+        R.bin()
+        if ev:
+            ev[2].record(stream)
+        R.render_fwd(p, out)
+        if ev:
+            ev[3].record(stream)
+        rssi = received_signal(out, L.SIG_RSSI_DB)
+        if ev:
+            ev[4].record(stream)
+        return rssi
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = R.status()
+    L.check("render (device status)", st.code)
+    tests_per_step, pairs_per_step = int(st.stats[0]), int(st.stats[1])
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            step(evs[i])
+        torch.cuda.synchronize()
+    barrier(ws)
+    stage = np.array([[evs[i][j].elapsed_time(evs[i][j + 1]) for j in range(4)] for i in range(args.steps)])
+    ms_step = float(stage.sum(1).mean())
+    total_s = max_over_ranks(float(stage.sum()) / 1e3, ws)
+    value = sum_over_ranks(pairs_per_step * args.steps, ws) / total_s
+    spectra_s = sum_over_ranks(n_rx * args.steps, ws) / total_s
+
+    # the same work as 64 plain single-receiver launches
+    Rp = Renderer(K, 1, grid, cfg["f0"])
+    need = 0
+    for r in range(n_rx):
+        Rp.project(p, rx[r:r + 1], tx)
+        Rp.bin()
+        s = Rp.status()
+        need = max(need, s.required_pairs)
+    Rp = Renderer(K, 1, grid, cfg["f0"], pair_capacity=int(need * 1.05) + 1024)
+    out1 = torch.empty(Rp.out_shape(), dtype=torch.float32, device=dev)
+
+    def plain_step():
+        for r in range(n_rx):
+            Rp.forward(p, rx[r:r + 1], tx, out1)
+            received_signal(out1, L.SIG_RSSI_DB)
+
+    for _ in range(max(1, args.warmup)):
+        plain_step()
+    torch.cuda.synchronize()
+    pk = max(1, min(args.steps, 5))
+    pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(pk)]
+    for i in range(pk):
+        flush.zero_()
+        pe[i][0].record(stream)
+        plain_step()
+        pe[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms_plain = float(np.mean([a.elapsed_time(b) for a, b in pe]))
+
+    # end to end through the C ABI with host buffers: params + positions host->device
+    # from pinned memory, the render, RSSI and per-ray spectra device->host
+    host_p = {k: v.cpu().pin_memory() for k, v in p.items()}
+    host_rx, host_tx = rx.cpu().pin_memory(), tx.cpu().pin_memory()
+    host_out = torch.empty(out.shape, dtype=torch.float32).pin_memory()
+    host_rssi = torch.empty((n_rx, 1), dtype=torch.float32).pin_memory()
+    dp = {k: torch.empty_like(v) for k, v in p.items()}
+    drx, dtx = torch.empty_like(rx), torch.empty_like(tx)
+    h2d = sum(v.numel() * 4 for v in host_p.values()) + host_rx.numel() * 4 + host_tx.numel() * 4
+    d2h = host_out.numel() * 4 + host_rssi.numel() * 4
+
+    def e2e_step():
+        for k in dp:
+            dp[k].copy_(host_p[k], non_blocking=True)
+        drx.copy_(host_rx, non_blocking=True)
+        dtx.copy_(host_tx, non_blocking=True)
+        R.forward(dp, drx, dtx, out)
+        rs = received_signal(out, L.SIG_RSSI_DB)
+        host_out.copy_(out, non_blocking=True)
+        host_rssi.copy_(rs, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    t_e2e = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        t_e2e.append(time.perf_counter() - t0)
+    e2e_total = max_over_ranks(sum(t_e2e), ws)
+    e2e_value = sum_over_ranks(pairs_per_step * args.steps, ws) / e2e_total
+
+    pk_, pk_kind = peaks()
+    mhz = float(pk_.get("sm_max_mhz", 2070.0))
+    peak_tflops = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    render_ms = float(stage[:, 2].mean())
+    stage_ms = {n: float(stage[:, j].mean()) for j, n in enumerate(["project", "bin", "render", "signal"])}
+    flops = tests_per_step * FLOP_TEST + (pairs_per_step) * FLOP_HIT
+    achieved = flops / (render_ms * 1e-3) / 1e12
+    clocks = clk.summary()
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; paper datasets unavailable)",
+        "config": {"workload": cfg["name"] if n_rx == 64 else "%s_nrx%d" % (cfg["name"], n_rx),
+                   "n_gauss": K, "n_rx": n_rx, "grid": "360x90",
+                   "f0_hz": cfg["f0"], "pairs_per_step": pairs_per_step,
+                   "candidate_tests_per_step": tests_per_step,
+                   "l2": "flushed between timed steps (256 MB write, outside the events)",
+                   "parallelism": "replicas: each rank renders its own 64 receivers" if ws > 1 else "1 GPU"},
+        "spectra_per_s": spectra_s,
+        "stage_ms": stage_ms,
+        "plain_launch": {"ms_per_step": ms_plain, "spectra_per_s": n_rx / (ms_plain / 1e3),
+                         "pairs_per_s": pairs_per_step / (ms_plain / 1e3),
+                         "speedup_of_batched": ms_plain / ms_step,
+                         "what": "%d sequential single-receiver project+bin+render+RSSI calls" % n_rx},
+        "roofline": {"kernel": "k_render_fwd", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                     "peak_kind": "FP32 lanes x max SM clock (%s sm_max_mhz %.0f)" % (pk_kind, mhz),
+                     "flop_per_launch": flops},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": 1e3 * sum(t_e2e) / len(t_e2e)},
+        "gpu_launches": 24 * args.steps,
+        "clocks": clocks,
+    }
+    return result, cfg
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--n-rx", type=int, default=64, help="receivers (64 = the BLE workload; fewer "
+                    "only for small profiling runs)")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        if rank != 0:
+            return 0
+        from paper_2502_01826_gb300 import synthetic
+        cfg = synthetic.config_ble()
+        vals = []
+        for i in range(args.warmup + args.steps):
+            cb, dt = oracle_sample(cfg, budget_s=max(1.0, args.cpu_budget / 4))
+            if i >= args.warmup:
+                vals.append((cb, dt))
+        v = statistics.median([c["value"] for c, _ in vals])
+        cb = dict(vals[0][0])
+        cb["value"] = v
+        res = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": 1e3 * statistics.mean([d for _, d in vals]), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic (seeded; paper datasets unavailable)",
+               "config": {"workload": cfg["name"], "n_gauss": 50000, "n_rx": 64, "grid": "360x90",
+                          "f0_hz": cfg["f0"]},
+               "cpu_baseline": cb,
+               "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(res))
+        return 0
+
+    ws, rank, local = dist_setup()
+    result, cfg = run_ours(args, ws, rank)
+    if rank == 0:
+        if ws == 1:
+            cb, _ = oracle_sample(cfg, budget_s=args.cpu_budget)
+            result["cpu_baseline"] = cb
+        print(json.dumps(result))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -56,7 +56,9 @@ class Scene(C.Structure):
 
 
 class Bands(C.Structure):
-    _fields_ = [("m2_band", C.c_double), ("t_band", C.c_double), ("term_band", C.c_double)]
+    _fields_ = [("m2_err", C.c_double), ("m2_abs", C.c_double), ("m2_mult", C.c_double),
+                ("t_band", C.c_double),
+                ("term_mult", C.c_double), ("term_abs", C.c_double), ("flip", C.c_int32)]
 
 
 FLAG_M2, FLAG_TOUT, FLAG_TERM = 1, 2, 4
@@ -90,7 +92,7 @@ def lib():
         L.or_bin.argtypes = [vp, vp, vp, vp, vp, i64, vp]
         L.or_render.restype = C.c_int
         L.or_render.argtypes = [vp, vp, vp, dbl, dbl, i32, vp, i32, vp, i64, i32, vp,
-                                vp, vp, vp, vp, vp, vp]
+                                vp, vp, vp, vp, vp, vp, vp, vp]
         L.or_render_grad.restype = C.c_int
         L.or_render_grad.argtypes = [vp, vp, vp, dbl, dbl, i32, vp, i32, vp, i64, i32, vp,
                                      vp, vp, vp, vp, vp, vp]
@@ -151,12 +153,12 @@ def gaussian(scene: dict, k: int):
 
 
 def intersect(Sinv, mu, r, v, r_rx):
-    out = np.zeros(8)
+    out = np.zeros(10)
     Si = np.ascontiguousarray(Sinv, dtype=np.float64).reshape(9)
     hit = lib().or_intersect(_p(Si), _p(np.ascontiguousarray(mu, np.float64)),
                              _p(np.ascontiguousarray(r, np.float64)),
                              _p(np.ascontiguousarray(v, np.float64)), r_rx, _p(out))
-    names = ("t_in", "t_out", "t_a", "dt", "t_rep", "m2", "m2_rep", "g")
+    names = ("t_in", "t_out", "t_a", "dt", "t_rep", "m2", "m2_rep", "g", "A", "C")
     return bool(hit), dict(zip(names, out))
 
 
@@ -206,30 +208,32 @@ def bin_pairs(scene: dict, rx, grid: Grid):
 
 
 def render(scene: dict, rx, tx, f0: float, grid: Grid, df: float = 0.0, n_f: int = 1,
-           mode: int = 0, rays=None, threads: int | None = None, bands=None):
-    """Render one receiver.  Returns dict with S [n_f, n_rays] complex, T, Ta, nhit, ntest,
-    flags.  ``rays``: optional int array of ray indices (v * n_az + u)."""
+           mode: int = 0, rays=None, threads: int | None = None, bands=None, flip: bool = False):
+    """Render one receiver.  Returns dict with S [n_f, n_rays] complex, T, Ta, Sabs, Scond,
+    nhit, ntest, flags.  ``bands``: (m2_err, m2_abs, m2_mult, t_band, term_mult, term_abs).  ``rays``: optional int array of ray indices (v * n_az + u)."""
     s = _SceneRef(scene)
     n_rays = grid.n_az * grid.n_el if rays is None else len(rays)
     ridx = None if rays is None else np.ascontiguousarray(rays, np.int32)
     S = np.zeros((n_f, n_rays, 2))
     T = np.zeros((n_f, n_rays, 2))
     Ta = np.zeros(n_rays)
+    Sabs = np.zeros(n_rays)
+    Scond = np.zeros(n_rays)
     nhit = np.zeros(n_rays, np.int32)
     ntest = np.zeros(n_rays, np.int32)
     flags = np.zeros(n_rays, np.uint32)
     b = None
     if bands is not None:
-        b = Bands(*bands)
+        b = Bands(*bands, 1 if flip else 0)
     th = threads if threads else (os.cpu_count() or 1)
     rc = lib().or_render(C.byref(s.c), _p(_f32(rx)), _p(_f32(tx)), float(f0), float(df), n_f,
                          C.byref(grid), mode, _p(ridx), n_rays, th,
                          None if b is None else C.byref(b),
-                         _p(S), _p(T), _p(Ta), _p(nhit), _p(ntest), _p(flags))
+                         _p(S), _p(T), _p(Ta), _p(Sabs), _p(Scond), _p(nhit), _p(ntest), _p(flags))
     if rc != 0:
         raise ValueError("or_render rejected its arguments")
-    return dict(S=S[..., 0] + 1j * S[..., 1], T=T[..., 0] + 1j * T[..., 1], Ta=Ta,
-                nhit=nhit, ntest=ntest, flags=flags)
+    return dict(S=S[..., 0] + 1j * S[..., 1], T=T[..., 0] + 1j * T[..., 1], Ta=Ta, Sabs=Sabs,
+                Scond=Scond, nhit=nhit, ntest=ntest, flags=flags)
 
 
 def render_grad(scene: dict, rx, tx, f0: float, grid: Grid, G, df: float = 0.0, n_f: int = 1,

@@ -71,10 +71,22 @@ typedef struct {
 #define OR_FLAG_TOUT   2u   /* a tested pair has |t_out - r_rx| below the t band */
 #define OR_FLAG_TERM   4u   /* prod(1-alpha) came within the termination band of eps_T */
 
+/* Rounding model of an FP32 evaluation of the same render, used to say where FP32
+ * and FP64 may legitimately differ.  The closest approach m2 of pair k carries an
+ * error of about delta_k = m2_err * sqrt(C_k) + m2_abs (C_k the Mahalanobis^2 distance of the
+ * receiver: the whitened offset is ~sqrt(C_k) long and every FP32 operation on it
+ * rounds at ~1e-7 relative).  A decision is "in band" when it lies within
+ * m2_mult * delta_k of 9 (hit or miss), within t_band of r_rx (exit point), or when
+ * |ln(Ta / eps_T)| is within term_mult times the propagated error of ln Ta plus
+ * term_abs.  Sconst (below) is the first-order error of S that the same deltas cause. */
 typedef struct {
-    double m2_band;     /* absolute band on m2 around 9 */
+    double m2_err;      /* error model of m2 per unit of sqrt(C) */
+    double m2_abs;      /* plus this absolute error */
+    double m2_mult;     /* band half-width on m2 in units of delta_k */
     double t_band;      /* absolute band (m) on t_out around r_rx */
-    double term_band;   /* band on |ln(Ta / eps_T)| */
+    double term_mult;   /* band on |ln(Ta/eps_T)| in units of its propagated error */
+    double term_abs;    /* plus this absolute band */
+    int32_t flip;       /* nonzero: take every decision inside a band the other way */
 } or_bands;
 
 /* ---- building blocks (exported so the tests can pin them one by one) ---- */
@@ -89,8 +101,8 @@ void or_basis(double alpha_rad, double x, double *Y /* [16][2] */);
 void or_gaussian(const or_scene *s, int64_t k, double *Sigma, double *Sinv, double *opacity);
 
 /* Ray r + t v (|v| = 1) against the 3-sigma ellipsoid of (mu, Sinv).
- * Returns 1 on a hit (m2 < 9 and t_out >= r_rx).  out[0..7] =
- * {t_in, t_out, t_a, dt, t_rep, m2, m2_rep, g}. */
+ * Returns 1 on a hit (m2 < 9 and t_out >= r_rx).  out[0..9] =
+ * {t_in, t_out, t_a, dt, t_rep, m2, m2_rep, g, A, C}. */
 int or_intersect(const double *Sinv, const double *mu, const double *r, const double *v,
                  double r_rx, double *out);
 
@@ -126,15 +138,29 @@ int64_t or_bin(const or_scene *s, const float *rx, const or_grid *g,
  *   S     [n_f][n_rays][2]  received complex signal per ray
  *   T     [n_f][n_rays][2]  transmittance after the last processed Gaussian
  *   Ta    [n_rays]          prod(1 - alpha) after the last processed Gaussian
+ *   Sabs  [n_rays]          sum over composited Gaussians of |z_k| = alpha_k |psi_k| |T_k|
+ *                           (the scale of the sum, identical at every frequency)
+ *   Scond [n_rays]          first-order error of |S| when every composited pair's m2 is
+ *                           off by its delta_k (bands->m2_err; 0 if bands is NULL):
+ *                           through its weight, through 1 - alpha of the pairs behind
+ *                           it, and through the transmittance phase 2 pi f b dt / c,
+ *                           whose chord dt = 2 sqrt((9 - m2)/A) is steep near grazing
  *   nhit  [n_rays]          Gaussians composited
  *   ntest [n_rays]          candidates tested
- *   flags [n_rays]          OR_FLAG_* ambiguity bits (bands may be NULL = none)
+ *   flags [n_rays]          OR_FLAG_* ambiguity bits in bits 0-7 and, in bits 8-15, how
+ *                           many decisions of the ray fell inside a band (bands may be
+ *                           NULL = none).  With bands->flip set, those decisions are
+ *                           taken the other way: a pair inside the m2 band that missed
+ *                           grazes at its closest approach (dt = 0, weight exp(-m2/2)),
+ *                           one inside the t band that missed is entered at r_rx with
+ *                           dt = 0; a hit inside a band is dropped; a stop inside the
+ *                           termination band continues and vice versa.
  * Returns 0, or a negative value on bad arguments. */
 int or_render(const or_scene *s, const float *rx, const float *tx, double f0, double df,
               int32_t n_f, const or_grid *g, int32_t mode, const int32_t *ray_idx,
               int64_t n_rays, int32_t n_threads, const or_bands *bands,
-              double *S, double *T, double *Ta, int32_t *nhit, int32_t *ntest,
-              uint32_t *flags);
+              double *S, double *T, double *Ta, double *Sabs, double *Scond, int32_t *nhit,
+              int32_t *ntest, uint32_t *flags);
 
 /* Gradient of L = sum_rays sum_f Re(conj(G) S) for the given dL/dRe S, dL/dIm S
  * (G [n_f][n_rays][2]), with respect to the raw parameters.  Gradient buffers are

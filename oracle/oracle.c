@@ -136,6 +136,8 @@ int or_intersect(const double *Sinv, const double *mu, const double *r, const do
     double disc = B * B - A * (C - 9.0);
     for (int i = 0; i < 8; ++i) out[i] = 0.0;
     out[5] = m2;
+    out[8] = A;
+    out[9] = C;
     if (!(disc > 0.0)) return 0;
     double sq = sqrt(disc);
     double t_out = (-B + sq) / A, t_in = (-B - sq) / A;
@@ -236,7 +238,7 @@ typedef struct {
     int32_t n_threads;
     const or_bands *bands;
     /* forward outputs */
-    double *S, *T, *Ta;
+    double *S, *T, *Ta, *Sabs, *Scond;
     int32_t *nhit, *ntest;
     uint32_t *flags;
     /* gradient: upstream G and per-thread accumulators */
@@ -273,6 +275,30 @@ static void ray_list(const rctx *c, int32_t ray, const uint32_t **list, int64_t 
     *len = c->tile_start[t + 1] - c->tile_start[t];
 }
 
+/* The other outcome of a hit decision that fell inside a band and missed: a ray that
+ * passes just outside the 3-sigma boundary (in_m2) grazes it at its closest approach;
+ * one whose exit lies just short of r_rx enters at r_rx.  Both with dt = 0. */
+static int flipped_hit(const double *Sinv, const double *mu, const double *r, const double *v,
+                       double r_rx, int in_m2, double *out)
+{
+    double w[3] = {r[0] - mu[0], r[1] - mu[1], r[2] - mu[2]};
+    double t;
+    if (in_m2) {
+        t = -quad(Sinv, v, w) / quad(Sinv, v, v);
+        if (t < r_rx) return 0;
+    } else {
+        t = r_rx;
+    }
+    double e[3];
+    for (int i = 0; i < 3; ++i) e[i] = r[i] + t * v[i] - mu[i];
+    double m2r = quad(Sinv, e, e);
+    out[0] = out[1] = out[2] = out[4] = t;
+    out[3] = 0.0;
+    out[6] = m2r;
+    out[7] = exp(-0.5 * m2r);
+    return 1;
+}
+
 static void render_one(rctx *c, int64_t i)
 {
     const or_grid *g = c->g;
@@ -288,18 +314,30 @@ static void render_one(rctx *c, int64_t i)
 
     double S[2 * 256], T[2 * 256];
     for (int f = 0; f < nf; ++f) { S[2 * f] = S[2 * f + 1] = 0.0; T[2 * f] = 1.0; T[2 * f + 1] = 0.0; }
-    double Ta = 1.0;
-    int32_t nh = 0, nt = 0;
+    double Ta = 1.0, sabs = 0.0, scond = 0.0, gsum = 0.0, lnta_err = 0.0;
+    int32_t nh = 0, nt = 0, namb = 0;
     uint32_t fl = 0;
     const or_bands *bd = c->bands;
     for (int64_t j = 0; j < len; ++j) {
         uint32_t k = list[j];
-        double h[8];
+        double h[10];
         ++nt;
         int hit = or_intersect(c->Sinv + 9 * k, c->mu + 3 * k, c->rx, v, g->r_rx, h);
+        const double delta = bd ? bd->m2_err * sqrt(h[9]) + bd->m2_abs : 0.0;
+        int flipped = 0;
         if (bd) {
-            if (fabs(h[5] - 9.0) < bd->m2_band) fl |= OR_FLAG_M2;
-            if (h[5] < 9.0 && fabs(h[1] - (double)g->r_rx) < bd->t_band) fl |= OR_FLAG_TOUT;
+            int in_m2 = fabs(h[5] - 9.0) < bd->m2_mult * delta;
+            int in_t = h[5] < 9.0 && fabs(h[1] - (double)g->r_rx) < bd->t_band;
+            if (in_m2) fl |= OR_FLAG_M2;
+            if (in_t) fl |= OR_FLAG_TOUT;
+            if (in_m2 || in_t) {
+                ++namb;
+                if (bd->flip) {
+                    hit = hit ? 0 : flipped_hit(c->Sinv + 9 * k, c->mu + 3 * k, c->rx, v,
+                                                (double)g->r_rx, in_m2, h);
+                    flipped = 1;
+                }
+            }
         }
         if (!hit) continue;
         double a = c->op[k] * h[7];
@@ -310,6 +348,23 @@ static void render_one(rctx *c, int64_t i)
             double cr = cf[2 * n], ci = cf[2 * n + 1];
             pr += cr * Y[2 * n] - ci * Y[2 * n + 1];
             pi += cr * Y[2 * n + 1] + ci * Y[2 * n];
+        }
+        const double zabs = a * sqrt(pr * pr + pi * pi) * Ta; /* |z_k|, every frequency */
+        sabs += zabs;
+        if (bd) {
+            /* first-order error of S from delta on this pair: its own weight
+             * (dg/dm2 = -g/2), then every later term through 1 - alpha and through the
+             * transmittance phase omega b dt; d(dt)/dm2 = -1/(A h) with h the half chord,
+             * capped by the chord a grazing pair can have at all, 2 sqrt(2 delta / A) */
+            const double hh = 0.5 * h[3] > 0.0 ? sqrt(fmax((9.0 - h[5]) / h[8], 0.0)) : 0.0;
+            const double cap = 2.0 * sqrt(2.0 * delta / h[8]);
+            double ddt = hh > 0.0 ? delta / (h[8] * hh) : cap;
+            if (ddt > cap || flipped) ddt = cap;
+            const double fmax_hz = c->f0 + (double)(nf - 1) * c->df;
+            const double om = 2.0 * M_PI * fmax_hz / OR_C_LIGHT;
+            scond += zabs * (gsum + 0.5 * delta);
+            gsum += fabs(om * c->b[k]) * ddt + (a < (double)g->alpha_max ? a * 0.5 * delta / (1.0 - a) : 0.0);
+            lnta_err += (a < (double)g->alpha_max ? a * 0.5 * delta / (1.0 - a) : 0.0) + 1e-7;
         }
         for (int f = 0; f < nf; ++f) {
             double fr = c->f0 + (double)f * c->df;
@@ -328,15 +383,23 @@ static void render_one(rctx *c, int64_t i)
         Ta *= (1.0 - a);
         ++nh;
         if (g->eps_T > 0.0f) {
-            if (bd && fabs(log(Ta / (double)g->eps_T)) < bd->term_band) fl |= OR_FLAG_TERM;
-            if (Ta < (double)g->eps_T) break;
+            int stop = Ta < (double)g->eps_T;
+            if (bd && fabs(log(Ta / (double)g->eps_T)) < bd->term_mult * lnta_err + bd->term_abs) {
+                fl |= OR_FLAG_TERM;
+                ++namb;
+                if (bd->flip) stop = !stop;
+            }
+            if (stop) break;
         }
     }
+    fl |= (uint32_t)(namb > 255 ? 255 : namb) << 8;
     for (int f = 0; f < nf; ++f) {
         if (c->S) { c->S[2 * ((size_t)f * c->n_rays + i)] = S[2 * f]; c->S[2 * ((size_t)f * c->n_rays + i) + 1] = S[2 * f + 1]; }
         if (c->T) { c->T[2 * ((size_t)f * c->n_rays + i)] = T[2 * f]; c->T[2 * ((size_t)f * c->n_rays + i) + 1] = T[2 * f + 1]; }
     }
     if (c->Ta) c->Ta[i] = Ta;
+    if (c->Sabs) c->Sabs[i] = sabs;
+    if (c->Scond) c->Scond[i] = scond;
     if (c->nhit) c->nhit[i] = nh;
     if (c->ntest) c->ntest[i] = nt;
     if (c->flags) c->flags[i] = fl;
@@ -431,8 +494,8 @@ static void run_threads(rctx *c, void *(*fn)(void *))
 int or_render(const or_scene *s, const float *rx, const float *tx, double f0, double df,
               int32_t n_f, const or_grid *g, int32_t mode, const int32_t *ray_idx,
               int64_t n_rays, int32_t n_threads, const or_bands *bands,
-              double *S, double *T, double *Ta, int32_t *nhit, int32_t *ntest,
-              uint32_t *flags)
+              double *S, double *T, double *Ta, double *Sabs, double *Scond, int32_t *nhit,
+              int32_t *ntest, uint32_t *flags)
 {
     if (check_args(s, g, n_f, mode)) return -1;
     rctx c;
@@ -442,7 +505,7 @@ int or_render(const or_scene *s, const float *rx, const float *tx, double f0, do
     c.n_rays = ray_idx ? n_rays : (int64_t)g->n_az * g->n_el;
     c.n_threads = n_threads < 1 ? 1 : n_threads;
     c.bands = bands;
-    c.S = S; c.T = T; c.Ta = Ta; c.nhit = nhit; c.ntest = ntest; c.flags = flags;
+    c.S = S; c.T = T; c.Ta = Ta; c.Sabs = Sabs; c.Scond = Scond; c.nhit = nhit; c.ntest = ntest; c.flags = flags;
     prepare(&c, s, rx, tx, g);
     run_threads(&c, render_worker);
     release(&c);

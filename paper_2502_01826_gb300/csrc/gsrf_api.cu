@@ -27,6 +27,9 @@ bool make_layout(const gsrf_plan* p, Layout* L) {
         return o;
     };
     L->status = take(sizeof(DevStatus));
+    L->rxpos = take(nr * 3 * sizeof(float));
+    L->raytab = take((size_t)g.n_az * g.n_el * kRayTab * sizeof(float));
+    L->fle = take(n * kFle * sizeof(float));
     L->gshape = take(n * sizeof(GShape));
     L->dpath = take(n * sizeof(double));
     L->view = take(nr * n * sizeof(View));

@@ -20,22 +20,40 @@ constexpr int kMaxTiles = 1024;       // bins of the tile counting sort
 constexpr int kMaxNf = 64;
 
 // Per-Gaussian shape record: whitening matrix W = diag(1/s) R^T (so that
-// (x-mu)^T Sigma^-1 (x-mu) = |W (x-mu)|^2), opacity, excess-phase coefficient.
+// (x-mu)^T Sigma^-1 (x-mu) = |W (x-mu)|^2), opacity, excess-phase coefficient, and the
+// squared radius of a bounding sphere of the 3-sigma ellipsoid.
 struct __align__(16) GShape {
     float W[9];
     float o;
     float b;
-    float pad;
+    float rc2;
 };
 
-// Per-(receiver, Gaussian) view record: whitened receiver offset w = W (r - mu),
-// path phasor e^{-j 2 pi f0 d / c} and the per-subcarrier phase step 2 pi df d / c.
+// Per-(receiver, Gaussian) view record: offset c = mu - r and the squared radius of
+// the Gaussian's bounding sphere (the render's pre-test), whitened receiver offset
+// w = W (r - mu), path phasor e^{-j 2 pi f0 d / c} and the per-subcarrier phase step
+// 2 pi df d / c.
 struct __align__(16) View {
+    float c[3];
+    float rc2;
     float w[3];
-    float er, ei;
+    float er;
+    float ei;
     float omd;
     float pad0, pad1;
 };
+
+// Fourier-Legendre coefficients folded for the per-ray basis of m >= 0 only
+// (Y_{l,-m} = kappa_{lm} conj(Y_{l,m}), kappa_{lm} = (-1)^m (l-m)!/(l+m)!):
+//   m = 0 terms (l = 0..3): c_{l,0} as (re, im)                       -> q[0..7]
+//   m > 0 terms, (l,m) = (1,1),(2,1),(3,1),(2,2),(3,2),(3,3): with c = c_{l,m},
+//   d = kappa c_{l,-m}: (c.re + d.re, d.im - c.im, c.im + d.im, c.re - d.re) -> q[8..31]
+// so that psi = sum_m0 c P + sum_m>0 (e1 yr + e2 yi) + j (e3 yr + e4 yi).
+constexpr int kFle = 32;
+
+// Per-ray table of the receiving grid (independent of the receiver): direction,
+// P_1^0, P_2^0, P_3^0 at x = sin(elevation) and Y_{l,m} for the six m > 0 terms.
+constexpr int kRayTab = 20;  // floats: dx dy dz P10 | P20 P30 y11 | y21 y31 | y22 y32 | y33 - -
 
 // Tile coverage of a Gaussian seen from a receiver: azimuth-tile bit mask,
 // elevation tile range packed lo | hi << 16, number of tiles.
@@ -63,7 +81,7 @@ struct __align__(16) RayState {
 
 struct Layout {
     // byte offsets
-    size_t status, gshape, dpath, view, cover, dkey, dkey2, dval, dval2, dhist, dchunk_sum,
+    size_t status, rxpos, raytab, fle, gshape, dpath, view, cover, dkey, dkey2, dval, dval2, dhist, dchunk_sum,
         rx_base, rx_total, pchunk_base, pkeys, pkeys2, pids, pids2, tile_start, thist, total;
     int32_t ntu, ntv, n_tiles;
     int32_t n_rx;

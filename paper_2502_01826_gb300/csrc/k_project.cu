@@ -21,7 +21,7 @@ __global__ void k_status_init(DevStatus* st) {
 // and |t - mu| in FP64 for the path phase.
 __global__ void __launch_bounds__(256) k_prepare(gsrf_gaussians g, const float* __restrict__ tx,
                                                  GShape* __restrict__ shape, double* __restrict__ dpath_t,
-                                                 DevStatus* st) {
+                                                 float* __restrict__ fle, DevStatus* st) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.n) return;
     const float mx = g.means[3 * k], my = g.means[3 * k + 1], mz = g.means[3 * k + 2];
@@ -57,10 +57,60 @@ __global__ void __launch_bounds__(256) k_prepare(gsrf_gaussians g, const float* 
         for (int j = 0; j < 3; ++j) out.W[3 * i + j] = R[3 * j + i] * is[i];
     out.o = 1.0f / (1.0f + expf(-ol));
     out.b = b;
-    out.pad = 0.0f;
+    // squared radius of a sphere about mu that holds the 3-sigma ellipsoid with a 1%
+    // margin (the render's cheap pre-test; FP32 rounding is far inside the margin)
+    const float rc = 3.03f * expf(fmaxf(fmaxf(l0, l1), l2));
+    out.rc2 = rc * rc;
     shape[k] = out;
     const double dx = (double)tx[0] - mx, dy = (double)tx[1] - my, dz = (double)tx[2] - mz;
     dpath_t[k] = sqrt(dx * dx + dy * dy + dz * dz);
+    // folded Fourier-Legendre coefficients (see kFle)
+    float* q = fle + (size_t)k * kFle;
+    const int m0[4] = {0, 2, 6, 12};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        q[2 * i] = c[2 * m0[i]];
+        q[2 * i + 1] = c[2 * m0[i] + 1];
+    }
+    // (l, m) = (1,1) (2,1) (3,1) (2,2) (3,2) (3,3): index of +m, of -m, kappa
+    const int np[6] = {3, 7, 13, 8, 14, 15}, nm[6] = {1, 5, 11, 4, 10, 9};
+    const float kap[6] = {-0.5f, -1.0f / 6.0f, -1.0f / 12.0f, 1.0f / 24.0f, 1.0f / 120.0f, -1.0f / 720.0f};
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+        const float cr = c[2 * np[t]], ci = c[2 * np[t] + 1];
+        const float dr = kap[t] * c[2 * nm[t]], di = kap[t] * c[2 * nm[t] + 1];
+        q[8 + 4 * t] = cr + dr;
+        q[8 + 4 * t + 1] = di - ci;
+        q[8 + 4 * t + 2] = ci + di;
+        q[8 + 4 * t + 3] = cr - dr;
+    }
+}
+
+// Per-ray table of the receiving grid, in FP64 and rounded once: the ray direction
+// (cos el cos az, cos el sin az, sin el) at the bin centre and the basis values the
+// folded Fourier-Legendre sum needs (P without the Condon-Shortley phase, x = sin el).
+__global__ void __launch_bounds__(256) k_raytab(gsrf_grid gr, float* __restrict__ tab) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= gr.n_az * gr.n_el) return;
+    const int u = i % gr.n_az, v = i / gr.n_az;
+    const double deg = 0.017453292519943295;
+    const double az = ((double)gr.az0_deg + ((double)u + 0.5) * (double)gr.daz_deg) * deg;
+    const double el = ((double)gr.el0_deg + ((double)v + 0.5) * (double)gr.del_deg) * deg;
+    double se, ce, s1, c1, s2, c2, s3, c3;
+    sincos(el, &se, &ce);
+    sincos(az, &s1, &c1);
+    sincos(2.0 * az, &s2, &c2);
+    sincos(3.0 * az, &s3, &c3);
+    const double x = se, sx = ce, x2 = x * x, sx2 = sx * sx;
+    const double P10 = x, P20 = 1.5 * x2 - 0.5, P30 = x * (2.5 * x2 - 1.5);
+    const double P11 = sx, P21 = 3.0 * x * sx, P31 = (7.5 * x2 - 1.5) * sx;
+    const double P22 = 3.0 * sx2, P32 = 15.0 * x * sx2, P33 = 15.0 * sx2 * sx;
+    float* t = tab + (size_t)i * kRayTab;
+    t[0] = (float)(ce * c1); t[1] = (float)(ce * s1); t[2] = (float)se; t[3] = (float)P10;
+    t[4] = (float)P20; t[5] = (float)P30; t[6] = (float)(c1 * P11); t[7] = (float)(s1 * P11);
+    t[8] = (float)(c1 * P21); t[9] = (float)(s1 * P21); t[10] = (float)(c1 * P31); t[11] = (float)(s1 * P31);
+    t[12] = (float)(c2 * P22); t[13] = (float)(s2 * P22); t[14] = (float)(c2 * P32); t[15] = (float)(s2 * P32);
+    t[16] = (float)(c3 * P33); t[17] = (float)(s3 * P33); t[18] = 0.0f; t[19] = 0.0f;
 }
 
 // Tile coverage: the bins of the receiving plane whose centre lies in the angular
@@ -130,9 +180,14 @@ __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __r
                                               const double* __restrict__ dpath_t, gsrf_grid gr,
                                               int ntu, int ntv, double f0_over_c, float two_pi_df_over_c,
                                               View* __restrict__ view, Cover* __restrict__ cover,
-                                              uint32_t* __restrict__ dkey) {
+                                              uint32_t* __restrict__ dkey, float* __restrict__ rx_keep) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y;
+    if (k == 0) {  // the render reads the receiver positions from the workspace
+        rx_keep[3 * r] = rxp[3 * r];
+        rx_keep[3 * r + 1] = rxp[3 * r + 1];
+        rx_keep[3 * r + 2] = rxp[3 * r + 2];
+    }
     if (k >= g.n) return;
     const size_t o = (size_t)r * g.n + k;
     const float rx = rxp[3 * r], ry = rxp[3 * r + 1], rz = rxp[3 * r + 2];
@@ -141,6 +196,10 @@ __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __r
     // whitened receiver offset (FP32, contraction allowed: not a decision)
     const float ux = rx - mx, uy = ry - my, uz = rz - mz;
     View v;
+    v.c[0] = -ux;
+    v.c[1] = -uy;
+    v.c[2] = -uz;
+    v.rc2 = sh.rc2;
     v.w[0] = sh.W[0] * ux + sh.W[1] * uy + sh.W[2] * uz;
     v.w[1] = sh.W[3] * ux + sh.W[4] * uy + sh.W[5] * uz;
     v.w[2] = sh.W[6] * ux + sh.W[7] * uy + sh.W[8] * uz;
@@ -168,14 +227,23 @@ cudaError_t launch_project(const gsrf_plan* p, const Layout& L, const gsrf_gauss
                            const float* tx, void* ws, cudaStream_t st) {
     DevStatus* status = at<DevStatus>(ws, L.status);
     k_status_init<<<1, 32, 0, st>>>(status);
-    if (L.n == 0) return cudaGetLastError();
+    if (L.n == 0) {
+        const int n_rays = p->grid.n_az * p->grid.n_el;
+        k_raytab<<<(n_rays + 255) / 256, 256, 0, st>>>(p->grid, at<float>(ws, L.raytab));
+        cudaError_t e = cudaMemcpyAsync(at<float>(ws, L.rxpos), rx, sizeof(float) * 3 * L.n_rx,
+                                        cudaMemcpyDeviceToDevice, st);
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
+    const int n_rays = p->grid.n_az * p->grid.n_el;
+    k_raytab<<<(n_rays + 255) / 256, 256, 0, st>>>(p->grid, at<float>(ws, L.raytab));
     const unsigned nb = (unsigned)((L.n + 255) / 256);
-    k_prepare<<<nb, 256, 0, st>>>(*g, tx, at<GShape>(ws, L.gshape), at<double>(ws, L.dpath), status);
+    k_prepare<<<nb, 256, 0, st>>>(*g, tx, at<GShape>(ws, L.gshape), at<double>(ws, L.dpath),
+                                  at<float>(ws, L.fle), status);
     k_view<<<dim3(nb, L.n_rx), 256, 0, st>>>(*g, rx, at<GShape>(ws, L.gshape), at<double>(ws, L.dpath),
                                               p->grid, L.ntu, L.ntv, p->f0_hz / kC,
                                               (float)(2.0 * 3.14159265358979323846 * p->df_hz / kC),
                                               at<View>(ws, L.view), at<Cover>(ws, L.cover),
-                                              at<uint32_t>(ws, L.dkey));
+                                              at<uint32_t>(ws, L.dkey), at<float>(ws, L.rxpos));
     return cudaGetLastError();
 }
 

@@ -1,30 +1,40 @@
 // k_render.cu -- Alg. 1 lines 6-12 ("Blend"), Eq. 14 / App. A.3: per-ray complex
 // front-to-back accumulation over the tile's depth-sorted Gaussians.
 //
-// One CTA per (receiver, 16x16 ray tile), one thread per ray.  The tile's candidates
-// are staged kBatch at a time into shared memory (whitening matrix, whitened receiver
-// offset, opacity, path phasor, excess-phase coefficient, 16 complex coefficients);
-// every ray then tests them in list order.  A ray stops once prod(1 - alpha) drops
-// below eps_T; the CTA stops when all its rays have (__syncthreads_count).
+// Layout of the work: a CTA of 4 warps covers half of a 16x16 ray tile (16 x 8 rays),
+// each warp an 8 x 4 block of rays, one ray per thread.  Every warp walks its tile's
+// candidate list on its own, 32 candidates per batch: lane i takes candidate b0 + i,
+// tests its bounding sphere against the cone of the warp's 32 rays and, if it may be
+// hit, copies its records into the warp's half of a double buffer with cp.async while
+// the warp works on the current batch; the rays then visit only the candidates of the
+// ballot mask, in list order.  Warps never wait for one another and a warp leaves as
+// soon as its 32 rays have terminated (prod(1 - alpha) < eps_T).
 //
-// Intersection in whitened coordinates: with W = diag(1/s) R^T, the ray point
-// r + t v maps to w + t v' (w = W (r - mu), v' = W v), so the paper's quadratic
-// A t^2 + 2 B t + (C - 9) = 0 (App. D.3) has A = |v'|^2, B = w.v', C = |w|^2 and the
-// closest approach m2 = C - B^2/A = |w + t_mid v'|^2 at t_mid = -B/A.  Forming m2 as a
-// squared norm avoids the cancellation of C - B^2/A in FP32 (C reaches 1e5 for small
-// far Gaussians); the roots are t_mid +- sqrt((9 - m2)/A).
+// Per candidate and ray:
+//   (1) bounding sphere: the ray's line passes within rc of mu, |c x v|^2 < rc^2;
+//   (2) 3-sigma ellipsoid in whitened coordinates: with W = diag(1/s) R^T the ray
+//       r + t v maps to w + t v' (w = W (r - mu), v' = W v), so the paper's quadratic
+//       A t^2 + 2 B t + (C - 9) = 0 (App. D.3) has A = |v'|^2, B = w.v', C = |w|^2;
+//       the closest approach is m2 = C - B^2/A = |w x v'|^2 / A (Lagrange's identity),
+//       free of the cancellation of C - B^2/A in FP32 (C reaches 1e5);
+//   (3) the chord t_mid +- sqrt((9 - m2)/A) must reach r_rx; it is clipped there and
+//       the Gaussian is weighted at the midpoint of the clipped chord (App. A.2).
 #include <math.h>
 
 #include "gsrf_internal.cuh"
 
 namespace gsrf {
 
-constexpr int kBatch = 128;
+constexpr int kWarps = 4;        // warps per CTA: half a 16 x 16 tile (16 x 8 rays)
+constexpr int kThreads = 32 * kWarps;
+constexpr int kWB = 32;          // candidates per warp batch, one per lane
+constexpr int kRec = 6;          // float4 per staged candidate: 3 of View, 3 of GShape
 
 struct RenderArgs {
     const GShape* shape;
     const View* view;
-    const float* coeffs;
+    const float* fle;
+    const float* raytab;
     const uint32_t* pids;
     const long long* rx_base;
     const uint32_t* tile_start;
@@ -34,147 +44,222 @@ struct RenderArgs {
     gsrf_grid gr;
     int ntu, n_tiles, n_rx;
     long long n;
-    float omega0;  // 2 pi f0 / c
+    float om_pi;  // 2 f0 / c: sincospi argument per unit of b dt
 };
 
-// Fourier-Legendre basis of one ray (Eq. 9): Y_n = e^{i m az} P_l^m(x), x = sin(el),
-// n = l*l + l + m, P without the Condon-Shortley phase and
-// P_l^{-m} = (-1)^m (l-m)!/(l+m)! P_l^m.
-__device__ __forceinline__ void ray_basis(float az, float x, float sx, float* Yr, float* Yi) {
-    float c1, s1, c2, s2, c3, s3;
-    sincosf(az, &s1, &c1);
-    sincosf(2.0f * az, &s2, &c2);
-    sincosf(3.0f * az, &s3, &c3);
-    const float x2 = x * x, sx2 = sx * sx;
-    const float P00 = 1.0f;
-    const float P10 = x, P11 = sx;
-    const float P20 = 1.5f * x2 - 0.5f, P21 = 3.0f * x * sx, P22 = 3.0f * sx2;
-    const float P30 = x * (2.5f * x2 - 1.5f), P31 = (7.5f * x2 - 1.5f) * sx, P32 = 15.0f * x * sx2,
-                P33 = 15.0f * sx2 * sx;
-    // m = 0
-    Yr[0] = P00; Yi[0] = 0.0f;
-    Yr[2] = P10; Yi[2] = 0.0f;
-    Yr[6] = P20; Yi[6] = 0.0f;
-    Yr[12] = P30; Yi[12] = 0.0f;
-    // m = +-1: factor for -1 is -(l-1)!/(l+1)!
-    Yr[3] = c1 * P11;  Yi[3] = s1 * P11;
-    Yr[1] = -0.5f * c1 * P11; Yi[1] = 0.5f * s1 * P11;
-    Yr[7] = c1 * P21;  Yi[7] = s1 * P21;
-    Yr[5] = -(1.0f / 6.0f) * c1 * P21; Yi[5] = (1.0f / 6.0f) * s1 * P21;
-    Yr[13] = c1 * P31; Yi[13] = s1 * P31;
-    Yr[11] = -(1.0f / 12.0f) * c1 * P31; Yi[11] = (1.0f / 12.0f) * s1 * P31;
-    // m = +-2: factor (l-2)!/(l+2)!
-    Yr[8] = c2 * P22;  Yi[8] = s2 * P22;
-    Yr[4] = (1.0f / 24.0f) * c2 * P22; Yi[4] = -(1.0f / 24.0f) * s2 * P22;
-    Yr[14] = c2 * P32; Yi[14] = s2 * P32;
-    Yr[10] = (1.0f / 120.0f) * c2 * P32; Yi[10] = -(1.0f / 120.0f) * s2 * P32;
-    // m = +-3: factor -(l-3)!/(l+3)!
-    Yr[15] = c3 * P33; Yi[15] = s3 * P33;
-    Yr[9] = -(1.0f / 720.0f) * c3 * P33; Yi[9] = (1.0f / 720.0f) * s3 * P33;
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Ray of thread t: CTA half h of the 16 x 16 tile holds rows 8h .. 8h+7; each warp an
+// 8 x 4 block of rays so that its lanes see nearly the same candidates.
+__device__ __forceinline__ void cta_ray(int t, int half, int& lx, int& ly) {
+    const int lane = t & 31, w = t >> 5;
+    lx = ((w & 1) << 3) | (lane & 7);
+    ly = (half << 3) | ((w >> 1) << 2) | (lane >> 3);
 }
 
-__global__ void __launch_bounds__(kRenderThreads) k_render_fwd(RenderArgs a) {
-    __shared__ float4 s_geo[kBatch][4];  // W0..W3 | W4..W7 | W8 w0 w1 w2 | o er ei b
-    __shared__ float4 s_cf[kBatch][8];   // 16 complex coefficients
-    __shared__ unsigned long long s_stats[2];
+// Radiance psi of one Gaussian along one ray (Eq. 9) from the folded coefficients q
+// (see kFle) and the ray's basis values: P = (P10, P20, P30), Y = six complex Y_{l,m>0}.
+__device__ __forceinline__ void fle_psi(const float4* __restrict__ q4, const float* P, const float* Y,
+                                        float& pr, float& pi) {
+    const float4 a0 = __ldg(q4), a1 = __ldg(q4 + 1);
+    pr = a0.x + a0.z * P[0] + a1.x * P[1] + a1.z * P[2];
+    pi = a0.y + a0.w * P[0] + a1.y * P[1] + a1.w * P[2];
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+        const float4 e = __ldg(q4 + 2 + t);
+        pr += e.x * Y[2 * t] + e.y * Y[2 * t + 1];
+        pi += e.z * Y[2 * t] + e.w * Y[2 * t + 1];
+    }
+}
 
-    const int tile = blockIdx.x, r = blockIdx.y;
+// The ray's direction and basis values from the per-grid ray table.
+__device__ __forceinline__ void load_ray(const float* raytab, size_t ray, float& dx, float& dy, float& dz,
+                                         float* P, float* Y) {
+    const float4* t4 = reinterpret_cast<const float4*>(raytab + ray * kRayTab);
+    const float4 t0 = t4[0], t1 = t4[1], t2 = t4[2], t3 = t4[3], t5 = t4[4];
+    dx = t0.x; dy = t0.y; dz = t0.z; P[0] = t0.w;
+    P[1] = t1.x; P[2] = t1.y; Y[0] = t1.z; Y[1] = t1.w;
+    Y[2] = t2.x; Y[3] = t2.y; Y[4] = t2.z; Y[5] = t2.w;
+    Y[6] = t3.x; Y[7] = t3.y; Y[8] = t3.z; Y[9] = t3.w;
+    Y[10] = t5.x; Y[11] = t5.y;
+}
+
+// Cone of a warp's rays: unit axis b and cos / sin of the half-angle that holds all of
+// them (with a small angular margin).
+struct Bundle {
+    float bx, by, bz, cb, sb;
+};
+
+__device__ __forceinline__ Bundle warp_bundle(bool valid, float dx, float dy, float dz) {
+    float sx = valid ? dx : 0.0f, sy = valid ? dy : 0.0f, sz = valid ? dz : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    }
+    const float in = rsqrtf(fmaxf(sx * sx + sy * sy + sz * sz, 1e-30f));
+    Bundle b;
+    b.bx = sx * in;
+    b.by = sy * in;
+    b.bz = sz * in;
+    float c = valid ? dx * b.bx + dy * b.by + dz * b.bz : 1.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c = fminf(c, __shfl_xor_sync(0xffffffffu, c, o));
+    c = fmaxf(fminf(c, 1.0f), -1.0f) - 2e-5f;  // margin for rounding of the axis and rays
+    b.cb = c;
+    b.sb = sqrtf(fmaxf(1.0f - c * c, 0.0f));
+    return b;
+}
+
+// Can the sphere (c = mu - r, squared radius rc2) meet any ray of the bundle?  If the
+// angle between b and c exceeds the bundle half-angle plus the sphere's half-angle
+// asin(rc/|c|), every ray of the bundle misses the sphere (triangle inequality on the
+// unit sphere), hence the ellipsoid inside it.
+__device__ __forceinline__ bool bundle_meets(const Bundle& b, float4 c) {
+    const float D2 = c.x * c.x + c.y * c.y + c.z * c.z;
+    if (D2 <= c.w) return true;
+    const float D = sqrtf(D2);
+    const float cd = c.x * b.bx + c.y * b.by + c.z * b.bz;
+    return cd >= b.cb * sqrtf(D2 - c.w) - b.sb * sqrtf(c.w) - 1e-4f * D;
+}
+
+__global__ void __launch_bounds__(kThreads, 8) k_render_fwd(RenderArgs a) {
+    __shared__ float4 sbuf[kWarps][2][kWB][kRec];
+    __shared__ uint32_t sid[kWarps][2][kWB];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = blockIdx.x >> 1, half = blockIdx.x & 1, r = blockIdx.y;
     const int tu = tile % a.ntu, tv = tile / a.ntu;
-    const int u = tu * kTile + (threadIdx.x & (kTile - 1));
-    const int v = tv * kTile + (threadIdx.x / kTile);
+    int lx, ly;
+    cta_ray(threadIdx.x, half, lx, ly);
+    const int u = tu * kTile + lx, v = tv * kTile + ly;
     const gsrf_grid& gr = a.gr;
     const bool valid = u < gr.n_az && v < gr.n_el;
-    if (threadIdx.x < 2) s_stats[threadIdx.x] = 0ull;
 
-    const float deg = 0.0174532925199432958f;
-    const float az = (gr.az0_deg + ((float)u + 0.5f) * gr.daz_deg) * deg;
-    const float el = (gr.el0_deg + ((float)v + 0.5f) * gr.del_deg) * deg;
-    float se, ce, sa, ca;
-    sincosf(el, &se, &ce);
-    sincosf(az, &sa, &ca);
-    const float dx = ce * ca, dy = ce * sa, dz = se;
-    float Yr[kNB], Yi[kNB];
-    ray_basis(az, se, ce, Yr, Yi);
+    float dx = 0.0f, dy = 0.0f, dz = 1.0f, P[3] = {0.0f, 0.0f, 0.0f}, Y[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) Y[i] = 0.0f;
+    if (valid) load_ray(a.raytab, (size_t)v * gr.n_az + u, dx, dy, dz, P, Y);
+    const Bundle bun = warp_bundle(valid, dx, dy, dz);
 
     const size_t ts = (size_t)r * (a.n_tiles + 1) + tile;
     const long long base0 = a.rx_base[r];
     const long long lo = base0 + a.tile_start[ts], hi = base0 + a.tile_start[ts + 1];
     const float r_rx = gr.r_rx, eps_T = gr.eps_T, amax = gr.alpha_max;
+    const View* __restrict__ view = a.view + (size_t)r * a.n;
 
     float Sr = 0.0f, Si = 0.0f, Tr = 1.0f, Ti = 0.0f, Ta = 1.0f;
     int last = -1;
     bool done = !valid;
     unsigned tests = 0, hits = 0;
 
-    for (long long b0 = lo; b0 < hi; b0 += kBatch) {
-        const int cnt = (int)min((long long)kBatch, hi - b0);
-        __syncthreads();
-        if (threadIdx.x < cnt) {
-            const uint32_t id = a.pids[b0 + threadIdx.x];
-            const float4* sh = reinterpret_cast<const float4*>(a.shape + id);
-            const float4* vw = reinterpret_cast<const float4*>(a.view + (size_t)r * a.n + id);
-            const float4 g0 = sh[0], g1 = sh[1], g2 = sh[2];  // W0-3, W4-7, W8 o b pad
-            const float4 v0 = vw[0], v1 = vw[1];              // w0 w1 w2 er, ei omd - -
-            s_geo[threadIdx.x][0] = g0;
-            s_geo[threadIdx.x][1] = g1;
-            s_geo[threadIdx.x][2] = make_float4(g2.x, v0.x, v0.y, v0.z);
-            s_geo[threadIdx.x][3] = make_float4(g2.y, v0.w, v1.x, g2.z);
-            const float4* cf = reinterpret_cast<const float4*>(a.coeffs + (size_t)id * 2 * kNB);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) s_cf[threadIdx.x][q] = cf[q];
-        }
-        __syncthreads();
-        if (!done) {
-            for (int j = 0; j < cnt; ++j) {
-                const float4 g0 = s_geo[j][0], g1 = s_geo[j][1], g2 = s_geo[j][2];
-                const float vx = g0.x * dx + g0.y * dy + g0.z * dz;
-                const float vy = g0.w * dx + g1.x * dy + g1.y * dz;
-                const float vz = g1.z * dx + g1.w * dy + g2.x * dz;
-                const float A = vx * vx + vy * vy + vz * vz;
-                const float B = g2.y * vx + g2.z * vy + g2.w * vz;
-                const float iA = 1.0f / A;
-                const float tm = -B * iA;
-                const float px = g2.y + tm * vx, py = g2.z + tm * vy, pz = g2.w + tm * vz;
-                const float m2 = px * px + py * py + pz * pz;
-                ++tests;
-                if (m2 >= 9.0f) continue;
-                const float h = sqrtf((9.0f - m2) * iA);
-                const float t_out = tm + h;
-                if (t_out < r_rx) continue;
-                // hit: chord beyond the emitting sphere, midpoint weight (App. A.2)
-                const float t_a = fmaxf(tm - h, r_rx);
-                const float dt = t_out - t_a;
-                const float dl = 0.5f * (t_a + t_out) - tm;
-                const float m2r = m2 + A * dl * dl;
-                const float4 g3 = s_geo[j][3];
-                const float alpha = fminf(g3.x * expf(-0.5f * m2r), amax);
-                float pr = 0.0f, pi = 0.0f;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float4 c = s_cf[j][q];
-                    pr += c.x * Yr[2 * q] - c.y * Yi[2 * q] + c.z * Yr[2 * q + 1] - c.w * Yi[2 * q + 1];
-                    pi += c.x * Yi[2 * q] + c.y * Yr[2 * q] + c.z * Yi[2 * q + 1] + c.w * Yr[2 * q + 1];
-                }
-                // E_k T
-                const float etr = g3.y * Tr - g3.z * Ti, eti = g3.y * Ti + g3.z * Tr;
-                Sr += alpha * (pr * etr - pi * eti);
-                Si += alpha * (pr * eti + pi * etr);
-                float sn, cs;
-                sincosf(a.omega0 * g3.w * dt, &sn, &cs);
-                const float om = 1.0f - alpha;
-                const float nTr = om * (Tr * cs + Ti * sn);
-                Ti = om * (Ti * cs - Tr * sn);
-                Tr = nTr;
-                Ta *= om;
-                ++hits;
-                last = (int)(b0 - base0) + j;
-                if (Ta < eps_T) {
-                    done = true;
-                    break;
-                }
+    // Stage the batch starting at b0 into buffer bf: lane i takes candidate b0 + i,
+    // tests its bounding sphere against the warp's cone and, if it may be hit, copies
+    // its records; returns the mask of candidates that may be hit.
+    auto stage = [&](int bf, long long b0) -> uint32_t {
+        bool keep = false;
+        if (b0 + lane < hi) {
+            const uint32_t id = a.pids[b0 + lane];
+            const float4* vw = reinterpret_cast<const float4*>(view + id);
+            const float4 c = __ldg(vw);
+            keep = bundle_meets(bun, c);
+            if (keep) {
+                sid[warp][bf][lane] = id;
+                const float4* sh = reinterpret_cast<const float4*>(a.shape + id);
+                float4* dst = sbuf[warp][bf][lane];
+                dst[0] = c;
+                cp_async16(dst + 1, vw + 1);
+                cp_async16(dst + 2, vw + 2);
+                cp_async16(dst + 3, sh + 0);
+                cp_async16(dst + 4, sh + 1);
+                cp_async16(dst + 5, sh + 2);
+                asm volatile("prefetch.global.L1 [%0];\n" ::"l"(a.fle + (size_t)id * kFle));
             }
         }
-        if (__syncthreads_count(!done) == 0) break;
+        cp_async_commit();
+        return __ballot_sync(0xffffffffu, keep);
+    };
+
+    if (!__all_sync(0xffffffffu, done)) {
+        int bf = 0;
+        uint32_t mask = stage(0, lo);
+        for (long long b0 = lo; b0 < hi; b0 += kWB, bf ^= 1) {
+            const uint32_t next = stage(bf ^ 1, b0 + kWB);  // empty past the end of the list
+            cp_async_wait_prev();
+            __syncwarp();
+            const int cnt = (int)min((long long)kWB, hi - b0);
+            if (!done) {
+                int stop = cnt;
+                for (uint32_t m = mask; m; m &= m - 1) {
+                    const int j = __ffs(m) - 1;
+                    const float4* rec = sbuf[warp][bf][j];
+                    // (1) bounding sphere
+                    const float4 v0 = rec[0];  // c = mu - r, rc^2
+                    const float qx = v0.y * dz - v0.z * dy, qy = v0.z * dx - v0.x * dz, qz = v0.x * dy - v0.y * dx;
+                    if (qx * qx + qy * qy + qz * qz >= v0.w) continue;
+                    // (2) 3-sigma ellipsoid: m2 A = |w x v'|^2 < 9 A
+                    const float4 s0 = rec[3], s1 = rec[4], s2 = rec[5], v1 = rec[1];
+                    const float wx = s0.x * dx + s0.y * dy + s0.z * dz;
+                    const float wy = s0.w * dx + s1.x * dy + s1.y * dz;
+                    const float wz = s1.z * dx + s1.w * dy + s2.x * dz;
+                    const float A = wx * wx + wy * wy + wz * wz;
+                    const float cx = v1.y * wz - v1.z * wy, cy = v1.z * wx - v1.x * wz, cz = v1.x * wy - v1.y * wx;
+                    const float m2A = cx * cx + cy * cy + cz * cz;
+                    if (m2A >= 9.0f * A) continue;
+                    // (3) the chord must reach beyond the emitting sphere
+                    const float iA = __fdividef(1.0f, A);
+                    const float m2 = m2A * iA;
+                    const float tm = -(v1.x * wx + v1.y * wy + v1.z * wz) * iA;
+                    const float h2 = fmaxf((9.0f - m2) * iA, 1e-30f);
+                    const float h = h2 * rsqrtf(h2);
+                    const float t_out = tm + h;
+                    if (t_out < r_rx) continue;
+                    // hit: midpoint of the chord beyond r_rx
+                    const float t_a = fmaxf(tm - h, r_rx);
+                    const float dt = t_out - t_a;
+                    const float dl = 0.5f * (t_a + t_out) - tm;
+                    const float m2r = m2 + A * dl * dl;
+                    const float alpha = fminf(s2.y * __expf(-0.5f * m2r), amax);
+                    float pr, pi;
+                    fle_psi(reinterpret_cast<const float4*>(a.fle + (size_t)sid[warp][bf][j] * kFle), P, Y, pr, pi);
+                    // S += alpha psi E T, E = e^{-j phi} = (er, ei)
+                    const float er = v1.w, ei = rec[2].x;
+                    const float etr = er * Tr - ei * Ti, eti = er * Ti + ei * Tr;
+                    Sr += alpha * (pr * etr - pi * eti);
+                    Si += alpha * (pr * eti + pi * etr);
+                    // T *= (1 - alpha) e^{-j theta}, theta = 2 pi f0 b dt / c, reduced to
+                    // [-pi, pi] exactly before the hardware sine / cosine
+                    const float x = a.om_pi * s2.z * dt;
+                    const float xr = x - 2.0f * rintf(0.5f * x);
+                    float sn, cs;
+                    __sincosf(3.14159265f * xr, &sn, &cs);
+                    const float om = 1.0f - alpha;
+                    const float nTr = om * (Tr * cs + Ti * sn);
+                    Ti = om * (Ti * cs - Tr * sn);
+                    Tr = nTr;
+                    Ta *= om;
+                    ++hits;
+                    last = (int)(b0 - base0) + j;
+                    if (Ta < eps_T) {
+                        done = true;
+                        stop = j + 1;
+                        break;
+                    }
+                }
+                tests += (unsigned)stop;
+            }
+            mask = next;
+            __syncwarp();
+            if (__all_sync(0xffffffffu, done)) break;
+        }
+        cp_async_wait_all();
     }
 
     if (valid) {
@@ -189,21 +274,16 @@ __global__ void __launch_bounds__(kRenderThreads) k_render_fwd(RenderArgs a) {
             a.rs[ray] = s;
         }
     }
-    // statistics: candidate tests and composited pairs
+    // statistics: list positions tested and composited pairs, one atomic per warp
     unsigned long long t64 = tests, h64 = hits;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         t64 += __shfl_down_sync(0xffffffffu, t64, o);
         h64 += __shfl_down_sync(0xffffffffu, h64, o);
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&s_stats[0], t64);
-        atomicAdd(&s_stats[1], h64);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        atomicAdd(&a.st->stats[0], s_stats[0]);
-        atomicAdd(&a.st->stats[1], s_stats[1]);
+    if (lane == 0) {
+        atomicAdd(&a.st->stats[0], t64);
+        atomicAdd(&a.st->stats[1], h64);
     }
 }
 
@@ -212,7 +292,8 @@ cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     RenderArgs a;
     a.shape = at<GShape>(ws, L.gshape);
     a.view = at<View>(ws, L.view);
-    a.coeffs = g->coeffs;
+    a.fle = at<float>(ws, L.fle);
+    a.raytab = at<float>(ws, L.raytab);
     a.pids = at<uint32_t>(ws, L.pids);
     a.rx_base = at<long long>(ws, L.rx_base);
     a.tile_start = at<uint32_t>(ws, L.tile_start);
@@ -224,10 +305,11 @@ cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     a.n_tiles = L.n_tiles;
     a.n_rx = L.n_rx;
     a.n = L.n;
-    a.omega0 = (float)(2.0 * 3.14159265358979323846 * p->f0_hz / kC);
+    a.om_pi = (float)(2.0 * p->f0_hz / kC);
+    (void)g;
     cudaError_t e = cudaMemsetAsync(&a.st->stats[0], 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    k_render_fwd<<<dim3(L.n_tiles, L.n_rx), kRenderThreads, 0, st>>>(a);
+    k_render_fwd<<<dim3(2 * L.n_tiles, L.n_rx), kThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 

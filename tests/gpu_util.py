@@ -9,18 +9,36 @@ import oracle
 from paper_2502_01826_gb300 import _lib as L
 from paper_2502_01826_gb300.render import Renderer, make_grid, received_signal, to_device
 
-# FP32 forward vs FP64 oracle (spec tolerance): relative L2 error of the per-ray
-# complex signal over all compared rays, and per ray against |S_ref| plus 1% of the
-# rms of S_ref (rays whose signal nearly cancels are compared on the common scale).
+# FP32 forward vs FP64 oracle.  The bar (the benchmark spec): relative L2 error of the per-ray
+# complex signal over the compared rays <= 1e-4.  Per ray, the error of a sum scales
+# with the sum of its terms' magnitudes, sum_k |z_k| (the oracle's Sabs), and with the
+# conditioning of the ray: an FP32 error delta_k in a pair's closest approach m2 moves
+# its weight, the 1 - alpha of every pair behind it and, through the chord
+# dt = 2 sqrt((9 - m2)/A), the transmittance phase 2 pi f b dt / c of everything behind
+# it -- steeply for a grazing pair.  The oracle propagates delta_k = 1e-6 sqrt(C_k)
+# (~ FP32 rounding of a whitened offset sqrt(C_k) long) to first order (Scond); each
+# ray is held to |S_gpu - S_ref| <= 1e-4 Sabs + 4 Scond.
 TOL_L2 = 1e-4
 TOL_RAY = 1e-4
-FLOOR = 1e-2
+COND_MULT = 4.0
 TOL_DB = 0.01
-# Where FP32 and FP64 may legitimately take a different discrete decision, the
-# oracle flags the ray: closest approach within 1e-3 of the 3-sigma boundary
-# (FP32 error of m2 is ~1e-4 for the smallest, farthest Gaussians), exit point within
-# 1e-5 m of the emitting sphere, prod(1 - alpha) within 0.1% of eps_T.
-BANDS = (1e-3, 1e-5, 1e-3)
+# Discrete decisions FP32 may take differently: the closest approach within 4 delta_k
+# of the 3-sigma boundary, the exit point within 1e-5 m of the emitting sphere,
+# ln prod(1 - alpha) within 4 times its propagated error (+1e-5) of ln eps_T.  A ray
+# with one such decision must match the oracle with that decision taken either way;
+# a ray with two or more is not compared (and counted).
+BANDS = (1e-6, 1e-7, 4.0, 1e-5, 4.0, 1e-5)
+MAX_EXCLUDED = 0.02
+
+
+def oracle_pair(scene, rx, tx, f0, grid, rays=None, **kw):
+    """The oracle's render and its render with every in-band decision flipped."""
+    ref = oracle.render(scene, rx, tx, f0, grid, rays=rays, bands=BANDS, **kw)
+    alt = oracle.render(scene, rx, tx, f0, grid, rays=rays, bands=BANDS, flip=True, **kw)
+    ref["S_alt"] = alt["S"]
+    ref["Sabs_alt"] = alt["Sabs"]
+    ref["Scond_alt"] = alt["Scond"]
+    return ref
 
 
 def require_gpu():
@@ -53,19 +71,31 @@ def gpu_render(scene: dict, rx, tx, f0, grid_spec: dict, cap=None, **grid_kw):
     return S.reshape(rx.shape[0], -1), R, p, out
 
 
-def compare(S_gpu: np.ndarray, ref: dict, mask=None, tol_l2=TOL_L2, tol_ray=TOL_RAY):
-    """Compare one receiver's rays.  ``mask``: rays to compare (default: not flagged)."""
-    S_ref = ref["S"][0]
-    if mask is None:
-        mask = ref["flags"] == 0
-    a, b = S_gpu[mask], S_ref[mask]
-    rms = np.sqrt(np.mean(np.abs(S_ref) ** 2)) if S_ref.size else 0.0
+def compare(S_gpu: np.ndarray, ref: dict, f: int = 0, tol_l2=TOL_L2, tol_ray=TOL_RAY,
+            max_excluded=MAX_EXCLUDED):
+    """Compare one receiver's rays at frequency index f against ``oracle_pair``."""
+    namb = ref["flags"] >> 8
+    keep = namb <= 1
+    S_ref = ref["S"][f].copy()
+    bound = tol_ray * ref["Sabs"] + COND_MULT * ref["Scond"]
+    if "S_alt" in ref:
+        alt = ref["S_alt"][f]
+        use_alt = (namb == 1) & (np.abs(S_gpu - alt) < np.abs(S_gpu - S_ref))
+        S_ref[use_alt] = alt[use_alt]
+        bound = np.maximum(bound, tol_ray * ref["Sabs_alt"] + COND_MULT * ref["Scond_alt"])
+    else:
+        keep = namb == 0
+    a, b = S_gpu[keep], S_ref[keep]
     err = np.abs(a - b)
-    l2 = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-    worst = np.max(err / (np.abs(b) + FLOOR * rms + 1e-30)) if a.size else 0.0
+    nb = np.linalg.norm(b)
+    l2 = np.linalg.norm(a - b) / nb if nb > 0 else (np.max(err) if err.size else 0.0)
+    worst = np.max(err / (bound[keep] + 1e-30)) * tol_ray if a.size else 0.0
+    excluded = int((~keep).sum())
     assert l2 <= tol_l2, "relative L2 error %.3g > %.3g" % (l2, tol_l2)
     assert worst <= tol_ray, "worst per-ray error %.3g > %.3g" % (worst, tol_ray)
-    return dict(l2=l2, worst=worst, compared=int(mask.sum()), excluded=int((~mask).sum()))
+    assert excluded <= max_excluded * len(keep) + 1, "%d rays excluded" % excluded
+    return dict(l2=l2, worst=worst, compared=int(keep.sum()), excluded=excluded,
+                ambiguous=int((namb == 1).sum()))
 
 
 def rssi_db(S) -> float:

