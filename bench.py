@@ -226,6 +226,7 @@ def run_ours(args, ws, rank):
     st = R.status()
     L.check("render (device status)", st.code)
     tests_per_step, pairs_per_step = int(st.stats[0]), int(st.stats[1])
+    binned_per_step = int(st.required_pairs)
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     barrier(ws)
@@ -322,6 +323,7 @@ def run_ours(args, ws, rank):
                    "n_gauss": K, "n_rx": n_rx, "grid": "360x90",
                    "f0_hz": cfg["f0"], "pairs_per_step": pairs_per_step,
                    "candidate_tests_per_step": tests_per_step,
+                   "tile_gaussian_pairs_binned_per_step": binned_per_step,
                    "l2": "flushed between timed steps (256 MB write, outside the events)",
                    "parallelism": "replicas: each rank renders its own 64 receivers" if ws > 1 else "1 GPU"},
         "spectra_per_s": spectra_s,

@@ -253,7 +253,10 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_pairs(uint32_t* __restric
 }
 
 // Expand each chunk of depth-sorted Gaussians into its (tile, Gaussian) pairs, written
-// contiguously in depth order (one thread per output pair).
+// contiguously in depth order.  Thread t takes Gaussians t, t + 256, ... of the chunk
+// (consecutive lanes hold consecutive Gaussians, so their pair ranges are adjacent)
+// and walks its tile rectangle row by row; a Gaussian with more than 32 tiles is
+// written by the whole warp instead, one row at a time, a lane per azimuth tile.
 __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restrict__ dval,
                                                        const uint32_t* __restrict__ dkey_sorted,
                                                        const Cover* __restrict__ cover, long long n, int dchunks,
@@ -263,13 +266,15 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
                                                        unsigned long long* __restrict__ pkeys,
                                                        uint32_t* __restrict__ pids, const DevStatus* st) {
     if (capacity_failed(st)) return;
-    __shared__ uint32_t offs[kChunk + 1];
+    __shared__ uint32_t offs[kChunk];
     __shared__ uint32_t sh[kSortWarps];
+    __shared__ uint8_t sbits[kSortWarps][64];
     const int r = blockIdx.y, c = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long lo = (long long)c * kChunk, hi = min(lo + (long long)kChunk, n);
     const int m = (int)(hi - lo);
     constexpr int per = kChunk / kSortThreads;
-    // blocked exclusive scan of the chunk's pair counts
+    // exclusive scan of the pair counts over the chunk, in item order (blocked per thread)
     uint32_t v[per];
     uint32_t s = 0;
 #pragma unroll
@@ -285,30 +290,61 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
         offs[threadIdx.x * per + j] = ex;
         ex += v[j];
     }
-    if (threadIdx.x == 0) offs[kChunk] = tot;
     __syncthreads();
-    const long long out0 = rx_base[r] + chunk_off[(size_t)r * dchunks + c];
-    for (uint32_t p = threadIdx.x; p < tot; p += kSortThreads) {
-        // item owning pair p: last idx with offs[idx] <= p
-        int a = 0, z = m - 1;
-        while (a < z) {
-            const int mid = (a + z + 1) >> 1;
-            if (offs[mid] <= p) a = mid;
-            else z = mid - 1;
+    unsigned long long* kout = pkeys + rx_base[r] + chunk_off[(size_t)r * dchunks + c];
+    uint32_t* iout = pids + rx_base[r] + chunk_off[(size_t)r * dchunks + c];
+    for (int i0 = 0; i0 < m; i0 += kSortThreads) {
+        const int i = i0 + threadIdx.x;
+        bool big = false;
+        Cover cv;
+        cv.mask = 0ull;
+        cv.tv = 0u;
+        cv.count = 0u;
+        uint32_t gid = 0, dk = 0, o = 0;
+        if (i < m) {
+            const size_t gi = (size_t)r * n + lo + i;
+            gid = dval[gi];
+            dk = dkey_sorted[gi];
+            cv = cover[(size_t)r * n + gid];
+            o = offs[i];
+            big = cv.count > 32u;
+            if (!big && cv.count) {
+                const int tvl = (int)(cv.tv & 0xffffu), tvh = (int)(cv.tv >> 16);
+                for (int tv = tvl; tv <= tvh; ++tv)
+                    for (unsigned long long mk = cv.mask; mk; mk &= mk - 1ull) {
+                        const int tu = __ffsll((long long)mk) - 1;
+                        kout[o] = ((unsigned long long)(uint32_t)(tv * ntu + tu) << 32) | dk;
+                        iout[o] = gid;
+                        ++o;
+                    }
+            }
         }
-        const size_t gi = (size_t)r * n + lo + a;
-        const uint32_t gid = dval[gi];
-        const Cover cv = cover[(size_t)r * n + gid];
-        const uint32_t j = p - offs[a];
-        const int nb = __popcll(cv.mask);
-        const int tv = (int)(cv.tv & 0xffffu) + (int)(j / nb);
-        unsigned long long mk = cv.mask;
-        for (uint32_t q = j % nb; q > 0; --q) mk &= mk - 1ull;
-        const int tu = __ffsll((long long)mk) - 1;
-        const uint32_t tile = (uint32_t)(tv * ntu + tu);
-        pkeys[out0 + p] = ((unsigned long long)tile << 32) | dkey_sorted[gi];
-        pids[out0 + p] = gid;
+        for (uint32_t bm = __ballot_sync(0xffffffffu, big); bm; bm &= bm - 1) {
+            const int L = __ffs(bm) - 1;
+            const uint32_t bo = __shfl_sync(0xffffffffu, o, L);
+            const uint32_t bgid = __shfl_sync(0xffffffffu, gid, L);
+            const uint32_t bdk = __shfl_sync(0xffffffffu, dk, L);
+            const uint32_t btv = __shfl_sync(0xffffffffu, cv.tv, L);
+            const uint32_t mlo = __shfl_sync(0xffffffffu, (uint32_t)cv.mask, L);
+            const uint32_t mhi = __shfl_sync(0xffffffffu, (uint32_t)(cv.mask >> 32), L);
+            const unsigned long long bmask = ((unsigned long long)mhi << 32) | mlo;
+            const int nb = __popcll(bmask);
+            // positions of the set azimuth tiles, in order
+            for (int b = lane; b < 64; b += 32)
+                if ((bmask >> b) & 1ull) sbits[warp][__popcll(bmask & ((1ull << b) - 1ull))] = (uint8_t)b;
+            __syncwarp();
+            const int tvl = (int)(btv & 0xffffu), tvh = (int)(btv >> 16);
+            uint32_t row = bo;
+            for (int tv = tvl; tv <= tvh; ++tv, row += nb)
+                for (int q = lane; q < nb; q += 32) {
+                    const int tu = sbits[warp][q];
+                    kout[row + q] = ((unsigned long long)(uint32_t)(tv * ntu + tu) << 32) | bdk;
+                    iout[row + q] = bgid;
+                }
+            __syncwarp();
+        }
     }
+    (void)rx_total;
 }
 
 __global__ void k_zero_tile_start(uint32_t* ts, size_t n) {
