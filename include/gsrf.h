@@ -51,7 +51,8 @@ typedef enum {
     GSRF_ERR_CAPACITY = 3,     /* more (tile, Gaussian) pairs than plan.pair_capacity */
     GSRF_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out */
     GSRF_ERR_NONFINITE = 5,    /* a Gaussian parameter is NaN or infinite */
-    GSRF_ERR_UNSUPPORTED = 6   /* a configuration this build does not implement */
+    GSRF_ERR_UNSUPPORTED = 6,  /* a configuration this build does not implement */
+    GSRF_ERR_TOO_LARGE = 7     /* the problem does not fit gsrf_render_static's fixed array */
 } gsrf_status;
 
 /* The receiver's ray grid (Sec. 4.3, Eqs. 10-12): ray (u, v) points at azimuth
@@ -162,6 +163,28 @@ typedef struct {
 } gsrf_run_status;
 gsrf_status gsrf_read_status(const void *workspace, size_t ws_bytes, gsrf_run_status *out,
                              void *stream);
+
+/* gsrf_render without a caller-supplied workspace, for callers that cannot allocate
+ * device memory: hosts that forbid allocation once running (real-time or embedded
+ * loops), plugins inside an application whose allocator owns all device memory, code
+ * held to a fixed memory budget.  The paper has no counterpart; this is a deployment
+ * convenience of this library.
+ *   Inputs and outputs as for gsrf_render (out_rays [dev]); the workspace is a device
+ *   array of GSRF_STATIC_SCRATCH_BYTES compiled into the library, which every device
+ *   that loads the library holds until the process exits.
+ *   A plan whose gsrf_workspace_size exceeds GSRF_STATIC_SCRATCH_BYTES is rejected with
+ *   GSRF_ERR_TOO_LARGE before anything is launched (32 MiB holds, for one receiver on a
+ *   360 x 90 grid, about 50,000 Gaussians with 300,000 tile pairs).
+ *   status [host] NULL, or filled with the device status after the call (this
+ *   synchronises `stream`).
+ *   The first call on a device looks up the array's device address; make that first
+ *   call before any stream capture.  All calls share the array and it keeps the last
+ *   call's contents (every call initialises what it reads); calls that overlap on the
+ *   GPU -- other streams, other host threads -- race on it.  Nothing is allocated. */
+#define GSRF_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
+gsrf_status gsrf_render_static(const gsrf_plan *plan, const gsrf_gaussians *g, const float *rx_pos,
+                               const float *tx_pos, float *out_rays, gsrf_run_status *status,
+                               void *stream);
 
 /* Library version string. */
 const char *gsrf_version(void);

@@ -11,15 +11,17 @@ import os
 from . import _build
 
 GSRF_OK, GSRF_ERR_INVALID_ARG, GSRF_ERR_CUDA, GSRF_ERR_CAPACITY = 0, 1, 2, 3
-GSRF_ERR_TIMEOUT, GSRF_ERR_NONFINITE, GSRF_ERR_UNSUPPORTED = 4, 5, 6
+GSRF_ERR_TIMEOUT, GSRF_ERR_NONFINITE, GSRF_ERR_UNSUPPORTED, GSRF_ERR_TOO_LARGE = 4, 5, 6, 7
+GSRF_STATIC_SCRATCH_BYTES = 32 << 20
 STATUS_NAMES = {0: "GSRF_OK", 1: "GSRF_ERR_INVALID_ARG", 2: "GSRF_ERR_CUDA", 3: "GSRF_ERR_CAPACITY",
-                4: "GSRF_ERR_TIMEOUT", 5: "GSRF_ERR_NONFINITE", 6: "GSRF_ERR_UNSUPPORTED"}
+                4: "GSRF_ERR_TIMEOUT", 5: "GSRF_ERR_NONFINITE", 6: "GSRF_ERR_UNSUPPORTED",
+                7: "GSRF_ERR_TOO_LARGE"}
 SIG_COMPLEX_SUM, SIG_RSSI_DB, SIG_POWER_SUM, SIG_SPECTRUM_MAG = 0, 1, 2, 3
 
 # every exported symbol of include/gsrf.h
 EXPORTS = ["gsrf_workspace_size", "gsrf_workspace_layout", "gsrf_ray_state_bytes", "gsrf_project",
            "gsrf_bin", "gsrf_render_fwd", "gsrf_render", "gsrf_received_signal", "gsrf_read_status",
-           "gsrf_version"]
+           "gsrf_render_static", "gsrf_version"]
 
 
 class GsrfError(RuntimeError):
@@ -85,6 +87,7 @@ def load(build_if_missing: bool = False):
     L.gsrf_render.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, vp, vp, sz, vp, vp, vp]
     L.gsrf_received_signal.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, vp]
     L.gsrf_read_status.argtypes = [vp, sz, P(gsrf_run_status), vp]
+    L.gsrf_render_static.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, vp, vp, P(gsrf_run_status), vp]
     L.gsrf_version.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("gsrf_ray_state_bytes", "gsrf_version"):
