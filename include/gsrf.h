@@ -133,6 +133,24 @@ gsrf_status gsrf_render_fwd(const gsrf_plan *plan, const gsrf_gaussians *g, void
                             size_t ws_bytes, float *out_rays, void *ray_state, void *stream);
 size_t gsrf_ray_state_bytes(const gsrf_plan *plan);
 
+/* Step 4 -- the backward (adjoint) render of App. D, after gsrf_render_fwd with a ray
+ * state and the same plan and workspace.  Each ray is walked back to front from its last
+ * composited Gaussian, recomputing the transmittance T_k = T_{k+1} / ((1 - alpha_k)
+ * e^{-j theta_k}) instead of storing it; with the suffix R_k of later contributions,
+ * dS/dalpha_k = psi_k E_k T_k - R_k / (1 - alpha_k), dS/dtheta_k = -j R_k,
+ * dS/dphi_k = -j z_k, dS/dpsi_k = alpha_k E_k T_k (App. D.1-D.2), carried through the
+ * midpoint weight and the ray-ellipsoid quadratic (App. D.3) to the raw parameters.
+ *   ray_state [dev] from gsrf_render_fwd; grad_rays [dev] [n_rx][n_f][n_el][n_az][2] holds
+ *   dL/dRe S and dL/dIm S.  Gradients [dev], same shapes as the parameters, are ADDED to
+ *   (+=); any may be NULL.  The gradient of the opacity is taken through its sigmoid, of
+ *   the rotation through the quaternion's normalisation, of the scales through exp.
+ *   Hit decisions that sit on the integer steps of the method (splatting, the 3-sigma
+ *   boundary, the early stop) carry no gradient.  This build: n_f == 1. */
+gsrf_status gsrf_render_bwd(const gsrf_plan *plan, const gsrf_gaussians *g, void *workspace,
+                            size_t ws_bytes, const void *ray_state, const float *grad_rays,
+                            float *g_means, float *g_log_scales, float *g_quats,
+                            float *g_opacity_logit, float *g_coeffs, float *g_phase_b, void *stream);
+
 /* Convenience: gsrf_project + gsrf_bin + gsrf_render_fwd in one call. */
 gsrf_status gsrf_render(const gsrf_plan *plan, const gsrf_gaussians *g, const float *rx_pos,
                         const float *tx_pos, void *workspace, size_t ws_bytes, float *out_rays,

@@ -20,8 +20,8 @@ SIG_COMPLEX_SUM, SIG_RSSI_DB, SIG_POWER_SUM, SIG_SPECTRUM_MAG = 0, 1, 2, 3
 
 # every exported symbol of include/gsrf.h
 EXPORTS = ["gsrf_workspace_size", "gsrf_workspace_layout", "gsrf_ray_state_bytes", "gsrf_project",
-           "gsrf_bin", "gsrf_render_fwd", "gsrf_render", "gsrf_received_signal", "gsrf_read_status",
-           "gsrf_render_static", "gsrf_version"]
+           "gsrf_bin", "gsrf_render_fwd", "gsrf_render_bwd", "gsrf_render", "gsrf_received_signal",
+           "gsrf_read_status", "gsrf_render_static", "gsrf_version"]
 
 
 class GsrfError(RuntimeError):
@@ -85,6 +85,7 @@ def load(build_if_missing: bool = False):
     L.gsrf_bin.argtypes = [P(gsrf_plan), vp, sz, vp]
     L.gsrf_render_fwd.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, sz, vp, vp, vp]
     L.gsrf_render.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, vp, vp, sz, vp, vp, vp]
+    L.gsrf_render_bwd.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, sz, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.gsrf_received_signal.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, vp]
     L.gsrf_read_status.argtypes = [vp, sz, P(gsrf_run_status), vp]
     L.gsrf_render_static.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, vp, vp, P(gsrf_run_status), vp]

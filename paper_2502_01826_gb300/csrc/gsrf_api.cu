@@ -28,6 +28,8 @@ bool make_layout(const gsrf_plan* p, Layout* L) {
     };
     L->status = take(sizeof(DevStatus));
     L->rxpos = take(nr * 3 * sizeof(float));
+    L->txpos = take(3 * sizeof(float));
+    L->gacc = take(n * 48 * sizeof(float));
     L->raytab = take((size_t)g.n_az * g.n_el * kRayTab * sizeof(float));
     L->fle = take(n * kFle * sizeof(float));
     L->gshape = take(n * sizeof(GShape));
@@ -162,6 +164,21 @@ gsrf_status gsrf_render_fwd(const gsrf_plan* plan, const gsrf_gaussians* g, void
         return GSRF_ERR_INVALID_ARG;
     if (plan->n_f != 1) return GSRF_ERR_UNSUPPORTED;
     return cuda_status(launch_render_fwd(plan, L, g, workspace, out_rays, ray_state, (cudaStream_t)stream));
+}
+
+gsrf_status gsrf_render_bwd(const gsrf_plan* plan, const gsrf_gaussians* g, void* workspace, size_t ws_bytes,
+                            const void* ray_state, const float* grad_rays, float* g_means, float* g_log_scales,
+                            float* g_quats, float* g_opacity_logit, float* g_coeffs, float* g_phase_b,
+                            void* stream) {
+    Layout L;
+    gsrf_status s = check_ws(plan, workspace, ws_bytes, &L);
+    if (s != GSRF_OK) return s;
+    if ((s = check_gauss(plan, g)) != GSRF_OK) return s;
+    if (!ray_state || !grad_rays || ((uintptr_t)ray_state & 15) != 0 || ((uintptr_t)grad_rays & 7) != 0)
+        return GSRF_ERR_INVALID_ARG;
+    if (plan->n_f != 1) return GSRF_ERR_UNSUPPORTED;
+    return cuda_status(launch_render_bwd(plan, L, g, workspace, ray_state, grad_rays, g_means, g_log_scales, g_quats,
+                                         g_opacity_logit, g_coeffs, g_phase_b, (cudaStream_t)stream));
 }
 
 gsrf_status gsrf_render(const gsrf_plan* plan, const gsrf_gaussians* g, const float* rx_pos, const float* tx_pos,

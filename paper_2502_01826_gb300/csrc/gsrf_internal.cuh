@@ -81,7 +81,7 @@ struct __align__(16) RayState {
 
 struct Layout {
     // byte offsets
-    size_t status, rxpos, raytab, fle, gshape, dpath, view, cover, dkey, dkey2, dval, dval2, dhist, dchunk_sum,
+    size_t status, rxpos, txpos, gacc, raytab, fle, gshape, dpath, view, cover, dkey, dkey2, dval, dval2, dhist, dchunk_sum,
         rx_base, rx_total, pchunk_base, pkeys, pkeys2, pids, pids2, tile_start, thist, total;
     int32_t ntu, ntv, n_tiles;
     int32_t n_rx;
@@ -170,5 +170,76 @@ cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
                               void* ws, float* out, void* ray_state, cudaStream_t st);
 cudaError_t launch_signal(const float* rays, int n_rx, int n_f, int n_el, int n_az, int mode,
                           float* out, cudaStream_t st);
+cudaError_t launch_render_bwd(const gsrf_plan* p, const Layout& L, const gsrf_gaussians* g, void* ws,
+                              const void* ray_state, const float* grad_rays, float* g_means, float* g_log_scales,
+                              float* g_quats, float* g_opacity_logit, float* g_coeffs, float* g_phase_b,
+                              cudaStream_t st);
+
+}  // namespace gsrf
+
+namespace gsrf {
+
+// ---------------------------------------------------------------------------
+// Geometry of one (ray, candidate) pair, shared by the forward and the backward
+// render so that both take exactly the same hit decisions: every operation that
+// feeds a decision is an explicit round-to-nearest intrinsic, so the compiler cannot
+// contract it differently in the two kernels.
+//
+// Records (6 float4): v0 = (c = mu - r, rc^2), v1 = (w = W (r - mu), er),
+// v2 = (ei, omd, -, -), s0 = W0..W3, s1 = W4..W7, s2 = (W8, o, b, -).
+// Tests, in order: the bounding sphere |c x v|^2 < rc^2; the 3-sigma ellipsoid in
+// whitened coordinates, m2 A = |w x v'|^2 < 9 A (v' = W v, Lagrange's identity, App.
+// D.3 quadratic with A = |v'|^2, B = w.v', C = |w|^2); the chord's exit
+// t_out = t_mid + h >= r_rx with t_mid = -B/A, h = sqrt((9 - m2)/A).
+// ---------------------------------------------------------------------------
+struct PairGeo {
+    float vx, vy, vz;  // v' = W v
+    float A, iA, m2, tm, h, t_out, t_a, dt, dl, m2r;
+};
+
+__device__ __forceinline__ bool pair_sphere(const float4& v0, float dx, float dy, float dz) {
+    const float qx = __fsub_rn(__fmul_rn(v0.y, dz), __fmul_rn(v0.z, dy));
+    const float qy = __fsub_rn(__fmul_rn(v0.z, dx), __fmul_rn(v0.x, dz));
+    const float qz = __fsub_rn(__fmul_rn(v0.x, dy), __fmul_rn(v0.y, dx));
+    return __fmaf_rn(qz, qz, __fmaf_rn(qy, qy, __fmul_rn(qx, qx))) < v0.w;
+}
+
+__device__ __forceinline__ bool pair_hits(const float4& v1, const float4& s0, const float4& s1, const float4& s2,
+                                          float dx, float dy, float dz, float r_rx, PairGeo& g) {
+    g.vx = __fmaf_rn(s0.z, dz, __fmaf_rn(s0.y, dy, __fmul_rn(s0.x, dx)));
+    g.vy = __fmaf_rn(s1.y, dz, __fmaf_rn(s1.x, dy, __fmul_rn(s0.w, dx)));
+    g.vz = __fmaf_rn(s2.x, dz, __fmaf_rn(s1.w, dy, __fmul_rn(s1.z, dx)));
+    g.A = __fmaf_rn(g.vz, g.vz, __fmaf_rn(g.vy, g.vy, __fmul_rn(g.vx, g.vx)));
+    const float cx = __fsub_rn(__fmul_rn(v1.y, g.vz), __fmul_rn(v1.z, g.vy));
+    const float cy = __fsub_rn(__fmul_rn(v1.z, g.vx), __fmul_rn(v1.x, g.vz));
+    const float cz = __fsub_rn(__fmul_rn(v1.x, g.vy), __fmul_rn(v1.y, g.vx));
+    const float m2A = __fmaf_rn(cz, cz, __fmaf_rn(cy, cy, __fmul_rn(cx, cx)));
+    if (m2A >= __fmul_rn(9.0f, g.A)) return false;
+    g.iA = __frcp_rn(g.A);
+    g.m2 = __fmul_rn(m2A, g.iA);
+    const float B = __fmaf_rn(v1.z, g.vz, __fmaf_rn(v1.y, g.vy, __fmul_rn(v1.x, g.vx)));
+    g.tm = -__fmul_rn(B, g.iA);
+    g.h = __fsqrt_rn(fmaxf(__fmul_rn(__fsub_rn(9.0f, g.m2), g.iA), 0.0f));
+    g.t_out = __fadd_rn(g.tm, g.h);
+    if (g.t_out < r_rx) return false;
+    g.t_a = fmaxf(__fsub_rn(g.tm, g.h), r_rx);
+    g.dt = __fsub_rn(g.t_out, g.t_a);
+    g.dl = __fsub_rn(__fmul_rn(0.5f, __fadd_rn(g.t_a, g.t_out)), g.tm);
+    g.m2r = __fmaf_rn(__fmul_rn(g.A, g.dl), g.dl, g.m2);
+    return true;
+}
+
+// Opacity-weighted Gaussian at the midpoint and its clamp (R1, R2): alpha = min(o g, amax).
+__device__ __forceinline__ float pair_alpha(float o, float m2r, float amax, float& gw) {
+    gw = __expf(-0.5f * m2r);
+    return fminf(o * gw, amax);
+}
+
+// Transmittance phase rotation e^{-j theta}, theta = pi x, x = 2 f b dt / c, with x
+// reduced exactly to [-1, 1] before the hardware sine / cosine.
+__device__ __forceinline__ void phase_rot(float x, float& sn, float& cs) {
+    const float xr = x - 2.0f * rintf(0.5f * x);
+    __sincosf(3.14159265f * xr, &sn, &cs);
+}
 
 }  // namespace gsrf

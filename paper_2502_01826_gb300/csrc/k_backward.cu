@@ -1,0 +1,439 @@
+// k_backward.cu -- the adjoint of the render (App. D): gradients of a real loss L with
+// respect to every Gaussian parameter, given G = dL/dRe S + j dL/dIm S per ray.
+//
+// k_render_bwd walks each ray's list back to front from its last composited pair, with
+// the same CTA / warp / staging layout and the same hit decisions (pair_hits) as the
+// forward.  Transmittance is recomputed, not stored: T_k = T_{k+1} e^{+j theta_k} /
+// (1 - alpha_k), starting from the T the forward left in the ray state.  With
+// z_k = alpha_k psi_k E_k T_k and the suffix R_k = sum_{j>k} z_j (App. D.1, D.2):
+//     dS/dalpha_k = psi_k E_k T_k - R_k / (1 - alpha_k),   dS/dtheta_k = -j R_k,
+//     dS/dphi_k = -j z_k,                                  dS/dpsi_k = alpha_k E_k T_k,
+// and dL/dp = Re(conj(G) dS/dp).  App. D.3 then carries dL/dalpha through the midpoint
+// weight and the quadratic A t^2 + 2 B t + (C - 9) = 0 (here A = |v'|^2, B = w.v',
+// C = |w|^2 in whitened coordinates) to the whitening matrix W and the mean; the path
+// phase phi = 2 pi f d / c adds its own term to the mean.  Per candidate, the 46
+// gradient values of the warp's 32 rays are summed by a butterfly reduce-scatter
+// (47 shuffles; lane L ends with totals L and L/2) and added to the Gaussian's
+// accumulator with one atomic per value.
+//
+// k_grad_params chains the accumulators to the raw parameters: W = diag(1/s) R^T to the
+// log-scales and to the (unnormalised) quaternion, the opacity through its sigmoid, the
+// folded Fourier-Legendre coefficients back to the 16 complex coefficients.
+#include <math.h>
+
+#include "gsrf_internal.cuh"
+
+namespace gsrf {
+
+constexpr int kBW = 4;           // warps per CTA
+constexpr int kBThreads = 32 * kBW;
+constexpr int kBB = 32;          // candidates per warp batch
+constexpr int kGrad = 48;        // accumulator floats per Gaussian: W 9, mu 3, o, b, q 32, pad 2
+
+struct BwdArgs {
+    const GShape* shape;
+    const View* view;
+    const float* fle;
+    const float* raytab;
+    const uint32_t* pids;
+    const long long* rx_base;
+    const uint32_t* tile_start;
+    const float* rxpos;
+    const float* txpos;
+    const RayState* rs;
+    const float* grad_rays;
+    float* acc;
+    gsrf_grid gr;
+    int ntu, n_tiles;
+    long long n;
+    float om_pi;  // 2 f0 / c
+};
+
+__device__ __forceinline__ void cp_async16b(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// Butterfly reduce-scatter of 32 values over a warp: afterwards lane L holds the sum of
+// value L over all lanes.
+__device__ __forceinline__ float reduce_scatter32(float* v, int lane) {
+#pragma unroll
+    for (int off = 16, n = 32; off >= 1; off >>= 1, n >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if (i < n / 2) {
+                const float send = up ? v[i] : v[i + n / 2];
+                const float keep = up ? v[i + n / 2] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+            }
+        }
+    }
+    return v[0];
+}
+
+// Same for 16 values: lane L holds the sum of value L / 2.
+__device__ __forceinline__ float reduce_scatter16(float* v, int lane) {
+#pragma unroll
+    for (int off = 16, n = 16; off >= 2; off >>= 1, n >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (i < n / 2) {
+                const float send = up ? v[i] : v[i + n / 2];
+                const float keep = up ? v[i + n / 2] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+            }
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+__global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
+    __shared__ float4 sbuf[kBW][2][kBB][6];
+    __shared__ uint32_t sid[kBW][2][kBB];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = blockIdx.x >> 1, half = blockIdx.x & 1, r = blockIdx.y;
+    const int tu = tile % a.ntu, tv = tile / a.ntu;
+    const int lx = ((warp & 1) << 3) | (lane & 7);
+    const int ly = (half << 3) | ((warp >> 1) << 2) | (lane >> 3);
+    const int u = tu * kTile + lx, v = tv * kTile + ly;
+    const gsrf_grid& gr = a.gr;
+    const bool valid = u < gr.n_az && v < gr.n_el;
+
+    // ray: direction, basis, cone of the warp, state and upstream gradient
+    float dx = 0.0f, dy = 0.0f, dz = 1.0f, P[3] = {0.0f, 0.0f, 0.0f}, Y[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) Y[i] = 0.0f;
+    int last = -1;
+    float Tr = 0.0f, Ti = 0.0f, Gr = 0.0f, Gi = 0.0f;
+    if (valid) {
+        const size_t gi = (size_t)v * gr.n_az + u;
+        const float4* t4 = reinterpret_cast<const float4*>(a.raytab + gi * kRayTab);
+        const float4 t0 = t4[0], t1 = t4[1], t2 = t4[2], t3 = t4[3], t5 = t4[4];
+        dx = t0.x; dy = t0.y; dz = t0.z; P[0] = t0.w;
+        P[1] = t1.x; P[2] = t1.y; Y[0] = t1.z; Y[1] = t1.w;
+        Y[2] = t2.x; Y[3] = t2.y; Y[4] = t2.z; Y[5] = t2.w;
+        Y[6] = t3.x; Y[7] = t3.y; Y[8] = t3.z; Y[9] = t3.w;
+        Y[10] = t5.x; Y[11] = t5.y;
+        const size_t ray = ((size_t)r * gr.n_el + v) * gr.n_az + u;
+        const RayState s = a.rs[ray];
+        last = s.last;
+        Tr = s.Tr;
+        Ti = s.Ti;
+        const float2 g2 = reinterpret_cast<const float2*>(a.grad_rays)[ray];
+        Gr = g2.x;
+        Gi = g2.y;
+    }
+    // the warp's cone (same construction as the forward)
+    float sx = valid ? dx : 0.0f, sy = valid ? dy : 0.0f, sz = valid ? dz : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    }
+    const float inv = rsqrtf(fmaxf(sx * sx + sy * sy + sz * sz, 1e-30f));
+    const float bx = sx * inv, by = sy * inv, bz = sz * inv;
+    float cb = valid ? dx * bx + dy * by + dz * bz : 1.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cb = fminf(cb, __shfl_xor_sync(0xffffffffu, cb, o));
+    cb = fmaxf(fminf(cb, 1.0f), -1.0f) - 2e-5f;
+    const float sb = sqrtf(fmaxf(1.0f - cb * cb, 0.0f));
+
+    // positions are inside the tile's list; a state that points past it (another plan's,
+    // or garbage) is clamped so that no read leaves the list
+    const size_t ts = (size_t)r * (a.n_tiles + 1) + tile;
+    const long long base0 = a.rx_base[r];
+    const long long lo = base0 + a.tile_start[ts];
+    const int len = (int)(a.tile_start[ts + 1] - a.tile_start[ts]);
+    last = min(last, len - 1);
+    int wlast = last;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wlast = max(wlast, __shfl_xor_sync(0xffffffffu, wlast, o));
+    if (wlast < 0) return;  // no ray of this warp composited anything
+    const float r_rx = gr.r_rx, amax = gr.alpha_max;
+    const View* __restrict__ view = a.view + (size_t)r * a.n;
+    const float rx = a.rxpos[3 * r], ry = a.rxpos[3 * r + 1], rz = a.rxpos[3 * r + 2];
+    const float omega = 3.14159265f * a.om_pi;  // 2 pi f0 / c
+
+    float Rr = 0.0f, Ri = 0.0f;  // suffix sum of contributions behind the current pair
+
+    auto stage = [&](int bf, long long b0, long long bend) -> uint32_t {
+        bool keep = false;
+        if (b0 + lane < bend) {
+            const uint32_t id = a.pids[b0 + lane];
+            const float4* vw = reinterpret_cast<const float4*>(view + id);
+            const float4 c = __ldg(vw);
+            const float D2 = c.x * c.x + c.y * c.y + c.z * c.z;
+            if (D2 <= c.w) {
+                keep = true;
+            } else {
+                const float D = sqrtf(D2);
+                keep = c.x * bx + c.y * by + c.z * bz >= cb * sqrtf(D2 - c.w) - sb * sqrtf(c.w) - 1e-4f * D;
+            }
+            if (keep) {
+                sid[warp][bf][lane] = id;
+                const float4* sh = reinterpret_cast<const float4*>(a.shape + id);
+                float4* dst = sbuf[warp][bf][lane];
+                dst[0] = c;
+                cp_async16b(dst + 1, vw + 1);
+                cp_async16b(dst + 2, vw + 2);
+                cp_async16b(dst + 3, sh + 0);
+                cp_async16b(dst + 4, sh + 1);
+                cp_async16b(dst + 5, sh + 2);
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        return __ballot_sync(0xffffffffu, keep);
+    };
+
+    // batches that hold list positions 0 .. wlast, from the last one down
+    const long long end = lo + wlast + 1;
+    long long b0 = lo + ((long long)wlast / kBB) * kBB;
+    int bf = 0;
+    uint32_t mask = stage(0, b0, end);
+    for (; b0 >= lo; b0 -= kBB, bf ^= 1) {
+        const uint32_t next = b0 - kBB >= lo ? stage(bf ^ 1, b0 - kBB, end) : (stage(bf ^ 1, end, end), 0u);
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        __syncwarp();
+        for (uint32_t m = mask; m;) {
+            const int j = 31 - __clz(m);
+            m &= ~(1u << j);
+            const int pos = (int)(b0 - lo) + j;
+            const float4* rec = sbuf[warp][bf][j];
+            const float4 v0 = rec[0], v1 = rec[1], s0 = rec[3], s1 = rec[4], s2 = rec[5];
+            PairGeo pg;
+            bool hit = pos <= last && pair_sphere(v0, dx, dy, dz) && pair_hits(v1, s0, s1, s2, dx, dy, dz, r_rx, pg);
+            if (!__any_sync(0xffffffffu, hit)) continue;
+            float gq[32], go[16];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) gq[i] = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) go[i] = 0.0f;
+            if (hit) {
+                float gw;
+                const float o = s2.y;
+                const float alpha = pair_alpha(o, pg.m2r, amax, gw);
+                const bool clamped = o * gw >= amax;
+                float pr, pi;
+                const float4* q4 = reinterpret_cast<const float4*>(a.fle + (size_t)sid[warp][bf][j] * kFle);
+                {
+                    const float4 a0 = __ldg(q4), a1 = __ldg(q4 + 1);
+                    pr = a0.x + a0.z * P[0] + a1.x * P[1] + a1.z * P[2];
+                    pi = a0.y + a0.w * P[0] + a1.y * P[1] + a1.w * P[2];
+#pragma unroll
+                    for (int t = 0; t < 6; ++t) {
+                        const float4 e = __ldg(q4 + 2 + t);
+                        pr += e.x * Y[2 * t] + e.y * Y[2 * t + 1];
+                        pi += e.z * Y[2 * t] + e.w * Y[2 * t + 1];
+                    }
+                }
+                // T before this pair: undo (1 - alpha) e^{-j theta}
+                float sn, cs;
+                phase_rot(a.om_pi * s2.z * pg.dt, sn, cs);
+                const float iom = 1.0f / (1.0f - alpha);
+                const float nTr = (Tr * cs - Ti * sn) * iom;
+                Ti = (Ti * cs + Tr * sn) * iom;
+                Tr = nTr;
+                // w = E T, z = alpha psi w
+                const float er = v1.w, ei = rec[2].x;
+                const float wr = er * Tr - ei * Ti, wi = er * Ti + ei * Tr;
+                const float zr = alpha * (pr * wr - pi * wi), zi = alpha * (pr * wi + pi * wr);
+                // App. D.1, D.2
+                const float Xr = pr * wr - pi * wi - Rr * iom, Xi = pr * wi + pi * wr - Ri * iom;
+                const float g_alpha = Gr * Xr + Gi * Xi;
+                const float g_th = Gr * Ri - Gi * Rr;
+                const float g_ph = Gr * zi - Gi * zr;
+                const float ur = alpha * wr, ui = alpha * wi;
+                const float g_pr = Gr * ur + Gi * ui, g_pi = Gi * ur - Gr * ui;
+                Rr += zr;
+                Ri += zi;
+                // folded coefficients
+                gq[0] = g_pr; gq[1] = g_pi;
+                gq[2] = g_pr * P[0]; gq[3] = g_pi * P[0];
+                gq[4] = g_pr * P[1]; gq[5] = g_pi * P[1];
+                gq[6] = g_pr * P[2]; gq[7] = g_pi * P[2];
+#pragma unroll
+                for (int t = 0; t < 6; ++t) {
+                    gq[8 + 4 * t] = g_pr * Y[2 * t];
+                    gq[8 + 4 * t + 1] = g_pr * Y[2 * t + 1];
+                    gq[8 + 4 * t + 2] = g_pi * Y[2 * t];
+                    gq[8 + 4 * t + 3] = g_pi * Y[2 * t + 1];
+                }
+                // transmittance phase theta = omega b dt
+                const float g_b = g_th * omega * pg.dt;
+                const float g_dt = g_th * omega * s2.z;
+                // alpha = o g, g = exp(-m2r / 2)
+                float g_o = 0.0f, g_m2r = 0.0f;
+                if (!clamped) {
+                    g_o = g_alpha * gw;
+                    g_m2r = -0.5f * g_alpha * o * gw;
+                }
+                // (m2r, dt) <- (A, B, C); t_mid = -B/A, h = sqrt((9 - m2)/A), B = -A t_mid
+                const float A = pg.A, tm = pg.tm, h = pg.h;
+                const float iAh = 1.0f / fmaxf(A * h, 1e-30f);
+                float gA, gB, gC;
+                if (tm - h >= r_rx) {
+                    gA = g_m2r * tm * tm - g_dt * (tm * tm + h * h) * iAh;
+                    gB = g_m2r * 2.0f * tm - g_dt * 2.0f * tm * iAh;
+                    gC = g_m2r - g_dt * iAh;
+                } else {
+                    const float t_out = pg.t_out, t_rep = 0.5f * (r_rx + t_out);
+                    const float doA = -t_out * pg.iA - 0.5f * (tm * tm - h * h) * iAh;
+                    const float doB = (-1.0f - tm / fmaxf(h, 1e-30f)) * pg.iA;
+                    const float doC = -0.5f * iAh;
+                    const float lin = A * pg.dl;  // half of d m2r / d t_rep
+                    gA = g_m2r * (t_rep * t_rep + lin * doA) + g_dt * doA;
+                    gB = g_m2r * (2.0f * t_rep + lin * doB) + g_dt * doB;
+                    gC = g_m2r * (1.0f + lin * doC) + g_dt * doC;
+                }
+                // A = |v'|^2, B = w.v', C = |w|^2
+                const float w0 = v1.x, w1 = v1.y, w2 = v1.z;
+                const float gv0 = 2.0f * gA * pg.vx + gB * w0, gv1 = 2.0f * gA * pg.vy + gB * w1,
+                            gv2 = 2.0f * gA * pg.vz + gB * w2;
+                const float gw0 = gB * pg.vx + 2.0f * gC * w0, gw1 = gB * pg.vy + 2.0f * gC * w1,
+                            gw2 = gB * pg.vz + 2.0f * gC * w2;
+                // v' = W v, w = W (r - mu) with r - mu = -c
+                const float ux = -v0.x, uy = -v0.y, uz = -v0.z;
+                go[0] = gv0 * dx + gw0 * ux; go[1] = gv0 * dy + gw0 * uy; go[2] = gv0 * dz + gw0 * uz;
+                go[3] = gv1 * dx + gw1 * ux; go[4] = gv1 * dy + gw1 * uy; go[5] = gv1 * dz + gw1 * uz;
+                go[6] = gv2 * dx + gw2 * ux; go[7] = gv2 * dy + gw2 * uy; go[8] = gv2 * dz + gw2 * uz;
+                // dL/dmu = -W^T g_w + (path) g_phi omega (unit(mu - t) + unit(mu - r))
+                float gmx = -(s0.x * gw0 + s0.w * gw1 + s1.z * gw2);
+                float gmy = -(s0.y * gw0 + s1.x * gw1 + s1.w * gw2);
+                float gmz = -(s0.z * gw0 + s1.y * gw1 + s2.x * gw2);
+                const float mx = v0.x + rx, my = v0.y + ry, mz = v0.z + rz;
+                const float tx = mx - a.txpos[0], ty = my - a.txpos[1], tz = mz - a.txpos[2];
+                const float it = rsqrtf(fmaxf(tx * tx + ty * ty + tz * tz, 1e-30f));
+                const float ir = rsqrtf(fmaxf(v0.x * v0.x + v0.y * v0.y + v0.z * v0.z, 1e-30f));
+                const float gd = g_ph * omega;
+                gmx += gd * (tx * it + v0.x * ir);
+                gmy += gd * (ty * it + v0.y * ir);
+                gmz += gd * (tz * it + v0.z * ir);
+                go[9] = gmx; go[10] = gmy; go[11] = gmz;
+                go[12] = g_o;
+                go[13] = g_b;
+            }
+            float* acc = a.acc + (size_t)sid[warp][bf][j] * kGrad;
+            const float sq = reduce_scatter32(gq, lane);
+            atomicAdd(acc + 14 + lane, sq);
+            const float so = reduce_scatter16(go, lane);
+            if ((lane & 1) == 0 && (lane >> 1) < 14) atomicAdd(acc + (lane >> 1), so);
+        }
+        mask = next;
+        __syncwarp();
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Raw-parameter gradients from the accumulators (one thread per Gaussian, += into the
+// caller's buffers; any may be null).
+__global__ void __launch_bounds__(256) k_grad_params(gsrf_gaussians g, const GShape* __restrict__ shape,
+                                                     const float* __restrict__ acc, float* g_means,
+                                                     float* g_log_scales, float* g_quats, float* g_opacity_logit,
+                                                     float* g_coeffs, float* g_phase_b) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.n) return;
+    const float* A = acc + (size_t)k * kGrad;
+    // W = diag(1/s) R^T: W_ij = R_ji / s_i
+    float qw = g.quats[4 * k], qx = g.quats[4 * k + 1], qy = g.quats[4 * k + 2], qz = g.quats[4 * k + 3];
+    const float n2 = qw * qw + qx * qx + qy * qy + qz * qz;
+    const bool degenerate = !(n2 > 0.0f);
+    const float qn = degenerate ? 1.0f : sqrtf(n2);
+    if (degenerate) { qw = 1.0f; qx = qy = qz = 0.0f; }
+    else { qw /= qn; qx /= qn; qy /= qn; qz /= qn; }
+    const float R[9] = {1.0f - 2.0f * (qy * qy + qz * qz), 2.0f * (qx * qy - qw * qz), 2.0f * (qx * qz + qw * qy),
+                        2.0f * (qx * qy + qw * qz), 1.0f - 2.0f * (qx * qx + qz * qz), 2.0f * (qy * qz - qw * qx),
+                        2.0f * (qx * qz - qw * qy), 2.0f * (qy * qz + qw * qx), 1.0f - 2.0f * (qx * qx + qy * qy)};
+    float GR[9];
+    for (int i = 0; i < 3; ++i) {
+        const float is = expf(-g.log_scales[3 * k + i]);
+        float gis = 0.0f;
+        for (int j = 0; j < 3; ++j) {
+            GR[3 * j + i] = A[3 * i + j] * is;  // dL/dR_ji
+            gis += A[3 * i + j] * R[3 * j + i];
+        }
+        if (g_log_scales) g_log_scales[3 * k + i] += -gis * is;  // d(1/s)/dls = -1/s
+    }
+    if (g_quats) {
+        const float dw[9] = {0, -2 * qz, 2 * qy, 2 * qz, 0, -2 * qx, -2 * qy, 2 * qx, 0};
+        const float ddx[9] = {0, 2 * qy, 2 * qz, 2 * qy, -4 * qx, -2 * qw, 2 * qz, 2 * qw, -4 * qx};
+        const float ddy[9] = {-4 * qy, 2 * qx, 2 * qw, 2 * qx, 0, 2 * qz, -2 * qw, 2 * qz, -4 * qy};
+        const float ddz[9] = {-4 * qz, -2 * qw, 2 * qx, 2 * qw, -4 * qz, 2 * qy, 2 * qx, 2 * qy, 0};
+        float gq[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int i = 0; i < 9; ++i) {
+            gq[0] += GR[i] * dw[i];
+            gq[1] += GR[i] * ddx[i];
+            gq[2] += GR[i] * ddy[i];
+            gq[3] += GR[i] * ddz[i];
+        }
+        if (!degenerate) {
+            const float qh[4] = {qw, qx, qy, qz};
+            const float dot = gq[0] * qh[0] + gq[1] * qh[1] + gq[2] * qh[2] + gq[3] * qh[3];
+            for (int i = 0; i < 4; ++i) g_quats[4 * k + i] += (gq[i] - qh[i] * dot) / qn;
+        }
+    }
+    if (g_means)
+        for (int i = 0; i < 3; ++i) g_means[3 * k + i] += A[9 + i];
+    if (g_opacity_logit) {
+        const float o = shape[k].o;
+        g_opacity_logit[k] += A[12] * o * (1.0f - o);
+    }
+    if (g_phase_b) g_phase_b[k] += A[13];
+    if (g_coeffs) {
+        const float* q = A + 14;
+        float* gc = g_coeffs + (size_t)k * 2 * kNB;
+        const int m0[4] = {0, 2, 6, 12};
+        for (int i = 0; i < 4; ++i) {
+            gc[2 * m0[i]] += q[2 * i];
+            gc[2 * m0[i] + 1] += q[2 * i + 1];
+        }
+        // e1 = cr + dr, e2 = di - ci, e3 = ci + di, e4 = cr - dr, d = kappa c_{l,-m}
+        const int np[6] = {3, 7, 13, 8, 14, 15}, nm[6] = {1, 5, 11, 4, 10, 9};
+        const float kap[6] = {-0.5f, -1.0f / 6.0f, -1.0f / 12.0f, 1.0f / 24.0f, 1.0f / 120.0f, -1.0f / 720.0f};
+        for (int t = 0; t < 6; ++t) {
+            const float e1 = q[8 + 4 * t], e2 = q[8 + 4 * t + 1], e3 = q[8 + 4 * t + 2], e4 = q[8 + 4 * t + 3];
+            gc[2 * np[t]] += e1 + e4;
+            gc[2 * np[t] + 1] += e3 - e2;
+            gc[2 * nm[t]] += kap[t] * (e1 - e4);
+            gc[2 * nm[t] + 1] += kap[t] * (e2 + e3);
+        }
+    }
+}
+
+cudaError_t launch_render_bwd(const gsrf_plan* p, const Layout& L, const gsrf_gaussians* g, void* ws,
+                              const void* ray_state, const float* grad_rays, float* g_means, float* g_log_scales,
+                              float* g_quats, float* g_opacity_logit, float* g_coeffs, float* g_phase_b,
+                              cudaStream_t st) {
+    if (L.n == 0) return cudaSuccess;
+    float* acc = at<float>(ws, L.gacc);
+    cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)L.n * kGrad * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    BwdArgs a;
+    a.shape = at<GShape>(ws, L.gshape);
+    a.view = at<View>(ws, L.view);
+    a.fle = at<float>(ws, L.fle);
+    a.raytab = at<float>(ws, L.raytab);
+    a.pids = at<uint32_t>(ws, L.pids);
+    a.rx_base = at<long long>(ws, L.rx_base);
+    a.tile_start = at<uint32_t>(ws, L.tile_start);
+    a.rxpos = at<float>(ws, L.rxpos);
+    a.txpos = at<float>(ws, L.txpos);
+    a.rs = static_cast<const RayState*>(ray_state);
+    a.grad_rays = grad_rays;
+    a.acc = acc;
+    a.gr = p->grid;
+    a.ntu = L.ntu;
+    a.n_tiles = L.n_tiles;
+    a.n = L.n;
+    a.om_pi = (float)(2.0 * p->f0_hz / kC);
+    k_render_bwd<<<dim3(2 * L.n_tiles, L.n_rx), kBThreads, 0, st>>>(a);
+    const unsigned nb = (unsigned)((L.n + 255) / 256);
+    k_grad_params<<<nb, 256, 0, st>>>(*g, at<GShape>(ws, L.gshape), acc, g_means, g_log_scales, g_quats,
+                                      g_opacity_logit, g_coeffs, g_phase_b);
+    return cudaGetLastError();
+}
+
+}  // namespace gsrf

@@ -180,13 +180,19 @@ __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __r
                                               const double* __restrict__ dpath_t, gsrf_grid gr,
                                               int ntu, int ntv, double f0_over_c, float two_pi_df_over_c,
                                               View* __restrict__ view, Cover* __restrict__ cover,
-                                              uint32_t* __restrict__ dkey, float* __restrict__ rx_keep) {
+                                              uint32_t* __restrict__ dkey, float* __restrict__ rx_keep,
+                                              const float* __restrict__ txp, float* __restrict__ tx_keep) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y;
-    if (k == 0) {  // the render reads the receiver positions from the workspace
+    if (k == 0) {  // the render and its backward read the positions from the workspace
         rx_keep[3 * r] = rxp[3 * r];
         rx_keep[3 * r + 1] = rxp[3 * r + 1];
         rx_keep[3 * r + 2] = rxp[3 * r + 2];
+        if (r == 0) {
+            tx_keep[0] = txp[0];
+            tx_keep[1] = txp[1];
+            tx_keep[2] = txp[2];
+        }
     }
     if (k >= g.n) return;
     const size_t o = (size_t)r * g.n + k;
@@ -243,7 +249,8 @@ cudaError_t launch_project(const gsrf_plan* p, const Layout& L, const gsrf_gauss
                                               p->grid, L.ntu, L.ntv, p->f0_hz / kC,
                                               (float)(2.0 * 3.14159265358979323846 * p->df_hz / kC),
                                               at<View>(ws, L.view), at<Cover>(ws, L.cover),
-                                              at<uint32_t>(ws, L.dkey), at<float>(ws, L.rxpos));
+                                              at<uint32_t>(ws, L.dkey), at<float>(ws, L.rxpos), tx,
+                                              at<float>(ws, L.txpos));
     return cudaGetLastError();
 }
 

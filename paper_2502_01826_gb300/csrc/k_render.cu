@@ -10,7 +10,7 @@
 // ballot mask, in list order.  Warps never wait for one another and a warp leaves as
 // soon as its 32 rays have terminated (prod(1 - alpha) < eps_T).
 //
-// Per candidate and ray:
+// Per candidate and ray (pair_sphere / pair_hits, shared with the backward):
 //   (1) bounding sphere: the ray's line passes within rc of mu, |c x v|^2 < rc^2;
 //   (2) 3-sigma ellipsoid in whitened coordinates: with W = diag(1/s) R^T the ray
 //       r + t v maps to w + t v' (w = W (r - mu), v' = W v), so the paper's quadratic
@@ -200,33 +200,12 @@ __global__ void __launch_bounds__(kThreads, 8) k_render_fwd(RenderArgs a) {
                 for (uint32_t m = mask; m; m &= m - 1) {
                     const int j = __ffs(m) - 1;
                     const float4* rec = sbuf[warp][bf][j];
-                    // (1) bounding sphere
-                    const float4 v0 = rec[0];  // c = mu - r, rc^2
-                    const float qx = v0.y * dz - v0.z * dy, qy = v0.z * dx - v0.x * dz, qz = v0.x * dy - v0.y * dx;
-                    if (qx * qx + qy * qy + qz * qz >= v0.w) continue;
-                    // (2) 3-sigma ellipsoid: m2 A = |w x v'|^2 < 9 A
-                    const float4 s0 = rec[3], s1 = rec[4], s2 = rec[5], v1 = rec[1];
-                    const float wx = s0.x * dx + s0.y * dy + s0.z * dz;
-                    const float wy = s0.w * dx + s1.x * dy + s1.y * dz;
-                    const float wz = s1.z * dx + s1.w * dy + s2.x * dz;
-                    const float A = wx * wx + wy * wy + wz * wz;
-                    const float cx = v1.y * wz - v1.z * wy, cy = v1.z * wx - v1.x * wz, cz = v1.x * wy - v1.y * wx;
-                    const float m2A = cx * cx + cy * cy + cz * cz;
-                    if (m2A >= 9.0f * A) continue;
-                    // (3) the chord must reach beyond the emitting sphere
-                    const float iA = __fdividef(1.0f, A);
-                    const float m2 = m2A * iA;
-                    const float tm = -(v1.x * wx + v1.y * wy + v1.z * wz) * iA;
-                    const float h2 = fmaxf((9.0f - m2) * iA, 1e-30f);
-                    const float h = h2 * rsqrtf(h2);
-                    const float t_out = tm + h;
-                    if (t_out < r_rx) continue;
-                    // hit: midpoint of the chord beyond r_rx
-                    const float t_a = fmaxf(tm - h, r_rx);
-                    const float dt = t_out - t_a;
-                    const float dl = 0.5f * (t_a + t_out) - tm;
-                    const float m2r = m2 + A * dl * dl;
-                    const float alpha = fminf(s2.y * __expf(-0.5f * m2r), amax);
+                    if (!pair_sphere(rec[0], dx, dy, dz)) continue;
+                    const float4 v1 = rec[1], s2 = rec[5];
+                    PairGeo pg;
+                    if (!pair_hits(v1, rec[3], rec[4], s2, dx, dy, dz, r_rx, pg)) continue;
+                    float gw;
+                    const float alpha = pair_alpha(s2.y, pg.m2r, amax, gw);
                     float pr, pi;
                     fle_psi(reinterpret_cast<const float4*>(a.fle + (size_t)sid[warp][bf][j] * kFle), P, Y, pr, pi);
                     // S += alpha psi E T, E = e^{-j phi} = (er, ei)
@@ -234,19 +213,16 @@ __global__ void __launch_bounds__(kThreads, 8) k_render_fwd(RenderArgs a) {
                     const float etr = er * Tr - ei * Ti, eti = er * Ti + ei * Tr;
                     Sr += alpha * (pr * etr - pi * eti);
                     Si += alpha * (pr * eti + pi * etr);
-                    // T *= (1 - alpha) e^{-j theta}, theta = 2 pi f0 b dt / c, reduced to
-                    // [-pi, pi] exactly before the hardware sine / cosine
-                    const float x = a.om_pi * s2.z * dt;
-                    const float xr = x - 2.0f * rintf(0.5f * x);
+                    // T *= (1 - alpha) e^{-j theta}, theta = 2 pi f0 b dt / c
                     float sn, cs;
-                    __sincosf(3.14159265f * xr, &sn, &cs);
+                    phase_rot(a.om_pi * s2.z * pg.dt, sn, cs);
                     const float om = 1.0f - alpha;
                     const float nTr = om * (Tr * cs + Ti * sn);
                     Ti = om * (Ti * cs - Tr * sn);
                     Tr = nTr;
                     Ta *= om;
                     ++hits;
-                    last = (int)(b0 - base0) + j;
+                    last = (int)(b0 - lo) + j;  // position inside the tile's list
                     if (Ta < eps_T) {
                         done = true;
                         stop = j + 1;

@@ -118,6 +118,18 @@ class Renderer:
                self.ws_bytes, _ptr(out), _ptr(ray_state), _stream(stream))
         return out
 
+    def render_bwd(self, params: dict, ray_state: torch.Tensor, grad_rays: torch.Tensor, grads: dict,
+                   stream=None):
+        """Add the gradients of sum Re(conj(grad_rays) S) to ``grads`` (same keys and
+        shapes as the parameters; missing keys are skipped)."""
+        gs = gaussians_struct(params)
+        if not (grad_rays.is_cuda and grad_rays.dtype == torch.float32 and grad_rays.is_contiguous()):
+            raise ValueError("grad_rays must be a contiguous float32 CUDA tensor")
+        L.call("gsrf_render_bwd", C.byref(self.plan), C.byref(gs), _ptr(self.ws), self.ws_bytes,
+               _ptr(ray_state), _ptr(grad_rays), *[_ptr(grads.get(k)) for k in PARAM_NAMES],
+               _stream(stream))
+        return grads
+
     def status(self, stream=None) -> L.gsrf_run_status:
         s = L.gsrf_run_status()
         L.call("gsrf_read_status", _ptr(self.ws), self.ws_bytes, C.byref(s), _stream(stream))
@@ -170,3 +182,39 @@ def received_signal(rays: torch.Tensor, mode: int = L.SIG_COMPLEX_SUM, stream=No
         out = torch.empty((n_rx, n_f), dtype=torch.float32, device=rays.device)
     L.call("gsrf_received_signal", _ptr(rays), n_rx, n_f, n_el, n_az, mode, _ptr(out), _stream(stream))
     return out
+
+
+class RenderFunction(torch.autograd.Function):
+    """S = render(theta) with the hand-written backward (App. D) as its gradient.
+
+    forward(renderer, rx, tx, means, log_scales, quats, opacity_logit, coeffs, phase_b)
+    returns the per-ray signal [n_rx, n_f, n_el, n_az, 2].  The renderer's workspace
+    holds the forward's lists until backward runs, so one renderer serves one pending
+    backward at a time."""
+
+    @staticmethod
+    def forward(ctx, renderer: Renderer, rx, tx, means, log_scales, quats, opacity_logit, coeffs, phase_b):
+        params = dict(means=means.detach(), log_scales=log_scales.detach(), quats=quats.detach(),
+                      opacity_logit=opacity_logit.detach(), coeffs=coeffs.detach(),
+                      phase_b=None if phase_b is None else phase_b.detach())
+        state = renderer.ray_state()
+        out = renderer.forward(params, rx, tx, ray_state=state)
+        ctx.renderer = renderer
+        ctx.state = state
+        ctx.params = params
+        ctx.has_b = phase_b is not None
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        p = ctx.params
+        grads = {k: torch.zeros_like(v) for k, v in p.items() if v is not None}
+        ctx.renderer.render_bwd(p, ctx.state, grad_out.contiguous().float(), grads)
+        return (None, None, None, grads["means"], grads["log_scales"], grads["quats"],
+                grads["opacity_logit"], grads["coeffs"], grads.get("phase_b") if ctx.has_b else None)
+
+
+def render(renderer: Renderer, params: dict, rx: torch.Tensor, tx: torch.Tensor) -> torch.Tensor:
+    """Differentiable render: per-ray complex signal as [n_rx, n_f, n_el, n_az, 2]."""
+    return RenderFunction.apply(renderer, rx, tx, params["means"], params["log_scales"], params["quats"],
+                                params["opacity_logit"], params["coeffs"], params.get("phase_b"))

@@ -1,0 +1,168 @@
+"""GPU parity of the hand-written backward (App. D) against the FP64 oracle gradient
+and against central finite differences of the GPU forward, through the C ABI and the
+torch.autograd.Function.
+
+Bar: <= 1e-3 relative, norm-wise per parameter group, and per element against
+|g_ref| + 10% of the group's rms.  Rays that pass within 0.05 of a 3-sigma boundary
+(in m2), within 1 cm of the emitting sphere, or near the termination threshold get no
+weight in the loss: the chord length 2 sqrt((9 - m2)/A) has an unbounded derivative at
+grazing, so there FP32 and FP64 gradients (and finite differences) legitimately part.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2502_01826_gb300 import synthetic
+from paper_2502_01826_gb300.render import Renderer, make_grid, render, to_device
+
+from gpu_util import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ("means", "log_scales", "quats", "opacity_logit", "coeffs", "phase_b")
+MASK_BANDS = (0.0, 0.05, 1.0, 1e-2, 0.0, 0.05)  # m2 within 0.05, exit within 1 cm, ln Ta within 0.05
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+    oracle.build()
+
+
+def masked_upstream(scene, rx, tx, f0, spec, rng, eps_T=1e-4):
+    """Random upstream dL/dS per ray, zero on rays near a discrete decision."""
+    g = oracle.make_grid(**spec, eps_T=eps_T)
+    G = []
+    for r in range(rx.shape[0]):
+        out = oracle.render(scene, rx[r], tx, f0, g, bands=MASK_BANDS)
+        Gr = rng.normal(size=out["S"].shape[1]) + 1j * rng.normal(size=out["S"].shape[1])
+        Gr[out["flags"] != 0] = 0
+        G.append(Gr)
+    return np.array(G), g
+
+
+def gpu_grads(scene, rx, tx, f0, spec, G, eps_T=1e-4):
+    """Gradients of sum Re(conj(G) S) through the autograd Function."""
+    K = scene["means"].shape[0]
+    grid = make_grid(**spec, eps_T=eps_T)
+    R = Renderer(K, rx.shape[0], grid, f0)
+    p = {k: v.clone().requires_grad_(True) for k, v in to_device(scene).items()}
+    rxd = torch.tensor(rx, device="cuda")
+    txd = torch.tensor(tx, device="cuda")
+    R.ensure_capacity({k: v.detach() for k, v in p.items()}, rxd, txd)
+    S = render(R, p, rxd, txd)  # [n_rx, 1, n_el, n_az, 2]
+    Gt = torch.tensor(np.stack([G.real, G.imag], -1), dtype=torch.float32, device="cuda")
+    Gt = Gt.reshape(S.shape)
+    loss = (S * Gt).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    return {k: p[k].grad.cpu().numpy().astype(np.float64) for k in NAMES}
+
+
+def oracle_grads(scene, rx, tx, f0, g, G):
+    tot = None
+    for r in range(rx.shape[0]):
+        gr = oracle.render_grad(scene, rx[r], tx, f0, g, G[r][None])
+        tot = gr if tot is None else {k: tot[k] + gr[k] for k in tot}
+    return tot
+
+
+def compare_grads(gg, go, tol=1e-3):
+    report = {}
+    for k in NAMES:
+        a, b = gg[k].ravel(), go[k].ravel()
+        nb = np.linalg.norm(b)
+        rel = np.linalg.norm(a - b) / max(nb, 1e-30)
+        rms = np.sqrt(np.mean(b ** 2))
+        worst = np.max(np.abs(a - b) / (np.abs(b) + 0.1 * rms + 1e-30))
+        report[k] = (rel, worst)
+        assert rel <= tol, "%s: relative error %.3g" % (k, rel)
+        assert worst <= 10 * tol, "%s: worst element %.3g" % (k, worst)
+    return report
+
+
+def test_backward_matches_oracle_gradient_small():
+    scene = synthetic.tiny_scene(300, 201, box=(6.0, 5.0, 3.0), log_scale_mu=math.log(0.25))
+    rng = np.random.default_rng(1)
+    rx = (rng.uniform(0, 1, (2, 3)) * [6.0, 5.0, 3.0]).astype(np.float32)
+    tx = np.array([0.5, 4.0, 2.0], np.float32)
+    spec = dict(n_az=72, n_el=18)
+    G, g = masked_upstream(scene, rx, tx, 2.4e9, spec, rng)
+    assert np.count_nonzero(G) > 0.5 * G.size
+    compare_grads(gpu_grads(scene, rx, tx, 2.4e9, spec, G), oracle_grads(scene, rx, tx, 2.4e9, g, G))
+
+
+def test_backward_matches_oracle_on_512_gaussian_training_subscene():
+    """A 512-Gaussian sub-scene of the training workload (same box and distributions),
+    16 receivers on the 360 x 90 grid, loss = complex MSE against targets the oracle
+    renders from a separately seeded ground-truth set."""
+    cfg = synthetic.config_train(K=512, n_rx=16)
+    scene, gt = cfg["scene"], cfg["gt_scene"]
+    rx, tx, f0 = cfg["rx"], cfg["tx"], cfg["f0"]
+    spec = cfg["grid"]
+    g = oracle.make_grid(**spec)
+    rng = np.random.default_rng(2)
+    # dL/dS for L = mean |S - S_gt|^2 is 2 (S - S_gt) / N, evaluated with the oracle
+    G = []
+    for r in range(rx.shape[0]):
+        S = oracle.render(scene, rx[r], tx, f0, g, bands=MASK_BANDS)
+        S_gt = oracle.render(gt, rx[r], tx, f0, g)["S"][0]
+        Gr = 2.0 * (S["S"][0] - S_gt) / S_gt.size
+        Gr[S["flags"] != 0] = 0
+        G.append(Gr)
+    G = np.array(G)
+    assert np.count_nonzero(G) > 0.5 * G.size
+    compare_grads(gpu_grads(scene, rx, tx, f0, spec, G), oracle_grads(scene, rx, tx, f0, g, G))
+
+
+def test_backward_against_central_differences_of_the_gpu_forward():
+    """Central differences (eps = 1e-3 relative) of the GPU forward on 32 random
+    parameters.  FP32 forward noise and the curvature of the path phase bound the
+    difference quotient's accuracy, so the check is at 2e-2 (plus an rms floor)."""
+    scene = synthetic.tiny_scene(200, 202, box=(5.0, 5.0, 3.0), log_scale_mu=math.log(0.3))
+    rng = np.random.default_rng(3)
+    rx = (rng.uniform(0, 1, (1, 3)) * [5.0, 5.0, 3.0]).astype(np.float32)
+    tx = np.array([4.0, 0.5, 1.0], np.float32)
+    spec = dict(n_az=72, n_el=18)
+    f0 = 3.0e8  # low carrier keeps the phase curvature inside the step
+    G, g = masked_upstream(scene, rx, tx, f0, spec, rng, eps_T=0.0)
+    grads = gpu_grads(scene, rx, tx, f0, spec, G, eps_T=0.0)
+    K = scene["means"].shape[0]
+    grid = make_grid(**spec, eps_T=0.0)
+    R = Renderer(K, 1, grid, f0)
+    rxd = torch.tensor(rx, device="cuda")
+    txd = torch.tensor(tx, device="cuda")
+    Gt = torch.tensor(np.stack([G.real, G.imag], -1), dtype=torch.float64, device="cuda")
+
+    def loss_of(sc):
+        p = to_device(sc)
+        R.ensure_capacity(p, rxd, txd)
+        S = R.forward(p, rxd, txd).double().reshape(Gt.shape)
+        return float((S * Gt).sum().item())
+
+    errs, checked = [], 0
+    for _ in range(200):
+        name = NAMES[rng.integers(len(NAMES))]
+        arr = scene[name]
+        idx = tuple(rng.integers(n) for n in arr.shape)
+        x0 = float(arr[idx])
+        h = 1e-3 * max(1.0, abs(x0))
+        sp = {k: v.copy() for k, v in scene.items()}
+        sm = {k: v.copy() for k, v in scene.items()}
+        sp[name][idx] = np.float32(x0 + h)
+        sm[name][idx] = np.float32(x0 - h)
+        fd = (loss_of(sp) - loss_of(sm)) / (float(sp[name][idx]) - float(sm[name][idx]))
+        an = grads[name][idx]
+        if abs(an) < 1e-12 and abs(fd) < 1e-9:
+            continue
+        errs.append((abs(fd - an), abs(an)))
+        checked += 1
+        if checked >= 32:
+            break
+    errs = np.array(errs)
+    rms = np.sqrt(np.mean(errs[:, 1] ** 2))
+    bad = errs[:, 0] > 2e-2 * (errs[:, 1] + 0.1 * rms)
+    assert checked >= 24 and bad.sum() <= 2, errs[bad]
