@@ -94,7 +94,7 @@ typedef struct {
 gsrf_status gsrf_workspace_size(const gsrf_plan *plan, size_t *bytes);
 
 /* Byte offsets inside the workspace of the arrays tests and tools may inspect after
- * gsrf_bin: sorted 64-bit splat keys (tile << 32 | FP32 depth bits) [uint64], their
+ * gsrf_project (view) and gsrf_bin (the rest): sorted 64-bit splat keys (tile << 32 | FP32 depth bits) [uint64], their
  * Gaussian ids [uint32], both over all receivers back to back; per receiver the first
  * pair (int64, [n_rx + 1]); per receiver and tile the list start relative to the
  * receiver's first pair (uint32, [n_rx][n_tiles + 1]). */
@@ -102,6 +102,11 @@ typedef struct {
     size_t pair_keys, pair_ids, rx_pair_base, tile_start;
     size_t status;
     int32_t n_tiles_u, n_tiles_v;
+    size_t view;               /* per (receiver, Gaussian) 48-byte records after gsrf_project,
+                                * receiver-major: floats 0-2 mu - r, 3 bounding radius^2,
+                                * 4-6 whitened receiver offset, 7-8 e^{-j 2 pi f0 d / c}
+                                * (cos, -sin) with the phase reduced in FP64, 9 the
+                                * per-subcarrier step 2 pi df d / c, 10-11 unused */
 } gsrf_layout;
 gsrf_status gsrf_workspace_layout(const gsrf_plan *plan, gsrf_layout *out);
 

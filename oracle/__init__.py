@@ -90,6 +90,8 @@ def lib():
         L.or_cover_f32.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.or_bin.restype = i64
         L.or_bin.argtypes = [vp, vp, vp, vp, vp, i64, vp]
+        L.or_path_phase.restype = None
+        L.or_path_phase.argtypes = [vp, vp, vp, dbl, vp]
         L.or_render.restype = C.c_int
         L.or_render.argtypes = [vp, vp, vp, dbl, dbl, i32, vp, i32, vp, i64, i32, vp,
                                 vp, vp, vp, vp, vp, vp, vp, vp]
@@ -205,6 +207,14 @@ def bin_pairs(scene: dict, rx, grid: Grid):
     got = lib().or_bin(C.byref(s.c), _p(rxa), C.byref(grid), _p(keys), _p(ids), tot, _p(ts))
     assert got == tot
     return keys[:tot], ids[:tot], ts
+
+
+def path_phase(scene: dict, rx, tx, f: float) -> np.ndarray:
+    """phi_k = 2 pi f (|t - mu_k| + |mu_k - r|) / c in [0, 2 pi), FP64."""
+    s = _SceneRef(scene)
+    out = np.zeros(s.n)
+    lib().or_path_phase(C.byref(s.c), _p(_f32(rx)), _p(_f32(tx)), float(f), _p(out))
+    return out
 
 
 def render(scene: dict, rx, tx, f0: float, grid: Grid, df: float = 0.0, n_f: int = 1,

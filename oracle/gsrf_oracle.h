@@ -129,6 +129,10 @@ int32_t or_cover_f32(const float *mu, const float *log_scale, const float *r, co
 int64_t or_bin(const or_scene *s, const float *rx, const or_grid *g,
                uint64_t *keys, uint32_t *ids, int64_t cap, int64_t *tile_start);
 
+/* Path phase of every Gaussian at frequency f (Sec. 2 multipath model, reading R8):
+ * phi_k = 2 pi f (|t - mu_k| + |mu_k - r|) / c reduced to [0, 2 pi), FP64. */
+void or_path_phase(const or_scene *s, const float *rx, const float *tx, double f, double *phi);
+
 /* ---- the render ---- */
 
 /* Render receiver rx for transmitter tx at frequencies f0 + i*df, i < n_f.

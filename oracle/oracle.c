@@ -217,6 +217,20 @@ int64_t or_bin(const or_scene *s, const float *rx, const or_grid *g,
     return total <= cap ? total : -total;
 }
 
+void or_path_phase(const or_scene *s, const float *rx, const float *tx, double f, double *phi)
+{
+    for (int64_t k = 0; k < s->n; ++k) {
+        double dt = 0.0, dr = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            double m = s->means[3 * k + i];
+            dt += ((double)tx[i] - m) * ((double)tx[i] - m);
+            dr += (m - (double)rx[i]) * (m - (double)rx[i]);
+        }
+        double cyc = f * (sqrt(dt) + sqrt(dr)) / OR_C_LIGHT;
+        phi[k] = 2.0 * M_PI * (cyc - floor(cyc));
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* The render (Alg. 1 lines 6-12; Eq. 14; App. A.3)                             */
 /* ------------------------------------------------------------------------- */

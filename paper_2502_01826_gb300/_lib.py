@@ -49,7 +49,7 @@ class gsrf_plan(C.Structure):
 class gsrf_layout(C.Structure):
     _fields_ = [("pair_keys", C.c_size_t), ("pair_ids", C.c_size_t), ("rx_pair_base", C.c_size_t),
                 ("tile_start", C.c_size_t), ("status", C.c_size_t), ("n_tiles_u", C.c_int32),
-                ("n_tiles_v", C.c_int32)]
+                ("n_tiles_v", C.c_int32), ("view", C.c_size_t)]
 
 
 class gsrf_run_status(C.Structure):

@@ -129,6 +129,7 @@ gsrf_status gsrf_workspace_layout(const gsrf_plan* plan, gsrf_layout* out) {
     out->status = L.status;
     out->n_tiles_u = L.ntu;
     out->n_tiles_v = L.ntv;
+    out->view = L.view;
     return GSRF_OK;
 }
 
@@ -162,7 +163,6 @@ gsrf_status gsrf_render_fwd(const gsrf_plan* plan, const gsrf_gaussians* g, void
     if ((s = check_gauss(plan, g)) != GSRF_OK) return s;
     if (!out_rays || ((uintptr_t)out_rays & 7) != 0 || ((uintptr_t)ray_state & 15) != 0)
         return GSRF_ERR_INVALID_ARG;
-    if (plan->n_f != 1) return GSRF_ERR_UNSUPPORTED;
     return cuda_status(launch_render_fwd(plan, L, g, workspace, out_rays, ray_state, (cudaStream_t)stream));
 }
 

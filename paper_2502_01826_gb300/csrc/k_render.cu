@@ -45,6 +45,8 @@ struct RenderArgs {
     int ntu, n_tiles, n_rx;
     long long n;
     float om_pi;  // 2 f0 / c: sincospi argument per unit of b dt
+    int n_f;      // frequencies f0 + s df
+    float dlt;    // 2 pi df / c: subcarrier phase step per metre of excess path
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -130,7 +132,13 @@ __device__ __forceinline__ bool bundle_meets(const Bundle& b, float4 c) {
     return cd >= b.cb * sqrtf(D2 - c.w) - b.sb * sqrtf(c.w) - 1e-4f * D;
 }
 
-__global__ void __launch_bounds__(kThreads, 8) k_render_fwd(RenderArgs a) {
+// NFC = 1: one frequency.  NFC > 1: thread handles subcarriers s0 .. s0 + NFC - 1 of the
+// grid's z-th chunk; the contribution of a pair at f0 + s df is z0 r^s with
+// r = e^{-j (2 pi df d / c + 2 pi df Gamma / c)}, Gamma = sum over earlier pairs of b dt,
+// because T(f0 + s df) = T(f0) e^{-j s 2 pi df Gamma / c} and E(f0 + s df) =
+// E(f0) e^{-j s 2 pi df d / c}; the powers of r come from one sincos and a recurrence.
+template <int NFC>
+__global__ void __launch_bounds__(kThreads, NFC == 1 ? 8 : 4) k_render_fwd(RenderArgs a) {
     __shared__ float4 sbuf[kWarps][2][kWB][kRec];
     __shared__ uint32_t sid[kWarps][2][kWB];
 
@@ -156,6 +164,11 @@ __global__ void __launch_bounds__(kThreads, 8) k_render_fwd(RenderArgs a) {
     const View* __restrict__ view = a.view + (size_t)r * a.n;
 
     float Sr = 0.0f, Si = 0.0f, Tr = 1.0f, Ti = 0.0f, Ta = 1.0f;
+    float Sf[2 * NFC];
+#pragma unroll
+    for (int i = 0; i < 2 * NFC; ++i) Sf[i] = 0.0f;
+    float Gam = 0.0f;
+    const int s0 = (int)blockIdx.z * NFC;
     int last = -1;
     bool done = !valid;
     unsigned tests = 0, hits = 0;
@@ -211,8 +224,27 @@ __global__ void __launch_bounds__(kThreads, 8) k_render_fwd(RenderArgs a) {
                     // S += alpha psi E T, E = e^{-j phi} = (er, ei)
                     const float er = v1.w, ei = rec[2].x;
                     const float etr = er * Tr - ei * Ti, eti = er * Ti + ei * Tr;
-                    Sr += alpha * (pr * etr - pi * eti);
-                    Si += alpha * (pr * eti + pi * etr);
+                    if constexpr (NFC == 1) {
+                        Sr += alpha * (pr * etr - pi * eti);
+                        Si += alpha * (pr * eti + pi * etr);
+                    } else {
+                        // z at the chunk's first subcarrier, then one rotation per step
+                        const float ws = rec[2].y + a.dlt * Gam;
+                        float rs, rc, ss, sc;
+                        sincosf(ws, &rs, &rc);
+                        sincosf((float)s0 * ws, &ss, &sc);
+                        const float z0r = alpha * (pr * etr - pi * eti), z0i = alpha * (pr * eti + pi * etr);
+                        float zr = z0r * sc + z0i * ss, zi = z0i * sc - z0r * ss;
+#pragma unroll
+                        for (int q = 0; q < NFC; ++q) {
+                            Sf[2 * q] += zr;
+                            Sf[2 * q + 1] += zi;
+                            const float nzr = zr * rc + zi * rs;
+                            zi = zi * rc - zr * rs;
+                            zr = nzr;
+                        }
+                        Gam += s2.z * pg.dt;
+                    }
                     // T *= (1 - alpha) e^{-j theta}, theta = 2 pi f0 b dt / c
                     float sn, cs;
                     phase_rot(a.om_pi * s2.z * pg.dt, sn, cs);
@@ -239,9 +271,17 @@ __global__ void __launch_bounds__(kThreads, 8) k_render_fwd(RenderArgs a) {
     }
 
     if (valid) {
-        const size_t ray = ((size_t)r * gr.n_el + v) * gr.n_az + u;  // n_f == 1
-        reinterpret_cast<float2*>(a.out)[ray] = make_float2(Sr, Si);
-        if (a.rs) {
+        const size_t plane = (size_t)gr.n_el * gr.n_az, pix = (size_t)v * gr.n_az + u;
+        const size_t ray = (size_t)r * plane + pix;
+        if constexpr (NFC == 1) {
+            reinterpret_cast<float2*>(a.out)[ray] = make_float2(Sr, Si);
+        } else {
+            float2* o2 = reinterpret_cast<float2*>(a.out) + ((size_t)r * a.n_f + s0) * plane + pix;
+#pragma unroll
+            for (int q = 0; q < NFC; ++q)
+                if (s0 + q < a.n_f) o2[(size_t)q * plane] = make_float2(Sf[2 * q], Sf[2 * q + 1]);
+        }
+        if (a.rs && blockIdx.z == 0) {
             RayState s;
             s.last = last;
             s.Ta = Ta;
@@ -257,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_render_fwd(RenderArgs a) {
         t64 += __shfl_down_sync(0xffffffffu, t64, o);
         h64 += __shfl_down_sync(0xffffffffu, h64, o);
     }
-    if (lane == 0) {
+    if (lane == 0 && blockIdx.z == 0) {
         atomicAdd(&a.st->stats[0], t64);
         atomicAdd(&a.st->stats[1], h64);
     }
@@ -282,10 +322,18 @@ cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     a.n_rx = L.n_rx;
     a.n = L.n;
     a.om_pi = (float)(2.0 * p->f0_hz / kC);
+    a.n_f = p->n_f;
+    a.dlt = (float)(2.0 * 3.14159265358979323846 * p->df_hz / kC);
     (void)g;
     cudaError_t e = cudaMemsetAsync(&a.st->stats[0], 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    k_render_fwd<<<dim3(2 * L.n_tiles, L.n_rx), kThreads, 0, st>>>(a);
+    if (p->n_f == 1) {
+        k_render_fwd<1><<<dim3(2 * L.n_tiles, L.n_rx), kThreads, 0, st>>>(a);
+    } else if (p->n_f <= 8) {
+        k_render_fwd<8><<<dim3(2 * L.n_tiles, L.n_rx, 1), kThreads, 0, st>>>(a);
+    } else {
+        k_render_fwd<16><<<dim3(2 * L.n_tiles, L.n_rx, (p->n_f + 15) / 16), kThreads, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -154,6 +154,12 @@ class Renderer:
         L.call("gsrf_workspace_layout", C.byref(self.plan), C.byref(lay))
         return lay
 
+    def view_records(self) -> torch.Tensor:
+        """View records after project: float32 [n_rx, n_gauss, 12] (see gsrf_layout.view)."""
+        lay = self.layout()
+        nr, n = self.plan.n_rx, self.plan.n_gauss
+        return self.ws[lay.view: lay.view + 48 * nr * n].view(torch.float32).view(nr, n, 12)
+
     def pairs(self):
         """Views into the workspace after bin: (keys uint64 [total], ids int32 [total],
         rx_base int64 [n_rx+1], tile_start int32 [n_rx, n_tiles+1])."""

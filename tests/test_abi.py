@@ -49,8 +49,8 @@ def test_struct_layouts_match_header(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\\n", sizeof(gsrf_grid), sizeof(gsrf_gaussians), sizeof(gsrf_plan),
          sizeof(gsrf_layout), sizeof(gsrf_run_status));
-  printf("%zu %zu %zu %zu\\n", offsetof(gsrf_plan, f0_hz), offsetof(gsrf_plan, grid),
-         offsetof(gsrf_plan, pair_capacity), offsetof(gsrf_run_status, stats));
+  printf("%zu %zu %zu %zu %zu\\n", offsetof(gsrf_plan, f0_hz), offsetof(gsrf_plan, grid),
+         offsetof(gsrf_plan, pair_capacity), offsetof(gsrf_run_status, stats), offsetof(gsrf_layout, view));
   return 0;
 }
 """)
@@ -62,7 +62,7 @@ int main(void) {
     assert sizes == [C.sizeof(L.gsrf_grid), C.sizeof(L.gsrf_gaussians), C.sizeof(L.gsrf_plan),
                      C.sizeof(L.gsrf_layout), C.sizeof(L.gsrf_run_status)]
     assert offs == [L.gsrf_plan.f0_hz.offset, L.gsrf_plan.grid.offset, L.gsrf_plan.pair_capacity.offset,
-                    L.gsrf_run_status.stats.offset]
+                    L.gsrf_run_status.stats.offset, L.gsrf_layout.view.offset]
 
 
 def plan(n=1000, n_rx=4, n_az=360, n_el=90, cap=100000, **kw):

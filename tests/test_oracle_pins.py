@@ -642,3 +642,25 @@ def test_flipped_decisions_change_only_flagged_rays(oracle_lib):
     assert np.any(a["S"][:, namb > 0] != b["S"][:, namb > 0])
     zero = oracle_lib.render(s, r, t, 2.4e9, g, bands=(0.0, 0.0, 0.0, 0.0, 0.0, 0.0), flip=True)
     assert np.array_equal(zero["S"], oracle_lib.render(s, r, t, 2.4e9, g)["S"])
+
+
+def test_path_phase_reduction(oracle_lib):
+    """The FP64 distance-to-phase step: the Sec. 2 example (0.0625 m more at 2.4 GHz is
+    a pi shift) and numpy FP64 arithmetic on the same float32 positions."""
+    gold = read_golden("worked_example_phase.txt")
+    s = one_gaussian((4.0, 0.0, 0.0))
+    r = np.zeros(3, np.float32)
+    t1 = np.array([4.0, 3.0, 0.0], np.float32)      # d = 3 + 4 = 7 m
+    t2 = np.array([4.0, 3.0625, 0.0], np.float32)   # 0.0625 m further
+    p1 = oracle_lib.path_phase(s, r, t1, gold["f_c_hz"])[0]
+    p2 = oracle_lib.path_phase(s, r, t2, gold["f_c_hz"])[0]
+    assert abs(((p2 - p1) % (2 * np.pi)) - gold["delta_phi_rad"]) < 1e-9
+    sc = synthetic.scene(200, 91)
+    rx = np.array([1.0, 2.0, 0.5], np.float32)
+    tx = np.array([9.0, 7.0, 2.5], np.float32)
+    ph = oracle_lib.path_phase(sc, rx, tx, 5.2e9)
+    m = sc["means"].astype(np.float64)
+    d = np.linalg.norm(m - tx.astype(np.float64), axis=1) + np.linalg.norm(m - rx.astype(np.float64), axis=1)
+    ref = np.mod(2 * np.pi * 5.2e9 * d / 3e8, 2 * np.pi)
+    diff = np.angle(np.exp(1j * (ph - ref)))
+    assert np.max(np.abs(diff)) < 1e-9 and np.all((ph >= 0) & (ph < 2 * np.pi))
