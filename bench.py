@@ -306,7 +306,9 @@ def run_ours(args, ws, rank):
     e2e_total = max_over_ranks(sum(t_e2e), ws)
     e2e_value = sum_over_ranks(pairs_per_step * args.steps, ws) / e2e_total
 
+    persistent = persistent_leg(args, cfg, p, rx, tx, R, flush, pairs_per_step)
     fwd_bwd = train_leg(args, ws, flush) if not args.no_train else None
+    uneven = uneven_leg(args, flush) if args.uneven else None
 
     pk_, pk_kind = peaks()
     mhz = float(pk_.get("sm_max_mhz", 2070.0))
@@ -340,11 +342,151 @@ def run_ours(args, ws, rank):
                      "flop_per_launch": flops},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": 1e3 * sum(t_e2e) / len(t_e2e)},
+        "persistent": persistent,
         "fwd_bwd": fwd_bwd,
+        "uneven": uneven,
         "gpu_launches": 24 * args.steps,
         "clocks": clocks,
     }
     return result, cfg
+
+
+def _time_steps(fn, steps, flush):
+    import numpy as np
+    import torch
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        fn()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+
+def persistent_leg(args, cfg, p, rx, tx, R, flush, pairs_per_step):
+    """The same step with the render as one persistent launch (heaviest-first work
+    queue), then the whole step captured in one CUDA graph; and the 64 receivers as 64
+    single-receiver jobs in one persistent launch (the batched form of the plain
+    per-receiver launch)."""
+    import torch
+
+    from paper_2502_01826_gb300 import _lib as L
+    from paper_2502_01826_gb300.render import BatchRender, Renderer, make_grid, received_signal
+
+    B = BatchRender([R])
+
+    def step():
+        R.project(p, rx, tx)
+        R.bin()
+        B.render()
+        received_signal(B.outs[0], L.SIG_RSSI_DB)
+
+    for _ in range(args.warmup):
+        step()
+    ms_q = _time_steps(step, args.steps, flush)
+    # CUDA graph of the whole step
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            step()
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(args.warmup):
+        g.replay()
+    ms_g = _time_steps(g.replay, args.steps, flush)
+    # 64 single-receiver jobs, one persistent launch
+    n_rx = rx.shape[0]
+    grid = make_grid(**cfg["grid"])
+    K = cfg["scene"]["means"].shape[0]
+    jobs = []
+    for r in range(n_rx):
+        Rj = Renderer(K, 1, grid, cfg["f0"], pair_capacity=1024)
+        Rj.ensure_capacity(p, rx[r:r + 1], tx)
+        jobs.append(Rj)
+    Bj = BatchRender(jobs)
+
+    def step_jobs():
+        for r, Rj in enumerate(jobs):
+            Rj.project(p, rx[r:r + 1], tx)
+            Rj.bin()
+        for o in Bj.render():
+            received_signal(o, L.SIG_RSSI_DB)
+
+    for _ in range(args.warmup):
+        step_jobs()
+    ms_j = _time_steps(step_jobs, max(1, min(args.steps, 5)), flush)
+    return {"render": "gsrf_render_batch (persistent, heaviest-first queue)",
+            "ms_per_step": ms_q, "pairs_per_s": pairs_per_step / (ms_q / 1e3),
+            "graph_ms_per_step": ms_g, "graph_pairs_per_s": pairs_per_step / (ms_g / 1e3),
+            "single_rx_jobs_ms_per_step": ms_j,
+            "single_rx_jobs_spectra_per_s": n_rx / (ms_j / 1e3)}
+
+
+def uneven_leg(args, flush, max_records=1.5e8):
+    """Uneven serving stress: 256 requests over 8 scenes with Gaussian counts
+    log-uniform in [1e4, 1e6], 1-32 receivers each, 360 x 90, 2.4 or 5.2 GHz.  Requests
+    are rendered in waves bounded by receiver x Gaussian records (memory); a wave is the
+    projections and bins of its requests plus one persistent render of all of them; a
+    request's latency is its wave's time."""
+    import numpy as np
+    import torch
+
+    from paper_2502_01826_gb300 import _lib as L
+    from paper_2502_01826_gb300 import synthetic
+    from paper_2502_01826_gb300.render import BatchRender, Renderer, make_grid, received_signal, to_device
+
+    cfg = synthetic.config_uneven()
+    grid = make_grid(**cfg["grid"])
+    scenes = [to_device(sc) for sc in cfg["scenes"]]
+    Ks = [sc["means"].shape[0] for sc in cfg["scenes"]]
+    reqs = cfg["requests"]
+    waves, cur, load = [], [], 0.0
+    for i, q in enumerate(reqs):
+        rec = q["rx"].shape[0] * Ks[q["scene"]]
+        if cur and (load + rec > max_records or len(cur) == L.GSRF_MAX_BATCH_JOBS):
+            waves.append(cur)
+            cur, load = [], 0.0
+        cur.append(i)
+        load += rec
+    if cur:
+        waves.append(cur)
+    lat, pairs_total, t_total = [], 0, 0.0
+    for wv in waves:
+        jobs = []
+        for i in wv:
+            q = reqs[i]
+            R = Renderer(Ks[q["scene"]], q["rx"].shape[0], grid, q["f0"], pair_capacity=1024)
+            rx = torch.tensor(q["rx"], device="cuda")
+            tx = torch.tensor(q["tx"], device="cuda")
+            R.ensure_capacity(scenes[q["scene"]], rx, tx)
+            jobs.append((R, scenes[q["scene"]], rx, tx))
+        B = BatchRender([j[0] for j in jobs])
+
+        def wave():
+            for R, p, rx, tx in jobs:
+                R.project(p, rx, tx)
+                R.bin()
+            for o in B.render():
+                received_signal(o, L.SIG_RSSI_DB)
+
+        wave()
+        ms = _time_steps(wave, 1, flush)
+        pairs = sum(int(j[0].status().stats[1]) for j in jobs)
+        lat += [ms] * len(wv)
+        pairs_total += pairs
+        t_total += ms / 1e3
+        del B, jobs
+        torch.cuda.empty_cache()
+    lat = np.array(lat)
+    return {"workload": cfg["name"], "requests": len(reqs), "waves": len(waves),
+            "receivers": int(sum(q["rx"].shape[0] for q in reqs)), "gaussian_counts": Ks,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "pairs_per_s": pairs_total / t_total, "total_s": t_total}
 
 
 def train_leg(args, ws, flush):
@@ -407,13 +549,14 @@ def train_leg(args, ws, flush):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--n-rx", type=int, default=64, help="receivers (64 = the BLE workload; fewer "
                     "only for small profiling runs)")
     ap.add_argument("--no-train", action="store_true", help="skip the forward+backward training leg")
+    ap.add_argument("--uneven", action="store_true", help="add the uneven serving-stress leg (slow setup)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

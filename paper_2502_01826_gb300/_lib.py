@@ -21,7 +21,9 @@ SIG_COMPLEX_SUM, SIG_RSSI_DB, SIG_POWER_SUM, SIG_SPECTRUM_MAG = 0, 1, 2, 3
 # every exported symbol of include/gsrf.h
 EXPORTS = ["gsrf_workspace_size", "gsrf_workspace_layout", "gsrf_ray_state_bytes", "gsrf_project",
            "gsrf_bin", "gsrf_render_fwd", "gsrf_render_bwd", "gsrf_render", "gsrf_received_signal",
-           "gsrf_read_status", "gsrf_render_static", "gsrf_version"]
+           "gsrf_read_status", "gsrf_render_static", "gsrf_batch_workspace_size", "gsrf_render_batch",
+           "gsrf_version"]
+GSRF_MAX_BATCH_JOBS = 96
 
 
 class GsrfError(RuntimeError):
@@ -89,6 +91,8 @@ def load(build_if_missing: bool = False):
     L.gsrf_received_signal.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, vp]
     L.gsrf_read_status.argtypes = [vp, sz, P(gsrf_run_status), vp]
     L.gsrf_render_static.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, vp, vp, P(gsrf_run_status), vp]
+    L.gsrf_batch_workspace_size.argtypes = [C.c_int32, P(gsrf_plan), P(C.c_size_t)]
+    L.gsrf_render_batch.argtypes = [C.c_int32, P(gsrf_plan), P(vp), P(C.c_size_t), P(vp), vp, sz, vp]
     L.gsrf_version.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("gsrf_ray_state_bytes", "gsrf_version"):

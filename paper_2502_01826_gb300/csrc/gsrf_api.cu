@@ -189,6 +189,32 @@ gsrf_status gsrf_render(const gsrf_plan* plan, const gsrf_gaussians* g, const fl
     return gsrf_render_fwd(plan, g, workspace, ws_bytes, out_rays, ray_state, stream);
 }
 
+gsrf_status gsrf_batch_workspace_size(int32_t n_jobs, const gsrf_plan* plans, size_t* bytes) {
+    if (n_jobs < 1 || n_jobs > GSRF_MAX_BATCH_JOBS || !plans || !bytes) return GSRF_ERR_INVALID_ARG;
+    for (int j = 0; j < n_jobs; ++j) {
+        gsrf_status s = check_plan(&plans[j]);
+        if (s != GSRF_OK) return s;
+        if (plans[j].n_f != 1) return GSRF_ERR_UNSUPPORTED;
+    }
+    *bytes = batch_workspace_bytes(n_jobs, plans);
+    return GSRF_OK;
+}
+
+gsrf_status gsrf_render_batch(int32_t n_jobs, const gsrf_plan* plans, void* const* workspaces, const size_t* ws_bytes,
+                              float* const* outs, void* batch_ws, size_t batch_ws_bytes, void* stream) {
+    size_t need = 0;
+    gsrf_status s = gsrf_batch_workspace_size(n_jobs, plans, &need);
+    if (s != GSRF_OK) return s;
+    if (!workspaces || !ws_bytes || !outs || !batch_ws || ((uintptr_t)batch_ws & 255) != 0 || batch_ws_bytes < need)
+        return GSRF_ERR_INVALID_ARG;
+    for (int j = 0; j < n_jobs; ++j) {
+        Layout L;
+        if ((s = check_ws(&plans[j], workspaces[j], ws_bytes[j], &L)) != GSRF_OK) return s;
+        if (!outs[j] || ((uintptr_t)outs[j] & 7) != 0) return GSRF_ERR_INVALID_ARG;
+    }
+    return cuda_status(launch_render_batch(n_jobs, plans, workspaces, outs, batch_ws, (cudaStream_t)stream));
+}
+
 gsrf_status gsrf_received_signal(const float* rays, int32_t n_rx, int32_t n_f, int32_t n_el, int32_t n_az,
                                  int32_t mode, float* out, void* stream) {
     if (!rays || !out || n_rx < 1 || n_f < 1 || n_el < 1 || n_az < 1 || mode < 0 || mode > 3)

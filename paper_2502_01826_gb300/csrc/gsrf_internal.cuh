@@ -170,6 +170,12 @@ cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
                               void* ws, float* out, void* ray_state, cudaStream_t st);
 cudaError_t launch_signal(const float* rays, int n_rx, int n_f, int n_el, int n_az, int mode,
                           float* out, cudaStream_t st);
+cudaError_t launch_sort_small_keys(const uint32_t* keys, uint32_t* keys_out, uint32_t* vals_out, long long n,
+                                   int nbins, uint32_t* hist, cudaStream_t st);
+// Persistent batched render of n_jobs projected and binned problems (n_f == 1 each).
+size_t batch_workspace_bytes(int n_jobs, const gsrf_plan* plans);
+cudaError_t launch_render_batch(int n_jobs, const gsrf_plan* plans, void* const* workspaces, float* const* outs,
+                                void* batch_ws, cudaStream_t st);
 cudaError_t launch_render_bwd(const gsrf_plan* p, const Layout& L, const gsrf_gaussians* g, void* ws,
                               const void* ray_state, const float* grad_rays, float* g_means, float* g_log_scales,
                               float* g_quats, float* g_opacity_logit, float* g_coeffs, float* g_phase_b,
@@ -192,6 +198,19 @@ namespace gsrf {
 // D.3 quadratic with A = |v'|^2, B = w.v', C = |w|^2); the chord's exit
 // t_out = t_mid + h >= r_rx with t_mid = -B/A, h = sqrt((9 - m2)/A).
 // ---------------------------------------------------------------------------
+// Single hardware instructions (no compiler choice of sequence), so that the forward and
+// the backward take the same value.
+__device__ __forceinline__ float rcp_hw(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_hw(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 struct PairGeo {
     float vx, vy, vz;  // v' = W v
     float A, iA, m2, tm, h, t_out, t_a, dt, dl, m2r;
@@ -215,11 +234,11 @@ __device__ __forceinline__ bool pair_hits(const float4& v1, const float4& s0, co
     const float cz = __fsub_rn(__fmul_rn(v1.x, g.vy), __fmul_rn(v1.y, g.vx));
     const float m2A = __fmaf_rn(cz, cz, __fmaf_rn(cy, cy, __fmul_rn(cx, cx)));
     if (m2A >= __fmul_rn(9.0f, g.A)) return false;
-    g.iA = __frcp_rn(g.A);
+    g.iA = rcp_hw(g.A);
     g.m2 = __fmul_rn(m2A, g.iA);
     const float B = __fmaf_rn(v1.z, g.vz, __fmaf_rn(v1.y, g.vy, __fmul_rn(v1.x, g.vx)));
     g.tm = -__fmul_rn(B, g.iA);
-    g.h = __fsqrt_rn(fmaxf(__fmul_rn(__fsub_rn(9.0f, g.m2), g.iA), 0.0f));
+    g.h = sqrt_hw(fmaxf(__fmul_rn(__fsub_rn(9.0f, g.m2), g.iA), 0.0f));
     g.t_out = __fadd_rn(g.tm, g.h);
     if (g.t_out < r_rx) return false;
     g.t_a = fmaxf(__fsub_rn(g.tm, g.h), r_rx);

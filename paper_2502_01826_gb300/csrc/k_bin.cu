@@ -351,6 +351,20 @@ __global__ void k_zero_tile_start(uint32_t* ts, size_t n) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) ts[i] = 0;
 }
 
+// One stable counting pass over n 32-bit keys (digit = key & (nbins - 1), nbins <= 256):
+// vals_out gets the item indices in key order.  hist needs ceil(n / kChunk) * nbins words.
+cudaError_t launch_sort_small_keys(const uint32_t* keys, uint32_t* keys_out, uint32_t* vals_out, long long n,
+                                   int nbins, uint32_t* hist, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const int chunks = (int)((n + kChunk - 1) / kChunk);
+    Segs sg{1, n, chunks, nullptr, nullptr};
+    k_hist<uint32_t><<<chunks, kSortThreads, 0, st>>>(keys, sg, 0, (uint32_t)(nbins - 1), nbins, hist, nullptr);
+    k_scan<<<1, kSortThreads, 0, st>>>(sg, nbins, hist, nullptr, nullptr);
+    k_scatter<uint32_t><<<chunks, kSortThreads, 0, st>>>(keys, nullptr, keys_out, vals_out, sg, 0,
+                                                          (uint32_t)(nbins - 1), nbins, hist, nullptr);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream_t st) {
     DevStatus* status = at<DevStatus>(ws, L.status);
     const size_t nts = (size_t)L.n_rx * (L.n_tiles + 1);

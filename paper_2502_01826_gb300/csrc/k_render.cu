@@ -49,6 +49,16 @@ struct RenderArgs {
     float dlt;    // 2 pi df / c: subcarrier phase step per metre of excess path
 };
 
+constexpr int kMaxJobs = 96;
+
+// Up to kMaxJobs render problems (one receiver group of one scene each) passed by value
+// to the persistent kernel; item_base[j] is the first work item of job j.
+struct BatchArgs {
+    int n_jobs;
+    unsigned long long item_base[kMaxJobs + 1];
+    RenderArgs jobs[kMaxJobs];
+};
+
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
@@ -132,21 +142,22 @@ __device__ __forceinline__ bool bundle_meets(const Bundle& b, float4 c) {
     return cd >= b.cb * sqrtf(D2 - c.w) - b.sb * sqrtf(c.w) - 1e-4f * D;
 }
 
-// NFC = 1: one frequency.  NFC > 1: thread handles subcarriers s0 .. s0 + NFC - 1 of the
-// grid's z-th chunk; the contribution of a pair at f0 + s df is z0 r^s with
+// One warp renders the 8 x 4 block wq (0..7) of rays of tile `tile` for receiver r: it
+// walks the tile's list in batches of 32 candidates staged into its own buffers
+// (sbuf, sid), without waiting for any other warp.
+//
+// NFC = 1: one frequency.  NFC > 1: the lanes handle subcarriers s0 .. s0 + NFC - 1
+// (s0 = chunk * NFC); the contribution of a pair at f0 + s df is z0 r^s with
 // r = e^{-j (2 pi df d / c + 2 pi df Gamma / c)}, Gamma = sum over earlier pairs of b dt,
 // because T(f0 + s df) = T(f0) e^{-j s 2 pi df Gamma / c} and E(f0 + s df) =
 // E(f0) e^{-j s 2 pi df d / c}; the powers of r come from one sincos and a recurrence.
 template <int NFC>
-__global__ void __launch_bounds__(kThreads, NFC == 1 ? 8 : 4) k_render_fwd(RenderArgs a) {
-    __shared__ float4 sbuf[kWarps][2][kWB][kRec];
-    __shared__ uint32_t sid[kWarps][2][kWB];
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.x >> 1, half = blockIdx.x & 1, r = blockIdx.y;
+__device__ __forceinline__ void render_block(const RenderArgs& a, int r, int tile, int wq, int chunk,
+                                             float4 (*sbuf)[kWB][kRec], uint32_t (*sid)[kWB]) {
+    const int lane = threadIdx.x & 31;
     const int tu = tile % a.ntu, tv = tile / a.ntu;
-    int lx, ly;
-    cta_ray(threadIdx.x, half, lx, ly);
+    const int lx = ((wq & 1) << 3) | (lane & 7);
+    const int ly = ((wq >> 1) << 2) | (lane >> 3);
     const int u = tu * kTile + lx, v = tv * kTile + ly;
     const gsrf_grid& gr = a.gr;
     const bool valid = u < gr.n_az && v < gr.n_el;
@@ -168,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, NFC == 1 ? 8 : 4) k_render_fwd(Rende
 #pragma unroll
     for (int i = 0; i < 2 * NFC; ++i) Sf[i] = 0.0f;
     float Gam = 0.0f;
-    const int s0 = (int)blockIdx.z * NFC;
+    const int s0 = chunk * NFC;
     int last = -1;
     bool done = !valid;
     unsigned tests = 0, hits = 0;
@@ -184,9 +195,9 @@ __global__ void __launch_bounds__(kThreads, NFC == 1 ? 8 : 4) k_render_fwd(Rende
             const float4 c = __ldg(vw);
             keep = bundle_meets(bun, c);
             if (keep) {
-                sid[warp][bf][lane] = id;
+                sid[bf][lane] = id;
                 const float4* sh = reinterpret_cast<const float4*>(a.shape + id);
-                float4* dst = sbuf[warp][bf][lane];
+                float4* dst = sbuf[bf][lane];
                 dst[0] = c;
                 cp_async16(dst + 1, vw + 1);
                 cp_async16(dst + 2, vw + 2);
@@ -212,7 +223,7 @@ __global__ void __launch_bounds__(kThreads, NFC == 1 ? 8 : 4) k_render_fwd(Rende
                 int stop = cnt;
                 for (uint32_t m = mask; m; m &= m - 1) {
                     const int j = __ffs(m) - 1;
-                    const float4* rec = sbuf[warp][bf][j];
+                    const float4* rec = sbuf[bf][j];
                     if (!pair_sphere(rec[0], dx, dy, dz)) continue;
                     const float4 v1 = rec[1], s2 = rec[5];
                     PairGeo pg;
@@ -220,7 +231,7 @@ __global__ void __launch_bounds__(kThreads, NFC == 1 ? 8 : 4) k_render_fwd(Rende
                     float gw;
                     const float alpha = pair_alpha(s2.y, pg.m2r, amax, gw);
                     float pr, pi;
-                    fle_psi(reinterpret_cast<const float4*>(a.fle + (size_t)sid[warp][bf][j] * kFle), P, Y, pr, pi);
+                    fle_psi(reinterpret_cast<const float4*>(a.fle + (size_t)sid[bf][j] * kFle), P, Y, pr, pi);
                     // S += alpha psi E T, E = e^{-j phi} = (er, ei)
                     const float er = v1.w, ei = rec[2].x;
                     const float etr = er * Tr - ei * Ti, eti = er * Ti + ei * Tr;
@@ -281,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, NFC == 1 ? 8 : 4) k_render_fwd(Rende
             for (int q = 0; q < NFC; ++q)
                 if (s0 + q < a.n_f) o2[(size_t)q * plane] = make_float2(Sf[2 * q], Sf[2 * q + 1]);
         }
-        if (a.rs && blockIdx.z == 0) {
+        if (a.rs && chunk == 0) {
             RayState s;
             s.last = last;
             s.Ta = Ta;
@@ -297,14 +308,64 @@ __global__ void __launch_bounds__(kThreads, NFC == 1 ? 8 : 4) k_render_fwd(Rende
         t64 += __shfl_down_sync(0xffffffffu, t64, o);
         h64 += __shfl_down_sync(0xffffffffu, h64, o);
     }
-    if (lane == 0 && blockIdx.z == 0) {
+    if (lane == 0 && chunk == 0) {
         atomicAdd(&a.st->stats[0], t64);
         atomicAdd(&a.st->stats[1], h64);
     }
 }
 
-cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_gaussians* g, void* ws,
-                              float* out, void* ray_state, cudaStream_t st) {
+// Plain launch: CTA = (half tile, receiver, subcarrier chunk), 4 warps = 4 ray blocks.
+template <int NFC>
+__global__ void __launch_bounds__(kThreads, NFC == 1 ? 8 : 4) k_render_fwd(RenderArgs a) {
+    __shared__ float4 sbuf[kWarps][2][kWB][kRec];
+    __shared__ uint32_t sid[kWarps][2][kWB];
+    const int warp = threadIdx.x >> 5;
+    render_block<NFC>(a, blockIdx.y, blockIdx.x >> 1, (blockIdx.x & 1) * kWarps + warp, blockIdx.z, sbuf[warp],
+                      sid[warp]);
+}
+
+// Persistent batched launch: every warp takes work items -- (job, receiver, tile, ray
+// block) -- from one counter, in the heaviest-first order the item sort produced, until
+// none is left.  No warp waits for another.
+__global__ void __launch_bounds__(kThreads, 8) k_render_batch(BatchArgs b, const uint32_t* __restrict__ order,
+                                                              unsigned long long* __restrict__ counter) {
+    __shared__ float4 sbuf[kWarps][2][kWB][kRec];
+    __shared__ uint32_t sid[kWarps][2][kWB];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned long long total = b.item_base[b.n_jobs];
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1ull);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= total) break;
+        const unsigned long long id = order[it];
+        int j = 0;
+        while (j + 1 < b.n_jobs && b.item_base[j + 1] <= id) ++j;
+        const RenderArgs& a = b.jobs[j];
+        const unsigned long long local = id - b.item_base[j];
+        const int per_rx = a.n_tiles * 8;
+        const int r = (int)(local / per_rx), rem = (int)(local % per_rx);
+        render_block<1>(a, r, rem >> 3, rem & 7, 0, sbuf[warp], sid[warp]);
+    }
+}
+
+// Cost key of every work item: its tile's list length, heaviest first (bucket
+// 31 - floor(log2(len + 1)), so that an ascending stable sort puts long lists first).
+__global__ void k_batch_keys(BatchArgs b, uint32_t* __restrict__ keys) {
+    const unsigned long long id = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= b.item_base[b.n_jobs]) return;
+    int j = 0;
+    while (j + 1 < b.n_jobs && b.item_base[j + 1] <= id) ++j;
+    const RenderArgs& a = b.jobs[j];
+    const unsigned long long local = id - b.item_base[j];
+    const int per_rx = a.n_tiles * 8;
+    const int r = (int)(local / per_rx), tile = (int)(local % per_rx) >> 3;
+    const size_t ts = (size_t)r * (a.n_tiles + 1) + tile;
+    const uint32_t len = a.tile_start[ts + 1] - a.tile_start[ts];
+    keys[id] = 31u - (31u - (uint32_t)__clz((int)(len + 1u)));
+}
+
+static RenderArgs render_args(const gsrf_plan* p, const Layout& L, void* ws, float* out, void* ray_state) {
     RenderArgs a;
     a.shape = at<GShape>(ws, L.gshape);
     a.view = at<View>(ws, L.view);
@@ -324,6 +385,12 @@ cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     a.om_pi = (float)(2.0 * p->f0_hz / kC);
     a.n_f = p->n_f;
     a.dlt = (float)(2.0 * 3.14159265358979323846 * p->df_hz / kC);
+    return a;
+}
+
+cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_gaussians* g, void* ws,
+                              float* out, void* ray_state, cudaStream_t st) {
+    RenderArgs a = render_args(p, L, ws, out, ray_state);
     (void)g;
     cudaError_t e = cudaMemsetAsync(&a.st->stats[0], 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
@@ -334,6 +401,70 @@ cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     } else {
         k_render_fwd<16><<<dim3(2 * L.n_tiles, L.n_rx, (p->n_f + 15) / 16), kThreads, 0, st>>>(a);
     }
+    return cudaGetLastError();
+}
+
+}  // namespace gsrf
+
+namespace gsrf {
+
+static long long batch_items(int n_jobs, const gsrf_plan* plans) {
+    long long t = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        Layout L;
+        make_layout(&plans[j], &L);
+        t += (long long)L.n_rx * L.n_tiles * 8;
+    }
+    return t;
+}
+
+// batch workspace: keys, sorted keys, order, histogram, counter
+size_t batch_workspace_bytes(int n_jobs, const gsrf_plan* plans) {
+    const long long n = batch_items(n_jobs, plans);
+    const long long chunks = (n + kChunk - 1) / kChunk;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    return al(n * 4) * 3 + al(chunks * 32 * 4) + al(8);
+}
+
+cudaError_t launch_render_batch(int n_jobs, const gsrf_plan* plans, void* const* workspaces, float* const* outs,
+                                void* batch_ws, cudaStream_t st) {
+    BatchArgs b;
+    b.n_jobs = n_jobs;
+    unsigned long long base = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        Layout L;
+        make_layout(&plans[j], &L);
+        b.jobs[j] = render_args(&plans[j], L, workspaces[j], outs[j], nullptr);
+        b.item_base[j] = base;
+        base += (unsigned long long)L.n_rx * L.n_tiles * 8;
+        cudaError_t e = cudaMemsetAsync(&b.jobs[j].st->stats[0], 0, 2 * sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return e;
+    }
+    b.item_base[n_jobs] = base;
+    const long long n = (long long)base;
+    const long long chunks = (n + kChunk - 1) / kChunk;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    char* w = static_cast<char*>(batch_ws);
+    uint32_t* keys = reinterpret_cast<uint32_t*>(w);
+    uint32_t* keys2 = reinterpret_cast<uint32_t*>(w + al(n * 4));
+    uint32_t* order = reinterpret_cast<uint32_t*>(w + 2 * al(n * 4));
+    uint32_t* hist = reinterpret_cast<uint32_t*>(w + 3 * al(n * 4));
+    unsigned long long* counter = reinterpret_cast<unsigned long long*>(w + 3 * al(n * 4) + al(chunks * 32 * 4));
+    if (n == 0) return cudaSuccess;
+    k_batch_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(b, keys);
+    cudaError_t e = launch_sort_small_keys(keys, keys2, order, n, 32, hist, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    // one resident wave: every SM holds as many CTAs as it can run at once
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_batch, kThreads, 0)) != cudaSuccess)
+        return e;
+    const long long ctas_needed = (n + kWarps - 1) / kWarps;
+    const int grid = (int)min((long long)sms * max(per_sm, 1), ctas_needed);
+    k_render_batch<<<grid, kThreads, 0, st>>>(b, order, counter);
     return cudaGetLastError();
 }
 

@@ -175,6 +175,34 @@ class Renderer:
         return keys, ids, rb, ts
 
 
+class BatchRender:
+    """Many render problems (each a Renderer that has run project and bin) rendered by one
+    persistent kernel launch, work items heaviest first (gsrf_render_batch)."""
+
+    def __init__(self, renderers: list):
+        if not 1 <= len(renderers) <= L.GSRF_MAX_BATCH_JOBS:
+            raise ValueError("1..%d jobs per batch" % L.GSRF_MAX_BATCH_JOBS)
+        self.renderers = list(renderers)
+        n = len(self.renderers)
+        self.plans = (L.gsrf_plan * n)(*[r.plan for r in self.renderers])
+        nbytes = C.c_size_t()
+        L.call("gsrf_batch_workspace_size", n, self.plans, C.byref(nbytes))
+        self.ws_bytes = nbytes.value
+        dev = self.renderers[0].device
+        self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
+        self.outs = [torch.empty(r.out_shape(), dtype=torch.float32, device=dev) for r in self.renderers]
+
+    def render(self, stream=None):
+        n = len(self.renderers)
+        for i, r in enumerate(self.renderers):  # plans may have grown their capacity
+            self.plans[i] = r.plan
+        wss = (C.c_void_p * n)(*[r.ws.data_ptr() for r in self.renderers])
+        wsb = (C.c_size_t * n)(*[r.ws_bytes for r in self.renderers])
+        outs = (C.c_void_p * n)(*[o.data_ptr() for o in self.outs])
+        L.call("gsrf_render_batch", n, self.plans, wss, wsb, outs, _ptr(self.ws), self.ws_bytes, _stream(stream))
+        return self.outs
+
+
 def received_signal(rays: torch.Tensor, mode: int = L.SIG_COMPLEX_SUM, stream=None) -> torch.Tensor:
     """rays [n_rx, n_f, n_el, n_az, 2] -> per mode (see include/gsrf.h)."""
     if not (rays.is_cuda and rays.dtype == torch.float32 and rays.is_contiguous() and rays.dim() == 5):
