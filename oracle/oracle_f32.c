@@ -12,14 +12,22 @@
  *
  * Coverage rule (a conservative reading of the paper's splatting, written out in the
  * design notes): the 3-sigma ellipsoid lies inside the sphere of radius
- * 3 * max(scale) about mu; the sphere radius is inflated by 1% (Rc = 3.03 max s) and
- * a tile is covered when the centre of at least one of its ray bins lies inside the
- * angular bounding box of that sphere seen from the receiver:
- *   elevation  el_c +- asin(Rc / D),        el_c = asin(cz / D)
- *   azimuth    az_c +- asin(Rc / rho),      az_c = atan2(cy, cx), rho = |(cx, cy)|
- * with every azimuth when rho <= Rc (the sphere meets the vertical through r),
- * every tile when D <= Rc, and no tile when D + Rc < r_rx (the sphere lies inside
- * the ray-emitting sphere).  exp, atan2 and asin are evaluated by the short
+ * 3 * max(scale) about mu; the sphere radius is inflated by 1% (Rc = 3.03 max s).  A
+ * ray starts on the emitting sphere |x - r| = r_rx (App. A.2), so only directions
+ * whose ray meets that sphere of radius Rc beyond r_rx matter.  They form a cone about
+ * c = mu - r (D = |c|) whose half-angle theta has D sin(theta) = Rs:
+ *   Rs = Rc            when r_e^2 <= D^2 - Rc^2 (the tangent points lie beyond r_e);
+ *   cos(theta) = (D^2 + r_e^2 - Rc^2) / (2 D r_e) otherwise (the rim of the part of
+ *                      the sphere beyond r_e, by the law of cosines), and every
+ *                      direction when that numerator is <= 0;
+ * with r_e = 0.999 r_rx (a margin for the FP32 exit distance of the hit test).  A tile
+ * is covered when the centre of at least one of its ray bins lies inside the angular
+ * bounding box of that cone:
+ *   elevation  el_c +- asin(Rs / D),        el_c = asin(cz / D)
+ *   azimuth    az_c +- asin(Rs / rho),      az_c = atan2(cy, cx), rho = |(cx, cy)|
+ * with every azimuth when rho <= Rs (the cone holds the vertical), every tile when
+ * the cone is a hemisphere or wider, and no tile when D + Rc < r_rx (the sphere lies
+ * inside the ray-emitting sphere).  exp, atan2 and asin are evaluated by the short
  * formulas below (textbook series after exact argument reduction), not by libm,
  * so that both sides round identically.
  */
@@ -125,7 +133,24 @@ int32_t or_cover_f32(const float *mu, const float *log_scale, const float *r, co
     *tv_lo_out = 1;
     *tv_hi_out = 0;
     if (D + Rc < g->r_rx) return 0;
-    if (D <= Rc) {
+    /* the cone of directions that meet the sphere beyond r_e */
+    float Rs = Rc;
+    int all = D <= Rc;
+    float re = g->r_rx * 0.999f;
+    if (re > 0.0f) {
+        float re2 = re * re;
+        float a = d2 - Rc * Rc;
+        if (re2 > a) {
+            float num = a + re2;
+            if (num > 0.0f) {
+                float cm = num / ((2.0f * D) * re);
+                if (cm > 1.0f) cm = 1.0f;
+                Rs = D * sqrtf((1.0f - cm) * (1.0f + cm));
+                all = 0;
+            }
+        }
+    }
+    if (all) {
         *mask_out = all_u;
         *tv_lo_out = 0;
         *tv_hi_out = ntv - 1;
@@ -134,7 +159,7 @@ int32_t or_cover_f32(const float *mu, const float *log_scale, const float *r, co
 
     /* elevation bins whose centre lies in [el_c - d, el_c + d] */
     float elc = det_asin(cz / D) * RAD2DEG_F;
-    float eld = det_asin(Rc / D) * RAD2DEG_F;
+    float eld = det_asin(Rs / D) * RAD2DEG_F;
     float vlo = ceilf((elc - eld - g->el0_deg) / g->del_deg - 0.5f);
     float vhi = floorf((elc + eld - g->el0_deg) / g->del_deg - 0.5f);
     if (vlo < 0.0f) vlo = 0.0f;
@@ -144,11 +169,11 @@ int32_t or_cover_f32(const float *mu, const float *log_scale, const float *r, co
 
     uint64_t mask = 0;
     float rho = sqrtf(rho2);
-    if (rho <= Rc) {
+    if (rho <= Rs) {
         mask = all_u;
     } else {
         float azc = det_atan2(cy, cx) * RAD2DEG_F;
-        float azd = det_asin(Rc / rho) * RAD2DEG_F;
+        float azd = det_asin(Rs / rho) * RAD2DEG_F;
         float rel = azc - g->az0_deg;
         if (rel < 0.0f) rel = rel + 360.0f;
         if (rel < 0.0f) rel = rel + 360.0f;

@@ -20,22 +20,22 @@ constexpr int kMaxTiles = 1024;       // bins of the tile counting sort
 constexpr int kMaxNf = 64;
 
 // Per-Gaussian shape record: whitening matrix W = diag(1/s) R^T (so that
-// (x-mu)^T Sigma^-1 (x-mu) = |W (x-mu)|^2), opacity, excess-phase coefficient, and the
-// squared radius of a bounding sphere of the 3-sigma ellipsoid.
+// (x-mu)^T Sigma^-1 (x-mu) = |W (x-mu)|^2), opacity and excess-phase coefficient.
 struct __align__(16) GShape {
     float W[9];
     float o;
     float b;
-    float rc2;
+    float pad;
 };
 
-// Per-(receiver, Gaussian) view record: offset c = mu - r and the squared radius of
-// the Gaussian's bounding sphere (the render's pre-test), whitened receiver offset
+// Per-(receiver, Gaussian) view record: offset c = mu - r and D cos(theta) of the cone
+// of directions that can meet the Gaussian's bounding sphere beyond the emitting sphere
+// (the render's pre-test; negative when every direction can), whitened receiver offset
 // w = W (r - mu), path phasor e^{-j 2 pi f0 d / c} and the per-subcarrier phase step
 // 2 pi df d / c.
 struct __align__(16) View {
     float c[3];
-    float rc2;
+    float ccos;
     float w[3];
     float er;
     float ei;
@@ -191,9 +191,12 @@ namespace gsrf {
 // feeds a decision is an explicit round-to-nearest intrinsic, so the compiler cannot
 // contract it differently in the two kernels.
 //
-// Records (6 float4): v0 = (c = mu - r, rc^2), v1 = (w = W (r - mu), er),
+// Records (6 float4): v0 = (c = mu - r, D cos theta), v1 = (w = W (r - mu), er),
 // v2 = (ei, omd, -, -), s0 = W0..W3, s1 = W4..W7, s2 = (W8, o, b, -).
-// Tests, in order: the bounding sphere |c x v|^2 < rc^2; the 3-sigma ellipsoid in
+// Tests, in order: the direction cone c.v >= D cos(theta) (theta: half-angle of the
+// cone of directions that meet the bounding sphere beyond the emitting sphere, set by
+// the projection with margins far above FP32 rounding, so it never rejects a pair the
+// next two tests accept); the 3-sigma ellipsoid in
 // whitened coordinates, m2 A = |w x v'|^2 < 9 A (v' = W v, Lagrange's identity, App.
 // D.3 quadratic with A = |v'|^2, B = w.v', C = |w|^2); the chord's exit
 // t_out = t_mid + h >= r_rx with t_mid = -B/A, h = sqrt((9 - m2)/A).
@@ -211,16 +214,53 @@ __device__ __forceinline__ float sqrt_hw(float x) {
     return r;
 }
 
+// Cone of a warp's rays: unit axis b and cos / sin of the half-angle beta that holds
+// all of them (with a small angular margin).
+struct Bundle {
+    float bx, by, bz, cb, sb;
+};
+
+__device__ __forceinline__ Bundle warp_bundle(bool valid, float dx, float dy, float dz) {
+    float sx = valid ? dx : 0.0f, sy = valid ? dy : 0.0f, sz = valid ? dz : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    }
+    const float in = rsqrtf(fmaxf(sx * sx + sy * sy + sz * sz, 1e-30f));
+    Bundle b;
+    b.bx = sx * in;
+    b.by = sy * in;
+    b.bz = sz * in;
+    float c = valid ? dx * b.bx + dy * b.by + dz * b.bz : 1.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c = fminf(c, __shfl_xor_sync(0xffffffffu, c, o));
+    c = fmaxf(fminf(c, 1.0f), -1.0f) - 2e-5f;  // margin for rounding of the axis and rays
+    b.cb = c;
+    b.sb = sqrtf(fmaxf(1.0f - c * c, 0.0f));
+    return b;
+}
+
+// Can a ray of the bundle lie in the record's direction cone (axis c = mu - r, half-angle
+// theta, c.w = D cos(theta))?  Only if angle(b, c) <= beta + theta, i.e.
+// c.b >= D cos(beta + theta) = cos(beta) D cos(theta) - sin(beta) D sin(theta).  Every
+// ray may when either cone is a hemisphere or wider.
+__device__ __forceinline__ bool bundle_meets(const Bundle& b, float4 c) {
+    if (c.w < 0.0f || b.cb <= 0.0f) return true;
+    const float D2 = c.x * c.x + c.y * c.y + c.z * c.z;
+    const float dsn = sqrtf(fmaxf(D2 - c.w * c.w, 0.0f));  // D sin(theta)
+    const float cd = c.x * b.bx + c.y * b.by + c.z * b.bz;
+    return cd >= b.cb * c.w - b.sb * dsn - 1e-4f * (c.w + dsn);
+}
+
 struct PairGeo {
     float vx, vy, vz;  // v' = W v
     float A, iA, m2, tm, h, t_out, t_a, dt, dl, m2r;
 };
 
-__device__ __forceinline__ bool pair_sphere(const float4& v0, float dx, float dy, float dz) {
-    const float qx = __fsub_rn(__fmul_rn(v0.y, dz), __fmul_rn(v0.z, dy));
-    const float qy = __fsub_rn(__fmul_rn(v0.z, dx), __fmul_rn(v0.x, dz));
-    const float qz = __fsub_rn(__fmul_rn(v0.x, dy), __fmul_rn(v0.y, dx));
-    return __fmaf_rn(qz, qz, __fmaf_rn(qy, qy, __fmul_rn(qx, qx))) < v0.w;
+__device__ __forceinline__ bool pair_cone(const float4& v0, float dx, float dy, float dz) {
+    return __fmaf_rn(v0.z, dz, __fmaf_rn(v0.y, dy, __fmul_rn(v0.x, dx))) >= v0.w;
 }
 
 __device__ __forceinline__ bool pair_hits(const float4& v1, const float4& s0, const float4& s1, const float4& s2,

@@ -126,21 +126,7 @@ __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
         Gr = g2.x;
         Gi = g2.y;
     }
-    // the warp's cone (same construction as the forward)
-    float sx = valid ? dx : 0.0f, sy = valid ? dy : 0.0f, sz = valid ? dz : 0.0f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        sx += __shfl_xor_sync(0xffffffffu, sx, o);
-        sy += __shfl_xor_sync(0xffffffffu, sy, o);
-        sz += __shfl_xor_sync(0xffffffffu, sz, o);
-    }
-    const float inv = rsqrtf(fmaxf(sx * sx + sy * sy + sz * sz, 1e-30f));
-    const float bx = sx * inv, by = sy * inv, bz = sz * inv;
-    float cb = valid ? dx * bx + dy * by + dz * bz : 1.0f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cb = fminf(cb, __shfl_xor_sync(0xffffffffu, cb, o));
-    cb = fmaxf(fminf(cb, 1.0f), -1.0f) - 2e-5f;
-    const float sb = sqrtf(fmaxf(1.0f - cb * cb, 0.0f));
+    const Bundle bun = warp_bundle(valid, dx, dy, dz);  // the forward's warp cone
 
     // positions are inside the tile's list; a state that points past it (another plan's,
     // or garbage) is clamped so that no read leaves the list
@@ -166,13 +152,7 @@ __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
             const uint32_t id = a.pids[b0 + lane];
             const float4* vw = reinterpret_cast<const float4*>(view + id);
             const float4 c = __ldg(vw);
-            const float D2 = c.x * c.x + c.y * c.y + c.z * c.z;
-            if (D2 <= c.w) {
-                keep = true;
-            } else {
-                const float D = sqrtf(D2);
-                keep = c.x * bx + c.y * by + c.z * bz >= cb * sqrtf(D2 - c.w) - sb * sqrtf(c.w) - 1e-4f * D;
-            }
+            keep = bundle_meets(bun, c);
             if (keep) {
                 sid[warp][bf][lane] = id;
                 const float4* sh = reinterpret_cast<const float4*>(a.shape + id);
@@ -205,7 +185,7 @@ __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
             const float4* rec = sbuf[warp][bf][j];
             const float4 v0 = rec[0], v1 = rec[1], s0 = rec[3], s1 = rec[4], s2 = rec[5];
             PairGeo pg;
-            bool hit = pos <= last && pair_sphere(v0, dx, dy, dz) && pair_hits(v1, s0, s1, s2, dx, dy, dz, r_rx, pg);
+            bool hit = pos <= last && pair_cone(v0, dx, dy, dz) && pair_hits(v1, s0, s1, s2, dx, dy, dz, r_rx, pg);
             if (!__any_sync(0xffffffffu, hit)) continue;
             float gq[32], go[16];
 #pragma unroll

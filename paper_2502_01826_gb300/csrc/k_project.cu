@@ -57,10 +57,7 @@ __global__ void __launch_bounds__(256) k_prepare(gsrf_gaussians g, const float* 
         for (int j = 0; j < 3; ++j) out.W[3 * i + j] = R[3 * j + i] * is[i];
     out.o = 1.0f / (1.0f + expf(-ol));
     out.b = b;
-    // squared radius of a sphere about mu that holds the 3-sigma ellipsoid with a 1%
-    // margin (the render's cheap pre-test; FP32 rounding is far inside the margin)
-    const float rc = 3.03f * expf(fmaxf(fmaxf(l0, l1), l2));
-    out.rc2 = rc * rc;
+    out.pad = 0.0f;
     shape[k] = out;
     const double dx = (double)tx[0] - mx, dy = (double)tx[1] - my, dz = (double)tx[2] - mz;
     dpath_t[k] = sqrt(dx * dx + dy * dy + dz * dz);
@@ -114,20 +111,52 @@ __global__ void __launch_bounds__(256) k_raytab(gsrf_grid gr, float* __restrict_
 }
 
 // Tile coverage: the bins of the receiving plane whose centre lies in the angular
-// bounding box of the sphere of radius 3.03 max(s) about mu (it contains the 3-sigma
-// ellipsoid with a 1% margin), in deterministic FP32.
+// bounding box of the cone of directions along which a ray, after leaving the emitting
+// sphere |x - r| = r_rx (App. A.2), can still meet the sphere of radius
+// Rc = 3.03 max(s) about mu (it holds the 3-sigma ellipsoid with a 1% margin).  The cone
+// has axis c = mu - r and half-angle theta with Rs = D sin(theta) (D = |c|):
+//   Rs = Rc when the tangent points of the sphere lie beyond the emitting sphere
+//        (r_e^2 <= D^2 - Rc^2), the usual cone of a sphere;
+//   else the sphere's exit point must lie beyond r_e, and the rim of that cap is the
+//        circle where both spheres meet: cos(theta) = (D^2 + r_e^2 - Rc^2) / (2 D r_e)
+//        (law of cosines), every direction when that is <= 0;
+// with r_e = 0.999 r_rx, a margin for the FP32 exit distance of the hit test.  Nothing
+// is covered when D + Rc < r_rx.  Deterministic FP32 throughout: the oracle takes the
+// same sequence of correctly rounded operations.  Rs_out returns D sin(theta) and wide
+// whether theta reaches 90 degrees (every tile), for the render's direction pre-test.
 __device__ __forceinline__ Cover cover_of(float cx, float cy, float cz, float lsm, const gsrf_grid& gr,
-                                          int ntu, int ntv) {
+                                          int ntu, int ntv, float& D_out, float& Rs_out, bool& wide) {
     const unsigned long long all_u = ntu >= 64 ? ~0ull : ((1ull << ntu) - 1ull);
     Cover cv;
     cv.mask = 0ull;
     cv.tv = 1u;  // lo = 1 > hi = 0: empty
     cv.count = 0u;
     const float rho2 = dadd(dmul(cx, cx), dmul(cy, cy));
-    const float D = dsqrt(dadd(rho2, dmul(cz, cz)));
+    const float d2 = dadd(rho2, dmul(cz, cz));
+    const float D = dsqrt(d2);
     const float Rc = dmul(3.03f, det_exp(lsm));
+    D_out = D;
+    Rs_out = 0.0f;
+    wide = false;
     if (dadd(D, Rc) < gr.r_rx) return cv;
-    if (D <= Rc) {
+    float Rs = Rc;
+    bool all = D <= Rc;
+    const float re = dmul(gr.r_rx, 0.999f);
+    if (re > 0.0f) {
+        const float re2 = dmul(re, re);
+        const float a = dsub(d2, dmul(Rc, Rc));
+        if (re2 > a) {
+            const float num = dadd(a, re2);
+            if (num > 0.0f) {
+                const float cm = fminf(ddiv(num, dmul(dmul(2.0f, D), re)), 1.0f);
+                Rs = dmul(D, dsqrt(dmul(dsub(1.0f, cm), dadd(1.0f, cm))));
+                all = false;
+            }
+        }
+    }
+    Rs_out = Rs;
+    if (all) {
+        wide = true;
         cv.mask = all_u;
         cv.tv = (uint32_t)(ntv - 1) << 16;
         cv.count = (uint32_t)(ntu * ntv);
@@ -135,7 +164,7 @@ __device__ __forceinline__ Cover cover_of(float cx, float cy, float cz, float ls
     }
     const float rad2deg = 57.2957795f;
     const float elc = dmul(det_asin(ddiv(cz, D)), rad2deg);
-    const float eld = dmul(det_asin(ddiv(Rc, D)), rad2deg);
+    const float eld = dmul(det_asin(ddiv(Rs, D)), rad2deg);
     float vlo = ceilf(dsub(ddiv(dsub(dsub(elc, eld), gr.el0_deg), gr.del_deg), 0.5f));
     float vhi = floorf(dsub(ddiv(dsub(dadd(elc, eld), gr.el0_deg), gr.del_deg), 0.5f));
     vlo = fmaxf(vlo, 0.0f);
@@ -144,11 +173,11 @@ __device__ __forceinline__ Cover cover_of(float cx, float cy, float cz, float ls
     const int tv_lo = (int)vlo / gr.tile_h, tv_hi = (int)vhi / gr.tile_h;
     unsigned long long mask = 0ull;
     const float rho = dsqrt(rho2);
-    if (rho <= Rc) {
+    if (rho <= Rs) {
         mask = all_u;
     } else {
         const float azc = dmul(det_atan2(cy, cx), rad2deg);
-        const float azd = dmul(det_asin(ddiv(Rc, rho)), rad2deg);
+        const float azd = dmul(det_asin(ddiv(Rs, rho)), rad2deg);
         float rel = dsub(azc, gr.az0_deg);
         if (rel < 0.0f) rel = dadd(rel, 360.0f);
         if (rel < 0.0f) rel = dadd(rel, 360.0f);
@@ -205,7 +234,6 @@ __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __r
     v.c[0] = -ux;
     v.c[1] = -uy;
     v.c[2] = -uz;
-    v.rc2 = sh.rc2;
     v.w[0] = sh.W[0] * ux + sh.W[1] * uy + sh.W[2] * uz;
     v.w[1] = sh.W[3] * ux + sh.W[4] * uy + sh.W[5] * uz;
     v.w[2] = sh.W[6] * ux + sh.W[7] * uy + sh.W[8] * uz;
@@ -214,7 +242,12 @@ __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __r
     const float D = dsqrt(dadd(dadd(dmul(cx, cx), dmul(cy, cy)), dmul(cz, cz)));
     dkey[o] = __float_as_uint(D);
     const float lsm = fmaxf(fmaxf(g.log_scales[3 * k], g.log_scales[3 * k + 1]), g.log_scales[3 * k + 2]);
-    cover[o] = cover_of(cx, cy, cz, lsm, gr, ntu, ntv);
+    float D_c, Rs;
+    bool wide;
+    cover[o] = cover_of(cx, cy, cz, lsm, gr, ntu, ntv, D_c, Rs, wide);
+    // direction pre-test of the render: D cos(theta) of the cover's cone less a rounding
+    // margin; below -D (every direction passes) when the cone is a hemisphere or wider
+    v.ccos = wide ? -1.0f - D_c : sqrtf(fmaxf(D_c * D_c - Rs * Rs, 0.0f)) - 2e-6f * D_c;
     // path phase: d = |t - mu| + |mu - r| and d f0 / c reduced to [0, 1) in FP64
     const double ex = (double)mx - rx, ey = (double)my - ry, ez = (double)mz - rz;
     const double d = dpath_t[k] + sqrt(ex * ex + ey * ey + ez * ez);

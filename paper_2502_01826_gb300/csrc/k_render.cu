@@ -4,14 +4,15 @@
 // Layout of the work: a CTA of 4 warps covers half of a 16x16 ray tile (16 x 8 rays),
 // each warp an 8 x 4 block of rays, one ray per thread.  Every warp walks its tile's
 // candidate list on its own, 32 candidates per batch: lane i takes candidate b0 + i,
-// tests its bounding sphere against the cone of the warp's 32 rays and, if it may be
+// tests its direction cone against the cone of the warp's 32 rays and, if it may be
 // hit, copies its records into the warp's half of a double buffer with cp.async while
 // the warp works on the current batch; the rays then visit only the candidates of the
 // ballot mask, in list order.  Warps never wait for one another and a warp leaves as
 // soon as its 32 rays have terminated (prod(1 - alpha) < eps_T).
 //
-// Per candidate and ray (pair_sphere / pair_hits, shared with the backward):
-//   (1) bounding sphere: the ray's line passes within rc of mu, |c x v|^2 < rc^2;
+// Per candidate and ray (pair_cone / pair_hits, shared with the backward):
+//   (1) direction cone: v lies in the cone of directions that meet the bounding sphere
+//       of the 3-sigma ellipsoid beyond the emitting sphere, c.v >= D cos(theta);
 //   (2) 3-sigma ellipsoid in whitened coordinates: with W = diag(1/s) R^T the ray
 //       r + t v maps to w + t v' (w = W (r - mu), v' = W v), so the paper's quadratic
 //       A t^2 + 2 B t + (C - 9) = 0 (App. D.3) has A = |v'|^2, B = w.v', C = |w|^2;
@@ -102,46 +103,6 @@ __device__ __forceinline__ void load_ray(const float* raytab, size_t ray, float&
     Y[10] = t5.x; Y[11] = t5.y;
 }
 
-// Cone of a warp's rays: unit axis b and cos / sin of the half-angle that holds all of
-// them (with a small angular margin).
-struct Bundle {
-    float bx, by, bz, cb, sb;
-};
-
-__device__ __forceinline__ Bundle warp_bundle(bool valid, float dx, float dy, float dz) {
-    float sx = valid ? dx : 0.0f, sy = valid ? dy : 0.0f, sz = valid ? dz : 0.0f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        sx += __shfl_xor_sync(0xffffffffu, sx, o);
-        sy += __shfl_xor_sync(0xffffffffu, sy, o);
-        sz += __shfl_xor_sync(0xffffffffu, sz, o);
-    }
-    const float in = rsqrtf(fmaxf(sx * sx + sy * sy + sz * sz, 1e-30f));
-    Bundle b;
-    b.bx = sx * in;
-    b.by = sy * in;
-    b.bz = sz * in;
-    float c = valid ? dx * b.bx + dy * b.by + dz * b.bz : 1.0f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c = fminf(c, __shfl_xor_sync(0xffffffffu, c, o));
-    c = fmaxf(fminf(c, 1.0f), -1.0f) - 2e-5f;  // margin for rounding of the axis and rays
-    b.cb = c;
-    b.sb = sqrtf(fmaxf(1.0f - c * c, 0.0f));
-    return b;
-}
-
-// Can the sphere (c = mu - r, squared radius rc2) meet any ray of the bundle?  If the
-// angle between b and c exceeds the bundle half-angle plus the sphere's half-angle
-// asin(rc/|c|), every ray of the bundle misses the sphere (triangle inequality on the
-// unit sphere), hence the ellipsoid inside it.
-__device__ __forceinline__ bool bundle_meets(const Bundle& b, float4 c) {
-    const float D2 = c.x * c.x + c.y * c.y + c.z * c.z;
-    if (D2 <= c.w) return true;
-    const float D = sqrtf(D2);
-    const float cd = c.x * b.bx + c.y * b.by + c.z * b.bz;
-    return cd >= b.cb * sqrtf(D2 - c.w) - b.sb * sqrtf(c.w) - 1e-4f * D;
-}
-
 // One warp renders the 8 x 4 block wq (0..7) of rays of tile `tile` for receiver r: it
 // walks the tile's list in batches of 32 candidates staged into its own buffers
 // (sbuf, sid), without waiting for any other warp.
@@ -224,7 +185,7 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
                 for (uint32_t m = mask; m; m &= m - 1) {
                     const int j = __ffs(m) - 1;
                     const float4* rec = sbuf[bf][j];
-                    if (!pair_sphere(rec[0], dx, dy, dz)) continue;
+                    if (!pair_cone(rec[0], dx, dy, dz)) continue;
                     const float4 v1 = rec[1], s2 = rec[5];
                     PairGeo pg;
                     if (!pair_hits(v1, rec[3], rec[4], s2, dx, dy, dz, r_rx, pg)) continue;

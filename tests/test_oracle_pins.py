@@ -12,7 +12,8 @@ Coverage (oracle function -> pins):
   or_intersect     axis-aligned closed form; clipped chord; Cholesky least squares;
                    midpoint = maximum of the density along the ray; line integral
   det_* / keys     numpy float32 / float64; monotone in the FP64 distance
-  or_cover_f32     cone brute force over every ray direction (conservative)
+  or_cover_f32     brute force over every ray direction of the sphere beyond the
+                   emitting sphere (conservative); FP64 cone box (tight)
   or_bin           numpy lexsort of the enumerated pairs
   or_render        single / two Gaussians in closed form, zero opacity, permutation
                    invariance, phase linear in frequency, the worked example of
@@ -244,10 +245,29 @@ def test_depth_key_is_float32_distance(oracle_lib):
     assert np.all(np.diff(keys[o64].astype(np.int64)) >= 0)
 
 
+def near_scene(K, seed, r, r_rx=1.0):
+    """Gaussians whose 3-sigma spheres straddle the emitting sphere about r: centres at
+    distance 0 .. 2.5 r_rx in random directions, scales around 0.35 m."""
+    rng = np.random.default_rng(seed)
+    u = rng.normal(size=(K, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    s = synthetic.scene(K, seed)
+    s["means"] = (r[None, :] + u * rng.uniform(0.0, 2.5 * r_rx, (K, 1))).astype(np.float32)
+    s["log_scales"] = rng.normal(math.log(0.35), 0.4, (K, 3)).astype(np.float32)
+    return s
+
+
+def covered_tiles(mask, lo, hi, ntu):
+    return {tv * ntu + tu for tv in range(lo, hi + 1) for tu in range(ntu) if (mask >> tu) & 1}
+
+
 @pytest.mark.parametrize("grid_args", [(36, 9), (72, 18), (360, 90), (30, 7, 10.0, 9.0, -20.0, 7.0)])
-def test_cover_is_conservative(oracle_lib, grid_args):
-    """Every ray direction inside the cone of the sphere of radius 3 max(s) (which
-    contains the 3-sigma ellipsoid) falls in a covered tile."""
+@pytest.mark.parametrize("near", [False, True])
+def test_cover_is_conservative(oracle_lib, grid_args, near):
+    """Brute force over every ray direction: each ray whose part beyond the emitting
+    sphere (t >= r_rx) meets the sphere of radius 3 max(s) about mu -- which holds the
+    3-sigma ellipsoid -- lies in a covered tile.  The near scene exercises the cap
+    branch (spheres that straddle the emitting sphere or hold the receiver)."""
     if len(grid_args) == 2:
         grid = oracle_lib.make_grid(*grid_args)
     else:
@@ -258,28 +278,65 @@ def test_cover_is_conservative(oracle_lib, grid_args):
     u = np.tile(np.arange(grid.n_az), grid.n_el)
     v = np.repeat(np.arange(grid.n_el), grid.n_az)
     tiles = (v // grid.tile_h) * ntu + u // grid.tile_w
-    s = synthetic.scene(300, 9)
     r = np.array([5.0, 4.0, 1.2], np.float32)
+    s = near_scene(300, 19, r.astype(np.float64)) if near else synthetic.scene(300, 9)
+    n_partial = 0
     for k in range(300):
         mu = s["means"][k].astype(np.float64)
         c = mu - r
-        D = np.linalg.norm(c)
         R = 3 * np.exp(s["log_scales"][k].astype(np.float64).max())
         n, mask, lo, hi = oracle_lib.cover_f32(s["means"][k], s["log_scales"][k], r, grid)
-        cov = set()
-        for tv in range(lo, hi + 1):
-            for tu in range(ntu):
-                if (mask >> tu) & 1:
-                    cov.add(tv * ntu + tu)
+        cov = covered_tiles(mask, lo, hi, ntu)
         assert n == len(cov)
-        if D + R < grid.r_rx:
-            continue
-        if D <= R:
-            need = set(tiles.tolist())
-        else:
-            inside = dirs @ (c / D) >= math.sqrt(max(0.0, 1 - (R / D) ** 2))
-            need = set(tiles[inside].tolist())
+        # exit distance of each ray from the sphere: t_out = c.d + sqrt(R^2 - |c x d|^2)
+        cd = dirs @ c
+        q = R * R - (c @ c - cd * cd)
+        reach = (q >= 0) & (cd + np.sqrt(np.maximum(q, 0.0)) >= grid.r_rx)
+        need = set(tiles[reach].tolist())
         assert need <= cov, (k, sorted(need - cov))
+        n_partial += 0 < n < ntu * ntv
+    if near and ntu * ntv >= 20:
+        assert n_partial > 100  # the cap branch does cut most straddling spheres
+
+
+def test_cover_cap_is_tight(oracle_lib):
+    """The cap rule covers no more than the angular box of the same cone built with a
+    2% larger sphere and a 2% smaller emitting sphere, in FP64: a stray factor or a
+    wrong branch that covers far too much fails here."""
+    grid = oracle_lib.make_grid(360, 90)
+    ntu, ntv = oracle_lib.n_tiles(grid)
+    r = np.array([5.0, 4.0, 1.2], np.float32)
+    s = near_scene(300, 23, r.astype(np.float64))
+    A, E, dirs = ray_dirs(grid)
+    u = np.tile(np.arange(grid.n_az), grid.n_el)
+    v = np.repeat(np.arange(grid.n_el), grid.n_az)
+    tiles = (v // grid.tile_h) * ntu + u // grid.tile_w
+    for k in range(300):
+        c = s["means"][k].astype(np.float64) - r
+        D = np.linalg.norm(c)
+        R = 3.03 * 1.02 * np.exp(s["log_scales"][k].astype(np.float64).max())
+        re = 0.98 * grid.r_rx
+        n, mask, lo, hi = oracle_lib.cover_f32(s["means"][k], s["log_scales"][k], r, grid)
+        if n == 0 or D + R < grid.r_rx:
+            continue
+        if re * re > D * D - R * R:
+            cm = (D * D + re * re - R * R) / (2 * D * re)
+            if cm <= 0:
+                continue  # a hemisphere or more: no bound to check
+            th = math.acos(min(cm, 1.0))
+        else:
+            th = math.asin(R / D)
+        # angular box of the cone, in bin units, widened by one bin
+        elc = math.asin(c[2] / D)
+        rho = math.hypot(c[0], c[1])
+        box = (np.abs(E - elc) <= th + np.deg2rad(grid.del_deg))
+        if rho > D * math.sin(th):
+            azd = math.asin(min(1.0, D * math.sin(th) / rho))
+            dA = np.angle(np.exp(1j * (A - math.atan2(c[1], c[0]))))
+            box &= np.abs(dA) <= azd + np.deg2rad(grid.daz_deg)
+        allowed = set(tiles[box].tolist())
+        cov = covered_tiles(mask, lo, hi, ntu)
+        assert cov <= allowed, (k, len(cov - allowed))
 
 
 def test_bin_matches_lexsort_of_pairs(oracle_lib):
@@ -485,6 +542,21 @@ def test_culled_equals_brute_force(oracle_lib, seed, K, grid_args):
     assert np.max(np.abs(a["S"] - b["S"])) == 0.0
     assert np.sum(a["nhit"]) > 50
     assert np.all(a["ntest"] <= b["ntest"])
+
+
+def test_culled_equals_brute_force_near_receiver(oracle_lib):
+    """Large Gaussians straddling the emitting sphere: the cap-narrowed cover drops only
+    pairs that no ray hits."""
+    grid = oracle_lib.make_grid(72, 18)
+    r = np.array([2.0, 2.1, 0.9], np.float32)
+    t = np.array([3.5, 0.2, 1.7], np.float32)
+    s = near_scene(60, 37, r.astype(np.float64))
+    a = oracle_lib.render(s, r, t, 2.4e9, grid, mode=0)
+    b = oracle_lib.render(s, r, t, 2.4e9, grid, mode=1)
+    assert np.array_equal(a["nhit"], b["nhit"])
+    assert np.max(np.abs(a["S"] - b["S"])) == 0.0
+    assert np.sum(a["nhit"]) > 50
+    assert np.sum(a["ntest"]) < 0.8 * np.sum(b["ntest"])
 
 
 def test_front_to_back_sum_is_associative(oracle_lib):
