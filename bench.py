@@ -308,6 +308,7 @@ def run_ours(args, ws, rank):
 
     persistent = persistent_leg(args, cfg, p, rx, tx, R, flush, pairs_per_step)
     fwd_bwd = train_leg(args, ws, flush) if not args.no_train else None
+    csi = csi_leg(args, ws, flush) if not args.no_train else None
     uneven = uneven_leg(args, flush) if args.uneven else None
 
     pk_, pk_kind = peaks()
@@ -344,6 +345,7 @@ def run_ours(args, ws, rank):
                 "ms_per_step": 1e3 * sum(t_e2e) / len(t_e2e)},
         "persistent": persistent,
         "fwd_bwd": fwd_bwd,
+        "csi": csi,
         "uneven": uneven,
         "gpu_launches": 24 * args.steps,
         "clocks": clocks,
@@ -546,6 +548,68 @@ def train_leg(args, ws, flush):
             "what": "forward + complex-MSE loss + hand-written backward to all parameters"}
 
 
+def csi_leg(args, ws, flush):
+    """CSI workload (Sec. 5: antenna arrays, OFDM subcarriers): 100,000 Gaussians, 8
+    four-element arrays (32 receivers), 64 subcarriers at 312.5 kHz around 5.2 GHz,
+    180 x 45 grid.  Forward = project + bin + multi-frequency render + complex sum per
+    (element, subcarrier); fwd+bwd adds loss = mean |CSI - CSI_gt|^2 against the CSI of a
+    separately seeded ground-truth set and the hand-written backward over all 64
+    subcarriers.  CUDA events, L2 flushed between steps."""
+    import torch
+
+    from paper_2502_01826_gb300 import _lib as L
+    from paper_2502_01826_gb300 import synthetic
+    from paper_2502_01826_gb300.render import Renderer, make_grid, received_signal, render, to_device
+
+    cfg = synthetic.config_csi(gt=True)
+    K, n_rx = cfg["scene"]["means"].shape[0], cfg["rx"].shape[0]
+    grid = make_grid(**cfg["grid"])
+    rx = torch.tensor(cfg["rx"], device="cuda")
+    tx = torch.tensor(cfg["tx"], device="cuda")
+    gt = to_device(cfg["gt_scene"])
+    Rg = Renderer(K, n_rx, grid, cfg["f0"], df_hz=cfg["df"], n_f=cfg["n_f"])
+    Rg.ensure_capacity(gt, rx, tx)
+    csi_gt = received_signal(Rg.forward(gt, rx, tx), L.SIG_COMPLEX_SUM).clone()
+    del Rg
+    p = {k: v.clone().requires_grad_(True) for k, v in to_device(cfg["scene"]).items()}
+    R = Renderer(K, n_rx, grid, cfg["f0"], df_hz=cfg["df"], n_f=cfg["n_f"])
+    pd = {k: v.detach() for k, v in p.items()}
+    R.ensure_capacity(pd, rx, tx)
+    out = torch.empty(R.out_shape(), dtype=torch.float32, device="cuda")
+
+    def fwd():
+        R.forward(pd, rx, tx, out=out)
+        return received_signal(out, L.SIG_COMPLEX_SUM)
+
+    def fwd_bwd():
+        for v in p.values():
+            v.grad = None
+        S = render(R, p, rx, tx)
+        csi = S.sum(dim=(2, 3))
+        loss = ((csi - csi_gt) ** 2).sum() / csi_gt.numel()
+        loss.backward()
+        return loss
+
+    for _ in range(args.warmup):
+        fwd()
+    torch.cuda.synchronize()
+    pairs = int(R.status().stats[1])  # composited pairs (each carries all 64 subcarriers)
+    ms_f = _time_steps(fwd, args.steps, flush)
+    for _ in range(args.warmup):
+        fwd_bwd()
+    ms_fb = _time_steps(fwd_bwd, args.steps, flush)
+    tf = max_over_ranks(ms_f * args.steps / 1e3, ws)
+    tfb = max_over_ranks(ms_fb * args.steps / 1e3, ws)
+    n_csi = n_rx * cfg["n_f"]
+    return {"workload": cfg["name"], "n_gauss": K, "n_rx": n_rx, "n_f": cfg["n_f"],
+            "pairs_per_step": pairs,
+            "fwd": {"ms_per_step": ms_f, "pairs_per_s": sum_over_ranks(pairs * args.steps, ws) / tf,
+                    "csi_values_per_s": sum_over_ranks(n_csi * args.steps, ws) / tf},
+            "fwd_bwd": {"ms_per_step": ms_fb, "pairs_per_s": sum_over_ranks(pairs * args.steps, ws) / tfb,
+                        "csi_values_per_s": sum_over_ranks(n_csi * args.steps, ws) / tfb},
+            "what": "per composited pair all 64 subcarriers; loss on the complex CSI"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -555,7 +619,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--n-rx", type=int, default=64, help="receivers (64 = the BLE workload; fewer "
                     "only for small profiling runs)")
-    ap.add_argument("--no-train", action="store_true", help="skip the forward+backward training leg")
+    ap.add_argument("--no-train", action="store_true", help="skip the training and CSI legs")
     ap.add_argument("--uneven", action="store_true", help="add the uneven serving-stress leg (slow setup)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

@@ -133,7 +133,8 @@ gsrf_status gsrf_bin(const gsrf_plan *plan, void *workspace, size_t ws_bytes, vo
  * of the chord beyond r_rx (App. A.2), evaluates the Fourier-Legendre radiance and
  * accumulates S += alpha psi e^{-j phi} T, T *= (1 - alpha) e^{-j theta}.
  *   out_rays  [dev] [n_rx][n_f][n_el][n_az][2]  per-ray received signal S.
- *   ray_state [dev] NULL, or gsrf_ray_state_bytes(plan) bytes the backward needs. */
+ *   ray_state [dev] NULL, or gsrf_ray_state_bytes(plan) bytes (32 per ray, 16-byte
+ *             aligned) that the backward needs. */
 gsrf_status gsrf_render_fwd(const gsrf_plan *plan, const gsrf_gaussians *g, void *workspace,
                             size_t ws_bytes, float *out_rays, void *ray_state, void *stream);
 size_t gsrf_ray_state_bytes(const gsrf_plan *plan);
@@ -150,7 +151,9 @@ size_t gsrf_ray_state_bytes(const gsrf_plan *plan);
  *   (+=); any may be NULL.  The gradient of the opacity is taken through its sigmoid, of
  *   the rotation through the quaternion's normalisation, of the scales through exp.
  *   Hit decisions that sit on the integer steps of the method (splatting, the 3-sigma
- *   boundary, the early stop) carry no gradient.  This build: n_f == 1. */
+ *   boundary, the early stop) carry no gradient.  With n_f > 1 every subcarrier
+ *   f0 + s df contributes with its own suffix sum and its own 2 pi f_s / c in the path and
+ *   transmittance phases; the ray state then also carries sum(b dt) of each ray. */
 gsrf_status gsrf_render_bwd(const gsrf_plan *plan, const gsrf_gaussians *g, void *workspace,
                             size_t ws_bytes, const void *ray_state, const float *grad_rays,
                             float *g_means, float *g_log_scales, float *g_quats,

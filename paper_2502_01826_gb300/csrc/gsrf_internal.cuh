@@ -72,11 +72,15 @@ struct __align__(16) DevStatus {
 
 // Per-ray state the backward replays from: list position (inside the tile's list) of
 // the last composited Gaussian (-1 = none), prod(1 - alpha) and the complex
-// transmittance at f0 after it.
+// transmittance at f0 after it, and (several frequencies) Gamma = sum of b dt over the
+// composited pairs, which gives the transmittance at f0 + s df as T(f0) e^{-j s 2 pi df
+// Gamma / c}.
 struct __align__(16) RayState {
     int32_t last;
     float Ta;
     float Tr, Ti;
+    float Gam;
+    float pad[3];
 };
 
 struct Layout {

@@ -47,6 +47,8 @@ struct BwdArgs {
     int ntu, n_tiles;
     long long n;
     float om_pi;  // 2 f0 / c
+    int n_f;      // frequencies f0 + s df
+    float dlt;    // 2 pi df / c
 };
 
 __device__ __forceinline__ void cp_async16b(void* smem, const void* gmem) {
@@ -89,12 +91,20 @@ __device__ __forceinline__ float reduce_scatter16(float* v, int lane) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+// NFC = 1: one frequency.  NFC > 1: the CTA's lanes take subcarriers fs0 .. fs0 + NFC - 1
+// (fs0 = NFC blockIdx.z) of f0 + s df.  The pair's contribution there is z_k(f0) r_k^s
+// with r_k = e^{-j (2 pi df d_k / c + 2 pi df Gamma_k / c)} (Gamma_k = sum of b dt in front
+// of k), exactly as the forward builds it; each subcarrier keeps its own suffix R, and
+// the transmittance and path phases enter with their own 2 pi f_s / c.  Every chunk adds
+// its share of the gradient to the same accumulators.
+template <int NFC>
 __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
     __shared__ float4 sbuf[kBW][2][kBB][6];
     __shared__ uint32_t sid[kBW][2][kBB];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = blockIdx.x >> 1, half = blockIdx.x & 1, r = blockIdx.y;
+    const int fs0 = (int)blockIdx.z * NFC;  // first subcarrier of the chunk
     const int tu = tile % a.ntu, tv = tile / a.ntu;
     const int lx = ((warp & 1) << 3) | (lane & 7);
     const int ly = (half << 3) | ((warp >> 1) << 2) | (lane >> 3);
@@ -107,7 +117,10 @@ __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
 #pragma unroll
     for (int i = 0; i < 12; ++i) Y[i] = 0.0f;
     int last = -1;
-    float Tr = 0.0f, Ti = 0.0f, Gr = 0.0f, Gi = 0.0f;
+    float Tr = 0.0f, Ti = 0.0f, Gam = 0.0f;
+    float Gs[2 * NFC], Rs[2 * NFC];  // upstream G and suffix R per subcarrier of the chunk
+#pragma unroll
+    for (int i = 0; i < 2 * NFC; ++i) Gs[i] = Rs[i] = 0.0f;
     if (valid) {
         const size_t gi = (size_t)v * gr.n_az + u;
         const float4* t4 = reinterpret_cast<const float4*>(a.raytab + gi * kRayTab);
@@ -117,14 +130,21 @@ __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
         Y[2] = t2.x; Y[3] = t2.y; Y[4] = t2.z; Y[5] = t2.w;
         Y[6] = t3.x; Y[7] = t3.y; Y[8] = t3.z; Y[9] = t3.w;
         Y[10] = t5.x; Y[11] = t5.y;
-        const size_t ray = ((size_t)r * gr.n_el + v) * gr.n_az + u;
-        const RayState s = a.rs[ray];
+        const size_t plane = (size_t)gr.n_el * gr.n_az, pix = (size_t)v * gr.n_az + u;
+        const RayState s = a.rs[(size_t)r * plane + pix];
         last = s.last;
         Tr = s.Tr;
         Ti = s.Ti;
-        const float2 g2 = reinterpret_cast<const float2*>(a.grad_rays)[ray];
-        Gr = g2.x;
-        Gi = g2.y;
+        Gam = s.Gam;
+        const float2* g2 = reinterpret_cast<const float2*>(a.grad_rays) + ((size_t)r * a.n_f + fs0) * plane + pix;
+#pragma unroll
+        for (int q = 0; q < NFC; ++q) {
+            if (fs0 + q < a.n_f) {
+                const float2 gq2 = g2[(size_t)q * plane];
+                Gs[2 * q] = gq2.x;
+                Gs[2 * q + 1] = gq2.y;
+            }
+        }
     }
     const Bundle bun = warp_bundle(valid, dx, dy, dz);  // the forward's warp cone
 
@@ -143,8 +163,6 @@ __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
     const View* __restrict__ view = a.view + (size_t)r * a.n;
     const float rx = a.rxpos[3 * r], ry = a.rxpos[3 * r + 1], rz = a.rxpos[3 * r + 2];
     const float omega = 3.14159265f * a.om_pi;  // 2 pi f0 / c
-
-    float Rr = 0.0f, Ri = 0.0f;  // suffix sum of contributions behind the current pair
 
     auto stage = [&](int bf, long long b0, long long bend) -> uint32_t {
         bool keep = false;
@@ -217,19 +235,53 @@ __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
                 const float nTr = (Tr * cs - Ti * sn) * iom;
                 Ti = (Ti * cs + Tr * sn) * iom;
                 Tr = nTr;
-                // w = E T, z = alpha psi w
+                // w = E T at f0; Theta = sum_s omega_s Re(conj(G_s) dS_s/dtheta_s),
+                // Phi = sum_s omega_s Re(conj(G_s) dS_s/dphi_s) (App. D.1, D.2)
                 const float er = v1.w, ei = rec[2].x;
                 const float wr = er * Tr - ei * Ti, wi = er * Ti + ei * Tr;
-                const float zr = alpha * (pr * wr - pi * wi), zi = alpha * (pr * wi + pi * wr);
-                // App. D.1, D.2
-                const float Xr = pr * wr - pi * wi - Rr * iom, Xi = pr * wi + pi * wr - Ri * iom;
-                const float g_alpha = Gr * Xr + Gi * Xi;
-                const float g_th = Gr * Ri - Gi * Rr;
-                const float g_ph = Gr * zi - Gi * zr;
-                const float ur = alpha * wr, ui = alpha * wi;
-                const float g_pr = Gr * ur + Gi * ui, g_pi = Gi * ur - Gr * ui;
-                Rr += zr;
-                Ri += zi;
+                float g_alpha, Theta, Phi, g_pr, g_pi;
+                if constexpr (NFC == 1) {
+                    const float Gr = Gs[0], Gi = Gs[1], Rr = Rs[0], Ri = Rs[1];
+                    const float zr = alpha * (pr * wr - pi * wi), zi = alpha * (pr * wi + pi * wr);
+                    const float Xr = pr * wr - pi * wi - Rr * iom, Xi = pr * wi + pi * wr - Ri * iom;
+                    g_alpha = Gr * Xr + Gi * Xi;
+                    Theta = (Gr * Ri - Gi * Rr) * omega;
+                    Phi = (Gr * zi - Gi * zr) * omega;
+                    const float ur = alpha * wr, ui = alpha * wi;
+                    g_pr = Gr * ur + Gi * ui;
+                    g_pi = Gi * ur - Gr * ui;
+                    Rs[0] = Rr + zr;
+                    Rs[1] = Ri + zi;
+                } else {
+                    Gam -= s2.z * pg.dt;  // Gamma in front of this pair
+                    const float ws = rec[2].y + a.dlt * Gam;
+                    float rs, rc, ss, sc;
+                    sincosf(ws, &rs, &rc);
+                    sincosf((float)fs0 * ws, &ss, &sc);
+                    // w and psi w at the chunk's first subcarrier, then one rotation per step
+                    float Wr = wr * sc + wi * ss, Wi = wi * sc - wr * ss;
+                    float pwr = pr * Wr - pi * Wi, pwi = pr * Wi + pi * Wr;
+                    g_alpha = Theta = Phi = g_pr = g_pi = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < NFC; ++q) {
+                        const float Gr = Gs[2 * q], Gi = Gs[2 * q + 1], Rr = Rs[2 * q], Ri = Rs[2 * q + 1];
+                        const float om_s = omega + (float)(fs0 + q) * a.dlt;
+                        const float zr = alpha * pwr, zi = alpha * pwi;
+                        g_alpha += Gr * (pwr - Rr * iom) + Gi * (pwi - Ri * iom);
+                        Theta += om_s * (Gr * Ri - Gi * Rr);
+                        Phi += om_s * (Gr * zi - Gi * zr);
+                        g_pr += alpha * (Gr * Wr + Gi * Wi);
+                        g_pi += alpha * (Gi * Wr - Gr * Wi);
+                        Rs[2 * q] = Rr + zr;
+                        Rs[2 * q + 1] = Ri + zi;
+                        const float nWr = Wr * rc + Wi * rs;
+                        Wi = Wi * rc - Wr * rs;
+                        Wr = nWr;
+                        const float npr = pwr * rc + pwi * rs;
+                        pwi = pwi * rc - pwr * rs;
+                        pwr = npr;
+                    }
+                }
                 // folded coefficients
                 gq[0] = g_pr; gq[1] = g_pi;
                 gq[2] = g_pr * P[0]; gq[3] = g_pi * P[0];
@@ -242,9 +294,9 @@ __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
                     gq[8 + 4 * t + 2] = g_pi * Y[2 * t];
                     gq[8 + 4 * t + 3] = g_pi * Y[2 * t + 1];
                 }
-                // transmittance phase theta = omega b dt
-                const float g_b = g_th * omega * pg.dt;
-                const float g_dt = g_th * omega * s2.z;
+                // transmittance phase theta_s = omega_s b dt
+                const float g_b = Theta * pg.dt;
+                const float g_dt = Theta * s2.z;
                 // alpha = o g, g = exp(-m2r / 2)
                 float g_o = 0.0f, g_m2r = 0.0f;
                 if (!clamped) {
@@ -288,7 +340,7 @@ __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
                 const float tx = mx - a.txpos[0], ty = my - a.txpos[1], tz = mz - a.txpos[2];
                 const float it = rsqrtf(fmaxf(tx * tx + ty * ty + tz * tz, 1e-30f));
                 const float ir = rsqrtf(fmaxf(v0.x * v0.x + v0.y * v0.y + v0.z * v0.z, 1e-30f));
-                const float gd = g_ph * omega;
+                const float gd = Phi;
                 gmx += gd * (tx * it + v0.x * ir);
                 gmy += gd * (ty * it + v0.y * ir);
                 gmz += gd * (tz * it + v0.z * ir);
@@ -409,7 +461,13 @@ cudaError_t launch_render_bwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     a.n_tiles = L.n_tiles;
     a.n = L.n;
     a.om_pi = (float)(2.0 * p->f0_hz / kC);
-    k_render_bwd<<<dim3(2 * L.n_tiles, L.n_rx), kBThreads, 0, st>>>(a);
+    a.n_f = p->n_f;
+    a.dlt = (float)(2.0 * 3.14159265358979323846 * p->df_hz / kC);
+    if (p->n_f == 1) {
+        k_render_bwd<1><<<dim3(2 * L.n_tiles, L.n_rx), kBThreads, 0, st>>>(a);
+    } else {
+        k_render_bwd<8><<<dim3(2 * L.n_tiles, L.n_rx, (p->n_f + 7) / 8), kBThreads, 0, st>>>(a);
+    }
     const unsigned nb = (unsigned)((L.n + 255) / 256);
     k_grad_params<<<nb, 256, 0, st>>>(*g, at<GShape>(ws, L.gshape), acc, g_means, g_log_scales, g_quats,
                                       g_opacity_logit, g_coeffs, g_phase_b);

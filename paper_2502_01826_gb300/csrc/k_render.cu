@@ -259,6 +259,8 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
             s.Ta = Ta;
             s.Tr = Tr;
             s.Ti = Ti;
+            s.Gam = Gam;
+            s.pad[0] = s.pad[1] = s.pad[2] = 0.0f;
             a.rs[ray] = s;
         }
     }

@@ -88,9 +88,10 @@ def config_train(K: int = 200_000, n_rx: int = 16) -> dict:
                 f0=2.4e9, df=0.0, n_f=1, grid=grid_spec(360, 90))
 
 
-def config_csi(K: int = 100_000) -> dict:
+def config_csi(K: int = 100_000, gt: bool = False) -> dict:
     """CSI shaped: 100,000 Gaussians, 8 receivers x 4 elements spaced half a carrier
-    wavelength along x, 64 subcarriers at 312.5 kHz around 5.2 GHz, 180x45 grid."""
+    wavelength along x, 64 subcarriers at 312.5 kHz around 5.2 GHz, 180x45 grid.  With
+    gt=True also a separately seeded ground-truth set of the same size."""
     s = scene(K, BASE_SEED + 3)
     centres = positions(s["_rng"], 8)
     tx = positions(s["_rng"], 1)[0]
@@ -98,8 +99,11 @@ def config_csi(K: int = 100_000) -> dict:
     off = (np.arange(4) - 1.5) * lam / 2.0
     rx = np.repeat(centres.astype(np.float64), 4, axis=0)
     rx[:, 0] += np.tile(off, 8)
-    return dict(name="csi_100k_8x4rx_64sc_180x45", scene=strip(s), rx=rx.astype(np.float32),
-                tx=tx, f0=5.2e9 - 32 * 312.5e3, df=312.5e3, n_f=64, grid=grid_spec(180, 45))
+    out = dict(name="csi_100k_8x4rx_64sc_180x45", scene=strip(s), rx=rx.astype(np.float32),
+               tx=tx, f0=5.2e9 - 32 * 312.5e3, df=312.5e3, n_f=64, grid=grid_spec(180, 45))
+    if gt:
+        out["gt_scene"] = strip(scene(K, BASE_SEED + 3 + 1000))
+    return out
 
 
 def config_uneven(n_scenes: int = 8, n_req: int = 256, k_lo: float = 1e4, k_hi: float = 1e6):

@@ -67,7 +67,8 @@ def gpu_render(scene: dict, rx, tx, f0, grid_spec: dict, cap=None, **grid_kw):
     out = R.forward(p, rxd, txd)
     torch.cuda.synchronize()
     S = out.cpu().numpy()
-    S = S[..., 0] + 1j * S[..., 1]
+    with np.errstate(invalid="ignore"):  # outputs of a refused (non-finite) input are undefined
+        S = S[..., 0] + 1j * S[..., 1]
     return S.reshape(rx.shape[0], -1), R, p, out
 
 

@@ -81,7 +81,7 @@ def test_workspace_size_grows_with_problem(lib):
     assert lib.gsrf_workspace_layout(C.byref(plan()), C.byref(lay)) == L.GSRF_OK
     assert (lay.n_tiles_u, lay.n_tiles_v) == (23, 6)
     assert lay.status == 0 and lay.pair_keys % 256 == 0 and lay.tile_start % 256 == 0
-    assert lib.gsrf_ray_state_bytes(C.byref(plan())) == 4 * 360 * 90 * 16
+    assert lib.gsrf_ray_state_bytes(C.byref(plan())) == 4 * 360 * 90 * 32
 
 
 @pytest.mark.parametrize("bad", [

@@ -32,23 +32,25 @@ def _gpu():
     oracle.build()
 
 
-def masked_upstream(scene, rx, tx, f0, spec, rng, eps_T=1e-4):
-    """Random upstream dL/dS per ray, zero on rays near a discrete decision."""
+def masked_upstream(scene, rx, tx, f0, spec, rng, eps_T=1e-4, n_f=1):
+    """Random upstream dL/dS per ray (and subcarrier), zero on rays near a discrete
+    decision.  Returns [n_rx, rays] for one frequency, else [n_rx, n_f, rays]."""
     g = oracle.make_grid(**spec, eps_T=eps_T)
     G = []
     for r in range(rx.shape[0]):
         out = oracle.render(scene, rx[r], tx, f0, g, bands=MASK_BANDS)
-        Gr = rng.normal(size=out["S"].shape[1]) + 1j * rng.normal(size=out["S"].shape[1])
-        Gr[out["flags"] != 0] = 0
-        G.append(Gr)
+        shape = (n_f, out["S"].shape[1])
+        Gr = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+        Gr[:, out["flags"] != 0] = 0
+        G.append(Gr[0] if n_f == 1 else Gr)
     return np.array(G), g
 
 
-def gpu_grads(scene, rx, tx, f0, spec, G, eps_T=1e-4):
+def gpu_grads(scene, rx, tx, f0, spec, G, eps_T=1e-4, df=0.0, n_f=1):
     """Gradients of sum Re(conj(G) S) through the autograd Function."""
     K = scene["means"].shape[0]
     grid = make_grid(**spec, eps_T=eps_T)
-    R = Renderer(K, rx.shape[0], grid, f0)
+    R = Renderer(K, rx.shape[0], grid, f0, df_hz=df, n_f=n_f)
     p = {k: v.clone().requires_grad_(True) for k, v in to_device(scene).items()}
     rxd = torch.tensor(rx, device="cuda")
     txd = torch.tensor(tx, device="cuda")
@@ -62,10 +64,10 @@ def gpu_grads(scene, rx, tx, f0, spec, G, eps_T=1e-4):
     return {k: p[k].grad.cpu().numpy().astype(np.float64) for k in NAMES}
 
 
-def oracle_grads(scene, rx, tx, f0, g, G):
+def oracle_grads(scene, rx, tx, f0, g, G, df=0.0, n_f=1):
     tot = None
     for r in range(rx.shape[0]):
-        gr = oracle.render_grad(scene, rx[r], tx, f0, g, G[r][None])
+        gr = oracle.render_grad(scene, rx[r], tx, f0, g, G[r].reshape(n_f, -1), df=df, n_f=n_f)
         tot = gr if tot is None else {k: tot[k] + gr[k] for k in tot}
     return tot
 
@@ -93,6 +95,22 @@ def test_backward_matches_oracle_gradient_small():
     G, g = masked_upstream(scene, rx, tx, 2.4e9, spec, rng)
     assert np.count_nonzero(G) > 0.5 * G.size
     compare_grads(gpu_grads(scene, rx, tx, 2.4e9, spec, G), oracle_grads(scene, rx, tx, 2.4e9, g, G))
+
+
+@pytest.mark.parametrize("n_f,df", [(3, 2.0e7), (12, 2.0e6)])
+def test_backward_multifrequency_matches_oracle(n_f, df):
+    """Subcarriers f0 + s df (12 = one chunk of 8 and a ragged one of 4): every
+    subcarrier's upstream enters with its own suffix sum and its own 2 pi f_s / c."""
+    scene = synthetic.tiny_scene(300, 203, box=(6.0, 5.0, 3.0), log_scale_mu=math.log(0.25))
+    rng = np.random.default_rng(4)
+    rx = (rng.uniform(0, 1, (2, 3)) * [6.0, 5.0, 3.0]).astype(np.float32)
+    tx = np.array([5.5, 0.5, 2.5], np.float32)
+    spec = dict(n_az=72, n_el=18)
+    f0 = 5.2e9
+    G, g = masked_upstream(scene, rx, tx, f0, spec, rng, n_f=n_f)
+    assert np.count_nonzero(G) > 0.5 * G.size
+    compare_grads(gpu_grads(scene, rx, tx, f0, spec, G, df=df, n_f=n_f),
+                  oracle_grads(scene, rx, tx, f0, g, G, df=df, n_f=n_f))
 
 
 def test_backward_matches_oracle_on_512_gaussian_training_subscene():
