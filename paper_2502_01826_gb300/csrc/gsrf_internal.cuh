@@ -20,12 +20,17 @@ constexpr int kMaxTiles = 1024;       // bins of the tile counting sort
 constexpr int kMaxNf = 64;
 
 // Per-Gaussian shape record: whitening matrix W = diag(1/s) R^T (so that
-// (x-mu)^T Sigma^-1 (x-mu) = |W (x-mu)|^2), opacity and excess-phase coefficient.
+// (x-mu)^T Sigma^-1 (x-mu) = |W (x-mu)|^2), opacity and excess-phase coefficient; then
+// M = diag(s) R^T = W^-T, with n^T Sigma n = |M n|^2, so that the 3-sigma ellipsoid
+// reaches 3 |M n| along a unit normal n (its support function).  The render stages the
+// first 48 bytes per candidate; M feeds its warp-level plane test.
 struct __align__(16) GShape {
     float W[9];
     float o;
     float b;
     float pad;
+    float M[9];
+    float pad2[3];
 };
 
 // Per-(receiver, Gaussian) view record: offset c = mu - r and D cos(theta) of the cone
@@ -256,6 +261,67 @@ __device__ __forceinline__ bool bundle_meets(const Bundle& b, float4 c) {
     const float dsn = sqrtf(fmaxf(D2 - c.w * c.w, 0.0f));  // D sin(theta)
     const float cd = c.x * b.bx + c.y * b.by + c.z * b.bz;
     return cd >= b.cb * c.w - b.sb * dsn - 1e-4f * (c.w + dsn);
+}
+
+// Four planes through the receiver that hold every ray of a warp's 8 x 4 block on
+// their inner side (n.d >= 0): the vertical planes at the block's first and last
+// azimuth, and planes tilted to its lowest and highest elevation; each is moved along
+// the warp axis b until it clears all of the warp's rays (a margin of 1e-6 in n.d).  A
+// ray point x = t d (t >= r_rx > 0) then has n.x >= 0, so an ellipsoid that lies wholly
+// on the outer side of one plane meets no ray of the warp.  Every lane computes the
+// same planes; lane j < 4 writes plane j to the warp's shared slots.
+__device__ __forceinline__ void warp_planes(const gsrf_grid& gr, int u_lo, int v_lo, const Bundle& b,
+                                            bool valid, float dx, float dy, float dz, float4* spl) {
+    const int u_hi = min(u_lo + 7, gr.n_az - 1), v_hi = min(v_lo + 3, gr.n_el - 1);
+    const float kDeg = 0.0174532925f;
+    const float a0 = (gr.az0_deg + ((float)u_lo + 0.5f) * gr.daz_deg) * kDeg;
+    const float a1 = (gr.az0_deg + ((float)u_hi + 0.5f) * gr.daz_deg) * kDeg;
+    const float e0 = (gr.el0_deg + ((float)v_lo + 0.5f) * gr.del_deg) * kDeg;
+    const float e1 = (gr.el0_deg + ((float)v_hi + 0.5f) * gr.del_deg) * kDeg;
+    float sa0, ca0, sa1, ca1, se0, ce0, se1, ce1, sam, cam;
+    sincosf(a0, &sa0, &ca0);
+    sincosf(a1, &sa1, &ca1);
+    sincosf(e0, &se0, &ce0);
+    sincosf(e1, &se1, &ce1);
+    sincosf(0.5f * (a0 + a1), &sam, &cam);
+    float n[4][3] = {{-sa0, ca0, 0.0f}, {sa1, -ca1, 0.0f}, {-se0 * cam, -se0 * sam, ce0}, {se1 * cam, se1 * sam, -ce1}};
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float m = valid ? n[j][0] * dx + n[j][1] * dy + n[j][2] * dz : 1e30f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        m -= 1e-6f;
+        if (m < 0.0f) {
+            // b.d >= b.cb > 0 on every ray, so n + (-m / b.cb) b clears them all
+            const float lam = b.cb > 0.0f ? -m / b.cb : 0.0f;
+            const float keep = b.cb > 0.0f ? 1.0f : 0.0f;  // no plane when the warp spans a hemisphere
+            n[j][0] = keep * (n[j][0] + lam * b.bx);
+            n[j][1] = keep * (n[j][1] + lam * b.by);
+            n[j][2] = keep * (n[j][2] + lam * b.bz);
+        }
+        if (lane == j) spl[j] = make_float4(n[j][0], n[j][1], n[j][2], 0.0f);
+    }
+    __syncwarp();
+}
+
+// Can the 3-sigma ellipsoid about mu (c = mu - r; M from the shape record) reach the
+// inner side of all four planes?  Its support along n is n.c + 3 |M n|; a 1% margin
+// (3.03) covers rounding.  A zero plane never rejects.
+__device__ __forceinline__ bool planes_meet(const float4* spl, const float4& c, const GShape* sh) {
+    const float4* mm = reinterpret_cast<const float4*>(sh) + 3;
+    const float4 m0 = __ldg(mm), m1 = __ldg(mm + 1), m2 = __ldg(mm + 2);
+    bool meet = true;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float4 n = spl[j];
+        const float s0 = m0.x * n.x + m0.y * n.y + m0.z * n.z;
+        const float s1 = m0.w * n.x + m1.x * n.y + m1.y * n.z;
+        const float s2 = m1.z * n.x + m1.w * n.y + m2.x * n.z;
+        const float nc = n.x * c.x + n.y * c.y + n.z * c.z;
+        meet = meet && (nc >= 0.0f || nc * nc <= 9.1809f * (s0 * s0 + s1 * s1 + s2 * s2));
+    }
+    return meet;
 }
 
 struct PairGeo {

@@ -101,6 +101,7 @@ template <int NFC>
 __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
     __shared__ float4 sbuf[kBW][2][kBB][6];
     __shared__ uint32_t sid[kBW][2][kBB];
+    __shared__ float4 spl[kBW][4];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = blockIdx.x >> 1, half = blockIdx.x & 1, r = blockIdx.y;
@@ -146,7 +147,9 @@ __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
             }
         }
     }
-    const Bundle bun = warp_bundle(valid, dx, dy, dz);  // the forward's warp cone
+    const Bundle bun = warp_bundle(valid, dx, dy, dz);  // the forward's warp cone and planes
+    warp_planes(gr, tu * kTile + ((warp & 1) << 3), tv * kTile + (half << 3) + ((warp >> 1) << 2), bun, valid, dx,
+                dy, dz, spl[warp]);
 
     // positions are inside the tile's list; a state that points past it (another plan's,
     // or garbage) is clamped so that no read leaves the list
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
             const uint32_t id = a.pids[b0 + lane];
             const float4* vw = reinterpret_cast<const float4*>(view + id);
             const float4 c = __ldg(vw);
-            keep = bundle_meets(bun, c);
+            keep = bundle_meets(bun, c) && planes_meet(spl[warp], c, a.shape + id);
             if (keep) {
                 sid[warp][bf][lane] = id;
                 const float4* sh = reinterpret_cast<const float4*>(a.shape + id);

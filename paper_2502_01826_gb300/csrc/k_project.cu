@@ -51,10 +51,15 @@ __global__ void __launch_bounds__(256) k_prepare(gsrf_gaussians g, const float* 
                         2.0f * (qx * qz - qw * qy), 2.0f * (qy * qz + qw * qx), 1.0f - 2.0f * (qx * qx + qy * qy)};
     const float is[3] = {expf(-l0), expf(-l1), expf(-l2)};
     GShape out;
+    const float sc[3] = {expf(l0), expf(l1), expf(l2)};
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) out.W[3 * i + j] = R[3 * j + i] * is[i];
+        for (int j = 0; j < 3; ++j) {
+            out.W[3 * i + j] = R[3 * j + i] * is[i];
+            out.M[3 * i + j] = R[3 * j + i] * sc[i];
+        }
+    out.pad2[0] = out.pad2[1] = out.pad2[2] = 0.0f;
     out.o = 1.0f / (1.0f + expf(-ol));
     out.b = b;
     out.pad = 0.0f;

@@ -4,8 +4,9 @@
 // Layout of the work: a CTA of 4 warps covers half of a 16x16 ray tile (16 x 8 rays),
 // each warp an 8 x 4 block of rays, one ray per thread.  Every warp walks its tile's
 // candidate list on its own, 32 candidates per batch: lane i takes candidate b0 + i,
-// tests its direction cone against the cone of the warp's 32 rays and, if it may be
-// hit, copies its records into the warp's half of a double buffer with cp.async while
+// tests its direction cone against the cone of the warp's 32 rays and its ellipsoid
+// against four planes that bound those rays and, if it may be hit, copies its
+// records into the warp's half of a double buffer with cp.async while
 // the warp works on the current batch; the rays then visit only the candidates of the
 // ballot mask, in list order.  Warps never wait for one another and a warp leaves as
 // soon as its 32 rays have terminated (prod(1 - alpha) < eps_T).
@@ -114,7 +115,7 @@ __device__ __forceinline__ void load_ray(const float* raytab, size_t ray, float&
 // E(f0) e^{-j s 2 pi df d / c}; the powers of r come from one sincos and a recurrence.
 template <int NFC>
 __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int tile, int wq, int chunk,
-                                             float4 (*sbuf)[kWB][kRec], uint32_t (*sid)[kWB]) {
+                                             float4 (*sbuf)[kWB][kRec], uint32_t (*sid)[kWB], float4* spl) {
     const int lane = threadIdx.x & 31;
     const int tu = tile % a.ntu, tv = tile / a.ntu;
     const int lx = ((wq & 1) << 3) | (lane & 7);
@@ -128,6 +129,7 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
     for (int i = 0; i < 12; ++i) Y[i] = 0.0f;
     if (valid) load_ray(a.raytab, (size_t)v * gr.n_az + u, dx, dy, dz, P, Y);
     const Bundle bun = warp_bundle(valid, dx, dy, dz);
+    warp_planes(gr, tu * kTile + ((wq & 1) << 3), tv * kTile + ((wq >> 1) << 2), bun, valid, dx, dy, dz, spl);
 
     const size_t ts = (size_t)r * (a.n_tiles + 1) + tile;
     const long long base0 = a.rx_base[r];
@@ -154,7 +156,7 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
             const uint32_t id = a.pids[b0 + lane];
             const float4* vw = reinterpret_cast<const float4*>(view + id);
             const float4 c = __ldg(vw);
-            keep = bundle_meets(bun, c);
+            keep = bundle_meets(bun, c) && planes_meet(spl, c, a.shape + id);
             if (keep) {
                 sid[bf][lane] = id;
                 const float4* sh = reinterpret_cast<const float4*>(a.shape + id);
@@ -282,9 +284,10 @@ template <int NFC>
 __global__ void __launch_bounds__(kThreads, NFC == 1 ? 8 : 4) k_render_fwd(RenderArgs a) {
     __shared__ float4 sbuf[kWarps][2][kWB][kRec];
     __shared__ uint32_t sid[kWarps][2][kWB];
+    __shared__ float4 spl[kWarps][4];
     const int warp = threadIdx.x >> 5;
     render_block<NFC>(a, blockIdx.y, blockIdx.x >> 1, (blockIdx.x & 1) * kWarps + warp, blockIdx.z, sbuf[warp],
-                      sid[warp]);
+                      sid[warp], spl[warp]);
 }
 
 // Persistent batched launch: every warp takes work items -- (job, receiver, tile, ray
@@ -294,6 +297,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_render_batch(BatchArgs b, const
                                                               unsigned long long* __restrict__ counter) {
     __shared__ float4 sbuf[kWarps][2][kWB][kRec];
     __shared__ uint32_t sid[kWarps][2][kWB];
+    __shared__ float4 spl[kWarps][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned long long total = b.item_base[b.n_jobs];
     for (;;) {
@@ -308,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 8) k_render_batch(BatchArgs b, const
         const unsigned long long local = id - b.item_base[j];
         const int per_rx = a.n_tiles * 8;
         const int r = (int)(local / per_rx), rem = (int)(local % per_rx);
-        render_block<1>(a, r, rem >> 3, rem & 7, 0, sbuf[warp], sid[warp]);
+        render_block<1>(a, r, rem >> 3, rem & 7, 0, sbuf[warp], sid[warp], spl[warp]);
     }
 }
 
