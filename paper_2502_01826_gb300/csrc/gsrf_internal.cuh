@@ -13,7 +13,8 @@ constexpr int kNB = 16;               // Fourier-Legendre coefficients, L = 3 (S
 constexpr double kC = 3.0e8;          // propagation speed (Sec. 2 worked example)
 constexpr int kTile = 16;             // rays per tile side (App. E)
 constexpr int kRenderThreads = kTile * kTile;
-constexpr int kChunk = 4096;          // items per block in the sort / emit passes
+constexpr int kChunk = 4096;          // items per block in the sort passes
+constexpr int kEChunk = 1024;         // depth-sorted Gaussians per block in the emission
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kMaxTiles = 1024;       // bins of the tile counting sort
@@ -97,6 +98,7 @@ struct Layout {
     int64_t n;
     int64_t cap;
     int32_t dchunks;      // depth-sort chunks per receiver
+    int32_t echunks;      // emission chunks per receiver
     int64_t pchunks_max;  // upper bound on pair chunks over all receivers
 };
 

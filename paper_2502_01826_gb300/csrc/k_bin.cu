@@ -120,10 +120,15 @@ __global__ void __launch_bounds__(kSortThreads) k_scan(Segs S, int nbins, uint32
     chunk_range(S, seg, c0, c1);
     for (int d = threadIdx.x; d < nbins; d += kSortThreads) {
         uint32_t run = 0;
-        for (long long c = c0; c < c1; ++c) {
-            const uint32_t v = H[(size_t)c * nbins + d];
-            H[(size_t)c * nbins + d] = run;
-            run += v;
+        for (long long cb = c0; cb < c1; cb += 8) {  // 8 independent loads in flight
+            uint32_t v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = cb + j < c1 ? H[(size_t)(cb + j) * nbins + d] : 0u;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (cb + j < c1) H[(size_t)(cb + j) * nbins + d] = run;
+                run += v[j];
+            }
         }
         tot[d] = run;
     }
@@ -137,7 +142,14 @@ __global__ void __launch_bounds__(kSortThreads) k_scan(Segs S, int nbins, uint32
         const uint32_t ex = block_excl_scan<uint32_t>(v, &t, sh);
         if (d < nbins) {
             const uint32_t start = carry + ex;
-            for (long long c = c0; c < c1; ++c) H[(size_t)c * nbins + d] += start;
+            for (long long cb = c0; cb < c1; cb += 8) {
+                uint32_t v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = cb + j < c1 ? H[(size_t)(cb + j) * nbins + d] : 0u;
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (cb + j < c1) H[(size_t)(cb + j) * nbins + d] = v[j] + start;
+            }
             if (bin_start) bin_start[(size_t)seg * (nbins + 1) + d] = start;
         }
         carry += t;
@@ -201,13 +213,13 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const K* __restrict__ 
 
 // ---- emission -------------------------------------------------------------
 
-// Per (receiver, chunk of the depth-sorted Gaussians): number of pairs.
+// Per (receiver, emission chunk of kEChunk depth-sorted Gaussians): number of pairs.
 __global__ void __launch_bounds__(kSortThreads) k_count_chunks(const uint32_t* __restrict__ dval,
                                                                const Cover* __restrict__ cover, long long n,
                                                                int dchunks, uint32_t* __restrict__ chunk_sum) {
     __shared__ uint32_t sh[kSortWarps];
     const int r = blockIdx.y, c = blockIdx.x;
-    const long long lo = (long long)c * kChunk, hi = min(lo + (long long)kChunk, n);
+    const long long lo = (long long)c * kEChunk, hi = min(lo + (long long)kEChunk, n);
     uint32_t s = 0;
     for (long long i = lo + threadIdx.x; i < hi; i += kSortThreads)
         s += cover[(size_t)r * n + dval[(size_t)r * n + i]].count;
@@ -224,10 +236,16 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_pairs(uint32_t* __restric
                                                              uint32_t* __restrict__ pchunk_base, DevStatus* st) {
     for (int r = threadIdx.x; r < n_rx; r += kSortThreads) {
         uint32_t run = 0;
-        for (int c = 0; c < dchunks; ++c) {
-            const uint32_t v = chunk_sum[(size_t)r * dchunks + c];
-            chunk_sum[(size_t)r * dchunks + c] = run;
-            run += v;
+        uint32_t* cs = chunk_sum + (size_t)r * dchunks;
+        for (int cb = 0; cb < dchunks; cb += 8) {  // 8 independent loads in flight
+            uint32_t v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = cb + j < dchunks ? cs[cb + j] : 0u;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (cb + j < dchunks) cs[cb + j] = run;
+                run += v[j];
+            }
         }
         rx_total[r] = run;
     }
@@ -266,14 +284,14 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
                                                        unsigned long long* __restrict__ pkeys,
                                                        uint32_t* __restrict__ pids, const DevStatus* st) {
     if (capacity_failed(st)) return;
-    __shared__ uint32_t offs[kChunk];
+    __shared__ uint32_t offs[kEChunk];
     __shared__ uint32_t sh[kSortWarps];
     __shared__ uint8_t sbits[kSortWarps][64];
     const int r = blockIdx.y, c = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long lo = (long long)c * kChunk, hi = min(lo + (long long)kChunk, n);
+    const long long lo = (long long)c * kEChunk, hi = min(lo + (long long)kEChunk, n);
     const int m = (int)(hi - lo);
-    constexpr int per = kChunk / kSortThreads;
+    constexpr int per = kEChunk / kSortThreads;
     // exclusive scan of the pair counts over the chunk, in item order (blocked per thread)
     uint32_t v[per];
     uint32_t s = 0;
@@ -398,12 +416,12 @@ cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream
 
     // (2) emission in depth order
     uint32_t* chunk_sum = at<uint32_t>(ws, L.dchunk_sum);
-    k_count_chunks<<<dim3(L.dchunks, L.n_rx), kSortThreads, 0, st>>>(dval_sorted, at<Cover>(ws, L.cover), L.n,
-                                                                       L.dchunks, chunk_sum);
-    k_scan_pairs<<<1, kSortThreads, 0, st>>>(chunk_sum, L.n_rx, L.dchunks, L.cap, at<long long>(ws, L.rx_base),
+    k_count_chunks<<<dim3(L.echunks, L.n_rx), kSortThreads, 0, st>>>(dval_sorted, at<Cover>(ws, L.cover), L.n,
+                                                                       L.echunks, chunk_sum);
+    k_scan_pairs<<<1, kSortThreads, 0, st>>>(chunk_sum, L.n_rx, L.echunks, L.cap, at<long long>(ws, L.rx_base),
                                              at<uint32_t>(ws, L.rx_total), at<uint32_t>(ws, L.pchunk_base), status);
-    k_emit<<<dim3(L.dchunks, L.n_rx), kSortThreads, 0, st>>>(
-        dval_sorted, dkey_sorted, at<Cover>(ws, L.cover), L.n, L.dchunks, chunk_sum, at<long long>(ws, L.rx_base),
+    k_emit<<<dim3(L.echunks, L.n_rx), kSortThreads, 0, st>>>(
+        dval_sorted, dkey_sorted, at<Cover>(ws, L.cover), L.n, L.echunks, chunk_sum, at<long long>(ws, L.rx_base),
         at<uint32_t>(ws, L.rx_total), L.ntu, at<unsigned long long>(ws, L.pkeys2), at<uint32_t>(ws, L.pids2), status);
 
     // (3) stable counting sort of each receiver's pairs by tile: pkeys2 -> pkeys
