@@ -337,7 +337,7 @@ def run_ours(args, ws, rank):
                          "pairs_per_s": pairs_per_step / (ms_plain / 1e3),
                          "speedup_of_batched": ms_plain / ms_step,
                          "what": "%d sequential single-receiver project+bin+render+RSSI calls" % n_rx},
-        "roofline": {"kernel": "k_render_fwd", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
+        "roofline": {"kernel": "k_render_queue", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
                      "peak_kind": "FP32 lanes x max SM clock (%s sm_max_mhz %.0f)" % (pk_kind, mhz),
                      "flop_per_launch": flops},

@@ -52,6 +52,13 @@ bool make_layout(const gsrf_plan* p, Layout* L) {
     L->pids2 = take(cap * 4);
     L->tile_start = take(nr * (size_t)(L->n_tiles + 1) * 4);
     L->thist = take((size_t)L->pchunks_max * L->n_tiles * 4);
+    // the render's work queue: one item per (receiver, tile, 8 x 4 ray block)
+    const size_t items = nr * (size_t)L->n_tiles * 8;
+    L->qkeys = take(items * 4);
+    L->qkeys2 = take(items * 4);
+    L->qorder = take(items * 4);
+    L->qhist = take((items + kChunk - 1) / kChunk * 32 * 4);
+    L->qcounter = take(8);
     L->total = off;
     return true;
 }

@@ -92,7 +92,8 @@ struct __align__(16) RayState {
 struct Layout {
     // byte offsets
     size_t status, rxpos, txpos, gacc, raytab, fle, gshape, dpath, view, cover, dkey, dkey2, dval, dval2, dhist, dchunk_sum,
-        rx_base, rx_total, pchunk_base, pkeys, pkeys2, pids, pids2, tile_start, thist, total;
+        rx_base, rx_total, pchunk_base, pkeys, pkeys2, pids, pids2, tile_start, thist, qkeys, qkeys2, qorder, qhist,
+        qcounter, total;
     int32_t ntu, ntv, n_tiles;
     int32_t n_rx;
     int64_t n;

@@ -316,6 +316,39 @@ __global__ void __launch_bounds__(kThreads, 8) k_render_batch(BatchArgs b, const
     }
 }
 
+// Persistent launch of one problem (n_f = 1): like k_render_batch, every warp takes work
+// items (receiver, tile, ray block) from one counter, in the heaviest-first order of
+// k_queue_keys, until none is left; a warp that finishes early takes the next item
+// instead of idling until the other warps of its CTA are done.
+__global__ void __launch_bounds__(kThreads, 8) k_render_queue(RenderArgs a, const uint32_t* __restrict__ order,
+                                                              unsigned long long* __restrict__ counter,
+                                                              unsigned long long total) {
+    __shared__ float4 sbuf[kWarps][2][kWB][kRec];
+    __shared__ uint32_t sid[kWarps][2][kWB];
+    __shared__ float4 spl[kWarps][4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int per_rx = a.n_tiles * 8;
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1ull);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= total) break;
+        const uint32_t id = order[it];
+        const int r = (int)(id / (uint32_t)per_rx), rem = (int)(id % (uint32_t)per_rx);
+        render_block<1>(a, r, rem >> 3, rem & 7, 0, sbuf[warp], sid[warp], spl[warp]);
+    }
+}
+
+__global__ void k_queue_keys(RenderArgs a, unsigned long long total, uint32_t* __restrict__ keys) {
+    const unsigned long long id = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= total) return;
+    const int per_rx = a.n_tiles * 8;
+    const int r = (int)(id / per_rx), tile = (int)(id % per_rx) >> 3;
+    const size_t ts = (size_t)r * (a.n_tiles + 1) + tile;
+    const uint32_t len = a.tile_start[ts + 1] - a.tile_start[ts];
+    keys[id] = (uint32_t)__clz((int)(len + 1u));  // 31 - floor(log2(len + 1))
+}
+
 // Cost key of every work item: its tile's list length, heaviest first (bucket
 // 31 - floor(log2(len + 1)), so that an ascending stable sort puts long lists first).
 __global__ void k_batch_keys(BatchArgs b, uint32_t* __restrict__ keys) {
@@ -362,7 +395,24 @@ cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     cudaError_t e = cudaMemsetAsync(&a.st->stats[0], 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     if (p->n_f == 1) {
-        k_render_fwd<1><<<dim3(2 * L.n_tiles, L.n_rx), kThreads, 0, st>>>(a);
+        // persistent: heaviest-first work queue over (receiver, tile, ray block) items
+        const long long n = (long long)L.n_rx * L.n_tiles * 8;
+        uint32_t* keys = at<uint32_t>(ws, L.qkeys);
+        uint32_t* keys2 = at<uint32_t>(ws, L.qkeys2);
+        uint32_t* order = at<uint32_t>(ws, L.qorder);
+        uint32_t* hist = at<uint32_t>(ws, L.qhist);
+        unsigned long long* counter = at<unsigned long long>(ws, L.qcounter);
+        k_queue_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, (unsigned long long)n, keys);
+        if ((e = launch_sort_small_keys(keys, keys2, order, n, 32, hist, st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_queue, kThreads, 0)) != cudaSuccess)
+            return e;
+        const long long ctas_needed = (n + kWarps - 1) / kWarps;
+        const int grid = (int)min((long long)sms * max(per_sm, 1), ctas_needed);
+        k_render_queue<<<grid, kThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
     } else if (p->n_f <= 8) {
         k_render_fwd<8><<<dim3(2 * L.n_tiles, L.n_rx, 1), kThreads, 0, st>>>(a);
     } else {
