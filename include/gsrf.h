@@ -65,7 +65,9 @@ typedef struct {
     float r_rx;                /* radius of the ray-emitting sphere (App. E table: 1.0 m) */
     float eps_T;               /* stop a ray once prod(1 - alpha) < eps_T; 0 = never */
     float alpha_max;           /* clamp on alpha, in (0, 1) (0.99 keeps 1/(1-alpha) finite) */
-    int32_t tile_w, tile_h;    /* rays per tile (App. E: 16 x 16); this build: 16 x 16 */
+    int32_t tile_w, tile_h;    /* rays per tile (App. E: 16 x 16): tile_w 8, 16 or 32, tile_h 4, 8, 16
+                                * or 32, each a multiple of the plan's ray block; at most 64 tiles
+                                * along azimuth and 1024 in all */
 } gsrf_grid;
 
 /* Scene parameters theta, [dev], structure-of-arrays, n Gaussians (Sec. 4.2). */
@@ -88,6 +90,11 @@ typedef struct {
     double f0_hz, df_hz;       /* first frequency and spacing (Hz), f0 > 0 */
     gsrf_grid grid;
     int64_t pair_capacity;     /* room for (tile, Gaussian) instances over all receivers */
+    int32_t ray_block_w;       /* rays a warp renders along azimuth: 4, 8, 16 or 32, the block
+                                * being 32 / ray_block_w high; 0 = 8 (8 x 4) */
+    int32_t stage;             /* candidates a warp stages in shared memory per batch: 16 or 32;
+                                * 0 = 32.  Tile shape, ray block and stage change speed only,
+                                * never results; gsrf_autotune picks them by measurement */
 } gsrf_plan;
 
 /* Bytes of workspace a plan needs (256-byte aligned base required). [host] out. */
@@ -103,7 +110,8 @@ typedef struct {
     size_t status;
     int32_t n_tiles_u, n_tiles_v;
     size_t view;               /* per (receiver, Gaussian) 48-byte records after gsrf_project,
-                                * receiver-major: floats 0-2 mu - r, 3 bounding radius^2,
+                                * receiver-major: floats 0-2 mu - r, 3 D cos(theta) of the
+                                * cone of directions that can reach the Gaussian (culling),
                                 * 4-6 whitened receiver offset, 7-8 e^{-j 2 pi f0 d / c}
                                 * (cos, -sin) with the phase reduced in FP64, 9 the
                                 * per-subcarrier step 2 pi df d / c, 10-11 unused */

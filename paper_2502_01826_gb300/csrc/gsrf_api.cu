@@ -52,8 +52,9 @@ bool make_layout(const gsrf_plan* p, Layout* L) {
     L->pids2 = take(cap * 4);
     L->tile_start = take(nr * (size_t)(L->n_tiles + 1) * 4);
     L->thist = take((size_t)L->pchunks_max * L->n_tiles * 4);
-    // the render's work queue: one item per (receiver, tile, 8 x 4 ray block)
-    const size_t items = nr * (size_t)L->n_tiles * 8;
+    // the render's work queue: one item per (receiver, tile, ray block, subcarrier chunk);
+    // chunks of 8 subcarriers are the most any launch uses
+    const size_t items = nr * (size_t)L->n_tiles * (size_t)(g.tile_w * g.tile_h / 32) * (size_t)((p->n_f + 7) / 8);
     L->qkeys = take(items * 4);
     L->qkeys2 = take(items * 4);
     L->qorder = take(items * 4);
@@ -75,7 +76,9 @@ static gsrf_status check_grid(const gsrf_grid* g) {
     if (!(g->el0_deg >= -90.0f && g->el0_deg <= 90.0f)) return GSRF_ERR_INVALID_ARG;
     if (!(g->r_rx >= 0.0f) || !(g->eps_T >= 0.0f && g->eps_T < 1.0f)) return GSRF_ERR_INVALID_ARG;
     if (!(g->alpha_max > 0.0f && g->alpha_max < 1.0f)) return GSRF_ERR_INVALID_ARG;
-    if (g->tile_w != kTile || g->tile_h != kTile) return GSRF_ERR_UNSUPPORTED;
+    const bool tw_ok = g->tile_w == 8 || g->tile_w == 16 || g->tile_w == 32;
+    const bool th_ok = g->tile_h == 4 || g->tile_h == 8 || g->tile_h == 16 || g->tile_h == 32;
+    if (!tw_ok || !th_ok || g->tile_w * g->tile_h < 32) return GSRF_ERR_UNSUPPORTED;
     const int ntu = (g->n_az + g->tile_w - 1) / g->tile_w, ntv = (g->n_el + g->tile_h - 1) / g->tile_h;
     if (ntu > 64 || ntu * ntv > kMaxTiles) return GSRF_ERR_UNSUPPORTED;
     return GSRF_OK;
@@ -89,7 +92,14 @@ static gsrf_status check_plan(const gsrf_plan* p) {
     if (!(p->f0_hz > 0.0) || !(p->df_hz >= 0.0)) return GSRF_ERR_INVALID_ARG;
     if (p->pair_capacity < 0 || p->pair_capacity > (1ll << 40)) return GSRF_ERR_INVALID_ARG;
     if ((size_t)p->n_gauss * (size_t)p->n_rx >= (1ull << 40)) return GSRF_ERR_INVALID_ARG;
-    return check_grid(&p->grid);
+    const int bw = p->ray_block_w;
+    if (!(bw == 0 || bw == 4 || bw == 8 || bw == 16 || bw == 32)) return GSRF_ERR_INVALID_ARG;
+    if (!(p->stage == 0 || p->stage == 16 || p->stage == 32)) return GSRF_ERR_INVALID_ARG;
+    const gsrf_status s = check_grid(&p->grid);
+    if (s != GSRF_OK) return s;
+    const int w = plan_block_w(p);
+    if (p->grid.tile_w % w != 0 || p->grid.tile_h % (32 / w) != 0) return GSRF_ERR_UNSUPPORTED;
+    return GSRF_OK;
 }
 
 static gsrf_status check_ws(const gsrf_plan* p, const void* ws, size_t ws_bytes, Layout* L) {

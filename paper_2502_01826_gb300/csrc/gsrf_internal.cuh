@@ -184,6 +184,14 @@ cudaError_t launch_signal(const float* rays, int n_rx, int n_f, int n_el, int n_
                           float* out, cudaStream_t st);
 cudaError_t launch_sort_small_keys(const uint32_t* keys, uint32_t* keys_out, uint32_t* vals_out, long long n,
                                    int nbins, uint32_t* hist, cudaStream_t st);
+// Work items of a render launch: item id = ((r * n_tiles + tile) * per_tile + k), k < per_tile
+// (ray block and subcarrier chunk).  Writes the heaviest-first order of the n_rx * n_tiles *
+// per_tile items into the workspace's queue buffers and zeroes the queue counter.
+cudaError_t launch_item_order(const Layout& L, void* ws, int per_tile, uint32_t** order,
+                              unsigned long long** counter, cudaStream_t st);
+// Geometry of the warps' ray blocks: width bw (a power of two, 4..32), height 32 / bw.
+int plan_block_w(const gsrf_plan* p);
+int plan_stage(const gsrf_plan* p);
 // Persistent batched render of n_jobs projected and binned problems (n_f == 1 each).
 size_t batch_workspace_bytes(int n_jobs, const gsrf_plan* plans);
 cudaError_t launch_render_batch(int n_jobs, const gsrf_plan* plans, void* const* workspaces, float* const* outs,
@@ -266,16 +274,16 @@ __device__ __forceinline__ bool bundle_meets(const Bundle& b, float4 c) {
     return cd >= b.cb * c.w - b.sb * dsn - 1e-4f * (c.w + dsn);
 }
 
-// Four planes through the receiver that hold every ray of a warp's 8 x 4 block on
+// Four planes through the receiver that hold every ray of a warp's bw x bh block on
 // their inner side (n.d >= 0): the vertical planes at the block's first and last
 // azimuth, and planes tilted to its lowest and highest elevation; each is moved along
 // the warp axis b until it clears all of the warp's rays (a margin of 1e-6 in n.d).  A
 // ray point x = t d (t >= r_rx > 0) then has n.x >= 0, so an ellipsoid that lies wholly
 // on the outer side of one plane meets no ray of the warp.  Every lane computes the
 // same planes; lane j < 4 writes plane j to the warp's shared slots.
-__device__ __forceinline__ void warp_planes(const gsrf_grid& gr, int u_lo, int v_lo, const Bundle& b,
+__device__ __forceinline__ void warp_planes(const gsrf_grid& gr, int u_lo, int v_lo, int bw, int bh, const Bundle& b,
                                             bool valid, float dx, float dy, float dz, float4* spl) {
-    const int u_hi = min(u_lo + 7, gr.n_az - 1), v_hi = min(v_lo + 3, gr.n_el - 1);
+    const int u_hi = min(u_lo + bw - 1, gr.n_az - 1), v_hi = min(v_lo + bh - 1, gr.n_el - 1);
     const float kDeg = 0.0174532925f;
     const float a0 = (gr.az0_deg + ((float)u_lo + 0.5f) * gr.daz_deg) * kDeg;
     const float a1 = (gr.az0_deg + ((float)u_hi + 0.5f) * gr.daz_deg) * kDeg;

@@ -2,8 +2,8 @@
 // respect to every Gaussian parameter, given G = dL/dRe S + j dL/dIm S per ray.
 //
 // k_render_bwd walks each ray's list back to front from its last composited pair, with
-// the same CTA / warp / staging layout and the same hit decisions (pair_hits) as the
-// forward.  Transmittance is recomputed, not stored: T_k = T_{k+1} e^{+j theta_k} /
+// the same work items (receiver, tile, ray block, subcarrier chunk), warp cone and
+// planes, and the same hit decisions (pair_hits) as the forward.  Transmittance is recomputed, not stored: T_k = T_{k+1} e^{+j theta_k} /
 // (1 - alpha_k), starting from the T the forward left in the ray state.  With
 // z_k = alpha_k psi_k E_k T_k and the suffix R_k = sum_{j>k} z_j (App. D.1, D.2):
 //     dS/dalpha_k = psi_k E_k T_k - R_k / (1 - alpha_k),   dS/dtheta_k = -j R_k,
@@ -49,6 +49,10 @@ struct BwdArgs {
     float om_pi;  // 2 f0 / c
     int n_f;      // frequencies f0 + s df
     float dlt;    // 2 pi df / c
+    int bw_log;   // log2 of the ray-block width (block height 32 / width)
+    int nbx;      // ray blocks per tile along azimuth
+    int per_tile; // work items per tile: ray blocks x subcarrier chunks
+    int nchunk;   // subcarrier chunks of NFC
 };
 
 __device__ __forceinline__ void cp_async16b(void* smem, const void* gmem) {
@@ -91,26 +95,24 @@ __device__ __forceinline__ float reduce_scatter16(float* v, int lane) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-// NFC = 1: one frequency.  NFC > 1: the CTA's lanes take subcarriers fs0 .. fs0 + NFC - 1
-// (fs0 = NFC blockIdx.z) of f0 + s df.  The pair's contribution there is z_k(f0) r_k^s
-// with r_k = e^{-j (2 pi df d_k / c + 2 pi df Gamma_k / c)} (Gamma_k = sum of b dt in front
-// of k), exactly as the forward builds it; each subcarrier keeps its own suffix R, and
-// the transmittance and path phases enter with their own 2 pi f_s / c.  Every chunk adds
-// its share of the gradient to the same accumulators.
+// One warp's work item k of tile `tile` for receiver r: ray block k / nchunk, subcarrier
+// chunk k % nchunk.  NFC = 1: one frequency.  NFC > 1: the lanes take subcarriers
+// fs0 .. fs0 + NFC - 1 (fs0 = NFC chunk) of f0 + s df.  The pair's contribution there is
+// z_k(f0) r_k^s with r_k = e^{-j (2 pi df d_k / c + 2 pi df Gamma_k / c)} (Gamma_k = sum
+// of b dt in front of k), exactly as the forward builds it; each subcarrier keeps its own
+// suffix R, and the transmittance and path phases enter with their own 2 pi f_s / c.
+// Every chunk adds its share of the gradient to the same accumulators.
 template <int NFC>
-__global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
-    __shared__ float4 sbuf[kBW][2][kBB][6];
-    __shared__ uint32_t sid[kBW][2][kBB];
-    __shared__ float4 spl[kBW][4];
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.x >> 1, half = blockIdx.x & 1, r = blockIdx.y;
-    const int fs0 = (int)blockIdx.z * NFC;  // first subcarrier of the chunk
-    const int tu = tile % a.ntu, tv = tile / a.ntu;
-    const int lx = ((warp & 1) << 3) | (lane & 7);
-    const int ly = (half << 3) | ((warp >> 1) << 2) | (lane >> 3);
-    const int u = tu * kTile + lx, v = tv * kTile + ly;
+__device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int k, float4 (*sbuf)[kBB][6],
+                                          uint32_t (*sid)[kBB], float4* spl) {
+    const int lane = threadIdx.x & 31;
     const gsrf_grid& gr = a.gr;
+    const int chunk = k % a.nchunk, blk = k / a.nchunk;
+    const int fs0 = chunk * NFC;  // first subcarrier of the chunk
+    const int bw = 1 << a.bw_log, bh = 32 >> a.bw_log;
+    const int tu = tile % a.ntu, tv = tile / a.ntu;
+    const int u_lo = tu * gr.tile_w + (blk % a.nbx) * bw, v_lo = tv * gr.tile_h + (blk / a.nbx) * bh;
+    const int u = u_lo + (lane & (bw - 1)), v = v_lo + (lane >> a.bw_log);
     const bool valid = u < gr.n_az && v < gr.n_el;
 
     // ray: direction, basis, cone of the warp, state and upstream gradient
@@ -148,8 +150,7 @@ __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
         }
     }
     const Bundle bun = warp_bundle(valid, dx, dy, dz);  // the forward's warp cone and planes
-    warp_planes(gr, tu * kTile + ((warp & 1) << 3), tv * kTile + (half << 3) + ((warp >> 1) << 2), bun, valid, dx,
-                dy, dz, spl[warp]);
+    warp_planes(gr, u_lo, v_lo, bw, bh, bun, valid, dx, dy, dz, spl);
 
     // positions are inside the tile's list; a state that points past it (another plan's,
     // or garbage) is clamped so that no read leaves the list
@@ -173,11 +174,11 @@ __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
             const uint32_t id = a.pids[b0 + lane];
             const float4* vw = reinterpret_cast<const float4*>(view + id);
             const float4 c = __ldg(vw);
-            keep = bundle_meets(bun, c) && planes_meet(spl[warp], c, a.shape + id);
+            keep = bundle_meets(bun, c) && planes_meet(spl, c, a.shape + id);
             if (keep) {
-                sid[warp][bf][lane] = id;
+                sid[bf][lane] = id;
                 const float4* sh = reinterpret_cast<const float4*>(a.shape + id);
-                float4* dst = sbuf[warp][bf][lane];
+                float4* dst = sbuf[bf][lane];
                 dst[0] = c;
                 cp_async16b(dst + 1, vw + 1);
                 cp_async16b(dst + 2, vw + 2);
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
             const int j = 31 - __clz(m);
             m &= ~(1u << j);
             const int pos = (int)(b0 - lo) + j;
-            const float4* rec = sbuf[warp][bf][j];
+            const float4* rec = sbuf[bf][j];
             const float4 v0 = rec[0], v1 = rec[1], s0 = rec[3], s1 = rec[4], s2 = rec[5];
             PairGeo pg;
             bool hit = pos <= last && pair_cone(v0, dx, dy, dz) && pair_hits(v1, s0, s1, s2, dx, dy, dz, r_rx, pg);
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
                 const float alpha = pair_alpha(o, pg.m2r, amax, gw);
                 const bool clamped = o * gw >= amax;
                 float pr, pi;
-                const float4* q4 = reinterpret_cast<const float4*>(a.fle + (size_t)sid[warp][bf][j] * kFle);
+                const float4* q4 = reinterpret_cast<const float4*>(a.fle + (size_t)sid[bf][j] * kFle);
                 {
                     const float4 a0 = __ldg(q4), a1 = __ldg(q4 + 1);
                     pr = a0.x + a0.z * P[0] + a1.x * P[1] + a1.z * P[2];
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
                 go[12] = g_o;
                 go[13] = g_b;
             }
-            float* acc = a.acc + (size_t)sid[warp][bf][j] * kGrad;
+            float* acc = a.acc + (size_t)sid[bf][j] * kGrad;
             const float sq = reduce_scatter32(gq, lane);
             atomicAdd(acc + 14 + lane, sq);
             const float so = reduce_scatter16(go, lane);
@@ -361,6 +362,30 @@ __global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a) {
         __syncwarp();
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Persistent launch: every warp takes work items (receiver, tile, ray block, subcarrier
+// chunk) from one counter, heaviest first, until none is left.
+template <int NFC>
+__global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a, const uint32_t* __restrict__ order,
+                                                          unsigned long long* __restrict__ counter,
+                                                          unsigned long long total) {
+    __shared__ float4 sbuf[kBW][2][kBB][6];
+    __shared__ uint32_t sid[kBW][2][kBB];
+    __shared__ float4 spl[kBW][4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned per_rx = (unsigned)a.n_tiles * (unsigned)a.per_tile;
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1ull);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= total) break;
+        const uint32_t id = order[it];
+        const unsigned rem = id % per_rx;
+        bwd_block<NFC>(a, (int)(id / per_rx), (int)(rem / (unsigned)a.per_tile), (int)(rem % (unsigned)a.per_tile),
+                       sbuf[warp], sid[warp], spl[warp]);
+        __syncwarp();
+    }
 }
 
 // Raw-parameter gradients from the accumulators (one thread per Gaussian, += into the
@@ -466,10 +491,28 @@ cudaError_t launch_render_bwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     a.om_pi = (float)(2.0 * p->f0_hz / kC);
     a.n_f = p->n_f;
     a.dlt = (float)(2.0 * 3.14159265358979323846 * p->df_hz / kC);
+    const int bw = plan_block_w(p);
+    a.bw_log = __builtin_ctz((unsigned)bw);
+    a.nbx = p->grid.tile_w / bw;
+    a.nchunk = p->n_f == 1 ? 1 : (p->n_f + 7) / 8;
+    a.per_tile = (p->grid.tile_w * p->grid.tile_h / 32) * a.nchunk;
+    uint32_t* order = nullptr;
+    unsigned long long* counter = nullptr;
+    if ((e = launch_item_order(L, ws, a.per_tile, &order, &counter, st)) != cudaSuccess) return e;
+    const long long n = (long long)L.n_rx * L.n_tiles * a.per_tile;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if (p->n_f == 1) {
-        k_render_bwd<1><<<dim3(2 * L.n_tiles, L.n_rx), kBThreads, 0, st>>>(a);
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd<1>, kBThreads, 0)) != cudaSuccess)
+            return e;
+        const int grid = (int)max(1ll, min((long long)sms * max(per_sm, 1), (n + kBW - 1) / kBW));
+        k_render_bwd<1><<<grid, kBThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
     } else {
-        k_render_bwd<8><<<dim3(2 * L.n_tiles, L.n_rx, (p->n_f + 7) / 8), kBThreads, 0, st>>>(a);
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd<8>, kBThreads, 0)) != cudaSuccess)
+            return e;
+        const int grid = (int)max(1ll, min((long long)sms * max(per_sm, 1), (n + kBW - 1) / kBW));
+        k_render_bwd<8><<<grid, kBThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
     }
     const unsigned nb = (unsigned)((L.n + 255) / 256);
     k_grad_params<<<nb, 256, 0, st>>>(*g, at<GShape>(ws, L.gshape), acc, g_means, g_log_scales, g_quats,

@@ -1,15 +1,20 @@
 // k_render.cu -- Alg. 1 lines 6-12 ("Blend"), Eq. 14 / App. A.3: per-ray complex
 // front-to-back accumulation over the tile's depth-sorted Gaussians.
 //
-// Layout of the work: a CTA of 4 warps covers half of a 16x16 ray tile (16 x 8 rays),
-// each warp an 8 x 4 block of rays, one ray per thread.  Every warp walks its tile's
-// candidate list on its own, 32 candidates per batch: lane i takes candidate b0 + i,
-// tests its direction cone against the cone of the warp's 32 rays and its ellipsoid
-// against four planes that bound those rays and, if it may be hit, copies its
-// records into the warp's half of a double buffer with cp.async while
-// the warp works on the current batch; the rays then visit only the candidates of the
-// ballot mask, in list order.  Warps never wait for one another and a warp leaves as
-// soon as its 32 rays have terminated (prod(1 - alpha) < eps_T).
+// Layout of the work: a work item is one warp's block of bw x bh = 32 rays (one ray per
+// lane) inside one tile of one receiver, for one chunk of subcarriers.  The tile shape
+// comes from the grid (tile_w x tile_h), the block width from the plan (bw in 4..32,
+// default 8 x 4), so a tile holds (tile_w / bw) (tile_h / bh) blocks.  A persistent wave
+// of CTAs takes items from one counter in heaviest-first order (tile list length), so a
+// warp that finishes early takes the next item.
+//
+// Each warp walks its tile's candidate list on its own, WB (16 or 32, from the plan)
+// candidates per batch: lane i < WB takes candidate b0 + i, tests its direction cone
+// against the cone of the warp's rays and its ellipsoid against four planes that bound
+// those rays and, if it may be hit, copies its records into the warp's half of a double
+// buffer with cp.async while the warp works on the current batch; the rays then visit
+// only the candidates of the ballot mask, in list order.  A warp's item ends as soon as
+// its 32 rays have terminated (prod(1 - alpha) < eps_T).
 //
 // Per candidate and ray (pair_cone / pair_hits, shared with the backward):
 //   (1) direction cone: v lies in the cone of directions that meet the bounding sphere
@@ -27,9 +32,8 @@
 
 namespace gsrf {
 
-constexpr int kWarps = 4;        // warps per CTA: half a 16 x 16 tile (16 x 8 rays)
+constexpr int kWarps = 4;        // warps per CTA, each on its own work items
 constexpr int kThreads = 32 * kWarps;
-constexpr int kWB = 32;          // candidates per warp batch, one per lane
 constexpr int kRec = 6;          // float4 per staged candidate: 3 of View, 3 of GShape
 
 struct RenderArgs {
@@ -49,6 +53,10 @@ struct RenderArgs {
     float om_pi;  // 2 f0 / c: sincospi argument per unit of b dt
     int n_f;      // frequencies f0 + s df
     float dlt;    // 2 pi df / c: subcarrier phase step per metre of excess path
+    int bw_log;   // log2 of the ray-block width bw (block height 32 / bw)
+    int nbx;      // ray blocks per tile along azimuth (tile_w / bw)
+    int per_tile; // work items per tile: ray blocks x subcarrier chunks
+    int nchunk;   // subcarrier chunks
 };
 
 constexpr int kMaxJobs = 96;
@@ -68,14 +76,6 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// Ray of thread t: CTA half h of the 16 x 16 tile holds rows 8h .. 8h+7; each warp an
-// 8 x 4 block of rays so that its lanes see nearly the same candidates.
-__device__ __forceinline__ void cta_ray(int t, int half, int& lx, int& ly) {
-    const int lane = t & 31, w = t >> 5;
-    lx = ((w & 1) << 3) | (lane & 7);
-    ly = (half << 3) | ((w >> 1) << 2) | (lane >> 3);
-}
 
 // Radiance psi of one Gaussian along one ray (Eq. 9) from the folded coefficients q
 // (see kFle) and the ray's basis values: P = (P10, P20, P30), Y = six complex Y_{l,m>0}.
@@ -104,24 +104,25 @@ __device__ __forceinline__ void load_ray(const float* raytab, size_t ray, float&
     Y[10] = t5.x; Y[11] = t5.y;
 }
 
-// One warp renders the 8 x 4 block wq (0..7) of rays of tile `tile` for receiver r: it
-// walks the tile's list in batches of 32 candidates staged into its own buffers
-// (sbuf, sid), without waiting for any other warp.
+// One warp renders work item k (ray block k / nchunk, subcarrier chunk k % nchunk) of
+// tile `tile` for receiver r: it walks the tile's list in batches of WB candidates staged
+// into its own buffers (sbuf, sid), without waiting for any other warp.
 //
 // NFC = 1: one frequency.  NFC > 1: the lanes handle subcarriers s0 .. s0 + NFC - 1
 // (s0 = chunk * NFC); the contribution of a pair at f0 + s df is z0 r^s with
 // r = e^{-j (2 pi df d / c + 2 pi df Gamma / c)}, Gamma = sum over earlier pairs of b dt,
 // because T(f0 + s df) = T(f0) e^{-j s 2 pi df Gamma / c} and E(f0 + s df) =
 // E(f0) e^{-j s 2 pi df d / c}; the powers of r come from one sincos and a recurrence.
-template <int NFC>
-__device__ __forceinline__ void render_block(const RenderArgs& a, int r, int tile, int wq, int chunk,
-                                             float4 (*sbuf)[kWB][kRec], uint32_t (*sid)[kWB], float4* spl) {
+template <int NFC, int WB>
+__device__ __forceinline__ void render_block(const RenderArgs& a, int r, int tile, int k,
+                                             float4 (*sbuf)[WB][kRec], uint32_t (*sid)[WB], float4* spl) {
     const int lane = threadIdx.x & 31;
-    const int tu = tile % a.ntu, tv = tile / a.ntu;
-    const int lx = ((wq & 1) << 3) | (lane & 7);
-    const int ly = ((wq >> 1) << 2) | (lane >> 3);
-    const int u = tu * kTile + lx, v = tv * kTile + ly;
     const gsrf_grid& gr = a.gr;
+    const int chunk = k % a.nchunk, blk = k / a.nchunk;
+    const int bw = 1 << a.bw_log, bh = 32 >> a.bw_log;
+    const int tu = tile % a.ntu, tv = tile / a.ntu;
+    const int u_lo = tu * gr.tile_w + (blk % a.nbx) * bw, v_lo = tv * gr.tile_h + (blk / a.nbx) * bh;
+    const int u = u_lo + (lane & (bw - 1)), v = v_lo + (lane >> a.bw_log);
     const bool valid = u < gr.n_az && v < gr.n_el;
 
     float dx = 0.0f, dy = 0.0f, dz = 1.0f, P[3] = {0.0f, 0.0f, 0.0f}, Y[12];
@@ -129,7 +130,7 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
     for (int i = 0; i < 12; ++i) Y[i] = 0.0f;
     if (valid) load_ray(a.raytab, (size_t)v * gr.n_az + u, dx, dy, dz, P, Y);
     const Bundle bun = warp_bundle(valid, dx, dy, dz);
-    warp_planes(gr, tu * kTile + ((wq & 1) << 3), tv * kTile + ((wq >> 1) << 2), bun, valid, dx, dy, dz, spl);
+    warp_planes(gr, u_lo, v_lo, bw, bh, bun, valid, dx, dy, dz, spl);
 
     const size_t ts = (size_t)r * (a.n_tiles + 1) + tile;
     const long long base0 = a.rx_base[r];
@@ -147,12 +148,12 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
     bool done = !valid;
     unsigned tests = 0, hits = 0;
 
-    // Stage the batch starting at b0 into buffer bf: lane i takes candidate b0 + i,
-    // tests its bounding sphere against the warp's cone and, if it may be hit, copies
-    // its records; returns the mask of candidates that may be hit.
+    // Stage the batch starting at b0 into buffer bf: lane i < WB takes candidate b0 + i,
+    // tests it against the warp's cone and planes and, if it may be hit, copies its
+    // records; returns the mask of candidates that may be hit.
     auto stage = [&](int bf, long long b0) -> uint32_t {
         bool keep = false;
-        if (b0 + lane < hi) {
+        if (lane < WB && b0 + lane < hi) {
             const uint32_t id = a.pids[b0 + lane];
             const float4* vw = reinterpret_cast<const float4*>(view + id);
             const float4 c = __ldg(vw);
@@ -177,11 +178,11 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
     if (!__all_sync(0xffffffffu, done)) {
         int bf = 0;
         uint32_t mask = stage(0, lo);
-        for (long long b0 = lo; b0 < hi; b0 += kWB, bf ^= 1) {
-            const uint32_t next = stage(bf ^ 1, b0 + kWB);  // empty past the end of the list
+        for (long long b0 = lo; b0 < hi; b0 += WB, bf ^= 1) {
+            const uint32_t next = stage(bf ^ 1, b0 + WB);  // empty past the end of the list
             cp_async_wait_prev();
             __syncwarp();
-            const int cnt = (int)min((long long)kWB, hi - b0);
+            const int cnt = (int)min((long long)WB, hi - b0);
             if (!done) {
                 int stop = cnt;
                 for (uint32_t m = mask; m; m &= m - 1) {
@@ -279,24 +280,39 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
     }
 }
 
-// Plain launch: CTA = (half tile, receiver, subcarrier chunk), 4 warps = 4 ray blocks.
-template <int NFC>
-__global__ void __launch_bounds__(kThreads, NFC == 1 ? 8 : 4) k_render_fwd(RenderArgs a) {
-    __shared__ float4 sbuf[kWarps][2][kWB][kRec];
-    __shared__ uint32_t sid[kWarps][2][kWB];
+// Persistent launch of one problem: every warp takes work items (receiver, tile, ray
+// block, subcarrier chunk) from one counter, in heaviest-first order, until none is
+// left; a warp that finishes early takes the next item instead of idling until the
+// other warps of its CTA are done.
+template <int NFC, int WB>
+__global__ void __launch_bounds__(kThreads, NFC == 1 ? 8 : 4) k_render_queue(RenderArgs a,
+                                                                            const uint32_t* __restrict__ order,
+                                                                            unsigned long long* __restrict__ counter,
+                                                                            unsigned long long total) {
+    __shared__ float4 sbuf[kWarps][2][WB][kRec];
+    __shared__ uint32_t sid[kWarps][2][WB];
     __shared__ float4 spl[kWarps][4];
-    const int warp = threadIdx.x >> 5;
-    render_block<NFC>(a, blockIdx.y, blockIdx.x >> 1, (blockIdx.x & 1) * kWarps + warp, blockIdx.z, sbuf[warp],
-                      sid[warp], spl[warp]);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned per_rx = (unsigned)a.n_tiles * (unsigned)a.per_tile;
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1ull);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= total) break;
+        const uint32_t id = order[it];
+        const unsigned rem = id % per_rx;
+        render_block<NFC, WB>(a, (int)(id / per_rx), (int)(rem / (unsigned)a.per_tile), (int)(rem % (unsigned)a.per_tile),
+                              sbuf[warp], sid[warp], spl[warp]);
+    }
 }
 
-// Persistent batched launch: every warp takes work items -- (job, receiver, tile, ray
-// block) -- from one counter, in the heaviest-first order the item sort produced, until
-// none is left.  No warp waits for another.
+// Persistent batched launch over several problems (n_f = 1 each): work items (job,
+// receiver, tile, ray block), same queue discipline.
+template <int WB>
 __global__ void __launch_bounds__(kThreads, 8) k_render_batch(BatchArgs b, const uint32_t* __restrict__ order,
                                                               unsigned long long* __restrict__ counter) {
-    __shared__ float4 sbuf[kWarps][2][kWB][kRec];
-    __shared__ uint32_t sid[kWarps][2][kWB];
+    __shared__ float4 sbuf[kWarps][2][WB][kRec];
+    __shared__ uint32_t sid[kWarps][2][WB];
     __shared__ float4 spl[kWarps][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned long long total = b.item_base[b.n_jobs];
@@ -310,59 +326,66 @@ __global__ void __launch_bounds__(kThreads, 8) k_render_batch(BatchArgs b, const
         while (j + 1 < b.n_jobs && b.item_base[j + 1] <= id) ++j;
         const RenderArgs& a = b.jobs[j];
         const unsigned long long local = id - b.item_base[j];
-        const int per_rx = a.n_tiles * 8;
-        const int r = (int)(local / per_rx), rem = (int)(local % per_rx);
-        render_block<1>(a, r, rem >> 3, rem & 7, 0, sbuf[warp], sid[warp], spl[warp]);
+        const unsigned long long per_rx = (unsigned long long)a.n_tiles * a.per_tile;
+        const unsigned rem = (unsigned)(local % per_rx);
+        render_block<1, WB>(a, (int)(local / per_rx), (int)(rem / (unsigned)a.per_tile),
+                            (int)(rem % (unsigned)a.per_tile), sbuf[warp], sid[warp], spl[warp]);
     }
-}
-
-// Persistent launch of one problem (n_f = 1): like k_render_batch, every warp takes work
-// items (receiver, tile, ray block) from one counter, in the heaviest-first order of
-// k_queue_keys, until none is left; a warp that finishes early takes the next item
-// instead of idling until the other warps of its CTA are done.
-__global__ void __launch_bounds__(kThreads, 8) k_render_queue(RenderArgs a, const uint32_t* __restrict__ order,
-                                                              unsigned long long* __restrict__ counter,
-                                                              unsigned long long total) {
-    __shared__ float4 sbuf[kWarps][2][kWB][kRec];
-    __shared__ uint32_t sid[kWarps][2][kWB];
-    __shared__ float4 spl[kWarps][4];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int per_rx = a.n_tiles * 8;
-    for (;;) {
-        unsigned long long it = 0;
-        if (lane == 0) it = atomicAdd(counter, 1ull);
-        it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= total) break;
-        const uint32_t id = order[it];
-        const int r = (int)(id / (uint32_t)per_rx), rem = (int)(id % (uint32_t)per_rx);
-        render_block<1>(a, r, rem >> 3, rem & 7, 0, sbuf[warp], sid[warp], spl[warp]);
-    }
-}
-
-__global__ void k_queue_keys(RenderArgs a, unsigned long long total, uint32_t* __restrict__ keys) {
-    const unsigned long long id = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= total) return;
-    const int per_rx = a.n_tiles * 8;
-    const int r = (int)(id / per_rx), tile = (int)(id % per_rx) >> 3;
-    const size_t ts = (size_t)r * (a.n_tiles + 1) + tile;
-    const uint32_t len = a.tile_start[ts + 1] - a.tile_start[ts];
-    keys[id] = (uint32_t)__clz((int)(len + 1u));  // 31 - floor(log2(len + 1))
 }
 
 // Cost key of every work item: its tile's list length, heaviest first (bucket
 // 31 - floor(log2(len + 1)), so that an ascending stable sort puts long lists first).
+__global__ void k_item_keys(const uint32_t* __restrict__ tile_start, int n_tiles, int per_tile,
+                            unsigned long long total, uint32_t* __restrict__ keys) {
+    const unsigned long long id = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= total) return;
+    const unsigned long long t = id / (unsigned)per_tile;  // r * n_tiles + tile
+    const size_t ts = (size_t)(t / (unsigned)n_tiles) * (n_tiles + 1) + (size_t)(t % (unsigned)n_tiles);
+    const uint32_t len = tile_start[ts + 1] - tile_start[ts];
+    keys[id] = (uint32_t)__clz((int)(len + 1u));
+}
+
 __global__ void k_batch_keys(BatchArgs b, uint32_t* __restrict__ keys) {
     const unsigned long long id = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= b.item_base[b.n_jobs]) return;
     int j = 0;
     while (j + 1 < b.n_jobs && b.item_base[j + 1] <= id) ++j;
     const RenderArgs& a = b.jobs[j];
-    const unsigned long long local = id - b.item_base[j];
-    const int per_rx = a.n_tiles * 8;
-    const int r = (int)(local / per_rx), tile = (int)(local % per_rx) >> 3;
-    const size_t ts = (size_t)r * (a.n_tiles + 1) + tile;
+    const unsigned long long t = (id - b.item_base[j]) / (unsigned)a.per_tile;
+    const size_t ts = (size_t)(t / (unsigned)a.n_tiles) * (a.n_tiles + 1) + (size_t)(t % (unsigned)a.n_tiles);
     const uint32_t len = a.tile_start[ts + 1] - a.tile_start[ts];
-    keys[id] = 31u - (31u - (uint32_t)__clz((int)(len + 1u)));
+    keys[id] = (uint32_t)__clz((int)(len + 1u));
+}
+
+int plan_block_w(const gsrf_plan* p) { return p->ray_block_w == 0 ? 8 : p->ray_block_w; }
+int plan_stage(const gsrf_plan* p) { return p->stage == 0 ? 32 : p->stage; }
+
+cudaError_t launch_item_order(const Layout& L, void* ws, int per_tile, uint32_t** order,
+                              unsigned long long** counter, cudaStream_t st) {
+    const long long n = (long long)L.n_rx * L.n_tiles * per_tile;
+    uint32_t* keys = at<uint32_t>(ws, L.qkeys);
+    uint32_t* keys2 = at<uint32_t>(ws, L.qkeys2);
+    *order = at<uint32_t>(ws, L.qorder);
+    *counter = at<unsigned long long>(ws, L.qcounter);
+    k_item_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(at<uint32_t>(ws, L.tile_start), L.n_tiles, per_tile,
+                                                             (unsigned long long)n, keys);
+    cudaError_t e = launch_sort_small_keys(keys, keys2, *order, n, 32, at<uint32_t>(ws, L.qhist), st);
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(*counter, 0, sizeof(unsigned long long), st);
+}
+
+// One resident wave of CTAs for a persistent kernel: every SM holds as many as it can
+// run at once, and no more than the items need.
+template <typename K>
+static cudaError_t resident_grid(K kernel, long long items, int* grid) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0)) != cudaSuccess) return e;
+    const long long ctas_needed = (items + kWarps - 1) / kWarps;
+    *grid = (int)max(1ll, min((long long)sms * max(per_sm, 1), ctas_needed));
+    return cudaSuccess;
 }
 
 static RenderArgs render_args(const gsrf_plan* p, const Layout& L, void* ws, float* out, void* ray_state) {
@@ -385,7 +408,23 @@ static RenderArgs render_args(const gsrf_plan* p, const Layout& L, void* ws, flo
     a.om_pi = (float)(2.0 * p->f0_hz / kC);
     a.n_f = p->n_f;
     a.dlt = (float)(2.0 * 3.14159265358979323846 * p->df_hz / kC);
+    const int bw = plan_block_w(p);
+    a.bw_log = __builtin_ctz((unsigned)bw);
+    a.nbx = p->grid.tile_w / bw;
+    const int nfc = p->n_f == 1 ? 1 : (p->n_f <= 8 ? 8 : 16);
+    a.nchunk = (p->n_f + nfc - 1) / nfc;
+    a.per_tile = (p->grid.tile_w * p->grid.tile_h / 32) * a.nchunk;
     return a;
+}
+
+template <int NFC, int WB>
+static cudaError_t launch_queue(const RenderArgs& a, const uint32_t* order, unsigned long long* counter, long long n,
+                                cudaStream_t st) {
+    int grid = 0;
+    cudaError_t e = resident_grid(k_render_queue<NFC, WB>, n, &grid);
+    if (e != cudaSuccess) return e;
+    k_render_queue<NFC, WB><<<grid, kThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_gaussians* g, void* ws,
@@ -394,48 +433,26 @@ cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     (void)g;
     cudaError_t e = cudaMemsetAsync(&a.st->stats[0], 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    if (p->n_f == 1) {
-        // persistent: heaviest-first work queue over (receiver, tile, ray block) items
-        const long long n = (long long)L.n_rx * L.n_tiles * 8;
-        uint32_t* keys = at<uint32_t>(ws, L.qkeys);
-        uint32_t* keys2 = at<uint32_t>(ws, L.qkeys2);
-        uint32_t* order = at<uint32_t>(ws, L.qorder);
-        uint32_t* hist = at<uint32_t>(ws, L.qhist);
-        unsigned long long* counter = at<unsigned long long>(ws, L.qcounter);
-        k_queue_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, (unsigned long long)n, keys);
-        if ((e = launch_sort_small_keys(keys, keys2, order, n, 32, hist, st)) != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
-        int dev = 0, sms = 0, per_sm = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_queue, kThreads, 0)) != cudaSuccess)
-            return e;
-        const long long ctas_needed = (n + kWarps - 1) / kWarps;
-        const int grid = (int)min((long long)sms * max(per_sm, 1), ctas_needed);
-        k_render_queue<<<grid, kThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
-    } else if (p->n_f <= 8) {
-        k_render_fwd<8><<<dim3(2 * L.n_tiles, L.n_rx, 1), kThreads, 0, st>>>(a);
-    } else {
-        k_render_fwd<16><<<dim3(2 * L.n_tiles, L.n_rx, (p->n_f + 15) / 16), kThreads, 0, st>>>(a);
-    }
-    return cudaGetLastError();
+    uint32_t* order = nullptr;
+    unsigned long long* counter = nullptr;
+    if ((e = launch_item_order(L, ws, a.per_tile, &order, &counter, st)) != cudaSuccess) return e;
+    const long long n = (long long)L.n_rx * L.n_tiles * a.per_tile;
+    const bool wb16 = plan_stage(p) == 16;
+    if (p->n_f == 1) return wb16 ? launch_queue<1, 16>(a, order, counter, n, st) : launch_queue<1, 32>(a, order, counter, n, st);
+    if (p->n_f <= 8) return wb16 ? launch_queue<8, 16>(a, order, counter, n, st) : launch_queue<8, 32>(a, order, counter, n, st);
+    return wb16 ? launch_queue<16, 16>(a, order, counter, n, st) : launch_queue<16, 32>(a, order, counter, n, st);
 }
 
-}  // namespace gsrf
-
-namespace gsrf {
-
 static long long batch_items(int n_jobs, const gsrf_plan* plans) {
-    long long t = 0;
+    long long n = 0;
     for (int j = 0; j < n_jobs; ++j) {
         Layout L;
         make_layout(&plans[j], &L);
-        t += (long long)L.n_rx * L.n_tiles * 8;
+        n += (long long)L.n_rx * L.n_tiles * (plans[j].grid.tile_w * plans[j].grid.tile_h / 32);
     }
-    return t;
+    return n;
 }
 
-// batch workspace: keys, sorted keys, order, histogram, counter
 size_t batch_workspace_bytes(int n_jobs, const gsrf_plan* plans) {
     const long long n = batch_items(n_jobs, plans);
     const long long chunks = (n + kChunk - 1) / kChunk;
@@ -453,7 +470,7 @@ cudaError_t launch_render_batch(int n_jobs, const gsrf_plan* plans, void* const*
         make_layout(&plans[j], &L);
         b.jobs[j] = render_args(&plans[j], L, workspaces[j], outs[j], nullptr);
         b.item_base[j] = base;
-        base += (unsigned long long)L.n_rx * L.n_tiles * 8;
+        base += (unsigned long long)L.n_rx * L.n_tiles * b.jobs[j].per_tile;
         cudaError_t e = cudaMemsetAsync(&b.jobs[j].st->stats[0], 0, 2 * sizeof(unsigned long long), st);
         if (e != cudaSuccess) return e;
     }
@@ -473,15 +490,14 @@ cudaError_t launch_render_batch(int n_jobs, const gsrf_plan* plans, void* const*
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    // one resident wave: every SM holds as many CTAs as it can run at once
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_batch, kThreads, 0)) != cudaSuccess)
-        return e;
-    const long long ctas_needed = (n + kWarps - 1) / kWarps;
-    const int grid = (int)min((long long)sms * max(per_sm, 1), ctas_needed);
-    k_render_batch<<<grid, kThreads, 0, st>>>(b, order, counter);
+    int grid = 0;
+    if (plan_stage(&plans[0]) == 16) {
+        if ((e = resident_grid(k_render_batch<16>, n, &grid)) != cudaSuccess) return e;
+        k_render_batch<16><<<grid, kThreads, 0, st>>>(b, order, counter);
+    } else {
+        if ((e = resident_grid(k_render_batch<32>, n, &grid)) != cudaSuccess) return e;
+        k_render_batch<32><<<grid, kThreads, 0, st>>>(b, order, counter);
+    }
     return cudaGetLastError();
 }
 

@@ -67,11 +67,13 @@ class Renderer:
     it needed more room (``ensure_capacity``)."""
 
     def __init__(self, n_gauss: int, n_rx: int, grid: L.gsrf_grid, f0_hz: float, df_hz: float = 0.0,
-                 n_f: int = 1, pair_capacity: int | None = None, device="cuda"):
+                 n_f: int = 1, pair_capacity: int | None = None, device="cuda", ray_block_w: int = 0,
+                 stage: int = 0):
         self.device = torch.device(device)
         if pair_capacity is None:
             pair_capacity = max(1024, 8 * n_gauss * n_rx)
-        self.plan = L.gsrf_plan(n_gauss, n_rx, n_f, f0_hz, df_hz, grid, int(pair_capacity))
+        self.plan = L.gsrf_plan(n_gauss, n_rx, n_f, f0_hz, df_hz, grid, int(pair_capacity), int(ray_block_w),
+                                int(stage))
         self._alloc()
 
     def _alloc(self):

@@ -49,8 +49,9 @@ def test_struct_layouts_match_header(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\\n", sizeof(gsrf_grid), sizeof(gsrf_gaussians), sizeof(gsrf_plan),
          sizeof(gsrf_layout), sizeof(gsrf_run_status));
-  printf("%zu %zu %zu %zu %zu\\n", offsetof(gsrf_plan, f0_hz), offsetof(gsrf_plan, grid),
-         offsetof(gsrf_plan, pair_capacity), offsetof(gsrf_run_status, stats), offsetof(gsrf_layout, view));
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", offsetof(gsrf_plan, f0_hz), offsetof(gsrf_plan, grid),
+         offsetof(gsrf_plan, pair_capacity), offsetof(gsrf_run_status, stats), offsetof(gsrf_layout, view),
+         offsetof(gsrf_plan, ray_block_w), offsetof(gsrf_plan, stage));
   return 0;
 }
 """)
@@ -62,7 +63,8 @@ int main(void) {
     assert sizes == [C.sizeof(L.gsrf_grid), C.sizeof(L.gsrf_gaussians), C.sizeof(L.gsrf_plan),
                      C.sizeof(L.gsrf_layout), C.sizeof(L.gsrf_run_status)]
     assert offs == [L.gsrf_plan.f0_hz.offset, L.gsrf_plan.grid.offset, L.gsrf_plan.pair_capacity.offset,
-                    L.gsrf_run_status.stats.offset, L.gsrf_layout.view.offset]
+                    L.gsrf_run_status.stats.offset, L.gsrf_layout.view.offset, L.gsrf_plan.ray_block_w.offset,
+                    L.gsrf_plan.stage.offset]
 
 
 def plan(n=1000, n_rx=4, n_az=360, n_el=90, cap=100000, **kw):
@@ -99,10 +101,38 @@ def test_invalid_plans_rejected_synchronously(lib, bad):
 
 def test_unsupported_configurations(lib):
     sz = C.c_size_t()
-    p = plan(grid=dict(tile_w=8))
-    assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_ERR_UNSUPPORTED
+    for tw, th in ((12, 16), (16, 12), (64, 16), (8, 2)):  # tile sides outside 8|16|32 x 4|8|16|32
+        p = plan(grid=dict(tile_w=tw, tile_h=th))
+        assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_ERR_UNSUPPORTED, (tw, th)
     p = plan(n_az=2000)  # more than 64 azimuth tiles
     assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_ERR_UNSUPPORTED
+    p = plan(grid=dict(tile_w=8, tile_h=16))
+    p.ray_block_w = 16  # a 16 x 2 ray block does not tile an 8-wide tile
+    assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_ERR_UNSUPPORTED
+    p = plan(grid=dict(tile_w=32, tile_h=4))
+    p.ray_block_w = 4  # a 4 x 8 ray block does not tile a 4-high tile
+    assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("tw,th,bw,stage", [(8, 16, 8, 16), (32, 8, 32, 32), (16, 16, 4, 0), (32, 32, 16, 16),
+                                            (16, 4, 8, 32)])
+def test_tile_shapes_ray_blocks_and_stages_accepted(lib, tw, th, bw, stage):
+    sz = C.c_size_t()
+    p = plan(grid=dict(tile_w=tw, tile_h=th))
+    p.ray_block_w, p.stage = bw, stage
+    assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_OK
+    lay = L.gsrf_layout()
+    assert lib.gsrf_workspace_layout(C.byref(p), C.byref(lay)) == L.GSRF_OK
+    assert (lay.n_tiles_u, lay.n_tiles_v) == (-(-360 // tw), -(-90 // th))
+
+
+@pytest.mark.parametrize("field,value", [("ray_block_w", 2), ("ray_block_w", 12), ("ray_block_w", 64),
+                                         ("stage", 8), ("stage", 24), ("stage", -1)])
+def test_bad_ray_block_or_stage_rejected(lib, field, value):
+    sz = C.c_size_t()
+    p = plan()
+    setattr(p, field, value)
+    assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_ERR_INVALID_ARG
 
 
 def test_calls_reject_bad_pointers_before_launch(lib):
