@@ -181,6 +181,27 @@ def oracle_sample(cfg, budget_s: float = 12.0, threads: int | None = None):
 
 # ------------------------------------------------------------------ our arm
 
+def split_grid(cfg, R):
+    """The workload's grid with the tile shape R's plan uses."""
+    from paper_2502_01826_gb300.render import make_grid
+    return make_grid(**cfg["grid"], tile_w=R.plan.grid.tile_w, tile_h=R.plan.grid.tile_h)
+
+
+def autotune(R, p, rx, tx, args, reps):
+    """Tune R's work split on its own problem (gsrf_autotune), outside any timed region;
+    returns the choice and the default split's times, or None with --no-tune."""
+    if args.no_tune:
+        return None
+    cap = R.plan.pair_capacity
+    R.plan.pair_capacity = 3 * cap  # room for the small-tile candidates' extra pairs
+    R._alloc()
+    best, table = R.autotune(p, rx, tx, reps=reps)
+    dflt = [t for t in table if (t["tile_w"], t["tile_h"], t["ray_block_w"], t["stage"]) == (16, 16, 8, 32)]
+    return {"best": best, "default_16x16_8x4_32": dflt[0] if dflt else None, "candidates": len(table),
+            "what": "median of %d event-timed runs per candidate: project + bin per tile shape, render per "
+                    "(tile shape, ray block, stage)" % reps}
+
+
 def run_ours(args, ws, rank):
     import numpy as np
     import torch
@@ -202,6 +223,12 @@ def run_ours(args, ws, rank):
     out = torch.empty(R.out_shape(), dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
+    # algorithmic candidate tests: those of the paper's 16 x 16 tiles (App. E), counted
+    # once with the default split, whatever split the timed steps use
+    R.render_fwd(p, out)
+    torch.cuda.synchronize()
+    tests_16x16 = int(R.status().stats[0])
+    tune = autotune(R, p, rx, tx, args, reps=3)
 
     def step(ev=None):
         if ev:
@@ -243,15 +270,17 @@ def run_ours(args, ws, rank):
     value = sum_over_ranks(pairs_per_step * args.steps, ws) / total_s
     spectra_s = sum_over_ranks(n_rx * args.steps, ws) / total_s
 
-    # the same work as 64 plain single-receiver launches
-    Rp = Renderer(K, 1, grid, cfg["f0"])
+    # the same work as 64 plain single-receiver launches, with the same split
+    grid1 = split_grid(cfg, R)
+    Rp = Renderer(K, 1, grid1, cfg["f0"], ray_block_w=R.plan.ray_block_w, stage=R.plan.stage)
     need = 0
     for r in range(n_rx):
         Rp.project(p, rx[r:r + 1], tx)
         Rp.bin()
         s = Rp.status()
         need = max(need, s.required_pairs)
-    Rp = Renderer(K, 1, grid, cfg["f0"], pair_capacity=int(need * 1.05) + 1024)
+    Rp = Renderer(K, 1, grid1, cfg["f0"], pair_capacity=int(need * 1.05) + 1024, ray_block_w=R.plan.ray_block_w,
+                  stage=R.plan.stage)
     out1 = torch.empty(Rp.out_shape(), dtype=torch.float32, device=dev)
 
     def plain_step():
@@ -316,7 +345,7 @@ def run_ours(args, ws, rank):
     peak_tflops = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
     render_ms = float(stage[:, 2].mean())
     stage_ms = {n: float(stage[:, j].mean()) for j, n in enumerate(["project", "bin", "render", "signal"])}
-    flops = tests_per_step * FLOP_TEST + (pairs_per_step) * FLOP_HIT
+    flops = tests_16x16 * FLOP_TEST + (pairs_per_step) * FLOP_HIT
     achieved = flops / (render_ms * 1e-3) / 1e12
     clocks = clk.summary()
 
@@ -328,6 +357,10 @@ def run_ours(args, ws, rank):
                    "n_gauss": K, "n_rx": n_rx, "grid": "360x90",
                    "f0_hz": cfg["f0"], "pairs_per_step": pairs_per_step,
                    "candidate_tests_per_step": tests_per_step,
+                   "candidate_tests_16x16_tiles": tests_16x16,
+                   "split": {"tile": "%dx%d" % (R.plan.grid.tile_w, R.plan.grid.tile_h),
+                             "ray_block": "%dx%d" % (R.plan.ray_block_w or 8, 32 // (R.plan.ray_block_w or 8)),
+                             "stage": R.plan.stage or 32, "autotuned": tune is not None},
                    "tile_gaussian_pairs_binned_per_step": binned_per_step,
                    "l2": "flushed between timed steps (256 MB write, outside the events)",
                    "parallelism": "replicas: each rank renders its own 64 receivers" if ws > 1 else "1 GPU"},
@@ -343,6 +376,7 @@ def run_ours(args, ws, rank):
                      "flop_per_launch": flops},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": 1e3 * sum(t_e2e) / len(t_e2e)},
+        "autotune": tune,
         "persistent": persistent,
         "fwd_bwd": fwd_bwd,
         "csi": csi,
@@ -403,11 +437,11 @@ def persistent_leg(args, cfg, p, rx, tx, R, flush, pairs_per_step):
     ms_g = _time_steps(g.replay, args.steps, flush)
     # 64 single-receiver jobs, one persistent launch
     n_rx = rx.shape[0]
-    grid = make_grid(**cfg["grid"])
+    grid = split_grid(cfg, R)
     K = cfg["scene"]["means"].shape[0]
     jobs = []
     for r in range(n_rx):
-        Rj = Renderer(K, 1, grid, cfg["f0"], pair_capacity=1024)
+        Rj = Renderer(K, 1, grid, cfg["f0"], pair_capacity=1024, ray_block_w=R.plan.ray_block_w, stage=R.plan.stage)
         Rj.ensure_capacity(p, rx[r:r + 1], tx)
         jobs.append(Rj)
     Bj = BatchRender(jobs)
@@ -457,12 +491,27 @@ def uneven_leg(args, flush, max_records=1.5e8):
         load += rec
     if cur:
         waves.append(cur)
+    # one tuned split per scene, measured on its first request
+    splits = {}
+    for i, q in enumerate(reqs):
+        si = q["scene"]
+        if si in splits or args.no_tune:
+            continue
+        R = Renderer(Ks[si], q["rx"].shape[0], grid, q["f0"], pair_capacity=1024)
+        rx = torch.tensor(q["rx"], device="cuda")
+        tx = torch.tensor(q["tx"], device="cuda")
+        R.ensure_capacity(scenes[si], rx, tx)
+        t = autotune(R, scenes[si], rx, tx, args, reps=1)
+        splits[si] = (t["best"]["tile_w"], t["best"]["tile_h"], t["best"]["ray_block_w"], t["best"]["stage"])
+        del R
     lat, pairs_total, t_total = [], 0, 0.0
     for wv in waves:
         jobs = []
         for i in wv:
             q = reqs[i]
-            R = Renderer(Ks[q["scene"]], q["rx"].shape[0], grid, q["f0"], pair_capacity=1024)
+            tw, th, bw, stg = splits.get(q["scene"], (16, 16, 0, 0))
+            R = Renderer(Ks[q["scene"]], q["rx"].shape[0], make_grid(**cfg["grid"], tile_w=tw, tile_h=th), q["f0"],
+                         pair_capacity=1024, ray_block_w=bw, stage=stg)
             rx = torch.tensor(q["rx"], device="cuda")
             tx = torch.tensor(q["tx"], device="cuda")
             R.ensure_capacity(scenes[q["scene"]], rx, tx)
@@ -488,7 +537,8 @@ def uneven_leg(args, flush, max_records=1.5e8):
     return {"workload": cfg["name"], "requests": len(reqs), "waves": len(waves),
             "receivers": int(sum(q["rx"].shape[0] for q in reqs)), "gaussian_counts": Ks,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "pairs_per_s": pairs_total / t_total, "total_s": t_total}
+            "pairs_per_s": pairs_total / t_total, "total_s": t_total,
+            "splits_per_scene": {str(k): "%dx%d tiles, %d-wide ray block, stage %d" % v for k, v in splits.items()}}
 
 
 def train_leg(args, ws, flush):
@@ -517,6 +567,7 @@ def train_leg(args, ws, flush):
     p = {k: v.clone().requires_grad_(True) for k, v in to_device(cfg["scene"]).items()}
     R = Renderer(K, n_rx, grid, cfg["f0"])
     R.ensure_capacity({k: v.detach() for k, v in p.items()}, rx, tx)
+    tune = autotune(R, {k: v.detach() for k, v in p.items()}, rx, tx, args, reps=2)
     n = S_gt.numel() // 2
 
     def step():
@@ -545,6 +596,7 @@ def train_leg(args, ws, flush):
     return {"workload": cfg["name"], "n_gauss": K, "n_rx": n_rx, "ms_per_step": ms,
             "pairs_per_step": pairs, "pairs_per_s": sum_over_ranks(pairs * args.steps, ws) / t,
             "spectra_per_s": sum_over_ranks(n_rx * args.steps, ws) / t,
+            "split": tune["best"] if tune else None,
             "what": "forward + complex-MSE loss + hand-written backward to all parameters"}
 
 
@@ -575,6 +627,7 @@ def csi_leg(args, ws, flush):
     R = Renderer(K, n_rx, grid, cfg["f0"], df_hz=cfg["df"], n_f=cfg["n_f"])
     pd = {k: v.detach() for k, v in p.items()}
     R.ensure_capacity(pd, rx, tx)
+    tune = autotune(R, pd, rx, tx, args, reps=2)
     out = torch.empty(R.out_shape(), dtype=torch.float32, device="cuda")
 
     def fwd():
@@ -607,6 +660,7 @@ def csi_leg(args, ws, flush):
                     "csi_values_per_s": sum_over_ranks(n_csi * args.steps, ws) / tf},
             "fwd_bwd": {"ms_per_step": ms_fb, "pairs_per_s": sum_over_ranks(pairs * args.steps, ws) / tfb,
                         "csi_values_per_s": sum_over_ranks(n_csi * args.steps, ws) / tfb},
+            "split": tune["best"] if tune else None,
             "what": "per composited pair all 64 subcarriers; loss on the complex CSI"}
 
 
@@ -621,6 +675,8 @@ def main():
                     "only for small profiling runs)")
     ap.add_argument("--no-train", action="store_true", help="skip the training and CSI legs")
     ap.add_argument("--uneven", action="store_true", help="add the uneven serving-stress leg (slow setup)")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default work split (16 x 16 tiles, 8 x 4 "
+                    "rays per warp, 32 candidates per stage) instead of autotuning it")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

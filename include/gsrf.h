@@ -215,6 +215,33 @@ typedef struct {
 gsrf_status gsrf_read_status(const void *workspace, size_t ws_bytes, gsrf_run_status *out,
                              void *stream);
 
+/* Autotuner of the work split (tile shape, rays per warp block, candidates per
+ * shared-memory stage), which changes speed, never results.  The paper fixes 16 x 16
+ * tiles (App. E) and has no tuner; this is a property of this library.  For the
+ * caller's own problem, on the caller's stream, it tries the tile shapes 16x16, 32x8,
+ * 16x8, 8x16, 32x16, 16x32, 32x32 and 8x8 (each timed over gsrf_project + gsrf_bin).
+ * Within each tile shape it tries every ray block width 4, 8, 16 or 32 that tiles it and
+ * stages of 16 and 32 candidates (each timed over gsrf_render_fwd).  Every time is the
+ * median of `reps` event-timed runs after one untimed run.  best gets the split with the
+ * smallest sum of the two times; results (up to max_results, may be NULL when
+ * max_results is 0) get every measurement, and n_results their number.
+ *   plan, g, rx_pos, tx_pos as for gsrf_render; workspace [dev] of at least
+ *   gsrf_autotune_workspace_size bytes; out_rays [dev] as for gsrf_render_fwd (holds the
+ *   last candidate's rays).  Tile shapes whose tiles exceed the grid limits or whose
+ *   pairs exceed plan.pair_capacity are skipped; GSRF_ERR_CAPACITY if all are.  The call
+ *   synchronises the stream and must not be captured into a graph.  To use the choice,
+ *   copy best into plan.grid.tile_w / tile_h, plan.ray_block_w and plan.stage. */
+typedef struct {
+    int32_t tile_w, tile_h, ray_block_w, stage;
+    float project_bin_ms;      /* gsrf_project + gsrf_bin with this tile shape */
+    float render_ms;           /* gsrf_render_fwd with this tile shape, ray block and stage */
+} gsrf_tune_result;
+gsrf_status gsrf_autotune_workspace_size(const gsrf_plan *plan, size_t *bytes);
+gsrf_status gsrf_autotune(const gsrf_plan *plan, const gsrf_gaussians *g, const float *rx_pos,
+                          const float *tx_pos, void *workspace, size_t ws_bytes, float *out_rays,
+                          int32_t reps, gsrf_tune_result *results, int32_t max_results,
+                          int32_t *n_results, gsrf_tune_result *best, void *stream);
+
 /* gsrf_render without a caller-supplied workspace, for callers that cannot allocate
  * device memory: hosts that forbid allocation once running (real-time or embedded
  * loops), plugins inside an application whose allocator owns all device memory, code

@@ -11,7 +11,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 SO = os.path.join(PKG, "libgsrf.so")
-SOURCES = ["gsrf_api.cu", "k_project.cu", "k_bin.cu", "k_render.cu", "k_signal.cu", "k_backward.cu", "gsrf_static.cu"]
+SOURCES = ["gsrf_api.cu", "k_project.cu", "k_bin.cu", "k_render.cu", "k_signal.cu", "k_backward.cu", "gsrf_static.cu",
+           "gsrf_tune.cu"]
 HEADERS = ["gsrf_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -22,7 +22,7 @@ SIG_COMPLEX_SUM, SIG_RSSI_DB, SIG_POWER_SUM, SIG_SPECTRUM_MAG = 0, 1, 2, 3
 EXPORTS = ["gsrf_workspace_size", "gsrf_workspace_layout", "gsrf_ray_state_bytes", "gsrf_project",
            "gsrf_bin", "gsrf_render_fwd", "gsrf_render_bwd", "gsrf_render", "gsrf_received_signal",
            "gsrf_read_status", "gsrf_render_static", "gsrf_batch_workspace_size", "gsrf_render_batch",
-           "gsrf_version"]
+           "gsrf_autotune_workspace_size", "gsrf_autotune", "gsrf_version"]
 GSRF_MAX_BATCH_JOBS = 96
 
 
@@ -53,6 +53,11 @@ class gsrf_layout(C.Structure):
     _fields_ = [("pair_keys", C.c_size_t), ("pair_ids", C.c_size_t), ("rx_pair_base", C.c_size_t),
                 ("tile_start", C.c_size_t), ("status", C.c_size_t), ("n_tiles_u", C.c_int32),
                 ("n_tiles_v", C.c_int32), ("view", C.c_size_t)]
+
+
+class gsrf_tune_result(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("ray_block_w", C.c_int32), ("stage", C.c_int32),
+                ("project_bin_ms", C.c_float), ("render_ms", C.c_float)]
 
 
 class gsrf_run_status(C.Structure):
@@ -94,6 +99,9 @@ def load(build_if_missing: bool = False):
     L.gsrf_render_static.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, vp, vp, P(gsrf_run_status), vp]
     L.gsrf_batch_workspace_size.argtypes = [C.c_int32, P(gsrf_plan), P(C.c_size_t)]
     L.gsrf_render_batch.argtypes = [C.c_int32, P(gsrf_plan), P(vp), P(C.c_size_t), P(vp), vp, sz, vp]
+    L.gsrf_autotune_workspace_size.argtypes = [P(gsrf_plan), P(C.c_size_t)]
+    L.gsrf_autotune.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, vp, vp, sz, vp, C.c_int32,
+                                P(gsrf_tune_result), C.c_int32, P(C.c_int32), P(gsrf_tune_result), vp]
     L.gsrf_version.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("gsrf_ray_state_bytes", "gsrf_version"):

@@ -120,6 +120,30 @@ class Renderer:
                self.ws_bytes, _ptr(out), _ptr(ray_state), _stream(stream))
         return out
 
+    def autotune(self, params: dict, rx: torch.Tensor, tx: torch.Tensor, reps: int = 3, stream=None):
+        """Measure the work splits on this problem (gsrf_autotune) and adopt the fastest:
+        the plan's tile shape, ray block and stage change and the workspace is re-allocated
+        (and its pair capacity re-fitted) for them.  Returns (best, every measurement) as
+        dicts of tile_w, tile_h, ray_block_w, stage, project_bin_ms, render_ms."""
+        nbytes = C.c_size_t()
+        L.call("gsrf_autotune_workspace_size", C.byref(self.plan), C.byref(nbytes))
+        ws = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        out = torch.empty(self.out_shape(), dtype=torch.float32, device=self.device)
+        cap = 128
+        results = (L.gsrf_tune_result * cap)()
+        n = C.c_int32()
+        best = L.gsrf_tune_result()
+        gs = gaussians_struct(params)
+        L.call("gsrf_autotune", C.byref(self.plan), C.byref(gs), _ptr(rx), _ptr(tx), _ptr(ws), nbytes.value,
+               _ptr(out), int(reps), results, cap, C.byref(n), C.byref(best), _stream(stream))
+        as_dict = lambda r: {k: getattr(r, k) for k, _ in L.gsrf_tune_result._fields_}
+        del ws, out
+        self.plan.grid.tile_w, self.plan.grid.tile_h = best.tile_w, best.tile_h
+        self.plan.ray_block_w, self.plan.stage = best.ray_block_w, best.stage
+        self._alloc()
+        self.ensure_capacity(params, rx, tx)
+        return as_dict(best), [as_dict(results[i]) for i in range(min(n.value, cap))]
+
     def render_bwd(self, params: dict, ray_state: torch.Tensor, grad_rays: torch.Tensor, grads: dict,
                    stream=None):
         """Add the gradients of sum Re(conj(grad_rays) S) to ``grads`` (same keys and

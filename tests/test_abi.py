@@ -150,3 +150,29 @@ def test_calls_reject_bad_pointers_before_launch(lib):
     assert lib.gsrf_received_signal(None, 1, 1, 1, 1, 0, None, None) == L.GSRF_ERR_INVALID_ARG
     assert lib.gsrf_received_signal(C.c_void_p(256), 1, 1, 1, 1, 9, C.c_void_p(256), None) == \
         L.GSRF_ERR_INVALID_ARG
+
+
+def test_autotune_sizing_and_argument_checks(lib):
+    p = plan()
+    a, b = C.c_size_t(), C.c_size_t()
+    assert lib.gsrf_workspace_size(C.byref(p), C.byref(a)) == L.GSRF_OK
+    assert lib.gsrf_autotune_workspace_size(C.byref(p), C.byref(b)) == L.GSRF_OK
+    assert b.value >= a.value
+    for tw, th in ((32, 8), (8, 8), (32, 32)):  # every candidate tile shape fits the tuner's workspace
+        q = plan(grid=dict(tile_w=tw, tile_h=th))
+        assert lib.gsrf_workspace_size(C.byref(q), C.byref(a)) == L.GSRF_OK
+        assert b.value >= a.value
+    g = L.gsrf_gaussians(1000, None, None, None, None, None, None)
+    best = L.gsrf_tune_result()
+    res = (L.gsrf_tune_result * 4)()
+    n = C.c_int32()
+    dev = C.c_void_p(4096)
+    # null workspace, zero repetitions, results wanted without a buffer, no best
+    assert lib.gsrf_autotune(C.byref(p), C.byref(g), dev, dev, None, b.value, dev, 3, res, 4, C.byref(n),
+                             C.byref(best), None) == L.GSRF_ERR_INVALID_ARG
+    assert lib.gsrf_autotune(C.byref(p), C.byref(g), dev, dev, dev, b.value, dev, 0, res, 4, C.byref(n),
+                             C.byref(best), None) == L.GSRF_ERR_INVALID_ARG
+    assert lib.gsrf_autotune(C.byref(p), C.byref(g), dev, dev, dev, b.value, dev, 3, None, 4, C.byref(n),
+                             C.byref(best), None) == L.GSRF_ERR_INVALID_ARG
+    assert lib.gsrf_autotune(C.byref(p), C.byref(g), dev, dev, dev, b.value, dev, 3, res, 4, C.byref(n),
+                             None, None) == L.GSRF_ERR_INVALID_ARG
