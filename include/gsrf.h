@@ -95,6 +95,11 @@ typedef struct {
     int32_t stage;             /* candidates a warp stages in shared memory per batch: 16 or 32;
                                 * 0 = 32.  Tile shape, ray block and stage change speed only,
                                 * never results; gsrf_autotune picks them by measurement */
+    int32_t ckpt_every;        /* transmittance checkpoints for the backward: 0 = none, else K, a
+                                * multiple of 32 -- the forward keeps every ray's transmittance
+                                * in front of tile-list positions K, 2K, ... (ckpt_slots of them)
+                                * and the backward re-anchors its recomputed transmittance there */
+    int32_t ckpt_slots;        /* checkpoints kept per ray, 1..64 when ckpt_every > 0 */
 } gsrf_plan;
 
 /* Bytes of workspace a plan needs (256-byte aligned base required). [host] out. */
@@ -141,8 +146,9 @@ gsrf_status gsrf_bin(const gsrf_plan *plan, void *workspace, size_t ws_bytes, vo
  * of the chord beyond r_rx (App. A.2), evaluates the Fourier-Legendre radiance and
  * accumulates S += alpha psi e^{-j phi} T, T *= (1 - alpha) e^{-j theta}.
  *   out_rays  [dev] [n_rx][n_f][n_el][n_az][2]  per-ray received signal S.
- *   ray_state [dev] NULL, or gsrf_ray_state_bytes(plan) bytes (32 per ray, 16-byte
- *             aligned) that the backward needs. */
+ *   ray_state [dev] NULL, or gsrf_ray_state_bytes(plan) bytes (16-byte aligned) that the
+ *             backward needs: 32 per ray, plus 16 per ray and checkpoint slot when
+ *             plan.ckpt_every > 0. */
 gsrf_status gsrf_render_fwd(const gsrf_plan *plan, const gsrf_gaussians *g, void *workspace,
                             size_t ws_bytes, float *out_rays, void *ray_state, void *stream);
 size_t gsrf_ray_state_bytes(const gsrf_plan *plan);
@@ -159,7 +165,10 @@ size_t gsrf_ray_state_bytes(const gsrf_plan *plan);
  *   (+=); any may be NULL.  The gradient of the opacity is taken through its sigmoid, of
  *   the rotation through the quaternion's normalisation, of the scales through exp.
  *   Hit decisions that sit on the integer steps of the method (splatting, the 3-sigma
- *   boundary, the early stop) carry no gradient.  With n_f > 1 every subcarrier
+ *   boundary, the early stop) carry no gradient.  With plan.ckpt_every = K > 0 the
+ *   recomputed transmittance is replaced by the forward's own at every checkpoint the
+ *   walk crosses, so division by (1 - alpha) never runs over more than K list positions
+ *   (the per-tile checkpointing of deep scenes).  With n_f > 1 every subcarrier
  *   f0 + s df contributes with its own suffix sum and its own 2 pi f_s / c in the path and
  *   transmittance phases; the ray state then also carries sum(b dt) of each ray. */
 gsrf_status gsrf_render_bwd(const gsrf_plan *plan, const gsrf_gaussians *g, void *workspace,

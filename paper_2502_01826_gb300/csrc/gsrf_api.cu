@@ -95,6 +95,8 @@ static gsrf_status check_plan(const gsrf_plan* p) {
     const int bw = p->ray_block_w;
     if (!(bw == 0 || bw == 4 || bw == 8 || bw == 16 || bw == 32)) return GSRF_ERR_INVALID_ARG;
     if (!(p->stage == 0 || p->stage == 16 || p->stage == 32)) return GSRF_ERR_INVALID_ARG;
+    if (p->ckpt_every < 0 || p->ckpt_every % 32 != 0 || p->ckpt_every > (1 << 24)) return GSRF_ERR_INVALID_ARG;
+    if (p->ckpt_every > 0 && (p->ckpt_slots < 1 || p->ckpt_slots > 64)) return GSRF_ERR_INVALID_ARG;
     const gsrf_status s = check_grid(&p->grid);
     if (s != GSRF_OK) return s;
     const int w = plan_block_w(p);
@@ -153,7 +155,8 @@ gsrf_status gsrf_workspace_layout(const gsrf_plan* plan, gsrf_layout* out) {
 
 size_t gsrf_ray_state_bytes(const gsrf_plan* plan) {
     if (check_plan(plan) != GSRF_OK) return 0;
-    return (size_t)plan->n_rx * plan->grid.n_az * plan->grid.n_el * sizeof(RayState);
+    const size_t rays = (size_t)plan->n_rx * plan->grid.n_az * plan->grid.n_el;
+    return rays * sizeof(RayState) + (plan->ckpt_every > 0 ? rays * (size_t)plan->ckpt_slots * sizeof(float4) : 0);
 }
 
 gsrf_status gsrf_project(const gsrf_plan* plan, const gsrf_gaussians* g, const float* rx_pos,

@@ -53,6 +53,9 @@ struct BwdArgs {
     int nbx;      // ray blocks per tile along azimuth
     int per_tile; // work items per tile: ray blocks x subcarrier chunks
     int nchunk;   // subcarrier chunks of NFC
+    int n_rx;
+    const float4* ck;  // the forward's transmittance checkpoints [slot][ray], or null
+    int ck_every, ck_slots;
 };
 
 __device__ __forceinline__ void cp_async16b(void* smem, const void* gmem) {
@@ -359,6 +362,19 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
             if ((lane & 1) == 0 && (lane >> 1) < 14) atomicAdd(acc + (lane >> 1), so);
         }
         mask = next;
+        if (a.ck) {
+            // in front of list position b0 - lo: take the forward's own transmittance
+            // where it kept one, so that division by (1 - alpha) runs over at most K positions
+            const long long p = b0 - lo;
+            if (p > 0 && p % a.ck_every == 0 && p / a.ck_every <= a.ck_slots && valid) {
+                const size_t rays = (size_t)a.n_rx * gr.n_el * gr.n_az;
+                const size_t ray = ((size_t)r * gr.n_el + v) * gr.n_az + u;
+                const float4 c = a.ck[(size_t)(p / a.ck_every - 1) * rays + ray];
+                Tr = c.x;
+                Ti = c.y;
+                Gam = c.z;
+            }
+        }
         __syncwarp();
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -496,6 +512,13 @@ cudaError_t launch_render_bwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     a.nbx = p->grid.tile_w / bw;
     a.nchunk = p->n_f == 1 ? 1 : (p->n_f + 7) / 8;
     a.per_tile = (p->grid.tile_w * p->grid.tile_h / 32) * a.nchunk;
+    a.n_rx = L.n_rx;
+    const size_t rays = (size_t)p->n_rx * p->grid.n_az * p->grid.n_el;
+    a.ck = p->ckpt_every > 0
+               ? reinterpret_cast<const float4*>(static_cast<const char*>(ray_state) + rays * sizeof(RayState))
+               : nullptr;
+    a.ck_every = p->ckpt_every > 0 ? p->ckpt_every : 1;
+    a.ck_slots = p->ckpt_slots;
     uint32_t* order = nullptr;
     unsigned long long* counter = nullptr;
     if ((e = launch_item_order(L, ws, a.per_tile, &order, &counter, st)) != cudaSuccess) return e;

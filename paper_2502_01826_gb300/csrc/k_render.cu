@@ -57,6 +57,9 @@ struct RenderArgs {
     int nbx;      // ray blocks per tile along azimuth (tile_w / bw)
     int per_tile; // work items per tile: ray blocks x subcarrier chunks
     int nchunk;   // subcarrier chunks
+    float4* ck;   // transmittance checkpoints [slot][ray] (Tr, Ti, Gamma, Ta), or null
+    int ck_every; // list positions between checkpoints (a multiple of 32)
+    int ck_slots;
 };
 
 constexpr int kMaxJobs = 96;
@@ -179,6 +182,15 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
         int bf = 0;
         uint32_t mask = stage(0, lo);
         for (long long b0 = lo; b0 < hi; b0 += WB, bf ^= 1) {
+            if (a.ck && chunk == 0) {
+                // transmittance in front of list position K, 2K, ... (a batch start)
+                const long long p = b0 - lo;
+                if (p > 0 && p % a.ck_every == 0 && p / a.ck_every <= a.ck_slots && valid) {
+                    const size_t rays = (size_t)a.n_rx * gr.n_el * gr.n_az;
+                    const size_t ray = ((size_t)r * gr.n_el + v) * gr.n_az + u;
+                    a.ck[(size_t)(p / a.ck_every - 1) * rays + ray] = make_float4(Tr, Ti, Gam, Ta);
+                }
+            }
             const uint32_t next = stage(bf ^ 1, b0 + WB);  // empty past the end of the list
             cp_async_wait_prev();
             __syncwarp();
@@ -414,6 +426,12 @@ static RenderArgs render_args(const gsrf_plan* p, const Layout& L, void* ws, flo
     const int nfc = p->n_f == 1 ? 1 : (p->n_f <= 8 ? 8 : 16);
     a.nchunk = (p->n_f + nfc - 1) / nfc;
     a.per_tile = (p->grid.tile_w * p->grid.tile_h / 32) * a.nchunk;
+    const size_t rays = (size_t)p->n_rx * p->grid.n_az * p->grid.n_el;
+    a.ck = (ray_state && p->ckpt_every > 0)
+               ? reinterpret_cast<float4*>(static_cast<char*>(ray_state) + rays * sizeof(RayState))
+               : nullptr;
+    a.ck_every = p->ckpt_every > 0 ? p->ckpt_every : 1;
+    a.ck_slots = p->ckpt_slots;
     return a;
 }
 

@@ -49,9 +49,10 @@ def test_struct_layouts_match_header(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\\n", sizeof(gsrf_grid), sizeof(gsrf_gaussians), sizeof(gsrf_plan),
          sizeof(gsrf_layout), sizeof(gsrf_run_status));
-  printf("%zu %zu %zu %zu %zu %zu %zu\\n", offsetof(gsrf_plan, f0_hz), offsetof(gsrf_plan, grid),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", offsetof(gsrf_plan, f0_hz), offsetof(gsrf_plan, grid),
          offsetof(gsrf_plan, pair_capacity), offsetof(gsrf_run_status, stats), offsetof(gsrf_layout, view),
-         offsetof(gsrf_plan, ray_block_w), offsetof(gsrf_plan, stage));
+         offsetof(gsrf_plan, ray_block_w), offsetof(gsrf_plan, stage), offsetof(gsrf_plan, ckpt_every),
+         offsetof(gsrf_plan, ckpt_slots));
   return 0;
 }
 """)
@@ -64,7 +65,7 @@ int main(void) {
                      C.sizeof(L.gsrf_layout), C.sizeof(L.gsrf_run_status)]
     assert offs == [L.gsrf_plan.f0_hz.offset, L.gsrf_plan.grid.offset, L.gsrf_plan.pair_capacity.offset,
                     L.gsrf_run_status.stats.offset, L.gsrf_layout.view.offset, L.gsrf_plan.ray_block_w.offset,
-                    L.gsrf_plan.stage.offset]
+                    L.gsrf_plan.stage.offset, L.gsrf_plan.ckpt_every.offset, L.gsrf_plan.ckpt_slots.offset]
 
 
 def plan(n=1000, n_rx=4, n_az=360, n_el=90, cap=100000, **kw):
@@ -126,13 +127,23 @@ def test_tile_shapes_ray_blocks_and_stages_accepted(lib, tw, th, bw, stage):
     assert (lay.n_tiles_u, lay.n_tiles_v) == (-(-360 // tw), -(-90 // th))
 
 
-@pytest.mark.parametrize("field,value", [("ray_block_w", 2), ("ray_block_w", 12), ("ray_block_w", 64),
-                                         ("stage", 8), ("stage", 24), ("stage", -1)])
-def test_bad_ray_block_or_stage_rejected(lib, field, value):
+@pytest.mark.parametrize("fields", [dict(ray_block_w=2), dict(ray_block_w=12), dict(ray_block_w=64),
+                                    dict(stage=8), dict(stage=24), dict(stage=-1), dict(ckpt_every=48, ckpt_slots=4),
+                                    dict(ckpt_every=-32, ckpt_slots=4), dict(ckpt_every=64, ckpt_slots=0),
+                                    dict(ckpt_every=64, ckpt_slots=65)])
+def test_bad_ray_block_stage_or_checkpoints_rejected(lib, fields):
     sz = C.c_size_t()
     p = plan()
-    setattr(p, field, value)
+    for k, v in fields.items():
+        setattr(p, k, v)
     assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_ERR_INVALID_ARG
+
+
+def test_ray_state_grows_with_checkpoints(lib):
+    p = plan()
+    base = lib.gsrf_ray_state_bytes(C.byref(p))
+    p.ckpt_every, p.ckpt_slots = 256, 6
+    assert lib.gsrf_ray_state_bytes(C.byref(p)) == base + 4 * 360 * 90 * 6 * 16
 
 
 def test_calls_reject_bad_pointers_before_launch(lib):

@@ -46,11 +46,11 @@ def masked_upstream(scene, rx, tx, f0, spec, rng, eps_T=1e-4, n_f=1):
     return np.array(G), g
 
 
-def gpu_grads(scene, rx, tx, f0, spec, G, eps_T=1e-4, df=0.0, n_f=1):
+def gpu_grads(scene, rx, tx, f0, spec, G, eps_T=1e-4, df=0.0, n_f=1, **plan_kw):
     """Gradients of sum Re(conj(G) S) through the autograd Function."""
     K = scene["means"].shape[0]
     grid = make_grid(**spec, eps_T=eps_T)
-    R = Renderer(K, rx.shape[0], grid, f0, df_hz=df, n_f=n_f)
+    R = Renderer(K, rx.shape[0], grid, f0, df_hz=df, n_f=n_f, **plan_kw)
     p = {k: v.clone().requires_grad_(True) for k, v in to_device(scene).items()}
     rxd = torch.tensor(rx, device="cuda")
     txd = torch.tensor(tx, device="cuda")
@@ -184,3 +184,49 @@ def test_backward_against_central_differences_of_the_gpu_forward():
     rms = np.sqrt(np.mean(errs[:, 1] ** 2))
     bad = errs[:, 0] > 2e-2 * (errs[:, 1] + 0.1 * rms)
     assert checked >= 24 and bad.sum() <= 2, errs[bad]
+
+
+def deep_scene():
+    """Dense, large Gaussians around the receivers and no early termination: rays
+    composite hundreds of pairs, so the recomputed transmittance runs over long walks."""
+    scene = synthetic.tiny_scene(1500, 204, box=(3.0, 3.0, 2.0), log_scale_mu=math.log(0.3))
+    scene["opacity_logit"] = (scene["opacity_logit"] - 3.0).astype(np.float32)  # thin: deep walks
+    rng = np.random.default_rng(8)
+    rx = (0.25 + rng.uniform(0, 1, (2, 3)) * [2.5, 2.5, 1.5]).astype(np.float32)
+    tx = np.array([2.9, 0.1, 1.9], np.float32)
+    return scene, rx, tx
+
+
+def test_checkpoints_leave_the_forward_unchanged():
+    scene, rx, tx = deep_scene()
+    K = scene["means"].shape[0]
+    outs = []
+    for kw in (dict(), dict(ckpt_every=64, ckpt_slots=8)):
+        R = Renderer(K, rx.shape[0], make_grid(72, 18, eps_T=0.0), 2.4e9, **kw)
+        p = to_device(scene)
+        rxd, txd = torch.tensor(rx, device="cuda"), torch.tensor(tx, device="cuda")
+        R.ensure_capacity(p, rxd, txd)
+        state = R.ray_state()
+        outs.append(R.forward(p, rxd, txd, ray_state=state).cpu().numpy())
+        rays = rx.shape[0] * 72 * 18
+        assert state.numel() == rays * 32 + (rays * 8 * 16 if kw else 0)  # slots follow the ray states
+    assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("every,slots", [(32, 64), (64, 4)])
+def test_checkpointed_backward_on_deep_walks(every, slots):
+    """Checkpoints every 32 positions (all of the walk covered) and every 64 with only 4
+    slots (beyond them the division takes over): both gradients within the bar of the
+    FP64 oracle's, and at least as close to it as the division-only backward."""
+    scene, rx, tx = deep_scene()
+    spec = dict(n_az=72, n_el=18)
+    rng = np.random.default_rng(9)
+    G, g = masked_upstream(scene, rx, tx, 2.4e9, spec, rng, eps_T=0.0)
+    ref = oracle_grads(scene, rx, tx, 2.4e9, g, G)
+    div = gpu_grads(scene, rx, tx, 2.4e9, spec, G, eps_T=0.0)
+    ck = gpu_grads(scene, rx, tx, 2.4e9, spec, G, eps_T=0.0, ckpt_every=every, ckpt_slots=slots)
+    compare_grads(ck, ref)
+    e_div = sum(np.linalg.norm(div[k] - ref[k]) ** 2 for k in NAMES)
+    e_ck = sum(np.linalg.norm(ck[k] - ref[k]) ** 2 for k in NAMES)
+    print("squared gradient error vs oracle: division only %.3g, checkpoints %.3g" % (e_div, e_ck))
+    assert e_ck <= 1.5 * e_div + 1e-30
