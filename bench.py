@@ -338,6 +338,7 @@ def run_ours(args, ws, rank):
     persistent = persistent_leg(args, cfg, p, rx, tx, R, flush, pairs_per_step)
     fwd_bwd = train_leg(args, ws, flush) if not args.no_train else None
     csi = csi_leg(args, ws, flush) if not args.no_train else None
+    million = million_leg(args, ws, flush) if not args.no_train else None
     uneven = uneven_leg(args, flush) if args.uneven else None
 
     pk_, pk_kind = peaks()
@@ -380,6 +381,7 @@ def run_ours(args, ws, rank):
         "persistent": persistent,
         "fwd_bwd": fwd_bwd,
         "csi": csi,
+        "fwd_bwd_1m": million,
         "uneven": uneven,
         "gpu_launches": 24 * args.steps,
         "clocks": clocks,
@@ -662,6 +664,57 @@ def csi_leg(args, ws, flush):
                         "csi_values_per_s": sum_over_ranks(n_csi * args.steps, ws) / tfb},
             "split": tune["best"] if tune else None,
             "what": "per composited pair all 64 subcarriers; loss on the complex CSI"}
+
+
+def million_leg(args, ws, flush, every=128, slots=32):
+    """Forward + backward at 1,000,000 Gaussians (the top of the uneven workload's range)
+    with transmittance checkpoints every `every` tile-list positions (`slots` per ray):
+    8 receivers, 360 x 90, 2.4 GHz, loss = mean |S - S_gt|^2 against a separately seeded
+    ground-truth set rendered by the same library.  CUDA events, L2 flushed between
+    steps."""
+    import torch
+
+    from paper_2502_01826_gb300 import synthetic
+    from paper_2502_01826_gb300.render import Renderer, make_grid, render, to_device
+
+    cfg = synthetic.config_million()
+    K, n_rx = cfg["scene"]["means"].shape[0], cfg["rx"].shape[0]
+    grid = make_grid(**cfg["grid"])
+    rx = torch.tensor(cfg["rx"], device="cuda")
+    tx = torch.tensor(cfg["tx"], device="cuda")
+    gt = to_device(cfg["gt_scene"])
+    Rg = Renderer(K, n_rx, grid, cfg["f0"])
+    Rg.ensure_capacity(gt, rx, tx)
+    S_gt = Rg.forward(gt, rx, tx).clone()
+    del Rg, gt
+    p = {k: v.clone().requires_grad_(True) for k, v in to_device(cfg["scene"]).items()}
+    pd = {k: v.detach() for k, v in p.items()}
+    R = Renderer(K, n_rx, grid, cfg["f0"], ckpt_every=every, ckpt_slots=slots)
+    R.ensure_capacity(pd, rx, tx)
+    tune = autotune(R, pd, rx, tx, args, reps=1)
+    n = S_gt.numel() // 2
+
+    def step():
+        for v in p.values():
+            v.grad = None
+        S = render(R, p, rx, tx)
+        loss = ((S - S_gt) ** 2).sum() / n
+        loss.backward()
+        return loss
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    pairs = int(R.status().stats[1])
+    steps = max(3, min(args.steps, 20))
+    ms = _time_steps(step, steps, flush)
+    t = max_over_ranks(ms * steps / 1e3, ws)
+    return {"workload": cfg["name"], "n_gauss": K, "n_rx": n_rx, "ms_per_step": ms, "steps": steps,
+            "pairs_per_step": pairs, "pairs_per_s": sum_over_ranks(pairs * steps, ws) / t,
+            "checkpoints": {"every_list_positions": every, "slots_per_ray": slots,
+                            "ray_state_bytes": int(R.ray_state().numel())},
+            "split": tune["best"] if tune else None,
+            "what": "forward + complex-MSE loss + backward with transmittance checkpoints"}
 
 
 def main():

@@ -106,6 +106,19 @@ def config_csi(K: int = 100_000, gt: bool = False) -> dict:
     return out
 
 
+def config_million(n_rx: int = 8) -> dict:
+    """Training at the top of the uneven workload's range: 1,000,000 Gaussians from the
+    same distributions, n_rx receivers, 360x90, 2.4 GHz, and a separately seeded
+    ground-truth set of the same size."""
+    K = 1_000_000
+    s = scene(K, BASE_SEED + 5)
+    rx = positions(s["_rng"], n_rx)
+    tx = positions(s["_rng"], 1)[0]
+    gt = scene(K, BASE_SEED + 5 + 1000)
+    return dict(name="train_1m_%drx_360x90" % n_rx, scene=strip(s), gt_scene=strip(gt), rx=rx, tx=tx, f0=2.4e9,
+                df=0.0, n_f=1, grid=grid_spec(360, 90))
+
+
 def config_uneven(n_scenes: int = 8, n_req: int = 256, k_lo: float = 1e4, k_hi: float = 1e6):
     """Uneven serving stress: scenes with log-uniform Gaussian counts, requests with
     1-32 receivers and a 2.4 or 5.2 GHz carrier, 360x90 grids."""
