@@ -187,19 +187,27 @@ def split_grid(cfg, R):
     return make_grid(**cfg["grid"], tile_w=R.plan.grid.tile_w, tile_h=R.plan.grid.tile_h)
 
 
-def autotune(R, p, rx, tx, args, reps):
+def autotune(R, p, rx, tx, args, reps, training=False):
     """Tune R's work split on its own problem (gsrf_autotune), outside any timed region;
     returns the choice and the default split's times, or None with --no-tune."""
+    if args.split:
+        tile, bw, stg = args.split.split(",")
+        tw, th = (int(x) for x in tile.split("x"))
+        R.plan.grid.tile_w, R.plan.grid.tile_h = tw, th
+        R.plan.ray_block_w, R.plan.stage = int(bw), int(stg)
+        R._alloc()
+        R.ensure_capacity(p, rx, tx)
+        return {"fixed": args.split}
     if args.no_tune:
         return None
     cap = R.plan.pair_capacity
     R.plan.pair_capacity = 3 * cap  # room for the small-tile candidates' extra pairs
     R._alloc()
-    best, table = R.autotune(p, rx, tx, reps=reps)
+    best, table = R.autotune(p, rx, tx, reps=reps, training=training)
     dflt = [t for t in table if (t["tile_w"], t["tile_h"], t["ray_block_w"], t["stage"]) == (16, 16, 8, 32)]
     return {"best": best, "default_16x16_8x4_32": dflt[0] if dflt else None, "candidates": len(table),
-            "what": "median of %d event-timed runs per candidate: project + bin per tile shape, render per "
-                    "(tile shape, ray block, stage)" % reps}
+            "what": "median of %d event-timed runs per candidate: project + bin per tile shape, %s per "
+                    "(tile shape, ray block, stage)" % (reps, "forward + backward render" if training else "render")}
 
 
 def run_ours(args, ws, rank):
@@ -361,7 +369,7 @@ def run_ours(args, ws, rank):
                    "candidate_tests_16x16_tiles": tests_16x16,
                    "split": {"tile": "%dx%d" % (R.plan.grid.tile_w, R.plan.grid.tile_h),
                              "ray_block": "%dx%d" % (R.plan.ray_block_w or 8, 32 // (R.plan.ray_block_w or 8)),
-                             "stage": R.plan.stage or 32, "autotuned": tune is not None},
+                             "stage": R.plan.stage or 32, "autotuned": tune is not None and "best" in tune},
                    "tile_gaussian_pairs_binned_per_step": binned_per_step,
                    "l2": "flushed between timed steps (256 MB write, outside the events)",
                    "parallelism": "replicas: each rank renders its own 64 receivers" if ws > 1 else "1 GPU"},
@@ -497,7 +505,7 @@ def uneven_leg(args, flush, max_records=1.5e8):
     splits = {}
     for i, q in enumerate(reqs):
         si = q["scene"]
-        if si in splits or args.no_tune:
+        if si in splits or args.no_tune or args.split:
             continue
         R = Renderer(Ks[si], q["rx"].shape[0], grid, q["f0"], pair_capacity=1024)
         rx = torch.tensor(q["rx"], device="cuda")
@@ -569,7 +577,7 @@ def train_leg(args, ws, flush):
     p = {k: v.clone().requires_grad_(True) for k, v in to_device(cfg["scene"]).items()}
     R = Renderer(K, n_rx, grid, cfg["f0"])
     R.ensure_capacity({k: v.detach() for k, v in p.items()}, rx, tx)
-    tune = autotune(R, {k: v.detach() for k, v in p.items()}, rx, tx, args, reps=2)
+    tune = autotune(R, {k: v.detach() for k, v in p.items()}, rx, tx, args, reps=2, training=True)
     n = S_gt.numel() // 2
 
     def step():
@@ -598,7 +606,7 @@ def train_leg(args, ws, flush):
     return {"workload": cfg["name"], "n_gauss": K, "n_rx": n_rx, "ms_per_step": ms,
             "pairs_per_step": pairs, "pairs_per_s": sum_over_ranks(pairs * args.steps, ws) / t,
             "spectra_per_s": sum_over_ranks(n_rx * args.steps, ws) / t,
-            "split": tune["best"] if tune else None,
+            "split": tune.get("best", tune) if tune else None,
             "what": "forward + complex-MSE loss + hand-written backward to all parameters"}
 
 
@@ -629,7 +637,7 @@ def csi_leg(args, ws, flush):
     R = Renderer(K, n_rx, grid, cfg["f0"], df_hz=cfg["df"], n_f=cfg["n_f"])
     pd = {k: v.detach() for k, v in p.items()}
     R.ensure_capacity(pd, rx, tx)
-    tune = autotune(R, pd, rx, tx, args, reps=2)
+    tune = autotune(R, pd, rx, tx, args, reps=2, training=True)
     out = torch.empty(R.out_shape(), dtype=torch.float32, device="cuda")
 
     def fwd():
@@ -662,7 +670,7 @@ def csi_leg(args, ws, flush):
                     "csi_values_per_s": sum_over_ranks(n_csi * args.steps, ws) / tf},
             "fwd_bwd": {"ms_per_step": ms_fb, "pairs_per_s": sum_over_ranks(pairs * args.steps, ws) / tfb,
                         "csi_values_per_s": sum_over_ranks(n_csi * args.steps, ws) / tfb},
-            "split": tune["best"] if tune else None,
+            "split": tune.get("best", tune) if tune else None,
             "what": "per composited pair all 64 subcarriers; loss on the complex CSI"}
 
 
@@ -691,7 +699,7 @@ def million_leg(args, ws, flush, every=128, slots=32):
     pd = {k: v.detach() for k, v in p.items()}
     R = Renderer(K, n_rx, grid, cfg["f0"], ckpt_every=every, ckpt_slots=slots)
     R.ensure_capacity(pd, rx, tx)
-    tune = autotune(R, pd, rx, tx, args, reps=1)
+    tune = autotune(R, pd, rx, tx, args, reps=1, training=True)
     n = S_gt.numel() // 2
 
     def step():
@@ -713,7 +721,7 @@ def million_leg(args, ws, flush, every=128, slots=32):
             "pairs_per_step": pairs, "pairs_per_s": sum_over_ranks(pairs * steps, ws) / t,
             "checkpoints": {"every_list_positions": every, "slots_per_ray": slots,
                             "ray_state_bytes": int(R.ray_state().numel())},
-            "split": tune["best"] if tune else None,
+            "split": tune.get("best", tune) if tune else None,
             "what": "forward + complex-MSE loss + backward with transmittance checkpoints"}
 
 
@@ -730,6 +738,8 @@ def main():
     ap.add_argument("--uneven", action="store_true", help="add the uneven serving-stress leg (slow setup)")
     ap.add_argument("--no-tune", action="store_true", help="keep the default work split (16 x 16 tiles, 8 x 4 "
                     "rays per warp, 32 candidates per stage) instead of autotuning it")
+    ap.add_argument("--split", default=None, help="fix the work split instead of tuning it: TWxTH,BW,STAGE "
+                    "(e.g. 32x16,8,32), for profiling runs")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

@@ -236,20 +236,32 @@ gsrf_status gsrf_read_status(const void *workspace, size_t ws_bytes, gsrf_run_st
  * max_results is 0) get every measurement, and n_results their number.
  *   plan, g, rx_pos, tx_pos as for gsrf_render; workspace [dev] of at least
  *   gsrf_autotune_workspace_size bytes; out_rays [dev] as for gsrf_render_fwd (holds the
- *   last candidate's rays).  Tile shapes whose tiles exceed the grid limits or whose
+ *   last candidate's rays); backward NULL to tune the forward, else the buffers below
+ *   to tune forward + backward (the split that renders fastest need not be the one
+ *   that trains fastest: larger tiles shorten binning but lengthen the backward's walk).  Tile shapes whose tiles exceed the grid limits or whose
  *   pairs exceed plan.pair_capacity are skipped; GSRF_ERR_CAPACITY if all are.  The call
  *   synchronises the stream and must not be captured into a graph.  To use the choice,
  *   copy best into plan.grid.tile_w / tile_h, plan.ray_block_w and plan.stage. */
 typedef struct {
     int32_t tile_w, tile_h, ray_block_w, stage;
     float project_bin_ms;      /* gsrf_project + gsrf_bin with this tile shape */
-    float render_ms;           /* gsrf_render_fwd with this tile shape, ray block and stage */
+    float render_ms;           /* gsrf_render_fwd (+ gsrf_render_bwd when tuning for training) */
 } gsrf_tune_result;
+/* Buffers that make the tuner time the training step's render: gsrf_render_fwd with
+ * a ray state, then gsrf_render_bwd.  All [dev]; ray_state of gsrf_ray_state_bytes(plan)
+ * bytes, grad_rays shaped like out_rays; the gradient buffers are scratch (their
+ * contents are overwritten with meaningless sums) and any may be NULL. */
+typedef struct {
+    void *ray_state;
+    const float *grad_rays;
+    float *g_means, *g_log_scales, *g_quats, *g_opacity_logit, *g_coeffs, *g_phase_b;
+} gsrf_tune_backward;
 gsrf_status gsrf_autotune_workspace_size(const gsrf_plan *plan, size_t *bytes);
 gsrf_status gsrf_autotune(const gsrf_plan *plan, const gsrf_gaussians *g, const float *rx_pos,
                           const float *tx_pos, void *workspace, size_t ws_bytes, float *out_rays,
-                          int32_t reps, gsrf_tune_result *results, int32_t max_results,
-                          int32_t *n_results, gsrf_tune_result *best, void *stream);
+                          const gsrf_tune_backward *backward, int32_t reps,
+                          gsrf_tune_result *results, int32_t max_results, int32_t *n_results,
+                          gsrf_tune_result *best, void *stream);
 
 /* gsrf_render without a caller-supplied workspace, for callers that cannot allocate
  * device memory: hosts that forbid allocation once running (real-time or embedded

@@ -61,6 +61,12 @@ class gsrf_tune_result(C.Structure):
                 ("project_bin_ms", C.c_float), ("render_ms", C.c_float)]
 
 
+class gsrf_tune_backward(C.Structure):
+    _fields_ = [("ray_state", C.c_void_p), ("grad_rays", C.c_void_p), ("g_means", C.c_void_p),
+                ("g_log_scales", C.c_void_p), ("g_quats", C.c_void_p), ("g_opacity_logit", C.c_void_p),
+                ("g_coeffs", C.c_void_p), ("g_phase_b", C.c_void_p)]
+
+
 class gsrf_run_status(C.Structure):
     _fields_ = [("code", C.c_int32), ("first_bad", C.c_int32), ("required_pairs", C.c_int64),
                 ("stats", C.c_int64 * 4)]
@@ -101,8 +107,8 @@ def load(build_if_missing: bool = False):
     L.gsrf_batch_workspace_size.argtypes = [C.c_int32, P(gsrf_plan), P(C.c_size_t)]
     L.gsrf_render_batch.argtypes = [C.c_int32, P(gsrf_plan), P(vp), P(C.c_size_t), P(vp), vp, sz, vp]
     L.gsrf_autotune_workspace_size.argtypes = [P(gsrf_plan), P(C.c_size_t)]
-    L.gsrf_autotune.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, vp, vp, sz, vp, C.c_int32,
-                                P(gsrf_tune_result), C.c_int32, P(C.c_int32), P(gsrf_tune_result), vp]
+    L.gsrf_autotune.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, vp, vp, sz, vp, P(gsrf_tune_backward),
+                                C.c_int32, P(gsrf_tune_result), C.c_int32, P(C.c_int32), P(gsrf_tune_result), vp]
     L.gsrf_version.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("gsrf_ray_state_bytes", "gsrf_version"):

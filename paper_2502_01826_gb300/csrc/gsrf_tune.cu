@@ -84,11 +84,12 @@ gsrf_status gsrf_autotune_workspace_size(const gsrf_plan* plan, size_t* bytes) {
 }
 
 gsrf_status gsrf_autotune(const gsrf_plan* plan, const gsrf_gaussians* g, const float* rx_pos, const float* tx_pos,
-                          void* workspace, size_t ws_bytes, float* out_rays, int32_t reps,
-                          gsrf_tune_result* results, int32_t max_results, int32_t* n_results,
+                          void* workspace, size_t ws_bytes, float* out_rays, const gsrf_tune_backward* bwd,
+                          int32_t reps, gsrf_tune_result* results, int32_t max_results, int32_t* n_results,
                           gsrf_tune_result* best, void* stream) {
     if (!plan || !g || !rx_pos || !tx_pos || !workspace || !out_rays || !best || reps < 1 || reps > 100)
         return GSRF_ERR_INVALID_ARG;
+    if (bwd && (!bwd->ray_state || !bwd->grad_rays)) return GSRF_ERR_INVALID_ARG;
     if (max_results < 0 || (max_results > 0 && !results)) return GSRF_ERR_INVALID_ARG;
     size_t need = 0;
     gsrf_status s = gsrf_workspace_size(plan, &need);  // validates the caller's plan
@@ -114,8 +115,14 @@ gsrf_status gsrf_autotune(const gsrf_plan* plan, const gsrf_gaussians* g, const 
             for (int stg : kStages) {
                 const gsrf_plan c = with_split(*plan, ts[0], ts[1], bw, stg);
                 float r_ms = 0.0f;
-                s = time_median([&]() { return gsrf_render_fwd(&c, g, workspace, ws_bytes, out_rays, nullptr, stream); },
-                                reps, st, &r_ms);
+                s = time_median([&]() -> gsrf_status {
+                    gsrf_status r = gsrf_render_fwd(&c, g, workspace, ws_bytes, out_rays, bwd ? bwd->ray_state : nullptr,
+                                                    stream);
+                    if (r != GSRF_OK || !bwd) return r;
+                    return gsrf_render_bwd(&c, g, workspace, ws_bytes, bwd->ray_state, bwd->grad_rays, bwd->g_means,
+                                           bwd->g_log_scales, bwd->g_quats, bwd->g_opacity_logit, bwd->g_coeffs,
+                                           bwd->g_phase_b, stream);
+                }, reps, st, &r_ms);
                 if (s != GSRF_OK) return s;
                 const gsrf_tune_result res = {ts[0], ts[1], bw, stg, pb_ms, r_ms};
                 if (n < max_results) results[n] = res;

@@ -381,11 +381,13 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
 }
 
 // Persistent launch: every warp takes work items (receiver, tile, ray block, subcarrier
-// chunk) from one counter, heaviest first, until none is left.
+// chunk) from one counter, heaviest first, until none is left.  One frequency: 4 CTAs
+// per SM (at most 128 registers); several subcarriers: 3 (at most 168).
 template <int NFC>
-__global__ void __launch_bounds__(kBThreads) k_render_bwd(BwdArgs a, const uint32_t* __restrict__ order,
-                                                          unsigned long long* __restrict__ counter,
-                                                          unsigned long long total) {
+__global__ void __launch_bounds__(kBThreads, NFC == 1 ? 4 : 3) k_render_bwd(BwdArgs a,
+                                                                            const uint32_t* __restrict__ order,
+                                                                            unsigned long long* __restrict__ counter,
+                                                                            unsigned long long total) {
     __shared__ float4 sbuf[kBW][2][kBB][6];
     __shared__ uint32_t sid[kBW][2][kBB];
     __shared__ float4 spl[kBW][4];

@@ -297,7 +297,7 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
 // left; a warp that finishes early takes the next item instead of idling until the
 // other warps of its CTA are done.
 template <int NFC, int WB>
-__global__ void __launch_bounds__(kThreads, NFC == 1 ? 8 : 4) k_render_queue(RenderArgs a,
+__global__ void __launch_bounds__(kThreads, NFC == 1 ? 6 : 4) k_render_queue(RenderArgs a,
                                                                             const uint32_t* __restrict__ order,
                                                                             unsigned long long* __restrict__ counter,
                                                                             unsigned long long total) {
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, NFC == 1 ? 8 : 4) k_render_queue(Ren
 // Persistent batched launch over several problems (n_f = 1 each): work items (job,
 // receiver, tile, ray block), same queue discipline.
 template <int WB>
-__global__ void __launch_bounds__(kThreads, 8) k_render_batch(BatchArgs b, const uint32_t* __restrict__ order,
+__global__ void __launch_bounds__(kThreads, 6) k_render_batch(BatchArgs b, const uint32_t* __restrict__ order,
                                                               unsigned long long* __restrict__ counter) {
     __shared__ float4 sbuf[kWarps][2][WB][kRec];
     __shared__ uint32_t sid[kWarps][2][WB];

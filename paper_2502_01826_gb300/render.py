@@ -120,11 +120,13 @@ class Renderer:
                self.ws_bytes, _ptr(out), _ptr(ray_state), _stream(stream))
         return out
 
-    def autotune(self, params: dict, rx: torch.Tensor, tx: torch.Tensor, reps: int = 3, stream=None):
+    def autotune(self, params: dict, rx: torch.Tensor, tx: torch.Tensor, reps: int = 3, stream=None,
+                 training: bool = False):
         """Measure the work splits on this problem (gsrf_autotune) and adopt the fastest:
         the plan's tile shape, ray block and stage change and the workspace is re-allocated
-        (and its pair capacity re-fitted) for them.  Returns (best, every measurement) as
-        dicts of tile_w, tile_h, ray_block_w, stage, project_bin_ms, render_ms."""
+        (and its pair capacity re-fitted) for them.  training=True times forward + backward
+        renders (scratch upstream and gradient buffers).  Returns (best, every measurement)
+        as dicts of tile_w, tile_h, ray_block_w, stage, project_bin_ms, render_ms."""
         nbytes = C.c_size_t()
         L.call("gsrf_autotune_workspace_size", C.byref(self.plan), C.byref(nbytes))
         ws = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
@@ -134,10 +136,18 @@ class Renderer:
         n = C.c_int32()
         best = L.gsrf_tune_result()
         gs = gaussians_struct(params)
+        bwd, keep = None, []
+        if training:
+            state = self.ray_state()
+            up = torch.randn(self.out_shape(), dtype=torch.float32, device=self.device)
+            gr = {k: torch.zeros_like(v) for k, v in params.items() if v is not None}
+            keep = [state, up, gr]
+            bwd = L.gsrf_tune_backward(_ptr(state), _ptr(up), *[_ptr(gr.get(k)) for k in PARAM_NAMES])
         L.call("gsrf_autotune", C.byref(self.plan), C.byref(gs), _ptr(rx), _ptr(tx), _ptr(ws), nbytes.value,
-               _ptr(out), int(reps), results, cap, C.byref(n), C.byref(best), _stream(stream))
+               _ptr(out), C.byref(bwd) if bwd is not None else None, int(reps), results, cap, C.byref(n),
+               C.byref(best), _stream(stream))
         as_dict = lambda r: {k: getattr(r, k) for k, _ in L.gsrf_tune_result._fields_}
-        del ws, out
+        del ws, out, keep
         self.plan.grid.tile_w, self.plan.grid.tile_h = best.tile_w, best.tile_h
         self.plan.ray_block_w, self.plan.stage = best.ray_block_w, best.stage
         self._alloc()

@@ -179,11 +179,14 @@ def test_autotune_sizing_and_argument_checks(lib):
     n = C.c_int32()
     dev = C.c_void_p(4096)
     # null workspace, zero repetitions, results wanted without a buffer, no best
-    assert lib.gsrf_autotune(C.byref(p), C.byref(g), dev, dev, None, b.value, dev, 3, res, 4, C.byref(n),
+    assert lib.gsrf_autotune(C.byref(p), C.byref(g), dev, dev, None, b.value, dev, None, 3, res, 4, C.byref(n),
                              C.byref(best), None) == L.GSRF_ERR_INVALID_ARG
-    assert lib.gsrf_autotune(C.byref(p), C.byref(g), dev, dev, dev, b.value, dev, 0, res, 4, C.byref(n),
+    assert lib.gsrf_autotune(C.byref(p), C.byref(g), dev, dev, dev, b.value, dev, None, 0, res, 4, C.byref(n),
                              C.byref(best), None) == L.GSRF_ERR_INVALID_ARG
-    assert lib.gsrf_autotune(C.byref(p), C.byref(g), dev, dev, dev, b.value, dev, 3, None, 4, C.byref(n),
+    assert lib.gsrf_autotune(C.byref(p), C.byref(g), dev, dev, dev, b.value, dev, None, 3, None, 4, C.byref(n),
                              C.byref(best), None) == L.GSRF_ERR_INVALID_ARG
-    assert lib.gsrf_autotune(C.byref(p), C.byref(g), dev, dev, dev, b.value, dev, 3, res, 4, C.byref(n),
+    assert lib.gsrf_autotune(C.byref(p), C.byref(g), dev, dev, dev, b.value, dev, None, 3, res, 4, C.byref(n),
                              None, None) == L.GSRF_ERR_INVALID_ARG
+    bwd = L.gsrf_tune_backward(None, 4096, None, None, None, None, None, None)  # no ray state
+    assert lib.gsrf_autotune(C.byref(p), C.byref(g), dev, dev, dev, b.value, dev, C.byref(bwd), 3, res, 4,
+                             C.byref(n), C.byref(best), None) == L.GSRF_ERR_INVALID_ARG

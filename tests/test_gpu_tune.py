@@ -42,3 +42,21 @@ def test_autotune_picks_its_fastest_split_and_keeps_results():
     assert R.status().code == 0
     assert np.array_equal(out, ref)
     print("autotune best:", best)
+
+
+def test_autotune_for_training_times_forward_and_backward():
+    scene = {k: v for k, v in synthetic.scene(4000, 92).items() if not k.startswith("_")}
+    rng = np.random.default_rng(8)
+    rx = torch.tensor((rng.uniform(0, 1, (2, 3)) * [10.0, 8.0, 3.0]).astype(np.float32), device="cuda")
+    tx = torch.tensor(np.array([2.0, 6.0, 1.5], np.float32), device="cuda")
+    p = to_device(scene)
+    R = Renderer(4000, 2, make_grid(180, 45), 2.4e9, pair_capacity=2_000_000, ckpt_every=64, ckpt_slots=8)
+    fwd_best, fwd = R.autotune(p, rx, tx, reps=1)
+    trn_best, trn = R.autotune(p, rx, tx, reps=1, training=True)
+    assert len(trn) == len(fwd) >= 20
+    tot = [t["project_bin_ms"] + t["render_ms"] for t in trn]
+    assert trn_best["project_bin_ms"] + trn_best["render_ms"] == min(tot)
+    # forward + backward costs more than the forward alone for the same split
+    key = lambda t: (t["tile_w"], t["tile_h"], t["ray_block_w"], t["stage"])
+    f = {key(t): t["render_ms"] for t in fwd}
+    assert sum(t["render_ms"] > f[key(t)] for t in trn) >= 0.8 * len(trn)
