@@ -239,7 +239,7 @@ gsrf_status gsrf_received_signal(const float* rays, int32_t n_rx, int32_t n_f, i
                                  int32_t mode, float* out, void* stream) {
     if (!rays || !out || n_rx < 1 || n_f < 1 || n_el < 1 || n_az < 1 || mode < 0 || mode > 3)
         return GSRF_ERR_INVALID_ARG;
-    if ((size_t)n_rx * n_f > 0x7fffffffu || (size_t)n_el * n_az > 0x7fffffffu) return GSRF_ERR_INVALID_ARG;
+    if ((size_t)n_rx * n_f > 0x0fffffffu || (size_t)n_el * n_az > 0x7fffffffu) return GSRF_ERR_INVALID_ARG;
     return cuda_status(launch_signal(rays, n_rx, n_f, n_el, n_az, mode, out, (cudaStream_t)stream));
 }
 

@@ -208,6 +208,41 @@ __device__ __forceinline__ Cover cover_of(float cx, float cy, float cz, float ls
     return cv;
 }
 
+// Error-free FP32 transformations (Knuth's two-sum, the FMA two-product) and |a - b| of
+// two FP32 points to about 47 bits, returned in FP64.  Every step is an explicit
+// round-to-nearest operation, so the compiler cannot contract or reorder it.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void pair_add(float& h, float& l, float bh, float bl) {
+    float s, e;
+    two_sum(h, bh, s, e);
+    e = __fadd_rn(e, __fadd_rn(l, bl));
+    h = __fadd_rn(s, e);
+    l = __fsub_rn(e, __fsub_rn(h, s));
+}
+__device__ __forceinline__ double pair_dist(float ax, float ay, float az, float bx, float by, float bz) {
+    float ch[3], cl[3];
+    two_sum(ax, -bx, ch[0], cl[0]);
+    two_sum(ay, -by, ch[1], cl[1]);
+    two_sum(az, -bz, ch[2], cl[2]);
+    float h = 0.0f, l = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float p = __fmul_rn(ch[i], ch[i]);
+        const float pe = __fmaf_rn(ch[i], ch[i], -p);              // ch^2 = p + pe exactly
+        const float q = __fmaf_rn(__fmul_rn(2.0f, ch[i]), cl[i], pe);  // + 2 ch cl (cl^2 < 2^-48 ch^2)
+        pair_add(h, l, p, q);
+    }
+    if (!(h > 0.0f)) return 0.0;
+    const float sq = __fsqrt_rn(h);
+    const float res = __fadd_rn(__fmaf_rn(-sq, sq, h), l);            // (h + l) - sq^2
+    const float corr = __fdiv_rn(res, __fmul_rn(2.0f, sq));
+    return (double)sq + (double)corr;
+}
+
 // One thread per (receiver, Gaussian): whitened offset, depth key, coverage, phase.
 __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __restrict__ rxp,
                                               const GShape* __restrict__ shape,
@@ -253,9 +288,11 @@ __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __r
     // direction pre-test of the render: D cos(theta) of the cover's cone less a rounding
     // margin; below -D (every direction passes) when the cone is a hemisphere or wider
     v.ccos = wide ? -1.0f - D_c : sqrtf(fmaxf(D_c * D_c - Rs * Rs, 0.0f)) - 2e-6f * D_c;
-    // path phase: d = |t - mu| + |mu - r| and d f0 / c reduced to [0, 1) in FP64
-    const double ex = (double)mx - rx, ey = (double)my - ry, ez = (double)mz - rz;
-    const double d = dpath_t[k] + sqrt(ex * ex + ey * ey + ez * ez);
+    // path phase: d = |t - mu| + |mu - r| and d f0 / c reduced to [0, 1) in FP64.  |mu - r|
+    // comes as an exact FP32 pair computation (FP64 square roots are slow on this part):
+    // mu - r by two-sum, the squares by FMA two-products, their sum by pair additions and
+    // the square root by one Newton correction, about 47 significant bits in all.
+    const double d = dpath_t[k] + pair_dist(mx, my, mz, rx, ry, rz);
     const double cyc = d * f0_over_c;
     const float fr = (float)(cyc - floor(cyc));
     float s, c;

@@ -1,22 +1,33 @@
 // k_signal.cu -- received signal from the per-ray signals (Sec. 4.4, loss paragraph):
 // the single-antenna complex sum over rays, its power in dB, the incoherent power sum,
 // and the spatial-spectrum magnitude.  FP64 accumulation in a fixed order.
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "gsrf_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace gsrf {
 
 constexpr int kSigThreads = 256;
 
-// One block per (receiver, frequency): thread t sums rays t, t + 256, ...; then a
-// fixed tree in shared memory.  The order never depends on timing.
-__global__ void __launch_bounds__(kSigThreads) k_signal_sum(const float2* __restrict__ rays, int n_rays, int mode,
-                                                            float* __restrict__ out) {
+constexpr int kSigCluster = 8;  // CTAs per (receiver, frequency) sum
+
+// One thread-block cluster of kSigCluster CTAs per (receiver, frequency): CTA c, thread t
+// sums rays c * 256 + t + k * 256 * kSigCluster (k = 0, 1, ...) in FP64, a fixed tree in
+// shared memory gives each CTA's partial, and CTA 0 adds the partials of CTAs
+// 0 .. kSigCluster - 1, in that order, through distributed shared memory.  The order
+// never depends on timing, and all SMs share the work.
+__global__ void __cluster_dims__(kSigCluster, 1, 1) __launch_bounds__(kSigThreads)
+    k_signal_sum(const float2* __restrict__ rays, int n_rays, int mode, float* __restrict__ out) {
     __shared__ double sr[kSigThreads], si[kSigThreads], sp[kSigThreads];
-    const float2* S = rays + (size_t)blockIdx.x * n_rays;
+    cg::cluster_group cl = cg::this_cluster();
+    const int c = (int)cl.block_rank();
+    const int rf = blockIdx.x / kSigCluster;
+    const float2* S = rays + (size_t)rf * n_rays;
     double ar = 0.0, ai = 0.0, ap = 0.0;
-    for (int i = threadIdx.x; i < n_rays; i += kSigThreads) {
+    for (int i = c * kSigThreads + threadIdx.x; i < n_rays; i += kSigThreads * kSigCluster) {
         const float2 s = S[i];
         ar += (double)s.x;
         ai += (double)s.y;
@@ -34,16 +45,24 @@ __global__ void __launch_bounds__(kSigThreads) k_signal_sum(const float2* __rest
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
+    cl.sync();  // every CTA's partial is in its shared memory
+    if (c == 0 && threadIdx.x == 0) {
+        double tr = 0.0, ti = 0.0, tp = 0.0;
+        for (int k = 0; k < kSigCluster; ++k) {
+            tr += *cl.map_shared_rank(&sr[0], k);
+            ti += *cl.map_shared_rank(&si[0], k);
+            tp += *cl.map_shared_rank(&sp[0], k);
+        }
         if (mode == GSRF_SIG_COMPLEX_SUM) {
-            out[2 * blockIdx.x] = (float)sr[0];
-            out[2 * blockIdx.x + 1] = (float)si[0];
+            out[2 * rf] = (float)tr;
+            out[2 * rf + 1] = (float)ti;
         } else if (mode == GSRF_SIG_RSSI_DB) {
-            out[blockIdx.x] = (float)(10.0 * log10(sr[0] * sr[0] + si[0] * si[0]));
+            out[rf] = (float)(10.0 * log10(tr * tr + ti * ti));
         } else {
-            out[blockIdx.x] = (float)sp[0];
+            out[rf] = (float)tp;
         }
     }
+    cl.sync();  // CTA 0 has read the others' shared memory
 }
 
 __global__ void k_spectrum_mag(const float2* __restrict__ rays, size_t n, float* __restrict__ out) {
@@ -61,7 +80,7 @@ cudaError_t launch_signal(const float* rays, int n_rx, int n_f, int n_el, int n_
         const unsigned blocks = (unsigned)min((size_t)152 * 16, (n + 255) / 256);
         k_spectrum_mag<<<blocks, 256, 0, st>>>(R, n, out);
     } else {
-        k_signal_sum<<<n_rx * n_f, kSigThreads, 0, st>>>(R, n_el * n_az, mode, out);
+        k_signal_sum<<<n_rx * n_f * kSigCluster, kSigThreads, 0, st>>>(R, n_el * n_az, mode, out);
     }
     return cudaGetLastError();
 }
