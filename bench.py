@@ -42,6 +42,14 @@ UNIT = "pairs/s"
 # 16, Fourier-Legendre radiance 128, accumulation and transmittance 28).
 FLOP_TEST = 37
 FLOP_HIT = 172
+# DRAM bytes (read + write) of one k_render_queue launch on the 64-receiver workload,
+# from ncu (dram__bytes_read.sum + dram__bytes_write.sum, one pass, full size), per
+# work split; reported only for a split that was measured (profiles/).
+RENDER_TRAFFIC = {(32, 32, 8, 32): 84175104 + 6679808}
+# library kernels per step: project 4 (status, ray table, shape records, view records),
+# bin 19 (zero, 4 x (hist, scan, scatter), count, scan, emit, tile hist, scan, scatter),
+# render 5 (item keys, counting pass of 3, persistent render), received signal 1
+LAUNCHES_PER_STEP = 29
 # FP32 peak: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x the maximum SM clock.
 SMS, FP32_LANES = 152, 128
 
@@ -380,7 +388,9 @@ def run_ours(args, ws, rank):
                          "speedup_of_batched": ms_plain / ms_step,
                          "what": "%d sequential single-receiver project+bin+render+RSSI calls" % n_rx},
         "roofline": {"kernel": "k_render_queue", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                     "traffic": RENDER_TRAFFIC.get((R.plan.grid.tile_w, R.plan.grid.tile_h, R.plan.ray_block_w or 8,
+                                                    R.plan.stage or 32)) if n_rx == 64 else None,
                      "peak_kind": "FP32 lanes x max SM clock (%s sm_max_mhz %.0f)" % (pk_kind, mhz),
                      "flop_per_launch": flops},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -391,7 +401,7 @@ def run_ours(args, ws, rank):
         "csi": csi,
         "fwd_bwd_1m": million,
         "uneven": uneven,
-        "gpu_launches": 24 * args.steps,
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": clocks,
     }
     return result, cfg
@@ -564,7 +574,7 @@ def train_leg(args, ws, flush):
     from paper_2502_01826_gb300 import synthetic
     from paper_2502_01826_gb300.render import Renderer, make_grid, render, to_device
 
-    cfg = synthetic.config_train()
+    cfg = synthetic.config_train(K=args.train_gauss, n_rx=args.train_rx)
     K, n_rx = cfg["scene"]["means"].shape[0], cfg["rx"].shape[0]
     grid = make_grid(**cfg["grid"])
     rx = torch.tensor(cfg["rx"], device="cuda")
@@ -740,6 +750,10 @@ def main():
                     "rays per warp, 32 candidates per stage) instead of autotuning it")
     ap.add_argument("--split", default=None, help="fix the work split instead of tuning it: TWxTH,BW,STAGE "
                     "(e.g. 32x16,8,32), for profiling runs")
+    ap.add_argument("--only", choices=["train", "csi", "million"], default=None,
+                    help="run one secondary leg alone and print its record (profiling runs)")
+    ap.add_argument("--train-gauss", type=int, default=200_000, help="Gaussians of the training leg")
+    ap.add_argument("--train-rx", type=int, default=16, help="receivers of the training leg")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -770,6 +784,14 @@ def main():
         return 0
 
     ws, rank, local = dist_setup()
+    if args.only:
+        import torch
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        leg = {"train": train_leg, "csi": csi_leg, "million": million_leg}[args.only]
+        rec = leg(args, ws, flush)
+        if rank == 0:
+            print(json.dumps({"only": args.only, **rec}))
+        return 0
     result, cfg = run_ours(args, ws, rank)
     if rank == 0:
         if ws == 1:

@@ -84,7 +84,7 @@ def config_train(K: int = 200_000, n_rx: int = 16) -> dict:
     rx = positions(s["_rng"], n_rx)
     tx = positions(s["_rng"], 1)[0]
     gt = scene(K, BASE_SEED + 2 + 1000)
-    return dict(name="train_200k_16rx_360x90", scene=strip(s), gt_scene=strip(gt), rx=rx, tx=tx,
+    return dict(name="train_%dk_%drx_360x90" % (K // 1000, n_rx), scene=strip(s), gt_scene=strip(gt), rx=rx, tx=tx,
                 f0=2.4e9, df=0.0, n_f=1, grid=grid_spec(360, 90))
 
 
