@@ -382,9 +382,11 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
 
 // Persistent launch: every warp takes work items (receiver, tile, ray block, subcarrier
 // chunk) from one counter, heaviest first, until none is left.  One frequency: 4 CTAs
-// per SM (at most 128 registers); several subcarriers: 3 (at most 168).
+// per SM (at most 128 registers); chunks of 8 subcarriers: 3 (at most 168); of 16: 2.
+// More than 8 subcarriers go in chunks of 16: half the walks of chunks of 8 for 64
+// subcarriers, which outweighs the lower occupancy.
 template <int NFC>
-__global__ void __launch_bounds__(kBThreads, NFC == 1 ? 4 : 3) k_render_bwd(BwdArgs a,
+__global__ void __launch_bounds__(kBThreads, NFC == 1 ? 4 : (NFC == 8 ? 3 : 2)) k_render_bwd(BwdArgs a,
                                                                             const uint32_t* __restrict__ order,
                                                                             unsigned long long* __restrict__ counter,
                                                                             unsigned long long total) {
@@ -512,7 +514,8 @@ cudaError_t launch_render_bwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     const int bw = plan_block_w(p);
     a.bw_log = __builtin_ctz((unsigned)bw);
     a.nbx = p->grid.tile_w / bw;
-    a.nchunk = p->n_f == 1 ? 1 : (p->n_f + 7) / 8;
+    const int nfc = p->n_f == 1 ? 1 : (p->n_f <= 8 ? 8 : 16);
+    a.nchunk = (p->n_f + nfc - 1) / nfc;
     a.per_tile = (p->grid.tile_w * p->grid.tile_h / 32) * a.nchunk;
     a.n_rx = L.n_rx;
     const size_t rays = (size_t)p->n_rx * p->grid.n_az * p->grid.n_el;
@@ -533,11 +536,16 @@ cudaError_t launch_render_bwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
             return e;
         const int grid = (int)max(1ll, min((long long)sms * max(per_sm, 1), (n + kBW - 1) / kBW));
         k_render_bwd<1><<<grid, kBThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
-    } else {
+    } else if (nfc == 8) {
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd<8>, kBThreads, 0)) != cudaSuccess)
             return e;
         const int grid = (int)max(1ll, min((long long)sms * max(per_sm, 1), (n + kBW - 1) / kBW));
         k_render_bwd<8><<<grid, kBThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
+    } else {
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd<16>, kBThreads, 0)) != cudaSuccess)
+            return e;
+        const int grid = (int)max(1ll, min((long long)sms * max(per_sm, 1), (n + kBW - 1) / kBW));
+        k_render_bwd<16><<<grid, kBThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
     }
     const unsigned nb = (unsigned)((L.n + 255) / 256);
     k_grad_params<<<nb, 256, 0, st>>>(*g, at<GShape>(ws, L.gshape), acc, g_means, g_log_scales, g_quats,
