@@ -12,9 +12,10 @@
 // weight and the quadratic A t^2 + 2 B t + (C - 9) = 0 (here A = |v'|^2, B = w.v',
 // C = |w|^2 in whitened coordinates) to the whitening matrix W and the mean; the path
 // phase phi = 2 pi f d / c adds its own term to the mean.  Per candidate, the 46
-// gradient values of the warp's 32 rays are summed by a butterfly reduce-scatter
-// (47 shuffles; lane L ends with totals L and L/2) and added to the Gaussian's
-// accumulator with one atomic per value.
+// gradient values of the warp's 32 rays are summed by butterfly reduce-scatters (47
+// shuffles; lane L ends with totals L and L/2; the 32 coefficient values in a lane-
+// permuted order that needs no selects) and added to the Gaussian's accumulator with one
+// atomic per value.
 //
 // k_grad_params chains the accumulators to the raw parameters: W = diag(1/s) R^T to the
 // log-scales and to the (unnormalised) quaternion, the opacity through its sigmoid, the
@@ -63,25 +64,8 @@ __device__ __forceinline__ void cp_async16b(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 
-// Butterfly reduce-scatter of 32 values over a warp: afterwards lane L holds the sum of
-// value L over all lanes.
-__device__ __forceinline__ float reduce_scatter32(float* v, int lane) {
-#pragma unroll
-    for (int off = 16, n = 32; off >= 1; off >>= 1, n >>= 1) {
-        const bool up = (lane & off) != 0;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            if (i < n / 2) {
-                const float send = up ? v[i] : v[i + n / 2];
-                const float keep = up ? v[i + n / 2] : v[i];
-                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-            }
-        }
-    }
-    return v[0];
-}
-
-// Same for 16 values: lane L holds the sum of value L / 2.
+// Butterfly reduce-scatter of 16 values over a warp: afterwards lanes 2L and 2L + 1 hold
+// the sum of value L over all lanes.
 __device__ __forceinline__ float reduce_scatter16(float* v, int lane) {
 #pragma unroll
     for (int off = 16, n = 16; off >= 2; off >>= 1, n >>= 1) {
@@ -107,7 +91,7 @@ __device__ __forceinline__ float reduce_scatter16(float* v, int lane) {
 // Every chunk adds its share of the gradient to the same accumulators.
 template <int NFC>
 __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int k, float4 (*sbuf)[kBB][6],
-                                          uint32_t (*sid)[kBB], float4* spl) {
+                                          uint32_t (*sid)[kBB], float4* spl, float (*sbp)[32]) {
     const int lane = threadIdx.x & 31;
     const gsrf_grid& gr = a.gr;
     const int chunk = k % a.nchunk, blk = k / a.nchunk;
@@ -151,6 +135,16 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
                 Gs[2 * q + 1] = gq2.y;
             }
         }
+    }
+    // The ray's basis in the order of the coefficient accumulators -- 1, P10, P20, P30,
+    // then the six complex Y_{l,m>0} -- stored per lane with slot i holding basis value
+    // i ^ (lane & 15), the order the select-free reduce-scatter below needs.
+    {
+        const float b[16] = {1.0f, P[0], P[1], P[2], Y[0], Y[1], Y[2], Y[3], Y[4], Y[5], Y[6], Y[7], Y[8], Y[9],
+                             Y[10], Y[11]};
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sbp[i][lane] = b[i ^ (lane & 15)];
+        __syncwarp();
     }
     const Bundle bun = warp_bundle(valid, dx, dy, dz);  // the forward's warp cone and planes
     warp_planes(gr, u_lo, v_lo, bw, bh, bun, valid, dx, dy, dz, spl);
@@ -212,9 +206,8 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
             PairGeo pg;
             bool hit = pos <= last && pair_cone(v0, dx, dy, dz) && pair_hits(v1, s0, s1, s2, dx, dy, dz, r_rx, pg);
             if (!__any_sync(0xffffffffu, hit)) continue;
-            float gq[32], go[16];
-#pragma unroll
-            for (int i = 0; i < 32; ++i) gq[i] = 0.0f;
+            float go[16];
+            float g_pr = 0.0f, g_pi = 0.0f;  // dL/d psi (real, imaginary) of this pair on this ray
 #pragma unroll
             for (int i = 0; i < 16; ++i) go[i] = 0.0f;
             if (hit) {
@@ -246,7 +239,7 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
                 // Phi = sum_s omega_s Re(conj(G_s) dS_s/dphi_s) (App. D.1, D.2)
                 const float er = v1.w, ei = rec[2].x;
                 const float wr = er * Tr - ei * Ti, wi = er * Ti + ei * Tr;
-                float g_alpha, Theta, Phi, g_pr, g_pi;
+                float g_alpha, Theta, Phi;
                 if constexpr (NFC == 1) {
                     const float Gr = Gs[0], Gi = Gs[1], Rr = Rs[0], Ri = Rs[1];
                     const float zr = alpha * (pr * wr - pi * wi), zi = alpha * (pr * wi + pi * wr);
@@ -288,18 +281,6 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
                         pwi = pwi * rc - pwr * rs;
                         pwr = npr;
                     }
-                }
-                // folded coefficients
-                gq[0] = g_pr; gq[1] = g_pi;
-                gq[2] = g_pr * P[0]; gq[3] = g_pi * P[0];
-                gq[4] = g_pr * P[1]; gq[5] = g_pi * P[1];
-                gq[6] = g_pr * P[2]; gq[7] = g_pi * P[2];
-#pragma unroll
-                for (int t = 0; t < 6; ++t) {
-                    gq[8 + 4 * t] = g_pr * Y[2 * t];
-                    gq[8 + 4 * t + 1] = g_pr * Y[2 * t + 1];
-                    gq[8 + 4 * t + 2] = g_pi * Y[2 * t];
-                    gq[8 + 4 * t + 3] = g_pi * Y[2 * t + 1];
                 }
                 // transmittance phase theta_s = omega_s b dt
                 const float g_b = Theta * pg.dt;
@@ -356,8 +337,28 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
                 go[13] = g_b;
             }
             float* acc = a.acc + (size_t)sid[bf][j] * kGrad;
-            const float sq = reduce_scatter32(gq, lane);
-            atomicAdd(acc + 14 + lane, sq);
+            // coefficient gradients: value v (0..31) is g_pr b[v] for v < 16 and g_pi b[v - 16]
+            // after, summed over the warp's rays.  Stored in slot v ^ lane, every lane keeps
+            // the lower half and sends the upper half in every butterfly round, with no
+            // selects; lane L ends with value L.
+            {
+                const bool sw = (lane & 16) != 0;
+                const float ga = sw ? g_pi : g_pr, gb = sw ? g_pr : g_pi;
+                float q[32];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float bi = sbp[i][lane];
+                    q[i] = ga * bi;
+                    q[16 + i] = gb * bi;
+                }
+#pragma unroll
+                for (int off = 16, n = 32; off >= 1; off >>= 1, n >>= 1) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (i < n / 2) q[i] += __shfl_xor_sync(0xffffffffu, q[i + n / 2], off);
+                }
+                atomicAdd(acc + 14 + lane, q[0]);
+            }
             const float so = reduce_scatter16(go, lane);
             if ((lane & 1) == 0 && (lane >> 1) < 14) atomicAdd(acc + (lane >> 1), so);
         }
@@ -393,6 +394,7 @@ __global__ void __launch_bounds__(kBThreads, NFC == 1 ? 4 : (NFC == 8 ? 3 : 2)) 
     __shared__ float4 sbuf[kBW][2][kBB][6];
     __shared__ uint32_t sid[kBW][2][kBB];
     __shared__ float4 spl[kBW][4];
+    __shared__ float sbp[kBW][16][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned per_rx = (unsigned)a.n_tiles * (unsigned)a.per_tile;
     for (;;) {
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(kBThreads, NFC == 1 ? 4 : (NFC == 8 ? 3 : 2)) 
         const uint32_t id = order[it];
         const unsigned rem = id % per_rx;
         bwd_block<NFC>(a, (int)(id / per_rx), (int)(rem / (unsigned)a.per_tile), (int)(rem % (unsigned)a.per_tile),
-                       sbuf[warp], sid[warp], spl[warp]);
+                       sbuf[warp], sid[warp], spl[warp], sbp[warp]);
         __syncwarp();
     }
 }
@@ -463,7 +465,21 @@ __global__ void __launch_bounds__(256) k_grad_params(gsrf_gaussians g, const GSh
     }
     if (g_phase_b) g_phase_b[k] += A[13];
     if (g_coeffs) {
-        const float* q = A + 14;
+        // accumulators 14..29: dL/d psi_re times 1, P10, P20, P30, y11 .. y33 (re, im);
+        // 30..45: the same for dL/d psi_im.  q[] restores the folded order of kFle.
+        const float* ar = A + 14;
+        const float* ai = A + 30;
+        float q[kFle];
+        for (int i = 0; i < 4; ++i) {
+            q[2 * i] = ar[i];
+            q[2 * i + 1] = ai[i];
+        }
+        for (int t = 0; t < 6; ++t) {
+            q[8 + 4 * t] = ar[4 + 2 * t];
+            q[8 + 4 * t + 1] = ar[5 + 2 * t];
+            q[8 + 4 * t + 2] = ai[4 + 2 * t];
+            q[8 + 4 * t + 3] = ai[5 + 2 * t];
+        }
         float* gc = g_coeffs + (size_t)k * 2 * kNB;
         const int m0[4] = {0, 2, 6, 12};
         for (int i = 0; i < 4; ++i) {
