@@ -139,12 +139,18 @@ def barrier(ws):
         dist.barrier()
 
 
+def _reduce_device():
+    """NCCL reduces CUDA tensors, gloo (the CPU tests of this path) CPU tensors."""
+    import torch.distributed as dist
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
+
+
 def max_over_ranks(x: float, ws: int) -> float:
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -154,9 +160,24 @@ def sum_over_ranks(x: float, ws: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_reduce_device())
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def rank_receivers(cfg: dict, rank: int) -> dict:
+    """Replicas shard by receiver: every rank renders the same scene for its own
+    receivers.  Rank 0 keeps the workload's receivers; rank r > 0 draws its own from a
+    generator seeded by r (same box, same count)."""
+    if rank == 0:
+        return cfg
+    import numpy as np
+
+    from paper_2502_01826_gb300 import synthetic
+    g = np.random.Generator(np.random.PCG64(synthetic.BASE_SEED + 7919 * rank))
+    out = dict(cfg)
+    out["rx"] = synthetic.positions(g, cfg["rx"].shape[0])
+    return out
 
 
 # ------------------------------------------------------------------ CPU oracle leg
@@ -227,7 +248,7 @@ def run_ours(args, ws, rank):
     from paper_2502_01826_gb300.render import Renderer, make_grid, received_signal, to_device
 
     L.load(build_if_missing=True)
-    cfg = synthetic.config_ble(n_rx=args.n_rx, seed_offset=0)
+    cfg = rank_receivers(synthetic.config_ble(n_rx=args.n_rx, seed_offset=0), rank)
     K, n_rx = cfg["scene"]["means"].shape[0], cfg["rx"].shape[0]
     grid = make_grid(**cfg["grid"])
     dev = torch.device("cuda")
@@ -380,7 +401,8 @@ def run_ours(args, ws, rank):
                              "stage": R.plan.stage or 32, "autotuned": tune is not None and "best" in tune},
                    "tile_gaussian_pairs_binned_per_step": binned_per_step,
                    "l2": "flushed between timed steps (256 MB write, outside the events)",
-                   "parallelism": "replicas: each rank renders its own 64 receivers" if ws > 1 else "1 GPU"},
+                   "parallelism": "replicas: each rank renders the scene for its own %d receivers" % n_rx
+                   if ws > 1 else "1 GPU"},
         "spectra_per_s": spectra_s,
         "stage_ms": stage_ms,
         "plain_launch": {"ms_per_step": ms_plain, "spectra_per_s": n_rx / (ms_plain / 1e3),
