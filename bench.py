@@ -607,9 +607,14 @@ def train_leg(args, ws, flush):
     S_gt = Rg.forward(gt, rx, tx).clone()
     del Rg
     p = {k: v.clone().requires_grad_(True) for k, v in to_device(cfg["scene"]).items()}
+    pd = {k: v.detach() for k, v in p.items()}
     R = Renderer(K, n_rx, grid, cfg["f0"])
-    R.ensure_capacity({k: v.detach() for k, v in p.items()}, rx, tx)
-    tune = autotune(R, {k: v.detach() for k, v in p.items()}, rx, tx, args, reps=2, training=True)
+    R.ensure_capacity(pd, rx, tx)
+    out = torch.empty(R.out_shape(), dtype=torch.float32, device="cuda")
+    R.render_fwd(pd, out)  # algorithmic candidate tests: those of the paper's 16 x 16 tiles
+    torch.cuda.synchronize()
+    tests_16x16 = int(R.status().stats[0])
+    tune = autotune(R, pd, rx, tx, args, reps=2, training=True)
     n = S_gt.numel() // 2
 
     def step():
@@ -635,10 +640,26 @@ def train_leg(args, ws, flush):
     torch.cuda.synchronize()
     ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     t = max_over_ranks(ms * args.steps / 1e3, ws)
+    # the forward render and the backward render alone, with the same split (untimed
+    # for the step above): the 200k-Gaussian roofline of the compositing kernel
+    R.project(pd, rx, tx)
+    R.bin()
+    state = R.ray_state()
+    ms_f = _time_steps(lambda: R.render_fwd(pd, out, ray_state=state), args.steps, flush)
+    up = torch.randn(R.out_shape(), dtype=torch.float32, device="cuda")
+    gr = {k: torch.zeros_like(v) for k, v in pd.items()}
+    ms_b = _time_steps(lambda: R.render_bwd(pd, state, up, gr), args.steps, flush)
+    pk_, pk_kind = peaks()
+    peak = SMS * FP32_LANES * 2 * float(pk_.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    flops = tests_16x16 * FLOP_TEST + pairs * FLOP_HIT
     return {"workload": cfg["name"], "n_gauss": K, "n_rx": n_rx, "ms_per_step": ms,
             "pairs_per_step": pairs, "pairs_per_s": sum_over_ranks(pairs * args.steps, ws) / t,
             "spectra_per_s": sum_over_ranks(n_rx * args.steps, ws) / t,
             "split": tune.get("best", tune) if tune else None,
+            "render_fwd_ms": ms_f, "render_bwd_ms": ms_b,
+            "roofline_fwd": {"kernel": "k_render_queue", "bound": "alu", "achieved": flops / (ms_f * 1e-3) / 1e12,
+                             "peak": peak, "unit": "TFLOP/s", "frac": flops / (ms_f * 1e-3) / 1e12 / peak,
+                             "flop_per_launch": flops, "candidate_tests_16x16_tiles": tests_16x16},
             "what": "forward + complex-MSE loss + hand-written backward to all parameters"}
 
 
