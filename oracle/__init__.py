@@ -46,7 +46,7 @@ class Grid(C.Structure):
                 ("az0_deg", C.c_float), ("daz_deg", C.c_float),
                 ("el0_deg", C.c_float), ("del_deg", C.c_float),
                 ("r_rx", C.c_float), ("eps_T", C.c_float), ("alpha_max", C.c_float),
-                ("tile_w", C.c_int32), ("tile_h", C.c_int32)]
+                ("tile_w", C.c_int32), ("tile_h", C.c_int32), ("variant", C.c_int32)]
 
 
 class Scene(C.Structure):
@@ -111,13 +111,15 @@ def _f32(a):
 
 
 def make_grid(n_az, n_el, az0_deg=0.0, daz_deg=None, el0_deg=0.0, del_deg=None, r_rx=1.0,
-              eps_T=1e-4, alpha_max=0.99, tile_w=16, tile_h=16) -> Grid:
+              eps_T=1e-4, alpha_max=0.99, tile_w=16, tile_h=16, variant=0) -> Grid:
+    """variant: bit 1 = radiance at the Gaussian's direction, bit 2 = normalised weight
+    (see or_grid in gsrf_oracle.h)."""
     if daz_deg is None:
         daz_deg = 360.0 / n_az
     if del_deg is None:
         del_deg = 90.0 / n_el
     return Grid(n_az, n_el, az0_deg, daz_deg, el0_deg, del_deg, r_rx, eps_T, alpha_max,
-                tile_w, tile_h)
+                tile_w, tile_h, variant)
 
 
 class _SceneRef:

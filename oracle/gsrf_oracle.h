@@ -54,6 +54,12 @@ typedef struct {
     float eps_T;                 /* early-termination threshold on prod(1-alpha); 0 = off */
     float alpha_max;             /* clamp on alpha */
     int32_t tile_w, tile_h;      /* rays per tile along azimuth / elevation */
+    int32_t variant;             /* readings other than the default (bit mask), forward only:
+                                  *   1  the Fourier-Legendre radiance of Gaussian k is taken at
+                                  *      the direction of mu_k seen from the receiver (Sec. 4.3's
+                                  *      v_k) for every ray, instead of at each ray's direction;
+                                  *   2  the weight is the normalised Gaussian density at the
+                                  *      representative point (App. A.3), g / ((2 pi)^1.5 |Sigma|^0.5) */
 } or_grid;
 
 typedef struct {

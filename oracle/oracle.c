@@ -243,6 +243,7 @@ typedef struct {
     int32_t n_f, mode;
     /* per Gaussian, FP64 */
     double *Sinv, *mu, *op, *dpath, *b;
+    double *psig;           /* variant 1: psi_k at the direction of mu_k, [n][2] */
     /* candidate lists */
     const int64_t *tile_start;
     const uint32_t *ids;    /* mode 0 */
@@ -358,10 +359,15 @@ static void render_one(rctx *c, int64_t i)
         if (a > (double)g->alpha_max) a = (double)g->alpha_max;
         const float *cf = c->s->coeffs + (size_t)k * 2 * OR_NB;
         double pr = 0.0, pi = 0.0; /* psi_k(ray) = sum_n c_n Y_n */
-        for (int n = 0; n < OR_NB; ++n) {
-            double cr = cf[2 * n], ci = cf[2 * n + 1];
-            pr += cr * Y[2 * n] - ci * Y[2 * n + 1];
-            pi += cr * Y[2 * n + 1] + ci * Y[2 * n];
+        if (g->variant & 1) {
+            pr = c->psig[2 * k];
+            pi = c->psig[2 * k + 1];
+        } else {
+            for (int n = 0; n < OR_NB; ++n) {
+                double cr = cf[2 * n], ci = cf[2 * n + 1];
+                pr += cr * Y[2 * n] - ci * Y[2 * n + 1];
+                pi += cr * Y[2 * n + 1] + ci * Y[2 * n];
+            }
         }
         const double zabs = a * sqrt(pr * pr + pi * pi) * Ta; /* |z_k|, every frequency */
         sabs += zabs;
@@ -435,6 +441,7 @@ static int prepare(rctx *c, const or_scene *s, const float *rx, const float *tx,
     c->op = (double *)malloc(sizeof(double) * nn);
     c->dpath = (double *)malloc(sizeof(double) * nn);
     c->b = (double *)malloc(sizeof(double) * nn);
+    c->psig = (double *)malloc(sizeof(double) * 2 * nn);
     for (int i = 0; i < 3; ++i) c->rx[i] = rx[i];
     for (int64_t k = 0; k < n; ++k) {
         or_gaussian(s, k, NULL, c->Sinv + 9 * k, c->op + k);
@@ -447,6 +454,24 @@ static int prepare(rctx *c, const or_scene *s, const float *rx, const float *tx,
         }
         c->dpath[k] = sqrt(dt) + sqrt(dr); /* Tx -> mu_k -> Rx */
         c->b[k] = s->phase_b ? (double)s->phase_b[k] : 0.0;
+        if (g->variant & 2) { /* normalised density: 1 / ((2 pi)^1.5 |Sigma|^0.5), |Sigma|^0.5 = s0 s1 s2 */
+            double ls = (double)s->log_scales[3 * k] + s->log_scales[3 * k + 1] + s->log_scales[3 * k + 2];
+            c->op[k] *= exp(-ls) / pow(2.0 * M_PI, 1.5);
+        }
+        if (g->variant & 1) { /* psi_k at the direction of mu_k (alpha = 0 on the vertical) */
+            double v[3] = {c->mu[3 * k] - rx[0], c->mu[3 * k + 1] - rx[1], c->mu[3 * k + 2] - rx[2]};
+            double D = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), rho = hypot(v[0], v[1]);
+            double al = rho > 0.0 ? atan2(v[1], v[0]) : 0.0, x = D > 0.0 ? v[2] / D : 0.0;
+            double Yg[2 * OR_NB], pr = 0.0, pi = 0.0;
+            or_basis(al, x, Yg);
+            const float *cf = s->coeffs + (size_t)k * 2 * OR_NB;
+            for (int n2 = 0; n2 < OR_NB; ++n2) {
+                pr += cf[2 * n2] * Yg[2 * n2] - cf[2 * n2 + 1] * Yg[2 * n2 + 1];
+                pi += cf[2 * n2] * Yg[2 * n2 + 1] + cf[2 * n2 + 1] * Yg[2 * n2];
+            }
+            c->psig[2 * k] = pr;
+            c->psig[2 * k + 1] = pi;
+        }
     }
     /* candidate lists */
     int32_t nt = n_tiles_u(g) * n_tiles_v(g);
@@ -477,7 +502,7 @@ static int prepare(rctx *c, const or_scene *s, const float *rx, const float *tx,
 
 static void release(rctx *c)
 {
-    free(c->Sinv); free(c->mu); free(c->op); free(c->dpath); free(c->b);
+    free(c->Sinv); free(c->mu); free(c->op); free(c->dpath); free(c->b); free(c->psig);
     free((void *)c->tile_start); free((void *)c->ids); free((void *)c->order);
 }
 
@@ -487,6 +512,7 @@ static int check_args(const or_scene *s, const or_grid *g, int32_t n_f, int32_t 
     if (g->n_az < 1 || g->n_el < 1 || g->tile_w < 1 || g->tile_h < 1) return -1;
     if ((g->n_az + g->tile_w - 1) / g->tile_w > 64) return -1;
     if (!(g->daz_deg > 0.0f) || !(g->del_deg > 0.0f)) return -1;
+    if (g->variant < 0 || g->variant > 3) return -1;
     return 0;
 }
 

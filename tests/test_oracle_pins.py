@@ -736,3 +736,65 @@ def test_path_phase_reduction(oracle_lib):
     ref = np.mod(2 * np.pi * 5.2e9 * d / 3e8, 2 * np.pi)
     diff = np.angle(np.exp(1j * (ph - ref)))
     assert np.max(np.abs(diff)) < 1e-9 and np.all((ph >= 0) & (ph < 2 * np.pi))
+
+
+# --------------------------------------------------------------------------- variant readings
+
+def _psi(c, alpha, x):
+    """sum_n c_n e^{i m alpha} P_l^m(x), P without the Condon-Shortley phase, via scipy."""
+    from scipy.special import lpmv
+    return sum(c[l * l + l + m] * np.exp(1j * m * alpha) * (-1) ** m * lpmv(m, l, x)
+               for l in range(4) for m in range(-l, l + 1))
+
+
+def test_variant_radiance_at_the_gaussian_direction(oracle_lib):
+    """Variant 1 (radiance of Gaussian k at the direction of mu_k, Sec. 4.3's v_k): with
+    one Gaussian (T = 1) each hit ray's signal is the default reading's times
+    psi(v_k) / psi(ray); nothing else changes."""
+    rng = np.random.default_rng(3)
+    coeffs = rng.normal(0, 0.3, (16, 2))
+    r = np.array([2.0, 2.0, 0.5], np.float32)
+    t = np.array([7.0, 1.0, 2.5], np.float32)
+    s = one_gaussian((4.0, 3.0, 1.3), log_s=(math.log(0.4), math.log(0.25), math.log(0.3)),
+                     quat=(0.8, 0.2, -0.3, 0.1), logit=0.4, coeffs=coeffs, b=0.2)
+    out0 = oracle_lib.render(s, r, t, 2.4e9, small_grid(oracle_lib), mode=1)
+    out1 = oracle_lib.render(s, r, t, 2.4e9, small_grid(oracle_lib, variant=1), mode=1)
+    A, E, dirs = ray_dirs(small_grid(oracle_lib))
+    c = s["coeffs"][0, :, 0].astype(np.float64) + 1j * s["coeffs"][0, :, 1]
+    v = s["means"][0].astype(np.float64) - r.astype(np.float64)
+    psi_k = _psi(c, math.atan2(v[1], v[0]), v[2] / np.linalg.norm(v))
+    n = 0
+    for i in range(len(dirs)):
+        if out0["S"][0, i] == 0:
+            assert out1["S"][0, i] == 0
+            continue
+        ref = out0["S"][0, i] * psi_k / _psi(c, A[i], math.sin(E[i]))
+        assert abs(out1["S"][0, i] - ref) < 1e-9 * abs(ref)
+        n += 1
+    assert n > 10
+
+
+def test_variant_normalised_weight(oracle_lib):
+    """Variant 2 (normalised density, App. A.3): with one Gaussian whose alpha never
+    reaches the clamp, every ray's signal is the default's times
+    1 / ((2 pi)^1.5 s0 s1 s2)."""
+    rng = np.random.default_rng(4)
+    log_s = (0.1, -0.15, 0.05)
+    s = one_gaussian((4.5, 2.5, 1.0), log_s=log_s, quat=(0.7, -0.1, 0.3, 0.2), logit=0.2,
+                     coeffs=rng.normal(0, 0.3, (16, 2)), b=0.1)
+    r = np.array([1.5, 1.0, 0.8], np.float32)
+    t = np.array([8.0, 6.0, 2.0], np.float32)
+    out0 = oracle_lib.render(s, r, t, 2.4e9, small_grid(oracle_lib), mode=1)
+    out2 = oracle_lib.render(s, r, t, 2.4e9, small_grid(oracle_lib, variant=2), mode=1)
+    norm = 1.0 / ((2 * math.pi) ** 1.5 * math.exp(sum(float(np.float32(x)) for x in log_s)))
+    assert np.count_nonzero(out0["S"]) > 10
+    assert np.allclose(out2["S"], out0["S"] * norm, rtol=1e-12, atol=0)
+
+
+def test_variant_gradient_refused(oracle_lib):
+    s = one_gaussian((4.0, 3.0, 1.0))
+    r = np.array([2.0, 2.0, 0.5], np.float32)
+    G = np.ones((1, 72 * 18), complex)
+    oracle_lib.render_grad(s, r, r, 2.4e9, small_grid(oracle_lib), G)  # the default reading runs
+    with pytest.raises(ValueError, match="rejected"):
+        oracle_lib.render_grad(s, r, r, 2.4e9, small_grid(oracle_lib, variant=1), G)
