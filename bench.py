@@ -377,6 +377,8 @@ def run_ours(args, ws, rank):
     csi = csi_leg(args, ws, flush) if not args.no_train else None
     million = million_leg(args, ws, flush) if not args.no_train else None
     uneven = uneven_leg(args, flush) if args.uneven else None
+    variants = variants_leg(args, ws, flush, split=(R.plan.grid.tile_w, R.plan.grid.tile_h,
+                                                    R.plan.ray_block_w or 8, R.plan.stage or 32))
 
     pk_, pk_kind = peaks()
     mhz = float(pk_.get("sm_max_mhz", 2070.0))
@@ -423,6 +425,7 @@ def run_ours(args, ws, rank):
         "csi": csi,
         "fwd_bwd_1m": million,
         "uneven": uneven,
+        "variants": variants,
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": clocks,
     }
@@ -727,6 +730,59 @@ def csi_leg(args, ws, flush):
             "what": "per composited pair all 64 subcarriers; loss on the complex CSI"}
 
 
+def variants_leg(args, ws, flush, split=None):
+    """The BLE workload rendered under each reading of the radiance direction and the
+    Gaussian weight (bits: 1 = radiance at the direction of the mean, 2 = normalised
+    density), with the main run's work split: forward step time (project + bin + render +
+    RSSI) and how far each reading moves the per-ray signal and the RSSI from the default
+    reading (per-ray radiance, unnormalised weight).  CUDA events, L2 flushed between steps."""
+    import numpy as np
+    import torch
+
+    from paper_2502_01826_gb300 import _lib as L
+    from paper_2502_01826_gb300 import synthetic
+    from paper_2502_01826_gb300.render import Renderer, make_grid, received_signal, to_device
+
+    cfg = rank_receivers(synthetic.config_ble(n_rx=args.n_rx), int(os.environ.get("RANK", "0")))
+    K, n_rx = cfg["scene"]["means"].shape[0], cfg["rx"].shape[0]
+    tw, th, bw, stg = split or (16, 16, 8, 32)
+    grid = make_grid(**cfg["grid"], tile_w=tw, tile_h=th)
+    p = to_device(cfg["scene"])
+    rx = torch.tensor(cfg["rx"], device="cuda")
+    tx = torch.tensor(cfg["tx"], device="cuda")
+    res, ref = {}, None
+    for v in (0, 1, 2, 3):
+        R = Renderer(K, n_rx, grid, cfg["f0"], ray_block_w=bw, stage=stg, variant=v)
+        R.ensure_capacity(p, rx, tx)
+        out = torch.empty(R.out_shape(), dtype=torch.float32, device="cuda")
+
+        def fwd():
+            R.forward(p, rx, tx, out=out)
+            return received_signal(out, L.SIG_RSSI_DB)
+
+        for _ in range(args.warmup):
+            rssi = fwd()
+        torch.cuda.synchronize()
+        st = R.status()
+        L.check("variant %d render (device status)" % v, st.code)
+        ms = _time_steps(fwd, args.steps, flush)
+        S = out.double().cpu().numpy()
+        S = S[..., 0] + 1j * S[..., 1]
+        db = rssi.double().cpu().numpy().ravel()
+        rec = {"ms_per_step": max_over_ranks(ms * args.steps, ws) / args.steps,
+               "pairs_per_step": int(st.stats[1])}
+        if ref is None:
+            ref = (S, db)
+        else:
+            rec["rel_l2_rays_vs_default"] = float(np.linalg.norm(S - ref[0]) / np.linalg.norm(ref[0]))
+            rec["max_abs_rssi_db_vs_default"] = float(np.max(np.abs(db - ref[1])))
+        res["variant_%d" % v] = rec
+        del R, out
+    return {"workload": cfg["name"], "split": "%dx%d,%d,%d" % (tw, th, bw, stg), **res,
+            "what": "variant bits: 1 = radiance at the direction of the Gaussian's mean, 2 = weight "
+                    "normalised by (2 pi)^1.5 s0 s1 s2; forward only"}
+
+
 def million_leg(args, ws, flush, every=128, slots=32):
     """Forward + backward at 1,000,000 Gaussians (the top of the uneven workload's range)
     with transmittance checkpoints every `every` tile-list positions (`slots` per ray):
@@ -793,7 +849,7 @@ def main():
                     "rays per warp, 32 candidates per stage) instead of autotuning it")
     ap.add_argument("--split", default=None, help="fix the work split instead of tuning it: TWxTH,BW,STAGE "
                     "(e.g. 32x16,8,32), for profiling runs")
-    ap.add_argument("--only", choices=["train", "csi", "million"], default=None,
+    ap.add_argument("--only", choices=["train", "csi", "million", "variants"], default=None,
                     help="run one secondary leg alone and print its record (profiling runs)")
     ap.add_argument("--train-gauss", type=int, default=200_000, help="Gaussians of the training leg")
     ap.add_argument("--train-rx", type=int, default=16, help="receivers of the training leg")
@@ -830,7 +886,7 @@ def main():
     if args.only:
         import torch
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-        leg = {"train": train_leg, "csi": csi_leg, "million": million_leg}[args.only]
+        leg = {"train": train_leg, "csi": csi_leg, "million": million_leg, "variants": variants_leg}[args.only]
         rec = leg(args, ws, flush)
         if rank == 0:
             print(json.dumps({"only": args.only, **rec}))

@@ -100,7 +100,15 @@ typedef struct {
                                 * in front of tile-list positions K, 2K, ... (ckpt_slots of them)
                                 * and the backward re-anchors its recomputed transmittance there */
     int32_t ckpt_slots;        /* checkpoints kept per ray, 1..64 when ckpt_every > 0 */
+    int32_t variant;           /* other readings of the paper, forward only (bit mask, 0 = the
+                                * default): GSRF_VARIANT_RADIANCE_AT_MEAN takes Gaussian k's
+                                * Fourier-Legendre radiance at the direction of mu_k seen from
+                                * the receiver (Sec. 4.3's v_k) for all its rays instead of at
+                                * each ray's direction; GSRF_VARIANT_NORMALISED_WEIGHT weights by
+                                * the normalised density (App. A.3), g / ((2 pi)^1.5 |Sigma|^0.5) */
 } gsrf_plan;
+#define GSRF_VARIANT_RADIANCE_AT_MEAN 1
+#define GSRF_VARIANT_NORMALISED_WEIGHT 2
 
 /* Bytes of workspace a plan needs (256-byte aligned base required). [host] out. */
 gsrf_status gsrf_workspace_size(const gsrf_plan *plan, size_t *bytes);
@@ -119,7 +127,8 @@ typedef struct {
                                 * cone of directions that can reach the Gaussian (culling),
                                 * 4-6 whitened receiver offset, 7-8 e^{-j 2 pi f0 d / c}
                                 * (cos, -sin) with the phase reduced in FP64, 9 the
-                                * per-subcarrier step 2 pi df d / c, 10-11 unused */
+                                * per-subcarrier step 2 pi df d / c, 10-11 the radiance at
+                                * the direction of mu (GSRF_VARIANT_RADIANCE_AT_MEAN), else 0 */
 } gsrf_layout;
 gsrf_status gsrf_workspace_layout(const gsrf_plan *plan, gsrf_layout *out);
 
@@ -165,7 +174,8 @@ size_t gsrf_ray_state_bytes(const gsrf_plan *plan);
  *   (+=); any may be NULL.  The gradient of the opacity is taken through its sigmoid, of
  *   the rotation through the quaternion's normalisation, of the scales through exp.
  *   Hit decisions that sit on the integer steps of the method (splatting, the 3-sigma
- *   boundary, the early stop) carry no gradient.  With plan.ckpt_every = K > 0 the
+ *   boundary, the early stop) carry no gradient.  GSRF_ERR_UNSUPPORTED for a plan with
+ *   a variant reading.  With plan.ckpt_every = K > 0 the
  *   recomputed transmittance is replaced by the forward's own at every checkpoint the
  *   walk crosses, so division by (1 - alpha) never runs over more than K list positions
  *   (the per-tile checkpointing of deep scenes).  With n_f > 1 every subcarrier

@@ -17,6 +17,7 @@ STATUS_NAMES = {0: "GSRF_OK", 1: "GSRF_ERR_INVALID_ARG", 2: "GSRF_ERR_CUDA", 3: 
                 4: "GSRF_ERR_TIMEOUT", 5: "GSRF_ERR_NONFINITE", 6: "GSRF_ERR_UNSUPPORTED",
                 7: "GSRF_ERR_TOO_LARGE"}
 SIG_COMPLEX_SUM, SIG_RSSI_DB, SIG_POWER_SUM, SIG_SPECTRUM_MAG = 0, 1, 2, 3
+VARIANT_RADIANCE_AT_MEAN, VARIANT_NORMALISED_WEIGHT = 1, 2
 
 # every exported symbol of include/gsrf.h
 EXPORTS = ["gsrf_workspace_size", "gsrf_workspace_layout", "gsrf_ray_state_bytes", "gsrf_project",
@@ -47,7 +48,7 @@ class gsrf_plan(C.Structure):
     _fields_ = [("n_gauss", C.c_int64), ("n_rx", C.c_int32), ("n_f", C.c_int32), ("f0_hz", C.c_double),
                 ("df_hz", C.c_double), ("grid", gsrf_grid), ("pair_capacity", C.c_int64),
                 ("ray_block_w", C.c_int32), ("stage", C.c_int32), ("ckpt_every", C.c_int32),
-                ("ckpt_slots", C.c_int32)]
+                ("ckpt_slots", C.c_int32), ("variant", C.c_int32)]
 
 
 class gsrf_layout(C.Structure):

@@ -97,6 +97,7 @@ static gsrf_status check_plan(const gsrf_plan* p) {
     if (!(p->stage == 0 || p->stage == 16 || p->stage == 32)) return GSRF_ERR_INVALID_ARG;
     if (p->ckpt_every < 0 || p->ckpt_every % 32 != 0 || p->ckpt_every > (1 << 24)) return GSRF_ERR_INVALID_ARG;
     if (p->ckpt_every > 0 && (p->ckpt_slots < 1 || p->ckpt_slots > 64)) return GSRF_ERR_INVALID_ARG;
+    if (p->variant < 0 || p->variant > 3) return GSRF_ERR_INVALID_ARG;
     const gsrf_status s = check_grid(&p->grid);
     if (s != GSRF_OK) return s;
     const int w = plan_block_w(p);
@@ -197,6 +198,7 @@ gsrf_status gsrf_render_bwd(const gsrf_plan* plan, const gsrf_gaussians* g, void
     if ((s = check_gauss(plan, g)) != GSRF_OK) return s;
     if (!ray_state || !grad_rays || ((uintptr_t)ray_state & 15) != 0 || ((uintptr_t)grad_rays & 7) != 0)
         return GSRF_ERR_INVALID_ARG;
+    if (plan->variant != 0) return GSRF_ERR_UNSUPPORTED;  // the adjoint of the default reading only
     return cuda_status(launch_render_bwd(plan, L, g, workspace, ray_state, grad_rays, g_means, g_log_scales, g_quats,
                                          g_opacity_logit, g_coeffs, g_phase_b, (cudaStream_t)stream));
 }

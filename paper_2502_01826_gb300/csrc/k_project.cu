@@ -21,7 +21,7 @@ __global__ void k_status_init(DevStatus* st) {
 // and |t - mu| in FP64 for the path phase.
 __global__ void __launch_bounds__(256) k_prepare(gsrf_gaussians g, const float* __restrict__ tx,
                                                  GShape* __restrict__ shape, double* __restrict__ dpath_t,
-                                                 float* __restrict__ fle, DevStatus* st) {
+                                                 float* __restrict__ fle, DevStatus* st, int variant) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.n) return;
     const float mx = g.means[3 * k], my = g.means[3 * k + 1], mz = g.means[3 * k + 2];
@@ -61,6 +61,8 @@ __global__ void __launch_bounds__(256) k_prepare(gsrf_gaussians g, const float* 
         }
     out.pad2[0] = out.pad2[1] = out.pad2[2] = 0.0f;
     out.o = 1.0f / (1.0f + expf(-ol));
+    // normalised density (a variant reading): 1 / ((2 pi)^1.5 s0 s1 s2) folded into o
+    if (variant & GSRF_VARIANT_NORMALISED_WEIGHT) out.o *= expf(-(l0 + l1 + l2)) * 0.0634936359f;
     out.b = b;
     out.pad = 0.0f;
     shape[k] = out;
@@ -243,6 +245,32 @@ __device__ __forceinline__ double pair_dist(float ax, float ay, float az, float 
     return (double)sq + (double)corr;
 }
 
+// Radiance (Eq. 9) of one Gaussian, from its folded coefficients q (see kFle), in the
+// direction (cx, cy, cz) (a variant reading: the direction of mu from the receiver); the
+// same basis as the ray table, x = sin(elevation), azimuth 0 on the vertical.
+__device__ __forceinline__ void radiance_at(const float* __restrict__ q, float cx, float cy, float cz, float& pr,
+                                            float& pi) {
+    const float rho = sqrtf(cx * cx + cy * cy), D = sqrtf(rho * rho + cz * cz);
+    const float x = D > 0.0f ? cz / D : 0.0f, sx = D > 0.0f ? rho / D : 1.0f;
+    const float c1 = rho > 0.0f ? cx / rho : 1.0f, s1 = rho > 0.0f ? cy / rho : 0.0f;
+    const float c2 = c1 * c1 - s1 * s1, s2 = 2.0f * s1 * c1;
+    const float c3 = c1 * c2 - s1 * s2, s3 = s1 * c2 + c1 * s2;
+    const float x2 = x * x, sx2 = sx * sx;
+    const float P[3] = {x, 1.5f * x2 - 0.5f, x * (2.5f * x2 - 1.5f)};
+    const float P11 = sx, P21 = 3.0f * x * sx, P31 = (7.5f * x2 - 1.5f) * sx;
+    const float P22 = 3.0f * sx2, P32 = 15.0f * x * sx2, P33 = 15.0f * sx2 * sx;
+    const float Y[12] = {c1 * P11, s1 * P11, c1 * P21, s1 * P21, c1 * P31, s1 * P31,
+                         c2 * P22, s2 * P22, c2 * P32, s2 * P32, c3 * P33, s3 * P33};
+    pr = q[0] + q[2] * P[0] + q[4] * P[1] + q[6] * P[2];
+    pi = q[1] + q[3] * P[0] + q[5] * P[1] + q[7] * P[2];
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+        const float* e = q + 8 + 4 * t;
+        pr += e[0] * Y[2 * t] + e[1] * Y[2 * t + 1];
+        pi += e[2] * Y[2 * t] + e[3] * Y[2 * t + 1];
+    }
+}
+
 // One thread per (receiver, Gaussian): whitened offset, depth key, coverage, phase.
 __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __restrict__ rxp,
                                               const GShape* __restrict__ shape,
@@ -250,7 +278,8 @@ __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __r
                                               int ntu, int ntv, double f0_over_c, float two_pi_df_over_c,
                                               View* __restrict__ view, Cover* __restrict__ cover,
                                               uint32_t* __restrict__ dkey, float* __restrict__ rx_keep,
-                                              const float* __restrict__ txp, float* __restrict__ tx_keep) {
+                                              const float* __restrict__ txp, float* __restrict__ tx_keep,
+                                              const float* __restrict__ fle, int variant) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y;
     if (k == 0) {  // the render and its backward read the positions from the workspace
@@ -301,6 +330,7 @@ __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __r
     v.ei = -s;
     v.omd = two_pi_df_over_c * (float)d;
     v.pad0 = v.pad1 = 0.0f;
+    if (variant & GSRF_VARIANT_RADIANCE_AT_MEAN) radiance_at(fle + (size_t)k * kFle, -ux, -uy, -uz, v.pad0, v.pad1);
     view[o] = v;
 }
 
@@ -319,13 +349,13 @@ cudaError_t launch_project(const gsrf_plan* p, const Layout& L, const gsrf_gauss
     k_raytab<<<(n_rays + 255) / 256, 256, 0, st>>>(p->grid, at<float>(ws, L.raytab));
     const unsigned nb = (unsigned)((L.n + 255) / 256);
     k_prepare<<<nb, 256, 0, st>>>(*g, tx, at<GShape>(ws, L.gshape), at<double>(ws, L.dpath),
-                                  at<float>(ws, L.fle), status);
+                                  at<float>(ws, L.fle), status, p->variant);
     k_view<<<dim3(nb, L.n_rx), 256, 0, st>>>(*g, rx, at<GShape>(ws, L.gshape), at<double>(ws, L.dpath),
                                               p->grid, L.ntu, L.ntv, p->f0_hz / kC,
                                               (float)(2.0 * 3.14159265358979323846 * p->df_hz / kC),
                                               at<View>(ws, L.view), at<Cover>(ws, L.cover),
                                               at<uint32_t>(ws, L.dkey), at<float>(ws, L.rxpos), tx,
-                                              at<float>(ws, L.txpos));
+                                              at<float>(ws, L.txpos), at<float>(ws, L.fle), p->variant);
     return cudaGetLastError();
 }
 

@@ -60,6 +60,7 @@ struct RenderArgs {
     float4* ck;   // transmittance checkpoints [slot][ray] (Tr, Ti, Gamma, Ta), or null
     int ck_every; // list positions between checkpoints (a multiple of 32)
     int ck_slots;
+    int variant;  // GSRF_VARIANT_* bits
 };
 
 constexpr int kMaxJobs = 96;
@@ -207,7 +208,12 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
                     float gw;
                     const float alpha = pair_alpha(s2.y, pg.m2r, amax, gw);
                     float pr, pi;
-                    fle_psi(reinterpret_cast<const float4*>(a.fle + (size_t)sid[bf][j] * kFle), P, Y, pr, pi);
+                    if (a.variant & GSRF_VARIANT_RADIANCE_AT_MEAN) {  // one radiance per Gaussian
+                        pr = rec[2].z;
+                        pi = rec[2].w;
+                    } else {
+                        fle_psi(reinterpret_cast<const float4*>(a.fle + (size_t)sid[bf][j] * kFle), P, Y, pr, pi);
+                    }
                     // S += alpha psi E T, E = e^{-j phi} = (er, ei)
                     const float er = v1.w, ei = rec[2].x;
                     const float etr = er * Tr - ei * Ti, eti = er * Ti + ei * Tr;
@@ -432,6 +438,7 @@ static RenderArgs render_args(const gsrf_plan* p, const Layout& L, void* ws, flo
                : nullptr;
     a.ck_every = p->ckpt_every > 0 ? p->ckpt_every : 1;
     a.ck_slots = p->ckpt_slots;
+    a.variant = p->variant;
     return a;
 }
 

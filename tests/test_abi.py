@@ -49,10 +49,10 @@ def test_struct_layouts_match_header(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\\n", sizeof(gsrf_grid), sizeof(gsrf_gaussians), sizeof(gsrf_plan),
          sizeof(gsrf_layout), sizeof(gsrf_run_status));
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", offsetof(gsrf_plan, f0_hz), offsetof(gsrf_plan, grid),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", offsetof(gsrf_plan, f0_hz), offsetof(gsrf_plan, grid),
          offsetof(gsrf_plan, pair_capacity), offsetof(gsrf_run_status, stats), offsetof(gsrf_layout, view),
          offsetof(gsrf_plan, ray_block_w), offsetof(gsrf_plan, stage), offsetof(gsrf_plan, ckpt_every),
-         offsetof(gsrf_plan, ckpt_slots));
+         offsetof(gsrf_plan, ckpt_slots), offsetof(gsrf_plan, variant));
   return 0;
 }
 """)
@@ -65,7 +65,8 @@ int main(void) {
                      C.sizeof(L.gsrf_layout), C.sizeof(L.gsrf_run_status)]
     assert offs == [L.gsrf_plan.f0_hz.offset, L.gsrf_plan.grid.offset, L.gsrf_plan.pair_capacity.offset,
                     L.gsrf_run_status.stats.offset, L.gsrf_layout.view.offset, L.gsrf_plan.ray_block_w.offset,
-                    L.gsrf_plan.stage.offset, L.gsrf_plan.ckpt_every.offset, L.gsrf_plan.ckpt_slots.offset]
+                    L.gsrf_plan.stage.offset, L.gsrf_plan.ckpt_every.offset, L.gsrf_plan.ckpt_slots.offset,
+                    L.gsrf_plan.variant.offset]
 
 
 def plan(n=1000, n_rx=4, n_az=360, n_el=90, cap=100000, **kw):
@@ -130,7 +131,7 @@ def test_tile_shapes_ray_blocks_and_stages_accepted(lib, tw, th, bw, stage):
 @pytest.mark.parametrize("fields", [dict(ray_block_w=2), dict(ray_block_w=12), dict(ray_block_w=64),
                                     dict(stage=8), dict(stage=24), dict(stage=-1), dict(ckpt_every=48, ckpt_slots=4),
                                     dict(ckpt_every=-32, ckpt_slots=4), dict(ckpt_every=64, ckpt_slots=0),
-                                    dict(ckpt_every=64, ckpt_slots=65)])
+                                    dict(ckpt_every=64, ckpt_slots=65), dict(variant=4), dict(variant=-1)])
 def test_bad_ray_block_stage_or_checkpoints_rejected(lib, fields):
     sz = C.c_size_t()
     p = plan()
@@ -190,3 +191,14 @@ def test_autotune_sizing_and_argument_checks(lib):
     bwd = L.gsrf_tune_backward(None, 4096, None, None, None, None, None, None)  # no ray state
     assert lib.gsrf_autotune(C.byref(p), C.byref(g), dev, dev, dev, b.value, dev, C.byref(bwd), 3, res, 4,
                              C.byref(n), C.byref(best), None) == L.GSRF_ERR_INVALID_ARG
+
+
+def test_backward_refuses_variant_readings(lib):
+    p = plan()
+    p.variant = L.VARIANT_RADIANCE_AT_MEAN
+    sz = C.c_size_t()
+    assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_OK  # the forward takes it
+    dev = C.c_void_p(1 << 20)
+    g = L.gsrf_gaussians(1000, dev, dev, dev, dev, dev, None)
+    assert lib.gsrf_render_bwd(C.byref(p), C.byref(g), dev, sz.value, dev, dev, None, None, None, None, None,
+                               None, None) == L.GSRF_ERR_UNSUPPORTED

@@ -1,0 +1,41 @@
+"""Variant readings (forward only): the radiance at the direction of the Gaussian's mean
+instead of each ray's (GSRF_VARIANT_RADIANCE_AT_MEAN) and the normalised density weight
+(GSRF_VARIANT_NORMALISED_WEIGHT), alone and together, held to the same bars against the
+oracle rendering the same reading."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_01826_gb300 import _lib as L
+from paper_2502_01826_gb300 import synthetic
+
+from gpu_util import compare, gpu_render, oracle_pair, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+    oracle.build()
+
+
+@pytest.mark.parametrize("variant", [L.VARIANT_RADIANCE_AT_MEAN, L.VARIANT_NORMALISED_WEIGHT,
+                                     L.VARIANT_RADIANCE_AT_MEAN | L.VARIANT_NORMALISED_WEIGHT])
+@pytest.mark.parametrize("workload", ["plain", "dense"])
+def test_variant_matches_oracle(variant, workload):
+    if workload == "plain":
+        cfg = synthetic.config_plain()
+        scene, rx, tx, spec = cfg["scene"], cfg["rx"], cfg["tx"], cfg["grid"]
+    else:
+        scene = {k: v for k, v in synthetic.scene(6000, 778).items() if not k.startswith("_")}
+        rng = np.random.default_rng(12)
+        rx = (rng.uniform(0, 1, (2, 3)) * [10.0, 8.0, 3.0]).astype(np.float32)
+        tx = np.array([9.0, 1.0, 2.0], np.float32)
+        spec = dict(n_az=180, n_el=45)
+    S, R, _, _ = gpu_render(scene, rx, tx, 2.4e9, spec, variant=variant)
+    assert R.status().code == 0
+    g = oracle.make_grid(**spec, variant=variant)
+    for r in range(rx.shape[0]):
+        ref = oracle_pair(scene, rx[r], tx, 2.4e9, g)
+        compare(S[r], ref)
