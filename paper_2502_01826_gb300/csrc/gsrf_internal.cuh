@@ -213,13 +213,13 @@ namespace gsrf {
 //
 // Records (6 float4): v0 = (c = mu - r, D cos theta), v1 = (w = W (r - mu), er),
 // v2 = (ei, omd, -, -), s0 = W0..W3, s1 = W4..W7, s2 = (W8, o, b, -).
-// Tests, in order: the direction cone c.v >= D cos(theta) (theta: half-angle of the
-// cone of directions that meet the bounding sphere beyond the emitting sphere, set by
-// the projection with margins far above FP32 rounding, so it never rejects a pair the
-// next two tests accept); the 3-sigma ellipsoid in
-// whitened coordinates, m2 A = |w x v'|^2 < 9 A (v' = W v, Lagrange's identity, App.
-// D.3 quadratic with A = |v'|^2, B = w.v', C = |w|^2); the chord's exit
-// t_out = t_mid + h >= r_rx with t_mid = -B/A, h = sqrt((9 - m2)/A).
+// Per ray, in order: the 3-sigma ellipsoid in whitened coordinates,
+// m2 A = |w x v'|^2 < 9 A (v' = W v, Lagrange's identity, App. D.3 quadratic with
+// A = |v'|^2, B = w.v', C = |w|^2); the chord's exit t_out = t_mid + h >= r_rx with
+// t_mid = -B/A, h = sqrt((9 - m2)/A).  The direction cone (c, D cos theta: the
+// directions that meet the bounding sphere beyond the emitting sphere) is tested once
+// per warp (bundle_meets), never per ray: it only ever rejects pairs these two tests
+// reject too.
 // ---------------------------------------------------------------------------
 // Single hardware instructions (no compiler choice of sequence), so that the forward and
 // the backward take the same value.
@@ -274,13 +274,19 @@ __device__ __forceinline__ bool bundle_meets(const Bundle& b, float4 c) {
     return cd >= b.cb * c.w - b.sb * dsn - 1e-4f * (c.w + dsn);
 }
 
-// Four planes through the receiver that hold every ray of a warp's bw x bh block on
-// their inner side (n.d >= 0): the vertical planes at the block's first and last
-// azimuth, and planes tilted to its lowest and highest elevation; each is moved along
-// the warp axis b until it clears all of the warp's rays (a margin of 1e-6 in n.d).  A
-// ray point x = t d (t >= r_rx > 0) then has n.x >= 0, so an ellipsoid that lies wholly
-// on the outer side of one plane meets no ray of the warp.  Every lane computes the
-// same planes; lane j < 4 writes plane j to the warp's shared slots.
+// Five half-spaces n.x >= n.w that hold every point of the warp's bw x bh block of rays
+// beyond the emitting sphere (x = t d, t >= r_rx).  Four pass through the receiver
+// (n.w = 0): the vertical planes at the block's first and last azimuth, and planes
+// tilted to its lowest and highest elevation; each is moved along the warp axis b until
+// it clears all of the warp's rays (a margin of 1e-6 in n.d).  The fifth is the depth
+// plane b.x >= r_rx cb - 1e-4: b.d >= cb on every ray (cb holds a margin), so a ray
+// point at t >= r_rx lies beyond it; it drops candidates whose ellipsoid ends inside the
+// emitting sphere in the warp's directions, which are most of the near misses in a
+// dense scene.  An ellipsoid that lies wholly outside one half-space meets no ray of
+// the warp beyond r_rx.  Every lane computes the same planes; lane j < kPlanes writes
+// plane j to the warp's shared slots.
+constexpr int kPlanes = 5;
+
 __device__ __forceinline__ void warp_planes(const gsrf_grid& gr, int u_lo, int v_lo, int bw, int bh, const Bundle& b,
                                             bool valid, float dx, float dy, float dz, float4* spl) {
     const int u_hi = min(u_lo + bw - 1, gr.n_az - 1), v_hi = min(v_lo + bh - 1, gr.n_el - 1);
@@ -313,23 +319,27 @@ __device__ __forceinline__ void warp_planes(const gsrf_grid& gr, int u_lo, int v
         }
         if (lane == j) spl[j] = make_float4(n[j][0], n[j][1], n[j][2], 0.0f);
     }
+    if (lane == 4)
+        spl[4] = b.cb > 0.0f ? make_float4(b.bx, b.by, b.bz, gr.r_rx * b.cb - 1e-4f) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     __syncwarp();
 }
 
 // Can the 3-sigma ellipsoid about mu (c = mu - r; M from the shape record) reach the
-// inner side of all four planes?  Its support along n is n.c + 3 |M n|; a 1% margin
-// (3.03) covers rounding.  A zero plane never rejects.
+// inner side of all five half-spaces?  Its support along n is n.c + 3 |M n|, so it does
+// iff n.c - n.w + 3 |M n| >= 0; a 1% margin (3.03) covers rounding (at least 3e-4 m for
+// the smallest scales, far above the FP32 error of the per-ray exit point).  A zero
+// plane never rejects.
 __device__ __forceinline__ bool planes_meet(const float4* spl, const float4& c, const GShape* sh) {
     const float4* mm = reinterpret_cast<const float4*>(sh) + 3;
     const float4 m0 = __ldg(mm), m1 = __ldg(mm + 1), m2 = __ldg(mm + 2);
     bool meet = true;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < kPlanes; ++j) {
         const float4 n = spl[j];
         const float s0 = m0.x * n.x + m0.y * n.y + m0.z * n.z;
         const float s1 = m0.w * n.x + m1.x * n.y + m1.y * n.z;
         const float s2 = m1.z * n.x + m1.w * n.y + m2.x * n.z;
-        const float nc = n.x * c.x + n.y * c.y + n.z * c.z;
+        const float nc = n.x * c.x + n.y * c.y + n.z * c.z - n.w;
         meet = meet && (nc >= 0.0f || nc * nc <= 9.1809f * (s0 * s0 + s1 * s1 + s2 * s2));
     }
     return meet;
@@ -339,10 +349,6 @@ struct PairGeo {
     float vx, vy, vz;  // v' = W v
     float A, iA, m2, tm, h, t_out, t_a, dt, dl, m2r;
 };
-
-__device__ __forceinline__ bool pair_cone(const float4& v0, float dx, float dy, float dz) {
-    return __fmaf_rn(v0.z, dz, __fmaf_rn(v0.y, dy, __fmul_rn(v0.x, dx))) >= v0.w;
-}
 
 __device__ __forceinline__ bool pair_hits(const float4& v1, const float4& s0, const float4& s1, const float4& s2,
                                           float dx, float dy, float dz, float r_rx, PairGeo& g) {

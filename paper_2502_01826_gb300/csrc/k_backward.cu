@@ -202,9 +202,10 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
             m &= ~(1u << j);
             const int pos = (int)(b0 - lo) + j;
             const float4* rec = sbuf[bf][j];
-            const float4 v0 = rec[0], v1 = rec[1], s0 = rec[3], s1 = rec[4], s2 = rec[5];
+            const float4 v1 = rec[1], s0 = rec[3], s1 = rec[4], s2 = rec[5];
+            const float4 v0 = rec[0];  // c = mu - r, used by the hit path
             PairGeo pg;
-            bool hit = pos <= last && pair_cone(v0, dx, dy, dz) && pair_hits(v1, s0, s1, s2, dx, dy, dz, r_rx, pg);
+            bool hit = pos <= last && pair_hits(v1, s0, s1, s2, dx, dy, dz, r_rx, pg);
             if (!__any_sync(0xffffffffu, hit)) continue;
             float go[16];
             float g_pr = 0.0f, g_pi = 0.0f;  // dL/d psi (real, imaginary) of this pair on this ray
@@ -393,7 +394,7 @@ __global__ void __launch_bounds__(kBThreads, NFC == 1 ? 4 : (NFC == 8 ? 3 : 2)) 
                                                                             unsigned long long total) {
     __shared__ float4 sbuf[kBW][2][kBB][6];
     __shared__ uint32_t sid[kBW][2][kBB];
-    __shared__ float4 spl[kBW][4];
+    __shared__ float4 spl[kBW][kPlanes];
     __shared__ float sbp[kBW][16][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned per_rx = (unsigned)a.n_tiles * (unsigned)a.per_tile;

@@ -10,21 +10,22 @@
 //
 // Each warp walks its tile's candidate list on its own, WB (16 or 32, from the plan)
 // candidates per batch: lane i < WB takes candidate b0 + i, tests its direction cone
-// against the cone of the warp's rays and its ellipsoid against four planes that bound
-// those rays and, if it may be hit, copies its records into the warp's half of a double
-// buffer with cp.async while the warp works on the current batch; the rays then visit
-// only the candidates of the ballot mask, in list order.  A warp's item ends as soon as
-// its 32 rays have terminated (prod(1 - alpha) < eps_T).
+// against the cone of the warp's rays and its ellipsoid against five half-spaces that
+// hold those rays beyond the emitting sphere (warp_planes) and, if it may be hit,
+// copies its records into the warp's half of a double buffer with cp.async while the
+// warp works on the current batch; the rays then visit only the candidates of the
+// ballot mask, in list order.  A warp's item ends as soon as its 32 rays have
+// terminated (prod(1 - alpha) < eps_T).  After the warp-level tests, nine in ten rays
+// would pass a per-ray direction-cone test, so the forward goes straight to the exact
+// test.
 //
-// Per candidate and ray (pair_cone / pair_hits, shared with the backward):
-//   (1) direction cone: v lies in the cone of directions that meet the bounding sphere
-//       of the 3-sigma ellipsoid beyond the emitting sphere, c.v >= D cos(theta);
-//   (2) 3-sigma ellipsoid in whitened coordinates: with W = diag(1/s) R^T the ray
+// Per candidate and ray (pair_hits, shared with the backward):
+//   (1) 3-sigma ellipsoid in whitened coordinates: with W = diag(1/s) R^T the ray
 //       r + t v maps to w + t v' (w = W (r - mu), v' = W v), so the paper's quadratic
 //       A t^2 + 2 B t + (C - 9) = 0 (App. D.3) has A = |v'|^2, B = w.v', C = |w|^2;
 //       the closest approach is m2 = C - B^2/A = |w x v'|^2 / A (Lagrange's identity),
 //       free of the cancellation of C - B^2/A in FP32 (C reaches 1e5);
-//   (3) the chord t_mid +- sqrt((9 - m2)/A) must reach r_rx; it is clipped there and
+//   (2) the chord t_mid +- sqrt((9 - m2)/A) must reach r_rx; it is clipped there and
 //       the Gaussian is weighted at the midpoint of the clipped chord (App. A.2).
 #include <math.h>
 
@@ -172,7 +173,6 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
                 cp_async16(dst + 3, sh + 0);
                 cp_async16(dst + 4, sh + 1);
                 cp_async16(dst + 5, sh + 2);
-                asm volatile("prefetch.global.L1 [%0];\n" ::"l"(a.fle + (size_t)id * kFle));
             }
         }
         cp_async_commit();
@@ -201,7 +201,6 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
                 for (uint32_t m = mask; m; m &= m - 1) {
                     const int j = __ffs(m) - 1;
                     const float4* rec = sbuf[bf][j];
-                    if (!pair_cone(rec[0], dx, dy, dz)) continue;
                     const float4 v1 = rec[1], s2 = rec[5];
                     PairGeo pg;
                     if (!pair_hits(v1, rec[3], rec[4], s2, dx, dy, dz, r_rx, pg)) continue;
@@ -303,13 +302,13 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
 // left; a warp that finishes early takes the next item instead of idling until the
 // other warps of its CTA are done.
 template <int NFC, int WB>
-__global__ void __launch_bounds__(kThreads, NFC == 1 ? 6 : 4) k_render_queue(RenderArgs a,
+__global__ void __launch_bounds__(kThreads, NFC == 1 ? 7 : 4) k_render_queue(RenderArgs a,
                                                                             const uint32_t* __restrict__ order,
                                                                             unsigned long long* __restrict__ counter,
                                                                             unsigned long long total) {
     __shared__ float4 sbuf[kWarps][2][WB][kRec];
     __shared__ uint32_t sid[kWarps][2][WB];
-    __shared__ float4 spl[kWarps][4];
+    __shared__ float4 spl[kWarps][kPlanes];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned per_rx = (unsigned)a.n_tiles * (unsigned)a.per_tile;
     for (;;) {
@@ -331,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_render_batch(BatchArgs b, const
                                                               unsigned long long* __restrict__ counter) {
     __shared__ float4 sbuf[kWarps][2][WB][kRec];
     __shared__ uint32_t sid[kWarps][2][WB];
-    __shared__ float4 spl[kWarps][4];
+    __shared__ float4 spl[kWarps][kPlanes];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned long long total = b.item_base[b.n_jobs];
     for (;;) {
