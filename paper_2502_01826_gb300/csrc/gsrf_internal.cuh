@@ -286,6 +286,7 @@ __device__ __forceinline__ bool bundle_meets(const Bundle& b, float4 c) {
 // the warp beyond r_rx.  Every lane computes the same planes; lane j < kPlanes writes
 // plane j to the warp's shared slots.
 constexpr int kPlanes = 5;
+constexpr int kPlaneSlots = kPlanes + 1;  // + the warp bundle's cos / sin (bundle_at)
 
 __device__ __forceinline__ void warp_planes(const gsrf_grid& gr, int u_lo, int v_lo, int bw, int bh, const Bundle& b,
                                             bool valid, float dx, float dy, float dz, float4* spl) {
@@ -321,7 +322,22 @@ __device__ __forceinline__ void warp_planes(const gsrf_grid& gr, int u_lo, int v
     }
     if (lane == 4)
         spl[4] = b.cb > 0.0f ? make_float4(b.bx, b.by, b.bz, gr.r_rx * b.cb - 1e-4f) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (lane == 5) spl[5] = make_float4(b.cb, b.sb, 0.0f, 0.0f);
     __syncwarp();
+}
+
+// The warp bundle back from the slots warp_planes wrote (so that a kernel need not hold
+// it in registers across its loop).  The axis is only stored when cb > 0; otherwise the
+// bundle spans a hemisphere and bundle_meets accepts every candidate without it.
+__device__ __forceinline__ Bundle bundle_at(const float4* spl) {
+    const float4 ax = spl[4], cs = spl[5];
+    Bundle b;
+    b.bx = ax.x;
+    b.by = ax.y;
+    b.bz = ax.z;
+    b.cb = cs.x;
+    b.sb = cs.y;
+    return b;
 }
 
 // Can the 3-sigma ellipsoid about mu (c = mu - r; M from the shape record) reach the

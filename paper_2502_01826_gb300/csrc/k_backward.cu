@@ -152,8 +152,7 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
     // positions are inside the tile's list; a state that points past it (another plan's,
     // or garbage) is clamped so that no read leaves the list
     const size_t ts = (size_t)r * (a.n_tiles + 1) + tile;
-    const long long base0 = a.rx_base[r];
-    const long long lo = base0 + a.tile_start[ts];
+    const uint32_t* __restrict__ ids = a.pids + a.rx_base[r] + a.tile_start[ts];  // the tile's list
     const int len = (int)(a.tile_start[ts + 1] - a.tile_start[ts]);
     last = min(last, len - 1);
     int wlast = last;
@@ -165,13 +164,13 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
     const float rx = a.rxpos[3 * r], ry = a.rxpos[3 * r + 1], rz = a.rxpos[3 * r + 2];
     const float omega = 3.14159265f * a.om_pi;  // 2 pi f0 / c
 
-    auto stage = [&](int bf, long long b0, long long bend) -> uint32_t {
+    auto stage = [&](int bf, int p0, int pend) -> uint32_t {
         bool keep = false;
-        if (b0 + lane < bend) {
-            const uint32_t id = a.pids[b0 + lane];
+        if (p0 + lane < pend) {
+            const uint32_t id = ids[p0 + lane];
             const float4* vw = reinterpret_cast<const float4*>(view + id);
             const float4 c = __ldg(vw);
-            keep = bundle_meets(bun, c) && planes_meet(spl, c, a.shape + id);
+            keep = bundle_meets(bundle_at(spl), c) && planes_meet(spl, c, a.shape + id);
             if (keep) {
                 sid[bf][lane] = id;
                 const float4* sh = reinterpret_cast<const float4*>(a.shape + id);
@@ -189,18 +188,18 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
     };
 
     // batches that hold list positions 0 .. wlast, from the last one down
-    const long long end = lo + wlast + 1;
-    long long b0 = lo + ((long long)wlast / kBB) * kBB;
+    const int end = wlast + 1;
+    int b0 = (wlast / kBB) * kBB;
     int bf = 0;
     uint32_t mask = stage(0, b0, end);
-    for (; b0 >= lo; b0 -= kBB, bf ^= 1) {
-        const uint32_t next = b0 - kBB >= lo ? stage(bf ^ 1, b0 - kBB, end) : (stage(bf ^ 1, end, end), 0u);
+    for (; b0 >= 0; b0 -= kBB, bf ^= 1) {
+        const uint32_t next = b0 - kBB >= 0 ? stage(bf ^ 1, b0 - kBB, end) : (stage(bf ^ 1, end, end), 0u);
         asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         __syncwarp();
         for (uint32_t m = mask; m;) {
             const int j = 31 - __clz(m);
             m &= ~(1u << j);
-            const int pos = (int)(b0 - lo) + j;
+            const int pos = b0 + j;
             const float4* rec = sbuf[bf][j];
             const float4 v1 = rec[1], s0 = rec[3], s1 = rec[4], s2 = rec[5];
             const float4 v0 = rec[0];  // c = mu - r, used by the hit path
@@ -365,9 +364,9 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
         }
         mask = next;
         if (a.ck) {
-            // in front of list position b0 - lo: take the forward's own transmittance
-            // where it kept one, so that division by (1 - alpha) runs over at most K positions
-            const long long p = b0 - lo;
+            // in front of list position b0: take the forward's own transmittance where it
+            // kept one, so that division by (1 - alpha) runs over at most K positions
+            const int p = b0;
             if (p > 0 && p % a.ck_every == 0 && p / a.ck_every <= a.ck_slots && valid) {
                 const size_t rays = (size_t)a.n_rx * gr.n_el * gr.n_az;
                 const size_t ray = ((size_t)r * gr.n_el + v) * gr.n_az + u;
@@ -383,18 +382,19 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
 }
 
 // Persistent launch: every warp takes work items (receiver, tile, ray block, subcarrier
-// chunk) from one counter, heaviest first, until none is left.  One frequency: 4 CTAs
-// per SM (at most 128 registers); chunks of 8 subcarriers: 3 (at most 168); of 16: 2.
+// chunk) from one counter, heaviest first, until none is left.  One frequency: 5 CTAs
+// per SM (at most 102 registers, no spills); chunks of 8 subcarriers: 3 (at most 168;
+// 4 would spill); of 16: 2.
 // More than 8 subcarriers go in chunks of 16: half the walks of chunks of 8 for 64
 // subcarriers, which outweighs the lower occupancy.
 template <int NFC>
-__global__ void __launch_bounds__(kBThreads, NFC == 1 ? 4 : (NFC == 8 ? 3 : 2)) k_render_bwd(BwdArgs a,
+__global__ void __launch_bounds__(kBThreads, NFC == 1 ? 5 : (NFC == 8 ? 3 : 2)) k_render_bwd(BwdArgs a,
                                                                             const uint32_t* __restrict__ order,
                                                                             unsigned long long* __restrict__ counter,
                                                                             unsigned long long total) {
     __shared__ float4 sbuf[kBW][2][kBB][6];
     __shared__ uint32_t sid[kBW][2][kBB];
-    __shared__ float4 spl[kBW][kPlanes];
+    __shared__ float4 spl[kBW][kPlaneSlots];
     __shared__ float sbp[kBW][16][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned per_rx = (unsigned)a.n_tiles * (unsigned)a.per_tile;

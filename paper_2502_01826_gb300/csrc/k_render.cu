@@ -9,7 +9,7 @@
 // warp that finishes early takes the next item.
 //
 // Each warp walks its tile's candidate list on its own, WB (16 or 32, from the plan)
-// candidates per batch: lane i < WB takes candidate b0 + i, tests its direction cone
+// candidates per batch: lane i < WB takes candidate p0 + i, tests its direction cone
 // against the cone of the warp's rays and its ellipsoid against five half-spaces that
 // hold those rays beyond the emitting sphere (warp_planes) and, if it may be hit,
 // copies its records into the warp's half of a double buffer with cp.async while the
@@ -137,9 +137,11 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
     const Bundle bun = warp_bundle(valid, dx, dy, dz);
     warp_planes(gr, u_lo, v_lo, bw, bh, bun, valid, dx, dy, dz, spl);
 
+    // the tile's list: ids[0 .. len) (a list holds each Gaussian at most once, so its
+    // positions fit in 32 bits: n_gauss < 2^31)
     const size_t ts = (size_t)r * (a.n_tiles + 1) + tile;
-    const long long base0 = a.rx_base[r];
-    const long long lo = base0 + a.tile_start[ts], hi = base0 + a.tile_start[ts + 1];
+    const uint32_t* __restrict__ ids = a.pids + a.rx_base[r] + a.tile_start[ts];
+    const int len = (int)(a.tile_start[ts + 1] - a.tile_start[ts]);
     const float r_rx = gr.r_rx, eps_T = gr.eps_T, amax = gr.alpha_max;
     const View* __restrict__ view = a.view + (size_t)r * a.n;
 
@@ -151,18 +153,18 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
     const int s0 = chunk * NFC;
     int last = -1;
     bool done = !valid;
-    unsigned tests = 0, hits = 0;
+    unsigned hits = 0;
 
-    // Stage the batch starting at b0 into buffer bf: lane i < WB takes candidate b0 + i,
-    // tests it against the warp's cone and planes and, if it may be hit, copies its
-    // records; returns the mask of candidates that may be hit.
-    auto stage = [&](int bf, long long b0) -> uint32_t {
+    // Stage the batch starting at list position p0 into buffer bf: lane i < WB takes
+    // candidate p0 + i, tests it against the warp's cone and half-spaces and, if it may
+    // be hit, copies its records; returns the mask of candidates that may be hit.
+    auto stage = [&](int bf, int p0) -> uint32_t {
         bool keep = false;
-        if (lane < WB && b0 + lane < hi) {
-            const uint32_t id = a.pids[b0 + lane];
+        if (lane < WB && p0 + lane < len) {
+            const uint32_t id = ids[p0 + lane];
             const float4* vw = reinterpret_cast<const float4*>(view + id);
             const float4 c = __ldg(vw);
-            keep = bundle_meets(bun, c) && planes_meet(spl, c, a.shape + id);
+            keep = bundle_meets(bundle_at(spl), c) && planes_meet(spl, c, a.shape + id);
             if (keep) {
                 sid[bf][lane] = id;
                 const float4* sh = reinterpret_cast<const float4*>(a.shape + id);
@@ -181,23 +183,21 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
 
     if (!__all_sync(0xffffffffu, done)) {
         int bf = 0;
-        uint32_t mask = stage(0, lo);
-        for (long long b0 = lo; b0 < hi; b0 += WB, bf ^= 1) {
+        uint32_t mask = stage(0, 0);
+        for (int p0 = 0; p0 < len; p0 += WB, bf ^= 1) {
             if (a.ck && chunk == 0) {
                 // transmittance in front of list position K, 2K, ... (a batch start)
-                const long long p = b0 - lo;
+                const int p = p0;
                 if (p > 0 && p % a.ck_every == 0 && p / a.ck_every <= a.ck_slots && valid) {
                     const size_t rays = (size_t)a.n_rx * gr.n_el * gr.n_az;
                     const size_t ray = ((size_t)r * gr.n_el + v) * gr.n_az + u;
                     a.ck[(size_t)(p / a.ck_every - 1) * rays + ray] = make_float4(Tr, Ti, Gam, Ta);
                 }
             }
-            const uint32_t next = stage(bf ^ 1, b0 + WB);  // empty past the end of the list
+            const uint32_t next = stage(bf ^ 1, p0 + WB);  // empty past the end of the list
             cp_async_wait_prev();
             __syncwarp();
-            const int cnt = (int)min((long long)WB, hi - b0);
             if (!done) {
-                int stop = cnt;
                 for (uint32_t m = mask; m; m &= m - 1) {
                     const int j = __ffs(m) - 1;
                     const float4* rec = sbuf[bf][j];
@@ -246,14 +246,12 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
                     Tr = nTr;
                     Ta *= om;
                     ++hits;
-                    last = (int)(b0 - lo) + j;  // position inside the tile's list
+                    last = p0 + j;  // position inside the tile's list
                     if (Ta < eps_T) {
                         done = true;
-                        stop = j + 1;
                         break;
                     }
                 }
-                tests += (unsigned)stop;
             }
             mask = next;
             __syncwarp();
@@ -274,18 +272,16 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
                 if (s0 + q < a.n_f) o2[(size_t)q * plane] = make_float2(Sf[2 * q], Sf[2 * q + 1]);
         }
         if (a.rs && chunk == 0) {
-            RayState s;
-            s.last = last;
-            s.Ta = Ta;
-            s.Tr = Tr;
-            s.Ti = Ti;
-            s.Gam = Gam;
-            s.pad[0] = s.pad[1] = s.pad[2] = 0.0f;
-            a.rs[ray] = s;
+            // RayState {last, Ta, Tr, Ti | Gam, pad[3]} as two 16-byte stores
+            float4* rs4 = reinterpret_cast<float4*>(a.rs + ray);
+            rs4[0] = make_float4(__int_as_float(last), Ta, Tr, Ti);
+            rs4[1] = make_float4(Gam, 0.0f, 0.0f, 0.0f);
         }
     }
     // statistics: list positions tested and composited pairs, one atomic per warp
-    unsigned long long t64 = tests, h64 = hits;
+    // list positions this ray tested: up to its terminating pair, else the whole list
+    unsigned long long t64 = !valid ? 0ull : (done ? (unsigned long long)(last + 1) : (unsigned long long)len),
+                       h64 = hits;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         t64 += __shfl_down_sync(0xffffffffu, t64, o);
@@ -308,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, NFC == 1 ? 7 : 4) k_render_queue(Ren
                                                                             unsigned long long total) {
     __shared__ float4 sbuf[kWarps][2][WB][kRec];
     __shared__ uint32_t sid[kWarps][2][WB];
-    __shared__ float4 spl[kWarps][kPlanes];
+    __shared__ float4 spl[kWarps][kPlaneSlots];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned per_rx = (unsigned)a.n_tiles * (unsigned)a.per_tile;
     for (;;) {
@@ -326,11 +322,11 @@ __global__ void __launch_bounds__(kThreads, NFC == 1 ? 7 : 4) k_render_queue(Ren
 // Persistent batched launch over several problems (n_f = 1 each): work items (job,
 // receiver, tile, ray block), same queue discipline.
 template <int WB>
-__global__ void __launch_bounds__(kThreads, 6) k_render_batch(BatchArgs b, const uint32_t* __restrict__ order,
+__global__ void __launch_bounds__(kThreads, 7) k_render_batch(BatchArgs b, const uint32_t* __restrict__ order,
                                                               unsigned long long* __restrict__ counter) {
     __shared__ float4 sbuf[kWarps][2][WB][kRec];
     __shared__ uint32_t sid[kWarps][2][WB];
-    __shared__ float4 spl[kWarps][kPlanes];
+    __shared__ float4 spl[kWarps][kPlaneSlots];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned long long total = b.item_base[b.n_jobs];
     for (;;) {
