@@ -35,7 +35,9 @@ namespace gsrf {
 
 constexpr int kWarps = 4;        // warps per CTA, each on its own work items
 constexpr int kThreads = 32 * kWarps;
-constexpr int kRec = 6;          // float4 per staged candidate: 3 of View, 3 of GShape
+// float4 per staged candidate: View floats 4..11 (w, er | ei, omd, psi at the mean) and
+// the first 48 bytes of GShape (W, o, b); the forward needs no c or D cos(theta) per ray
+constexpr int kRec = 5;
 
 struct RenderArgs {
     const GShape* shape;
@@ -169,12 +171,11 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
                 sid[bf][lane] = id;
                 const float4* sh = reinterpret_cast<const float4*>(a.shape + id);
                 float4* dst = sbuf[bf][lane];
-                dst[0] = c;
-                cp_async16(dst + 1, vw + 1);
-                cp_async16(dst + 2, vw + 2);
-                cp_async16(dst + 3, sh + 0);
-                cp_async16(dst + 4, sh + 1);
-                cp_async16(dst + 5, sh + 2);
+                cp_async16(dst + 0, vw + 1);
+                cp_async16(dst + 1, vw + 2);
+                cp_async16(dst + 2, sh + 0);
+                cp_async16(dst + 3, sh + 1);
+                cp_async16(dst + 4, sh + 2);
             }
         }
         cp_async_commit();
@@ -201,27 +202,27 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
                 for (uint32_t m = mask; m; m &= m - 1) {
                     const int j = __ffs(m) - 1;
                     const float4* rec = sbuf[bf][j];
-                    const float4 v1 = rec[1], s2 = rec[5];
+                    const float4 v1 = rec[0], s2 = rec[4];
                     PairGeo pg;
-                    if (!pair_hits(v1, rec[3], rec[4], s2, dx, dy, dz, r_rx, pg)) continue;
+                    if (!pair_hits(v1, rec[2], rec[3], s2, dx, dy, dz, r_rx, pg)) continue;
                     float gw;
                     const float alpha = pair_alpha(s2.y, pg.m2r, amax, gw);
                     float pr, pi;
                     if (a.variant & GSRF_VARIANT_RADIANCE_AT_MEAN) {  // one radiance per Gaussian
-                        pr = rec[2].z;
-                        pi = rec[2].w;
+                        pr = rec[1].z;
+                        pi = rec[1].w;
                     } else {
                         fle_psi(reinterpret_cast<const float4*>(a.fle + (size_t)sid[bf][j] * kFle), P, Y, pr, pi);
                     }
                     // S += alpha psi E T, E = e^{-j phi} = (er, ei)
-                    const float er = v1.w, ei = rec[2].x;
+                    const float er = v1.w, ei = rec[1].x;
                     const float etr = er * Tr - ei * Ti, eti = er * Ti + ei * Tr;
                     if constexpr (NFC == 1) {
                         Sr += alpha * (pr * etr - pi * eti);
                         Si += alpha * (pr * eti + pi * etr);
                     } else {
                         // z at the chunk's first subcarrier, then one rotation per step
-                        const float ws = rec[2].y + a.dlt * Gam;
+                        const float ws = rec[1].y + a.dlt * Gam;
                         float rs, rc, ss, sc;
                         sincosf(ws, &rs, &rc);
                         sincosf((float)s0 * ws, &ss, &sc);
