@@ -88,6 +88,8 @@ def lib():
         L.or_depth_key_f32.argtypes = [vp, vp]
         L.or_cover_f32.restype = i32
         L.or_cover_f32.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.or_circle_f32.restype = None
+        L.or_circle_f32.argtypes = [vp, vp, vp, vp, vp, vp]
         L.or_bin.restype = i64
         L.or_bin.argtypes = [vp, vp, vp, vp, vp, i64, vp]
         L.or_path_phase.restype = None
@@ -112,8 +114,8 @@ def _f32(a):
 
 def make_grid(n_az, n_el, az0_deg=0.0, daz_deg=None, el0_deg=0.0, del_deg=None, r_rx=1.0,
               eps_T=1e-4, alpha_max=0.99, tile_w=16, tile_h=16, variant=0) -> Grid:
-    """variant: bit 1 = radiance at the Gaussian's direction, bit 2 = normalised weight
-    (see or_grid in gsrf_oracle.h)."""
+    """variant: bit 1 = radiance at the Gaussian's direction, bit 2 = normalised weight,
+    bit 4 = the paper's splatting-circle culling (see or_grid in gsrf_oracle.h)."""
     if daz_deg is None:
         daz_deg = 360.0 / n_az
     if del_deg is None:
@@ -189,6 +191,13 @@ def cover_f32(mu, log_scale, r, grid: Grid):
     n = lib().or_cover_f32(_p(_f32(mu)), _p(_f32(log_scale)), _p(_f32(r)), C.byref(grid),
                            _p(mask), _p(lo), _p(hi))
     return int(n), int(mask[0]), int(lo[0]), int(hi[0])
+
+
+def circle_f32(mu, log_scale, quat, r, grid: Grid):
+    """The paper's splatting circle (u_k, v_k, r_k^2) in bins, decided in FP32."""
+    out = np.zeros(3, np.float32)
+    lib().or_circle_f32(_p(_f32(mu)), _p(_f32(log_scale)), _p(_f32(quat)), _p(_f32(r)), C.byref(grid), _p(out))
+    return float(out[0]), float(out[1]), float(out[2])
 
 
 def n_tiles(grid: Grid):

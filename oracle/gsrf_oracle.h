@@ -59,7 +59,10 @@ typedef struct {
                                   *      the direction of mu_k seen from the receiver (Sec. 4.3's
                                   *      v_k) for every ray, instead of at each ray's direction;
                                   *   2  the weight is the normalised Gaussian density at the
-                                  *      representative point (App. A.3), g / ((2 pi)^1.5 |Sigma|^0.5) */
+                                  *      representative point (App. A.3), g / ((2 pi)^1.5 |Sigma|^0.5)
+                                  *   4  a ray (u, v) meets Gaussian k only inside its splatting
+                                  *      circle on the receiving plane (Sec. 4.3, the paper's own
+                                  *      culling: or_circle_f32), on top of the exact test */
 } or_grid;
 
 typedef struct {
@@ -127,6 +130,17 @@ uint32_t or_depth_key_f32(const float *mu, const float *r);
  * Returns the number of tiles covered. */
 int32_t or_cover_f32(const float *mu, const float *log_scale, const float *r, const or_grid *g,
                      uint64_t *mask, int32_t *tv_lo, int32_t *tv_hi);
+
+/* The paper's splatting circle of Gaussian (mu, log_scale, quat) seen from r (Sec. 4.3,
+ * "Splatting Process"): out = (u_k, v_k, r_k^2) with (u_k, v_k) the grid bin holding
+ * the direction of mu - r and r_k = 3 sqrt(lambda_max(J Sigma J^T)), J the Jacobian of
+ * the (u, v) bin coordinates with respect to mu, in bins; r_k^2 = +inf where J is
+ * undefined (mu - r vertical).  Ray (u, v) is inside when (u - u_k)^2 + (v - v_k)^2
+ * <= r_k^2, both sums in FP32 as here.  The decision is taken in FP32 with the kernels'
+ * sequence of correctly rounded operations. */
+void or_circle_f32(const float *mu, const float *log_scale, const float *quat, const float *r,
+                   const or_grid *g, float *out);
+int or_circle_in(const float *circle, int32_t u, int32_t v);
 
 /* Splatting + sort for one receiver: all (tile, Gaussian) instances ordered by
  * the 64-bit key (tile << 32 | depth bits), ties by Gaussian index.

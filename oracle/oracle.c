@@ -244,6 +244,7 @@ typedef struct {
     /* per Gaussian, FP64 */
     double *Sinv, *mu, *op, *dpath, *b;
     double *psig;           /* variant 1: psi_k at the direction of mu_k, [n][2] */
+    float *circ;            /* variant 4: splatting circle (u_k, v_k, r_k^2), [n][3] */
     /* candidate lists */
     const int64_t *tile_start;
     const uint32_t *ids;    /* mode 0 */
@@ -326,6 +327,7 @@ static void render_one(rctx *c, int64_t i)
     const uint32_t *list;
     int64_t len;
     ray_list(c, ray, &list, &len);
+    const int32_t ray_u = ray % g->n_az, ray_v = ray / g->n_az;
 
     double S[2 * 256], T[2 * 256];
     for (int f = 0; f < nf; ++f) { S[2 * f] = S[2 * f + 1] = 0.0; T[2 * f] = 1.0; T[2 * f + 1] = 0.0; }
@@ -337,6 +339,7 @@ static void render_one(rctx *c, int64_t i)
         uint32_t k = list[j];
         double h[10];
         ++nt;
+        if ((g->variant & 4) && !or_circle_in(c->circ + 3 * k, ray_u, ray_v)) continue;
         int hit = or_intersect(c->Sinv + 9 * k, c->mu + 3 * k, c->rx, v, g->r_rx, h);
         const double delta = bd ? bd->m2_err * sqrt(h[9]) + bd->m2_abs : 0.0;
         int flipped = 0;
@@ -442,6 +445,7 @@ static int prepare(rctx *c, const or_scene *s, const float *rx, const float *tx,
     c->dpath = (double *)malloc(sizeof(double) * nn);
     c->b = (double *)malloc(sizeof(double) * nn);
     c->psig = (double *)malloc(sizeof(double) * 2 * nn);
+    c->circ = (float *)malloc(sizeof(float) * 3 * nn);
     for (int i = 0; i < 3; ++i) c->rx[i] = rx[i];
     for (int64_t k = 0; k < n; ++k) {
         or_gaussian(s, k, NULL, c->Sinv + 9 * k, c->op + k);
@@ -454,6 +458,8 @@ static int prepare(rctx *c, const or_scene *s, const float *rx, const float *tx,
         }
         c->dpath[k] = sqrt(dt) + sqrt(dr); /* Tx -> mu_k -> Rx */
         c->b[k] = s->phase_b ? (double)s->phase_b[k] : 0.0;
+        if (g->variant & 4)
+            or_circle_f32(s->means + 3 * k, s->log_scales + 3 * k, s->quats + 4 * k, rx, g, c->circ + 3 * k);
         if (g->variant & 2) { /* normalised density: 1 / ((2 pi)^1.5 |Sigma|^0.5), |Sigma|^0.5 = s0 s1 s2 */
             double ls = (double)s->log_scales[3 * k] + s->log_scales[3 * k + 1] + s->log_scales[3 * k + 2];
             c->op[k] *= exp(-ls) / pow(2.0 * M_PI, 1.5);
@@ -502,7 +508,7 @@ static int prepare(rctx *c, const or_scene *s, const float *rx, const float *tx,
 
 static void release(rctx *c)
 {
-    free(c->Sinv); free(c->mu); free(c->op); free(c->dpath); free(c->b); free(c->psig);
+    free(c->Sinv); free(c->mu); free(c->op); free(c->dpath); free(c->b); free(c->psig); free(c->circ);
     free((void *)c->tile_start); free((void *)c->ids); free((void *)c->order);
 }
 
@@ -512,7 +518,7 @@ static int check_args(const or_scene *s, const or_grid *g, int32_t n_f, int32_t 
     if (g->n_az < 1 || g->n_el < 1 || g->tile_w < 1 || g->tile_h < 1) return -1;
     if ((g->n_az + g->tile_w - 1) / g->tile_w > 64) return -1;
     if (!(g->daz_deg > 0.0f) || !(g->del_deg > 0.0f)) return -1;
-    if (g->variant < 0 || g->variant > 3) return -1;
+    if (g->variant < 0 || g->variant > 7) return -1;
     return 0;
 }
 

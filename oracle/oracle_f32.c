@@ -1,5 +1,5 @@
 /*
- * oracle_f32.c -- the two integer decisions of the splatting step, taken in FP32.
+ * oracle_f32.c -- the integer decisions of the splatting step, taken in FP32.
  *
  * TEST INFRASTRUCTURE ONLY (see gsrf_oracle.h).
  *
@@ -195,4 +195,86 @@ int32_t or_cover_f32(const float *mu, const float *log_scale, const float *r, co
     *tv_lo_out = tv_lo;
     *tv_hi_out = tv_hi;
     return (int32_t)__builtin_popcountll(mask) * (tv_hi - tv_lo + 1);
+}
+
+/* The paper's splatting circle (Sec. 4.3, "Splatting Process"), the culling of plan
+ * variant 4.  The projected centre is the bin of the receiving plane that holds the
+ * direction of c = mu - r: the spherical coordinates of Sec. 4.3 (azimuth atan2(cy, cx),
+ * elevation asin(cz / D)) discretised by floor with the grid's own origin and step (the
+ * paper's one-degree grid has az0 = 0, el0 = -90).  The spread is the largest
+ * eigenvalue of Sigma2D = J Sigma J^T, J = d(u, v)/d mu at mu in bins per metre:
+ *   du/dmu = (180 / pi / daz) (-cy, cx, 0) / rho^2
+ *   dv/dmu = (180 / pi / del) (-cx cz, -cy cz, rho^2) / (rho D^2)
+ * (rho = |(cx, cy)|), with Sigma = R diag(s)^2 R^T; J Sigma J^T has entries
+ * (diag(s) R^T J_a) . (diag(s) R^T J_b).  r_k^2 = 9 lambda_max.  On the vertical
+ * (rho = 0) J does not exist and every ray passes (r_k^2 = +inf), as it does when the
+ * arithmetic overflows. */
+void or_circle_f32(const float *mu, const float *log_scale, const float *quat, const float *r,
+                   const or_grid *g, float *out)
+{
+    float cx = mu[0] - r[0], cy = mu[1] - r[1], cz = mu[2] - r[2];
+    float rho2 = cx * cx;
+    rho2 = rho2 + cy * cy;
+    float d2 = rho2 + cz * cz;
+    float D = sqrtf(d2);
+    float az = det_atan2(cy, cx) * RAD2DEG_F;
+    float rel = az - g->az0_deg;
+    if (rel < 0.0f) rel = rel + 360.0f;
+    if (rel < 0.0f) rel = rel + 360.0f;
+    if (rel >= 360.0f) rel = rel - 360.0f;
+    out[0] = floorf(rel / g->daz_deg);
+    float el = D > 0.0f ? det_asin(cz / D) * RAD2DEG_F : 0.0f;
+    out[1] = floorf((el - g->el0_deg) / g->del_deg);
+    out[2] = INFINITY;
+    if (!(rho2 > 0.0f)) return;
+    float rho = sqrtf(rho2);
+    float ku = RAD2DEG_F / (g->daz_deg * rho2);
+    float kv = RAD2DEG_F / (g->del_deg * (rho * d2));
+    float ju[3] = {-cy * ku, cx * ku, 0.0f};
+    float jv[3] = {(-cx * cz) * kv, (-cy * cz) * kv, rho2 * kv};
+    /* rotation of the normalised quaternion (w, x, y, z), scales exp(log s) */
+    float qw = quat[0], qx = quat[1], qy = quat[2], qz = quat[3];
+    float n2 = qw * qw;
+    n2 = n2 + qx * qx;
+    n2 = n2 + qy * qy;
+    n2 = n2 + qz * qz;
+    if (n2 > 0.0f) {
+        float qn = sqrtf(n2);
+        qw = qw / qn; qx = qx / qn; qy = qy / qn; qz = qz / qn;
+    } else {
+        qw = 1.0f; qx = 0.0f; qy = 0.0f; qz = 0.0f;
+    }
+    float R[9];
+    R[0] = 1.0f - 2.0f * (qy * qy + qz * qz);
+    R[1] = 2.0f * (qx * qy - qw * qz);
+    R[2] = 2.0f * (qx * qz + qw * qy);
+    R[3] = 2.0f * (qx * qy + qw * qz);
+    R[4] = 1.0f - 2.0f * (qx * qx + qz * qz);
+    R[5] = 2.0f * (qy * qz - qw * qx);
+    R[6] = 2.0f * (qx * qz - qw * qy);
+    R[7] = 2.0f * (qy * qz + qw * qx);
+    R[8] = 1.0f - 2.0f * (qx * qx + qy * qy);
+    float A = 0.0f, B = 0.0f, C = 0.0f;
+    for (int i = 0; i < 3; ++i) {
+        float si = det_exp(log_scale[i]);
+        float tu = R[i] * ju[0] + R[3 + i] * ju[1];
+        tu = tu + R[6 + i] * ju[2];
+        float tv = R[i] * jv[0] + R[3 + i] * jv[1];
+        tv = tv + R[6 + i] * jv[2];
+        float au = si * tu, av = si * tv;
+        A = A + au * au;
+        B = B + au * av;
+        C = C + av * av;
+    }
+    float h = (A - C) * 0.5f;
+    float lam = (A + C) * 0.5f + sqrtf(h * h + B * B);
+    float r2 = 9.0f * lam;
+    out[2] = r2 < INFINITY ? r2 : INFINITY; /* NaN from overflow: every ray */
+}
+
+int or_circle_in(const float *circle, int32_t u, int32_t v)
+{
+    float du = (float)u - circle[0], dv = (float)v - circle[1];
+    float d2 = du * du + dv * dv;
+    return d2 <= circle[2];
 }

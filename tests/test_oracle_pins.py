@@ -798,3 +798,102 @@ def test_variant_gradient_refused(oracle_lib):
     oracle_lib.render_grad(s, r, r, 2.4e9, small_grid(oracle_lib), G)  # the default reading runs
     with pytest.raises(ValueError, match="rejected"):
         oracle_lib.render_grad(s, r, r, 2.4e9, small_grid(oracle_lib, variant=1), G)
+
+
+# --------------------------------------------------------------------------- the paper's splatting circle
+
+def _bin_coords(c, grid):
+    """Continuous (u, v) bin coordinates of the direction c (Sec. 4.3 spherical coordinates,
+    discretised with the grid's origin and step), FP64."""
+    az = (math.degrees(math.atan2(c[1], c[0])) - grid.az0_deg) % 360.0
+    el = math.degrees(math.asin(c[2] / np.linalg.norm(c)))
+    return np.array([az / grid.daz_deg, (el - grid.el0_deg) / grid.del_deg])
+
+
+def _rot(q):
+    w, x, y, z = np.asarray(q, np.float64) / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def test_circle_isotropic_closed_form(oracle_lib):
+    """Isotropic Gaussian, Sigma = s^2 I: J J^T is diagonal with |J_u| = 180/(pi daz rho)
+    and |J_v| = 180/(pi del D), so r^2 = 9 s^2 max of the two squared; the centre is the
+    bin of mu's direction."""
+    g = oracle_lib.make_grid(360, 90)
+    rng = np.random.default_rng(21)
+    r = np.array([3.0, 4.0, 1.0], np.float32)
+    for _ in range(20):
+        mu = (r + rng.uniform(-4, 4, 3) * [1, 1, 0.4] + [0, 0, 0.6]).astype(np.float32)
+        ls = np.float32(rng.normal(math.log(0.15), 0.4))
+        uk, vk, r2 = oracle_lib.circle_f32(mu, [ls] * 3, [1, 0, 0, 0], r, g)
+        c = mu.astype(np.float64) - r
+        rho, D = math.hypot(c[0], c[1]), np.linalg.norm(c)
+        s = math.exp(float(ls))
+        ref = 9 * s * s * max((180 / math.pi / g.daz_deg / rho) ** 2, (180 / math.pi / g.del_deg / D) ** 2)
+        assert abs(r2 - ref) <= 2e-5 * ref
+        uv = _bin_coords(c, g)
+        if np.all(np.abs(uv - np.round(uv)) > 1e-3):
+            assert (uk, vk) == (math.floor(uv[0]), math.floor(uv[1]))
+
+
+def test_circle_matches_finite_difference_jacobian(oracle_lib):
+    """Rotated anisotropic Gaussians: r^2 = 9 lambda_max(J Sigma J^T) with J from central
+    differences of the bin coordinates and lambda_max from numpy's eigvalsh, in FP64."""
+    g = oracle_lib.make_grid(180, 45)
+    rng = np.random.default_rng(22)
+    r = np.array([5.0, 4.0, 1.5], np.float32)
+    for _ in range(20):
+        mu = (r + rng.uniform(-4, 4, 3) * [1, 1, 0.3] + [0, 0, 0.4]).astype(np.float32)
+        ls = rng.normal(math.log(0.15), 0.5, 3).astype(np.float32)
+        q = rng.normal(0, 1, 4).astype(np.float32)
+        _, _, r2 = oracle_lib.circle_f32(mu, ls, q, r, g)
+        c = mu.astype(np.float64) - r
+        J = np.zeros((2, 3))
+        for i in range(3):
+            e = np.zeros(3)
+            e[i] = 1e-5
+            J[:, i] = (_bin_coords(c + e, g) - _bin_coords(c - e, g)) / 2e-5
+        R = _rot(q)
+        Sig = R @ np.diag(np.exp(2 * ls.astype(np.float64))) @ R.T
+        lam = np.linalg.eigvalsh(J @ Sig @ J.T)[-1]
+        assert abs(r2 - 9 * lam) <= 1e-4 * 9 * lam
+
+
+def test_circle_variant_keeps_exact_hits_inside_the_circle(oracle_lib):
+    """Variant 4 with one Gaussian: a ray outside the circle (FP64 distance to the centre
+    beyond r_k by a margin) gets nothing; one inside keeps the default reading's value
+    exactly (the exact test still decides the hit).  A Gaussian 1.5 m away whose 3-sigma
+    sphere spans 53 degrees has hit rays outside its linearised circle."""
+    g = small_grid(oracle_lib)
+    r = np.array([2.0, 2.0, 0.5], np.float32)
+    t = np.array([7.0, 1.0, 2.5], np.float32)
+    for mu, ls in (((4.5, 3.5, 1.2), math.log(0.5)), ((3.2, 2.6, 1.2), math.log(0.22))):
+        s = one_gaussian(mu, log_s=(ls, ls * 0.9, ls * 1.1), quat=(0.9, 0.2, -0.3, 0.1), logit=0.3)
+        out0 = oracle_lib.render(s, r, t, 2.4e9, g, mode=1)
+        out4 = oracle_lib.render(s, r, t, 2.4e9, small_grid(oracle_lib, variant=4), mode=1)
+        uk, vk, r2 = oracle_lib.circle_f32(s["means"][0], s["log_scales"][0], s["quats"][0], r, g)
+        u = np.arange(g.n_az * g.n_el) % g.n_az
+        v = np.arange(g.n_az * g.n_el) // g.n_az
+        d = np.sqrt((u - uk) ** 2 + (v - vk) ** 2)
+        inside, outside = d < math.sqrt(r2) - 1e-3, d > math.sqrt(r2) + 1e-3
+        assert np.all(out4["S"][0, outside] == 0)
+        assert np.array_equal(out4["S"][0, inside], out0["S"][0, inside])
+        assert np.count_nonzero(out0["S"][0, inside]) > 3
+    # the near one: its linearised circle misses rays the exact test hits
+    assert np.count_nonzero(out0["S"][0] != 0) > np.count_nonzero(out4["S"][0] != 0)
+
+
+def test_circle_variant_hits_are_a_subset(oracle_lib):
+    """Without early termination every ray of variant 4 composites a subset of the
+    default reading's pairs, so it never counts more hits."""
+    sc = {k: v for k, v in __import__("paper_2502_01826_gb300.synthetic", fromlist=["scene"]).scene(400, 5).items()
+          if not k.startswith("_")}
+    r = np.array([4.0, 3.0, 1.2], np.float32)
+    t = np.array([9.0, 1.0, 2.0], np.float32)
+    g0 = oracle_lib.make_grid(72, 18, eps_T=0.0)
+    g4 = oracle_lib.make_grid(72, 18, eps_T=0.0, variant=4)
+    n0 = oracle_lib.render(sc, r, t, 2.4e9, g0)["nhit"]
+    n4 = oracle_lib.render(sc, r, t, 2.4e9, g4)["nhit"]
+    assert np.all(n4 <= n0) and n4.sum() < n0.sum()
