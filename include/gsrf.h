@@ -105,10 +105,16 @@ typedef struct {
                                 * Fourier-Legendre radiance at the direction of mu_k seen from
                                 * the receiver (Sec. 4.3's v_k) for all its rays instead of at
                                 * each ray's direction; GSRF_VARIANT_NORMALISED_WEIGHT weights by
-                                * the normalised density (App. A.3), g / ((2 pi)^1.5 |Sigma|^0.5) */
+                                * the normalised density (App. A.3), g / ((2 pi)^1.5 |Sigma|^0.5);
+                                * GSRF_VARIANT_PAPER_CULLING lets ray (u, v) meet Gaussian k only
+                                * inside its splatting circle (Sec. 4.3): centre (u_k, v_k) = the
+                                * bin of mu_k's direction, radius 3 sqrt(lambda_max(J Sigma J^T))
+                                * in bins, decided in FP32 with correctly rounded operations; the
+                                * exact test still decides the hit inside it.  0..7 */
 } gsrf_plan;
 #define GSRF_VARIANT_RADIANCE_AT_MEAN 1
 #define GSRF_VARIANT_NORMALISED_WEIGHT 2
+#define GSRF_VARIANT_PAPER_CULLING 4
 
 /* Bytes of workspace a plan needs (256-byte aligned base required). [host] out. */
 gsrf_status gsrf_workspace_size(const gsrf_plan *plan, size_t *bytes);

@@ -60,6 +60,8 @@ bool make_layout(const gsrf_plan* p, Layout* L) {
     L->qorder = take(items * 4);
     L->qhist = take((items + kChunk - 1) / kChunk * 32 * 4);
     L->qcounter = take(8);
+    // the paper's splatting circles, per (receiver, Gaussian), only for that variant
+    L->circle = take((p->variant & GSRF_VARIANT_PAPER_CULLING) ? nr * n * sizeof(float4) : 0);
     L->total = off;
     return true;
 }
@@ -97,7 +99,7 @@ static gsrf_status check_plan(const gsrf_plan* p) {
     if (!(p->stage == 0 || p->stage == 16 || p->stage == 32)) return GSRF_ERR_INVALID_ARG;
     if (p->ckpt_every < 0 || p->ckpt_every % 32 != 0 || p->ckpt_every > (1 << 24)) return GSRF_ERR_INVALID_ARG;
     if (p->ckpt_every > 0 && (p->ckpt_slots < 1 || p->ckpt_slots > 64)) return GSRF_ERR_INVALID_ARG;
-    if (p->variant < 0 || p->variant > 3) return GSRF_ERR_INVALID_ARG;
+    if (p->variant < 0 || p->variant > 7) return GSRF_ERR_INVALID_ARG;
     const gsrf_status s = check_grid(&p->grid);
     if (s != GSRF_OK) return s;
     const int w = plan_block_w(p);

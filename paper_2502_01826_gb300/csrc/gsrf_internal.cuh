@@ -93,7 +93,7 @@ struct Layout {
     // byte offsets
     size_t status, rxpos, txpos, gacc, raytab, fle, gshape, dpath, view, cover, dkey, dkey2, dval, dval2, dhist, dchunk_sum,
         rx_base, rx_total, pchunk_base, pkeys, pkeys2, pids, pids2, tile_start, thist, qkeys, qkeys2, qorder, qhist,
-        qcounter, total;
+        qcounter, circle, total;
     int32_t ntu, ntv, n_tiles;
     int32_t n_rx;
     int64_t n;
@@ -170,6 +170,85 @@ __device__ __forceinline__ float det_asin(float s) {
     s = fminf(fmaxf(s, -1.0f), 1.0f);
     float c = dsqrt(dmul(dsub(1.0f, s), dadd(1.0f, s)));
     return det_atan2(s, c);
+}
+
+// The paper's splatting circle (Sec. 4.3, "Splatting Process"; plan variant
+// GSRF_VARIANT_PAPER_CULLING).  Centre: the bin of the receiving plane that holds the
+// direction of c = mu - r (azimuth atan2(cy, cx), elevation asin(cz / D), floored with the
+// grid's origin and step).  Spread: lambda_max of Sigma2D = J Sigma J^T with J = d(u, v)/d mu
+// in bins per metre,
+//   du/dmu = (180 / pi / daz) (-cy, cx, 0) / rho^2,
+//   dv/dmu = (180 / pi / del) (-cx cz, -cy cz, rho^2) / (rho D^2),
+// Sigma = R diag(s)^2 R^T, so Sigma2D_ab = (diag(s) R^T J_a) . (diag(s) R^T J_b); r^2 = 9
+// lambda_max.  Returns (u_k, v_k, r^2, 0); r^2 = +inf (every ray) where J does not exist
+// (rho = 0) or the arithmetic overflows.  Deterministic FP32 (R and s rebuilt from the raw
+// parameters with correctly rounded operations), so the oracle decides identically.
+__device__ __forceinline__ float4 circle_of(float cx, float cy, float cz, const float* ls, const float* q,
+                                            const gsrf_grid& gr) {
+    const float rad2deg = 57.2957795f;
+    const float rho2 = dadd(dmul(cx, cx), dmul(cy, cy));
+    const float d2 = dadd(rho2, dmul(cz, cz));
+    const float D = dsqrt(d2);
+    float rel = dsub(dmul(det_atan2(cy, cx), rad2deg), gr.az0_deg);
+    if (rel < 0.0f) rel = dadd(rel, 360.0f);
+    if (rel < 0.0f) rel = dadd(rel, 360.0f);
+    if (rel >= 360.0f) rel = dsub(rel, 360.0f);
+    float4 out;
+    out.x = floorf(ddiv(rel, gr.daz_deg));
+    const float el = D > 0.0f ? dmul(det_asin(ddiv(cz, D)), rad2deg) : 0.0f;
+    out.y = floorf(ddiv(dsub(el, gr.el0_deg), gr.del_deg));
+    out.z = __int_as_float(0x7f800000);  // +inf
+    out.w = 0.0f;
+    if (!(rho2 > 0.0f)) return out;
+    const float rho = dsqrt(rho2);
+    const float ku = ddiv(rad2deg, dmul(gr.daz_deg, rho2));
+    const float kv = ddiv(rad2deg, dmul(gr.del_deg, dmul(rho, d2)));
+    const float ju0 = dmul(-cy, ku), ju1 = dmul(cx, ku), ju2 = 0.0f;
+    const float jv0 = dmul(dmul(-cx, cz), kv), jv1 = dmul(dmul(-cy, cz), kv), jv2 = dmul(rho2, kv);
+    float qw = q[0], qx = q[1], qy = q[2], qz = q[3];
+    const float n2 = dadd(dadd(dadd(dmul(qw, qw), dmul(qx, qx)), dmul(qy, qy)), dmul(qz, qz));
+    if (n2 > 0.0f) {
+        const float qn = dsqrt(n2);
+        qw = ddiv(qw, qn);
+        qx = ddiv(qx, qn);
+        qy = ddiv(qy, qn);
+        qz = ddiv(qz, qn);
+    } else {
+        qw = 1.0f;
+        qx = qy = qz = 0.0f;
+    }
+    float R[9];
+    R[0] = dsub(1.0f, dmul(2.0f, dadd(dmul(qy, qy), dmul(qz, qz))));
+    R[1] = dmul(2.0f, dsub(dmul(qx, qy), dmul(qw, qz)));
+    R[2] = dmul(2.0f, dadd(dmul(qx, qz), dmul(qw, qy)));
+    R[3] = dmul(2.0f, dadd(dmul(qx, qy), dmul(qw, qz)));
+    R[4] = dsub(1.0f, dmul(2.0f, dadd(dmul(qx, qx), dmul(qz, qz))));
+    R[5] = dmul(2.0f, dsub(dmul(qy, qz), dmul(qw, qx)));
+    R[6] = dmul(2.0f, dsub(dmul(qx, qz), dmul(qw, qy)));
+    R[7] = dmul(2.0f, dadd(dmul(qy, qz), dmul(qw, qx)));
+    R[8] = dsub(1.0f, dmul(2.0f, dadd(dmul(qx, qx), dmul(qy, qy))));
+    float A = 0.0f, B = 0.0f, C = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float si = det_exp(ls[i]);
+        const float tu = dadd(dadd(dmul(R[i], ju0), dmul(R[3 + i], ju1)), dmul(R[6 + i], ju2));
+        const float tv = dadd(dadd(dmul(R[i], jv0), dmul(R[3 + i], jv1)), dmul(R[6 + i], jv2));
+        const float au = dmul(si, tu), av = dmul(si, tv);
+        A = dadd(A, dmul(au, au));
+        B = dadd(B, dmul(au, av));
+        C = dadd(C, dmul(av, av));
+    }
+    const float h = dmul(dsub(A, C), 0.5f);
+    const float lam = dadd(dmul(dadd(A, C), 0.5f), dsqrt(dadd(dmul(h, h), dmul(B, B))));
+    const float r2 = dmul(9.0f, lam);
+    if (r2 < __int_as_float(0x7f800000)) out.z = r2;  // NaN or inf: every ray
+    return out;
+}
+
+// Ray (u, v) inside a splatting circle (circle_of): (u - u_k)^2 + (v - v_k)^2 <= r^2.
+__device__ __forceinline__ bool circle_in(const float4& cc, int u, int v) {
+    const float du = dsub((float)u, cc.x), dv = dsub((float)v, cc.y);
+    return dadd(dmul(du, du), dmul(dv, dv)) <= cc.z;
 }
 
 // ---------------------------------------------------------------------------

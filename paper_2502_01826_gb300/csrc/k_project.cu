@@ -279,7 +279,8 @@ __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __r
                                               View* __restrict__ view, Cover* __restrict__ cover,
                                               uint32_t* __restrict__ dkey, float* __restrict__ rx_keep,
                                               const float* __restrict__ txp, float* __restrict__ tx_keep,
-                                              const float* __restrict__ fle, int variant) {
+                                              const float* __restrict__ fle, int variant,
+                                              float4* __restrict__ circle) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y;
     if (k == 0) {  // the render and its backward read the positions from the workspace
@@ -314,6 +315,8 @@ __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __r
     float D_c, Rs;
     bool wide;
     cover[o] = cover_of(cx, cy, cz, lsm, gr, ntu, ntv, D_c, Rs, wide);
+    if (variant & GSRF_VARIANT_PAPER_CULLING)
+        circle[o] = circle_of(cx, cy, cz, g.log_scales + 3 * k, g.quats + 4 * k, gr);
     // direction pre-test of the render: D cos(theta) of the cover's cone less a rounding
     // margin; below -D (every direction passes) when the cone is a hemisphere or wider
     v.ccos = wide ? -1.0f - D_c : sqrtf(fmaxf(D_c * D_c - Rs * Rs, 0.0f)) - 2e-6f * D_c;
@@ -355,7 +358,8 @@ cudaError_t launch_project(const gsrf_plan* p, const Layout& L, const gsrf_gauss
                                               (float)(2.0 * 3.14159265358979323846 * p->df_hz / kC),
                                               at<View>(ws, L.view), at<Cover>(ws, L.cover),
                                               at<uint32_t>(ws, L.dkey), at<float>(ws, L.rxpos), tx,
-                                              at<float>(ws, L.txpos), at<float>(ws, L.fle), p->variant);
+                                              at<float>(ws, L.txpos), at<float>(ws, L.fle), p->variant,
+                                              at<float4>(ws, L.circle));
     return cudaGetLastError();
 }
 

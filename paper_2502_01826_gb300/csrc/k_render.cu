@@ -64,6 +64,7 @@ struct RenderArgs {
     int ck_every; // list positions between checkpoints (a multiple of 32)
     int ck_slots;
     int variant;  // GSRF_VARIANT_* bits
+    const float4* circle;  // the paper's splatting circles [receiver][Gaussian] (that variant only)
 };
 
 constexpr int kMaxJobs = 96;
@@ -202,6 +203,9 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
                 for (uint32_t m = mask; m; m &= m - 1) {
                     const int j = __ffs(m) - 1;
                     const float4* rec = sbuf[bf][j];
+                    if ((a.variant & GSRF_VARIANT_PAPER_CULLING) &&
+                        !circle_in(__ldg(a.circle + (size_t)r * a.n + sid[bf][j]), u, v))
+                        continue;  // outside the Gaussian's splatting circle (Sec. 4.3)
                     const float4 v1 = rec[0], s2 = rec[4];
                     PairGeo pg;
                     if (!pair_hits(v1, rec[2], rec[3], s2, dx, dy, dz, r_rx, pg)) continue;
@@ -435,6 +439,7 @@ static RenderArgs render_args(const gsrf_plan* p, const Layout& L, void* ws, flo
     a.ck_every = p->ckpt_every > 0 ? p->ckpt_every : 1;
     a.ck_slots = p->ckpt_slots;
     a.variant = p->variant;
+    a.circle = (p->variant & GSRF_VARIANT_PAPER_CULLING) ? at<float4>(ws, L.circle) : nullptr;
     return a;
 }
 

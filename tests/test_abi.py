@@ -131,7 +131,7 @@ def test_tile_shapes_ray_blocks_and_stages_accepted(lib, tw, th, bw, stage):
 @pytest.mark.parametrize("fields", [dict(ray_block_w=2), dict(ray_block_w=12), dict(ray_block_w=64),
                                     dict(stage=8), dict(stage=24), dict(stage=-1), dict(ckpt_every=48, ckpt_slots=4),
                                     dict(ckpt_every=-32, ckpt_slots=4), dict(ckpt_every=64, ckpt_slots=0),
-                                    dict(ckpt_every=64, ckpt_slots=65), dict(variant=4), dict(variant=-1)])
+                                    dict(ckpt_every=64, ckpt_slots=65), dict(variant=8), dict(variant=-1)])
 def test_bad_ray_block_stage_or_checkpoints_rejected(lib, fields):
     sz = C.c_size_t()
     p = plan()

@@ -1,7 +1,9 @@
 """Variant readings (forward only): the radiance at the direction of the Gaussian's mean
-instead of each ray's (GSRF_VARIANT_RADIANCE_AT_MEAN) and the normalised density weight
-(GSRF_VARIANT_NORMALISED_WEIGHT), alone and together, held to the same bars against the
-oracle rendering the same reading."""
+instead of each ray's (GSRF_VARIANT_RADIANCE_AT_MEAN), the normalised density weight
+(GSRF_VARIANT_NORMALISED_WEIGHT) and the paper's splatting-circle culling
+(GSRF_VARIANT_PAPER_CULLING), alone and together, held to the same bars against the
+oracle rendering the same reading.  The circle is a discrete decision both sides take
+in FP32 with the same operations, so it needs no band of its own."""
 import numpy as np
 import pytest
 
@@ -21,7 +23,8 @@ def _gpu():
 
 
 @pytest.mark.parametrize("variant", [L.VARIANT_RADIANCE_AT_MEAN, L.VARIANT_NORMALISED_WEIGHT,
-                                     L.VARIANT_RADIANCE_AT_MEAN | L.VARIANT_NORMALISED_WEIGHT])
+                                     L.VARIANT_RADIANCE_AT_MEAN | L.VARIANT_NORMALISED_WEIGHT,
+                                     L.VARIANT_PAPER_CULLING, L.VARIANT_PAPER_CULLING | L.VARIANT_RADIANCE_AT_MEAN])
 @pytest.mark.parametrize("workload", ["plain", "dense"])
 def test_variant_matches_oracle(variant, workload):
     if workload == "plain":
@@ -39,3 +42,18 @@ def test_variant_matches_oracle(variant, workload):
     for r in range(rx.shape[0]):
         ref = oracle_pair(scene, rx[r], tx, 2.4e9, g)
         compare(S[r], ref)
+
+
+def test_paper_culling_full_size_sampled():
+    """The paper's culling on the BLE workload in the benchmark's configuration (64
+    receivers, 360 x 90): 300 sampled rays of two receivers against the oracle."""
+    cfg = synthetic.config_ble()
+    S, R, _, _ = gpu_render(cfg["scene"], cfg["rx"], cfg["tx"], cfg["f0"], cfg["grid"],
+                            variant=L.VARIANT_PAPER_CULLING)
+    assert R.status().code == 0
+    g = oracle.make_grid(**cfg["grid"], variant=L.VARIANT_PAPER_CULLING)
+    rng = np.random.default_rng(31)
+    for r in (0, 47):
+        rays = np.sort(rng.choice(g.n_az * g.n_el, 300, replace=False)).astype(np.int32)
+        ref = oracle_pair(cfg["scene"], cfg["rx"][r], cfg["tx"], cfg["f0"], g, rays=rays)
+        compare(S[r][rays], ref)
