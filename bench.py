@@ -379,6 +379,7 @@ def run_ours(args, ws, rank):
     fwd_bwd = train_leg(args, ws, flush) if not args.no_train else None
     csi = csi_leg(args, ws, flush) if not args.no_train else None
     million = million_leg(args, ws, flush) if not args.no_train else None
+    paper_loop = paper_loop_leg(args, ws, flush) if not args.no_train else None
     uneven = uneven_leg(args, flush) if args.uneven else None
     variants = variants_leg(args, ws, flush, split=(R.plan.grid.tile_w, R.plan.grid.tile_h,
                                                     R.plan.ray_block_w or 8, R.plan.stage or 32))
@@ -427,6 +428,7 @@ def run_ours(args, ws, rank):
         "fwd_bwd": fwd_bwd,
         "csi": csi,
         "fwd_bwd_1m": million,
+        "paper_loop": paper_loop,
         "uneven": uneven,
         "variants": variants,
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
@@ -788,6 +790,37 @@ def variants_leg(args, ws, flush, split=None):
                     "forward only"}
 
 
+def paper_loop_leg(args, ws, flush):
+    """One iteration of the paper's training loop (Sec. 4.4, App. B) through
+    ``train.Trainer`` on the training-shaped workload (200,000 Gaussians, 16 receivers,
+    360 x 90): forward, |S| spatial spectra, (1 - l1 - l2) L1 + l1 (1 - SSIM) + l2 Fourier
+    against the spectra of a separately seeded ground-truth set, backward, per-attribute
+    SGD, and the loss read back to the host.  Gaussian-count updates are off in the timed
+    iterations (they run once per 100).  CUDA events, L2 flushed between steps."""
+    import torch
+
+    from paper_2502_01826_gb300 import synthetic, train
+    from paper_2502_01826_gb300.render import Renderer, make_grid, to_device
+
+    cfg = synthetic.config_train(K=args.train_gauss, n_rx=args.train_rx)
+    K, n_rx = cfg["scene"]["means"].shape[0], cfg["rx"].shape[0]
+    rx = torch.tensor(cfg["rx"], device="cuda")
+    tx = torch.tensor(cfg["tx"], device="cuda")
+    gt = to_device(cfg["gt_scene"])
+    Rg = Renderer(K, n_rx, make_grid(**cfg["grid"]), cfg["f0"])
+    Rg.ensure_capacity(gt, rx, tx)
+    target = train.spectrum_of(Rg.forward(gt, rx, tx)[:, 0]).clone()
+    del Rg
+    tr = train.Trainer(to_device(cfg["scene"]), cfg["rx"], cfg["tx"], cfg["grid"], cfg["f0"], densify=False)
+    for _ in range(args.warmup):
+        tr.step(target)
+    ms = _time_steps(lambda: tr.step(target), args.steps, flush)
+    t = max_over_ranks(ms * args.steps / 1e3, ws)
+    return {"workload": cfg["name"], "n_gauss": K, "n_rx": n_rx, "ms_per_step": ms,
+            "iterations_per_s": sum_over_ranks(args.steps, ws) / t,
+            "loss": "spectrum: 0.7 L1 + 0.2 (1 - SSIM) + 0.1 Fourier", "optimizer": "SGD, per-attribute rates"}
+
+
 def million_leg(args, ws, flush, every=128, slots=32):
     """Forward + backward at 1,000,000 Gaussians (the top of the uneven workload's range)
     with transmittance checkpoints every `every` tile-list positions (`slots` per ray):
@@ -854,7 +887,7 @@ def main():
                     "rays per warp, 32 candidates per stage) instead of autotuning it")
     ap.add_argument("--split", default=None, help="fix the work split instead of tuning it: TWxTH,BW,STAGE "
                     "(e.g. 32x16,8,32), for profiling runs")
-    ap.add_argument("--only", choices=["train", "csi", "million", "variants"], default=None,
+    ap.add_argument("--only", choices=["train", "csi", "million", "variants", "paper_loop"], default=None,
                     help="run one secondary leg alone and print its record (profiling runs)")
     ap.add_argument("--train-gauss", type=int, default=200_000, help="Gaussians of the training leg")
     ap.add_argument("--train-rx", type=int, default=16, help="receivers of the training leg")
@@ -891,7 +924,8 @@ def main():
     if args.only:
         import torch
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-        leg = {"train": train_leg, "csi": csi_leg, "million": million_leg, "variants": variants_leg}[args.only]
+        leg = {"train": train_leg, "csi": csi_leg, "million": million_leg, "variants": variants_leg,
+               "paper_loop": paper_loop_leg}[args.only]
         rec = leg(args, ws, flush)
         if rank == 0:
             print(json.dumps({"only": args.only, **rec}))
