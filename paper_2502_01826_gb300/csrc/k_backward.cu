@@ -291,18 +291,24 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
                     g_o = g_alpha * gw;
                     g_m2r = -0.5f * g_alpha * o * gw;
                 }
-                // (m2r, dt) <- (A, B, C); t_mid = -B/A, h = sqrt((9 - m2)/A), B = -A t_mid
-                const float A = pg.A, tm = pg.tm, h = pg.h;
-                const float iAh = 1.0f / fmaxf(A * h, 1e-30f);
+                // (m2r, dt) <- (A, B, C); t_mid = -B/A, h = sqrt((9 - m2)/A), B = -A t_mid.
+                // d dt / d m2 = -1 / (A h) is unbounded as the ray grazes the 3-sigma
+                // boundary, but m2 itself is only known to about 1e-6 |w| in FP32 (C = |w|^2
+                // reaches 1e5): below the chord such an error allows, h_f = sqrt(2e-6 |w| / A),
+                // the chord is rounding noise, so its derivatives are taken at h_f there
+                const float A = pg.A, tm = pg.tm;
+                const float wn = sqrtf(v1.x * v1.x + v1.y * v1.y + v1.z * v1.z);
+                const float h = fmaxf(pg.h, sqrtf(2e-6f * wn * pg.iA));
+                const float iAh = 1.0f / (A * h);
                 float gA, gB, gC;
-                if (tm - h >= r_rx) {
+                if (tm - pg.h >= r_rx) {  // the chord is not clipped at the emitting sphere
                     gA = g_m2r * tm * tm - g_dt * (tm * tm + h * h) * iAh;
                     gB = g_m2r * 2.0f * tm - g_dt * 2.0f * tm * iAh;
                     gC = g_m2r - g_dt * iAh;
                 } else {
                     const float t_out = pg.t_out, t_rep = 0.5f * (r_rx + t_out);
                     const float doA = -t_out * pg.iA - 0.5f * (tm * tm - h * h) * iAh;
-                    const float doB = (-1.0f - tm / fmaxf(h, 1e-30f)) * pg.iA;
+                    const float doB = (-1.0f - tm / h) * pg.iA;
                     const float doC = -0.5f * iAh;
                     const float lin = A * pg.dl;  // half of d m2r / d t_rep
                     gA = g_m2r * (t_rep * t_rep + lin * doA) + g_dt * doA;
