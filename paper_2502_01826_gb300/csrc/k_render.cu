@@ -89,14 +89,15 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // (see kFle) and the ray's basis values: P = (P10, P20, P30), Y = six complex Y_{l,m>0}.
 __device__ __forceinline__ void fle_psi(const float4* __restrict__ q4, const float* P, const float* Y,
                                         float& pr, float& pi) {
+    // one fused multiply-add per product, accumulated in order
     const float4 a0 = __ldg(q4), a1 = __ldg(q4 + 1);
-    pr = a0.x + a0.z * P[0] + a1.x * P[1] + a1.z * P[2];
-    pi = a0.y + a0.w * P[0] + a1.y * P[1] + a1.w * P[2];
+    pr = fmaf(a1.z, P[2], fmaf(a1.x, P[1], fmaf(a0.z, P[0], a0.x)));
+    pi = fmaf(a1.w, P[2], fmaf(a1.y, P[1], fmaf(a0.w, P[0], a0.y)));
 #pragma unroll
     for (int t = 0; t < 6; ++t) {
         const float4 e = __ldg(q4 + 2 + t);
-        pr += e.x * Y[2 * t] + e.y * Y[2 * t + 1];
-        pi += e.z * Y[2 * t] + e.w * Y[2 * t + 1];
+        pr = fmaf(e.y, Y[2 * t + 1], fmaf(e.x, Y[2 * t], pr));
+        pi = fmaf(e.w, Y[2 * t + 1], fmaf(e.z, Y[2 * t], pi));
     }
 }
 
