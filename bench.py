@@ -380,6 +380,7 @@ def run_ours(args, ws, rank):
     csi = csi_leg(args, ws, flush) if not args.no_train else None
     million = million_leg(args, ws, flush) if not args.no_train else None
     paper_loop = paper_loop_leg(args, ws, flush) if not args.no_train else None
+    angular = angular_leg(args, ws, flush)
     uneven = uneven_leg(args, flush) if args.uneven else None
     variants = variants_leg(args, ws, flush, split=(R.plan.grid.tile_w, R.plan.grid.tile_h,
                                                     R.plan.ray_block_w or 8, R.plan.stage or 32))
@@ -429,6 +430,7 @@ def run_ours(args, ws, rank):
         "csi": csi,
         "fwd_bwd_1m": million,
         "paper_loop": paper_loop,
+        "angular": angular,
         "uneven": uneven,
         "variants": variants,
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
@@ -821,6 +823,52 @@ def paper_loop_leg(args, ws, flush):
             "loss": "spectrum: 0.7 L1 + 0.2 (1 - SSIM) + 0.1 Fourier", "optimizer": "SGD, per-attribute rates"}
 
 
+ANGULAR_GRIDS = [  # the paper's angular-resolution study: name, n_az, n_el, el0_deg
+    ("5deg_hemisphere", 72, 18, 0.0), ("2deg_hemisphere", 180, 45, 0.0), ("1deg_hemisphere", 360, 90, 0.0),
+    ("0.5deg_hemisphere", 720, 180, 0.0), ("1deg_full_sphere", 360, 180, -90.0)]
+
+
+def angular_leg(args, ws, flush):
+    """The BLE scene (50,000 Gaussians, 64 receivers) at the angular resolutions of the
+    paper's study: forward step (project + bin + render + RSSI) with the default work
+    split per grid; composited pairs per second and spectra per second.  CUDA events,
+    L2 flushed between steps."""
+    import torch
+
+    from paper_2502_01826_gb300 import _lib as L
+    from paper_2502_01826_gb300 import synthetic
+    from paper_2502_01826_gb300.render import Renderer, make_grid, received_signal, to_device
+
+    cfg = rank_receivers(synthetic.config_ble(n_rx=args.n_rx), int(os.environ.get("RANK", "0")))
+    K, n_rx = cfg["scene"]["means"].shape[0], cfg["rx"].shape[0]
+    p = to_device(cfg["scene"])
+    rx = torch.tensor(cfg["rx"], device="cuda")
+    tx = torch.tensor(cfg["tx"], device="cuda")
+    res = {}
+    for name, n_az, n_el, el0 in ANGULAR_GRIDS:
+        grid = make_grid(n_az, n_el, el0_deg=el0, daz_deg=360.0 / n_az, del_deg=(90.0 - el0) / n_el)
+        R = Renderer(K, n_rx, grid, cfg["f0"])
+        R.ensure_capacity(p, rx, tx)
+        out = torch.empty(R.out_shape(), dtype=torch.float32, device="cuda")
+
+        def fwd():
+            R.forward(p, rx, tx, out=out)
+            return received_signal(out, L.SIG_RSSI_DB)
+
+        for _ in range(args.warmup):
+            fwd()
+        torch.cuda.synchronize()
+        st = R.status()
+        L.check("angular %s (device status)" % name, st.code)
+        ms = _time_steps(fwd, args.steps, flush)
+        t = max_over_ranks(ms * args.steps / 1e3, ws)
+        res[name] = {"grid": "%dx%d" % (n_az, n_el), "ms_per_step": ms, "pairs_per_step": int(st.stats[1]),
+                     "pairs_per_s": sum_over_ranks(int(st.stats[1]) * args.steps, ws) / t,
+                     "spectra_per_s": sum_over_ranks(n_rx * args.steps, ws) / t}
+        del R, out
+    return {"workload": cfg["name"], "split": "16x16,8,32 (default)", **res}
+
+
 def million_leg(args, ws, flush, every=128, slots=32):
     """Forward + backward at 1,000,000 Gaussians (the top of the uneven workload's range)
     with transmittance checkpoints every `every` tile-list positions (`slots` per ray):
@@ -887,7 +935,7 @@ def main():
                     "rays per warp, 32 candidates per stage) instead of autotuning it")
     ap.add_argument("--split", default=None, help="fix the work split instead of tuning it: TWxTH,BW,STAGE "
                     "(e.g. 32x16,8,32), for profiling runs")
-    ap.add_argument("--only", choices=["train", "csi", "million", "variants", "paper_loop"], default=None,
+    ap.add_argument("--only", choices=["train", "csi", "million", "variants", "paper_loop", "angular"], default=None,
                     help="run one secondary leg alone and print its record (profiling runs)")
     ap.add_argument("--train-gauss", type=int, default=200_000, help="Gaussians of the training leg")
     ap.add_argument("--train-rx", type=int, default=16, help="receivers of the training leg")
@@ -925,7 +973,7 @@ def main():
         import torch
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
         leg = {"train": train_leg, "csi": csi_leg, "million": million_leg, "variants": variants_leg,
-               "paper_loop": paper_loop_leg}[args.only]
+               "paper_loop": paper_loop_leg, "angular": angular_leg}[args.only]
         rec = leg(args, ws, flush)
         if rank == 0:
             print(json.dumps({"only": args.only, **rec}))

@@ -206,3 +206,29 @@ def test_ble_50k_64rx_full_size_sampled():
     for r in (5, 33):
         ref = oracle.render(cfg["scene"], cfg["rx"][r], cfg["tx"], cfg["f0"], g)
         assert abs(db[r] - rssi_db(ref["S"][0])) <= TOL_DB
+
+
+@pytest.mark.parametrize("spec", [
+    dict(n_az=360, n_el=180, el0_deg=-90.0, del_deg=1.0),  # 1 degree, the full sphere
+    dict(n_az=720, n_el=180),                              # 0.5 degree, the front hemisphere
+    dict(n_az=72, n_el=36, el0_deg=-90.0, del_deg=5.0),    # 5 degrees, the full sphere
+])
+def test_angular_resolutions_full_size(spec):
+    """The BLE scene (50,000 Gaussians) at the angular resolutions of the paper's study,
+    through the poles on the full sphere: bins of one receiver bit-exact, 300 sampled rays
+    of two receivers against the oracle."""
+    cfg = synthetic.config_ble()
+    rx = cfg["rx"][:4]
+    S, R, p, out = gpu_render(cfg["scene"], rx, cfg["tx"], cfg["f0"], spec)
+    assert R.status().code == 0
+    g = oracle_grid(spec)
+    keys, ids, rb, ts = R.pairs()
+    rb = rb.cpu().numpy()
+    k_ref, i_ref, t_ref = oracle.bin_pairs(cfg["scene"], rx[2], g)
+    assert np.array_equal(keys[rb[2]:rb[3]].cpu().numpy().view(np.uint64), k_ref)
+    assert np.array_equal(ids[rb[2]:rb[3]].cpu().numpy().view(np.uint32), i_ref)
+    rng = np.random.default_rng(13)
+    for r in (0, 3):
+        rays = np.sort(rng.choice(S.shape[1], 300, replace=False)).astype(np.int32)
+        ref = oracle_pair(cfg["scene"], rx[r], cfg["tx"], cfg["f0"], g, rays=rays)
+        compare(S[r, rays], ref)
