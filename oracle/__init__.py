@@ -46,7 +46,8 @@ class Grid(C.Structure):
                 ("az0_deg", C.c_float), ("daz_deg", C.c_float),
                 ("el0_deg", C.c_float), ("del_deg", C.c_float),
                 ("r_rx", C.c_float), ("eps_T", C.c_float), ("alpha_max", C.c_float),
-                ("tile_w", C.c_int32), ("tile_h", C.c_int32), ("variant", C.c_int32)]
+                ("tile_w", C.c_int32), ("tile_h", C.c_int32), ("variant", C.c_int32),
+                ("fle_degree", C.c_int32)]
 
 
 class Scene(C.Structure):
@@ -76,6 +77,8 @@ def lib():
         L.or_legendre.argtypes = [C.c_int, C.c_int, dbl]
         L.or_basis.restype = None
         L.or_basis.argtypes = [dbl, dbl, vp]
+        L.or_basis_l.restype = None
+        L.or_basis_l.argtypes = [dbl, dbl, i32, vp]
         L.or_gaussian.restype = None
         L.or_gaussian.argtypes = [vp, i64, vp, vp, vp]
         L.or_intersect.restype = C.c_int
@@ -113,15 +116,16 @@ def _f32(a):
 
 
 def make_grid(n_az, n_el, az0_deg=0.0, daz_deg=None, el0_deg=0.0, del_deg=None, r_rx=1.0,
-              eps_T=1e-4, alpha_max=0.99, tile_w=16, tile_h=16, variant=0) -> Grid:
+              eps_T=1e-4, alpha_max=0.99, tile_w=16, tile_h=16, variant=0, fle_degree=0) -> Grid:
     """variant: bit 1 = radiance at the Gaussian's direction, bit 2 = normalised weight,
-    bit 4 = the paper's splatting-circle culling (see or_grid in gsrf_oracle.h)."""
+    bit 4 = the paper's splatting-circle culling; fle_degree: L of the radiance, 0 = 3
+    (see or_grid in gsrf_oracle.h)."""
     if daz_deg is None:
         daz_deg = 360.0 / n_az
     if del_deg is None:
         del_deg = 90.0 / n_el
     return Grid(n_az, n_el, az0_deg, daz_deg, el0_deg, del_deg, r_rx, eps_T, alpha_max,
-                tile_w, tile_h, variant)
+                tile_w, tile_h, variant, fle_degree)
 
 
 class _SceneRef:
@@ -143,9 +147,9 @@ def legendre(l: int, m: int, x: float) -> float:
     return lib().or_legendre(l, m, x)
 
 
-def basis(alpha: float, x: float) -> np.ndarray:
-    Y = np.zeros((16, 2))
-    lib().or_basis(alpha, x, _p(Y))
+def basis(alpha: float, x: float, L: int = 3) -> np.ndarray:
+    Y = np.zeros(((L + 1) ** 2, 2))
+    lib().or_basis_l(alpha, x, L, _p(Y))
     return Y[:, 0] + 1j * Y[:, 1]
 
 

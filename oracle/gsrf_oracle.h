@@ -43,7 +43,9 @@
 extern "C" {
 #endif
 
-#define OR_NB 16            /* Fourier-Legendre coefficients, degree L = 3 */
+#define OR_NB 16            /* Fourier-Legendre coefficients at the default degree L = 3 */
+#define OR_L_MAX 5
+#define OR_NB_MAX 36        /* (OR_L_MAX + 1)^2 */
 #define OR_C_LIGHT 3.0e8    /* propagation speed, m/s */
 
 typedef struct {
@@ -63,6 +65,9 @@ typedef struct {
                                   *   4  a ray (u, v) meets Gaussian k only inside its splatting
                                   *      circle on the receiving plane (Sec. 4.3, the paper's own
                                   *      culling: or_circle_f32), on top of the exact test */
+    int32_t fle_degree;          /* Fourier-Legendre degree L of the radiance, 1..5 (0 = 3): the
+                                  * scene carries (L + 1)^2 complex coefficients per Gaussian,
+                                  * index l*l + l + m (Sec. 4.2); the gradient is L = 3 only */
 } or_grid;
 
 typedef struct {
@@ -103,8 +108,10 @@ typedef struct {
 /* Associated Legendre function P_l^m(x), -l <= m <= l, no Condon-Shortley phase. */
 double or_legendre(int l, int m, double x);
 
-/* The 16 complex basis values Y_n = e^{i m alpha} P_l^m(x), n = l*l + l + m. */
+/* The 16 complex basis values Y_n = e^{i m alpha} P_l^m(x), n = l*l + l + m (L = 3). */
 void or_basis(double alpha_rad, double x, double *Y /* [16][2] */);
+/* The same up to degree L (1..5): (L + 1)^2 values. */
+void or_basis_l(double alpha_rad, double x, int32_t L, double *Y /* [(L+1)^2][2] */);
 
 /* Gaussian k: Sigma (row-major 3x3), Sigma^-1, opacity in (0,1). */
 void or_gaussian(const or_scene *s, int64_t k, double *Sigma, double *Sinv, double *opacity);

@@ -55,9 +55,9 @@ double or_legendre(int l, int m, double x)
     return sign * factorial(l - am) / factorial(l + am) * legendre_pos(l, am, x);
 }
 
-void or_basis(double alpha, double x, double *Y)
+void or_basis_l(double alpha, double x, int32_t L, double *Y)
 {
-    for (int l = 0; l <= 3; ++l)
+    for (int l = 0; l <= L; ++l)
         for (int m = -l; m <= l; ++m) {
             int n = l * l + l + m;
             double p = or_legendre(l, m, x);
@@ -65,6 +65,10 @@ void or_basis(double alpha, double x, double *Y)
             Y[2 * n + 1] = sin((double)m * alpha) * p;
         }
 }
+
+void or_basis(double alpha, double x, double *Y) { or_basis_l(alpha, x, 3, Y); }
+
+static int32_t degree_of(const or_grid *g) { return g->fle_degree > 0 ? g->fle_degree : 3; }
 
 /* ------------------------------------------------------------------------- */
 /* Gaussian primitive (Sec. 4.2): Sigma = R S S^T R^T                          */
@@ -320,9 +324,10 @@ static void render_one(rctx *c, int64_t i)
     const or_grid *g = c->g;
     const int32_t ray = c->ray_idx ? c->ray_idx[i] : (int32_t)i;
     const int32_t nf = c->n_f;
-    double alpha, x, v[3], Y[2 * OR_NB];
+    const int32_t Ldeg = degree_of(g), nb = (Ldeg + 1) * (Ldeg + 1);
+    double alpha, x, v[3], Y[2 * OR_NB_MAX];
     ray_geometry(g, ray, &alpha, &x, v);
-    or_basis(alpha, x, Y);
+    or_basis_l(alpha, x, Ldeg, Y);
 
     const uint32_t *list;
     int64_t len;
@@ -360,13 +365,13 @@ static void render_one(rctx *c, int64_t i)
         if (!hit) continue;
         double a = c->op[k] * h[7];
         if (a > (double)g->alpha_max) a = (double)g->alpha_max;
-        const float *cf = c->s->coeffs + (size_t)k * 2 * OR_NB;
+        const float *cf = c->s->coeffs + (size_t)k * 2 * nb;
         double pr = 0.0, pi = 0.0; /* psi_k(ray) = sum_n c_n Y_n */
         if (g->variant & 1) {
             pr = c->psig[2 * k];
             pi = c->psig[2 * k + 1];
         } else {
-            for (int n = 0; n < OR_NB; ++n) {
+            for (int n = 0; n < nb; ++n) {
                 double cr = cf[2 * n], ci = cf[2 * n + 1];
                 pr += cr * Y[2 * n] - ci * Y[2 * n + 1];
                 pi += cr * Y[2 * n + 1] + ci * Y[2 * n];
@@ -468,10 +473,11 @@ static int prepare(rctx *c, const or_scene *s, const float *rx, const float *tx,
             double v[3] = {c->mu[3 * k] - rx[0], c->mu[3 * k + 1] - rx[1], c->mu[3 * k + 2] - rx[2]};
             double D = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]), rho = hypot(v[0], v[1]);
             double al = rho > 0.0 ? atan2(v[1], v[0]) : 0.0, x = D > 0.0 ? v[2] / D : 0.0;
-            double Yg[2 * OR_NB], pr = 0.0, pi = 0.0;
-            or_basis(al, x, Yg);
-            const float *cf = s->coeffs + (size_t)k * 2 * OR_NB;
-            for (int n2 = 0; n2 < OR_NB; ++n2) {
+            const int32_t Lg = degree_of(g), nbg = (Lg + 1) * (Lg + 1);
+            double Yg[2 * OR_NB_MAX], pr = 0.0, pi = 0.0;
+            or_basis_l(al, x, Lg, Yg);
+            const float *cf = s->coeffs + (size_t)k * 2 * nbg;
+            for (int n2 = 0; n2 < nbg; ++n2) {
                 pr += cf[2 * n2] * Yg[2 * n2] - cf[2 * n2 + 1] * Yg[2 * n2 + 1];
                 pi += cf[2 * n2] * Yg[2 * n2 + 1] + cf[2 * n2 + 1] * Yg[2 * n2];
             }
@@ -519,6 +525,7 @@ static int check_args(const or_scene *s, const or_grid *g, int32_t n_f, int32_t 
     if ((g->n_az + g->tile_w - 1) / g->tile_w > 64) return -1;
     if (!(g->daz_deg > 0.0f) || !(g->del_deg > 0.0f)) return -1;
     if (g->variant < 0 || g->variant > 7) return -1;
+    if (g->fle_degree < 0 || g->fle_degree > OR_L_MAX) return -1;
     return 0;
 }
 

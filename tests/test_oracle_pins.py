@@ -91,32 +91,36 @@ def test_legendre_all_orders_match_rodrigues(oracle_lib):
                 assert abs(oracle_lib.legendre(l, m, xv) - f(xv)) < 1e-12
 
 
-def test_basis_definition(oracle_lib):
+@pytest.mark.parametrize("L", [1, 2, 3, 4, 5])
+def test_basis_definition(oracle_lib, L):
     from scipy.special import lpmv
     for alpha, x in ((0.3, 0.2), (2.9, -0.7), (5.5, 0.95)):
-        Y = oracle_lib.basis(alpha, x)
-        for l in range(4):
+        Y = oracle_lib.basis(alpha, x, L)
+        assert Y.shape == ((L + 1) ** 2,)
+        for l in range(L + 1):
             for m in range(-l, l + 1):
                 ref = np.exp(1j * m * alpha) * (-1) ** m * lpmv(m, l, x)
-                assert abs(Y[l * l + l + m] - ref) < 1e-12
+                assert abs(Y[l * l + l + m] - ref) < 1e-11 * max(1.0, abs(ref))
 
 
-def test_basis_orthogonal_on_sphere(oracle_lib):
+@pytest.mark.parametrize("L", [3, 5])
+def test_basis_orthogonal_on_sphere(oracle_lib, L):
     """Gram matrix by Gauss-Legendre in x = sin(elevation) and uniform azimuth equals
     diag(2 pi * 2/(2l+1) * (l+m)!/(l-m)!): the basis is orthogonal on S^2 (Sec. 4.2)."""
+    nb = (L + 1) ** 2
     xs, wx = np.polynomial.legendre.leggauss(12)
     na = 16
     al = 2 * np.pi * np.arange(na) / na
-    G = np.zeros((16, 16), complex)
+    G = np.zeros((nb, nb), complex)
     for x, w in zip(xs, wx):
         for a in al:
-            Y = oracle_lib.basis(a, x)
+            Y = oracle_lib.basis(a, x, L)
             G += w * (2 * np.pi / na) * np.outer(Y, np.conj(Y))
-    D = np.zeros(16)
-    for l in range(4):
+    D = np.zeros(nb)
+    for l in range(L + 1):
         for m in range(-l, l + 1):
             D[l * l + l + m] = 2 * np.pi * 2 / (2 * l + 1) * math.factorial(l + m) / math.factorial(l - m)
-    assert np.allclose(G, np.diag(D), atol=1e-10)
+    assert np.allclose(G / np.sqrt(np.outer(D, D)), np.eye(nb), atol=1e-10)
 
 
 # --------------------------------------------------------------------------- primitive
@@ -368,24 +372,26 @@ def small_grid(oracle_lib, **kw):
     return oracle_lib.make_grid(72, 18, **kw)
 
 
-def test_single_gaussian_closed_form(oracle_lib):
-    """One Gaussian, T = 1: S = o g psi e^{-j 2 pi f d / c} on every hit ray (Eq. 14)."""
+@pytest.mark.parametrize("L", [3, 1, 5])
+def test_single_gaussian_closed_form(oracle_lib, L):
+    """One Gaussian, T = 1: S = o g psi e^{-j 2 pi f d / c} on every hit ray (Eq. 14), with
+    the radiance of degree L (Sec. 4.2's study of L)."""
     from scipy.special import lpmv
     rng = np.random.default_rng(1)
-    coeffs = rng.normal(0, 0.3, (16, 2))
+    coeffs = rng.normal(0, 0.3, ((L + 1) ** 2, 2))
     r = np.array([2.0, 2.0, 0.5], np.float32)
     t = np.array([7.0, 1.0, 2.5], np.float32)
     s = one_gaussian((4.0, 3.0, 1.0), log_s=(math.log(0.4), math.log(0.2), math.log(0.3)),
                      quat=(0.9, 0.1, -0.3, 0.2), logit=0.7, coeffs=coeffs, b=0.3)
-    grid = small_grid(oracle_lib)
+    grid = small_grid(oracle_lib, fle_degree=L)
     f = 2.4e9
     out = oracle_lib.render(s, r[None][0], t, f, grid, mode=1)
     Sg, Si, o = oracle_lib.gaussian(s, 0)
     mu = s["means"][0].astype(np.float64)
     d = np.linalg.norm(t.astype(np.float64) - mu) + np.linalg.norm(mu - r.astype(np.float64))
     A, E, dirs = ray_dirs(grid)
-    L = np.linalg.cholesky(Sg)
-    Li = np.linalg.inv(L)
+    Lc = np.linalg.cholesky(Sg)
+    Li = np.linalg.inv(Lc)
     cf = s["coeffs"][0].astype(np.float64)
     c = cf[:, 0] + 1j * cf[:, 1]
     n_hit = 0
@@ -401,7 +407,7 @@ def test_single_gaussian_closed_form(oracle_lib):
         n_hit += 1
         x = math.sin(E[i])
         psi = sum(c[l * l + l + m] * np.exp(1j * m * A[i]) * (-1) ** m * lpmv(m, l, x)
-                  for l in range(4) for m in range(-l, l + 1))
+                  for l in range(L + 1) for m in range(-l, l + 1))
         ref = min(o * math.exp(-m2 / 2), 0.99) * psi * np.exp(-2j * np.pi * f * d / 3e8)
         assert abs(out["S"][0, i] - ref) < 1e-10 * max(1e-3, abs(ref))
     assert n_hit > 10
@@ -897,3 +903,14 @@ def test_circle_variant_hits_are_a_subset(oracle_lib):
     n0 = oracle_lib.render(sc, r, t, 2.4e9, g0)["nhit"]
     n4 = oracle_lib.render(sc, r, t, 2.4e9, g4)["nhit"]
     assert np.all(n4 <= n0) and n4.sum() < n0.sum()
+
+
+def test_other_degrees_forward_only(oracle_lib):
+    """The gradient is the L = 3 adjoint only; other degrees are refused, not guessed."""
+    s = one_gaussian((4.0, 3.0, 1.0), coeffs=np.ones((36, 2)) * 0.1)
+    r = np.array([2.0, 2.0, 0.5], np.float32)
+    G = np.ones((1, 72 * 18), complex)
+    with pytest.raises(ValueError, match="rejected"):
+        oracle_lib.render_grad(s, r, r, 2.4e9, small_grid(oracle_lib, fle_degree=5), G)
+    out = oracle_lib.render(s, r, r, 2.4e9, small_grid(oracle_lib, fle_degree=5), mode=1)
+    assert np.count_nonzero(out["S"]) > 0
