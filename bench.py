@@ -381,6 +381,7 @@ def run_ours(args, ws, rank):
     million = million_leg(args, ws, flush) if not args.no_train else None
     paper_loop = paper_loop_leg(args, ws, flush) if not args.no_train else None
     angular = angular_leg(args, ws, flush)
+    fle_degree = fle_degree_leg(args, ws, flush)
     uneven = uneven_leg(args, flush) if args.uneven else None
     variants = variants_leg(args, ws, flush, split=(R.plan.grid.tile_w, R.plan.grid.tile_h,
                                                     R.plan.ray_block_w or 8, R.plan.stage or 32))
@@ -431,6 +432,7 @@ def run_ours(args, ws, rank):
         "fwd_bwd_1m": million,
         "paper_loop": paper_loop,
         "angular": angular,
+        "fle_degree": fle_degree,
         "uneven": uneven,
         "variants": variants,
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
@@ -869,6 +871,49 @@ def angular_leg(args, ws, flush):
     return {"workload": cfg["name"], "split": "16x16,8,32 (default)", **res}
 
 
+def fle_degree_leg(args, ws, flush):
+    """The BLE workload (50,000 Gaussians, 64 receivers, 360 x 90) with the radiance of
+    Fourier-Legendre degree L = 1..5 (the paper's study of L, Sec. 4.2): the same
+    geometry, receivers and split, (L + 1)^2 seeded coefficients per Gaussian; forward step
+    (project + bin + render + RSSI).  CUDA events, L2 flushed between steps."""
+    import numpy as np
+    import torch
+
+    from paper_2502_01826_gb300 import _lib as L
+    from paper_2502_01826_gb300 import synthetic
+    from paper_2502_01826_gb300.render import Renderer, make_grid, received_signal, to_device
+
+    cfg = rank_receivers(synthetic.config_ble(n_rx=args.n_rx), int(os.environ.get("RANK", "0")))
+    K, n_rx = cfg["scene"]["means"].shape[0], cfg["rx"].shape[0]
+    rx = torch.tensor(cfg["rx"], device="cuda")
+    tx = torch.tensor(cfg["tx"], device="cuda")
+    grid = make_grid(**cfg["grid"])
+    res = {}
+    for deg in (1, 2, 3, 4, 5):
+        sc = dict(cfg["scene"])
+        sc["coeffs"] = np.random.default_rng(100 + deg).normal(0.0, 0.1, (K, (deg + 1) ** 2, 2)).astype(np.float32)
+        p = to_device(sc)
+        R = Renderer(K, n_rx, grid, cfg["f0"], fle_degree=deg)
+        R.ensure_capacity(p, rx, tx)
+        out = torch.empty(R.out_shape(), dtype=torch.float32, device="cuda")
+
+        def fwd():
+            R.forward(p, rx, tx, out=out)
+            return received_signal(out, L.SIG_RSSI_DB)
+
+        for _ in range(args.warmup):
+            fwd()
+        torch.cuda.synchronize()
+        st = R.status()
+        L.check("degree %d (device status)" % deg, st.code)
+        ms = _time_steps(fwd, args.steps, flush)
+        t = max_over_ranks(ms * args.steps / 1e3, ws)
+        res["L%d" % deg] = {"coefficients": (deg + 1) ** 2, "ms_per_step": ms, "pairs_per_step": int(st.stats[1]),
+                            "pairs_per_s": sum_over_ranks(int(st.stats[1]) * args.steps, ws) / t}
+        del R, out, p
+    return {"workload": cfg["name"], "split": "16x16,8,32 (default)", **res}
+
+
 def million_leg(args, ws, flush, every=128, slots=32):
     """Forward + backward at 1,000,000 Gaussians (the top of the uneven workload's range)
     with transmittance checkpoints every `every` tile-list positions (`slots` per ray):
@@ -935,7 +980,7 @@ def main():
                     "rays per warp, 32 candidates per stage) instead of autotuning it")
     ap.add_argument("--split", default=None, help="fix the work split instead of tuning it: TWxTH,BW,STAGE "
                     "(e.g. 32x16,8,32), for profiling runs")
-    ap.add_argument("--only", choices=["train", "csi", "million", "variants", "paper_loop", "angular"], default=None,
+    ap.add_argument("--only", choices=["train", "csi", "million", "variants", "paper_loop", "angular", "fle_degree"], default=None,
                     help="run one secondary leg alone and print its record (profiling runs)")
     ap.add_argument("--train-gauss", type=int, default=200_000, help="Gaussians of the training leg")
     ap.add_argument("--train-rx", type=int, default=16, help="receivers of the training leg")
@@ -973,7 +1018,7 @@ def main():
         import torch
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
         leg = {"train": train_leg, "csi": csi_leg, "million": million_leg, "variants": variants_leg,
-               "paper_loop": paper_loop_leg, "angular": angular_leg}[args.only]
+               "paper_loop": paper_loop_leg, "angular": angular_leg, "fle_degree": fle_degree_leg}[args.only]
         rec = leg(args, ws, flush)
         if rank == 0:
             print(json.dumps({"only": args.only, **rec}))

@@ -77,7 +77,8 @@ typedef struct {
     const float *log_scales;   /* [n,3] log of the diagonal of S_k */
     const float *quats;        /* [n,4] rotation R_k as a quaternion (w,x,y,z), any non-zero norm */
     const float *opacity_logit;/* [n]   opacity before the sigmoid */
-    const float *coeffs;       /* [n,16,2] Fourier-Legendre coefficients c_{l,m}, index l*l+l+m */
+    const float *coeffs;       /* [n,(L+1)^2,2] Fourier-Legendre coefficients c_{l,m}, index l*l+l+m
+                                * (L = plan.fle_degree, 3 by default: [n,16,2]) */
     const float *phase_b;      /* [n] excess-phase coefficient b_k of the transmittance, or NULL (= 0) */
 } gsrf_gaussians;
 
@@ -111,6 +112,12 @@ typedef struct {
                                 * bin of mu_k's direction, radius 3 sqrt(lambda_max(J Sigma J^T))
                                 * in bins, decided in FP32 with correctly rounded operations; the
                                 * exact test still decides the hit inside it.  0..7 */
+    int32_t fle_degree;        /* degree L of the Fourier-Legendre radiance (Sec. 4.2), 1..5;
+                                * 0 = 3, the paper's choice.  The Gaussians then carry (L + 1)^2
+                                * complex coefficients each.  L != 3 is forward-only and
+                                * single-frequency: GSRF_ERR_UNSUPPORTED for n_f > 1, for the
+                                * backward, the batched render, and variant
+                                * GSRF_VARIANT_RADIANCE_AT_MEAN */
 } gsrf_plan;
 #define GSRF_VARIANT_RADIANCE_AT_MEAN 1
 #define GSRF_VARIANT_NORMALISED_WEIGHT 2

@@ -48,7 +48,7 @@ class gsrf_plan(C.Structure):
     _fields_ = [("n_gauss", C.c_int64), ("n_rx", C.c_int32), ("n_f", C.c_int32), ("f0_hz", C.c_double),
                 ("df_hz", C.c_double), ("grid", gsrf_grid), ("pair_capacity", C.c_int64),
                 ("ray_block_w", C.c_int32), ("stage", C.c_int32), ("ckpt_every", C.c_int32),
-                ("ckpt_slots", C.c_int32), ("variant", C.c_int32)]
+                ("ckpt_slots", C.c_int32), ("variant", C.c_int32), ("fle_degree", C.c_int32)]
 
 
 class gsrf_layout(C.Structure):

@@ -31,8 +31,8 @@ bool make_layout(const gsrf_plan* p, Layout* L) {
     L->rxpos = take(nr * 3 * sizeof(float));
     L->txpos = take(3 * sizeof(float));
     L->gacc = take(n * 48 * sizeof(float));
-    L->raytab = take((size_t)g.n_az * g.n_el * kRayTab * sizeof(float));
-    L->fle = take(n * kFle * sizeof(float));
+    L->raytab = take((size_t)g.n_az * g.n_el * raytab_floats(plan_degree(p)) * sizeof(float));
+    L->fle = take(n * fle_floats(plan_degree(p)) * sizeof(float));
     L->gshape = take(n * sizeof(GShape));
     L->dpath = take(n * sizeof(double));
     L->view = take(nr * n * sizeof(View));
@@ -100,6 +100,9 @@ static gsrf_status check_plan(const gsrf_plan* p) {
     if (p->ckpt_every < 0 || p->ckpt_every % 32 != 0 || p->ckpt_every > (1 << 24)) return GSRF_ERR_INVALID_ARG;
     if (p->ckpt_every > 0 && (p->ckpt_slots < 1 || p->ckpt_slots > 64)) return GSRF_ERR_INVALID_ARG;
     if (p->variant < 0 || p->variant > 7) return GSRF_ERR_INVALID_ARG;
+    if (p->fle_degree < 0 || p->fle_degree > 5) return GSRF_ERR_INVALID_ARG;
+    if (plan_degree(p) != 3 && (p->n_f > 1 || (p->variant & GSRF_VARIANT_RADIANCE_AT_MEAN)))
+        return GSRF_ERR_UNSUPPORTED;  // other degrees: one frequency, radiance per ray
     const gsrf_status s = check_grid(&p->grid);
     if (s != GSRF_OK) return s;
     const int w = plan_block_w(p);
@@ -200,7 +203,8 @@ gsrf_status gsrf_render_bwd(const gsrf_plan* plan, const gsrf_gaussians* g, void
     if ((s = check_gauss(plan, g)) != GSRF_OK) return s;
     if (!ray_state || !grad_rays || ((uintptr_t)ray_state & 15) != 0 || ((uintptr_t)grad_rays & 7) != 0)
         return GSRF_ERR_INVALID_ARG;
-    if (plan->variant != 0) return GSRF_ERR_UNSUPPORTED;  // the adjoint of the default reading only
+    if (plan->variant != 0 || plan_degree(plan) != 3)
+        return GSRF_ERR_UNSUPPORTED;  // the adjoint of the default reading and degree only
     return cuda_status(launch_render_bwd(plan, L, g, workspace, ray_state, grad_rays, g_means, g_log_scales, g_quats,
                                          g_opacity_logit, g_coeffs, g_phase_b, (cudaStream_t)stream));
 }
@@ -235,6 +239,7 @@ gsrf_status gsrf_render_batch(int32_t n_jobs, const gsrf_plan* plans, void* cons
         Layout L;
         if ((s = check_ws(&plans[j], workspaces[j], ws_bytes[j], &L)) != GSRF_OK) return s;
         if (!outs[j] || ((uintptr_t)outs[j] & 7) != 0) return GSRF_ERR_INVALID_ARG;
+        if (plan_degree(&plans[j]) != 3) return GSRF_ERR_UNSUPPORTED;
     }
     return cuda_status(launch_render_batch(n_jobs, plans, workspaces, outs, batch_ws, (cudaStream_t)stream));
 }

@@ -61,6 +61,16 @@ constexpr int kFle = 32;
 // P_1^0, P_2^0, P_3^0 at x = sin(elevation) and Y_{l,m} for the six m > 0 terms.
 constexpr int kRayTab = 20;  // floats: dx dy dz P10 | P20 P30 y11 | y21 y31 | y22 y32 | y33 - -
 
+// Per-degree sizes (Sec. 4.2's study of L = 1..5).  Folded coefficients: the m = 0
+// pairs (c_l0 re, im) for l = 0..L padded to whole float4, then one float4 per (l, m > 0)
+// in m-major order ((1,1) (2,1) .. (L,1) (2,2) .. (L,L)).  Ray table: direction, P_l0 for
+// l = 1..L, then (Re, Im) of Y_{l,m>0} in the same order, padded to whole float4.
+__host__ __device__ constexpr int fle_floats(int L) { return 4 * ((L + 2) / 2) + 2 * L * (L + 1); }
+__host__ __device__ constexpr int fle_m0_floats(int L) { return 4 * ((L + 2) / 2); }
+__host__ __device__ constexpr int raytab_floats(int L) { return 4 * ((L * (L + 2) + 6) / 4); }
+static_assert(fle_floats(3) == kFle && raytab_floats(3) == kRayTab, "the L = 3 layouts");
+inline int plan_degree(const gsrf_plan* p) { return p->fle_degree > 0 ? p->fle_degree : 3; }
+
 // Tile coverage of a Gaussian seen from a receiver: azimuth-tile bit mask,
 // elevation tile range packed lo | hi << 16, number of tiles.
 struct __align__(16) Cover {

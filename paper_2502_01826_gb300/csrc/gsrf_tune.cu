@@ -90,6 +90,7 @@ gsrf_status gsrf_autotune(const gsrf_plan* plan, const gsrf_gaussians* g, const 
     if (!plan || !g || !rx_pos || !tx_pos || !workspace || !out_rays || !best || reps < 1 || reps > 100)
         return GSRF_ERR_INVALID_ARG;
     if (bwd && (!bwd->ray_state || !bwd->grad_rays)) return GSRF_ERR_INVALID_ARG;
+    if (bwd && (plan->variant != 0 || plan_degree(plan) != 3)) return GSRF_ERR_UNSUPPORTED;
     if (max_results < 0 || (max_results > 0 && !results)) return GSRF_ERR_INVALID_ARG;
     size_t need = 0;
     gsrf_status s = gsrf_workspace_size(plan, &need);  // validates the caller's plan

@@ -21,7 +21,7 @@ __global__ void k_status_init(DevStatus* st) {
 // and |t - mu| in FP64 for the path phase.
 __global__ void __launch_bounds__(256) k_prepare(gsrf_gaussians g, const float* __restrict__ tx,
                                                  GShape* __restrict__ shape, double* __restrict__ dpath_t,
-                                                 float* __restrict__ fle, DevStatus* st, int variant) {
+                                                 float* __restrict__ fle, DevStatus* st, int variant, int L) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.n) return;
     const float mx = g.means[3 * k], my = g.means[3 * k + 1], mz = g.means[3 * k + 2];
@@ -32,9 +32,9 @@ __global__ void __launch_bounds__(256) k_prepare(gsrf_gaussians g, const float* 
     bool finite = isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(l0) && isfinite(l1) &&
                   isfinite(l2) && isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) &&
                   !isnan(ol) && isfinite(b);
-    const float* c = g.coeffs + (size_t)k * 2 * kNB;
-#pragma unroll
-    for (int i = 0; i < 2 * kNB; ++i) finite = finite && isfinite(c[i]);
+    const int nb = (L + 1) * (L + 1);  // coefficients of degree L (Sec. 4.2)
+    const float* c = g.coeffs + (size_t)k * 2 * nb;
+    for (int i = 0; i < 2 * nb; ++i) finite = finite && isfinite(c[i]);
     if (!finite) {
         atomicCAS(&st->code, (int)GSRF_OK, (int)GSRF_ERR_NONFINITE);
         atomicMin(&st->first_bad, (int)k);
@@ -68,53 +68,74 @@ __global__ void __launch_bounds__(256) k_prepare(gsrf_gaussians g, const float* 
     shape[k] = out;
     const double dx = (double)tx[0] - mx, dy = (double)tx[1] - my, dz = (double)tx[2] - mz;
     dpath_t[k] = sqrt(dx * dx + dy * dy + dz * dz);
-    // folded Fourier-Legendre coefficients (see kFle)
-    float* q = fle + (size_t)k * kFle;
-    const int m0[4] = {0, 2, 6, 12};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        q[2 * i] = c[2 * m0[i]];
-        q[2 * i + 1] = c[2 * m0[i] + 1];
+    // folded Fourier-Legendre coefficients (see fle_floats): the m = 0 pairs, then per
+    // (l, m > 0) in m-major order the four reals that fold c_{l,m} Y_{l,m} + c_{l,-m}
+    // Y_{l,-m} with Y_{l,-m} = kappa conj(Y_{l,m}), kappa = (-1)^m (l-m)!/(l+m)!
+    float* q = fle + (size_t)k * fle_floats(L);
+    const int m0 = fle_m0_floats(L);
+    for (int l = 0; l <= L; ++l) {
+        q[2 * l] = c[2 * (l * l + l)];
+        q[2 * l + 1] = c[2 * (l * l + l) + 1];
     }
-    // (l, m) = (1,1) (2,1) (3,1) (2,2) (3,2) (3,3): index of +m, of -m, kappa
-    const int np[6] = {3, 7, 13, 8, 14, 15}, nm[6] = {1, 5, 11, 4, 10, 9};
-    const float kap[6] = {-0.5f, -1.0f / 6.0f, -1.0f / 12.0f, 1.0f / 24.0f, 1.0f / 120.0f, -1.0f / 720.0f};
-#pragma unroll
-    for (int t = 0; t < 6; ++t) {
-        const float cr = c[2 * np[t]], ci = c[2 * np[t] + 1];
-        const float dr = kap[t] * c[2 * nm[t]], di = kap[t] * c[2 * nm[t] + 1];
-        q[8 + 4 * t] = cr + dr;
-        q[8 + 4 * t + 1] = di - ci;
-        q[8 + 4 * t + 2] = ci + di;
-        q[8 + 4 * t + 3] = cr - dr;
+    for (int i = 2 * (L + 1); i < m0; ++i) q[i] = 0.0f;
+    int t = 0;
+    for (int m = 1; m <= L; ++m) {
+        for (int l = m; l <= L; ++l, ++t) {
+            float prod = 1.0f;  // (l+m)!/(l-m)!, exact in FP32 up to L = 5 (10! < 2^24)
+            for (int i = l - m + 1; i <= l + m; ++i) prod *= (float)i;
+            const float kap = ((m & 1) ? -1.0f : 1.0f) / prod;
+            const int np = l * l + l + m, nm = l * l + l - m;
+            const float cr = c[2 * np], ci = c[2 * np + 1];
+            const float dr = kap * c[2 * nm], di = kap * c[2 * nm + 1];
+            q[m0 + 4 * t] = cr + dr;
+            q[m0 + 4 * t + 1] = di - ci;
+            q[m0 + 4 * t + 2] = ci + di;
+            q[m0 + 4 * t + 3] = cr - dr;
+        }
     }
 }
 
 // Per-ray table of the receiving grid, in FP64 and rounded once: the ray direction
 // (cos el cos az, cos el sin az, sin el) at the bin centre and the basis values the
-// folded Fourier-Legendre sum needs (P without the Condon-Shortley phase, x = sin el).
-__global__ void __launch_bounds__(256) k_raytab(gsrf_grid gr, float* __restrict__ tab) {
+// folded Fourier-Legendre sum of degree L needs (see raytab_floats): P_l^m without the
+// Condon-Shortley phase at x = sin el, by the recurrences P_m^m = (2m-1)!! (1-x^2)^{m/2},
+// P_{m+1}^m = (2m+1) x P_m^m, (l-m) P_l^m = (2l-1) x P_{l-1}^m - (l+m-1) P_{l-2}^m.
+__global__ void __launch_bounds__(256) k_raytab(gsrf_grid gr, int L, float* __restrict__ tab) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= gr.n_az * gr.n_el) return;
     const int u = i % gr.n_az, v = i / gr.n_az;
     const double deg = 0.017453292519943295;
     const double az = ((double)gr.az0_deg + ((double)u + 0.5) * (double)gr.daz_deg) * deg;
     const double el = ((double)gr.el0_deg + ((double)v + 0.5) * (double)gr.del_deg) * deg;
-    double se, ce, s1, c1, s2, c2, s3, c3;
+    double se, ce, s1, c1;
     sincos(el, &se, &ce);
     sincos(az, &s1, &c1);
-    sincos(2.0 * az, &s2, &c2);
-    sincos(3.0 * az, &s3, &c3);
-    const double x = se, sx = ce, x2 = x * x, sx2 = sx * sx;
-    const double P10 = x, P20 = 1.5 * x2 - 0.5, P30 = x * (2.5 * x2 - 1.5);
-    const double P11 = sx, P21 = 3.0 * x * sx, P31 = (7.5 * x2 - 1.5) * sx;
-    const double P22 = 3.0 * sx2, P32 = 15.0 * x * sx2, P33 = 15.0 * sx2 * sx;
-    float* t = tab + (size_t)i * kRayTab;
-    t[0] = (float)(ce * c1); t[1] = (float)(ce * s1); t[2] = (float)se; t[3] = (float)P10;
-    t[4] = (float)P20; t[5] = (float)P30; t[6] = (float)(c1 * P11); t[7] = (float)(s1 * P11);
-    t[8] = (float)(c1 * P21); t[9] = (float)(s1 * P21); t[10] = (float)(c1 * P31); t[11] = (float)(s1 * P31);
-    t[12] = (float)(c2 * P22); t[13] = (float)(s2 * P22); t[14] = (float)(c2 * P32); t[15] = (float)(s2 * P32);
-    t[16] = (float)(c3 * P33); t[17] = (float)(s3 * P33); t[18] = 0.0f; t[19] = 0.0f;
+    const double x = se, sx = ce;
+    double P[6][6];
+    for (int m = 0; m <= L; ++m) {
+        double pmm = 1.0;
+        for (int j = 1; j <= m; ++j) pmm *= (double)(2 * j - 1) * sx;
+        P[m][m] = pmm;
+        if (m + 1 <= L) P[m + 1][m] = (double)(2 * m + 1) * x * pmm;
+        for (int l = m + 2; l <= L; ++l)
+            P[l][m] = ((double)(2 * l - 1) * x * P[l - 1][m] - (double)(l + m - 1) * P[l - 2][m]) / (double)(l - m);
+    }
+    const int nf = raytab_floats(L);
+    float* t = tab + (size_t)i * nf;
+    t[0] = (float)(ce * c1);
+    t[1] = (float)(ce * s1);
+    t[2] = (float)se;
+    int o = 3;
+    for (int l = 1; l <= L; ++l) t[o++] = (float)P[l][0];
+    for (int m = 1; m <= L; ++m) {
+        double sm, cm;
+        sincos((double)m * az, &sm, &cm);
+        for (int l = m; l <= L; ++l) {
+            t[o++] = (float)(cm * P[l][m]);
+            t[o++] = (float)(sm * P[l][m]);
+        }
+    }
+    while (o < nf) t[o++] = 0.0f;
 }
 
 // Tile coverage: the bins of the receiving plane whose centre lies in the angular
@@ -343,16 +364,16 @@ cudaError_t launch_project(const gsrf_plan* p, const Layout& L, const gsrf_gauss
     k_status_init<<<1, 32, 0, st>>>(status);
     if (L.n == 0) {
         const int n_rays = p->grid.n_az * p->grid.n_el;
-        k_raytab<<<(n_rays + 255) / 256, 256, 0, st>>>(p->grid, at<float>(ws, L.raytab));
+        k_raytab<<<(n_rays + 255) / 256, 256, 0, st>>>(p->grid, plan_degree(p), at<float>(ws, L.raytab));
         cudaError_t e = cudaMemcpyAsync(at<float>(ws, L.rxpos), rx, sizeof(float) * 3 * L.n_rx,
                                         cudaMemcpyDeviceToDevice, st);
         return e != cudaSuccess ? e : cudaGetLastError();
     }
     const int n_rays = p->grid.n_az * p->grid.n_el;
-    k_raytab<<<(n_rays + 255) / 256, 256, 0, st>>>(p->grid, at<float>(ws, L.raytab));
+    k_raytab<<<(n_rays + 255) / 256, 256, 0, st>>>(p->grid, plan_degree(p), at<float>(ws, L.raytab));
     const unsigned nb = (unsigned)((L.n + 255) / 256);
     k_prepare<<<nb, 256, 0, st>>>(*g, tx, at<GShape>(ws, L.gshape), at<double>(ws, L.dpath),
-                                  at<float>(ws, L.fle), status, p->variant);
+                                  at<float>(ws, L.fle), status, p->variant, plan_degree(p));
     k_view<<<dim3(nb, L.n_rx), 256, 0, st>>>(*g, rx, at<GShape>(ws, L.gshape), at<double>(ws, L.dpath),
                                               p->grid, L.ntu, L.ntv, p->f0_hz / kC,
                                               (float)(2.0 * 3.14159265358979323846 * p->df_hz / kC),

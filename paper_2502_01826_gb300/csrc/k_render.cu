@@ -85,32 +85,59 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// Radiance psi of one Gaussian along one ray (Eq. 9) from the folded coefficients q
-// (see kFle) and the ray's basis values: P = (P10, P20, P30), Y = six complex Y_{l,m>0}.
+// Radiance psi of one Gaussian along one ray (Eq. 9) from its folded coefficients q
+// (see fle_floats) and the ray's basis values: P = (P_10 .. P_L0), Y = the complex
+// Y_{l,m>0} in m-major order.  One fused multiply-add per product, accumulated in order.
+template <int L>
 __device__ __forceinline__ void fle_psi(const float4* __restrict__ q4, const float* P, const float* Y,
                                         float& pr, float& pi) {
-    // one fused multiply-add per product, accumulated in order
-    const float4 a0 = __ldg(q4), a1 = __ldg(q4 + 1);
-    pr = fmaf(a1.z, P[2], fmaf(a1.x, P[1], fmaf(a0.z, P[0], a0.x)));
-    pi = fmaf(a1.w, P[2], fmaf(a1.y, P[1], fmaf(a0.w, P[0], a0.y)));
+    constexpr int kQ0 = fle_m0_floats(L) / 4;
+    float m0[4 * kQ0];
 #pragma unroll
-    for (int t = 0; t < 6; ++t) {
-        const float4 e = __ldg(q4 + 2 + t);
+    for (int i = 0; i < kQ0; ++i) {
+        const float4 a = __ldg(q4 + i);
+        m0[4 * i] = a.x;
+        m0[4 * i + 1] = a.y;
+        m0[4 * i + 2] = a.z;
+        m0[4 * i + 3] = a.w;
+    }
+    pr = m0[0];
+    pi = m0[1];
+#pragma unroll
+    for (int l = 1; l <= L; ++l) {
+        pr = fmaf(m0[2 * l], P[l - 1], pr);
+        pi = fmaf(m0[2 * l + 1], P[l - 1], pi);
+    }
+#pragma unroll
+    for (int t = 0; t < L * (L + 1) / 2; ++t) {
+        const float4 e = __ldg(q4 + kQ0 + t);
         pr = fmaf(e.y, Y[2 * t + 1], fmaf(e.x, Y[2 * t], pr));
         pi = fmaf(e.w, Y[2 * t + 1], fmaf(e.z, Y[2 * t], pi));
     }
 }
 
-// The ray's direction and basis values from the per-grid ray table.
+// The ray's direction and basis values from the per-grid ray table (see raytab_floats).
+template <int L>
 __device__ __forceinline__ void load_ray(const float* raytab, size_t ray, float& dx, float& dy, float& dz,
                                          float* P, float* Y) {
-    const float4* t4 = reinterpret_cast<const float4*>(raytab + ray * kRayTab);
-    const float4 t0 = t4[0], t1 = t4[1], t2 = t4[2], t3 = t4[3], t5 = t4[4];
-    dx = t0.x; dy = t0.y; dz = t0.z; P[0] = t0.w;
-    P[1] = t1.x; P[2] = t1.y; Y[0] = t1.z; Y[1] = t1.w;
-    Y[2] = t2.x; Y[3] = t2.y; Y[4] = t2.z; Y[5] = t2.w;
-    Y[6] = t3.x; Y[7] = t3.y; Y[8] = t3.z; Y[9] = t3.w;
-    Y[10] = t5.x; Y[11] = t5.y;
+    constexpr int kN = raytab_floats(L);
+    const float4* t4 = reinterpret_cast<const float4*>(raytab + ray * kN);
+    float t[kN];
+#pragma unroll
+    for (int i = 0; i < kN / 4; ++i) {
+        const float4 a = t4[i];
+        t[4 * i] = a.x;
+        t[4 * i + 1] = a.y;
+        t[4 * i + 2] = a.z;
+        t[4 * i + 3] = a.w;
+    }
+    dx = t[0];
+    dy = t[1];
+    dz = t[2];
+#pragma unroll
+    for (int l = 0; l < L; ++l) P[l] = t[3 + l];
+#pragma unroll
+    for (int n = 0; n < L * (L + 1); ++n) Y[n] = t[3 + L + n];
 }
 
 // One warp renders work item k (ray block k / nchunk, subcarrier chunk k % nchunk) of
@@ -122,7 +149,7 @@ __device__ __forceinline__ void load_ray(const float* raytab, size_t ray, float&
 // r = e^{-j (2 pi df d / c + 2 pi df Gamma / c)}, Gamma = sum over earlier pairs of b dt,
 // because T(f0 + s df) = T(f0) e^{-j s 2 pi df Gamma / c} and E(f0 + s df) =
 // E(f0) e^{-j s 2 pi df d / c}; the powers of r come from one sincos and a recurrence.
-template <int NFC, int WB>
+template <int NFC, int WB, int L>
 __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int tile, int k,
                                              float4 (*sbuf)[WB][kRec], uint32_t (*sid)[WB], float4* spl) {
     const int lane = threadIdx.x & 31;
@@ -134,10 +161,12 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
     const int u = u_lo + (lane & (bw - 1)), v = v_lo + (lane >> a.bw_log);
     const bool valid = u < gr.n_az && v < gr.n_el;
 
-    float dx = 0.0f, dy = 0.0f, dz = 1.0f, P[3] = {0.0f, 0.0f, 0.0f}, Y[12];
+    float dx = 0.0f, dy = 0.0f, dz = 1.0f, P[L], Y[L * (L + 1)];
 #pragma unroll
-    for (int i = 0; i < 12; ++i) Y[i] = 0.0f;
-    if (valid) load_ray(a.raytab, (size_t)v * gr.n_az + u, dx, dy, dz, P, Y);
+    for (int i = 0; i < L; ++i) P[i] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < L * (L + 1); ++i) Y[i] = 0.0f;
+    if (valid) load_ray<L>(a.raytab, (size_t)v * gr.n_az + u, dx, dy, dz, P, Y);
     const Bundle bun = warp_bundle(valid, dx, dy, dz);
     warp_planes(gr, u_lo, v_lo, bw, bh, bun, valid, dx, dy, dz, spl);
 
@@ -217,7 +246,8 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
                         pr = rec[1].z;
                         pi = rec[1].w;
                     } else {
-                        fle_psi(reinterpret_cast<const float4*>(a.fle + (size_t)sid[bf][j] * kFle), P, Y, pr, pi);
+                        fle_psi<L>(reinterpret_cast<const float4*>(a.fle + (size_t)sid[bf][j] * fle_floats(L)), P, Y,
+                                   pr, pi);
                     }
                     // S += alpha psi E T, E = e^{-j phi} = (er, ei)
                     const float er = v1.w, ei = rec[1].x;
@@ -303,8 +333,11 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
 // block, subcarrier chunk) from one counter, in heaviest-first order, until none is
 // left; a warp that finishes early takes the next item instead of idling until the
 // other warps of its CTA are done.
-template <int NFC, int WB>
-__global__ void __launch_bounds__(kThreads, NFC == 1 ? 7 : 4) k_render_queue(RenderArgs a,
+// One frequency: 7 CTAs per SM up to L = 3 (71 registers), fewer for the larger bases of
+// L = 4 and 5; chunks of subcarriers (L = 3 only): 4.
+template <int NFC, int WB, int L>
+__global__ void __launch_bounds__(kThreads, NFC == 1 ? (L <= 3 ? 7 : (L == 4 ? 6 : 5)) : 4)
+    k_render_queue(RenderArgs a,
                                                                             const uint32_t* __restrict__ order,
                                                                             unsigned long long* __restrict__ counter,
                                                                             unsigned long long total) {
@@ -320,8 +353,8 @@ __global__ void __launch_bounds__(kThreads, NFC == 1 ? 7 : 4) k_render_queue(Ren
         if (it >= total) break;
         const uint32_t id = order[it];
         const unsigned rem = id % per_rx;
-        render_block<NFC, WB>(a, (int)(id / per_rx), (int)(rem / (unsigned)a.per_tile), (int)(rem % (unsigned)a.per_tile),
-                              sbuf[warp], sid[warp], spl[warp]);
+        render_block<NFC, WB, L>(a, (int)(id / per_rx), (int)(rem / (unsigned)a.per_tile),
+                                 (int)(rem % (unsigned)a.per_tile), sbuf[warp], sid[warp], spl[warp]);
     }
 }
 
@@ -347,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, 7) k_render_batch(BatchArgs b, const
         const unsigned long long local = id - b.item_base[j];
         const unsigned long long per_rx = (unsigned long long)a.n_tiles * a.per_tile;
         const unsigned rem = (unsigned)(local % per_rx);
-        render_block<1, WB>(a, (int)(local / per_rx), (int)(rem / (unsigned)a.per_tile),
+        render_block<1, WB, 3>(a, (int)(local / per_rx), (int)(rem / (unsigned)a.per_tile),
                             (int)(rem % (unsigned)a.per_tile), sbuf[warp], sid[warp], spl[warp]);
     }
 }
@@ -444,14 +477,27 @@ static RenderArgs render_args(const gsrf_plan* p, const Layout& L, void* ws, flo
     return a;
 }
 
-template <int NFC, int WB>
+template <int NFC, int WB, int L = 3>
 static cudaError_t launch_queue(const RenderArgs& a, const uint32_t* order, unsigned long long* counter, long long n,
                                 cudaStream_t st) {
     int grid = 0;
-    cudaError_t e = resident_grid(k_render_queue<NFC, WB>, n, &grid);
+    cudaError_t e = resident_grid(k_render_queue<NFC, WB, L>, n, &grid);
     if (e != cudaSuccess) return e;
-    k_render_queue<NFC, WB><<<grid, kThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
+    k_render_queue<NFC, WB, L><<<grid, kThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
     return cudaGetLastError();
+}
+
+// One frequency at Fourier-Legendre degree L (1..5), stage of 16 or 32 candidates.
+template <int WB>
+static cudaError_t launch_queue_degree(int L, const RenderArgs& a, const uint32_t* order, unsigned long long* counter,
+                                       long long n, cudaStream_t st) {
+    switch (L) {
+        case 1: return launch_queue<1, WB, 1>(a, order, counter, n, st);
+        case 2: return launch_queue<1, WB, 2>(a, order, counter, n, st);
+        case 4: return launch_queue<1, WB, 4>(a, order, counter, n, st);
+        case 5: return launch_queue<1, WB, 5>(a, order, counter, n, st);
+        default: return launch_queue<1, WB, 3>(a, order, counter, n, st);
+    }
 }
 
 cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_gaussians* g, void* ws,
@@ -465,7 +511,9 @@ cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     if ((e = launch_item_order(L, ws, a.per_tile, &order, &counter, st)) != cudaSuccess) return e;
     const long long n = (long long)L.n_rx * L.n_tiles * a.per_tile;
     const bool wb16 = plan_stage(p) == 16;
-    if (p->n_f == 1) return wb16 ? launch_queue<1, 16>(a, order, counter, n, st) : launch_queue<1, 32>(a, order, counter, n, st);
+    if (p->n_f == 1)
+        return wb16 ? launch_queue_degree<16>(plan_degree(p), a, order, counter, n, st)
+                    : launch_queue_degree<32>(plan_degree(p), a, order, counter, n, st);
     if (p->n_f <= 8) return wb16 ? launch_queue<8, 16>(a, order, counter, n, st) : launch_queue<8, 32>(a, order, counter, n, st);
     return wb16 ? launch_queue<16, 16>(a, order, counter, n, st) : launch_queue<16, 32>(a, order, counter, n, st);
 }

@@ -68,12 +68,12 @@ class Renderer:
 
     def __init__(self, n_gauss: int, n_rx: int, grid: L.gsrf_grid, f0_hz: float, df_hz: float = 0.0,
                  n_f: int = 1, pair_capacity: int | None = None, device="cuda", ray_block_w: int = 0,
-                 stage: int = 0, ckpt_every: int = 0, ckpt_slots: int = 0, variant: int = 0):
+                 stage: int = 0, ckpt_every: int = 0, ckpt_slots: int = 0, variant: int = 0, fle_degree: int = 0):
         self.device = torch.device(device)
         if pair_capacity is None:
             pair_capacity = max(1024, 8 * n_gauss * n_rx)
         self.plan = L.gsrf_plan(n_gauss, n_rx, n_f, f0_hz, df_hz, grid, int(pair_capacity), int(ray_block_w),
-                                int(stage), int(ckpt_every), int(ckpt_slots), int(variant))
+                                int(stage), int(ckpt_every), int(ckpt_slots), int(variant), int(fle_degree))
         self._alloc()
 
     def _alloc(self):

@@ -29,7 +29,9 @@ BASE_SEED = 2502_01826
 C_LIGHT = 3.0e8
 
 
-def scene(K: int, seed: int) -> dict:
+def scene(K: int, seed: int, fle_degree: int = 3) -> dict:
+    """K Gaussians in the box; (L + 1)^2 complex Fourier-Legendre coefficients each for
+    degree L = fle_degree (16 for the paper's L = 3)."""
     g = np.random.Generator(np.random.PCG64(seed))
     box = np.asarray(BOX, np.float64)
     means = g.uniform(0.0, 1.0, size=(K, 3)) * box
@@ -37,7 +39,7 @@ def scene(K: int, seed: int) -> dict:
     q = g.normal(0.0, 1.0, size=(K, 4))
     q /= np.linalg.norm(q, axis=1, keepdims=True)
     opacity_logit = g.normal(0.0, 1.0, size=K)
-    coeffs = g.normal(0.0, 0.1, size=(K, 16, 2))
+    coeffs = g.normal(0.0, 0.1, size=(K, (fle_degree + 1) ** 2, 2))
     phase_b = g.normal(0.0, 0.1, size=K)
     return dict(means=means.astype(np.float32), log_scales=log_scales.astype(np.float32),
                 quats=q.astype(np.float32), opacity_logit=opacity_logit.astype(np.float32),

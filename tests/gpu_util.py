@@ -52,13 +52,13 @@ def oracle_grid(spec: dict, **kw):
     return oracle.make_grid(**args)
 
 
-def gpu_render(scene: dict, rx, tx, f0, grid_spec: dict, cap=None, variant=0, **grid_kw):
+def gpu_render(scene: dict, rx, tx, f0, grid_spec: dict, cap=None, variant=0, fle_degree=0, **grid_kw):
     """Render all receivers on the GPU.  Returns (rays complex [n_rx, n_el*n_az], renderer,
     params on device)."""
     rx = np.asarray(rx, np.float32).reshape(-1, 3)
     grid = make_grid(**{**grid_spec, **grid_kw})
     K = scene["means"].shape[0]
-    R = Renderer(K, rx.shape[0], grid, f0, pair_capacity=cap, variant=variant)
+    R = Renderer(K, rx.shape[0], grid, f0, pair_capacity=cap, variant=variant, fle_degree=fle_degree)
     p = to_device(scene)
     rxd = torch.tensor(rx, device="cuda")
     txd = torch.tensor(np.asarray(tx, np.float32), device="cuda")

@@ -49,10 +49,10 @@ def test_struct_layouts_match_header(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\\n", sizeof(gsrf_grid), sizeof(gsrf_gaussians), sizeof(gsrf_plan),
          sizeof(gsrf_layout), sizeof(gsrf_run_status));
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", offsetof(gsrf_plan, f0_hz), offsetof(gsrf_plan, grid),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", offsetof(gsrf_plan, f0_hz), offsetof(gsrf_plan, grid),
          offsetof(gsrf_plan, pair_capacity), offsetof(gsrf_run_status, stats), offsetof(gsrf_layout, view),
          offsetof(gsrf_plan, ray_block_w), offsetof(gsrf_plan, stage), offsetof(gsrf_plan, ckpt_every),
-         offsetof(gsrf_plan, ckpt_slots), offsetof(gsrf_plan, variant));
+         offsetof(gsrf_plan, ckpt_slots), offsetof(gsrf_plan, variant), offsetof(gsrf_plan, fle_degree));
   return 0;
 }
 """)
@@ -66,7 +66,7 @@ int main(void) {
     assert offs == [L.gsrf_plan.f0_hz.offset, L.gsrf_plan.grid.offset, L.gsrf_plan.pair_capacity.offset,
                     L.gsrf_run_status.stats.offset, L.gsrf_layout.view.offset, L.gsrf_plan.ray_block_w.offset,
                     L.gsrf_plan.stage.offset, L.gsrf_plan.ckpt_every.offset, L.gsrf_plan.ckpt_slots.offset,
-                    L.gsrf_plan.variant.offset]
+                    L.gsrf_plan.variant.offset, L.gsrf_plan.fle_degree.offset]
 
 
 def plan(n=1000, n_rx=4, n_az=360, n_el=90, cap=100000, **kw):
@@ -131,7 +131,8 @@ def test_tile_shapes_ray_blocks_and_stages_accepted(lib, tw, th, bw, stage):
 @pytest.mark.parametrize("fields", [dict(ray_block_w=2), dict(ray_block_w=12), dict(ray_block_w=64),
                                     dict(stage=8), dict(stage=24), dict(stage=-1), dict(ckpt_every=48, ckpt_slots=4),
                                     dict(ckpt_every=-32, ckpt_slots=4), dict(ckpt_every=64, ckpt_slots=0),
-                                    dict(ckpt_every=64, ckpt_slots=65), dict(variant=8), dict(variant=-1)])
+                                    dict(ckpt_every=64, ckpt_slots=65), dict(variant=8), dict(variant=-1),
+                                    dict(fle_degree=6), dict(fle_degree=-1)])
 def test_bad_ray_block_stage_or_checkpoints_rejected(lib, fields):
     sz = C.c_size_t()
     p = plan()
@@ -198,6 +199,33 @@ def test_backward_refuses_variant_readings(lib):
     p.variant = L.VARIANT_RADIANCE_AT_MEAN
     sz = C.c_size_t()
     assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_OK  # the forward takes it
+    dev = C.c_void_p(1 << 20)
+    g = L.gsrf_gaussians(1000, dev, dev, dev, dev, dev, None)
+    assert lib.gsrf_render_bwd(C.byref(p), C.byref(g), dev, sz.value, dev, dev, None, None, None, None, None,
+                               None, None) == L.GSRF_ERR_UNSUPPORTED
+
+
+def test_other_fle_degrees_are_forward_and_single_frequency(lib):
+    """Degrees 1..5 size the coefficient and ray tables by L; only L = 3 has the backward,
+    several subcarriers, the batched render and the radiance-at-the-mean variant."""
+    sizes = []
+    for deg in (1, 2, 0, 4, 5):
+        p = plan()
+        p.fle_degree = deg
+        sz = C.c_size_t()
+        assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_OK
+        sizes.append(sz.value)
+    assert sizes == sorted(sizes) and len(set(sizes)) == 5
+    for bad in (dict(n_f=4), dict(variant=L.VARIANT_RADIANCE_AT_MEAN)):
+        p = plan(n_f=bad.get("n_f", 1))
+        p.fle_degree = 5
+        p.variant = bad.get("variant", 0)
+        sz = C.c_size_t()
+        assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_ERR_UNSUPPORTED
+    p = plan()
+    p.fle_degree = 4
+    sz = C.c_size_t()
+    assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_OK
     dev = C.c_void_p(1 << 20)
     g = L.gsrf_gaussians(1000, dev, dev, dev, dev, dev, None)
     assert lib.gsrf_render_bwd(C.byref(p), C.byref(g), dev, sz.value, dev, dev, None, None, None, None, None,
