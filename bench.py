@@ -47,8 +47,8 @@ FLOP_HIT = 172
 # work split; reported only for a split that was measured (profiles/).
 # ncu DRAM bytes (read + write) of one full-size k_render_queue launch, per work split
 # (tile_w, tile_h, ray_block_w, stage); null in the output for a split not measured
-RENDER_TRAFFIC = {(16, 16, 8, 32): 83623168 + 6938368, (32, 16, 8, 32): 78922496 + 6352896,
-                  (32, 32, 8, 32): 83603200 + 6688000}
+RENDER_TRAFFIC = {(16, 16, 8, 32): 83646208 + 7084288, (32, 16, 8, 32): 78890752 + 6373120,
+                  (32, 32, 8, 32): 83668224 + 6735360}
 # library kernels per step: project 4 (status, ray table, shape records, view records),
 # bin 19 (zero, 4 x (hist, scan, scatter), count, scan, emit, tile hist, scan, scatter),
 # render 5 (item keys, counting pass of 3, persistent render), received signal 1

@@ -8,8 +8,8 @@
 // the pairs instead of 8 passes over the pairs.
 //
 // Every pass is a (histogram, scan, scatter) triple over blocks of kChunk items.
-// Ranks inside a block come from __match_any_sync peer groups, so equal digits keep
-// their input order: the sort is stable and its output deterministic.
+// Ranks inside a block come from warp peer groups (one ballot per digit bit), so equal
+// digits keep their input order: the sort is stable and its output deterministic.
 #include "gsrf_internal.cuh"
 
 namespace gsrf {
@@ -187,7 +187,14 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const K* __restrict__ 
             val = vin ? vin[i] : (uint32_t)(i - seg_lo);
             d = digit_of(key, shift, mask);
         }
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        // lanes with the same digit: one ballot per digit bit (every digit is below
+        // nbins), and the same validity
+        uint32_t peers = __ballot_sync(0xffffffffu, valid);
+        if (!valid) peers = ~peers;
+        for (uint32_t bit = 1; bit < (uint32_t)nbins; bit <<= 1) {
+            const uint32_t bb = __ballot_sync(0xffffffffu, (d & bit) != 0);
+            peers &= (d & bit) ? bb : ~bb;
+        }
         const int rank = __popc(peers & lt);
         if (valid && rank == 0) cnt[warp][d] = (uint8_t)__popc(peers);
         __syncthreads();
