@@ -980,7 +980,8 @@ def main():
                     "rays per warp, 32 candidates per stage) instead of autotuning it")
     ap.add_argument("--split", default=None, help="fix the work split instead of tuning it: TWxTH,BW,STAGE "
                     "(e.g. 32x16,8,32), for profiling runs")
-    ap.add_argument("--only", choices=["train", "csi", "million", "variants", "paper_loop", "angular", "fle_degree"], default=None,
+    ap.add_argument("--only", choices=["train", "csi", "million", "variants", "paper_loop", "angular", "fle_degree",
+                                       "uneven"], default=None,
                     help="run one secondary leg alone and print its record (profiling runs)")
     ap.add_argument("--train-gauss", type=int, default=200_000, help="Gaussians of the training leg")
     ap.add_argument("--train-rx", type=int, default=16, help="receivers of the training leg")
@@ -1018,7 +1019,8 @@ def main():
         import torch
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
         leg = {"train": train_leg, "csi": csi_leg, "million": million_leg, "variants": variants_leg,
-               "paper_loop": paper_loop_leg, "angular": angular_leg, "fle_degree": fle_degree_leg}[args.only]
+               "paper_loop": paper_loop_leg, "angular": angular_leg, "fle_degree": fle_degree_leg,
+               "uneven": lambda a, w, f: uneven_leg(a, f)}[args.only]
         rec = leg(args, ws, flush)
         if rank == 0:
             print(json.dumps({"only": args.only, **rec}))
