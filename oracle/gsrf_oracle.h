@@ -64,7 +64,10 @@ typedef struct {
                                   *      representative point (App. A.3), g / ((2 pi)^1.5 |Sigma|^0.5)
                                   *   4  a ray (u, v) meets Gaussian k only inside its splatting
                                   *      circle on the receiving plane (Sec. 4.3, the paper's own
-                                  *      culling: or_circle_f32), on top of the exact test */
+                                  *      culling: or_circle_f32), on top of the exact test
+                                  *   8  the path of each (ray, Gaussian) pair runs through its
+                                  *      representative point: d = |t - x_rep| + |x_rep - r|
+                                  *      (Sec. 4.4's x_rep) instead of through mu_k */
     int32_t fle_degree;          /* Fourier-Legendre degree L of the radiance, 1..5 (0 = 3): the
                                   * scene carries (L + 1)^2 complex coefficients per Gaussian,
                                   * index l*l + l + m (Sec. 4.2); the gradient is L = 3 only */

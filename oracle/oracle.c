@@ -242,7 +242,7 @@ void or_path_phase(const or_scene *s, const float *rx, const float *tx, double f
 typedef struct {
     const or_scene *s;
     const or_grid *g;
-    double rx[3];
+    double rx[3], tx[3];
     double f0, df;
     int32_t n_f, mode;
     /* per Gaussian, FP64 */
@@ -394,9 +394,19 @@ static void render_one(rctx *c, int64_t i)
             gsum += fabs(om * c->b[k]) * ddt + (a < (double)g->alpha_max ? a * 0.5 * delta / (1.0 - a) : 0.0);
             lnta_err += (a < (double)g->alpha_max ? a * 0.5 * delta / (1.0 - a) : 0.0) + 1e-7;
         }
+        double dk = c->dpath[k]; /* Tx -> mu_k -> Rx */
+        if (g->variant & 8) {    /* Tx -> x_rep -> Rx along this ray */
+            double a2 = 0.0, b2 = 0.0;
+            for (int i = 0; i < 3; ++i) {
+                const double xr = c->rx[i] + h[4] * v[i];
+                a2 += (c->tx[i] - xr) * (c->tx[i] - xr);
+                b2 += (xr - c->rx[i]) * (xr - c->rx[i]);
+            }
+            dk = sqrt(a2) + sqrt(b2);
+        }
         for (int f = 0; f < nf; ++f) {
             double fr = c->f0 + (double)f * c->df;
-            double ph = 2.0 * M_PI * fr * c->dpath[k] / OR_C_LIGHT;
+            double ph = 2.0 * M_PI * fr * dk / OR_C_LIGHT;
             double er = cos(ph), ei = -sin(ph);             /* e^{-j phi} */
             double zr = a * (pr * er - pi * ei), zi = a * (pr * ei + pi * er);
             S[2 * f] += zr * T[2 * f] - zi * T[2 * f + 1];
@@ -451,7 +461,10 @@ static int prepare(rctx *c, const or_scene *s, const float *rx, const float *tx,
     c->b = (double *)malloc(sizeof(double) * nn);
     c->psig = (double *)malloc(sizeof(double) * 2 * nn);
     c->circ = (float *)malloc(sizeof(float) * 3 * nn);
-    for (int i = 0; i < 3; ++i) c->rx[i] = rx[i];
+    for (int i = 0; i < 3; ++i) {
+        c->rx[i] = rx[i];
+        c->tx[i] = tx[i];
+    }
     for (int64_t k = 0; k < n; ++k) {
         or_gaussian(s, k, NULL, c->Sinv + 9 * k, c->op + k);
         double dt = 0.0, dr = 0.0;
@@ -524,7 +537,7 @@ static int check_args(const or_scene *s, const or_grid *g, int32_t n_f, int32_t 
     if (g->n_az < 1 || g->n_el < 1 || g->tile_w < 1 || g->tile_h < 1) return -1;
     if ((g->n_az + g->tile_w - 1) / g->tile_w > 64) return -1;
     if (!(g->daz_deg > 0.0f) || !(g->del_deg > 0.0f)) return -1;
-    if (g->variant < 0 || g->variant > 7) return -1;
+    if (g->variant < 0 || g->variant > 15) return -1;
     if (g->fle_degree < 0 || g->fle_degree > OR_L_MAX) return -1;
     return 0;
 }

@@ -914,3 +914,68 @@ def test_other_degrees_forward_only(oracle_lib):
         oracle_lib.render_grad(s, r, r, 2.4e9, small_grid(oracle_lib, fle_degree=5), G)
     out = oracle_lib.render(s, r, r, 2.4e9, small_grid(oracle_lib, fle_degree=5), mode=1)
     assert np.count_nonzero(out["S"]) > 0
+
+
+# --------------------------------------------------------------------------- path through x_rep
+
+def test_path_at_rep_equals_default_through_the_centre(oracle_lib):
+    """Variant 8 on a ray through the centre of a symmetric Gaussian: the chord's midpoint
+    is mu, so the path Tx -> x_rep -> Rx is the default Tx -> mu -> Rx."""
+    r = np.array([0.0, 0.0, 0.0], np.float32)
+    t = np.array([3.0, 4.0, 1.0], np.float32)
+    s = one_gaussian((5.0, 0.0, 0.0), log_s=(math.log(0.4),) * 3, logit=0.5, b=0.2)
+    kw = dict(az0_deg=-0.5, daz_deg=1.0, el0_deg=-0.5, del_deg=1.0, tile_w=1, tile_h=1)
+    out0 = oracle_lib.render(s, r, t, 2.4e9, oracle_lib.make_grid(1, 1, **kw), mode=1)
+    out8 = oracle_lib.render(s, r, t, 2.4e9, oracle_lib.make_grid(1, 1, variant=8, **kw), mode=1)
+    assert out0["S"][0, 0] != 0
+    assert abs(out8["S"][0, 0] - out0["S"][0, 0]) <= 1e-12 * abs(out0["S"][0, 0])
+
+
+def test_path_at_rep_single_gaussian_closed_form(oracle_lib):
+    """One Gaussian, variant 8: S = alpha psi e^{-j 2 pi f d_rep / c}, with the chord found
+    by bisection on the Mahalanobis distance along the ray (independent of the oracle's
+    quadratic), x_rep its midpoint beyond r_rx and d_rep = |t - x_rep| + |x_rep - r|."""
+    from scipy.special import lpmv
+    rng = np.random.default_rng(9)
+    coeffs = rng.normal(0, 0.3, (16, 2))
+    r = np.array([2.0, 2.0, 0.5], np.float32)
+    t = np.array([7.0, 1.0, 2.5], np.float32)
+    s = one_gaussian((4.0, 3.0, 1.0), log_s=(math.log(0.4), math.log(0.2), math.log(0.3)),
+                     quat=(0.9, 0.1, -0.3, 0.2), logit=0.7, coeffs=coeffs, b=0.3)
+    grid = small_grid(oracle_lib, variant=8)
+    f = 2.4e9
+    out = oracle_lib.render(s, r, t, f, grid, mode=1)
+    Sg, Si, o = oracle_lib.gaussian(s, 0)
+    mu = s["means"][0].astype(np.float64)
+    r64, t64 = r.astype(np.float64), t.astype(np.float64)
+    A, E, dirs = ray_dirs(grid)
+    c = s["coeffs"][0, :, 0].astype(np.float64) + 1j * s["coeffs"][0, :, 1]
+
+    def m2(tt, d):
+        e = r64 + tt * d - mu
+        return e @ Si @ e
+
+    n = 0
+    for i in range(len(dirs)):
+        d = dirs[i]
+        tc = (mu - r64) @ Si @ d / (d @ Si @ d)  # closest approach
+        if m2(tc, d) >= 9 - 1e-6 or out["S"][0, i] == 0:
+            continue
+        lo_in, hi_in = tc - 20.0, tc     # entry between: m2 > 9 then < 9
+        lo_out, hi_out = tc, tc + 20.0
+        for _ in range(200):
+            mid = 0.5 * (lo_in + hi_in)
+            (lo_in, hi_in) = (mid, hi_in) if m2(mid, d) > 9 else (lo_in, mid)
+            mid = 0.5 * (lo_out + hi_out)
+            (lo_out, hi_out) = (lo_out, mid) if m2(mid, d) > 9 else (mid, hi_out)
+        t_in, t_out = 0.5 * (lo_in + hi_in), 0.5 * (lo_out + hi_out)
+        t_rep = 0.5 * (max(t_in, 1.0) + t_out)
+        xr = r64 + t_rep * d
+        d_rep = np.linalg.norm(t64 - xr) + np.linalg.norm(xr - r64)
+        x = math.sin(E[i])
+        psi = sum(c[l * l + l + m] * np.exp(1j * m * A[i]) * (-1) ** m * lpmv(m, l, x)
+                  for l in range(4) for m in range(-l, l + 1))
+        ref = min(o * math.exp(-m2(t_rep, d) / 2), 0.99) * psi * np.exp(-2j * np.pi * f * d_rep / 3e8)
+        assert abs(out["S"][0, i] - ref) < 1e-8 * max(1e-3, abs(ref))
+        n += 1
+    assert n > 10
