@@ -111,7 +111,11 @@ typedef struct {
                                 * inside its splatting circle (Sec. 4.3): centre (u_k, v_k) = the
                                 * bin of mu_k's direction, radius 3 sqrt(lambda_max(J Sigma J^T))
                                 * in bins, decided in FP32 with correctly rounded operations; the
-                                * exact test still decides the hit inside it.  0..7 */
+                                * exact test still decides the hit inside it;
+                                * GSRF_VARIANT_PATH_AT_REP gives each (ray, Gaussian) pair the
+                                * path through its representative point, |t - x_rep| +
+                                * |x_rep - r|, instead of through mu (one frequency, L = 3, not
+                                * in the batched render).  0..15 */
     int32_t fle_degree;        /* degree L of the Fourier-Legendre radiance (Sec. 4.2), 1..5;
                                 * 0 = 3, the paper's choice.  The Gaussians then carry (L + 1)^2
                                 * complex coefficients each.  L != 3 is forward-only and
@@ -122,6 +126,7 @@ typedef struct {
 #define GSRF_VARIANT_RADIANCE_AT_MEAN 1
 #define GSRF_VARIANT_NORMALISED_WEIGHT 2
 #define GSRF_VARIANT_PAPER_CULLING 4
+#define GSRF_VARIANT_PATH_AT_REP 8
 
 /* Bytes of workspace a plan needs (256-byte aligned base required). [host] out. */
 gsrf_status gsrf_workspace_size(const gsrf_plan *plan, size_t *bytes);

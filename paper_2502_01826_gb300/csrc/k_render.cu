@@ -65,7 +65,38 @@ struct RenderArgs {
     int ck_slots;
     int variant;  // GSRF_VARIANT_* bits
     const float4* circle;  // the paper's splatting circles [receiver][Gaussian] (that variant only)
+    const float* rxpos;    // receiver and transmitter positions (the path-through-x_rep variant)
+    const float* txpos;
 };
+
+// Path of a composited pair through its representative point (plan variant
+// GSRF_VARIANT_PATH_AT_REP): delta = (|t - x_rep| + |x_rep - r|) - (|t - mu| + |mu - r|)
+// with x_rep = r + t_rep v.  Written without cancellation: e = x_rep - mu is the closest
+// approach's offset from mu, W^-1 (w + t_mid v') = M^T (v' x (w x v')) / A (Lagrange's
+// identity on the whitened quantities of the hit test), plus (t_rep - t_mid) v; then
+// |c + e| - |c| = (2 c.e + e.e) / (|c + e| + |c|) for c = mu - r (|c + e| = t_rep) and for
+// c = mu - t.  FP32 gives delta to about 1e-8 m, far below a wavelength.
+__device__ __forceinline__ float path_delta(const float4& cv, const GShape* sh, const float4& w, const PairGeo& g,
+                                            float dx, float dy, float dz, float tx, float ty, float tz) {
+    const float4* m4 = reinterpret_cast<const float4*>(sh) + 3;
+    const float4 m0 = __ldg(m4), m1 = __ldg(m4 + 1), m2 = __ldg(m4 + 2);
+    const float M[9] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x};
+    const float cx = w.y * g.vz - w.z * g.vy, cy = w.z * g.vx - w.x * g.vz, cz = w.x * g.vy - w.y * g.vx;
+    const float px = (g.vy * cz - g.vz * cy) * g.iA, py = (g.vz * cx - g.vx * cz) * g.iA,
+                pz = (g.vx * cy - g.vy * cx) * g.iA;
+    const float ex = M[0] * px + M[3] * py + M[6] * pz + g.dl * dx;
+    const float ey = M[1] * px + M[4] * py + M[7] * pz + g.dl * dy;
+    const float ez = M[2] * px + M[5] * py + M[8] * pz + g.dl * dz;
+    const float ee = ex * ex + ey * ey + ez * ez;
+    const float D = sqrtf(cv.x * cv.x + cv.y * cv.y + cv.z * cv.z);
+    const float t_rep = g.tm + g.dl;
+    const float dr = (2.0f * (cv.x * ex + cv.y * ey + cv.z * ez) + ee) / (t_rep + D);
+    const float qx = cv.x - tx, qy = cv.y - ty, qz = cv.z - tz;  // mu - t
+    const float Q = sqrtf(qx * qx + qy * qy + qz * qz);
+    const float Qe = sqrtf((qx + ex) * (qx + ex) + (qy + ey) * (qy + ey) + (qz + ez) * (qz + ez));
+    const float dt = (2.0f * (qx * ex + qy * ey + qz * ez) + ee) / (Qe + Q);
+    return dr + dt;
+}
 
 constexpr int kMaxJobs = 96;
 
@@ -149,7 +180,7 @@ __device__ __forceinline__ void load_ray(const float* raytab, size_t ray, float&
 // r = e^{-j (2 pi df d / c + 2 pi df Gamma / c)}, Gamma = sum over earlier pairs of b dt,
 // because T(f0 + s df) = T(f0) e^{-j s 2 pi df Gamma / c} and E(f0 + s df) =
 // E(f0) e^{-j s 2 pi df d / c}; the powers of r come from one sincos and a recurrence.
-template <int NFC, int WB, int L>
+template <int NFC, int WB, int L, bool PATH = false>
 __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int tile, int k,
                                              float4 (*sbuf)[WB][kRec], uint32_t (*sid)[WB], float4* spl) {
     const int lane = threadIdx.x & 31;
@@ -250,7 +281,19 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
                                    pr, pi);
                     }
                     // S += alpha psi E T, E = e^{-j phi} = (er, ei)
-                    const float er = v1.w, ei = rec[1].x;
+                    float er = v1.w, ei = rec[1].x;
+                    if constexpr (PATH) {  // GSRF_VARIANT_PATH_AT_REP: the path through x_rep
+                        const uint32_t id = sid[bf][j];
+                        const float4 cv = __ldg(reinterpret_cast<const float4*>(view + id));
+                        const float dl = path_delta(cv, a.shape + id, v1, pg, dx, dy, dz,
+                                                    a.txpos[0] - a.rxpos[3 * r], a.txpos[1] - a.rxpos[3 * r + 1],
+                                                    a.txpos[2] - a.rxpos[3 * r + 2]);
+                        float sn, cs;
+                        phase_rot(a.om_pi * dl, sn, cs);  // e^{-j 2 pi f0 delta / c}
+                        const float nr = er * cs + ei * sn;
+                        ei = ei * cs - er * sn;
+                        er = nr;
+                    }
                     const float etr = er * Tr - ei * Ti, eti = er * Ti + ei * Tr;
                     if constexpr (NFC == 1) {
                         Sr += alpha * (pr * etr - pi * eti);
@@ -333,10 +376,11 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
 // block, subcarrier chunk) from one counter, in heaviest-first order, until none is
 // left; a warp that finishes early takes the next item instead of idling until the
 // other warps of its CTA are done.
-// One frequency: 7 CTAs per SM up to L = 3 (71 registers), fewer for the larger bases of
-// L = 4 and 5; chunks of subcarriers (L = 3 only): 4.
-template <int NFC, int WB, int L>
-__global__ void __launch_bounds__(kThreads, NFC == 1 ? (L <= 3 ? 7 : (L == 4 ? 6 : 5)) : 4)
+// One frequency: 7 CTAs per SM up to L = 3 (72 registers), fewer for the larger bases of
+// L = 4 and 5; chunks of subcarriers (L = 3 only): 4.  PATH: the path-through-x_rep
+// variant, a separate instance so that its arithmetic costs the others no registers.
+template <int NFC, int WB, int L, bool PATH = false>
+__global__ void __launch_bounds__(kThreads, NFC == 1 ? (PATH ? 6 : (L <= 3 ? 7 : (L == 4 ? 6 : 5))) : 4)
     k_render_queue(RenderArgs a,
                                                                             const uint32_t* __restrict__ order,
                                                                             unsigned long long* __restrict__ counter,
@@ -353,7 +397,7 @@ __global__ void __launch_bounds__(kThreads, NFC == 1 ? (L <= 3 ? 7 : (L == 4 ? 6
         if (it >= total) break;
         const uint32_t id = order[it];
         const unsigned rem = id % per_rx;
-        render_block<NFC, WB, L>(a, (int)(id / per_rx), (int)(rem / (unsigned)a.per_tile),
+        render_block<NFC, WB, L, PATH>(a, (int)(id / per_rx), (int)(rem / (unsigned)a.per_tile),
                                  (int)(rem % (unsigned)a.per_tile), sbuf[warp], sid[warp], spl[warp]);
     }
 }
@@ -474,16 +518,18 @@ static RenderArgs render_args(const gsrf_plan* p, const Layout& L, void* ws, flo
     a.ck_slots = p->ckpt_slots;
     a.variant = p->variant;
     a.circle = (p->variant & GSRF_VARIANT_PAPER_CULLING) ? at<float4>(ws, L.circle) : nullptr;
+    a.rxpos = at<float>(ws, L.rxpos);
+    a.txpos = at<float>(ws, L.txpos);
     return a;
 }
 
-template <int NFC, int WB, int L = 3>
+template <int NFC, int WB, int L = 3, bool PATH = false>
 static cudaError_t launch_queue(const RenderArgs& a, const uint32_t* order, unsigned long long* counter, long long n,
                                 cudaStream_t st) {
     int grid = 0;
-    cudaError_t e = resident_grid(k_render_queue<NFC, WB, L>, n, &grid);
+    cudaError_t e = resident_grid(k_render_queue<NFC, WB, L, PATH>, n, &grid);
     if (e != cudaSuccess) return e;
-    k_render_queue<NFC, WB, L><<<grid, kThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
+    k_render_queue<NFC, WB, L, PATH><<<grid, kThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
     return cudaGetLastError();
 }
 
@@ -511,6 +557,9 @@ cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     if ((e = launch_item_order(L, ws, a.per_tile, &order, &counter, st)) != cudaSuccess) return e;
     const long long n = (long long)L.n_rx * L.n_tiles * a.per_tile;
     const bool wb16 = plan_stage(p) == 16;
+    if (p->variant & GSRF_VARIANT_PATH_AT_REP)  // one frequency, L = 3 (checked with the plan)
+        return wb16 ? launch_queue<1, 16, 3, true>(a, order, counter, n, st)
+                    : launch_queue<1, 32, 3, true>(a, order, counter, n, st);
     if (p->n_f == 1)
         return wb16 ? launch_queue_degree<16>(plan_degree(p), a, order, counter, n, st)
                     : launch_queue_degree<32>(plan_degree(p), a, order, counter, n, st);

@@ -1,7 +1,8 @@
 """Variant readings (forward only): the radiance at the direction of the Gaussian's mean
 instead of each ray's (GSRF_VARIANT_RADIANCE_AT_MEAN), the normalised density weight
-(GSRF_VARIANT_NORMALISED_WEIGHT) and the paper's splatting-circle culling
-(GSRF_VARIANT_PAPER_CULLING), alone and together, held to the same bars against the
+(GSRF_VARIANT_NORMALISED_WEIGHT), the paper's splatting-circle culling
+(GSRF_VARIANT_PAPER_CULLING) and the per-pair path through the representative point
+(GSRF_VARIANT_PATH_AT_REP), alone and together, held to the same bars against the
 oracle rendering the same reading.  The circle is a discrete decision both sides take
 in FP32 with the same operations, so it needs no band of its own."""
 import numpy as np
@@ -24,7 +25,8 @@ def _gpu():
 
 @pytest.mark.parametrize("variant", [L.VARIANT_RADIANCE_AT_MEAN, L.VARIANT_NORMALISED_WEIGHT,
                                      L.VARIANT_RADIANCE_AT_MEAN | L.VARIANT_NORMALISED_WEIGHT,
-                                     L.VARIANT_PAPER_CULLING, L.VARIANT_PAPER_CULLING | L.VARIANT_RADIANCE_AT_MEAN])
+                                     L.VARIANT_PAPER_CULLING, L.VARIANT_PAPER_CULLING | L.VARIANT_RADIANCE_AT_MEAN,
+                                     L.VARIANT_PATH_AT_REP, L.VARIANT_PATH_AT_REP | L.VARIANT_PAPER_CULLING])
 @pytest.mark.parametrize("workload", ["plain", "dense"])
 def test_variant_matches_oracle(variant, workload):
     if workload == "plain":
