@@ -188,8 +188,6 @@ def rank_receivers(cfg: dict, rank: int) -> dict:
 def oracle_sample(cfg, budget_s: float = 12.0, threads: int | None = None):
     """Time the FP64 oracle on a bounded sample of the workload: whole receivers (all
     their rays), as many as fit in about ``budget_s`` seconds.  Returns pairs/s."""
-    import numpy as np
-
     import oracle
     oracle.build()
     th = threads or (os.cpu_count() or 1)
@@ -463,7 +461,7 @@ def persistent_leg(args, cfg, p, rx, tx, R, flush, pairs_per_step):
     import torch
 
     from paper_2502_01826_gb300 import _lib as L
-    from paper_2502_01826_gb300.render import BatchRender, Renderer, make_grid, received_signal
+    from paper_2502_01826_gb300.render import BatchRender, Renderer, received_signal
 
     B = BatchRender([R])
 

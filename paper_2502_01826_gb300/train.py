@@ -27,9 +27,7 @@ import torch
 import torch.nn.functional as F
 
 from . import _lib as L
-from .render import Renderer, make_grid, render, to_device
-
-PARAM_NAMES = ("means", "log_scales", "quats", "opacity_logit", "coeffs", "phase_b")
+from .render import Renderer, make_grid, render
 
 # App. B learning rates: attenuation 0.01, emission (FLE coefficients) 0.0025, scaling
 # 0.01, rotation 0.005; the mean from 1.6e-4 down to 1.6e-6 over 30,000 iterations
