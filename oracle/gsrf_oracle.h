@@ -67,7 +67,11 @@ typedef struct {
                                   *      culling: or_circle_f32), on top of the exact test
                                   *   8  the path of each (ray, Gaussian) pair runs through its
                                   *      representative point: d = |t - x_rep| + |x_rep - r|
-                                  *      (Sec. 4.4's x_rep) instead of through mu_k */
+                                  *      (Sec. 4.4's x_rep) instead of through mu_k
+                                  *  16  a ray composites its hits in ascending t_mid (the
+                                  *      closest approach along the ray, Sec. 4.4's "distance
+                                  *      along the ray path"; ties by list position) instead of
+                                  *      in the list's order of |mu_k - r| (App. E) */
     int32_t fle_degree;          /* Fourier-Legendre degree L of the radiance, 1..5 (0 = 3): the
                                   * scene carries (L + 1)^2 complex coefficients per Gaussian,
                                   * index l*l + l + m (Sec. 4.2); the gradient is L = 3 only */
@@ -87,6 +91,7 @@ typedef struct {
 #define OR_FLAG_M2     1u   /* a tested pair has |m2 - 9| below the m2 band */
 #define OR_FLAG_TOUT   2u   /* a tested pair has |t_out - r_rx| below the t band */
 #define OR_FLAG_TERM   4u   /* prod(1-alpha) came within the termination band of eps_T */
+#define OR_FLAG_ORDER  8u   /* variant 16: two hits' t_mid within the order band */
 
 /* Rounding model of an FP32 evaluation of the same render, used to say where FP32
  * and FP64 may legitimately differ.  The closest approach m2 of pair k carries an

@@ -319,6 +319,21 @@ static int flipped_hit(const double *Sinv, const double *mu, const double *r, co
     return 1;
 }
 
+/* A hit of the variant that orders a ray's hits by t_mid (closest approach). */
+typedef struct {
+    double tm, h[10], delta;
+    int64_t pos;
+    uint32_t k;
+    int flipped;
+} tmid_hit;
+
+static int tmid_cmp(const void *a, const void *b)
+{
+    const tmid_hit *x = (const tmid_hit *)a, *y = (const tmid_hit *)b;
+    if (x->tm != y->tm) return x->tm < y->tm ? -1 : 1;
+    return x->pos < y->pos ? -1 : (x->pos > y->pos);
+}
+
 static void render_one(rctx *c, int64_t i)
 {
     const or_grid *g = c->g;
@@ -340,14 +355,75 @@ static void render_one(rctx *c, int64_t i)
     int32_t nh = 0, nt = 0, namb = 0;
     uint32_t fl = 0;
     const or_bands *bd = c->bands;
-    for (int64_t j = 0; j < len; ++j) {
+    /* variant 16: take every hit decision first, then composite the hits in ascending
+     * t_mid (ties by list position); two hits closer in t_mid than FP32 resolves on the
+     * GPU (4e-6 |t| + 1e-6) are an ambiguous order, swapped in flip mode */
+    const int by_tmid = (g->variant & 16) != 0;
+    tmid_hit *hits = NULL;
+    int64_t n_hits = 0;
+    for (int64_t j = 0; j < (by_tmid ? len : 0); ++j) {
         uint32_t k = list[j];
-        double h[10];
+        tmid_hit hr;
         ++nt;
         if ((g->variant & 4) && !or_circle_in(c->circ + 3 * k, ray_u, ray_v)) continue;
-        int hit = or_intersect(c->Sinv + 9 * k, c->mu + 3 * k, c->rx, v, g->r_rx, h);
-        const double delta = bd ? bd->m2_err * sqrt(h[9]) + bd->m2_abs : 0.0;
-        int flipped = 0;
+        int hit = or_intersect(c->Sinv + 9 * k, c->mu + 3 * k, c->rx, v, g->r_rx, hr.h);
+        hr.delta = bd ? bd->m2_err * sqrt(hr.h[9]) + bd->m2_abs : 0.0;
+        hr.flipped = 0;
+        if (bd) {
+            int in_m2 = fabs(hr.h[5] - 9.0) < bd->m2_mult * hr.delta;
+            int in_t = hr.h[5] < 9.0 && fabs(hr.h[1] - (double)g->r_rx) < bd->t_band;
+            if (in_m2) fl |= OR_FLAG_M2;
+            if (in_t) fl |= OR_FLAG_TOUT;
+            if (in_m2 || in_t) {
+                ++namb;
+                if (bd->flip) {
+                    hit = hit ? 0 : flipped_hit(c->Sinv + 9 * k, c->mu + 3 * k, c->rx, v, (double)g->r_rx, in_m2,
+                                                hr.h);
+                    hr.flipped = 1;
+                }
+            }
+        }
+        if (!hit) continue;
+        if (!hits) hits = (tmid_hit *)malloc(sizeof(tmid_hit) * (size_t)len);
+        hr.tm = hr.flipped ? hr.h[4] : 0.5 * (hr.h[0] + hr.h[1]);
+        hr.pos = j;
+        hr.k = k;
+        hits[n_hits++] = hr;
+    }
+    if (n_hits > 1) {
+        qsort(hits, (size_t)n_hits, sizeof(tmid_hit), tmid_cmp);
+        for (int64_t a = 0; a + 1 < n_hits; ++a) {
+            const double tb = 4e-6 * fmax(fabs(hits[a].tm), 1.0) + 1e-6;
+            if (fabs(hits[a + 1].tm - hits[a].tm) < tb) {
+                fl |= OR_FLAG_ORDER;
+                ++namb;
+                if (bd && bd->flip) {
+                    tmid_hit t = hits[a];
+                    hits[a] = hits[a + 1];
+                    hits[a + 1] = t;
+                    ++a;
+                }
+            }
+        }
+    }
+    for (int64_t j = 0; j < (by_tmid ? n_hits : len); ++j) {
+        uint32_t k;
+        double h[10];
+        double delta;
+        int hit, flipped = 0;
+        if (by_tmid) {
+            k = hits[j].k;
+            memcpy(h, hits[j].h, sizeof h);
+            delta = hits[j].delta;
+            flipped = hits[j].flipped;
+            hit = 1;
+            goto composite;
+        }
+        k = list[j];
+        ++nt;
+        if ((g->variant & 4) && !or_circle_in(c->circ + 3 * k, ray_u, ray_v)) continue;
+        hit = or_intersect(c->Sinv + 9 * k, c->mu + 3 * k, c->rx, v, g->r_rx, h);
+        delta = bd ? bd->m2_err * sqrt(h[9]) + bd->m2_abs : 0.0;
         if (bd) {
             int in_m2 = fabs(h[5] - 9.0) < bd->m2_mult * delta;
             int in_t = h[5] < 9.0 && fabs(h[1] - (double)g->r_rx) < bd->t_band;
@@ -363,6 +439,7 @@ static void render_one(rctx *c, int64_t i)
             }
         }
         if (!hit) continue;
+    composite:;
         double a = c->op[k] * h[7];
         if (a > (double)g->alpha_max) a = (double)g->alpha_max;
         const float *cf = c->s->coeffs + (size_t)k * 2 * nb;
@@ -430,6 +507,7 @@ static void render_one(rctx *c, int64_t i)
             if (stop) break;
         }
     }
+    free(hits);
     fl |= (uint32_t)(namb > 255 ? 255 : namb) << 8;
     for (int f = 0; f < nf; ++f) {
         if (c->S) { c->S[2 * ((size_t)f * c->n_rays + i)] = S[2 * f]; c->S[2 * ((size_t)f * c->n_rays + i) + 1] = S[2 * f + 1]; }
@@ -537,7 +615,7 @@ static int check_args(const or_scene *s, const or_grid *g, int32_t n_f, int32_t 
     if (g->n_az < 1 || g->n_el < 1 || g->tile_w < 1 || g->tile_h < 1) return -1;
     if ((g->n_az + g->tile_w - 1) / g->tile_w > 64) return -1;
     if (!(g->daz_deg > 0.0f) || !(g->del_deg > 0.0f)) return -1;
-    if (g->variant < 0 || g->variant > 15) return -1;
+    if (g->variant < 0 || g->variant > 31) return -1;
     if (g->fle_degree < 0 || g->fle_degree > OR_L_MAX) return -1;
     return 0;
 }

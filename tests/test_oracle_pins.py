@@ -979,3 +979,45 @@ def test_path_at_rep_single_gaussian_closed_form(oracle_lib):
         assert abs(out["S"][0, i] - ref) < 1e-8 * max(1e-3, abs(ref))
         n += 1
     assert n > 10
+
+
+# --------------------------------------------------------------------------- order by t_mid
+
+def test_tmid_order_reverses_a_depth_ordered_pair(oracle_lib):
+    """Variant 16 on one ray (+x) through two Gaussians whose order by |mu - r| (B at 4.10
+    m, A at 4.149 m) is the reverse of their order along the ray (A's closest approach at
+    4.05 m, B's at 4.10 m): the default composites B then A, the variant A then B, each
+    as S_first + T_first S_second from the single-Gaussian renders."""
+    r = np.array([0.0, 0.0, 0.0], np.float32)
+    t = np.array([3.0, 4.0, 1.0], np.float32)
+    cA = np.zeros((16, 2)); cA[0] = (0.7, 0.2)
+    cB = np.zeros((16, 2)); cB[0] = (-0.3, 0.9)
+    A = one_gaussian((4.05, 0.9, 0.0), log_s=(math.log(0.4),) * 3, logit=0.3, coeffs=cA, b=0.4)
+    B = one_gaussian((4.10, 0.0, 0.0), log_s=(math.log(0.3),) * 3, logit=-0.2, coeffs=cB, b=0.2)
+    kw = dict(az0_deg=-0.5, daz_deg=1.0, el0_deg=-0.5, del_deg=1.0, eps_T=0.0, tile_w=1, tile_h=1)
+    g0 = oracle_lib.make_grid(1, 1, **kw)
+    g16 = oracle_lib.make_grid(1, 1, variant=16, **kw)
+    f = 2.4e9
+    oA, oB = oracle_lib.render(A, r, t, f, g0, mode=1), oracle_lib.render(B, r, t, f, g0, mode=1)
+    SA, TA, SB, TB = oA["S"][0, 0], oA["T"][0, 0], oB["S"][0, 0], oB["T"][0, 0]
+    assert SA != 0 and SB != 0
+    both = concat(A, B)
+    S0 = oracle_lib.render(both, r, t, f, g0, mode=1)["S"][0, 0]
+    S16 = oracle_lib.render(both, r, t, f, g16, mode=1)["S"][0, 0]
+    assert abs(S0 - (SB + TB * SA)) <= 1e-12 * abs(S0)
+    assert abs(S16 - (SA + TA * SB)) <= 1e-12 * abs(S16)
+    assert abs(S16 - S0) > 1e-3 * abs(S0)
+
+
+def test_tmid_order_keeps_the_product_of_transmittances(oracle_lib):
+    """Without early termination the hits are the same and only their order changes, so
+    the transmittance after the last hit, a product, is the default's; S is not."""
+    sc = {k: v for k, v in __import__("paper_2502_01826_gb300.synthetic", fromlist=["scene"]).scene(400, 6).items()
+          if not k.startswith("_")}
+    r = np.array([4.0, 3.0, 1.2], np.float32)
+    t = np.array([9.0, 1.0, 2.0], np.float32)
+    o0 = oracle_lib.render(sc, r, t, 2.4e9, oracle_lib.make_grid(72, 18, eps_T=0.0))
+    o16 = oracle_lib.render(sc, r, t, 2.4e9, oracle_lib.make_grid(72, 18, eps_T=0.0, variant=16))
+    assert np.array_equal(o0["nhit"], o16["nhit"])
+    assert np.allclose(o16["T"], o0["T"], rtol=1e-11, atol=1e-14)
+    assert np.abs(o16["S"] - o0["S"]).max() > 1e-3 * np.abs(o0["S"]).max()
