@@ -741,7 +741,7 @@ def variants_leg(args, ws, flush, split=None):
     """The BLE workload rendered under each reading of the radiance direction, the
     Gaussian weight, the culling and the path (bits: 1 = radiance at the direction of the
     mean, 2 = normalised density, 4 = the paper's splatting circle, 8 = the path through
-    the representative point), with the main run's work
+    the representative point, 16 = each ray's hits in t_mid order), with the main run's work
     split: forward step time (project + bin + render + RSSI) and how far each reading moves
     the per-ray signal and the RSSI from the default reading (per-ray radiance,
     unnormalised weight, exact culling).  CUDA events, L2 flushed between steps."""
@@ -760,7 +760,7 @@ def variants_leg(args, ws, flush, split=None):
     rx = torch.tensor(cfg["rx"], device="cuda")
     tx = torch.tensor(cfg["tx"], device="cuda")
     res, ref = {}, None
-    for v in (0, 1, 2, 3, 4, 8):
+    for v in (0, 1, 2, 3, 4, 8, 16):
         R = Renderer(K, n_rx, grid, cfg["f0"], ray_block_w=bw, stage=stg, variant=v)
         R.ensure_capacity(p, rx, tx)
         out = torch.empty(R.out_shape(), dtype=torch.float32, device="cuda")
@@ -790,7 +790,8 @@ def variants_leg(args, ws, flush, split=None):
     return {"workload": cfg["name"], "split": "%dx%d,%d,%d" % (tw, th, bw, stg), **res,
             "what": "variant bits: 1 = radiance at the direction of the Gaussian's mean, 2 = weight "
                     "normalised by (2 pi)^1.5 s0 s1 s2, 4 = the paper's splatting-circle culling, 8 = the "
-                    "path of each pair through its representative point; forward only"}
+                    "path of each pair through its representative point, 16 = each ray's hits in t_mid "
+                    "order; forward only"}
 
 
 def paper_loop_leg(args, ws, flush):

@@ -115,7 +115,12 @@ typedef struct {
                                 * GSRF_VARIANT_PATH_AT_REP gives each (ray, Gaussian) pair the
                                 * path through its representative point, |t - x_rep| +
                                 * |x_rep - r|, instead of through mu (one frequency, L = 3, not
-                                * in the batched render).  0..15 */
+                                * in the batched render); GSRF_VARIANT_ORDER_T_MID composites a
+                                * ray's hits in ascending t_mid (closest approach along the ray,
+                                * ties by list position) instead of in the list's |mu - r|
+                                * order: one frequency, L = 3, without bit 8, not batched; a ray
+                                * keeps its 512 nearest hits and must terminate on them (else
+                                * GSRF_ERR_UNSUPPORTED in the status word).  0..31 */
     int32_t fle_degree;        /* degree L of the Fourier-Legendre radiance (Sec. 4.2), 1..5;
                                 * 0 = 3, the paper's choice.  The Gaussians then carry (L + 1)^2
                                 * complex coefficients each.  L != 3 is forward-only and
@@ -127,6 +132,7 @@ typedef struct {
 #define GSRF_VARIANT_NORMALISED_WEIGHT 2
 #define GSRF_VARIANT_PAPER_CULLING 4
 #define GSRF_VARIANT_PATH_AT_REP 8
+#define GSRF_VARIANT_ORDER_T_MID 16
 
 /* Bytes of workspace a plan needs (256-byte aligned base required). [host] out. */
 gsrf_status gsrf_workspace_size(const gsrf_plan *plan, size_t *bytes);

@@ -354,6 +354,7 @@ static void render_one(rctx *c, int64_t i)
     double Ta = 1.0, sabs = 0.0, scond = 0.0, gsum = 0.0, lnta_err = 0.0;
     int32_t nh = 0, nt = 0, namb = 0;
     uint32_t fl = 0;
+    double t_stop = INFINITY;  /* variant 16: t_mid of the terminating hit */
     const or_bands *bd = c->bands;
     /* variant 16: take every hit decision first, then composite the hits in ascending
      * t_mid (ties by list position); two hits closer in t_mid than FP32 resolves on the
@@ -361,6 +362,11 @@ static void render_one(rctx *c, int64_t i)
     const int by_tmid = (g->variant & 16) != 0;
     tmid_hit *hits = NULL;
     int64_t n_hits = 0;
+    /* variant 16 takes every decision before compositing, but like the default's walk only
+     * the ones at or before the termination point (along t_mid) can change the ray: their
+     * t_mid is kept here and counted once that point is known */
+    double *amb_tm = NULL;
+    int64_t n_amb = 0;
     for (int64_t j = 0; j < (by_tmid ? len : 0); ++j) {
         uint32_t k = list[j];
         tmid_hit hr;
@@ -375,7 +381,8 @@ static void render_one(rctx *c, int64_t i)
             if (in_m2) fl |= OR_FLAG_M2;
             if (in_t) fl |= OR_FLAG_TOUT;
             if (in_m2 || in_t) {
-                ++namb;
+                if (!amb_tm) amb_tm = (double *)malloc(sizeof(double) * (size_t)(2 * len + 1));
+                amb_tm[n_amb++] = 0.5 * (hr.h[0] + hr.h[1]);
                 if (bd->flip) {
                     hit = hit ? 0 : flipped_hit(c->Sinv + 9 * k, c->mu + 3 * k, c->rx, v, (double)g->r_rx, in_m2,
                                                 hr.h);
@@ -396,7 +403,8 @@ static void render_one(rctx *c, int64_t i)
             const double tb = 4e-6 * fmax(fabs(hits[a].tm), 1.0) + 1e-6;
             if (fabs(hits[a + 1].tm - hits[a].tm) < tb) {
                 fl |= OR_FLAG_ORDER;
-                ++namb;
+                if (!amb_tm) amb_tm = (double *)malloc(sizeof(double) * (size_t)(2 * len + 1));
+                amb_tm[n_amb++] = fmin(hits[a].tm, hits[a + 1].tm);
                 if (bd && bd->flip) {
                     tmid_hit t = hits[a];
                     hits[a] = hits[a + 1];
@@ -504,8 +512,16 @@ static void render_one(rctx *c, int64_t i)
                 ++namb;
                 if (bd->flip) stop = !stop;
             }
-            if (stop) break;
+            if (stop) {
+                if (by_tmid) t_stop = hits[j].tm;
+                break;
+            }
         }
+    }
+    if (by_tmid) {
+        const double tb = 4e-6 * fmax(fabs(t_stop), 1.0) + 1e-6;
+        for (int64_t a = 0; a < n_amb; ++a) namb += amb_tm[a] <= t_stop + tb;
+        free(amb_tm);
     }
     free(hits);
     fl |= (uint32_t)(namb > 255 ? 255 : namb) << 8;

@@ -18,6 +18,7 @@ STATUS_NAMES = {0: "GSRF_OK", 1: "GSRF_ERR_INVALID_ARG", 2: "GSRF_ERR_CUDA", 3: 
                 7: "GSRF_ERR_TOO_LARGE"}
 SIG_COMPLEX_SUM, SIG_RSSI_DB, SIG_POWER_SUM, SIG_SPECTRUM_MAG = 0, 1, 2, 3
 VARIANT_RADIANCE_AT_MEAN, VARIANT_NORMALISED_WEIGHT, VARIANT_PAPER_CULLING, VARIANT_PATH_AT_REP = 1, 2, 4, 8
+VARIANT_ORDER_T_MID = 16
 
 # every exported symbol of include/gsrf.h
 EXPORTS = ["gsrf_workspace_size", "gsrf_workspace_layout", "gsrf_ray_state_bytes", "gsrf_project",

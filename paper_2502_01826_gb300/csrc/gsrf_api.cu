@@ -62,6 +62,8 @@ bool make_layout(const gsrf_plan* p, Layout* L) {
     L->qcounter = take(8);
     // the paper's splatting circles, per (receiver, Gaussian), only for that variant
     L->circle = take((p->variant & GSRF_VARIANT_PAPER_CULLING) ? nr * n * sizeof(float4) : 0);
+    // the t_mid-order variant's per-ray hit keys
+    L->tbuf = take((p->variant & GSRF_VARIANT_ORDER_T_MID) ? nr * (size_t)g.n_az * g.n_el * kOrderCap * 8 : 0);
     L->total = off;
     return true;
 }
@@ -99,7 +101,10 @@ static gsrf_status check_plan(const gsrf_plan* p) {
     if (!(p->stage == 0 || p->stage == 16 || p->stage == 32)) return GSRF_ERR_INVALID_ARG;
     if (p->ckpt_every < 0 || p->ckpt_every % 32 != 0 || p->ckpt_every > (1 << 24)) return GSRF_ERR_INVALID_ARG;
     if (p->ckpt_every > 0 && (p->ckpt_slots < 1 || p->ckpt_slots > 64)) return GSRF_ERR_INVALID_ARG;
-    if (p->variant < 0 || p->variant > 15) return GSRF_ERR_INVALID_ARG;
+    if (p->variant < 0 || p->variant > 31) return GSRF_ERR_INVALID_ARG;
+    if ((p->variant & GSRF_VARIANT_ORDER_T_MID) &&
+        (p->n_f > 1 || plan_degree(p) != 3 || (p->variant & GSRF_VARIANT_PATH_AT_REP)))
+        return GSRF_ERR_UNSUPPORTED;  // its kernel instance: one frequency, L = 3
     if ((p->variant & GSRF_VARIANT_PATH_AT_REP) && (p->n_f > 1 || plan_degree(p) != 3))
         return GSRF_ERR_UNSUPPORTED;  // its kernel instance: one frequency, L = 3
     if (p->fle_degree < 0 || p->fle_degree > 5) return GSRF_ERR_INVALID_ARG;
@@ -241,7 +246,8 @@ gsrf_status gsrf_render_batch(int32_t n_jobs, const gsrf_plan* plans, void* cons
         Layout L;
         if ((s = check_ws(&plans[j], workspaces[j], ws_bytes[j], &L)) != GSRF_OK) return s;
         if (!outs[j] || ((uintptr_t)outs[j] & 7) != 0) return GSRF_ERR_INVALID_ARG;
-        if (plan_degree(&plans[j]) != 3 || (plans[j].variant & GSRF_VARIANT_PATH_AT_REP)) return GSRF_ERR_UNSUPPORTED;
+        if (plan_degree(&plans[j]) != 3 || (plans[j].variant & (GSRF_VARIANT_PATH_AT_REP | GSRF_VARIANT_ORDER_T_MID)))
+            return GSRF_ERR_UNSUPPORTED;
     }
     return cuda_status(launch_render_batch(n_jobs, plans, workspaces, outs, batch_ws, (cudaStream_t)stream));
 }

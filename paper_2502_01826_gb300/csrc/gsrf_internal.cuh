@@ -103,7 +103,7 @@ struct Layout {
     // byte offsets
     size_t status, rxpos, txpos, gacc, raytab, fle, gshape, dpath, view, cover, dkey, dkey2, dval, dval2, dhist, dchunk_sum,
         rx_base, rx_total, pchunk_base, pkeys, pkeys2, pids, pids2, tile_start, thist, qkeys, qkeys2, qorder, qhist,
-        qcounter, circle, total;
+        qcounter, circle, tbuf, total;
     int32_t ntu, ntv, n_tiles;
     int32_t n_rx;
     int64_t n;
@@ -374,6 +374,7 @@ __device__ __forceinline__ bool bundle_meets(const Bundle& b, float4 c) {
 // dense scene.  An ellipsoid that lies wholly outside one half-space meets no ray of
 // the warp beyond r_rx.  Every lane computes the same planes; lane j < kPlanes writes
 // plane j to the warp's shared slots.
+constexpr int kOrderCap = 512;  // hits per ray kept by the t_mid-order variant
 constexpr int kPlanes = 5;
 constexpr int kPlaneSlots = kPlanes + 1;  // + the warp bundle's cos / sin (bundle_at)
 

@@ -67,6 +67,7 @@ struct RenderArgs {
     const float4* circle;  // the paper's splatting circles [receiver][Gaussian] (that variant only)
     const float* rxpos;    // receiver and transmitter positions (the path-through-x_rep variant)
     const float* txpos;
+    unsigned long long* tbuf;  // per-ray hit keys of the t_mid-order variant [ray][kOrderCap]
 };
 
 // Path of a composited pair through its representative point (plan variant
@@ -180,7 +181,7 @@ __device__ __forceinline__ void load_ray(const float* raytab, size_t ray, float&
 // r = e^{-j (2 pi df d / c + 2 pi df Gamma / c)}, Gamma = sum over earlier pairs of b dt,
 // because T(f0 + s df) = T(f0) e^{-j s 2 pi df Gamma / c} and E(f0 + s df) =
 // E(f0) e^{-j s 2 pi df d / c}; the powers of r come from one sincos and a recurrence.
-template <int NFC, int WB, int L, bool PATH = false>
+template <int NFC, int WB, int L, bool PATH = false, bool ORDER = false>
 __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int tile, int k,
                                              float4 (*sbuf)[WB][kRec], uint32_t (*sid)[WB], float4* spl) {
     const int lane = threadIdx.x & 31;
@@ -218,6 +219,12 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
     int last = -1;
     bool done = !valid;
     unsigned hits = 0;
+    // the t_mid-order variant: this ray's sorted hit keys (in the workspace) and their count
+    int nord = 0;
+    bool overflow = false;
+    unsigned long long* tb = nullptr;
+    if constexpr (ORDER)
+        tb = a.tbuf + ((size_t)r * gr.n_el * gr.n_az + (size_t)(valid ? v : 0) * gr.n_az + (valid ? u : 0)) * kOrderCap;
 
     // Stage the batch starting at list position p0 into buffer bf: lane i < WB takes
     // candidate p0 + i, tests it against the warp's cone and half-spaces and, if it may
@@ -248,7 +255,7 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
         int bf = 0;
         uint32_t mask = stage(0, 0);
         for (int p0 = 0; p0 < len; p0 += WB, bf ^= 1) {
-            if (a.ck && chunk == 0) {
+            if (!ORDER && a.ck && chunk == 0) {
                 // transmittance in front of list position K, 2K, ... (a batch start)
                 const int p = p0;
                 if (p > 0 && p % a.ck_every == 0 && p / a.ck_every <= a.ck_slots && valid) {
@@ -270,6 +277,28 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
                     const float4 v1 = rec[0], s2 = rec[4];
                     PairGeo pg;
                     if (!pair_hits(v1, rec[2], rec[3], s2, dx, dy, dz, r_rx, pg)) continue;
+                    if constexpr (ORDER) {
+                        // GSRF_VARIANT_ORDER_T_MID, first pass: keep the kOrderCap smallest
+                        // (t_mid, list position) keys, sorted by insertion (the list's |mu - r|
+                        // order is close to t_mid order, so few keys move); a full buffer
+                        // drops its largest key
+                        uint32_t ku = __float_as_uint(pg.tm);
+                        ku = (ku & 0x80000000u) ? ~ku : (ku | 0x80000000u);
+                        const unsigned long long key = ((unsigned long long)ku << 32) | (uint32_t)(p0 + j);
+                        if (nord == kOrderCap) {
+                            overflow = true;
+                            if (key > tb[kOrderCap - 1]) continue;
+                            --nord;
+                        }
+                        int q = nord;
+                        while (q > 0 && tb[q - 1] > key) {
+                            tb[q] = tb[q - 1];
+                            --q;
+                        }
+                        tb[q] = key;
+                        ++nord;
+                        continue;
+                    }
                     float gw;
                     const float alpha = pair_alpha(s2.y, pg.m2r, amax, gw);
                     float pr, pi;
@@ -338,6 +367,47 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
         }
         cp_async_wait_all();
     }
+    if constexpr (ORDER) {
+        // second pass: the kept hits in ascending t_mid, each re-tested (the same FP32
+        // decision) and composited, until prod(1 - alpha) < eps_T; a ray that dropped hits
+        // and did not terminate on the kept ones needed more than kOrderCap
+        bool ended = false;
+        for (int q = 0; q < nord; ++q) {
+            const uint32_t pos = (uint32_t)tb[q];
+            const uint32_t id = ids[pos];
+            const float4* vw = reinterpret_cast<const float4*>(view + id);
+            const float4* sh = reinterpret_cast<const float4*>(a.shape + id);
+            const float4 v1 = __ldg(vw + 1), r1 = __ldg(vw + 2), s2 = __ldg(sh + 2);
+            PairGeo pg;
+            if (!pair_hits(v1, __ldg(sh), __ldg(sh + 1), s2, dx, dy, dz, r_rx, pg)) continue;
+            float gw;
+            const float alpha = pair_alpha(s2.y, pg.m2r, amax, gw);
+            float pr, pi;
+            if (a.variant & GSRF_VARIANT_RADIANCE_AT_MEAN) {
+                pr = r1.z;
+                pi = r1.w;
+            } else {
+                fle_psi<L>(reinterpret_cast<const float4*>(a.fle + (size_t)id * fle_floats(L)), P, Y, pr, pi);
+            }
+            const float er = v1.w, ei = r1.x;
+            const float etr = er * Tr - ei * Ti, eti = er * Ti + ei * Tr;
+            Sr += alpha * (pr * etr - pi * eti);
+            Si += alpha * (pr * eti + pi * etr);
+            float sn, cs;
+            phase_rot(a.om_pi * s2.z * pg.dt, sn, cs);
+            const float om = 1.0f - alpha;
+            const float nTr = om * (Tr * cs + Ti * sn);
+            Ti = om * (Ti * cs - Tr * sn);
+            Tr = nTr;
+            Ta *= om;
+            ++hits;
+            if (Ta < eps_T) {
+                ended = true;
+                break;
+            }
+        }
+        if (overflow && !ended) atomicCAS(&a.st->code, (int)GSRF_OK, (int)GSRF_ERR_UNSUPPORTED);
+    }
 
     if (valid) {
         const size_t plane = (size_t)gr.n_el * gr.n_az, pix = (size_t)v * gr.n_az + u;
@@ -350,7 +420,7 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
             for (int q = 0; q < NFC; ++q)
                 if (s0 + q < a.n_f) o2[(size_t)q * plane] = make_float2(Sf[2 * q], Sf[2 * q + 1]);
         }
-        if (a.rs && chunk == 0) {
+        if (!ORDER && a.rs && chunk == 0) {
             // RayState {last, Ta, Tr, Ti | Gam, pad[3]} as two 16-byte stores
             float4* rs4 = reinterpret_cast<float4*>(a.rs + ray);
             rs4[0] = make_float4(__int_as_float(last), Ta, Tr, Ti);
@@ -359,7 +429,8 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
     }
     // statistics: list positions tested and composited pairs, one atomic per warp
     // list positions this ray tested: up to its terminating pair, else the whole list
-    unsigned long long t64 = !valid ? 0ull : (done ? (unsigned long long)(last + 1) : (unsigned long long)len),
+    unsigned long long t64 = !valid ? 0ull
+                             : ((done && !ORDER) ? (unsigned long long)(last + 1) : (unsigned long long)len),
                        h64 = hits;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -379,8 +450,8 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
 // One frequency: 7 CTAs per SM up to L = 3 (72 registers), fewer for the larger bases of
 // L = 4 and 5; chunks of subcarriers (L = 3 only): 4.  PATH: the path-through-x_rep
 // variant, a separate instance so that its arithmetic costs the others no registers.
-template <int NFC, int WB, int L, bool PATH = false>
-__global__ void __launch_bounds__(kThreads, NFC == 1 ? (PATH ? 6 : (L <= 3 ? 7 : (L == 4 ? 6 : 5))) : 4)
+template <int NFC, int WB, int L, bool PATH = false, bool ORDER = false>
+__global__ void __launch_bounds__(kThreads, NFC == 1 ? ((PATH || ORDER) ? 6 : (L <= 3 ? 7 : (L == 4 ? 6 : 5))) : 4)
     k_render_queue(RenderArgs a,
                                                                             const uint32_t* __restrict__ order,
                                                                             unsigned long long* __restrict__ counter,
@@ -397,7 +468,7 @@ __global__ void __launch_bounds__(kThreads, NFC == 1 ? (PATH ? 6 : (L <= 3 ? 7 :
         if (it >= total) break;
         const uint32_t id = order[it];
         const unsigned rem = id % per_rx;
-        render_block<NFC, WB, L, PATH>(a, (int)(id / per_rx), (int)(rem / (unsigned)a.per_tile),
+        render_block<NFC, WB, L, PATH, ORDER>(a, (int)(id / per_rx), (int)(rem / (unsigned)a.per_tile),
                                  (int)(rem % (unsigned)a.per_tile), sbuf[warp], sid[warp], spl[warp]);
     }
 }
@@ -520,16 +591,17 @@ static RenderArgs render_args(const gsrf_plan* p, const Layout& L, void* ws, flo
     a.circle = (p->variant & GSRF_VARIANT_PAPER_CULLING) ? at<float4>(ws, L.circle) : nullptr;
     a.rxpos = at<float>(ws, L.rxpos);
     a.txpos = at<float>(ws, L.txpos);
+    a.tbuf = (p->variant & GSRF_VARIANT_ORDER_T_MID) ? at<unsigned long long>(ws, L.tbuf) : nullptr;
     return a;
 }
 
-template <int NFC, int WB, int L = 3, bool PATH = false>
+template <int NFC, int WB, int L = 3, bool PATH = false, bool ORDER = false>
 static cudaError_t launch_queue(const RenderArgs& a, const uint32_t* order, unsigned long long* counter, long long n,
                                 cudaStream_t st) {
     int grid = 0;
-    cudaError_t e = resident_grid(k_render_queue<NFC, WB, L, PATH>, n, &grid);
+    cudaError_t e = resident_grid(k_render_queue<NFC, WB, L, PATH, ORDER>, n, &grid);
     if (e != cudaSuccess) return e;
-    k_render_queue<NFC, WB, L, PATH><<<grid, kThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
+    k_render_queue<NFC, WB, L, PATH, ORDER><<<grid, kThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
     return cudaGetLastError();
 }
 
@@ -557,6 +629,9 @@ cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     if ((e = launch_item_order(L, ws, a.per_tile, &order, &counter, st)) != cudaSuccess) return e;
     const long long n = (long long)L.n_rx * L.n_tiles * a.per_tile;
     const bool wb16 = plan_stage(p) == 16;
+    if (p->variant & GSRF_VARIANT_ORDER_T_MID)  // one frequency, L = 3 (checked with the plan)
+        return wb16 ? launch_queue<1, 16, 3, false, true>(a, order, counter, n, st)
+                    : launch_queue<1, 32, 3, false, true>(a, order, counter, n, st);
     if (p->variant & GSRF_VARIANT_PATH_AT_REP)  // one frequency, L = 3 (checked with the plan)
         return wb16 ? launch_queue<1, 16, 3, true>(a, order, counter, n, st)
                     : launch_queue<1, 32, 3, true>(a, order, counter, n, st);

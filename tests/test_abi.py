@@ -131,7 +131,7 @@ def test_tile_shapes_ray_blocks_and_stages_accepted(lib, tw, th, bw, stage):
 @pytest.mark.parametrize("fields", [dict(ray_block_w=2), dict(ray_block_w=12), dict(ray_block_w=64),
                                     dict(stage=8), dict(stage=24), dict(stage=-1), dict(ckpt_every=48, ckpt_slots=4),
                                     dict(ckpt_every=-32, ckpt_slots=4), dict(ckpt_every=64, ckpt_slots=0),
-                                    dict(ckpt_every=64, ckpt_slots=65), dict(variant=16), dict(variant=-1),
+                                    dict(ckpt_every=64, ckpt_slots=65), dict(variant=32), dict(variant=-1),
                                     dict(fle_degree=6), dict(fle_degree=-1)])
 def test_bad_ray_block_stage_or_checkpoints_rejected(lib, fields):
     sz = C.c_size_t()
@@ -239,3 +239,18 @@ def test_path_variant_is_single_frequency_degree_three(lib):
         p.fle_degree = kw.get("fle_degree", 0)
         sz = C.c_size_t()
         assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_ERR_UNSUPPORTED, kw
+
+
+def test_tmid_order_variant_limits(lib):
+    for kw in (dict(n_f=4), dict(fle_degree=2), dict(extra=L.VARIANT_PATH_AT_REP)):
+        p = plan(n_f=kw.get("n_f", 1))
+        p.variant = L.VARIANT_ORDER_T_MID | kw.get("extra", 0)
+        p.fle_degree = kw.get("fle_degree", 0)
+        sz = C.c_size_t()
+        assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_ERR_UNSUPPORTED, kw
+    a, b = C.c_size_t(), C.c_size_t()
+    p = plan()
+    assert lib.gsrf_workspace_size(C.byref(p), C.byref(a)) == L.GSRF_OK
+    p.variant = L.VARIANT_ORDER_T_MID
+    assert lib.gsrf_workspace_size(C.byref(p), C.byref(b)) == L.GSRF_OK
+    assert b.value >= a.value + 4 * 360 * 90 * 512 * 8  # the per-ray hit keys

@@ -1,8 +1,9 @@
 """Variant readings (forward only): the radiance at the direction of the Gaussian's mean
 instead of each ray's (GSRF_VARIANT_RADIANCE_AT_MEAN), the normalised density weight
 (GSRF_VARIANT_NORMALISED_WEIGHT), the paper's splatting-circle culling
-(GSRF_VARIANT_PAPER_CULLING) and the per-pair path through the representative point
-(GSRF_VARIANT_PATH_AT_REP), alone and together, held to the same bars against the
+(GSRF_VARIANT_PAPER_CULLING), the per-pair path through the representative point
+(GSRF_VARIANT_PATH_AT_REP) and each ray's hits in t_mid order (GSRF_VARIANT_ORDER_T_MID),
+alone and together, held to the same bars against the
 oracle rendering the same reading.  The circle is a discrete decision both sides take
 in FP32 with the same operations, so it needs no band of its own."""
 import numpy as np
@@ -26,7 +27,8 @@ def _gpu():
 @pytest.mark.parametrize("variant", [L.VARIANT_RADIANCE_AT_MEAN, L.VARIANT_NORMALISED_WEIGHT,
                                      L.VARIANT_RADIANCE_AT_MEAN | L.VARIANT_NORMALISED_WEIGHT,
                                      L.VARIANT_PAPER_CULLING, L.VARIANT_PAPER_CULLING | L.VARIANT_RADIANCE_AT_MEAN,
-                                     L.VARIANT_PATH_AT_REP, L.VARIANT_PATH_AT_REP | L.VARIANT_PAPER_CULLING])
+                                     L.VARIANT_PATH_AT_REP, L.VARIANT_PATH_AT_REP | L.VARIANT_PAPER_CULLING,
+                                     L.VARIANT_ORDER_T_MID, L.VARIANT_ORDER_T_MID | L.VARIANT_PAPER_CULLING])
 @pytest.mark.parametrize("workload", ["plain", "dense"])
 def test_variant_matches_oracle(variant, workload):
     if workload == "plain":
@@ -59,3 +61,18 @@ def test_paper_culling_full_size_sampled():
         rays = np.sort(rng.choice(g.n_az * g.n_el, 300, replace=False)).astype(np.int32)
         ref = oracle_pair(cfg["scene"], cfg["rx"][r], cfg["tx"], cfg["f0"], g, rays=rays)
         compare(S[r][rays], ref)
+
+
+def test_tmid_order_full_size_sampled():
+    """Hits in t_mid order on the BLE workload's geometry (50,000 Gaussians, 360 x 90, four
+    receivers): dense rays keep their 512 nearest hits and terminate on them; 300 sampled
+    rays of two receivers against the oracle."""
+    cfg = synthetic.config_ble()
+    rx = cfg["rx"][:4]
+    S, R, _, _ = gpu_render(cfg["scene"], rx, cfg["tx"], cfg["f0"], cfg["grid"], variant=L.VARIANT_ORDER_T_MID)
+    assert R.status().code == 0
+    g = oracle.make_grid(**cfg["grid"], variant=L.VARIANT_ORDER_T_MID)
+    rng = np.random.default_rng(37)
+    for r in (0, 3):
+        rays = np.sort(rng.choice(g.n_az * g.n_el, 300, replace=False)).astype(np.int32)
+        compare(S[r][rays], oracle_pair(cfg["scene"], rx[r], cfg["tx"], cfg["f0"], g, rays=rays))
