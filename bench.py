@@ -995,8 +995,10 @@ def main():
         from paper_2502_01826_gb300 import synthetic
         cfg = synthetic.config_ble()
         vals = []
+        # each step a bounded sample: about two minutes for the whole run, whatever K and W
+        per_step = max(0.5, min(args.cpu_budget / 4, 120.0 / (args.warmup + args.steps)))
         for i in range(args.warmup + args.steps):
-            cb, dt = oracle_sample(cfg, budget_s=max(1.0, args.cpu_budget / 4))
+            cb, dt = oracle_sample(cfg, budget_s=per_step)
             if i >= args.warmup:
                 vals.append((cb, dt))
         v = statistics.median([c["value"] for c, _ in vals])
