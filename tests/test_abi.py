@@ -254,3 +254,31 @@ def test_tmid_order_variant_limits(lib):
     p.variant = L.VARIANT_ORDER_T_MID
     assert lib.gsrf_workspace_size(C.byref(p), C.byref(b)) == L.GSRF_OK
     assert b.value >= a.value + 4 * 360 * 90 * 512 * 8  # the per-ray hit keys
+
+
+def test_batch_and_tuned_backward_refuse_the_forward_only_readings(lib):
+    """The batched render takes only the default degree and no per-pair path or t_mid
+    order; the tuner times no backward for a variant or another degree.  Both refuse
+    before touching the (fake, aligned) device pointers."""
+    dev = C.c_void_p(1 << 20)
+    for field, value in (("fle_degree", 2), ("variant", L.VARIANT_PATH_AT_REP), ("variant", L.VARIANT_ORDER_T_MID)):
+        p = plan()
+        setattr(p, field, value)
+        sz, bsz = C.c_size_t(), C.c_size_t()
+        assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_OK
+        plans = (L.gsrf_plan * 1)(p)
+        assert lib.gsrf_batch_workspace_size(1, plans, C.byref(bsz)) == L.GSRF_OK
+        wss = (C.c_void_p * 1)(dev)
+        sizes = (C.c_size_t * 1)(sz.value)
+        outs = (C.c_void_p * 1)(dev)
+        assert lib.gsrf_render_batch(1, plans, wss, sizes, outs, dev, bsz.value, None) == L.GSRF_ERR_UNSUPPORTED
+    p = plan()
+    p.variant = L.VARIANT_RADIANCE_AT_MEAN
+    tsz = C.c_size_t()
+    assert lib.gsrf_autotune_workspace_size(C.byref(p), C.byref(tsz)) == L.GSRF_OK
+    g = L.gsrf_gaussians(1000, dev, dev, dev, dev, dev, None)
+    bwd = L.gsrf_tune_backward(dev, dev, dev, dev, dev, dev, dev, None)
+    best = L.gsrf_tune_result()
+    n = C.c_int32()
+    assert lib.gsrf_autotune(C.byref(p), C.byref(g), dev, dev, dev, tsz.value, dev, C.byref(bwd), 3, None, 0,
+                             C.byref(n), C.byref(best), None) == L.GSRF_ERR_UNSUPPORTED
