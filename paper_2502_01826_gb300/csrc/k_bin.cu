@@ -9,7 +9,8 @@
 //
 // Every pass is a (histogram, scan, scatter) triple over blocks of kChunk items.
 // Ranks inside a block come from warp peer groups (one ballot per digit bit), so equal
-// digits keep their input order: the sort is stable and its output deterministic.
+// digits keep their input order: the sort is stable and its output deterministic.  Passes
+// with at most 256 bins scatter four keys per thread per round (k_scatter4).
 #include "gsrf_internal.cuh"
 
 namespace gsrf {
@@ -218,6 +219,105 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const K* __restrict__ 
     }
 }
 
+// Stable scatter for at most 256 bins, four keys per thread per round: key s of thread t
+// is item r0 + 256 s + t, so the (sub-round, warp, lane) order of a round of 1024 keys is
+// the input order.  Ranks inside a warp come from ballots; a per-digit exclusive prefix
+// over the 32 (sub-round, warp) slots, in that order, places each warp's group.  Four
+// block barriers per 1024 keys, against three per 256 in k_scatter.
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) k_scatter4(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                           K* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                           Segs S, int shift, uint32_t mask, int nbins,
+                                                           const uint32_t* __restrict__ H, const DevStatus* st) {
+    if (capacity_failed(st)) return;
+    constexpr int R = 4;
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t tot[256];
+    __shared__ uint16_t cnt[R][kSortWarps][256];
+    long long lo, hi, seg_lo;
+    int seg;
+    if (!block_items(S, blockIdx.x, lo, hi, seg_lo, seg)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < 256; d += kSortThreads) {
+        base[d] = d < nbins ? H[(size_t)blockIdx.x * nbins + d] : 0u;
+#pragma unroll
+        for (int s = 0; s < R; ++s)
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) cnt[s][w][d] = 0;
+    }
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+    for (long long r0 = lo; r0 < hi; r0 += R * kSortThreads) {
+        K key[R];
+        uint32_t val[R], dg[R];
+        int rank[R];
+#pragma unroll
+        for (int s = 0; s < R; ++s) {
+            const long long i = r0 + (long long)s * kSortThreads + threadIdx.x;
+            const bool valid = i < hi;
+            key[s] = 0;
+            val[s] = 0;
+            dg[s] = 0xffffffffu;
+            if (valid) {
+                key[s] = kin[i];
+                val[s] = vin ? vin[i] : (uint32_t)(i - seg_lo);
+                dg[s] = digit_of(key[s], shift, mask);
+            }
+            uint32_t peers = __ballot_sync(0xffffffffu, valid);
+            if (!valid) peers = ~peers;
+            for (uint32_t bit = 1; bit < (uint32_t)nbins; bit <<= 1) {
+                const uint32_t bb = __ballot_sync(0xffffffffu, (dg[s] & bit) != 0);
+                peers &= (dg[s] & bit) ? bb : ~bb;
+            }
+            rank[s] = __popc(peers & lt);
+            if (valid && rank[s] == 0) cnt[s][warp][dg[s]] = (uint16_t)__popc(peers);
+        }
+        __syncthreads();
+        // per digit, the exclusive prefix over the slots in (sub-round, warp) order
+        for (int d = threadIdx.x; d < nbins; d += kSortThreads) {
+            uint32_t run = 0;
+#pragma unroll
+            for (int s = 0; s < R; ++s)
+#pragma unroll
+                for (int w = 0; w < kSortWarps; ++w) {
+                    const uint32_t c = cnt[s][w][d];
+                    cnt[s][w][d] = (uint16_t)run;
+                    run += c;
+                }
+            tot[d] = run;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < R; ++s) {
+            if (dg[s] != 0xffffffffu) {
+                const uint32_t off = base[dg[s]] + cnt[s][warp][dg[s]] + (uint32_t)rank[s];
+                kout[seg_lo + off] = key[s];
+                vout[seg_lo + off] = val[s];
+            }
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < nbins; d += kSortThreads) {
+            base[d] += tot[d];
+#pragma unroll
+            for (int s = 0; s < R; ++s)
+#pragma unroll
+                for (int w = 0; w < kSortWarps; ++w) cnt[s][w][d] = 0;
+        }
+        __syncthreads();
+    }
+}
+
+// The four-keys scatter where every digit is below 256, else one key per thread.
+template <typename K>
+static void launch_scatter(unsigned blocks, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout, Segs S,
+                           int shift, uint32_t mask, int nbins, const uint32_t* H, const DevStatus* st_dev,
+                           cudaStream_t st) {
+    if (nbins <= 256)
+        k_scatter4<K><<<blocks, kSortThreads, 0, st>>>(kin, vin, kout, vout, S, shift, mask, nbins, H, st_dev);
+    else
+        k_scatter<K><<<blocks, kSortThreads, 0, st>>>(kin, vin, kout, vout, S, shift, mask, nbins, H, st_dev);
+}
+
 // ---- emission -------------------------------------------------------------
 
 // Per (receiver, emission chunk of kEChunk depth-sorted Gaussians): number of pairs.
@@ -385,8 +485,8 @@ cudaError_t launch_sort_small_keys(const uint32_t* keys, uint32_t* keys_out, uin
     Segs sg{1, n, chunks, nullptr, nullptr};
     k_hist<uint32_t><<<chunks, kSortThreads, 0, st>>>(keys, sg, 0, (uint32_t)(nbins - 1), nbins, hist, nullptr);
     k_scan<<<1, kSortThreads, 0, st>>>(sg, nbins, hist, nullptr, nullptr);
-    k_scatter<uint32_t><<<chunks, kSortThreads, 0, st>>>(keys, nullptr, keys_out, vals_out, sg, 0,
-                                                          (uint32_t)(nbins - 1), nbins, hist, nullptr);
+    launch_scatter<uint32_t>(chunks, keys, nullptr, keys_out, vals_out, sg, 0, (uint32_t)(nbins - 1), nbins, hist,
+                             nullptr, st);
     return cudaGetLastError();
 }
 
@@ -411,8 +511,7 @@ cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream
         const int shift = 8 * pass;
         k_hist<uint32_t><<<dblocks, kSortThreads, 0, st>>>(k_in, ds, shift, 0xffu, 256, H, nullptr);
         k_scan<<<L.n_rx, kSortThreads, 0, st>>>(ds, 256, H, nullptr, nullptr);
-        k_scatter<uint32_t><<<dblocks, kSortThreads, 0, st>>>(k_in, v_in, k_out, v_out, ds, shift, 0xffu, 256, H,
-                                                               nullptr);
+        launch_scatter<uint32_t>(dblocks, k_in, v_in, k_out, v_out, ds, shift, 0xffu, 256, H, nullptr, st);
         uint32_t* t = k_in; k_in = k_out; k_out = t;
         v_in = v_out;
         v_out = (v_out == at<uint32_t>(ws, L.dval)) ? v_alt : at<uint32_t>(ws, L.dval);
@@ -438,9 +537,9 @@ cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream
     k_hist<unsigned long long><<<pblocks, kSortThreads, 0, st>>>(at<unsigned long long>(ws, L.pkeys2), ps, 32,
                                                                  0xffffffffu, L.n_tiles, TH, status);
     k_scan<<<L.n_rx, kSortThreads, 0, st>>>(ps, L.n_tiles, TH, at<uint32_t>(ws, L.tile_start), status);
-    k_scatter<unsigned long long><<<pblocks, kSortThreads, 0, st>>>(
-        at<unsigned long long>(ws, L.pkeys2), at<uint32_t>(ws, L.pids2), at<unsigned long long>(ws, L.pkeys),
-        at<uint32_t>(ws, L.pids), ps, 32, 0xffffffffu, L.n_tiles, TH, status);
+    launch_scatter<unsigned long long>(pblocks, at<unsigned long long>(ws, L.pkeys2), at<uint32_t>(ws, L.pids2),
+                                       at<unsigned long long>(ws, L.pkeys), at<uint32_t>(ws, L.pids), ps, 32,
+                                       0xffffffffu, L.n_tiles, TH, status, st);
     (void)p;
     return cudaGetLastError();
 }
