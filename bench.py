@@ -22,8 +22,10 @@ FP64 CPU oracle timed on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
+import signal
 import statistics
 import subprocess
 import sys
@@ -67,21 +69,29 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms around the timed region.
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Each sample carries nvidia-smi's own timestamp.  `mark(start=True)` and `mark()` bound
+    the timed region; the summary keeps the samples inside it or, when the region is
+    shorter than the interval, the nearest sample on each side of it."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.lines = []
+        self.t0 = self.t1 = None
+        self.first = threading.Event()
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -92,34 +102,67 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+            self.first.set()
+
+    def wait_first(self, timeout_s: float = 3.0):
+        """Until nvidia-smi has printed its first sample (bounded)."""
+        if self.proc is not None:
+            self.first.wait(timeout_s)
+
+    def mark(self, start: bool = False):
+        now = datetime.datetime.now()
+        if start:
+            self.t0 = now
+        else:
+            self.t1 = now
 
     def __exit__(self, *a):
         if self.proc is not None:
-            self.proc.terminate()
+            time.sleep(2.5 * self.INTERVAL_MS / 1e3)  # one sample after the region
+            self.proc.send_signal(signal.SIGINT)  # the loop's own stop, as Ctrl+C
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+                self.proc.wait(timeout=5)
+            self.t.join(timeout=5)
 
-    def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+    @classmethod
+    def parse(cls, lines):
+        """(time, sm MHz, max sm MHz, set of active reasons) per well-formed sample line."""
+        out = []
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                t = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f")
+                sm, mx = float(f[2]), float(f[3])
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        if not sm:
+            out.append((t, sm, mx, {n for n, v in zip(cls.REASONS, f[6:10]) if v.lower().startswith("active")}))
+        return out
+
+    @staticmethod
+    def select(samples, t0, t1):
+        """The samples inside [t0, t1], else the last one before t0 and the first after t1."""
+        if t0 is None or t1 is None:
+            return samples, "unbounded"
+        inside = [s for s in samples if t0 <= s[0] <= t1]
+        if inside:
+            return inside, "inside"
+        before = [s for s in samples if s[0] < t0][-1:]
+        after = [s for s in samples if s[0] > t1][:1]
+        return before + after, "bracketing"
+
+    def summary(self):
+        chosen, how = self.select(self.parse(self.lines), self.t0, self.t1)
+        if not chosen:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        reasons = set().union(*(s[3] for s in chosen))
+        return {"sm_mhz": statistics.median(s[1] for s in chosen), "sm_max_mhz": max(s[2] for s in chosen),
+                "reasons": sorted(reasons), "samples": len(chosen), "window": how,
+                "interval_ms": self.INTERVAL_MS}
 
 
 def dist_setup():
@@ -297,10 +340,14 @@ def run_ours(args, ws, rank):
     barrier(ws)
     torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clk:
+        clk.wait_first()
+        torch.cuda.synchronize()
+        clk.mark(start=True)
         for i in range(args.steps):
             flush.zero_()
             step(evs[i])
         torch.cuda.synchronize()
+        clk.mark()
     barrier(ws)
     stage = np.array([[evs[i][j].elapsed_time(evs[i][j + 1]) for j in range(4)] for i in range(args.steps)])
     ms_step = float(stage.sum(1).mean())

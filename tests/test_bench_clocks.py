@@ -1,0 +1,53 @@
+"""The clock record of the bench keeps the nvidia-smi samples taken during the timed
+region (or the two around it when the region is shorter than the sampling interval) and
+reports every throttle reason any of them saw.  Synthetic sample lines, no GPU."""
+import datetime
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+T = datetime.datetime(2026, 1, 2, 3, 4, 5)
+
+
+def _line(ms, sm, hw="Not Active", power="Not Active"):
+    t = (T + datetime.timedelta(milliseconds=ms)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+    return "%s, 0, %d, 2070, 900.5, 0x0, %s, Not Active, Not Active, %s" % (t, sm, hw, power)
+
+
+def _sampler(lines, t0_ms, t1_ms):
+    c = bench.ClockSampler(0)
+    c.lines = lines
+    c.t0 = T + datetime.timedelta(milliseconds=t0_ms)
+    c.t1 = T + datetime.timedelta(milliseconds=t1_ms)
+    return c
+
+
+def test_samples_inside_the_region_only():
+    lines = [_line(0, 1200), _line(50, 2070), _line(100, 2060), _line(150, 2070), _line(200, 900, hw="Active")]
+    s = _sampler(lines, 40, 160).summary()
+    assert s["window"] == "inside" and s["samples"] == 3
+    assert s["sm_mhz"] == 2070 and s["sm_max_mhz"] == 2070
+    assert s["reasons"] == []          # the throttled sample lies after the region
+
+
+def test_short_region_takes_the_samples_on_either_side():
+    lines = [_line(0, 2000), _line(50, 2070, power="Active"), _line(100, 2070)]
+    s = _sampler(lines, 60, 90).summary()
+    assert s["window"] == "bracketing" and s["samples"] == 2
+    assert s["sm_mhz"] == 2070
+    assert s["reasons"] == ["sw_power_cap"]
+
+
+def test_every_reason_seen_in_the_region_is_reported():
+    lines = [_line(10, 2070, hw="Active"), _line(20, 2070, power="Active")]
+    s = _sampler(lines, 0, 30).summary()
+    assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_malformed_lines_and_no_samples():
+    c = _sampler(["", "garbage", "[N/A], 0, x, y, 1, 0, a, b, c, d"], 0, 10)
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
