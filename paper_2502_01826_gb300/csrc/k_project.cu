@@ -213,11 +213,18 @@ __device__ __forceinline__ Cover cover_of(float cx, float cy, float cz, float ls
         if (rel < 0.0f) rel = dadd(rel, 360.0f);
         if (rel >= 360.0f) rel = dsub(rel, 360.0f);
         const float lo = dsub(rel, azd), hi = dadd(rel, azd);
+        // a window whose bins all fall outside the grid is skipped without its divides,
+        // with the result the full computation gives: xhi < 0 makes its last bin negative,
+        // and xlo >= daz (n_az + 2) (one bin of margin for the rounding of that product)
+        // puts its first bin beyond n_az.  Most Gaussians skip both wrapped windows.
+        const float past = dmul(gr.daz_deg, (float)(gr.n_az + 2));
 #pragma unroll
         for (int w = -1; w <= 1; ++w) {
             const float off = dmul(360.0f, (float)w);
-            float ulo = ceilf(dsub(ddiv(dadd(lo, off), gr.daz_deg), 0.5f));
-            float uhi = floorf(dsub(ddiv(dadd(hi, off), gr.daz_deg), 0.5f));
+            const float xlo = dadd(lo, off), xhi = dadd(hi, off);
+            if (xhi < 0.0f || xlo >= past) continue;
+            float ulo = ceilf(dsub(ddiv(xlo, gr.daz_deg), 0.5f));
+            float uhi = floorf(dsub(ddiv(xhi, gr.daz_deg), 0.5f));
             ulo = fmaxf(ulo, 0.0f);
             uhi = fminf(uhi, (float)(gr.n_az - 1));
             if (ulo > uhi) continue;
