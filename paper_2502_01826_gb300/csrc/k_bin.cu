@@ -320,6 +320,21 @@ static void launch_scatter(unsigned blocks, const K* kin, const uint32_t* vin, K
 
 // ---- emission -------------------------------------------------------------
 
+// Position of the k-th (from 0) set bit of x; k < popc(x).
+__device__ __forceinline__ int select_bit(uint32_t x, uint32_t k) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w; w >>= 1) {
+        const uint32_t c = (uint32_t)__popc(x & ((1u << w) - 1u));
+        if (k >= c) {
+            k -= c;
+            x >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
 // Per (receiver, emission chunk of kEChunk depth-sorted Gaussians): number of pairs.
 __global__ void __launch_bounds__(kSortThreads) k_count_chunks(const uint32_t* __restrict__ dval,
                                                                const Cover* __restrict__ cover, long long n,
@@ -393,7 +408,6 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
     if (capacity_failed(st)) return;
     __shared__ uint32_t offs[kEChunk];
     __shared__ uint32_t sh[kSortWarps];
-    __shared__ uint8_t sbits[kSortWarps][64];
     const int r = blockIdx.y, c = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long lo = (long long)c * kEChunk, hi = min(lo + (long long)kEChunk, n);
@@ -420,53 +434,50 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
     uint32_t* iout = pids + rx_base[r] + chunk_off[(size_t)r * dchunks + c];
     for (int i0 = 0; i0 < m; i0 += kSortThreads) {
         const int i = i0 + threadIdx.x;
-        bool big = false;
-        Cover cv;
-        cv.mask = 0ull;
-        cv.tv = 0u;
-        cv.count = 0u;
-        uint32_t gid = 0, dk = 0, o = 0;
+        uint32_t gid = 0, dk = 0, cnt = 0, tvw = 0, mlo = 0, mhi = 0, o = 0;
         if (i < m) {
             const size_t gi = (size_t)r * n + lo + i;
             gid = dval[gi];
             dk = dkey_sorted[gi];
-            cv = cover[(size_t)r * n + gid];
+            const Cover cv = cover[(size_t)r * n + gid];
+            cnt = cv.count;
+            tvw = cv.tv;
+            mlo = (uint32_t)cv.mask;
+            mhi = (uint32_t)(cv.mask >> 32);
             o = offs[i];
-            big = cv.count > 32u;
-            if (!big && cv.count) {
-                const int tvl = (int)(cv.tv & 0xffffu), tvh = (int)(cv.tv >> 16);
-                for (int tv = tvl; tv <= tvh; ++tv)
-                    for (unsigned long long mk = cv.mask; mk; mk &= mk - 1ull) {
-                        const int tu = __ffsll((long long)mk) - 1;
-                        kout[o] = ((unsigned long long)(uint32_t)(tv * ntu + tu) << 32) | dk;
-                        iout[o] = gid;
-                        ++o;
-                    }
-            }
         }
-        for (uint32_t bm = __ballot_sync(0xffffffffu, big); bm; bm &= bm - 1) {
-            const int L = __ffs(bm) - 1;
-            const uint32_t bo = __shfl_sync(0xffffffffu, o, L);
-            const uint32_t bgid = __shfl_sync(0xffffffffu, gid, L);
-            const uint32_t bdk = __shfl_sync(0xffffffffu, dk, L);
-            const uint32_t btv = __shfl_sync(0xffffffffu, cv.tv, L);
-            const uint32_t mlo = __shfl_sync(0xffffffffu, (uint32_t)cv.mask, L);
-            const uint32_t mhi = __shfl_sync(0xffffffffu, (uint32_t)(cv.mask >> 32), L);
-            const unsigned long long bmask = ((unsigned long long)mhi << 32) | mlo;
-            const int nb = __popcll(bmask);
-            // positions of the set azimuth tiles, in order
-            for (int b = lane; b < 64; b += 32)
-                if ((bmask >> b) & 1ull) sbits[warp][__popcll(bmask & ((1ull << b) - 1ull))] = (uint8_t)b;
-            __syncwarp();
-            const int tvl = (int)(btv & 0xffffu), tvh = (int)(btv >> 16);
-            uint32_t row = bo;
-            for (int tv = tvl; tv <= tvh; ++tv, row += nb)
-                for (int q = lane; q < nb; q += 32) {
-                    const int tu = sbits[warp][q];
-                    kout[row + q] = ((unsigned long long)(uint32_t)(tv * ntu + tu) << 32) | bdk;
-                    iout[row + q] = bgid;
-                }
-            __syncwarp();
+        // the warp's 32 consecutive items own one run of pairs from lane 0's offset; the
+        // warp writes it 32 slots at a time, each slot finding its item by a search over
+        // the inclusive counts and its (row, column) inside the item's cover
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += t;
+        }
+        const uint32_t wbase = __shfl_sync(0xffffffffu, o, 0);
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        for (uint32_t s0 = 0; s0 < total; s0 += 32) {
+            const uint32_t q = s0 + lane;
+            int j = 0;  // lanes whose inclusive count is <= q: the owner of slot q
+#pragma unroll
+            for (int b = 16; b; b >>= 1) {
+                const uint32_t t = __shfl_sync(0xffffffffu, incl, j + b - 1);
+                if (t <= q) j += b;
+            }
+            const uint32_t oi = __shfl_sync(0xffffffffu, incl, j), oc = __shfl_sync(0xffffffffu, cnt, j);
+            const uint32_t ogid = __shfl_sync(0xffffffffu, gid, j), odk = __shfl_sync(0xffffffffu, dk, j);
+            const uint32_t otv = __shfl_sync(0xffffffffu, tvw, j);
+            const uint32_t olo = __shfl_sync(0xffffffffu, mlo, j), ohi = __shfl_sync(0xffffffffu, mhi, j);
+            if (q < total) {
+                const uint32_t p = q - (oi - oc);  // pair index inside the owner's cover
+                const uint32_t nlo = __popc(olo), nb = nlo + __popc(ohi);
+                const uint32_t row = p / nb, col = p - row * nb;
+                const int tu = col < nlo ? select_bit(olo, col) : 32 + select_bit(ohi, col - nlo);
+                const int tv = (int)(otv & 0xffffu) + (int)row;
+                kout[wbase + q] = ((unsigned long long)(uint32_t)(tv * ntu + tu) << 32) | odk;
+                iout[wbase + q] = ogid;
+            }
         }
     }
     (void)rx_total;
