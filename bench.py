@@ -6,7 +6,7 @@ Workload (default): the BLE-RSSI-shaped scene -- 50,000 complex Gaussians in a
 transmitter, 2.4 GHz -- synthetic and seeded (the paper's datasets are not here).
 
 One step = one pass of the whole hot path for all 64 receivers: project (records,
-depth keys, tile coverage, path phase), bin (depth radix sort, pair emission,
+depth keys, tile coverage, FP64 path phase), bin (depth radix sort, pair emission,
 tile counting sort), render (per-ray complex front-to-back accumulation) and the
 received-signal reduction (RSSI per receiver).  Inputs are resident in HBM when the
 timed region starts; L2 is flushed (256 MB write) between timed steps, outside the

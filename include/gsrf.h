@@ -150,7 +150,7 @@ typedef struct {
                                 * receiver-major: floats 0-2 mu - r, 3 D cos(theta) of the
                                 * cone of directions that can reach the Gaussian (culling),
                                 * 4-6 whitened receiver offset, 7-8 e^{-j 2 pi f0 d / c}
-                                * (cos, -sin) with the phase reduced to ~44 bits, 9 the
+                                * (cos, -sin) with the phase reduced in FP64, 9 the
                                 * per-subcarrier step 2 pi df d / c, 10-11 the radiance at
                                 * the direction of mu (GSRF_VARIANT_RADIANCE_AT_MEAN), else 0 */
 } gsrf_layout;
@@ -160,8 +160,7 @@ gsrf_status gsrf_workspace_layout(const gsrf_plan *plan, gsrf_layout *out);
  * whitening matrix diag(1/s) R^T and opacity; per (receiver, Gaussian) the whitened
  * receiver offset, the FP32 depth |mu - r| (sort key), the set of tiles the Gaussian
  * may touch (conservative: every ray that can hit it lies in one of them) and the
- * path phase exp(-j 2 pi f0 d / c), d = |t - mu| + |mu - r|, range-reduced in FP32
- * pair arithmetic (about 44 significant bits of the cycle count d f0 / c).
+ * path phase exp(-j 2 pi f0 d / c), d = |t - mu| + |mu - r|, range-reduced in FP64.
  *   rx_pos [dev] [n_rx,3]; tx_pos [dev] [3].
  * Clears the status word.  Non-finite parameters set GSRF_ERR_NONFINITE. */
 gsrf_status gsrf_project(const gsrf_plan *plan, const gsrf_gaussians *g, const float *rx_pos,

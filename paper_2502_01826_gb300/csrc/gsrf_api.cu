@@ -34,7 +34,7 @@ bool make_layout(const gsrf_plan* p, Layout* L) {
     L->raytab = take((size_t)g.n_az * g.n_el * raytab_floats(plan_degree(p)) * sizeof(float));
     L->fle = take(n * fle_floats(plan_degree(p)) * sizeof(float));
     L->gshape = take(n * sizeof(GShape));
-    L->dpath = take(n * sizeof(float2));
+    L->dpath = take(n * sizeof(double));
     L->view = take(nr * n * sizeof(View));
     L->cover = take(nr * n * sizeof(Cover));
     L->dkey = take(nr * n * 4);

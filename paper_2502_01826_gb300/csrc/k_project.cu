@@ -18,9 +18,9 @@ __global__ void k_status_init(DevStatus* st) {
 
 // One thread per Gaussian: W = diag(1/s) R^T with R the rotation of the normalised
 // quaternion (Sec. 4.2, Sigma = R S S^T R^T, so Sigma^-1 = W^T W), opacity = sigmoid,
-// and |t - mu| for the path phase, taken in FP64 and kept as an FP32 (hi, lo) pair.
+// and |t - mu| in FP64 for the path phase.
 __global__ void __launch_bounds__(256) k_prepare(gsrf_gaussians g, const float* __restrict__ tx,
-                                                 GShape* __restrict__ shape, float2* __restrict__ dpath_t,
+                                                 GShape* __restrict__ shape, double* __restrict__ dpath_t,
                                                  float* __restrict__ fle, DevStatus* st, int variant, int L) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.n) return;
@@ -67,9 +67,7 @@ __global__ void __launch_bounds__(256) k_prepare(gsrf_gaussians g, const float* 
     out.pad = 0.0f;
     shape[k] = out;
     const double dx = (double)tx[0] - mx, dy = (double)tx[1] - my, dz = (double)tx[2] - mz;
-    const double dt = sqrt(dx * dx + dy * dy + dz * dz);
-    const float dt_hi = (float)dt;
-    dpath_t[k] = make_float2(dt_hi, (float)(dt - (double)dt_hi));
+    dpath_t[k] = sqrt(dx * dx + dy * dy + dz * dz);
     // folded Fourier-Legendre coefficients (see fle_floats): the m = 0 pairs, then per
     // (l, m > 0) in m-major order the four reals that fold c_{l,m} Y_{l,m} + c_{l,-m}
     // Y_{l,-m} with Y_{l,-m} = kappa conj(Y_{l,m}), kappa = (-1)^m (l-m)!/(l+m)!
@@ -241,7 +239,7 @@ __device__ __forceinline__ Cover cover_of(float cx, float cy, float cz, float ls
 }
 
 // Error-free FP32 transformations (Knuth's two-sum, the FMA two-product) and |a - b| of
-// two FP32 points to about 47 bits, as an FP32 pair.  Every step is an explicit
+// two FP32 points to about 47 bits, returned in FP64.  Every step is an explicit
 // round-to-nearest operation, so the compiler cannot contract or reorder it.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
@@ -255,11 +253,7 @@ __device__ __forceinline__ void pair_add(float& h, float& l, float bh, float bl)
     h = __fadd_rn(s, e);
     l = __fsub_rn(e, __fsub_rn(h, s));
 }
-// |a - b| as an FP32 pair (h, l): a - b by two-sum, the squares by FMA two-products,
-// their sum by pair additions and the square root by one Newton correction, about 47
-// significant bits in all.
-__device__ __forceinline__ void pair_dist(float ax, float ay, float az, float bx, float by, float bz, float& dh,
-                                          float& dl) {
+__device__ __forceinline__ double pair_dist(float ax, float ay, float az, float bx, float by, float bz) {
     float ch[3], cl[3];
     two_sum(ax, -bx, ch[0], cl[0]);
     two_sum(ay, -by, ch[1], cl[1]);
@@ -272,14 +266,11 @@ __device__ __forceinline__ void pair_dist(float ax, float ay, float az, float bx
         const float q = __fmaf_rn(__fmul_rn(2.0f, ch[i]), cl[i], pe);  // + 2 ch cl (cl^2 < 2^-48 ch^2)
         pair_add(h, l, p, q);
     }
-    dh = 0.0f;
-    dl = 0.0f;
-    if (!(h > 0.0f)) return;
+    if (!(h > 0.0f)) return 0.0;
     const float sq = __fsqrt_rn(h);
     const float res = __fadd_rn(__fmaf_rn(-sq, sq, h), l);            // (h + l) - sq^2
     const float corr = __fdiv_rn(res, __fmul_rn(2.0f, sq));
-    dh = __fadd_rn(sq, corr);
-    dl = __fsub_rn(corr, __fsub_rn(dh, sq));
+    return (double)sq + (double)corr;
 }
 
 // Radiance (Eq. 9) of one Gaussian, from its folded coefficients q (see kFle), in the
@@ -311,8 +302,8 @@ __device__ __forceinline__ void radiance_at(const float* __restrict__ q, float c
 // One thread per (receiver, Gaussian): whitened offset, depth key, coverage, phase.
 __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __restrict__ rxp,
                                               const GShape* __restrict__ shape,
-                                              const float2* __restrict__ dpath_t, gsrf_grid gr,
-                                              int ntu, int ntv, float f0c_hi, float f0c_lo, float two_pi_df_over_c,
+                                              const double* __restrict__ dpath_t, gsrf_grid gr,
+                                              int ntu, int ntv, double f0_over_c, float two_pi_df_over_c,
                                               View* __restrict__ view, Cover* __restrict__ cover,
                                               uint32_t* __restrict__ dkey, float* __restrict__ rx_keep,
                                               const float* __restrict__ txp, float* __restrict__ tx_keep,
@@ -357,28 +348,18 @@ __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __r
     // direction pre-test of the render: D cos(theta) of the cover's cone less a rounding
     // margin; below -D (every direction passes) when the cone is a hemisphere or wider
     v.ccos = wide ? -1.0f - D_c : sqrtf(fmaxf(D_c * D_c - Rs * Rs, 0.0f)) - 2e-6f * D_c;
-    // path phase: d = |t - mu| + |mu - r| and its d f0 / c cycles reduced to [0, 1), all in
-    // FP32 pairs (FP64 is slow on this part): the pair sum of the two distances, the
-    // cycles as the two-product of the leading parts plus the cross terms, and the
-    // fractional part of the leading product (exact in FP32) plus the tail.  About 44
-    // significant bits of the cycle count: 34 fractional bits at 1000 cycles (100 m at
-    // 3 GHz).
-    float dh = dpath_t[k].x, dl = dpath_t[k].y;
-    {
-        float rh, rl;
-        pair_dist(mx, my, mz, rx, ry, rz, rh, rl);
-        pair_add(dh, dl, rh, rl);
-    }
-    const float cp = __fmul_rn(dh, f0c_hi);
-    const float ce = __fmaf_rn(dh, f0c_lo, __fmaf_rn(dl, f0c_hi, __fmaf_rn(dh, f0c_hi, -cp)));
-    float fr = __fadd_rn(__fsub_rn(cp, floorf(cp)), ce);
-    if (fr < 0.0f) fr = __fadd_rn(fr, 1.0f);
-    if (fr >= 1.0f) fr = __fsub_rn(fr, 1.0f);
+    // path phase: d = |t - mu| + |mu - r| and d f0 / c reduced to [0, 1) in FP64.  |mu - r|
+    // comes as an exact FP32 pair computation (FP64 square roots are slow on this part):
+    // mu - r by two-sum, the squares by FMA two-products, their sum by pair additions and
+    // the square root by one Newton correction, about 47 significant bits in all.
+    const double d = dpath_t[k] + pair_dist(mx, my, mz, rx, ry, rz);
+    const double cyc = d * f0_over_c;
+    const float fr = (float)(cyc - floor(cyc));
     float s, c;
     sincospif(2.0f * fr, &s, &c);
     v.er = c;
     v.ei = -s;
-    v.omd = two_pi_df_over_c * dh;
+    v.omd = two_pi_df_over_c * (float)d;
     v.pad0 = v.pad1 = 0.0f;
     if (variant & GSRF_VARIANT_RADIANCE_AT_MEAN) radiance_at(fle + (size_t)k * kFle, -ux, -uy, -uz, v.pad0, v.pad1);
     view[o] = v;
@@ -398,12 +379,10 @@ cudaError_t launch_project(const gsrf_plan* p, const Layout& L, const gsrf_gauss
     const int n_rays = p->grid.n_az * p->grid.n_el;
     k_raytab<<<(n_rays + 255) / 256, 256, 0, st>>>(p->grid, plan_degree(p), at<float>(ws, L.raytab));
     const unsigned nb = (unsigned)((L.n + 255) / 256);
-    k_prepare<<<nb, 256, 0, st>>>(*g, tx, at<GShape>(ws, L.gshape), at<float2>(ws, L.dpath),
+    k_prepare<<<nb, 256, 0, st>>>(*g, tx, at<GShape>(ws, L.gshape), at<double>(ws, L.dpath),
                                   at<float>(ws, L.fle), status, p->variant, plan_degree(p));
-    const double f0c = p->f0_hz / kC;
-    const float f0c_hi = (float)f0c, f0c_lo = (float)(f0c - (double)f0c_hi);
-    k_view<<<dim3(nb, L.n_rx), 256, 0, st>>>(*g, rx, at<GShape>(ws, L.gshape), at<float2>(ws, L.dpath),
-                                              p->grid, L.ntu, L.ntv, f0c_hi, f0c_lo,
+    k_view<<<dim3(nb, L.n_rx), 256, 0, st>>>(*g, rx, at<GShape>(ws, L.gshape), at<double>(ws, L.dpath),
+                                              p->grid, L.ntu, L.ntv, p->f0_hz / kC,
                                               (float)(2.0 * 3.14159265358979323846 * p->df_hz / kC),
                                               at<View>(ws, L.view), at<Cover>(ws, L.cover),
                                               at<uint32_t>(ws, L.dkey), at<float>(ws, L.rxpos), tx,

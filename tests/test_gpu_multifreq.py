@@ -1,5 +1,5 @@
 """GPU parity of the multi-frequency render (CSI-shaped: subcarriers f0 + s df) and of
-the distance-to-phase step (FP32 pair arithmetic, about 44 bits), against the FP64 oracle.
+the FP64 distance-to-phase step, against the FP64 oracle.
 
 Per subcarrier the per-ray bars of gpu_util apply; the CSI value of a receiver (the
 complex sum over rays per subcarrier) must sit within the sum of its rays' bounds; the
@@ -63,7 +63,7 @@ def test_subcarriers_match_oracle(n_f):
 def test_csi_100k_full_size_and_phase_step():
     """The CSI workload in the benchmark's configuration: 100,000 Gaussians, 8 arrays of
     4 elements, 64 subcarriers at 312.5 kHz around 5.2 GHz, 180 x 45 grid.  Sampled rays
-    of two elements against the oracle at every subcarrier, and the stored range-reduced
+    of two elements against the oracle at every subcarrier, and the stored FP64-reduced
     path phase of every (element, Gaussian) of two elements within 1e-6 rad."""
     cfg = synthetic.config_csi()
     out, R = render_mf(cfg["scene"], cfg["rx"], cfg["tx"], cfg["f0"], cfg["df"], cfg["n_f"], cfg["grid"])
@@ -89,5 +89,5 @@ def test_csi_100k_full_size_and_phase_step():
         ph_gpu = np.arctan2(-views[r, :, 8], views[r, :, 7])
         err = np.abs(np.angle(np.exp(1j * (ph_gpu - ph_ref))))
         worst = max(worst, float(err.max()))
-    print("max |phase error| of the distance-to-phase step: %.3g rad" % worst)
+    print("max |phase error| of the FP64 distance-to-phase step: %.3g rad" % worst)
     assert worst <= 1e-6

@@ -22,7 +22,7 @@ from gpu_util import oracle_grid, require_gpu
 
 pytestmark = pytest.mark.gpu
 
-CONFIGS = [  # tile_w, tile_h, ray_block_w, stage
+SPLITS = [  # tile_w, tile_h, ray_block_w, stage
     (16, 16, 8, 32), (8, 16, 8, 16), (32, 8, 32, 32), (16, 16, 4, 32), (32, 32, 16, 16), (16, 4, 8, 32),
     (8, 8, 8, 16), (32, 16, 4, 32),
 ]
@@ -59,10 +59,10 @@ def run(scene, rx, tx, cfg, n_f=1, df=0.0, spec=dict(n_az=360, n_el=90)):
     return out.cpu().numpy(), R
 
 
-@pytest.mark.parametrize("cfg", CONFIGS)
+@pytest.mark.parametrize("cfg", SPLITS)
 def test_bins_match_oracle_and_rays_match_default(problem, cfg):
     scene, rx, tx = problem
-    ref, _ = run(scene, rx, tx, CONFIGS[0])
+    ref, _ = run(scene, rx, tx, SPLITS[0])
     out, R = run(scene, rx, tx, cfg)
     assert np.array_equal(out, ref), "per-ray signal differs from the default configuration"
     keys, ids, rb, ts = R.pairs()
@@ -78,11 +78,11 @@ def test_bins_match_oracle_and_rays_match_default(problem, cfg):
         assert np.array_equal(ts[r].astype(np.int64), t_ref)
 
 
-@pytest.mark.parametrize("cfg", [CONFIGS[1], CONFIGS[2], CONFIGS[4]])
+@pytest.mark.parametrize("cfg", [SPLITS[1], SPLITS[2], SPLITS[4]])
 def test_subcarriers_match_default(problem, cfg):
     scene, rx, tx = problem
     spec = dict(n_az=180, n_el=45)
-    ref, _ = run(scene, rx, tx, CONFIGS[0], n_f=20, df=1.0e6, spec=spec)
+    ref, _ = run(scene, rx, tx, SPLITS[0], n_f=20, df=1.0e6, spec=spec)
     out, _ = run(scene, rx, tx, cfg, n_f=20, df=1.0e6, spec=spec)
     assert np.array_equal(out, ref)
 
@@ -103,11 +103,11 @@ def grads(scene, rx, tx, cfg, n_f=1, df=0.0):
     return {k: v.grad.double().cpu().numpy() for k, v in p.items()}
 
 
-@pytest.mark.parametrize("cfg,n_f", [(CONFIGS[2], 1), (CONFIGS[3], 1), (CONFIGS[1], 9)])
+@pytest.mark.parametrize("cfg,n_f", [(SPLITS[2], 1), (SPLITS[3], 1), (SPLITS[1], 9)])
 def test_backward_matches_default(problem, cfg, n_f):
     scene, rx, tx = problem
     small = {k: v[:2000] for k, v in scene.items()}
-    ref = grads(small, rx, tx, CONFIGS[0], n_f=n_f, df=2.0e6)
+    ref = grads(small, rx, tx, SPLITS[0], n_f=n_f, df=2.0e6)
     got = grads(small, rx, tx, cfg, n_f=n_f, df=2.0e6)
     for k in ref:
         a, b = got[k].ravel(), ref[k].ravel()
