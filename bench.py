@@ -252,6 +252,25 @@ def oracle_sample(cfg, budget_s: float = 12.0, threads: int | None = None):
                        % (n - 1, cfg["name"], n, n_rx_all, n_rays, pairs, dt)), dt
 
 
+def oracle_phase_error(cfg, phasor):
+    """The path phase the GPU stored for every (receiver, Gaussian) (its view records'
+    phasor (cos, -sin)) against the oracle's FP64 path phase: largest and rms wrapped
+    difference in radians."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    worst, sq, n = 0.0, 0.0, 0
+    for r in range(phasor.shape[0]):
+        ref = oracle.path_phase(cfg["scene"], cfg["rx"][r], cfg["tx"], cfg["f0"])
+        gpu = np.arctan2(-phasor[r, :, 1].astype(np.float64), phasor[r, :, 0].astype(np.float64))
+        err = np.abs(np.angle(np.exp(1j * (gpu - ref))))
+        worst = max(worst, float(err.max()))
+        sq += float(np.square(err).sum())
+        n += err.size
+    return {"max": worst, "rms": (sq / max(n, 1)) ** 0.5, "pairs": n,
+            "vs": "the oracle's FP64 path phase, every (receiver, Gaussian) of the timed workload"}
+
+
 # ------------------------------------------------------------------ our arm
 
 def split_grid(cfg, R):
@@ -349,6 +368,9 @@ def run_ours(args, ws, rank):
         torch.cuda.synchronize()
         clk.mark()
     barrier(ws)
+    # the path phasors (cos, -sin) of every (receiver, Gaussian) the timed steps stored,
+    # for the phase error against the oracle that the CPU-oracle leg reports
+    phasor = R.view_records()[:, :, 7:9].cpu().numpy() if (ws == 1 and rank == 0) else None
     stage = np.array([[evs[i][j].elapsed_time(evs[i][j + 1]) for j in range(4)] for i in range(args.steps)])
     ms_step = float(stage.sum(1).mean())
     total_s = max_over_ranks(float(stage.sum()) / 1e3, ws)
@@ -483,7 +505,7 @@ def run_ours(args, ws, rank):
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": clocks,
     }
-    return result, cfg
+    return result, cfg, phasor
 
 
 def _time_steps(fn, steps, flush):
@@ -1074,10 +1096,11 @@ def main():
         if rank == 0:
             print(json.dumps({"only": args.only, **rec}))
         return 0
-    result, cfg = run_ours(args, ws, rank)
+    result, cfg, phasor = run_ours(args, ws, rank)
     if rank == 0:
         if ws == 1:
             cb, _ = oracle_sample(cfg, budget_s=args.cpu_budget)
+            cb["phase_error_rad"] = oracle_phase_error(cfg, phasor)
             result["cpu_baseline"] = cb
         print(json.dumps(result))
     if ws > 1:

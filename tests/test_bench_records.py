@@ -1,6 +1,8 @@
-"""The clock record of the bench keeps the nvidia-smi samples taken during the timed
-region (or the two around it when the region is shorter than the sampling interval) and
-reports every throttle reason any of them saw.  Synthetic sample lines, no GPU."""
+"""Records the bench adds to its line, checked on the CPU.  The clock record keeps the
+nvidia-smi samples taken during the timed region (or the two around it when the region
+is shorter than the sampling interval) and reports every throttle reason any of them saw
+(synthetic sample lines).  The phase check compares stored phasors with the oracle's
+FP64 path phase."""
 import datetime
 import os
 import sys
@@ -51,3 +53,22 @@ def test_every_reason_seen_in_the_region_is_reported():
 def test_malformed_lines_and_no_samples():
     c = _sampler(["", "garbage", "[N/A], 0, x, y, 1, 0, a, b, c, d"], 0, 10)
     assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+
+def test_phase_error_against_the_oracle():
+    """The bench's phase check reads the view records' phasor as (cos, -sin): phasors
+    built from the oracle's own phase give a rounding-sized error, and one phasor
+    rotated by 0.01 rad shows up as the largest error."""
+    import numpy as np
+    import oracle
+    from paper_2502_01826_gb300 import synthetic
+    cfg = synthetic.config_ble(K=64, n_rx=3)
+    oracle.build()
+    ph = np.stack([oracle.path_phase(cfg["scene"], cfg["rx"][r], cfg["tx"], cfg["f0"]) for r in range(3)])
+    phasor = np.stack([np.cos(ph), -np.sin(ph)], axis=-1).astype(np.float32)
+    e = bench.oracle_phase_error(cfg, phasor)
+    assert e["pairs"] == 3 * 64 and e["max"] < 1e-6
+    ph[1, 5] += 0.01
+    phasor[1, 5] = np.array([np.cos(ph[1, 5]), -np.sin(ph[1, 5])], np.float32)
+    e = bench.oracle_phase_error(cfg, phasor)
+    assert abs(e["max"] - 0.01) < 1e-5
