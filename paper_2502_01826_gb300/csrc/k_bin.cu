@@ -393,10 +393,11 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_pairs(uint32_t* __restric
 }
 
 // Expand each chunk of depth-sorted Gaussians into its (tile, Gaussian) pairs, written
-// contiguously in depth order.  Thread t takes Gaussians t, t + 256, ... of the chunk
-// (consecutive lanes hold consecutive Gaussians, so their pair ranges are adjacent)
-// and walks its tile rectangle row by row; a Gaussian with more than 32 tiles is
-// written by the whole warp instead, one row at a time, a lane per azimuth tile.
+// contiguously in depth order.  Thread t takes Gaussians t, t + 256, ... of the chunk, so
+// a warp holds 32 consecutive Gaussians whose pairs form one contiguous run; the warp
+// writes that run 32 slots at a time (coalesced), each slot finding its Gaussian by a
+// search over the warp's inclusive counts and its tile from its index inside that
+// Gaussian's cover (elevation rows of the set azimuth tiles, in order).
 __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restrict__ dval,
                                                        const uint32_t* __restrict__ dkey_sorted,
                                                        const Cover* __restrict__ cover, long long n, int dchunks,
