@@ -38,25 +38,84 @@ sys.path.insert(0, ROOT)
 METRIC = "ray-Gaussian pairs/s and Rx spectra/s (fwd, fwd+bwd) vs plain launch; % roofline"
 UNIT = "pairs/s"
 
-# Algorithmic FP32 work of the compositing kernel (FMA = 2 FLOP), counted from its
-# arithmetic: a candidate test (whitened direction 15, A 5, B 5, t_mid 1, closest
-# point 6, m2 5) and a composited pair on top of its test (chord and midpoint weight
-# 16, Fourier-Legendre radiance 128, accumulation and transmittance 28).
+# Algorithmic work per composited (ray, Gaussian) pair, one frequency, in the cost model
+# of the scope table (an FP32 operation is one instruction: a fused multiply-add counts
+# once).  Forward: geometry ~20 (the hit test's quadratic, the clipped chord, the
+# midpoint weight), Fourier-Legendre radiance 64 (16 complex multiply-adds), accumulation
+# and transmittance ~16 = 100 FP32 operations, with rcp, rsqrt (the chord's square
+# root), ex2 (the weight), sin and cos (the transmittance phase) on the special-function
+# unit.  Backward (the adjoint of App. D, per composited pair): the forward's geometry
+# (20) and radiance (64) recomputed, the transmittance undone (12), the adjoints of
+# S in alpha, theta, phi and psi with the suffix update (35), the chain through the
+# weight and the chord to A, B, C (25), to v' and w (12), to W (18) and to the mean with
+# the path phase (23), the 32 coefficient gradients (32) and the 46 additions that
+# accumulate the pair's gradient values = 287 operations, with ex2, 3 rcp (1/A, 1/(1 -
+# alpha), 1/(A h)), 2 sqrt, sin, cos and 2 rsqrt (the path's unit vectors).
+FWD_OPS, FWD_MUFU = 100, {"rcp": 1, "rsqrt": 1, "ex2": 1, "sin": 1, "cos": 1}
+BWD_OPS, BWD_MUFU = 287, {"ex2": 1, "rcp": 3, "sqrt": 2, "sin": 1, "cos": 1, "rsqrt": 2}
+# bytes the render must move per launch: the staged record of each (receiver, Gaussian)
+# (64 B) read once, and 8 B of output per (ray, frequency); the backward reads 8 B of
+# upstream gradient and 32 B of ray state per ray and writes 48 floats per Gaussian
+REC_BYTES, RAY_OUT_BYTES = 64, 8
+# The candidate-test-inclusive count of the earlier reports (FMA = 2 FLOP), kept as a
+# secondary figure: a candidate test (whitened direction 15, A 5, B 5, t_mid 1, closest
+# point 6, m2 5) and a composited pair on top of its test (chord and midpoint weight 16,
+# radiance 128, accumulation and transmittance 28).  Candidate tests are overhead of
+# the culling, not algorithmic work.
 FLOP_TEST = 37
 FLOP_HIT = 172
-# DRAM bytes (read + write) of one k_render_queue launch on the 64-receiver workload,
-# from ncu (dram__bytes_read.sum + dram__bytes_write.sum, one pass, full size), per
-# work split; reported only for a split that was measured (profiles/).
-# ncu DRAM bytes (read + write) of one full-size k_render_queue launch, per work split
-# (tile_w, tile_h, ray_block_w, stage); null in the output for a split not measured
+# ncu DRAM bytes (read + write) of one full-size k_render_queue launch on the 64-receiver
+# workload, per work split (tile_w, tile_h, ray_block_w, stage); null in the output for a
+# split not measured (profiles/)
 RENDER_TRAFFIC = {(16, 16, 8, 32): 83646208 + 7084288, (32, 16, 8, 32): 78890752 + 6373120,
                   (32, 32, 8, 32): 83668224 + 6735360}
 # library kernels per step: project 4 (status, ray table, shape records, view records),
 # bin 19 (zero, 4 x (hist, scan, scatter), count, scan, emit, tile hist, scan, scatter),
 # render 5 (item keys, counting pass of 3, persistent render), received signal 1
 LAUNCHES_PER_STEP = 29
-# FP32 peak: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x the maximum SM clock.
+# nominal FP32 lanes per SM (context beside the measured FP32 peak)
 SMS, FP32_LANES = 152, 128
+
+
+def render_roofline(kernel: str, pairs: float, ms: float, pk: dict, ops_per_pair: int, mufu_per_pair: dict,
+                    bytes_per_launch: float, hbm_gbs: float, sm_mhz: float, traffic=None) -> dict:
+    """Roofline of a compositing launch on the scope table's unit: composited pairs x
+    the algorithmic FP32 operations and special-function results per pair, against the
+    measured FP32 fused-multiply-add rate and MUFU rates; the bytes term against the
+    measured copy bandwidth.  frac = the slowest term's time / the measured time."""
+    t = ms * 1e-3
+    t_fp32 = pairs * ops_per_pair / pk["fma32"]["ops_per_s"]
+    t_mufu = sum(pairs * n / pk[f]["ops_per_s"] for f, n in mufu_per_pair.items())
+    t_hbm = bytes_per_launch / (hbm_gbs * 1e9)
+    terms = {"fp32": t_fp32, "mufu": t_mufu, "hbm": t_hbm}
+    bound = max(terms, key=terms.get)
+    achieved = pairs * ops_per_pair / t / 1e12
+    return {"kernel": kernel, "bound": "alu" if bound != "hbm" else "hbm",
+            "achieved": achieved, "peak": pk["fma32"]["ops_per_s"] / 1e12, "unit": "Top/s",
+            "frac": terms[bound] / t, "traffic": traffic,
+            "unit_note": "FP32 operations (a fused multiply-add is one), %d per composited pair; "
+                         "peak = the measured FP32 FMA rate of this run" % ops_per_pair,
+            "peak_nominal": SMS * FP32_LANES * sm_mhz * 1e6 / 1e12,
+            "peak_nominal_note": "152 SMs x 128 FP32 lanes x %.0f MHz (median SM clock of the peak run)" % sm_mhz,
+            "composited_pairs": pairs, "ms": ms,
+            "t_roof_ms": {k: v * 1e3 for k, v in terms.items()}, "bytes_per_launch": bytes_per_launch}
+
+
+def measured_peaks(index: int) -> dict:
+    """FP32 / MUFU / FP64 / TF32 rates on this GPU now (libgsrf_peaks.so), with the SM
+    clocks sampled while they ran."""
+    from paper_2502_01826_gb300 import peaks as P
+    with ClockSampler(index) as clk:
+        clk.wait_first()
+        clk.mark(start=True)
+        pk = P.measure()
+        clk.mark()
+    s = clk.summary()
+    pk["clocks"] = s
+    pk["sm_mhz"] = s.get("sm_mhz") or 2070.0
+    pk["per_sm_per_clk"] = {k: pk[k]["ops_per_s"] / (pk["sms"] * pk["sm_mhz"] * 1e6)
+                            for k in P.KINDS if k in pk}
+    return pk
 
 
 def peaks():
@@ -355,6 +414,8 @@ def run_ours(args, ws, rank):
     tests_per_step, pairs_per_step = int(st.stats[0]), int(st.stats[1])
     binned_per_step = int(st.required_pairs)
 
+    # the FP32 / MUFU / FP64 / TF32 peaks of this GPU, measured now, for the roofline
+    pk = measured_peaks(torch.cuda.current_device())
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     barrier(ws)
     torch.cuda.synchronize()
@@ -368,6 +429,8 @@ def run_ours(args, ws, rank):
         torch.cuda.synchronize()
         clk.mark()
     barrier(ws)
+    # the library's own stage timers (gsrf_stage_times) for the last timed step
+    stage_abi = R.stage_times()
     # the path phasors (cos, -sin) of every (receiver, Gaussian) the timed steps stored,
     # for the phase error against the oracle that the CPU-oracle leg reports
     phasor = R.view_records()[:, :, 7:9].cpu().numpy() if (ws == 1 and rank == 0) else None
@@ -443,7 +506,7 @@ def run_ours(args, ws, rank):
     e2e_value = sum_over_ranks(pairs_per_step * args.steps, ws) / e2e_total
 
     persistent = persistent_leg(args, cfg, p, rx, tx, R, flush, pairs_per_step)
-    fwd_bwd = train_leg(args, ws, flush) if not args.no_train else None
+    fwd_bwd = train_leg(args, ws, flush, pk) if not args.no_train else None
     csi = csi_leg(args, ws, flush) if not args.no_train else None
     million = million_leg(args, ws, flush) if not args.no_train else None
     paper_loop = paper_loop_leg(args, ws, flush) if not args.no_train else None
@@ -454,12 +517,21 @@ def run_ours(args, ws, rank):
                                                     R.plan.ray_block_w or 8, R.plan.stage or 32))
 
     pk_, pk_kind = peaks()
-    mhz = float(pk_.get("sm_max_mhz", 2070.0))
-    peak_tflops = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
     render_ms = float(stage[:, 2].mean())
     stage_ms = {n: float(stage[:, j].mean()) for j, n in enumerate(["project", "bin", "render", "signal"])}
-    flops = tests_16x16 * FLOP_TEST + (pairs_per_step) * FLOP_HIT
-    achieved = flops / (render_ms * 1e-3) / 1e12
+    roof = render_roofline("k_render_queue", pairs_per_step, render_ms, pk, FWD_OPS, FWD_MUFU,
+                           REC_BYTES * K * n_rx + RAY_OUT_BYTES * n_rx * grid.n_az * grid.n_el,
+                           float(pk_["hbm_gbs"]), pk["sm_mhz"],
+                           traffic=RENDER_TRAFFIC.get((R.plan.grid.tile_w, R.plan.grid.tile_h, R.plan.ray_block_w or 8,
+                                                       R.plan.stage or 32)) if n_rx == 64 else None)
+    flops = tests_16x16 * FLOP_TEST + pairs_per_step * FLOP_HIT
+    roof["incl_candidate_tests"] = {
+        "unit": "TFLOP/s (FMA = 2 FLOP)", "flop_per_launch": flops,
+        "candidate_tests_16x16_tiles": tests_16x16, "achieved": flops / (render_ms * 1e-3) / 1e12,
+        "frac": flops / (render_ms * 1e-3) / (2.0 * pk["fma32"]["ops_per_s"]),
+        "note": "37 FLOP per candidate test + 172 per composited pair over 2 x the measured FMA rate; "
+                "candidate tests are culling overhead, so this is not the roofline fraction"}
+    roof["hbm_peak_kind"] = pk_kind
     clocks = clk.summary()
 
     result = {
@@ -480,16 +552,13 @@ def run_ours(args, ws, rank):
                    if ws > 1 else "1 GPU"},
         "spectra_per_s": spectra_s,
         "stage_ms": stage_ms,
+        "stage_ms_library_last_step": stage_abi,
         "plain_launch": {"ms_per_step": ms_plain, "spectra_per_s": n_rx / (ms_plain / 1e3),
                          "pairs_per_s": pairs_per_step / (ms_plain / 1e3),
                          "speedup_of_batched": ms_plain / ms_step,
                          "what": "%d sequential single-receiver project+bin+render+RSSI calls" % n_rx},
-        "roofline": {"kernel": "k_render_queue", "bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                     "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                     "traffic": RENDER_TRAFFIC.get((R.plan.grid.tile_w, R.plan.grid.tile_h, R.plan.ray_block_w or 8,
-                                                    R.plan.stage or 32)) if n_rx == 64 else None,
-                     "peak_kind": "FP32 lanes x max SM clock (%s sm_max_mhz %.0f)" % (pk_kind, mhz),
-                     "flop_per_launch": flops},
+        "roofline": roof,
+        "peaks_measured": pk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": 1e3 * sum(t_e2e) / len(t_e2e)},
         "autotune": tune,
@@ -662,7 +731,7 @@ def uneven_leg(args, flush, max_records=1.5e8):
             "splits_per_scene": {str(k): "%dx%d tiles, %d-wide ray block, stage %d" % v for k, v in splits.items()}}
 
 
-def train_leg(args, ws, flush):
+def train_leg(args, ws, flush, pk=None):
     """Training step of the paper's loop (Sec. 4.4, App. B) on the training-shaped
     workload: 200,000 Gaussians, 16 receivers, 360 x 90, 2.4 GHz; loss = mean |S - S_gt|^2
     on the per-ray complex signal against targets rendered (by the same library) from a
@@ -728,17 +797,27 @@ def train_leg(args, ws, flush):
     up = torch.randn(R.out_shape(), dtype=torch.float32, device="cuda")
     gr = {k: torch.zeros_like(v) for k, v in pd.items()}
     ms_b = _time_steps(lambda: R.render_bwd(pd, state, up, gr), args.steps, flush)
-    pk_, pk_kind = peaks()
-    peak = SMS * FP32_LANES * 2 * float(pk_.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    pk_, _ = peaks()
+    pk = pk or measured_peaks(torch.cuda.current_device())
+    hbm = float(pk_["hbm_gbs"])
+    rays = n_rx * grid.n_az * grid.n_el
+    b_f = REC_BYTES * K * n_rx + RAY_OUT_BYTES * rays
+    b_b = REC_BYTES * K * n_rx + (RAY_OUT_BYTES + 32) * rays + 48 * 4 * K
+    roof_f = render_roofline("k_render_queue", pairs, ms_f, pk, FWD_OPS, FWD_MUFU, b_f, hbm, pk["sm_mhz"])
+    roof_b = render_roofline("k_render_bwd", pairs, ms_b, pk, BWD_OPS, BWD_MUFU, b_b, hbm, pk["sm_mhz"])
+    mufu_fb = {f: FWD_MUFU.get(f, 0) + BWD_MUFU.get(f, 0) for f in set(FWD_MUFU) | set(BWD_MUFU)}
+    roof_fb = render_roofline("k_render_queue + k_render_bwd", pairs, ms_f + ms_b, pk, FWD_OPS + BWD_OPS, mufu_fb,
+                              b_f + b_b, hbm, pk["sm_mhz"])
     flops = tests_16x16 * FLOP_TEST + pairs * FLOP_HIT
+    roof_f["incl_candidate_tests"] = {"unit": "TFLOP/s (FMA = 2 FLOP)", "flop_per_launch": flops,
+                                      "candidate_tests_16x16_tiles": tests_16x16,
+                                      "frac": flops / (ms_f * 1e-3) / (2.0 * pk["fma32"]["ops_per_s"])}
     return {"workload": cfg["name"], "n_gauss": K, "n_rx": n_rx, "ms_per_step": ms,
             "pairs_per_step": pairs, "pairs_per_s": sum_over_ranks(pairs * args.steps, ws) / t,
             "spectra_per_s": sum_over_ranks(n_rx * args.steps, ws) / t,
             "split": tune.get("best", tune) if tune else None,
             "render_fwd_ms": ms_f, "render_bwd_ms": ms_b,
-            "roofline_fwd": {"kernel": "k_render_queue", "bound": "alu", "achieved": flops / (ms_f * 1e-3) / 1e12,
-                             "peak": peak, "unit": "TFLOP/s", "frac": flops / (ms_f * 1e-3) / 1e12 / peak,
-                             "flop_per_launch": flops, "candidate_tests_16x16_tiles": tests_16x16},
+            "roofline_fwd": roof_f, "roofline_bwd": roof_b, "roofline_fwd_bwd": roof_fb,
             "what": "forward + complex-MSE loss + hand-written backward to all parameters"}
 
 

@@ -258,6 +258,26 @@ typedef struct {
 gsrf_status gsrf_read_status(const void *workspace, size_t ws_bytes, gsrf_run_status *out,
                              void *stream);
 
+/* Stage timers.  The paper reports the render's cost as training time and inference
+ * latency per spectrum (Sec. 5.1, "Training & Inference Efficiency"; App. F); this call
+ * splits that latency over the stages.  Every gsrf_project, gsrf_bin, gsrf_render_fwd and
+ * gsrf_render_bwd call records a CUDA event before and after its launches on its own
+ * stream, keyed by its workspace (gsrf_render_batch: by its batch_ws).  Recording never
+ * synchronises; a call on a stream that is capturing records nothing.  Only the last call
+ * of each stage per workspace is kept.
+ *   workspace [dev] a workspace (or batch_ws) passed to those calls; ms [host] float[8] gets
+ *   the milliseconds of the last call of GSRF_STAGE_PROJECT, _BIN, _RENDER_FWD, _RENDER_BWD
+ *   and _BATCH (slots 5..7 reserved), -1 for a stage not recorded.
+ * Synchronises on the recorded end events.  GSRF_ERR_INVALID_ARG for a workspace with no
+ * recorded call.  Host state only: events of up to 1024 workspaces are kept, the oldest
+ * forgotten first; nothing is allocated on the device. */
+#define GSRF_STAGE_PROJECT 0
+#define GSRF_STAGE_BIN 1
+#define GSRF_STAGE_RENDER_FWD 2
+#define GSRF_STAGE_RENDER_BWD 3
+#define GSRF_STAGE_BATCH 4
+gsrf_status gsrf_stage_times(const void *workspace, float ms[8]);
+
 /* Autotuner of the work split (tile shape, rays per warp block, candidates per
  * shared-memory stage), which changes speed, never results.  The paper fixes 16 x 16
  * tiles (App. E) and has no tuner; this is a property of this library.  For the
@@ -310,8 +330,9 @@ gsrf_status gsrf_autotune(const gsrf_plan *plan, const gsrf_gaussians *g, const 
  *   360 x 90 grid, about 50,000 Gaussians with 300,000 tile pairs).
  *   status [host] NULL, or filled with the device status after the call (this
  *   synchronises `stream`).
- *   The first call on a device looks up the array's device address; make that first
- *   call before any stream capture.  All calls share the array and it keeps the last
+ *   Every call made outside a stream capture looks up the array's device address
+ *   afresh (so a cudaDeviceReset, after which the array may move, leaves no stale
+ *   address); make the first call on a device before any stream capture.  All calls share the array and it keeps the last
  *   call's contents (every call initialises what it reads); calls that overlap on the
  *   GPU -- other streams, other host threads -- race on it.  Nothing is allocated. */
 #define GSRF_STATIC_SCRATCH_BYTES ((size_t)32 << 20)

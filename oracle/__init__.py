@@ -59,7 +59,8 @@ class Scene(C.Structure):
 class Bands(C.Structure):
     _fields_ = [("m2_err", C.c_double), ("m2_abs", C.c_double), ("m2_mult", C.c_double),
                 ("t_band", C.c_double),
-                ("term_mult", C.c_double), ("term_abs", C.c_double), ("flip", C.c_int32)]
+                ("term_mult", C.c_double), ("term_abs", C.c_double), ("flip", C.c_int32),
+                ("m2_shift", C.c_void_p), ("shift_stride", C.c_int32)]
 
 
 FLAG_M2, FLAG_TOUT, FLAG_TERM = 1, 2, 4
@@ -233,9 +234,13 @@ def path_phase(scene: dict, rx, tx, f: float) -> np.ndarray:
 
 
 def render(scene: dict, rx, tx, f0: float, grid: Grid, df: float = 0.0, n_f: int = 1,
-           mode: int = 0, rays=None, threads: int | None = None, bands=None, flip: bool = False):
+           mode: int = 0, rays=None, threads: int | None = None, bands=None, flip: bool = False,
+           m2_shift=None):
     """Render one receiver.  Returns dict with S [n_f, n_rays] complex, T, Ta, Sabs, Scond,
-    nhit, ntest, flags.  ``bands``: (m2_err, m2_abs, m2_mult, t_band, term_mult, term_abs).  ``rays``: optional int array of ray indices (v * n_az + u)."""
+    nhit, ntest, flags.  ``bands``: (m2_err, m2_abs, m2_mult, t_band, term_mult, term_abs).
+    ``rays``: optional int array of ray indices (v * n_az + u).  ``m2_shift`` (needs
+    ``bands``): [n_rays, J] array; the m2 of the j-th composited pair of each ray is moved
+    by m2_shift[i, j] times its delta_k (the perturbation study of the rounding model)."""
     s = _SceneRef(scene)
     n_rays = grid.n_az * grid.n_el if rays is None else len(rays)
     ridx = None if rays is None else np.ascontiguousarray(rays, np.int32)
@@ -250,6 +255,11 @@ def render(scene: dict, rx, tx, f0: float, grid: Grid, df: float = 0.0, n_f: int
     b = None
     if bands is not None:
         b = Bands(*bands, 1 if flip else 0)
+        if m2_shift is not None:
+            shift = np.ascontiguousarray(m2_shift, np.float64)
+            assert shift.ndim == 2 and shift.shape[0] == n_rays
+            b.m2_shift = shift.ctypes.data
+            b.shift_stride = shift.shape[1]
     th = threads if threads else (os.cpu_count() or 1)
     rc = lib().or_render(C.byref(s.c), _p(_f32(rx)), _p(_f32(tx)), float(f0), float(df), n_f,
                          C.byref(grid), mode, _p(ridx), n_rays, th,

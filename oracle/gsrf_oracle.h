@@ -109,6 +109,13 @@ typedef struct {
     double term_mult;   /* band on |ln(Ta/eps_T)| in units of its propagated error */
     double term_abs;    /* plus this absolute band */
     int32_t flip;       /* nonzero: take every decision inside a band the other way */
+    /* Perturbation study of this rounding model (tests of Scond), NULL = none: the m2 of
+     * the j-th composited pair of selected ray i (j < shift_stride) is moved by
+     * m2_shift[i * shift_stride + j] * delta_k, and the pair's clipped chord, midpoint and
+     * weight are derived again from the moved m2 (the hit decision is kept; a chord that
+     * no longer reaches r_rx has length 0 at r_rx). */
+    const double *m2_shift;
+    int32_t shift_stride;
 } or_bands;
 
 /* ---- building blocks (exported so the tests can pin them one by one) ---- */

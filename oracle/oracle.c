@@ -319,6 +319,28 @@ static int flipped_hit(const double *Sinv, const double *mu, const double *r, co
     return 1;
 }
 
+/* The intersection record out[] of or_intersect with the closest approach moved from m2
+ * to m2 + e: half chord sqrt((9 - m2)/A) about t_mid = (t_in + t_out) / 2, clipped at r_rx,
+ * midpoint of the clipped chord and the weight there (App. D.3, App. A.2).  Used only by
+ * the perturbation study of the rounding model (or_bands.m2_shift). */
+static void shift_m2(double *out, double e, double r_rx)
+{
+    const double A = out[8], tm = 0.5 * (out[0] + out[1]);
+    const double m2 = out[5] + e;
+    const double hh = sqrt(fmax(9.0 - m2, 0.0) / A);
+    const double t_out = tm + hh, t_a = fmax(tm - hh, r_rx);
+    const double dt = fmax(t_out - t_a, 0.0);
+    const double t_rep = t_a + 0.5 * dt;
+    out[0] = tm - hh;
+    out[1] = t_out;
+    out[2] = t_a;
+    out[3] = dt;
+    out[4] = t_rep;
+    out[5] = m2;
+    out[6] = m2 + A * (t_rep - tm) * (t_rep - tm);
+    out[7] = exp(-0.5 * out[6]);
+}
+
 /* A hit of the variant that orders a ray's hits by t_mid (closest approach). */
 typedef struct {
     double tm, h[10], delta;
@@ -448,6 +470,10 @@ static void render_one(rctx *c, int64_t i)
         }
         if (!hit) continue;
     composite:;
+        if (bd && bd->m2_shift && nh < bd->shift_stride) {
+            const double sh = bd->m2_shift[(size_t)i * (size_t)bd->shift_stride + (size_t)nh];
+            if (sh != 0.0) shift_m2(h, sh * delta, (double)g->r_rx);
+        }
         double a = c->op[k] * h[7];
         if (a > (double)g->alpha_max) a = (double)g->alpha_max;
         const float *cf = c->s->coeffs + (size_t)k * 2 * nb;

@@ -1,4 +1,6 @@
-"""Compile libgsrf.so for sm_103a with nvcc (one -gencode, sources in parallel)."""
+"""Compile libgsrf.so for sm_103a with nvcc (one -gencode, sources in parallel), and
+libgsrf_peaks.so, the pipe-throughput microbenchmarks that give the render's roofline
+its compute peaks."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -11,6 +13,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 SO = os.path.join(PKG, "libgsrf.so")
+PEAKS_SO = os.path.join(PKG, "libgsrf_peaks.so")
+PEAKS_SRC = "peaks.cu"
 SOURCES = ["gsrf_api.cu", "k_project.cu", "k_bin.cu", "k_render.cu", "k_signal.cu", "k_backward.cu", "gsrf_static.cu",
            "gsrf_tune.cu"]
 HEADERS = ["gsrf_internal.cuh"]
@@ -32,10 +36,10 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(SO):
+    if not os.path.exists(SO) or not os.path.exists(PEAKS_SO):
         return False
-    t = os.path.getmtime(SO)
-    return all(os.path.getmtime(d) <= t for d in _deps())
+    t = min(os.path.getmtime(SO), os.path.getmtime(PEAKS_SO))
+    return all(os.path.getmtime(d) <= t for d in _deps() + [os.path.join(CSRC, PEAKS_SRC)])
 
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
@@ -56,13 +60,14 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             print(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = SO + ".tmp%d" % os.getpid()
-    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("nvcc link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, SO)
+    with cf.ThreadPoolExecutor(max_workers=len(SOURCES) + 1) as ex:
+        objs = list(ex.map(compile_one, SOURCES + [PEAKS_SRC]))
+    for target, parts in ((SO, objs[:-1]), (PEAKS_SO, objs[-1:])):
+        tmp = target + ".tmp%d" % os.getpid()
+        r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *parts], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc link failed:\n%s\n%s" % (r.stdout, r.stderr))
+        os.replace(tmp, target)
     return SO
 
 

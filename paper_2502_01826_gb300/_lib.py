@@ -24,7 +24,8 @@ VARIANT_ORDER_T_MID = 16
 EXPORTS = ["gsrf_workspace_size", "gsrf_workspace_layout", "gsrf_ray_state_bytes", "gsrf_project",
            "gsrf_bin", "gsrf_render_fwd", "gsrf_render_bwd", "gsrf_render", "gsrf_received_signal",
            "gsrf_read_status", "gsrf_render_static", "gsrf_batch_workspace_size", "gsrf_render_batch",
-           "gsrf_autotune_workspace_size", "gsrf_autotune", "gsrf_version"]
+           "gsrf_autotune_workspace_size", "gsrf_autotune", "gsrf_stage_times", "gsrf_version"]
+STAGE_PROJECT, STAGE_BIN, STAGE_RENDER_FWD, STAGE_RENDER_BWD, STAGE_BATCH = 0, 1, 2, 3, 4
 GSRF_MAX_BATCH_JOBS = 96
 
 
@@ -111,6 +112,7 @@ def load(build_if_missing: bool = False):
     L.gsrf_autotune_workspace_size.argtypes = [P(gsrf_plan), P(C.c_size_t)]
     L.gsrf_autotune.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, vp, vp, sz, vp, P(gsrf_tune_backward),
                                 C.c_int32, P(gsrf_tune_result), C.c_int32, P(C.c_int32), P(gsrf_tune_result), vp]
+    L.gsrf_stage_times.argtypes = [vp, P(C.c_float)]
     L.gsrf_version.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("gsrf_ray_state_bytes", "gsrf_version"):

@@ -3,6 +3,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
+#include <unordered_map>
+
 #include "gsrf_internal.cuh"
 
 namespace gsrf {
@@ -67,6 +70,83 @@ bool make_layout(const gsrf_plan* p, Layout* L) {
     L->total = off;
     return true;
 }
+
+// ---------------------------------------------------------------------------
+// Stage timers (gsrf_stage_times): per workspace, a start and an end CUDA event per
+// stage, recorded on the caller's stream around the stage's launches.  Host-side state
+// only (events, no device memory); a stream that is capturing records nothing.
+// ---------------------------------------------------------------------------
+constexpr int kStages = 8;
+constexpr size_t kMaxTimedWorkspaces = 1024;
+
+struct StageEvents {
+    int device = -1;
+    cudaEvent_t ev[2 * kStages] = {};
+    bool done[kStages] = {};
+};
+
+static std::mutex g_stage_mu;
+static std::unordered_map<const void*, StageEvents> g_stage;
+
+static void destroy_events(StageEvents& e) {
+    for (int i = 0; i < 2 * kStages; ++i)
+        if (e.ev[i]) cudaEventDestroy(e.ev[i]);
+    e = StageEvents();
+}
+
+// The events of (workspace, stage) ready to record on `st`, or null when the stream is
+// capturing or an event cannot be had (timing is then simply not kept).
+static StageEvents* stage_slot(const void* ws, cudaStream_t st) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    auto it = g_stage.find(ws);
+    if (it == g_stage.end()) {
+        if (g_stage.size() >= kMaxTimedWorkspaces) {  // forget the oldest-inserted bucket entry
+            destroy_events(g_stage.begin()->second);
+            g_stage.erase(g_stage.begin());
+        }
+        it = g_stage.emplace(ws, StageEvents()).first;
+    }
+    StageEvents& e = it->second;
+    if (e.device != dev) {
+        destroy_events(e);
+        e.device = dev;
+        for (int i = 0; i < 2 * kStages; ++i) {
+            if (cudaEventCreate(&e.ev[i]) != cudaSuccess) {
+                cudaGetLastError();
+                destroy_events(e);
+                return nullptr;
+            }
+        }
+    }
+    return &e;
+}
+
+// Records the start of `stage` on construction and its end on destruction.
+struct StageTimer {
+    StageEvents* e = nullptr;
+    int stage;
+    cudaStream_t st;
+    StageTimer(const void* ws, int stage_, cudaStream_t st_) : stage(stage_), st(st_) {
+        std::lock_guard<std::mutex> lock(g_stage_mu);
+        e = stage_slot(ws, st);
+        if (e && cudaEventRecord(e->ev[2 * stage], st) != cudaSuccess) {
+            cudaGetLastError();
+            e = nullptr;
+        }
+    }
+    ~StageTimer() {
+        if (!e) return;
+        std::lock_guard<std::mutex> lock(g_stage_mu);
+        e->done[stage] = cudaEventRecord(e->ev[2 * stage + 1], st) == cudaSuccess;
+        if (!e->done[stage]) cudaGetLastError();
+    }
+};
 
 }  // namespace gsrf
 
@@ -179,6 +259,7 @@ gsrf_status gsrf_project(const gsrf_plan* plan, const gsrf_gaussians* g, const f
     if (s != GSRF_OK) return s;
     if ((s = check_gauss(plan, g)) != GSRF_OK) return s;
     if (!rx_pos || !tx_pos) return GSRF_ERR_INVALID_ARG;
+    StageTimer tm(workspace, GSRF_STAGE_PROJECT, (cudaStream_t)stream);
     return cuda_status(launch_project(plan, L, g, rx_pos, tx_pos, workspace, (cudaStream_t)stream));
 }
 
@@ -186,6 +267,7 @@ gsrf_status gsrf_bin(const gsrf_plan* plan, void* workspace, size_t ws_bytes, vo
     Layout L;
     gsrf_status s = check_ws(plan, workspace, ws_bytes, &L);
     if (s != GSRF_OK) return s;
+    StageTimer tm(workspace, GSRF_STAGE_BIN, (cudaStream_t)stream);
     return cuda_status(launch_bin(plan, L, workspace, (cudaStream_t)stream));
 }
 
@@ -197,6 +279,7 @@ gsrf_status gsrf_render_fwd(const gsrf_plan* plan, const gsrf_gaussians* g, void
     if ((s = check_gauss(plan, g)) != GSRF_OK) return s;
     if (!out_rays || ((uintptr_t)out_rays & 7) != 0 || ((uintptr_t)ray_state & 15) != 0)
         return GSRF_ERR_INVALID_ARG;
+    StageTimer tm(workspace, GSRF_STAGE_RENDER_FWD, (cudaStream_t)stream);
     return cuda_status(launch_render_fwd(plan, L, g, workspace, out_rays, ray_state, (cudaStream_t)stream));
 }
 
@@ -212,6 +295,7 @@ gsrf_status gsrf_render_bwd(const gsrf_plan* plan, const gsrf_gaussians* g, void
         return GSRF_ERR_INVALID_ARG;
     if (plan->variant != 0 || plan_degree(plan) != 3)
         return GSRF_ERR_UNSUPPORTED;  // the adjoint of the default reading and degree only
+    StageTimer tm(workspace, GSRF_STAGE_RENDER_BWD, (cudaStream_t)stream);
     return cuda_status(launch_render_bwd(plan, L, g, workspace, ray_state, grad_rays, g_means, g_log_scales, g_quats,
                                          g_opacity_logit, g_coeffs, g_phase_b, (cudaStream_t)stream));
 }
@@ -249,6 +333,7 @@ gsrf_status gsrf_render_batch(int32_t n_jobs, const gsrf_plan* plans, void* cons
         if (plan_degree(&plans[j]) != 3 || (plans[j].variant & (GSRF_VARIANT_PATH_AT_REP | GSRF_VARIANT_ORDER_T_MID)))
             return GSRF_ERR_UNSUPPORTED;
     }
+    StageTimer tm(batch_ws, GSRF_STAGE_BATCH, (cudaStream_t)stream);
     return cuda_status(launch_render_batch(n_jobs, plans, workspaces, outs, batch_ws, (cudaStream_t)stream));
 }
 
@@ -271,6 +356,32 @@ gsrf_status gsrf_read_status(const void* workspace, size_t ws_bytes, gsrf_run_st
     out->required_pairs = h.required_pairs;
     for (int i = 0; i < 4; ++i) out->stats[i] = (int64_t)h.stats[i];
     return GSRF_OK;
+}
+
+gsrf_status gsrf_stage_times(const void* workspace, float* ms) {
+    if (!workspace || !ms) return GSRF_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_stage_mu);
+    auto it = g_stage.find(workspace);
+    if (it == g_stage.end()) return GSRF_ERR_INVALID_ARG;
+    const StageEvents& e = it->second;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GSRF_ERR_CUDA;
+    if (dev != e.device && cudaSetDevice(e.device) != cudaSuccess) return GSRF_ERR_CUDA;
+    gsrf_status s = GSRF_OK;
+    for (int i = 0; i < kStages; ++i) {
+        ms[i] = -1.0f;
+        if (!e.done[i]) continue;
+        float t = 0.0f;
+        if (cudaEventSynchronize(e.ev[2 * i + 1]) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e.ev[2 * i], e.ev[2 * i + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            s = GSRF_ERR_CUDA;
+            continue;
+        }
+        ms[i] = t;
+    }
+    if (dev != e.device) cudaSetDevice(dev);
+    return s;
 }
 
 }  // extern "C"

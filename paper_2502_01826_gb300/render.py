@@ -185,6 +185,14 @@ class Renderer:
             return s.required_pairs
         raise L.GsrfError("ensure_capacity", L.GSRF_ERR_CAPACITY)
 
+    def stage_times(self) -> dict:
+        """Milliseconds of the last project, bin, forward and backward render on this
+        workspace (gsrf_stage_times; a stage never run is absent).  Synchronises."""
+        ms = (C.c_float * 8)()
+        L.call("gsrf_stage_times", _ptr(self.ws), ms)
+        names = ["project", "bin", "render_fwd", "render_bwd", "batch"]
+        return {n: float(ms[i]) for i, n in enumerate(names) if ms[i] >= 0.0}
+
     def layout(self) -> L.gsrf_layout:
         lay = L.gsrf_layout()
         L.call("gsrf_workspace_layout", C.byref(self.plan), C.byref(lay))

@@ -18,3 +18,11 @@ def oracle_lib():
     import oracle
     oracle.build()
     return oracle
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    mod = sys.modules.get("gpu_util")
+    if mod is None:
+        return
+    for line in mod.parity_summary():
+        terminalreporter.write_line(line)

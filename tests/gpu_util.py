@@ -1,6 +1,11 @@
 """Helpers shared by the GPU parity tests: run the CUDA path through the C ABI, run
-the oracle on the same seeded inputs, compare with the stated tolerances."""
+the oracle on the same seeded inputs, compare with the stated tolerances.  Every
+comparison is recorded in PARITY (test, rays compared and excluded, L2, worst per-ray
+ratio, rays outside the plain relative bar); conftest prints the summary at the end of
+the run."""
 from __future__ import annotations
+
+import os
 
 import numpy as np
 import torch
@@ -26,9 +31,12 @@ TOL_DB = 0.01
 # of the 3-sigma boundary, the exit point within 1e-5 m of the emitting sphere,
 # ln prod(1 - alpha) within 4 times its propagated error (+1e-5) of ln eps_T.  A ray
 # with one such decision must match the oracle with that decision taken either way;
-# a ray with two or more is not compared (and counted).
+# a ray with two or more is not compared (and counted): at most 0.1% of the rays (+1).
 BANDS = (1e-6, 1e-7, 4.0, 1e-5, 4.0, 1e-5)
-MAX_EXCLUDED = 0.02
+MAX_EXCLUDED = 1e-3
+# The plain per-ray bar |dS| <= 1e-4 (|S_ref| + 1e-2 rms(S_ref)) is reported beside the
+# conditioning-aware one for every comparison (rays outside it: "plain_bar_misses").
+PARITY: list = []
 
 
 def oracle_pair(scene, rx, tx, f0, grid, rays=None, **kw):
@@ -92,11 +100,49 @@ def compare(S_gpu: np.ndarray, ref: dict, f: int = 0, tol_l2=TOL_L2, tol_ray=TOL
     l2 = np.linalg.norm(a - b) / nb if nb > 0 else (np.max(err) if err.size else 0.0)
     worst = np.max(err / (bound[keep] + 1e-30)) * tol_ray if a.size else 0.0
     excluded = int((~keep).sum())
+    rms = np.sqrt(np.mean(np.abs(b) ** 2)) if b.size else 0.0
+    plain_miss = int(np.sum(err > tol_ray * (np.abs(b) + 1e-2 * rms))) if a.size else 0
+    rec = dict(test=os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0], l2=float(l2),
+               worst=float(worst), compared=int(keep.sum()), excluded=excluded,
+               ambiguous=int((namb == 1).sum()), plain_bar_misses=plain_miss)
+    PARITY.append(rec)
     assert l2 <= tol_l2, "relative L2 error %.3g > %.3g" % (l2, tol_l2)
     assert worst <= tol_ray, "worst per-ray error %.3g > %.3g" % (worst, tol_ray)
-    assert excluded <= max_excluded * len(keep) + 1, "%d rays excluded" % excluded
-    return dict(l2=l2, worst=worst, compared=int(keep.sum()), excluded=excluded,
-                ambiguous=int((namb == 1).sum()))
+    assert excluded <= max_excluded * len(keep) + 1, "%d of %d rays excluded" % (excluded, len(keep))
+    return rec
+
+
+def oracle_choice(S_gpu: np.ndarray, ref: dict, f: int = 0) -> np.ndarray:
+    """The oracle's rays at frequency index f with, on every ray holding an in-band
+    discrete decision, whichever of the two readings of it (``oracle_pair``) lies closer
+    to the GPU's ray: the reference for sums over rays (CSI, RSSI)."""
+    S_ref = ref["S"][f].copy()
+    if "S_alt" in ref:
+        alt = ref["S_alt"][f]
+        use_alt = ((ref["flags"] >> 8) >= 1) & (np.abs(S_gpu - alt) < np.abs(S_gpu - S_ref))
+        S_ref[use_alt] = alt[use_alt]
+    return S_ref
+
+
+def parity_summary() -> list[str]:
+    """Lines summarising every comparison of the run (printed by conftest)."""
+    if not PARITY:
+        return []
+    comp = sum(r["compared"] for r in PARITY)
+    excl = sum(r["excluded"] for r in PARITY)
+    amb = sum(r["ambiguous"] for r in PARITY)
+    miss = sum(r["plain_bar_misses"] for r in PARITY)
+    w = max(PARITY, key=lambda r: r["worst"])
+    l2 = max(PARITY, key=lambda r: r["l2"])
+    fr = max(PARITY, key=lambda r: r["excluded"] / max(1, r["compared"] + r["excluded"]))
+    return ["parity vs the FP64 oracle: %d comparisons, %d rays compared, %d excluded (%.2g%%; largest share "
+            "%.2g%% in %s), %d compared with one decision taken either way"
+            % (len(PARITY), comp, excl, 100.0 * excl / max(1, comp + excl),
+               100.0 * fr["excluded"] / max(1, fr["compared"] + fr["excluded"]), fr["test"], amb),
+            "  largest relative L2 %.3g (%s); worst per-ray error %.3g of the 1e-4 bar (%s)"
+            % (l2["l2"], l2["test"], w["worst"] / TOL_RAY, w["test"]),
+            "  rays outside the plain bar 1e-4 (|S| + 1e-2 rms): %d of %d (%.3g%%)"
+            % (miss, comp, 100.0 * miss / max(1, comp))]
 
 
 def rssi_db(S) -> float:

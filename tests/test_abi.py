@@ -282,3 +282,11 @@ def test_batch_and_tuned_backward_refuse_the_forward_only_readings(lib):
     n = C.c_int32()
     assert lib.gsrf_autotune(C.byref(p), C.byref(g), dev, dev, dev, tsz.value, dev, C.byref(bwd), 3, None, 0,
                              C.byref(n), C.byref(best), None) == L.GSRF_ERR_UNSUPPORTED
+
+
+def test_stage_times_argument_checks(lib):
+    # no CUDA call is reached: a workspace no stage was recorded on is refused first
+    ms = (C.c_float * 8)()
+    assert lib.gsrf_stage_times(None, ms) == L.GSRF_ERR_INVALID_ARG
+    assert lib.gsrf_stage_times(C.c_void_p(4096), None) == L.GSRF_ERR_INVALID_ARG
+    assert lib.gsrf_stage_times(C.c_void_p(4096), ms) == L.GSRF_ERR_INVALID_ARG

@@ -2,8 +2,9 @@
 the FP64 distance-to-phase step, against the FP64 oracle.
 
 Per subcarrier the per-ray bars of gpu_util apply; the CSI value of a receiver (the
-complex sum over rays per subcarrier) must sit within the sum of its rays' bounds; the
-stored path phase must be within 1e-6 rad of the oracle's FP64 phase."""
+complex sum over rays per subcarrier) is held per (element, subcarrier) to 1e-4 of its
+own magnitude plus 1e-2 of the element's rms over subcarriers; the stored path phase
+must be within 1e-6 rad of the oracle's FP64 phase."""
 import numpy as np
 import pytest
 import torch
@@ -13,7 +14,7 @@ from paper_2502_01826_gb300 import _lib as L
 from paper_2502_01826_gb300 import synthetic
 from paper_2502_01826_gb300.render import Renderer, make_grid, received_signal, to_device
 
-from gpu_util import COND_MULT, TOL_RAY, compare, oracle_pair, require_gpu
+from gpu_util import TOL_RAY, compare, oracle_choice, oracle_pair, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -54,10 +55,13 @@ def test_subcarriers_match_oracle(n_f):
             compare(S[r, f].reshape(-1), ref, f=f)
         # CSI: complex sum over rays per subcarrier, through the library's reduction
         cs = received_signal(out, L.SIG_COMPLEX_SUM).cpu().numpy()[r]
-        bound = np.sum(TOL_RAY * ref["Sabs"] + COND_MULT * ref["Scond"])
-        for f in range(n_f):
-            ref_sum = np.sum(ref["S"][f])
-            assert abs(cs[f, 0] + 1j * cs[f, 1] - ref_sum) <= bound + 1e-6 * abs(ref_sum)
+        got = cs[:, 0] + 1j * cs[:, 1]
+        want = np.array([np.sum(oracle_choice(S[r, f].reshape(-1), ref, f)) for f in range(n_f)])
+        rms = np.sqrt(np.mean(np.abs(want) ** 2))
+        ratio = np.abs(got - want) / (TOL_RAY * (np.abs(want) + 1e-2 * rms))
+        print("CSI element %d, %d subcarriers: worst error %.3g of the bar, relative L2 %.3g"
+              % (r, n_f, ratio.max(), np.linalg.norm(got - want) / np.linalg.norm(want)))
+        assert ratio.max() <= 1.0, ratio
 
 
 def test_csi_100k_full_size_and_phase_step():

@@ -232,3 +232,38 @@ def test_angular_resolutions_full_size(spec):
         rays = np.sort(rng.choice(S.shape[1], 300, replace=False)).astype(np.int32)
         ref = oracle_pair(cfg["scene"], rx[r], cfg["tx"], cfg["f0"], g, rays=rays)
         compare(S[r, rays], ref)
+
+
+# --------------------------------------------------------------------------- stage timers
+
+def test_stage_times_report_each_stage_of_the_last_call():
+    """gsrf_stage_times: every stage that ran on the workspace has a positive time, the
+    forward's stages add up to about the time CUDA events see around the same calls, and a
+    stage never run on this workspace is absent."""
+    cfg = synthetic.config_ble(n_rx=4)
+    K = cfg["scene"]["means"].shape[0]
+    p = to_device(cfg["scene"])
+    rx = torch.tensor(cfg["rx"], device="cuda")
+    tx = torch.tensor(cfg["tx"], device="cuda")
+    R = Renderer(K, rx.shape[0], make_grid(**cfg["grid"]), cfg["f0"])
+    R.ensure_capacity(p, rx, tx)
+    out = torch.empty(R.out_shape(), dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    R.forward(p, rx, tx, out)  # warm
+    a.record(s)
+    R.project(p, rx, tx)
+    R.bin()
+    R.render_fwd(p, out)
+    b.record(s)
+    t = R.stage_times()
+    assert set(t) == {"project", "bin", "render_fwd"}, t
+    assert all(v > 0.0 for v in t.values()), t
+    total = a.elapsed_time(b)
+    assert 0.7 * total <= sum(t.values()) <= 1.05 * total + 0.05, (t, total)
+    state = R.ray_state()
+    R.render_fwd(p, out, ray_state=state)
+    grads = {k: torch.zeros_like(v) for k, v in p.items()}
+    R.render_bwd(p, state, torch.ones_like(out), grads)
+    t2 = R.stage_times()
+    assert t2["render_bwd"] > 0.0 and t2["project"] == t["project"], t2

@@ -1021,3 +1021,125 @@ def test_tmid_order_keeps_the_product_of_transmittances(oracle_lib):
     assert np.array_equal(o0["nhit"], o16["nhit"])
     assert np.allclose(o16["T"], o0["T"], rtol=1e-11, atol=1e-14)
     assert np.abs(o16["S"] - o0["S"]).max() > 1e-3 * np.abs(o0["S"]).max()
+
+
+# --------------------------------------------------------------------------- rounding model
+# The parity bound of the GPU tests holds each ray to 1e-4 Sabs + 4 Scond, where Scond
+# is the oracle's first-order propagation of an error delta_k = 1e-6 sqrt(C_k) + 1e-7 in
+# every composited pair's closest approach m2 (through its weight, 1 - alpha of the pairs
+# behind it and the chord's transmittance phase).  These pins tie both halves to
+# something other than the oracle's own formula: delta_k to the error an FP32 evaluation
+# of m2 actually makes, and Scond to the change of S that moving each m2 by delta_k
+# actually causes in the FP64 render.
+
+PARITY_BANDS = (1e-6, 1e-7, 4.0, 1e-5, 4.0, 1e-5)  # the GPU parity tests' bands (tests/gpu_util.py)
+
+
+def _ray_dirs(g, rays):
+    u, v = rays % g.n_az, rays // g.n_az
+    az = np.radians(g.az0_deg + (u + 0.5) * g.daz_deg)
+    el = np.radians(g.el0_deg + (v + 0.5) * g.del_deg)
+    return np.stack([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)], -1)
+
+
+def _sensitivity(oracle, scene, rx, tx, f0, g, rays):
+    """Per ray: the unperturbed render, and sum_j max_{+-} |S(m2_j +- delta_j) - S|, the
+    size of the error when every composited pair's m2 is off by delta_j with the worst
+    signs (first order), from one perturbed FP64 render per pair index and sign."""
+    ref = oracle.render(scene, rx, tx, f0, g, rays=rays, bands=PARITY_BANDS)
+    J = int(ref["nhit"].max())
+    S0 = ref["S"][0]
+    lin = np.zeros(len(rays))
+    for j in range(J):
+        worst = np.zeros(len(rays))
+        for sgn in (1.0, -1.0):
+            sh = np.zeros((len(rays), J))
+            sh[:, j] = sgn
+            Sj = oracle.render(scene, rx, tx, f0, g, rays=rays, bands=PARITY_BANDS, m2_shift=sh)["S"][0]
+            worst = np.maximum(worst, np.abs(Sj - S0))
+        lin += worst
+    return ref, lin, J
+
+
+@pytest.mark.parametrize("case", ["plain_2k", "dense_6k"])
+def test_scond_bounds_the_effect_of_m2_errors_and_is_not_loose(oracle_lib, case):
+    oracle = oracle_lib
+    if case == "plain_2k":
+        cfg = synthetic.config_plain()
+        scene, rx, tx, f0 = cfg["scene"], cfg["rx"][0], cfg["tx"], cfg["f0"]
+        g = oracle.make_grid(**cfg["grid"])
+        rays = np.arange(g.n_az * g.n_el, dtype=np.int32)
+    else:  # deeper walks: a denser scene on the 1-degree grid, sampled rays
+        scene = synthetic.tiny_scene(6000, 77, box=(5.0, 4.0, 3.0), log_scale_mu=math.log(0.15))
+        rx, tx, f0 = np.array([2.5, 2.0, 1.5], np.float32), np.array([0.3, 3.7, 2.6], np.float32), 2.4e9
+        g = oracle.make_grid(360, 90)
+        rays = np.sort(np.random.default_rng(5).choice(360 * 90, 240, replace=False)).astype(np.int32)
+    ref, lin, J = _sensitivity(oracle, scene, rx, tx, f0, g, rays)
+    sc = ref["Scond"]
+    ok = (ref["flags"] == 0) & (ref["nhit"] > 0)
+    assert ok.sum() >= 0.9 * (ref["nhit"] > 0).sum() and ok.sum() >= 100 and J >= 5
+    # Scond bounds the first-order effect: up to the factor 1.5 by which a chord clipped at
+    # the emitting sphere can exceed the model's unclipped derivatives, always within the
+    # 4 Scond the parity bound allows
+    assert np.all(lin[ok] <= 4.0 * sc[ok] + 1e-15), np.max(lin[ok] / sc[ok])
+    assert np.mean(lin[ok] <= 1.5 * sc[ok] + 1e-15) >= 0.99
+    # and is not loose: on the typical ray it is within a small factor of the actual effect
+    r = sc[ok & (lin > 0)] / lin[ok & (lin > 0)]
+    assert np.median(r) <= 10.0, np.median(r)
+    assert np.percentile(r, 90) <= 30.0, np.percentile(r, 90)
+    # random signs stay inside the worst-sign sum (and so inside the bound)
+    sh = np.random.default_rng(6).choice([-1.0, 1.0], size=(len(rays), J))
+    Sr = oracle.render(scene, rx, tx, f0, g, rays=rays, bands=PARITY_BANDS, m2_shift=sh)["S"][0]
+    d = np.abs(Sr - ref["S"][0])
+    assert np.all(d[ok] <= 1.05 * lin[ok] + 1e-15)
+    assert np.all(d[ok] <= 4.0 * sc[ok] + 1e-15)
+
+
+def _m2_fp32(scene, k, r, v):
+    """m2 of ray r + t v against Gaussian k evaluated in FP32 the way the kernels do:
+    W = diag(1/s) R^T from the normalised quaternion, w = W (r - mu), v' = W v, and
+    m2 = |w x v'|^2 / |v'|^2 (Lagrange's identity), every operation rounded to FP32."""
+    f = np.float32
+    q = scene["quats"][k].astype(f)
+    q = (q / f(np.sqrt(np.sum(q * q, dtype=f)))).astype(f)
+    w_, x, y, z = q
+    two, one = f(2), f(1)
+    R = np.array([[one - two * (y * y + z * z), two * (x * y - w_ * z), two * (x * z + w_ * y)],
+                  [two * (x * y + w_ * z), one - two * (x * x + z * z), two * (y * z - w_ * x)],
+                  [two * (x * z - w_ * y), two * (y * z + w_ * x), one - two * (x * x + y * y)]], f)
+    s = np.exp(scene["log_scales"][k].astype(f)).astype(f)
+    W = (R.T / s[:, None]).astype(f)
+    w = (W @ (r.astype(f) - scene["means"][k].astype(f))).astype(f)
+    vp = (W @ v.astype(f)).astype(f)
+    c = np.cross(w, vp).astype(f)
+    return float(np.sum(c * c, dtype=f) / np.sum(vp * vp, dtype=f)), float(np.sum(w.astype(np.float64) ** 2))
+
+
+def test_m2_rounding_model_matches_an_fp32_evaluation(oracle_lib):
+    """delta_k = 1e-6 sqrt(C_k) + 1e-7, the m2 error the parity bands and Scond assume, is
+    the size of the error an FP32 evaluation of m2 makes: it covers nearly every hit pair
+    and is not far above the typical error."""
+    oracle = oracle_lib
+    cfg = synthetic.config_plain()
+    scene, rx = cfg["scene"], cfg["rx"][0].astype(np.float64)
+    g = oracle.make_grid(**cfg["grid"])
+    rays = np.arange(g.n_az * g.n_el)
+    dirs = _ray_dirs(g, rays).astype(np.float32)
+    rng = np.random.default_rng(12)
+    errs, deltas = [], []
+    for k in rng.choice(scene["means"].shape[0], 400, replace=False):
+        _, Sinv, _ = oracle.gaussian(scene, int(k))
+        mu = scene["means"][k].astype(np.float64)
+        for v in dirs:
+            hit, h = oracle.intersect(Sinv, mu, rx, v.astype(np.float64), 1.0)
+            if not (h["m2"] < 9.0):
+                continue
+            m2_32, _ = _m2_fp32(scene, k, cfg["rx"][0], v)
+            errs.append(abs(m2_32 - h["m2"]))
+            deltas.append(1e-6 * math.sqrt(h["C"]) + 1e-7)
+    errs, deltas = np.array(errs), np.array(deltas)
+    assert len(errs) > 200
+    assert np.mean(errs <= deltas) >= 0.95
+    assert np.mean(errs <= 4.0 * deltas) >= 0.999  # the band: 4 delta_k
+    ratio = deltas / np.maximum(errs, 1e-12)
+    assert np.median(ratio) <= 100.0, np.median(ratio)
