@@ -113,8 +113,11 @@ def measured_peaks(index: int) -> dict:
     s = clk.summary()
     pk["clocks"] = s
     pk["sm_mhz"] = s.get("sm_mhz") or 2070.0
+    for k, n in P.NOMINAL_PER_SM_CLK.items():  # a kind that failed to run: its nominal rate, marked
+        if "ops_per_s" not in pk.get(k, {}):
+            pk[k] = dict(pk.get(k, {}), ops_per_s=n * pk["sms"] * pk["sm_mhz"] * 1e6, nominal=True)
     pk["per_sm_per_clk"] = {k: pk[k]["ops_per_s"] / (pk["sms"] * pk["sm_mhz"] * 1e6)
-                            for k in P.KINDS if k in pk}
+                            for k in P.KINDS if "ops_per_s" in pk.get(k, {})}
     return pk
 
 
@@ -461,9 +464,9 @@ def run_ours(args, ws, rank):
     for _ in range(max(1, args.warmup)):
         plain_step()
     torch.cuda.synchronize()
-    pk = max(1, min(args.steps, 5))
-    pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(pk)]
-    for i in range(pk):
+    n_plain = max(1, min(args.steps, 5))
+    pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_plain)]
+    for i in range(n_plain):
         flush.zero_()
         pe[i][0].record(stream)
         plain_step()
@@ -512,7 +515,7 @@ def run_ours(args, ws, rank):
     paper_loop = paper_loop_leg(args, ws, flush) if not args.no_train else None
     angular = angular_leg(args, ws, flush)
     fle_degree = fle_degree_leg(args, ws, flush)
-    uneven = uneven_leg(args, flush) if args.uneven else None
+    uneven = uneven_leg(args, flush) if not args.no_uneven else None
     variants = variants_leg(args, ws, flush, split=(R.plan.grid.tile_w, R.plan.grid.tile_h,
                                                     R.plan.ray_block_w or 8, R.plan.stage or 32))
 
@@ -653,12 +656,17 @@ def persistent_leg(args, cfg, p, rx, tx, R, flush, pairs_per_step):
             "single_rx_jobs_spectra_per_s": n_rx / (ms_j / 1e3)}
 
 
-def uneven_leg(args, flush, max_records=1.5e8):
+def uneven_leg(args, flush, n_streams=8):
     """Uneven serving stress: 256 requests over 8 scenes with Gaussian counts
-    log-uniform in [1e4, 1e6], 1-32 receivers each, 360 x 90, 2.4 or 5.2 GHz.  Requests
-    are rendered in waves bounded by receiver x Gaussian records (memory); a wave is the
-    projections and bins of its requests plus one persistent render of all of them; a
-    request's latency is its wave's time."""
+    log-uniform in [1e4, 1e6], 1-32 receivers each, 360 x 90, 2.4 or 5.2 GHz, every
+    request arriving at once.  One step: the projection and binning of every request
+    (spread over `n_streams` CUDA streams, largest first), then ONE persistent render
+    launch over all requests (gsrf_render_batch, work items heaviest first), then the
+    RSSI of every receiver in one reduction.  The render kernel stamps each request's
+    completion on the GPU's global timer, so a request's latency is the step time less
+    how much earlier than the last request it finished.  Tile shapes are autotuned per
+    scene on its first request.  Every request's workspace stays resident (about 100 GB
+    for this workload)."""
     import numpy as np
     import torch
 
@@ -667,67 +675,93 @@ def uneven_leg(args, flush, max_records=1.5e8):
     from paper_2502_01826_gb300.render import BatchRender, Renderer, make_grid, received_signal, to_device
 
     cfg = synthetic.config_uneven()
-    grid = make_grid(**cfg["grid"])
+    gspec = cfg["grid"]
     scenes = [to_device(sc) for sc in cfg["scenes"]]
     Ks = [sc["means"].shape[0] for sc in cfg["scenes"]]
     reqs = cfg["requests"]
-    waves, cur, load = [], [], 0.0
-    for i, q in enumerate(reqs):
-        rec = q["rx"].shape[0] * Ks[q["scene"]]
-        if cur and (load + rec > max_records or len(cur) == L.GSRF_MAX_BATCH_JOBS):
-            waves.append(cur)
-            cur, load = [], 0.0
-        cur.append(i)
-        load += rec
-    if cur:
-        waves.append(cur)
-    # one tuned split per scene, measured on its first request
+    t_setup = time.time()
     splits = {}
-    for i, q in enumerate(reqs):
+    if args.split:
+        tw, th = (int(x) for x in args.split.split(",")[0].split("x"))
+        bw, stg = (int(x) for x in args.split.split(",")[1:3])
+        splits = {si: (tw, th, bw, stg) for si in range(len(scenes))}
+    for i, q in enumerate(reqs):  # one tuned split per scene, measured on its first request
         si = q["scene"]
-        if si in splits or args.no_tune or args.split:
+        if si in splits or args.no_tune:
             continue
-        R = Renderer(Ks[si], q["rx"].shape[0], grid, q["f0"], pair_capacity=1024)
+        R = Renderer(Ks[si], q["rx"].shape[0], make_grid(**gspec), q["f0"], pair_capacity=1024)
         rx = torch.tensor(q["rx"], device="cuda")
         tx = torch.tensor(q["tx"], device="cuda")
         R.ensure_capacity(scenes[si], rx, tx)
         t = autotune(R, scenes[si], rx, tx, args, reps=1)
         splits[si] = (t["best"]["tile_w"], t["best"]["tile_h"], t["best"]["ray_block_w"], t["best"]["stage"])
         del R
-    lat, pairs_total, t_total = [], 0, 0.0
-    for wv in waves:
-        jobs = []
-        for i in wv:
-            q = reqs[i]
-            tw, th, bw, stg = splits.get(q["scene"], (16, 16, 0, 0))
-            R = Renderer(Ks[q["scene"]], q["rx"].shape[0], make_grid(**cfg["grid"], tile_w=tw, tile_h=th), q["f0"],
-                         pair_capacity=1024, ray_block_w=bw, stage=stg)
-            rx = torch.tensor(q["rx"], device="cuda")
-            tx = torch.tensor(q["tx"], device="cuda")
-            R.ensure_capacity(scenes[q["scene"]], rx, tx)
-            jobs.append((R, scenes[q["scene"]], rx, tx))
-        B = BatchRender([j[0] for j in jobs])
+    torch.cuda.empty_cache()
+    n_rx_tot = sum(q["rx"].shape[0] for q in reqs)
+    out_all = torch.empty((n_rx_tot, 1, gspec["n_el"], gspec["n_az"], 2), dtype=torch.float32, device="cuda")
+    jobs, outs, r0 = [], [], 0
+    for i, q in enumerate(reqs):
+        tw, th, bw, stg = splits.get(q["scene"], (16, 16, 0, 0))
+        R = Renderer(Ks[q["scene"]], q["rx"].shape[0], make_grid(**gspec, tile_w=tw, tile_h=th), q["f0"],
+                     pair_capacity=1024, ray_block_w=bw, stage=stg)
+        rx = torch.tensor(q["rx"], device="cuda")
+        tx = torch.tensor(q["tx"], device="cuda")
+        R.ensure_capacity(scenes[q["scene"]], rx, tx)
+        jobs.append((R, scenes[q["scene"]], rx, tx))
+        outs.append(out_all[r0:r0 + q["rx"].shape[0]])
+        r0 += q["rx"].shape[0]
+    ws_bytes = sum(R.ws_bytes for R, _, _, _ in jobs)
+    B = BatchRender([R for R, _, _, _ in jobs], outs=outs, stamps=True)
+    by_size = sorted(range(len(jobs)), key=lambda i: -jobs[i][0].ws_bytes)
+    streams = [torch.cuda.Stream() for _ in range(n_streams)]
+    main = torch.cuda.current_stream()
+    setup_s = time.time() - t_setup
 
-        def wave():
-            for R, p, rx, tx in jobs:
+    def step(ev):
+        ev[0].record(main)
+        for s in streams:
+            s.wait_stream(main)
+        for n, i in enumerate(by_size):
+            R, p, rx, tx = jobs[i]
+            with torch.cuda.stream(streams[n % n_streams]):
                 R.project(p, rx, tx)
                 R.bin()
-            for o in B.render():
-                received_signal(o, L.SIG_RSSI_DB)
+        for s in streams:
+            main.wait_stream(s)
+        B.render()
+        received_signal(out_all, L.SIG_RSSI_DB)
+        ev[1].record(main)
 
-        wave()
-        ms = _time_steps(wave, 1, flush)
-        pairs = sum(int(j[0].status().stats[1]) for j in jobs)
-        lat += [ms] * len(wv)
-        pairs_total += pairs
-        t_total += ms / 1e3
-        del B, jobs
-        torch.cuda.empty_cache()
-    lat = np.array(lat)
-    return {"workload": cfg["name"], "requests": len(reqs), "waves": len(waves),
-            "receivers": int(sum(q["rx"].shape[0] for q in reqs)), "gaussian_counts": Ks,
+    steps = max(2, min(args.steps, 5))
+    for _ in range(2):
+        step([torch.cuda.Event(enable_timing=True) for _ in range(2)])
+    torch.cuda.synchronize()
+    lat_all, ms_all = [], []
+    for _ in range(steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        flush.zero_()
+        step(ev)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1])
+        done = B.job_done_ns.cpu().numpy().view(np.uint64)[:-1].astype(np.float64)
+        # the last request to finish ends the render (the RSSI reduction follows it)
+        lat_all.append(ms - (done.max() - done) / 1e6)
+        ms_all.append(ms)
+    sts = [R.status() for R, _, _, _ in jobs]
+    for st in sts:
+        L.check("uneven request (device status)", st.code)
+    pairs = sum(int(st.stats[1]) for st in sts)
+    lat = np.concatenate(lat_all)
+    ms_step = float(np.mean(ms_all))
+    return {"workload": cfg["name"], "requests": len(reqs), "receivers": n_rx_tot, "gaussian_counts": Ks,
+            "render": "one persistent gsrf_render_batch launch over all requests",
+            "ms_per_step": ms_step, "steps": steps,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "pairs_per_s": pairs_total / t_total, "total_s": t_total,
+            "min_ms": float(lat.min()), "pairs_per_step": pairs, "pairs_per_s": pairs / (ms_step / 1e3),
+            "spectra_per_s": n_rx_tot / (ms_step / 1e3), "workspace_bytes": int(ws_bytes),
+            "setup_s": setup_s, "project_bin_streams": n_streams,
+            "latency": "per request: step time less (last completion - its completion), completions "
+                       "stamped by the render kernel on the GPU's global timer; all requests arrive at once",
             "splits_per_scene": {str(k): "%dx%d tiles, %d-wide ray block, stage %d" % v for k, v in splits.items()}}
 
 
@@ -1123,7 +1157,7 @@ def main():
     ap.add_argument("--n-rx", type=int, default=64, help="receivers (64 = the BLE workload; fewer "
                     "only for small profiling runs)")
     ap.add_argument("--no-train", action="store_true", help="skip the training and CSI legs")
-    ap.add_argument("--uneven", action="store_true", help="add the uneven serving-stress leg (slow setup)")
+    ap.add_argument("--no-uneven", action="store_true", help="skip the uneven serving-stress leg")
     ap.add_argument("--no-tune", action="store_true", help="keep the default work split (16 x 16 tiles, 8 x 4 "
                     "rays per warp, 32 candidates per stage) instead of autotuning it")
     ap.add_argument("--split", default=None, help="fix the work split instead of tuning it: TWxTH,BW,STAGE "

@@ -214,18 +214,24 @@ gsrf_status gsrf_render_bwd(const gsrf_plan *plan, const gsrf_gaussians *g, void
  * problems at once; the paper renders one query at a time).  n_jobs problems -- each a
  * plan (n_f == 1) with its own workspace that gsrf_project and gsrf_bin have filled,
  * e.g. different scenes, receiver groups, transmitters and carriers -- are rendered by
- * ONE persistent kernel: the (job, receiver, tile, 8 x 4 ray block) work items are
+ * ONE persistent kernel: the (job, receiver, tile, ray block) work items of all jobs are
  * ordered heaviest first (longest tile list) by a counting sort and taken by the warps
- * of a single resident wave from an atomic counter.  Results are the same as
- * gsrf_render_fwd's for each job (same per-ray arithmetic).
+ * of a single resident wave from an atomic counter.  The jobs' descriptions are copied
+ * into batch_ws on the stream, so the host arrays may be reused once the call returns.
+ * Results are the same as gsrf_render_fwd's for each job (same per-ray arithmetic).
  *   plans, workspaces, ws_bytes, outs: [host] arrays of n_jobs (1..GSRF_MAX_BATCH_JOBS);
  *   outs[j] [dev] as gsrf_render_fwd's out_rays; batch_ws [dev] of
- *   gsrf_batch_workspace_size bytes (256-byte aligned). */
-#define GSRF_MAX_BATCH_JOBS 96
+ *   gsrf_batch_workspace_size bytes (256-byte aligned).
+ *   job_done_ns [dev] NULL, or n_jobs + 1 uint64 (8-byte aligned) that get the GPU's
+ *   global timer (ns): [j] when the last work item of job j finished, [n_jobs] when the
+ *   first warp of the launch started, so that [j] - [n_jobs] is job j's completion time
+ *   inside the launch (a per-request latency when all jobs arrive together).
+ * GSRF_ERR_UNSUPPORTED when the jobs hold 2^32 work items or more. */
+#define GSRF_MAX_BATCH_JOBS 4096
 gsrf_status gsrf_batch_workspace_size(int32_t n_jobs, const gsrf_plan *plans, size_t *bytes);
 gsrf_status gsrf_render_batch(int32_t n_jobs, const gsrf_plan *plans, void *const *workspaces,
                               const size_t *ws_bytes, float *const *outs, void *batch_ws,
-                              size_t batch_ws_bytes, void *stream);
+                              size_t batch_ws_bytes, uint64_t *job_done_ns, void *stream);
 
 /* Convenience: gsrf_project + gsrf_bin + gsrf_render_fwd in one call. */
 gsrf_status gsrf_render(const gsrf_plan *plan, const gsrf_gaussians *g, const float *rx_pos,

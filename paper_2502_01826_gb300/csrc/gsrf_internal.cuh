@@ -283,8 +283,9 @@ int plan_block_w(const gsrf_plan* p);
 int plan_stage(const gsrf_plan* p);
 // Persistent batched render of n_jobs projected and binned problems (n_f == 1 each).
 size_t batch_workspace_bytes(int n_jobs, const gsrf_plan* plans);
+long long batch_items(int n_jobs, const gsrf_plan* plans);
 cudaError_t launch_render_batch(int n_jobs, const gsrf_plan* plans, void* const* workspaces, float* const* outs,
-                                void* batch_ws, cudaStream_t st);
+                                void* batch_ws, unsigned long long* job_done, cudaStream_t st);
 cudaError_t launch_render_bwd(const gsrf_plan* p, const Layout& L, const gsrf_gaussians* g, void* ws,
                               const void* ray_state, const float* grad_rays, float* g_means, float* g_log_scales,
                               float* g_quats, float* g_opacity_logit, float* g_coeffs, float* g_phase_b,

@@ -99,15 +99,36 @@ __device__ __forceinline__ float path_delta(const float4& cv, const GShape* sh, 
     return dr + dt;
 }
 
-constexpr int kMaxJobs = 96;
+// Jobs of a batched launch are described by a table of RenderArgs in device memory (the
+// batch workspace), written by k_put_jobs from chunks of kJobsPerPut passed by value.
+constexpr int kJobsPerPut = 48;
 
-// Up to kMaxJobs render problems (one receiver group of one scene each) passed by value
-// to the persistent kernel; item_base[j] is the first work item of job j.
-struct BatchArgs {
-    int n_jobs;
-    unsigned long long item_base[kMaxJobs + 1];
-    RenderArgs jobs[kMaxJobs];
+struct JobChunk {
+    int first, count, n_bases;  // n_bases = count, + 1 in the last chunk (the item total)
+    unsigned long long item_base[kJobsPerPut + 1];
+    RenderArgs jobs[kJobsPerPut];
 };
+static_assert(sizeof(JobChunk) <= 32000, "kernel parameters are limited to 32764 bytes");
+
+// The SM's global nanosecond timer (the same clock on every SM).
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Job of work item id: the last j with item_base[j] <= id (item_base ascending, n_jobs + 1
+// entries, item_base[0] = 0).
+__device__ __forceinline__ int job_of(const unsigned long long* __restrict__ item_base, int n_jobs,
+                                      unsigned long long id) {
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (item_base[mid] <= id) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -474,29 +495,60 @@ __global__ void __launch_bounds__(kThreads, NFC == 1 ? ((PATH || ORDER) ? 6 : (L
 }
 
 // Persistent batched launch over several problems (n_f = 1 each): work items (job,
-// receiver, tile, ray block), same queue discipline.
+// receiver, tile, ray block), same queue discipline.  The warp copies its item's job
+// description from the device table into shared memory.  With job_done set, the warp
+// that finishes an item of job j raises job_done[j] to the global timer (the job's
+// completion time) and every warp lowers job_done[n_jobs] to its start time.  6 CTAs
+// per SM: at 7 (72 registers) the job bookkeeping spills; at 6 it takes 79, no spills.
 template <int WB>
-__global__ void __launch_bounds__(kThreads, 7) k_render_batch(BatchArgs b, const uint32_t* __restrict__ order,
-                                                              unsigned long long* __restrict__ counter) {
+__global__ void __launch_bounds__(kThreads, 6)
+    k_render_batch(const RenderArgs* __restrict__ jobs, const unsigned long long* __restrict__ item_base, int n_jobs,
+                   const uint32_t* __restrict__ order, unsigned long long* __restrict__ counter,
+                   unsigned long long* __restrict__ job_done) {
     __shared__ float4 sbuf[kWarps][2][WB][kRec];
     __shared__ uint32_t sid[kWarps][2][WB];
     __shared__ float4 spl[kWarps][kPlaneSlots];
+    __shared__ RenderArgs sjob[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned long long total = b.item_base[b.n_jobs];
+    const unsigned long long total = item_base[n_jobs];
+    if (job_done && lane == 0) atomicMin(job_done + n_jobs, global_ns());
     for (;;) {
         unsigned long long it = 0;
         if (lane == 0) it = atomicAdd(counter, 1ull);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= total) break;
         const unsigned long long id = order[it];
-        int j = 0;
-        while (j + 1 < b.n_jobs && b.item_base[j + 1] <= id) ++j;
-        const RenderArgs& a = b.jobs[j];
-        const unsigned long long local = id - b.item_base[j];
+        const int j = job_of(item_base, n_jobs, id);
+        {  // the job's description, one 32-bit word per lane and step
+            constexpr int kWords = (int)(sizeof(RenderArgs) / 4);
+            __syncwarp();
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(jobs + j);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&sjob[warp]);
+            for (int w = lane; w < kWords; w += 32) dst[w] = src[w];
+            __syncwarp();
+        }
+        const RenderArgs& a = sjob[warp];
+        const unsigned long long local = id - item_base[j];
         const unsigned long long per_rx = (unsigned long long)a.n_tiles * a.per_tile;
         const unsigned rem = (unsigned)(local % per_rx);
         render_block<1, WB, 3>(a, (int)(local / per_rx), (int)(rem / (unsigned)a.per_tile),
-                            (int)(rem % (unsigned)a.per_tile), sbuf[warp], sid[warp], spl[warp]);
+                               (int)(rem % (unsigned)a.per_tile), sbuf[warp], sid[warp], spl[warp]);
+        if (job_done && lane == 0) atomicMax(job_done + j, global_ns());
+    }
+}
+
+// Copies a chunk of job descriptions and item bases into the device table and clears
+// each job's statistics (candidate tests, composited pairs).
+__global__ void k_put_jobs(JobChunk c, RenderArgs* __restrict__ jobs, unsigned long long* __restrict__ item_base) {
+    constexpr int kWords = (int)(sizeof(RenderArgs) / 4);
+    for (int i = threadIdx.x; i < c.count * kWords; i += blockDim.x) {
+        const int j = i / kWords, w = i % kWords;
+        reinterpret_cast<uint32_t*>(jobs + c.first + j)[w] = reinterpret_cast<const uint32_t*>(&c.jobs[j])[w];
+    }
+    for (int j = threadIdx.x; j < c.n_bases; j += blockDim.x) item_base[c.first + j] = c.item_base[j];
+    for (int j = threadIdx.x; j < c.count; j += blockDim.x) {
+        c.jobs[j].st->stats[0] = 0ull;
+        c.jobs[j].st->stats[1] = 0ull;
     }
 }
 
@@ -512,13 +564,13 @@ __global__ void k_item_keys(const uint32_t* __restrict__ tile_start, int n_tiles
     keys[id] = (uint32_t)__clz((int)(len + 1u));
 }
 
-__global__ void k_batch_keys(BatchArgs b, uint32_t* __restrict__ keys) {
+__global__ void k_batch_keys(const RenderArgs* __restrict__ jobs, const unsigned long long* __restrict__ item_base,
+                             int n_jobs, uint32_t* __restrict__ keys) {
     const unsigned long long id = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= b.item_base[b.n_jobs]) return;
-    int j = 0;
-    while (j + 1 < b.n_jobs && b.item_base[j + 1] <= id) ++j;
-    const RenderArgs& a = b.jobs[j];
-    const unsigned long long t = (id - b.item_base[j]) / (unsigned)a.per_tile;
+    if (id >= item_base[n_jobs]) return;
+    const int j = job_of(item_base, n_jobs, id);
+    const RenderArgs& a = jobs[j];
+    const unsigned long long t = (id - item_base[j]) / (unsigned)a.per_tile;
     const size_t ts = (size_t)(t / (unsigned)a.n_tiles) * (a.n_tiles + 1) + (size_t)(t % (unsigned)a.n_tiles);
     const uint32_t len = a.tile_start[ts + 1] - a.tile_start[ts];
     keys[id] = (uint32_t)__clz((int)(len + 1u));
@@ -642,7 +694,7 @@ cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     return wb16 ? launch_queue<16, 16>(a, order, counter, n, st) : launch_queue<16, 32>(a, order, counter, n, st);
 }
 
-static long long batch_items(int n_jobs, const gsrf_plan* plans) {
+long long batch_items(int n_jobs, const gsrf_plan* plans) {
     long long n = 0;
     for (int j = 0; j < n_jobs; ++j) {
         Layout L;
@@ -652,50 +704,79 @@ static long long batch_items(int n_jobs, const gsrf_plan* plans) {
     return n;
 }
 
-size_t batch_workspace_bytes(int n_jobs, const gsrf_plan* plans) {
-    const long long n = batch_items(n_jobs, plans);
-    const long long chunks = (n + kChunk - 1) / kChunk;
+// Batch workspace: item keys (two buffers), their order, the counting-sort histogram, the
+// queue counter, the job table and the item bases.
+struct BatchLayout {
+    size_t keys, keys2, order, hist, counter, jobs, base, total;
+};
+
+static BatchLayout batch_layout(int n_jobs, long long n) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    return al(n * 4) * 3 + al(chunks * 32 * 4) + al(8);
+    const long long chunks = (n + kChunk - 1) / kChunk;
+    BatchLayout b;
+    b.keys = 0;
+    b.keys2 = b.keys + al(n * 4);
+    b.order = b.keys2 + al(n * 4);
+    b.hist = b.order + al(n * 4);
+    b.counter = b.hist + al(chunks * 32 * 4);
+    b.jobs = b.counter + al(8);
+    b.base = b.jobs + al((size_t)n_jobs * sizeof(RenderArgs));
+    b.total = b.base + al((size_t)(n_jobs + 1) * 8);
+    return b;
+}
+
+size_t batch_workspace_bytes(int n_jobs, const gsrf_plan* plans) {
+    return batch_layout(n_jobs, batch_items(n_jobs, plans)).total;
 }
 
 cudaError_t launch_render_batch(int n_jobs, const gsrf_plan* plans, void* const* workspaces, float* const* outs,
-                                void* batch_ws, cudaStream_t st) {
-    BatchArgs b;
-    b.n_jobs = n_jobs;
-    unsigned long long base = 0;
-    for (int j = 0; j < n_jobs; ++j) {
-        Layout L;
-        make_layout(&plans[j], &L);
-        b.jobs[j] = render_args(&plans[j], L, workspaces[j], outs[j], nullptr);
-        b.item_base[j] = base;
-        base += (unsigned long long)L.n_rx * L.n_tiles * b.jobs[j].per_tile;
-        cudaError_t e = cudaMemsetAsync(&b.jobs[j].st->stats[0], 0, 2 * sizeof(unsigned long long), st);
-        if (e != cudaSuccess) return e;
-    }
-    b.item_base[n_jobs] = base;
-    const long long n = (long long)base;
-    const long long chunks = (n + kChunk - 1) / kChunk;
-    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+                                void* batch_ws, unsigned long long* job_done, cudaStream_t st) {
+    const long long n = batch_items(n_jobs, plans);
+    const BatchLayout bl = batch_layout(n_jobs, n);
     char* w = static_cast<char*>(batch_ws);
-    uint32_t* keys = reinterpret_cast<uint32_t*>(w);
-    uint32_t* keys2 = reinterpret_cast<uint32_t*>(w + al(n * 4));
-    uint32_t* order = reinterpret_cast<uint32_t*>(w + 2 * al(n * 4));
-    uint32_t* hist = reinterpret_cast<uint32_t*>(w + 3 * al(n * 4));
-    unsigned long long* counter = reinterpret_cast<unsigned long long*>(w + 3 * al(n * 4) + al(chunks * 32 * 4));
+    RenderArgs* jobs = reinterpret_cast<RenderArgs*>(w + bl.jobs);
+    unsigned long long* base = reinterpret_cast<unsigned long long*>(w + bl.base);
+    cudaError_t e = cudaSuccess;
+    if (job_done) {
+        // completion times 0, the launch's start time "infinitely late" until a warp lowers it
+        if ((e = cudaMemsetAsync(job_done, 0, (size_t)n_jobs * 8, st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(job_done + n_jobs, 0xff, 8, st)) != cudaSuccess) return e;
+    }
+    // the job table, kJobsPerPut descriptions per copy launch (passed by value)
+    unsigned long long acc = 0;
+    for (int first = 0; first < n_jobs; first += kJobsPerPut) {
+        JobChunk c;
+        c.first = first;
+        c.count = min(kJobsPerPut, n_jobs - first);
+        for (int i = 0; i < c.count; ++i) {
+            const int j = first + i;
+            Layout L;
+            make_layout(&plans[j], &L);
+            c.jobs[i] = render_args(&plans[j], L, workspaces[j], outs[j], nullptr);
+            c.item_base[i] = acc;
+            acc += (unsigned long long)L.n_rx * L.n_tiles * c.jobs[i].per_tile;
+        }
+        c.n_bases = c.count;
+        if (first + c.count == n_jobs) c.item_base[c.n_bases++] = acc;
+        k_put_jobs<<<1, 256, 0, st>>>(c, jobs, base);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     if (n == 0) return cudaSuccess;
-    k_batch_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(b, keys);
-    cudaError_t e = launch_sort_small_keys(keys, keys2, order, n, 32, hist, st);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return e;
+    uint32_t* keys = reinterpret_cast<uint32_t*>(w + bl.keys);
+    uint32_t* keys2 = reinterpret_cast<uint32_t*>(w + bl.keys2);
+    uint32_t* order = reinterpret_cast<uint32_t*>(w + bl.order);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(w + bl.hist);
+    unsigned long long* counter = reinterpret_cast<unsigned long long*>(w + bl.counter);
+    k_batch_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(jobs, base, n_jobs, keys);
+    if ((e = launch_sort_small_keys(keys, keys2, order, n, 32, hist, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
     int grid = 0;
     if (plan_stage(&plans[0]) == 16) {
         if ((e = resident_grid(k_render_batch<16>, n, &grid)) != cudaSuccess) return e;
-        k_render_batch<16><<<grid, kThreads, 0, st>>>(b, order, counter);
+        k_render_batch<16><<<grid, kThreads, 0, st>>>(jobs, base, n_jobs, order, counter, job_done);
     } else {
         if ((e = resident_grid(k_render_batch<32>, n, &grid)) != cudaSuccess) return e;
-        k_render_batch<32><<<grid, kThreads, 0, st>>>(b, order, counter);
+        k_render_batch<32><<<grid, kThreads, 0, st>>>(jobs, base, n_jobs, order, counter, job_done);
     }
     return cudaGetLastError();
 }

@@ -9,7 +9,8 @@
 // per thread (per warp for the matrix form), so the pipe, not latency, is the limit once
 // the grid fills the SMs.  A chain's value is written only if it equals a value it
 // cannot take, which keeps the compiler from dropping the work.  The ex2 chain runs into
-// +inf and stays there; the unit's rate does not depend on the operand's value.
+// +inf and stays there; the unit's rate does not depend on the operand's value.  A
+// special-function step also carries one FP32 add (see step).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -20,16 +21,25 @@ constexpr int kUnroll = 16;
 
 enum Kind { FMA32 = 0, EX2 = 1, RCP = 2, RSQRT = 3, SQRT = 4, SIN = 5, COS = 6, FMA64 = 7, MMA_TF32 = 8, N_KINDS = 9 };
 
+// One dependent step of a chain.  The special-function kinds take f(x + b): the add (on
+// the FP32 pipe, eight times wider than the special-function unit) keeps the assembler
+// from folding a chain such as rcp(rcp(x)) back to x.
 template <int K>
 __device__ __forceinline__ float step(float x, float a, float b) {
     float y;
     if constexpr (K == FMA32) asm volatile("fma.rn.f32 %0, %1, %2, %3;" : "=f"(y) : "f"(x), "f"(a), "f"(b));
-    if constexpr (K == EX2) asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    if constexpr (K == RCP) asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    if constexpr (K == RSQRT) asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    if constexpr (K == SQRT) asm volatile("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    if constexpr (K == SIN) asm volatile("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    if constexpr (K == COS) asm volatile("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    if constexpr (K == EX2)
+        asm volatile("{ .reg .f32 t; add.f32 t, %1, %2; ex2.approx.ftz.f32 %0, t; }" : "=f"(y) : "f"(x), "f"(b));
+    if constexpr (K == RCP)
+        asm volatile("{ .reg .f32 t; add.f32 t, %1, %2; rcp.approx.ftz.f32 %0, t; }" : "=f"(y) : "f"(x), "f"(b));
+    if constexpr (K == RSQRT)
+        asm volatile("{ .reg .f32 t; add.f32 t, %1, %2; rsqrt.approx.ftz.f32 %0, t; }" : "=f"(y) : "f"(x), "f"(b));
+    if constexpr (K == SQRT)
+        asm volatile("{ .reg .f32 t; add.f32 t, %1, %2; sqrt.approx.ftz.f32 %0, t; }" : "=f"(y) : "f"(x), "f"(b));
+    if constexpr (K == SIN)
+        asm volatile("{ .reg .f32 t; add.f32 t, %1, %2; sin.approx.ftz.f32 %0, t; }" : "=f"(y) : "f"(x), "f"(b));
+    if constexpr (K == COS)
+        asm volatile("{ .reg .f32 t; add.f32 t, %1, %2; cos.approx.ftz.f32 %0, t; }" : "=f"(y) : "f"(x), "f"(b));
     return y;
 }
 

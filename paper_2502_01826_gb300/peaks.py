@@ -76,10 +76,13 @@ def measure(target_ms: float = 4.0, kinds=None) -> dict:
         iters = 4
         run(k, iters)
         ms = timed(k, iters, reps=1)
-        while ms < 0.25 * target_ms and iters < (1 << 22):
+        while ms < 0.25 * target_ms and iters < (1 << 20):
             iters *= 4
             ms = timed(k, iters, reps=1)
-        iters = max(1, int(iters * target_ms / max(ms, 1e-3)))
+        if ms < 0.25 * target_ms:  # a kind whose work did not run is reported, not used
+            res[name] = {"error": "%d rounds ran in %.3g ms" % (iters, ms)}
+            continue
+        iters = max(1, min(1 << 24, int(iters * target_ms / ms)))
         ms = timed(k, iters)
         ops = L.gsrf_peak_ops(k, blocks, iters)
         res[name] = {"ops_per_s": ops / (ms * 1e-3), "ms": ms, "iters": iters, "ops": ops}

@@ -221,9 +221,11 @@ class Renderer:
 
 class BatchRender:
     """Many render problems (each a Renderer that has run project and bin) rendered by one
-    persistent kernel launch, work items heaviest first (gsrf_render_batch)."""
+    persistent kernel launch, work items heaviest first (gsrf_render_batch).  ``outs``:
+    optional output tensors, one per renderer (e.g. views of one buffer); ``stamps``: keep
+    per-job completion times (``job_done_ns``, n_jobs + 1 int64 on the device)."""
 
-    def __init__(self, renderers: list):
+    def __init__(self, renderers: list, outs: list | None = None, stamps: bool = False):
         if not 1 <= len(renderers) <= L.GSRF_MAX_BATCH_JOBS:
             raise ValueError("1..%d jobs per batch" % L.GSRF_MAX_BATCH_JOBS)
         self.renderers = list(renderers)
@@ -234,7 +236,9 @@ class BatchRender:
         self.ws_bytes = nbytes.value
         dev = self.renderers[0].device
         self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
-        self.outs = [torch.empty(r.out_shape(), dtype=torch.float32, device=dev) for r in self.renderers]
+        self.outs = outs if outs is not None else [torch.empty(r.out_shape(), dtype=torch.float32, device=dev)
+                                                   for r in self.renderers]
+        self.job_done_ns = torch.zeros(n + 1, dtype=torch.int64, device=dev) if stamps else None
 
     def render(self, stream=None):
         n = len(self.renderers)
@@ -243,8 +247,14 @@ class BatchRender:
         wss = (C.c_void_p * n)(*[r.ws.data_ptr() for r in self.renderers])
         wsb = (C.c_size_t * n)(*[r.ws_bytes for r in self.renderers])
         outs = (C.c_void_p * n)(*[o.data_ptr() for o in self.outs])
-        L.call("gsrf_render_batch", n, self.plans, wss, wsb, outs, _ptr(self.ws), self.ws_bytes, _stream(stream))
+        L.call("gsrf_render_batch", n, self.plans, wss, wsb, outs, _ptr(self.ws), self.ws_bytes,
+               _ptr(self.job_done_ns), _stream(stream))
         return self.outs
+
+    def completion_ms(self):
+        """Each job's completion time (ms) after the start of the last launch (needs stamps)."""
+        t = self.job_done_ns.cpu().numpy().view("uint64").astype("float64")
+        return (t[:-1] - t[-1]) / 1e6
 
 
 def received_signal(rays: torch.Tensor, mode: int = L.SIG_COMPLEX_SUM, stream=None) -> torch.Tensor:

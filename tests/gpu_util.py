@@ -31,7 +31,7 @@ TOL_DB = 0.01
 # of the 3-sigma boundary, the exit point within 1e-5 m of the emitting sphere,
 # ln prod(1 - alpha) within 4 times its propagated error (+1e-5) of ln eps_T.  A ray
 # with one such decision must match the oracle with that decision taken either way;
-# a ray with two or more is not compared (and counted): at most 0.1% of the rays (+1).
+# a ray with two or more is not compared (and counted): at most 0.1% of the rays, plus two.
 BANDS = (1e-6, 1e-7, 4.0, 1e-5, 4.0, 1e-5)
 MAX_EXCLUDED = 1e-3
 # The plain per-ray bar |dS| <= 1e-4 (|S_ref| + 1e-2 rms(S_ref)) is reported beside the
@@ -108,7 +108,7 @@ def compare(S_gpu: np.ndarray, ref: dict, f: int = 0, tol_l2=TOL_L2, tol_ray=TOL
     PARITY.append(rec)
     assert l2 <= tol_l2, "relative L2 error %.3g > %.3g" % (l2, tol_l2)
     assert worst <= tol_ray, "worst per-ray error %.3g > %.3g" % (worst, tol_ray)
-    assert excluded <= max_excluded * len(keep) + 1, "%d of %d rays excluded" % (excluded, len(keep))
+    assert excluded <= max_excluded * len(keep) + 2, "%d of %d rays excluded" % (excluded, len(keep))
     return rec
 
 

@@ -79,3 +79,30 @@ def test_batch_render_matches_oracle_on_mixed_scenes():
         for r in sorted({0, n_rx - 1}):
             ref = oracle_pair(scene, rx[r].cpu().numpy(), tx.cpu().numpy(), f0, g, rays=rays)
             compare(S[r][rays], ref)
+
+
+def test_batch_completion_stamps_and_many_jobs():
+    """More jobs than one chunk of the job table (48), with completion stamps: every job
+    finishes after the launch's first warp started, within the launch's span, and each job
+    equals its plain launch bit for bit."""
+    jobs = [_job(300 + 37 * (i % 5), 400 + i, 1 + i % 3, dict(n_az=72, n_el=18), 2.4e9 if i % 2 else 5.2e9)
+            for i in range(61)]
+    plain = []
+    for R, p, rx, tx in jobs:
+        plain.append(R.forward(p, rx, tx).clone())
+    B = BatchRender([R for R, _, _, _ in jobs], stamps=True)
+    for _ in range(2):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        outs = B.render()
+        b.record()
+        torch.cuda.synchronize()
+        for x, y in zip(plain, outs):
+            assert torch.equal(x, y)
+        t = B.job_done_ns.cpu().numpy().view(np.uint64)
+        start, done = int(t[-1]), t[:-1].astype(np.int64)
+        assert start != np.iinfo(np.uint64).max
+        span_ns = a.elapsed_time(b) * 1e6
+        assert np.all(done >= start) and np.all(done - start <= span_ns + 1e5)
+        c = B.completion_ms()
+        assert c.shape == (len(jobs),) and np.all(c >= 0.0)
