@@ -267,3 +267,17 @@ def test_stage_times_report_each_stage_of_the_last_call():
     R.render_bwd(p, state, torch.ones_like(out), grads)
     t2 = R.stage_times()
     assert t2["render_bwd"] > 0.0 and t2["project"] == t["project"], t2
+
+
+@pytest.mark.parametrize("K", [150_000, 260_000])
+def test_bins_bit_exact_at_large_scenes(K):
+    """Scenes larger than the benchmark's (150k and 260k Gaussians, two receivers, 360 x
+    90): keys, ids and tile ranges equal the oracle's bit for bit (dozens of sort chunks
+    per receiver in every pass)."""
+    cfg = synthetic.config_ble(K=K, n_rx=2)
+    spec = dict(cfg["grid"])
+    K_ = cfg["scene"]["means"].shape[0]
+    R = Renderer(K_, 2, make_grid(**spec), cfg["f0"])
+    p = to_device(cfg["scene"])
+    R.ensure_capacity(p, torch.tensor(cfg["rx"], device="cuda"), torch.tensor(cfg["tx"], device="cuda"))
+    check_bins(R, cfg["scene"], cfg["rx"], spec)
