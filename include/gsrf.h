@@ -226,12 +226,17 @@ gsrf_status gsrf_render_bwd(const gsrf_plan *plan, const gsrf_gaussians *g, void
  *   global timer (ns): [j] when the last work item of job j finished, [n_jobs] when the
  *   first warp of the launch started, so that [j] - [n_jobs] is job j's completion time
  *   inside the launch (a per-request latency when all jobs arrive together).
+ *   flags: 0, or GSRF_BATCH_JOB_ORDER: the queue takes the jobs in the given order
+ *   (heaviest first inside each job) instead of heaviest first over all jobs, so that a
+ *   caller who orders its jobs (e.g. by deadline, or by size for shortest-first) gets
+ *   them completed roughly in that order; results are the same either way.
  * GSRF_ERR_UNSUPPORTED when the jobs hold 2^32 work items or more. */
 #define GSRF_MAX_BATCH_JOBS 4096
+#define GSRF_BATCH_JOB_ORDER 1
 gsrf_status gsrf_batch_workspace_size(int32_t n_jobs, const gsrf_plan *plans, size_t *bytes);
 gsrf_status gsrf_render_batch(int32_t n_jobs, const gsrf_plan *plans, void *const *workspaces,
                               const size_t *ws_bytes, float *const *outs, void *batch_ws,
-                              size_t batch_ws_bytes, uint64_t *job_done_ns, void *stream);
+                              size_t batch_ws_bytes, uint64_t *job_done_ns, int32_t flags, void *stream);
 
 /* Convenience: gsrf_project + gsrf_bin + gsrf_render_fwd in one call. */
 gsrf_status gsrf_render(const gsrf_plan *plan, const gsrf_gaussians *g, const float *rx_pos,

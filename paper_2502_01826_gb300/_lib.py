@@ -27,6 +27,7 @@ EXPORTS = ["gsrf_workspace_size", "gsrf_workspace_layout", "gsrf_ray_state_bytes
            "gsrf_autotune_workspace_size", "gsrf_autotune", "gsrf_stage_times", "gsrf_version"]
 STAGE_PROJECT, STAGE_BIN, STAGE_RENDER_FWD, STAGE_RENDER_BWD, STAGE_BATCH = 0, 1, 2, 3, 4
 GSRF_MAX_BATCH_JOBS = 4096
+BATCH_JOB_ORDER = 1
 
 
 class GsrfError(RuntimeError):
@@ -108,7 +109,7 @@ def load(build_if_missing: bool = False):
     L.gsrf_read_status.argtypes = [vp, sz, P(gsrf_run_status), vp]
     L.gsrf_render_static.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, vp, vp, P(gsrf_run_status), vp]
     L.gsrf_batch_workspace_size.argtypes = [C.c_int32, P(gsrf_plan), P(C.c_size_t)]
-    L.gsrf_render_batch.argtypes = [C.c_int32, P(gsrf_plan), P(vp), P(C.c_size_t), P(vp), vp, sz, vp, vp]
+    L.gsrf_render_batch.argtypes = [C.c_int32, P(gsrf_plan), P(vp), P(C.c_size_t), P(vp), vp, sz, vp, C.c_int32, vp]
     L.gsrf_autotune_workspace_size.argtypes = [P(gsrf_plan), P(C.c_size_t)]
     L.gsrf_autotune.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, vp, vp, sz, vp, P(gsrf_tune_backward),
                                 C.c_int32, P(gsrf_tune_result), C.c_int32, P(C.c_int32), P(gsrf_tune_result), vp]

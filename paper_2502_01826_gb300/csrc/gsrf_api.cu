@@ -321,7 +321,7 @@ gsrf_status gsrf_batch_workspace_size(int32_t n_jobs, const gsrf_plan* plans, si
 
 gsrf_status gsrf_render_batch(int32_t n_jobs, const gsrf_plan* plans, void* const* workspaces, const size_t* ws_bytes,
                               float* const* outs, void* batch_ws, size_t batch_ws_bytes, uint64_t* job_done_ns,
-                              void* stream) {
+                              int32_t flags, void* stream) {
     size_t need = 0;
     gsrf_status s = gsrf_batch_workspace_size(n_jobs, plans, &need);
     if (s != GSRF_OK) return s;
@@ -334,11 +334,12 @@ gsrf_status gsrf_render_batch(int32_t n_jobs, const gsrf_plan* plans, void* cons
         if (plan_degree(&plans[j]) != 3 || (plans[j].variant & (GSRF_VARIANT_PATH_AT_REP | GSRF_VARIANT_ORDER_T_MID)))
             return GSRF_ERR_UNSUPPORTED;
     }
-    if (((uintptr_t)job_done_ns & 7) != 0) return GSRF_ERR_INVALID_ARG;
+    if (((uintptr_t)job_done_ns & 7) != 0 || (flags & ~GSRF_BATCH_JOB_ORDER) != 0) return GSRF_ERR_INVALID_ARG;
     if (batch_items(n_jobs, plans) >= (1ll << 32)) return GSRF_ERR_UNSUPPORTED;  // 32-bit item ids
     StageTimer tm(batch_ws, GSRF_STAGE_BATCH, (cudaStream_t)stream);
     return cuda_status(launch_render_batch(n_jobs, plans, workspaces, outs, batch_ws,
-                                           reinterpret_cast<unsigned long long*>(job_done_ns), (cudaStream_t)stream));
+                                           reinterpret_cast<unsigned long long*>(job_done_ns),
+                                           (flags & GSRF_BATCH_JOB_ORDER) != 0, (cudaStream_t)stream));
 }
 
 gsrf_status gsrf_received_signal(const float* rays, int32_t n_rx, int32_t n_f, int32_t n_el, int32_t n_az,

@@ -273,6 +273,9 @@ cudaError_t launch_signal(const float* rays, int n_rx, int n_f, int n_el, int n_
                           float* out, cudaStream_t st);
 cudaError_t launch_sort_small_keys(const uint32_t* keys, uint32_t* keys_out, uint32_t* vals_out, long long n,
                                    int nbins, uint32_t* hist, cudaStream_t st);
+cudaError_t launch_sort_small_keys_segmented(const uint32_t* keys, uint32_t* keys_out, uint32_t* vals_out, int n_seg,
+                                             const long long* seg_base, const uint32_t* chunk_base, long long chunks,
+                                             int nbins, uint32_t* hist, cudaStream_t st);
 // Work items of a render launch: item id = ((r * n_tiles + tile) * per_tile + k), k < per_tile
 // (ray block and subcarrier chunk).  Writes the heaviest-first order of the n_rx * n_tiles *
 // per_tile items into the workspace's queue buffers and zeroes the queue counter.
@@ -285,7 +288,7 @@ int plan_stage(const gsrf_plan* p);
 size_t batch_workspace_bytes(int n_jobs, const gsrf_plan* plans);
 long long batch_items(int n_jobs, const gsrf_plan* plans);
 cudaError_t launch_render_batch(int n_jobs, const gsrf_plan* plans, void* const* workspaces, float* const* outs,
-                                void* batch_ws, unsigned long long* job_done, cudaStream_t st);
+                                void* batch_ws, unsigned long long* job_done, bool job_order, cudaStream_t st);
 cudaError_t launch_render_bwd(const gsrf_plan* p, const Layout& L, const gsrf_gaussians* g, void* ws,
                               const void* ray_state, const float* grad_rays, float* g_means, float* g_log_scales,
                               float* g_quats, float* g_opacity_logit, float* g_coeffs, float* g_phase_b,

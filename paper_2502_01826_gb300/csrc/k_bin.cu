@@ -502,6 +502,23 @@ cudaError_t launch_sort_small_keys(const uint32_t* keys, uint32_t* keys_out, uin
     return cudaGetLastError();
 }
 
+// The same per segment: n_seg segments of items [seg_base[s], seg_base[s + 1]) (device),
+// chunk_base = the prefix of their ceil(length / kChunk) (device, n_seg + 1 entries),
+// chunks = chunk_base[n_seg].  vals_out gets each item's index inside its segment, in
+// key order within the segment.  hist needs chunks * nbins words.
+cudaError_t launch_sort_small_keys_segmented(const uint32_t* keys, uint32_t* keys_out, uint32_t* vals_out, int n_seg,
+                                             const long long* seg_base, const uint32_t* chunk_base, long long chunks,
+                                             int nbins, uint32_t* hist, cudaStream_t st) {
+    if (chunks == 0) return cudaSuccess;
+    Segs sg{n_seg, -1, 0, seg_base, chunk_base};
+    k_hist<uint32_t><<<(unsigned)chunks, kSortThreads, 0, st>>>(keys, sg, 0, (uint32_t)(nbins - 1), nbins, hist,
+                                                                nullptr);
+    k_scan<<<n_seg, kSortThreads, 0, st>>>(sg, nbins, hist, nullptr, nullptr);
+    launch_scatter<uint32_t>((unsigned)chunks, keys, nullptr, keys_out, vals_out, sg, 0, (uint32_t)(nbins - 1), nbins,
+                             hist, nullptr, st);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream_t st) {
     DevStatus* status = at<DevStatus>(ws, L.status);
     const size_t nts = (size_t)L.n_rx * (L.n_tiles + 1);

@@ -106,6 +106,7 @@ constexpr int kJobsPerPut = 48;
 struct JobChunk {
     int first, count, n_bases;  // n_bases = count, + 1 in the last chunk (the item total)
     unsigned long long item_base[kJobsPerPut + 1];
+    uint32_t chunk_base[kJobsPerPut + 1];  // prefix of ceil(items / kChunk) (the job-order sort)
     RenderArgs jobs[kJobsPerPut];
 };
 static_assert(sizeof(JobChunk) <= 32000, "kernel parameters are limited to 32764 bytes");
@@ -500,11 +501,14 @@ __global__ void __launch_bounds__(kThreads, NFC == 1 ? ((PATH || ORDER) ? 6 : (L
 // that finishes an item of job j raises job_done[j] to the global timer (the job's
 // completion time) and every warp lowers job_done[n_jobs] to its start time.  6 CTAs
 // per SM: at 7 (72 registers) the job bookkeeping spills; at 6 it takes 79, no spills.
+// job_order: the order holds, for queue position `it`, an item's index inside the job
+// whose range of positions holds `it` (jobs taken in their given order, heaviest first
+// inside each); otherwise the item's global id (heaviest first over all jobs).
 template <int WB>
 __global__ void __launch_bounds__(kThreads, 6)
     k_render_batch(const RenderArgs* __restrict__ jobs, const unsigned long long* __restrict__ item_base, int n_jobs,
                    const uint32_t* __restrict__ order, unsigned long long* __restrict__ counter,
-                   unsigned long long* __restrict__ job_done) {
+                   unsigned long long* __restrict__ job_done, int job_order) {
     __shared__ float4 sbuf[kWarps][2][WB][kRec];
     __shared__ uint32_t sid[kWarps][2][WB];
     __shared__ float4 spl[kWarps][kPlaneSlots];
@@ -517,8 +521,15 @@ __global__ void __launch_bounds__(kThreads, 6)
         if (lane == 0) it = atomicAdd(counter, 1ull);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= total) break;
-        const unsigned long long id = order[it];
-        const int j = job_of(item_base, n_jobs, id);
+        int j;
+        unsigned long long id;
+        if (job_order) {
+            j = job_of(item_base, n_jobs, it);
+            id = item_base[j] + order[it];
+        } else {
+            id = order[it];
+            j = job_of(item_base, n_jobs, id);
+        }
         {  // the job's description, one 32-bit word per lane and step
             constexpr int kWords = (int)(sizeof(RenderArgs) / 4);
             __syncwarp();
@@ -539,13 +550,17 @@ __global__ void __launch_bounds__(kThreads, 6)
 
 // Copies a chunk of job descriptions and item bases into the device table and clears
 // each job's statistics (candidate tests, composited pairs).
-__global__ void k_put_jobs(JobChunk c, RenderArgs* __restrict__ jobs, unsigned long long* __restrict__ item_base) {
+__global__ void k_put_jobs(JobChunk c, RenderArgs* __restrict__ jobs, unsigned long long* __restrict__ item_base,
+                           uint32_t* __restrict__ chunk_base) {
     constexpr int kWords = (int)(sizeof(RenderArgs) / 4);
     for (int i = threadIdx.x; i < c.count * kWords; i += blockDim.x) {
         const int j = i / kWords, w = i % kWords;
         reinterpret_cast<uint32_t*>(jobs + c.first + j)[w] = reinterpret_cast<const uint32_t*>(&c.jobs[j])[w];
     }
-    for (int j = threadIdx.x; j < c.n_bases; j += blockDim.x) item_base[c.first + j] = c.item_base[j];
+    for (int j = threadIdx.x; j < c.n_bases; j += blockDim.x) {
+        item_base[c.first + j] = c.item_base[j];
+        chunk_base[c.first + j] = c.chunk_base[j];
+    }
     for (int j = threadIdx.x; j < c.count; j += blockDim.x) {
         c.jobs[j].st->stats[0] = 0ull;
         c.jobs[j].st->stats[1] = 0ull;
@@ -704,15 +719,16 @@ long long batch_items(int n_jobs, const gsrf_plan* plans) {
     return n;
 }
 
-// Batch workspace: item keys (two buffers), their order, the counting-sort histogram, the
-// queue counter, the job table and the item bases.
+// Batch workspace: item keys (two buffers), their order, the counting-sort histogram (per
+// job chunks in job order), the queue counter, the job table, the item bases and the
+// jobs' first sort chunks.
 struct BatchLayout {
-    size_t keys, keys2, order, hist, counter, jobs, base, total;
+    size_t keys, keys2, order, hist, counter, jobs, base, cbase, total;
 };
 
 static BatchLayout batch_layout(int n_jobs, long long n) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const long long chunks = (n + kChunk - 1) / kChunk;
+    const long long chunks = (n + kChunk - 1) / kChunk + n_jobs;
     BatchLayout b;
     b.keys = 0;
     b.keys2 = b.keys + al(n * 4);
@@ -721,7 +737,8 @@ static BatchLayout batch_layout(int n_jobs, long long n) {
     b.counter = b.hist + al(chunks * 32 * 4);
     b.jobs = b.counter + al(8);
     b.base = b.jobs + al((size_t)n_jobs * sizeof(RenderArgs));
-    b.total = b.base + al((size_t)(n_jobs + 1) * 8);
+    b.cbase = b.base + al((size_t)(n_jobs + 1) * 8);
+    b.total = b.cbase + al((size_t)(n_jobs + 1) * 4);
     return b;
 }
 
@@ -730,12 +747,13 @@ size_t batch_workspace_bytes(int n_jobs, const gsrf_plan* plans) {
 }
 
 cudaError_t launch_render_batch(int n_jobs, const gsrf_plan* plans, void* const* workspaces, float* const* outs,
-                                void* batch_ws, unsigned long long* job_done, cudaStream_t st) {
+                                void* batch_ws, unsigned long long* job_done, bool job_order, cudaStream_t st) {
     const long long n = batch_items(n_jobs, plans);
     const BatchLayout bl = batch_layout(n_jobs, n);
     char* w = static_cast<char*>(batch_ws);
     RenderArgs* jobs = reinterpret_cast<RenderArgs*>(w + bl.jobs);
     unsigned long long* base = reinterpret_cast<unsigned long long*>(w + bl.base);
+    uint32_t* cbase = reinterpret_cast<uint32_t*>(w + bl.cbase);
     cudaError_t e = cudaSuccess;
     if (job_done) {
         // completion times 0, the launch's start time "infinitely late" until a warp lowers it
@@ -744,6 +762,7 @@ cudaError_t launch_render_batch(int n_jobs, const gsrf_plan* plans, void* const*
     }
     // the job table, kJobsPerPut descriptions per copy launch (passed by value)
     unsigned long long acc = 0;
+    uint32_t cacc = 0;
     for (int first = 0; first < n_jobs; first += kJobsPerPut) {
         JobChunk c;
         c.first = first;
@@ -754,11 +773,17 @@ cudaError_t launch_render_batch(int n_jobs, const gsrf_plan* plans, void* const*
             make_layout(&plans[j], &L);
             c.jobs[i] = render_args(&plans[j], L, workspaces[j], outs[j], nullptr);
             c.item_base[i] = acc;
-            acc += (unsigned long long)L.n_rx * L.n_tiles * c.jobs[i].per_tile;
+            c.chunk_base[i] = cacc;
+            const unsigned long long items = (unsigned long long)L.n_rx * L.n_tiles * c.jobs[i].per_tile;
+            acc += items;
+            cacc += (uint32_t)((items + kChunk - 1) / kChunk);
         }
         c.n_bases = c.count;
-        if (first + c.count == n_jobs) c.item_base[c.n_bases++] = acc;
-        k_put_jobs<<<1, 256, 0, st>>>(c, jobs, base);
+        if (first + c.count == n_jobs) {
+            c.item_base[c.n_bases] = acc;
+            c.chunk_base[c.n_bases++] = cacc;
+        }
+        k_put_jobs<<<1, 256, 0, st>>>(c, jobs, base, cbase);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (n == 0) return cudaSuccess;
@@ -768,15 +793,18 @@ cudaError_t launch_render_batch(int n_jobs, const gsrf_plan* plans, void* const*
     uint32_t* hist = reinterpret_cast<uint32_t*>(w + bl.hist);
     unsigned long long* counter = reinterpret_cast<unsigned long long*>(w + bl.counter);
     k_batch_keys<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(jobs, base, n_jobs, keys);
-    if ((e = launch_sort_small_keys(keys, keys2, order, n, 32, hist, st)) != cudaSuccess) return e;
+    e = job_order ? launch_sort_small_keys_segmented(keys, keys2, order, n_jobs, reinterpret_cast<const long long*>(base),
+                                                     cbase, cacc, 32, hist, st)
+                  : launch_sort_small_keys(keys, keys2, order, n, 32, hist, st);
+    if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
     int grid = 0;
     if (plan_stage(&plans[0]) == 16) {
         if ((e = resident_grid(k_render_batch<16>, n, &grid)) != cudaSuccess) return e;
-        k_render_batch<16><<<grid, kThreads, 0, st>>>(jobs, base, n_jobs, order, counter, job_done);
+        k_render_batch<16><<<grid, kThreads, 0, st>>>(jobs, base, n_jobs, order, counter, job_done, job_order ? 1 : 0);
     } else {
         if ((e = resident_grid(k_render_batch<32>, n, &grid)) != cudaSuccess) return e;
-        k_render_batch<32><<<grid, kThreads, 0, st>>>(jobs, base, n_jobs, order, counter, job_done);
+        k_render_batch<32><<<grid, kThreads, 0, st>>>(jobs, base, n_jobs, order, counter, job_done, job_order ? 1 : 0);
     }
     return cudaGetLastError();
 }

@@ -1,7 +1,7 @@
 // peaks.cu -- throughput microbenchmarks of the GB300 pipes that bound the render:
-// FP32 fused multiply-add, the special-function unit (ex2, rcp, rsqrt, sqrt, sin, cos),
-// FP64 fused multiply-add and TF32 matrix multiply-accumulate (the warp-level mma.sync
-// form).  They give the denominators of the render's roofline; they are measurement
+// FP32 fused multiply-add (scalar and the packed pair form fma.rn.f32x2), the
+// special-function unit (ex2, rcp, rsqrt, sqrt, sin, cos), FP64 fused multiply-add and
+// TF32 matrix multiply-accumulate (the warp-level mma.sync form).  They give the denominators of the render's roofline; they are measurement
 // tools of this library, not part of the render (libgsrf_peaks.so, separate from
 // libgsrf.so).
 //
@@ -19,7 +19,10 @@ namespace gsrf_peaks {
 constexpr int kChains = 8;
 constexpr int kUnroll = 16;
 
-enum Kind { FMA32 = 0, EX2 = 1, RCP = 2, RSQRT = 3, SQRT = 4, SIN = 5, COS = 6, FMA64 = 7, MMA_TF32 = 8, N_KINDS = 9 };
+enum Kind {
+    FMA32 = 0, EX2 = 1, RCP = 2, RSQRT = 3, SQRT = 4, SIN = 5, COS = 6, FMA64 = 7, MMA_TF32 = 8, FMA32X2 = 9,
+    N_KINDS = 10
+};
 
 // One dependent step of a chain.  The special-function kinds take f(x + b): the add (on
 // the FP32 pipe, eight times wider than the special-function unit) keeps the assembler
@@ -80,6 +83,30 @@ __global__ void __launch_bounds__(256) k_fma64(int iters, float* out) {
     if (s == -1234.5) out[blockIdx.x * blockDim.x + threadIdx.x] = (float)s;
 }
 
+// Packed FP32 pairs: one fma.rn.f32x2 instruction is two fused multiply-adds.
+__global__ void __launch_bounds__(256) k_fma32x2(int iters, float* out) {
+    unsigned long long x[kChains], a, b;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "f"(0.999f + 1e-9f * threadIdx.x), "f"(0.998f));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(b) : "f"(1e-3f), "f"(2e-3f));
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) asm("mov.b64 %0, {%1, %2};" : "=l"(x[c]) : "f"(0.5f + 0.01f * c), "f"(0.25f));
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x[c]) : "l"(a), "l"(b));
+        }
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+        float lo, hi;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x[c]));
+        s += lo + hi;
+    }
+    if (s == -1234.5f) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // D = A B + D for a 16 x 8 x 8 TF32 tile per warp instruction (2048 FLOP), eight
 // independent accumulators per warp.
 __global__ void __launch_bounds__(256) k_mma_tf32(int iters, float* out) {
@@ -112,16 +139,18 @@ using namespace gsrf_peaks;
 
 extern "C" {
 
-// Operations one launch performs: per thread (scalar kinds) or per warp (the matrix
-// kind, in FLOP: 2 x 16 x 8 x 8 per instruction).
+// Operations one launch performs: per thread (scalar kinds; the packed kind counts its
+// two multiply-adds) or per warp (the matrix kind, in FLOP: 2 x 16 x 8 x 8 per
+// instruction).
 double gsrf_peak_ops(int kind, int blocks, int iters) {
     const double per = (double)iters * kUnroll * kChains;
     if (kind == MMA_TF32) return per * blocks * (256 / 32) * 2.0 * 16 * 8 * 8;
+    if (kind == FMA32X2) return per * blocks * 256.0 * 2.0;
     return per * blocks * 256.0;
 }
 
 // Launch microbenchmark `kind` (0 FP32 FMA, 1 ex2, 2 rcp, 3 rsqrt, 4 sqrt, 5 sin, 6 cos,
-// 7 FP64 FMA, 8 TF32 mma.sync) on `blocks` CTAs of 256 threads, `iters` rounds each, on
+// 7 FP64 FMA, 8 TF32 mma.sync, 9 packed FP32x2 FMA) on `blocks` CTAs of 256 threads, `iters` rounds each, on
 // `stream`.  out [dev] holds blocks x 256 floats (written only in a case that cannot
 // occur).  Returns 0, or the CUDA error of the launch; 1 for an unknown kind or a size
 // out of range.
@@ -137,6 +166,7 @@ int gsrf_peak_launch(int kind, int blocks, int iters, float* out, void* stream) 
         case SIN: k_scalar<SIN><<<blocks, 256, 0, st>>>(iters, out); break;
         case COS: k_scalar<COS><<<blocks, 256, 0, st>>>(iters, out); break;
         case FMA64: k_fma64<<<blocks, 256, 0, st>>>(iters, out); break;
+        case FMA32X2: k_fma32x2<<<blocks, 256, 0, st>>>(iters, out); break;
         default: k_mma_tf32<<<blocks, 256, 0, st>>>(iters, out); break;
     }
     return (int)cudaGetLastError();

@@ -5,8 +5,9 @@ function unit (MUFU: ex2, rcp, rsqrt, sqrt, sin, cos), which the copy-bandwidth 
 cuBLAS figures of the GPU do not give.  `measure()` times each microbenchmark with CUDA
 events on the current stream after one warm-up launch, on a grid that fills every SM
 (8 CTAs of 256 threads each), sized to run for a few milliseconds, and returns operations
-per second: FP32 and FP64 fused multiply-adds (one operation each), special-function
-results, and TF32 FLOP of the warp-level mma.sync form (2 per multiply-add).
+per second: FP32 and FP64 fused multiply-adds (one operation each; the packed FP32x2
+instruction counts its two), special-function results, and TF32 FLOP of the warp-level
+mma.sync form (2 per multiply-add).
 
   python -m paper_2502_01826_gb300.peaks      # prints the figures as JSON
 """
@@ -18,7 +19,7 @@ import os
 
 from . import _build
 
-KINDS = ["fma32", "ex2", "rcp", "rsqrt", "sqrt", "sin", "cos", "fma64", "mma_tf32"]
+KINDS = ["fma32", "ex2", "rcp", "rsqrt", "sqrt", "sin", "cos", "fma64", "mma_tf32", "fma32x2"]
 # issue slots per SM and clock that each kind has on this architecture's SM (4 sub-
 # partitions): 128 FP32 lanes; 16 special-function results; used only to express a
 # measured rate per SM and clock beside the nominal figure

@@ -223,9 +223,11 @@ class BatchRender:
     """Many render problems (each a Renderer that has run project and bin) rendered by one
     persistent kernel launch, work items heaviest first (gsrf_render_batch).  ``outs``:
     optional output tensors, one per renderer (e.g. views of one buffer); ``stamps``: keep
-    per-job completion times (``job_done_ns``, n_jobs + 1 int64 on the device)."""
+    per-job completion times (``job_done_ns``, n_jobs + 1 int64 on the device);
+    ``job_order``: take the jobs in the given order, heaviest first inside each, instead of
+    heaviest first over all jobs."""
 
-    def __init__(self, renderers: list, outs: list | None = None, stamps: bool = False):
+    def __init__(self, renderers: list, outs: list | None = None, stamps: bool = False, job_order: bool = False):
         if not 1 <= len(renderers) <= L.GSRF_MAX_BATCH_JOBS:
             raise ValueError("1..%d jobs per batch" % L.GSRF_MAX_BATCH_JOBS)
         self.renderers = list(renderers)
@@ -239,6 +241,7 @@ class BatchRender:
         self.outs = outs if outs is not None else [torch.empty(r.out_shape(), dtype=torch.float32, device=dev)
                                                    for r in self.renderers]
         self.job_done_ns = torch.zeros(n + 1, dtype=torch.int64, device=dev) if stamps else None
+        self.flags = L.BATCH_JOB_ORDER if job_order else 0
 
     def render(self, stream=None):
         n = len(self.renderers)
@@ -248,7 +251,7 @@ class BatchRender:
         wsb = (C.c_size_t * n)(*[r.ws_bytes for r in self.renderers])
         outs = (C.c_void_p * n)(*[o.data_ptr() for o in self.outs])
         L.call("gsrf_render_batch", n, self.plans, wss, wsb, outs, _ptr(self.ws), self.ws_bytes,
-               _ptr(self.job_done_ns), _stream(stream))
+               _ptr(self.job_done_ns), self.flags, _stream(stream))
         return self.outs
 
     def completion_ms(self):

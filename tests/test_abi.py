@@ -271,7 +271,7 @@ def test_batch_and_tuned_backward_refuse_the_forward_only_readings(lib):
         wss = (C.c_void_p * 1)(dev)
         sizes = (C.c_size_t * 1)(sz.value)
         outs = (C.c_void_p * 1)(dev)
-        assert lib.gsrf_render_batch(1, plans, wss, sizes, outs, dev, bsz.value, None, None) == L.GSRF_ERR_UNSUPPORTED
+        assert lib.gsrf_render_batch(1, plans, wss, sizes, outs, dev, bsz.value, None, 0, None) == L.GSRF_ERR_UNSUPPORTED
     p = plan()
     p.variant = L.VARIANT_RADIANCE_AT_MEAN
     tsz = C.c_size_t()

@@ -106,3 +106,12 @@ def test_batch_completion_stamps_and_many_jobs():
         assert np.all(done >= start) and np.all(done - start <= span_ns + 1e5)
         c = B.completion_ms()
         assert c.shape == (len(jobs),) and np.all(c >= 0.0)
+    # the same jobs taken in their given order (heaviest first inside each): same outputs,
+    # and the first jobs finish before the last ones
+    Bo = BatchRender([R for R, _, _, _ in jobs], stamps=True, job_order=True)
+    outs = Bo.render()
+    torch.cuda.synchronize()
+    for x, y in zip(plain, outs):
+        assert torch.equal(x, y)
+    c = Bo.completion_ms()
+    assert np.mean(c[:10]) < np.mean(c[-10:]), c
