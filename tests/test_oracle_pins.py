@@ -21,6 +21,8 @@ Coverage (oracle function -> pins):
                    cancellation, brute force == culled, associativity of the
                    front-to-back sum, |T| monotone and |S| bounded
   or_render_grad   central finite differences of or_render
+  rounding model   delta_k against an FP32 evaluation of m2; Scond against the FP64
+                   render with each composited pair's m2 moved by +-delta_k
 """
 import math
 import os
