@@ -280,8 +280,9 @@ def render_grad(scene: dict, rx, tx, f0: float, grid: Grid, G, df: float = 0.0, 
     ridx = None if rays is None else np.ascontiguousarray(rays, np.int32)
     G = np.asarray(G).reshape(n_f, n_rays)
     Gr = np.ascontiguousarray(np.stack([G.real, G.imag], -1), np.float64)
+    deg = grid.fle_degree if grid.fle_degree > 0 else 3
     out = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
-               opacity_logit=np.zeros(n), coeffs=np.zeros((n, 16, 2)), phase_b=np.zeros(n))
+               opacity_logit=np.zeros(n), coeffs=np.zeros((n, (deg + 1) ** 2, 2)), phase_b=np.zeros(n))
     th = threads if threads else (os.cpu_count() or 1)
     rc = lib().or_render_grad(C.byref(s.c), _p(_f32(rx)), _p(_f32(tx)), float(f0), float(df),
                               n_f, C.byref(grid), mode, _p(ridx), n_rays, th, _p(Gr),

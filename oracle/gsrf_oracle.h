@@ -74,7 +74,7 @@ typedef struct {
                                   *      in the list's order of |mu_k - r| (App. E) */
     int32_t fle_degree;          /* Fourier-Legendre degree L of the radiance, 1..5 (0 = 3): the
                                   * scene carries (L + 1)^2 complex coefficients per Gaussian,
-                                  * index l*l + l + m (Sec. 4.2); the gradient is L = 3 only */
+                                  * index l*l + l + m (Sec. 4.2) */
 } or_grid;
 
 typedef struct {
@@ -209,9 +209,10 @@ int or_render(const or_scene *s, const float *rx, const float *tx, double f0, do
               int32_t *ntest, uint32_t *flags);
 
 /* Gradient of L = sum_rays sum_f Re(conj(G) S) for the given dL/dRe S, dL/dIm S
- * (G [n_f][n_rays][2]), with respect to the raw parameters.  Gradient buffers are
- * overwritten ([n,3],[n,3],[n,4],[n],[n,16,2],[n]); any may be NULL.  Same ray
- * selection, mode and termination rule as or_render. */
+ * (G [n_f][n_rays][2]), with respect to the raw parameters, at the grid's degree L.
+ * Gradient buffers are overwritten ([n,3],[n,3],[n,4],[n],[n,(L+1)^2,2],[n]); any may be
+ * NULL.  Same ray selection, mode and termination rule as or_render; default reading
+ * (variant 0) only. */
 int or_render_grad(const or_scene *s, const float *rx, const float *tx, double f0, double df,
                    int32_t n_f, const or_grid *g, int32_t mode, const int32_t *ray_idx,
                    int64_t n_rays, int32_t n_threads, const double *G,

@@ -907,15 +907,21 @@ def test_circle_variant_hits_are_a_subset(oracle_lib):
     assert np.all(n4 <= n0) and n4.sum() < n0.sum()
 
 
-def test_other_degrees_forward_only(oracle_lib):
-    """The gradient is the L = 3 adjoint only; other degrees are refused, not guessed."""
-    s = one_gaussian((4.0, 3.0, 1.0), coeffs=np.ones((36, 2)) * 0.1)
-    r = np.array([2.0, 2.0, 0.5], np.float32)
-    G = np.ones((1, 72 * 18), complex)
-    with pytest.raises(ValueError, match="rejected"):
-        oracle_lib.render_grad(s, r, r, 2.4e9, small_grid(oracle_lib, fle_degree=5), G)
-    out = oracle_lib.render(s, r, r, 2.4e9, small_grid(oracle_lib, fle_degree=5), mode=1)
-    assert np.count_nonzero(out["S"]) > 0
+@pytest.mark.parametrize("deg", [1, 2, 4, 5])
+def test_gradient_at_other_degrees_matches_finite_differences(oracle_lib, deg):
+    """The adjoint at Fourier-Legendre degree L = 1, 2, 4, 5: dS/dc_n = alpha E T Y_n over
+    the (L + 1)^2 basis values, checked against central differences of the forward at the
+    same degree (a wrong basis index or count fails the coefficient gradients)."""
+    s = synthetic.tiny_scene(24, 71 + deg)
+    s["coeffs"] = np.random.default_rng(40 + deg).normal(0.0, 0.1, (24, (deg + 1) ** 2, 2)).astype(np.float32)
+    r = np.array([2.0, 2.0, 0.6], np.float32)
+    t = np.array([3.0, 0.5, 1.5], np.float32)
+    grid = oracle_lib.make_grid(72, 18, eps_T=0.0, fle_degree=deg)
+    rng = np.random.default_rng(5 + deg)
+    G = rng.normal(size=(1, 72 * 18)) + 1j * rng.normal(size=(1, 72 * 18))
+    _fd_check(oracle_lib, s, r, t, 2.0e8, grid, None, G, seed=10 + deg, rel_step=5e-5)
+    g = oracle_lib.render_grad(s, r, t, 2.0e8, grid, G)
+    assert g["coeffs"].shape == (24, (deg + 1) ** 2, 2)
 
 
 # --------------------------------------------------------------------------- path through x_rep
