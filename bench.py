@@ -1068,15 +1068,18 @@ def angular_leg(args, ws, flush):
 
 def fle_degree_leg(args, ws, flush):
     """The BLE workload (50,000 Gaussians, 64 receivers, 360 x 90) with the radiance of
-    Fourier-Legendre degree L = 1..5 (the paper's study of L, Sec. 4.2): the same
-    geometry, receivers and split, (L + 1)^2 seeded coefficients per Gaussian; forward step
-    (project + bin + render + RSSI).  CUDA events, L2 flushed between steps."""
+    Fourier-Legendre degree L = 1..5 (the paper's study of L, Sec. 4.2, which times
+    inference and training at each degree): the same geometry, receivers and split,
+    (L + 1)^2 seeded coefficients per Gaussian; the forward step (project + bin + render +
+    RSSI), and a training step (forward + loss sum Re(conj(G) S) with a fixed random G +
+    the hand-written backward to every parameter).  CUDA events, L2 flushed between
+    steps."""
     import numpy as np
     import torch
 
     from paper_2502_01826_gb300 import _lib as L
     from paper_2502_01826_gb300 import synthetic
-    from paper_2502_01826_gb300.render import Renderer, make_grid, received_signal, to_device
+    from paper_2502_01826_gb300.render import Renderer, make_grid, received_signal, render, to_device
 
     cfg = rank_receivers(synthetic.config_ble(n_rx=args.n_rx), int(os.environ.get("RANK", "0")))
     K, n_rx = cfg["scene"]["means"].shape[0], cfg["rx"].shape[0]
@@ -1103,9 +1106,22 @@ def fle_degree_leg(args, ws, flush):
         L.check("degree %d (device status)" % deg, st.code)
         ms = _time_steps(fwd, args.steps, flush)
         t = max_over_ranks(ms * args.steps / 1e3, ws)
+        pg = {k: v.clone().requires_grad_(True) for k, v in p.items()}
+        up = torch.randn(R.out_shape(), dtype=torch.float32, device="cuda")
+
+        def fwd_bwd():
+            for v in pg.values():
+                v.grad = None
+            loss = (render(R, pg, rx, tx) * up).sum()
+            loss.backward()
+
+        for _ in range(args.warmup):
+            fwd_bwd()
+        ms_fb = _time_steps(fwd_bwd, args.steps, flush)
         res["L%d" % deg] = {"coefficients": (deg + 1) ** 2, "ms_per_step": ms, "pairs_per_step": int(st.stats[1]),
-                            "pairs_per_s": sum_over_ranks(int(st.stats[1]) * args.steps, ws) / t}
-        del R, out, p
+                            "pairs_per_s": sum_over_ranks(int(st.stats[1]) * args.steps, ws) / t,
+                            "fwd_bwd_ms_per_step": ms_fb}
+        del R, out, p, pg, up
     return {"workload": cfg["name"], "split": "16x16,8,32 (default)", **res}
 
 

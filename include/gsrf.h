@@ -123,10 +123,10 @@ typedef struct {
                                 * GSRF_ERR_UNSUPPORTED in the status word).  0..31 */
     int32_t fle_degree;        /* degree L of the Fourier-Legendre radiance (Sec. 4.2), 1..5;
                                 * 0 = 3, the paper's choice.  The Gaussians then carry (L + 1)^2
-                                * complex coefficients each.  L != 3 is forward-only and
-                                * single-frequency: GSRF_ERR_UNSUPPORTED for n_f > 1, for the
-                                * backward, the batched render, and variant
-                                * GSRF_VARIANT_RADIANCE_AT_MEAN */
+                                * complex coefficients each.  L != 3 is single-frequency:
+                                * GSRF_ERR_UNSUPPORTED for n_f > 1, for the batched render and
+                                * for variant GSRF_VARIANT_RADIANCE_AT_MEAN; the forward and the
+                                * backward run at every degree */
 } gsrf_plan;
 #define GSRF_VARIANT_RADIANCE_AT_MEAN 1
 #define GSRF_VARIANT_NORMALISED_WEIGHT 2

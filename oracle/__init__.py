@@ -129,6 +129,15 @@ def make_grid(n_az, n_el, az0_deg=0.0, daz_deg=None, el0_deg=0.0, del_deg=None, 
                 tile_w, tile_h, variant, fle_degree)
 
 
+def _check_coeffs(scene: dict, grid: Grid):
+    """The scene's coefficients must match the grid's degree (the C code reads
+    (L + 1)^2 complex values per Gaussian)."""
+    deg = grid.fle_degree if grid.fle_degree > 0 else 3
+    c = np.asarray(scene["coeffs"])
+    if c.ndim != 3 or c.shape[1:] != ((deg + 1) ** 2, 2):
+        raise ValueError("coefficients %s do not match degree %d" % (c.shape, deg))
+
+
 class _SceneRef:
     """Keeps float32 copies alive for the duration of a call."""
 
@@ -241,6 +250,7 @@ def render(scene: dict, rx, tx, f0: float, grid: Grid, df: float = 0.0, n_f: int
     ``rays``: optional int array of ray indices (v * n_az + u).  ``m2_shift`` (needs
     ``bands``): [n_rays, J] array; the m2 of the j-th composited pair of each ray is moved
     by m2_shift[i, j] times its delta_k (the perturbation study of the rounding model)."""
+    _check_coeffs(scene, grid)
     s = _SceneRef(scene)
     n_rays = grid.n_az * grid.n_el if rays is None else len(rays)
     ridx = None if rays is None else np.ascontiguousarray(rays, np.int32)
@@ -274,6 +284,7 @@ def render(scene: dict, rx, tx, f0: float, grid: Grid, df: float = 0.0, n_f: int
 def render_grad(scene: dict, rx, tx, f0: float, grid: Grid, G, df: float = 0.0, n_f: int = 1,
                 mode: int = 0, rays=None, threads: int | None = None):
     """Gradient of sum Re(conj(G) S) with respect to the raw parameters (FP64)."""
+    _check_coeffs(scene, grid)
     s = _SceneRef(scene)
     n = s.n
     n_rays = grid.n_az * grid.n_el if rays is None else len(rays)

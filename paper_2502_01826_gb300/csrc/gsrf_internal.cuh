@@ -70,6 +70,11 @@ __host__ __device__ constexpr int fle_m0_floats(int L) { return 4 * ((L + 2) / 2
 __host__ __device__ constexpr int raytab_floats(int L) { return 4 * ((L * (L + 2) + 6) / 4); }
 static_assert(fle_floats(3) == kFle && raytab_floats(3) == kRayTab, "the L = 3 layouts");
 inline int plan_degree(const gsrf_plan* p) { return p->fle_degree > 0 ? p->fle_degree : 3; }
+// Backward accumulators per Gaussian: W 9, mu 3, opacity, b, then the coefficient
+// gradients in chunks of 16 basis values x (dL/d psi_re, dL/d psi_im), rounded to float4.
+__host__ __device__ constexpr int grad_chunks(int L) { return ((L + 1) * (L + 1) + 15) / 16; }
+__host__ __device__ constexpr int grad_floats(int L) { return 4 * ((14 + 32 * grad_chunks(L) + 3) / 4); }
+static_assert(grad_floats(3) == 48, "the L = 3 accumulator");
 
 // Tile coverage of a Gaussian seen from a receiver: azimuth-tile bit mask,
 // elevation tile range packed lo | hi << 16, number of tiles.
@@ -483,6 +488,61 @@ __device__ __forceinline__ bool pair_hits(const float4& v1, const float4& s0, co
     g.dl = __fsub_rn(__fmul_rn(0.5f, __fadd_rn(g.t_a, g.t_out)), g.tm);
     g.m2r = __fmaf_rn(__fmul_rn(g.A, g.dl), g.dl, g.m2);
     return true;
+}
+
+// Radiance psi of one Gaussian along one ray (Eq. 9) from its folded coefficients q
+// (see fle_floats) and the ray's basis values: P = (P_10 .. P_L0), Y = the complex
+// Y_{l,m>0} in m-major order.  One fused multiply-add per product, accumulated in order.
+template <int L>
+__device__ __forceinline__ void fle_psi(const float4* __restrict__ q4, const float* P, const float* Y,
+                                        float& pr, float& pi) {
+    constexpr int kQ0 = fle_m0_floats(L) / 4;
+    float m0[4 * kQ0];
+#pragma unroll
+    for (int i = 0; i < kQ0; ++i) {
+        const float4 a = __ldg(q4 + i);
+        m0[4 * i] = a.x;
+        m0[4 * i + 1] = a.y;
+        m0[4 * i + 2] = a.z;
+        m0[4 * i + 3] = a.w;
+    }
+    pr = m0[0];
+    pi = m0[1];
+#pragma unroll
+    for (int l = 1; l <= L; ++l) {
+        pr = fmaf(m0[2 * l], P[l - 1], pr);
+        pi = fmaf(m0[2 * l + 1], P[l - 1], pi);
+    }
+#pragma unroll
+    for (int t = 0; t < L * (L + 1) / 2; ++t) {
+        const float4 e = __ldg(q4 + kQ0 + t);
+        pr = fmaf(e.y, Y[2 * t + 1], fmaf(e.x, Y[2 * t], pr));
+        pi = fmaf(e.w, Y[2 * t + 1], fmaf(e.z, Y[2 * t], pi));
+    }
+}
+
+// The ray's direction and basis values from the per-grid ray table (see raytab_floats).
+template <int L>
+__device__ __forceinline__ void load_ray(const float* raytab, size_t ray, float& dx, float& dy, float& dz,
+                                         float* P, float* Y) {
+    constexpr int kN = raytab_floats(L);
+    const float4* t4 = reinterpret_cast<const float4*>(raytab + ray * kN);
+    float t[kN];
+#pragma unroll
+    for (int i = 0; i < kN / 4; ++i) {
+        const float4 a = t4[i];
+        t[4 * i] = a.x;
+        t[4 * i + 1] = a.y;
+        t[4 * i + 2] = a.z;
+        t[4 * i + 3] = a.w;
+    }
+    dx = t[0];
+    dy = t[1];
+    dz = t[2];
+#pragma unroll
+    for (int l = 0; l < L; ++l) P[l] = t[3 + l];
+#pragma unroll
+    for (int n = 0; n < L * (L + 1); ++n) Y[n] = t[3 + L + n];
 }
 
 // Opacity-weighted Gaussian at the midpoint and its clamp (R1, R2): alpha = min(o g, amax).

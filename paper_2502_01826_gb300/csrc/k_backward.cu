@@ -29,7 +29,9 @@ namespace gsrf {
 constexpr int kBW = 4;           // warps per CTA
 constexpr int kBThreads = 32 * kBW;
 constexpr int kBB = 32;          // candidates per warp batch
-constexpr int kGrad = 48;        // accumulator floats per Gaussian: W 9, mu 3, o, b, q 32, pad 2
+// Accumulator floats per Gaussian: W 9, mu 3, o, b, then the coefficient gradients in
+// chunks of 32 (dL/d psi_re and dL/d psi_im times 16 basis values each) -- grad_floats(L)
+// in the internal header; 48 at L <= 3.
 
 struct BwdArgs {
     const GShape* shape;
@@ -89,9 +91,10 @@ __device__ __forceinline__ float reduce_scatter16(float* v, int lane) {
 // of b dt in front of k), exactly as the forward builds it; each subcarrier keeps its own
 // suffix R, and the transmittance and path phases enter with their own 2 pi f_s / c.
 // Every chunk adds its share of the gradient to the same accumulators.
-template <int NFC>
+template <int NFC, int L>
 __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int k, float4 (*sbuf)[kBB][6],
                                           uint32_t (*sid)[kBB], float4* spl, float (*sbp)[32]) {
+    constexpr int NB = (L + 1) * (L + 1), NCH = grad_chunks(L);
     const int lane = threadIdx.x & 31;
     const gsrf_grid& gr = a.gr;
     const int chunk = k % a.nchunk, blk = k / a.nchunk;
@@ -103,23 +106,18 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
     const bool valid = u < gr.n_az && v < gr.n_el;
 
     // ray: direction, basis, cone of the warp, state and upstream gradient
-    float dx = 0.0f, dy = 0.0f, dz = 1.0f, P[3] = {0.0f, 0.0f, 0.0f}, Y[12];
+    float dx = 0.0f, dy = 0.0f, dz = 1.0f, P[L], Y[L * (L + 1)];
 #pragma unroll
-    for (int i = 0; i < 12; ++i) Y[i] = 0.0f;
+    for (int i = 0; i < L; ++i) P[i] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < L * (L + 1); ++i) Y[i] = 0.0f;
     int last = -1;
     float Tr = 0.0f, Ti = 0.0f, Gam = 0.0f;
     float Gs[2 * NFC], Rs[2 * NFC];  // upstream G and suffix R per subcarrier of the chunk
 #pragma unroll
     for (int i = 0; i < 2 * NFC; ++i) Gs[i] = Rs[i] = 0.0f;
     if (valid) {
-        const size_t gi = (size_t)v * gr.n_az + u;
-        const float4* t4 = reinterpret_cast<const float4*>(a.raytab + gi * kRayTab);
-        const float4 t0 = t4[0], t1 = t4[1], t2 = t4[2], t3 = t4[3], t5 = t4[4];
-        dx = t0.x; dy = t0.y; dz = t0.z; P[0] = t0.w;
-        P[1] = t1.x; P[2] = t1.y; Y[0] = t1.z; Y[1] = t1.w;
-        Y[2] = t2.x; Y[3] = t2.y; Y[4] = t2.z; Y[5] = t2.w;
-        Y[6] = t3.x; Y[7] = t3.y; Y[8] = t3.z; Y[9] = t3.w;
-        Y[10] = t5.x; Y[11] = t5.y;
+        load_ray<L>(a.raytab, (size_t)v * gr.n_az + u, dx, dy, dz, P, Y);
         const size_t plane = (size_t)gr.n_el * gr.n_az, pix = (size_t)v * gr.n_az + u;
         const RayState s = a.rs[(size_t)r * plane + pix];
         last = s.last;
@@ -136,14 +134,23 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
             }
         }
     }
-    // The ray's basis in the order of the coefficient accumulators -- 1, P10, P20, P30,
-    // then the six complex Y_{l,m>0} -- stored per lane with slot i holding basis value
-    // i ^ (lane & 15), the order the select-free reduce-scatter below needs.
+    // The ray's basis in the order of the coefficient accumulators -- 1, P_10 .. P_L0,
+    // then (Re, Im) of the Y_{l,m>0} in m-major order, zero-padded to chunks of 16 --
+    // stored per lane with slot 16 c + i holding basis value 16 c + (i ^ (lane & 15)),
+    // the order the select-free reduce-scatter below needs.
     {
-        const float b[16] = {1.0f, P[0], P[1], P[2], Y[0], Y[1], Y[2], Y[3], Y[4], Y[5], Y[6], Y[7], Y[8], Y[9],
-                             Y[10], Y[11]};
+        float b[16 * NCH];
+        b[0] = 1.0f;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) sbp[i][lane] = b[i ^ (lane & 15)];
+        for (int l = 0; l < L; ++l) b[1 + l] = P[l];
+#pragma unroll
+        for (int n = 0; n < L * (L + 1); ++n) b[1 + L + n] = Y[n];
+#pragma unroll
+        for (int i = NB; i < 16 * NCH; ++i) b[i] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < NCH; ++c)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) sbp[16 * c + i][lane] = b[16 * c + (i ^ (lane & 15))];
         __syncwarp();
     }
     const Bundle bun = warp_bundle(valid, dx, dy, dz);  // the forward's warp cone and planes
@@ -216,18 +223,7 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
                 const float alpha = pair_alpha(o, pg.m2r, amax, gw);
                 const bool clamped = o * gw >= amax;
                 float pr, pi;
-                const float4* q4 = reinterpret_cast<const float4*>(a.fle + (size_t)sid[bf][j] * kFle);
-                {
-                    const float4 a0 = __ldg(q4), a1 = __ldg(q4 + 1);
-                    pr = fmaf(a1.z, P[2], fmaf(a1.x, P[1], fmaf(a0.z, P[0], a0.x)));
-                    pi = fmaf(a1.w, P[2], fmaf(a1.y, P[1], fmaf(a0.w, P[0], a0.y)));
-#pragma unroll
-                    for (int t = 0; t < 6; ++t) {
-                        const float4 e = __ldg(q4 + 2 + t);
-                        pr = fmaf(e.y, Y[2 * t + 1], fmaf(e.x, Y[2 * t], pr));
-                        pi = fmaf(e.w, Y[2 * t + 1], fmaf(e.z, Y[2 * t], pi));
-                    }
-                }
+                fle_psi<L>(reinterpret_cast<const float4*>(a.fle + (size_t)sid[bf][j] * fle_floats(L)), P, Y, pr, pi);
                 // T before this pair: undo (1 - alpha) e^{-j theta}
                 float sn, cs;
                 phase_rot(a.om_pi * s2.z * pg.dt, sn, cs);
@@ -342,28 +338,32 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
                 go[12] = g_o;
                 go[13] = g_b;
             }
-            float* acc = a.acc + (size_t)sid[bf][j] * kGrad;
-            // coefficient gradients: value v (0..31) is g_pr b[v] for v < 16 and g_pi b[v - 16]
-            // after, summed over the warp's rays.  Stored in slot v ^ lane, every lane keeps
-            // the lower half and sends the upper half in every butterfly round, with no
-            // selects; lane L ends with value L.
+            float* acc = a.acc + (size_t)sid[bf][j] * grad_floats(L);
+            // coefficient gradients, per chunk c of 16 basis values: value v (0..31) is
+            // g_pr b[16 c + v] for v < 16 and g_pi b[16 c + v - 16] after, summed over the
+            // warp's rays.  Stored in slot v ^ lane, every lane keeps the lower half and
+            // sends the upper half in every butterfly round, with no selects; lane L ends
+            // with value L, added to accumulator 14 + 32 c + L.
             {
                 const bool sw = (lane & 16) != 0;
                 const float ga = sw ? g_pi : g_pr, gb = sw ? g_pr : g_pi;
-                float q[32];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const float bi = sbp[i][lane];
-                    q[i] = ga * bi;
-                    q[16 + i] = gb * bi;
+                for (int c = 0; c < NCH; ++c) {
+                    float q[32];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const float bi = sbp[16 * c + i][lane];
+                        q[i] = ga * bi;
+                        q[16 + i] = gb * bi;
+                    }
+#pragma unroll
+                    for (int off = 16, n = 32; off >= 1; off >>= 1, n >>= 1) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            if (i < n / 2) q[i] += __shfl_xor_sync(0xffffffffu, q[i + n / 2], off);
+                    }
+                    atomicAdd(acc + 14 + 32 * c + lane, q[0]);
                 }
-#pragma unroll
-                for (int off = 16, n = 32; off >= 1; off >>= 1, n >>= 1) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (i < n / 2) q[i] += __shfl_xor_sync(0xffffffffu, q[i + n / 2], off);
-                }
-                atomicAdd(acc + 14 + lane, q[0]);
             }
             const float so = reduce_scatter16(go, lane);
             if ((lane & 1) == 0 && (lane >> 1) < 14) atomicAdd(acc + (lane >> 1), so);
@@ -389,19 +389,18 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
 
 // Persistent launch: every warp takes work items (receiver, tile, ray block, subcarrier
 // chunk) from one counter, heaviest first, until none is left.  One frequency: 5 CTAs
-// per SM (at most 102 registers, no spills); chunks of 8 subcarriers: 3 (at most 168;
-// 4 would spill); of 16: 2.
-// More than 8 subcarriers go in chunks of 16: half the walks of chunks of 8 for 64
-// subcarriers, which outweighs the lower occupancy.
-template <int NFC>
-__global__ void __launch_bounds__(kBThreads, NFC == 1 ? 5 : (NFC == 8 ? 3 : 2)) k_render_bwd(BwdArgs a,
-                                                                            const uint32_t* __restrict__ order,
-                                                                            unsigned long long* __restrict__ counter,
-                                                                            unsigned long long total) {
+// per SM up to L = 3 (at most 102 registers, no spills), 4 at L = 4, 3 at L = 5 (the
+// larger basis); chunks of 8 subcarriers (L = 3): 3 (at most 168; 4 would spill); of
+// 16: 2.  More than 8 subcarriers go in chunks of 16: half the walks of chunks of 8 for
+// 64 subcarriers, which outweighs the lower occupancy.
+template <int NFC, int L>
+__global__ void __launch_bounds__(kBThreads, NFC == 1 ? (L <= 3 ? 5 : (L == 4 ? 4 : 3)) : (NFC == 8 ? 3 : 2))
+    k_render_bwd(BwdArgs a, const uint32_t* __restrict__ order, unsigned long long* __restrict__ counter,
+                 unsigned long long total) {
     __shared__ float4 sbuf[kBW][2][kBB][6];
     __shared__ uint32_t sid[kBW][2][kBB];
     __shared__ float4 spl[kBW][kPlaneSlots];
-    __shared__ float sbp[kBW][16][32];
+    __shared__ float sbp[kBW][16 * grad_chunks(L)][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned per_rx = (unsigned)a.n_tiles * (unsigned)a.per_tile;
     for (;;) {
@@ -411,21 +410,22 @@ __global__ void __launch_bounds__(kBThreads, NFC == 1 ? 5 : (NFC == 8 ? 3 : 2)) 
         if (it >= total) break;
         const uint32_t id = order[it];
         const unsigned rem = id % per_rx;
-        bwd_block<NFC>(a, (int)(id / per_rx), (int)(rem / (unsigned)a.per_tile), (int)(rem % (unsigned)a.per_tile),
-                       sbuf[warp], sid[warp], spl[warp], sbp[warp]);
+        bwd_block<NFC, L>(a, (int)(id / per_rx), (int)(rem / (unsigned)a.per_tile), (int)(rem % (unsigned)a.per_tile),
+                          sbuf[warp], sid[warp], spl[warp], sbp[warp]);
         __syncwarp();
     }
 }
 
 // Raw-parameter gradients from the accumulators (one thread per Gaussian, += into the
 // caller's buffers; any may be null).
+template <int L>
 __global__ void __launch_bounds__(256) k_grad_params(gsrf_gaussians g, const GShape* __restrict__ shape,
                                                      const float* __restrict__ acc, float* g_means,
                                                      float* g_log_scales, float* g_quats, float* g_opacity_logit,
                                                      float* g_coeffs, float* g_phase_b) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.n) return;
-    const float* A = acc + (size_t)k * kGrad;
+    const float* A = acc + (size_t)k * grad_floats(L);
     // W = diag(1/s) R^T: W_ij = R_ji / s_i
     float qw = g.quats[4 * k], qx = g.quats[4 * k + 1], qy = g.quats[4 * k + 2], qz = g.quats[4 * k + 3];
     const float n2 = qw * qw + qx * qx + qy * qy + qz * qz;
@@ -472,36 +472,34 @@ __global__ void __launch_bounds__(256) k_grad_params(gsrf_gaussians g, const GSh
     }
     if (g_phase_b) g_phase_b[k] += A[13];
     if (g_coeffs) {
-        // accumulators 14..29: dL/d psi_re times 1, P10, P20, P30, y11 .. y33 (re, im);
-        // 30..45: the same for dL/d psi_im.  q[] restores the folded order of kFle.
-        const float* ar = A + 14;
-        const float* ai = A + 30;
-        float q[kFle];
-        for (int i = 0; i < 4; ++i) {
-            q[2 * i] = ar[i];
-            q[2 * i + 1] = ai[i];
+        // accumulator 14 + 32 c + v: dL/d psi_re (v < 16) or dL/d psi_im (v >= 16) times
+        // basis value 16 c + v % 16 of (1, P_10 .. P_L0, Re Y, Im Y of the Y_{l,m>0});
+        // restored to the folded coefficients (see fle_floats), then unfolded
+        constexpr int NB = (L + 1) * (L + 1);
+        auto gre = [&](int i) { return A[14 + 32 * (i / 16) + i % 16]; };
+        auto gim = [&](int i) { return A[14 + 32 * (i / 16) + 16 + i % 16]; };
+        float* gc = g_coeffs + (size_t)k * 2 * NB;
+        for (int l = 0; l <= L; ++l) {  // m = 0: c_{l,0} multiplies P_l0 (P_00 = 1)
+            gc[2 * (l * l + l)] += gre(l);
+            gc[2 * (l * l + l) + 1] += gim(l);
         }
-        for (int t = 0; t < 6; ++t) {
-            q[8 + 4 * t] = ar[4 + 2 * t];
-            q[8 + 4 * t + 1] = ar[5 + 2 * t];
-            q[8 + 4 * t + 2] = ai[4 + 2 * t];
-            q[8 + 4 * t + 3] = ai[5 + 2 * t];
-        }
-        float* gc = g_coeffs + (size_t)k * 2 * kNB;
-        const int m0[4] = {0, 2, 6, 12};
-        for (int i = 0; i < 4; ++i) {
-            gc[2 * m0[i]] += q[2 * i];
-            gc[2 * m0[i] + 1] += q[2 * i + 1];
-        }
-        // e1 = cr + dr, e2 = di - ci, e3 = ci + di, e4 = cr - dr, d = kappa c_{l,-m}
-        const int np[6] = {3, 7, 13, 8, 14, 15}, nm[6] = {1, 5, 11, 4, 10, 9};
-        const float kap[6] = {-0.5f, -1.0f / 6.0f, -1.0f / 12.0f, 1.0f / 24.0f, 1.0f / 120.0f, -1.0f / 720.0f};
-        for (int t = 0; t < 6; ++t) {
-            const float e1 = q[8 + 4 * t], e2 = q[8 + 4 * t + 1], e3 = q[8 + 4 * t + 2], e4 = q[8 + 4 * t + 3];
-            gc[2 * np[t]] += e1 + e4;
-            gc[2 * np[t] + 1] += e3 - e2;
-            gc[2 * nm[t]] += kap[t] * (e1 - e4);
-            gc[2 * nm[t] + 1] += kap[t] * (e2 + e3);
+        // m > 0, m-major: e1 = cr + dr, e2 = di - ci, e3 = ci + di, e4 = cr - dr with
+        // d = kappa c_{l,-m}, kappa = (-1)^m (l-m)!/(l+m)!; e1, e2 multiply Re, Im Y in psi_re,
+        // e3, e4 in psi_im
+        int t = 0;
+        for (int m = 1; m <= L; ++m) {
+            for (int l = m; l <= L; ++l, ++t) {
+                float prod = 1.0f;
+                for (int i = l - m + 1; i <= l + m; ++i) prod *= (float)i;
+                const float kap = ((m & 1) ? -1.0f : 1.0f) / prod;
+                const int yb = 1 + L + 2 * t;
+                const float e1 = gre(yb), e2 = gre(yb + 1), e3 = gim(yb), e4 = gim(yb + 1);
+                const int np = l * l + l + m, nm = l * l + l - m;
+                gc[2 * np] += e1 + e4;
+                gc[2 * np + 1] += e3 - e2;
+                gc[2 * nm] += kap * (e1 - e4);
+                gc[2 * nm + 1] += kap * (e2 + e3);
+            }
         }
     }
 }
@@ -512,7 +510,8 @@ cudaError_t launch_render_bwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
                               cudaStream_t st) {
     if (L.n == 0) return cudaSuccess;
     float* acc = at<float>(ws, L.gacc);
-    cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)L.n * kGrad * sizeof(float), st);
+    const int deg = plan_degree(p);
+    cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)L.n * grad_floats(deg) * sizeof(float), st);
     if (e != cudaSuccess) return e;
     BwdArgs a;
     a.shape = at<GShape>(ws, L.gshape);
@@ -551,28 +550,40 @@ cudaError_t launch_render_bwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     unsigned long long* counter = nullptr;
     if ((e = launch_item_order(L, ws, a.per_tile, &order, &counter, st)) != cudaSuccess) return e;
     const long long n = (long long)L.n_rx * L.n_tiles * a.per_tile;
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    auto run = [&](auto kernel) -> cudaError_t {
+        int per_sm = 0;
+        cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBThreads, 0);
+        if (r != cudaSuccess) return r;
+        const int grid = (int)max(1ll, min((long long)sms * max(per_sm, 1), (n + kBW - 1) / kBW));
+        kernel<<<grid, kBThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
+        return cudaGetLastError();
+    };
     if (p->n_f == 1) {
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd<1>, kBThreads, 0)) != cudaSuccess)
-            return e;
-        const int grid = (int)max(1ll, min((long long)sms * max(per_sm, 1), (n + kBW - 1) / kBW));
-        k_render_bwd<1><<<grid, kBThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
+        switch (deg) {  // several frequencies: L = 3 only (checked with the plan)
+            case 1: e = run(k_render_bwd<1, 1>); break;
+            case 2: e = run(k_render_bwd<1, 2>); break;
+            case 4: e = run(k_render_bwd<1, 4>); break;
+            case 5: e = run(k_render_bwd<1, 5>); break;
+            default: e = run(k_render_bwd<1, 3>); break;
+        }
     } else if (nfc == 8) {
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd<8>, kBThreads, 0)) != cudaSuccess)
-            return e;
-        const int grid = (int)max(1ll, min((long long)sms * max(per_sm, 1), (n + kBW - 1) / kBW));
-        k_render_bwd<8><<<grid, kBThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
+        e = run(k_render_bwd<8, 3>);
     } else {
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd<16>, kBThreads, 0)) != cudaSuccess)
-            return e;
-        const int grid = (int)max(1ll, min((long long)sms * max(per_sm, 1), (n + kBW - 1) / kBW));
-        k_render_bwd<16><<<grid, kBThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
+        e = run(k_render_bwd<16, 3>);
     }
+    if (e != cudaSuccess) return e;
     const unsigned nb = (unsigned)((L.n + 255) / 256);
-    k_grad_params<<<nb, 256, 0, st>>>(*g, at<GShape>(ws, L.gshape), acc, g_means, g_log_scales, g_quats,
-                                      g_opacity_logit, g_coeffs, g_phase_b);
+    const GShape* sh = at<GShape>(ws, L.gshape);
+    switch (deg) {
+        case 1: k_grad_params<1><<<nb, 256, 0, st>>>(*g, sh, acc, g_means, g_log_scales, g_quats, g_opacity_logit, g_coeffs, g_phase_b); break;
+        case 2: k_grad_params<2><<<nb, 256, 0, st>>>(*g, sh, acc, g_means, g_log_scales, g_quats, g_opacity_logit, g_coeffs, g_phase_b); break;
+        case 4: k_grad_params<4><<<nb, 256, 0, st>>>(*g, sh, acc, g_means, g_log_scales, g_quats, g_opacity_logit, g_coeffs, g_phase_b); break;
+        case 5: k_grad_params<5><<<nb, 256, 0, st>>>(*g, sh, acc, g_means, g_log_scales, g_quats, g_opacity_logit, g_coeffs, g_phase_b); break;
+        default: k_grad_params<3><<<nb, 256, 0, st>>>(*g, sh, acc, g_means, g_log_scales, g_quats, g_opacity_logit, g_coeffs, g_phase_b); break;
+    }
     return cudaGetLastError();
 }
 

@@ -139,61 +139,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// Radiance psi of one Gaussian along one ray (Eq. 9) from its folded coefficients q
-// (see fle_floats) and the ray's basis values: P = (P_10 .. P_L0), Y = the complex
-// Y_{l,m>0} in m-major order.  One fused multiply-add per product, accumulated in order.
-template <int L>
-__device__ __forceinline__ void fle_psi(const float4* __restrict__ q4, const float* P, const float* Y,
-                                        float& pr, float& pi) {
-    constexpr int kQ0 = fle_m0_floats(L) / 4;
-    float m0[4 * kQ0];
-#pragma unroll
-    for (int i = 0; i < kQ0; ++i) {
-        const float4 a = __ldg(q4 + i);
-        m0[4 * i] = a.x;
-        m0[4 * i + 1] = a.y;
-        m0[4 * i + 2] = a.z;
-        m0[4 * i + 3] = a.w;
-    }
-    pr = m0[0];
-    pi = m0[1];
-#pragma unroll
-    for (int l = 1; l <= L; ++l) {
-        pr = fmaf(m0[2 * l], P[l - 1], pr);
-        pi = fmaf(m0[2 * l + 1], P[l - 1], pi);
-    }
-#pragma unroll
-    for (int t = 0; t < L * (L + 1) / 2; ++t) {
-        const float4 e = __ldg(q4 + kQ0 + t);
-        pr = fmaf(e.y, Y[2 * t + 1], fmaf(e.x, Y[2 * t], pr));
-        pi = fmaf(e.w, Y[2 * t + 1], fmaf(e.z, Y[2 * t], pi));
-    }
-}
-
-// The ray's direction and basis values from the per-grid ray table (see raytab_floats).
-template <int L>
-__device__ __forceinline__ void load_ray(const float* raytab, size_t ray, float& dx, float& dy, float& dz,
-                                         float* P, float* Y) {
-    constexpr int kN = raytab_floats(L);
-    const float4* t4 = reinterpret_cast<const float4*>(raytab + ray * kN);
-    float t[kN];
-#pragma unroll
-    for (int i = 0; i < kN / 4; ++i) {
-        const float4 a = t4[i];
-        t[4 * i] = a.x;
-        t[4 * i + 1] = a.y;
-        t[4 * i + 2] = a.z;
-        t[4 * i + 3] = a.w;
-    }
-    dx = t[0];
-    dy = t[1];
-    dz = t[2];
-#pragma unroll
-    for (int l = 0; l < L; ++l) P[l] = t[3 + l];
-#pragma unroll
-    for (int n = 0; n < L * (L + 1); ++n) Y[n] = t[3 + L + n];
-}
-
 // One warp renders work item k (ray block k / nchunk, subcarrier chunk k % nchunk) of
 // tile `tile` for receiver r: it walks the tile's list in batches of WB candidates staged
 // into its own buffers (sbuf, sid), without waiting for any other warp.

@@ -205,9 +205,10 @@ def test_backward_refuses_variant_readings(lib):
                                None, None) == L.GSRF_ERR_UNSUPPORTED
 
 
-def test_other_fle_degrees_are_forward_and_single_frequency(lib):
-    """Degrees 1..5 size the coefficient and ray tables by L; only L = 3 has the backward,
-    several subcarriers, the batched render and the radiance-at-the-mean variant."""
+def test_other_fle_degrees_are_single_frequency(lib):
+    """Degrees 1..5 size the coefficient and ray tables (and the backward's accumulators)
+    by L; only L = 3 has several subcarriers, the batched render and the
+    radiance-at-the-mean variant.  (The backward runs at every degree: GPU tests.)"""
     sizes = []
     for deg in (1, 2, 0, 4, 5):
         p = plan()
@@ -222,14 +223,6 @@ def test_other_fle_degrees_are_forward_and_single_frequency(lib):
         p.variant = bad.get("variant", 0)
         sz = C.c_size_t()
         assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_ERR_UNSUPPORTED
-    p = plan()
-    p.fle_degree = 4
-    sz = C.c_size_t()
-    assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_OK
-    dev = C.c_void_p(1 << 20)
-    g = L.gsrf_gaussians(1000, dev, dev, dev, dev, dev, None)
-    assert lib.gsrf_render_bwd(C.byref(p), C.byref(g), dev, sz.value, dev, dev, None, None, None, None, None,
-                               None, None) == L.GSRF_ERR_UNSUPPORTED
 
 
 def test_path_variant_is_single_frequency_degree_three(lib):

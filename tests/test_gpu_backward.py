@@ -32,10 +32,10 @@ def _gpu():
     oracle.build()
 
 
-def masked_upstream(scene, rx, tx, f0, spec, rng, eps_T=1e-4, n_f=1):
+def masked_upstream(scene, rx, tx, f0, spec, rng, eps_T=1e-4, n_f=1, fle_degree=0):
     """Random upstream dL/dS per ray (and subcarrier), zero on rays near a discrete
     decision.  Returns [n_rx, rays] for one frequency, else [n_rx, n_f, rays]."""
-    g = oracle.make_grid(**spec, eps_T=eps_T)
+    g = oracle.make_grid(**spec, eps_T=eps_T, fle_degree=fle_degree)
     G = []
     for r in range(rx.shape[0]):
         out = oracle.render(scene, rx[r], tx, f0, g, bands=MASK_BANDS)
@@ -255,3 +255,22 @@ def test_checkpointed_backward_on_deep_walks(every, slots):
     e_ck = sum(np.linalg.norm(ck[k] - ref[k]) ** 2 for k in NAMES)
     print("squared gradient error vs oracle: division only %.3g, checkpoints %.3g" % (e_div, e_ck))
     assert e_ck <= 1.5 * e_div + 1e-30
+
+
+@pytest.mark.parametrize("deg", [1, 2, 4, 5])
+def test_backward_at_other_degrees_matches_oracle(deg):
+    """The adjoint at Fourier-Legendre degree L = 1, 2, 4, 5 (Sec. 4.2's degree study):
+    (L + 1)^2 coefficient gradients per Gaussian from the basis chunks of the reduction,
+    and every other parameter group, against the FP64 oracle gradient at the same degree."""
+    scene = synthetic.tiny_scene(300, 210 + deg, box=(6.0, 5.0, 3.0), log_scale_mu=math.log(0.25))
+    scene["coeffs"] = np.random.default_rng(deg).normal(0.0, 0.1, (300, (deg + 1) ** 2, 2)).astype(np.float32)
+    rng = np.random.default_rng(20 + deg)
+    rx = (rng.uniform(0, 1, (2, 3)) * [6.0, 5.0, 3.0]).astype(np.float32)
+    tx = np.array([0.5, 4.0, 2.0], np.float32)
+    spec = dict(n_az=72, n_el=18)
+    G, g = masked_upstream(scene, rx, tx, 2.4e9, spec, rng, fle_degree=deg)
+    assert np.count_nonzero(G) > 0.5 * G.size
+    ref = oracle_grads(scene, rx, tx, 2.4e9, g, G)
+    got = gpu_grads(scene, rx, tx, 2.4e9, spec, G, fle_degree=deg)
+    assert got["coeffs"].shape == ((300, (deg + 1) ** 2, 2))
+    compare_grads(got, ref)
