@@ -13,7 +13,8 @@
 // against the cone of the warp's rays and its ellipsoid against five half-spaces that
 // hold those rays beyond the emitting sphere (warp_planes) and, if it may be hit,
 // copies its records into the warp's half of a double buffer with cp.async while the
-// warp works on the current batch; the rays then visit only the candidates of the
+// warp works on the current batch (the cone test's input, and the list ids, are fetched
+// one and two batches earlier still); the rays then visit only the candidates of the
 // ballot mask, in list order.  A warp's item ends as soon as its 32 rays have
 // terminated (prod(1 - alpha) < eps_T).  After the warp-level tests, nine in ten rays
 // would pass a per-ray direction-cone test, so the forward goes straight to the exact
@@ -150,7 +151,8 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // E(f0) e^{-j s 2 pi df d / c}; the powers of r come from one sincos and a recurrence.
 template <int NFC, int WB, int L, bool PATH = false, bool ORDER = false>
 __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int tile, int k,
-                                             float4 (*sbuf)[WB][kRec], uint32_t (*sid)[WB], float4* spl) {
+                                             float4 (*sbuf)[WB][kRec], uint32_t (*sid)[WB], float4* spl,
+                                             float4 (*stin)[1]) {
     const int lane = threadIdx.x & 31;
     const gsrf_grid& gr = a.gr;
     const int chunk = k % a.nchunk, blk = k / a.nchunk;
@@ -193,18 +195,31 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
     if constexpr (ORDER)
         tb = a.tbuf + ((size_t)r * gr.n_el * gr.n_az + (size_t)(valid ? v : 0) * gr.n_az + (valid ? u : 0)) * kOrderCap;
 
-    // Stage the batch starting at list position p0 into buffer bf: lane i < WB takes
-    // candidate p0 + i, tests it against the warp's cone and half-spaces and, if it may
-    // be hit, copies its records; returns the mask of candidates that may be hit.
-    auto stage = [&](int bf, int p0) -> uint32_t {
+    // The staging runs one batch ahead of the test: the first 16 bytes of each list
+    // position's view record (c, D cos(theta): the cone test's input) are copied into the
+    // warp's stin slot with cp.async while the warp composites the batch before, and the
+    // list ids two batches ahead are loaded into registers, so that a batch's test waits
+    // on one dependent load (the M block, only where the cone test passes) instead of
+    // three (id, c, M).
+    auto issue_tin = [&](int p0, uint32_t id) {
+        if (lane < WB && p0 + lane < len) {
+            const float4* vw = reinterpret_cast<const float4*>(view + id);
+            const float4* sh = reinterpret_cast<const float4*>(a.shape + id);
+            cp_async16(stin[lane] + 0, vw);
+        }
+        cp_async_commit();
+    };
+    // Test the batch at p0 against the warp's cone (c from its arrived stin slot) and
+    // half-spaces, and copy the records of the candidates that may be hit into buffer bf;
+    // returns the mask of candidates that may be hit.
+    auto test_stage = [&](int bf, int p0, uint32_t id) -> uint32_t {
         bool keep = false;
         if (lane < WB && p0 + lane < len) {
-            const uint32_t id = ids[p0 + lane];
-            const float4* vw = reinterpret_cast<const float4*>(view + id);
-            const float4 c = __ldg(vw);
+            const float4 c = stin[lane][0];
             keep = bundle_meets(bundle_at(spl), c) && planes_meet(spl, c, a.shape + id);
             if (keep) {
                 sid[bf][lane] = id;
+                const float4* vw = reinterpret_cast<const float4*>(view + id);
                 const float4* sh = reinterpret_cast<const float4*>(a.shape + id);
                 float4* dst = sbuf[bf][lane];
                 cp_async16(dst + 0, vw + 1);
@@ -217,10 +232,18 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
         cp_async_commit();
         return __ballot_sync(0xffffffffu, keep);
     };
+    auto list_id = [&](int p) -> uint32_t { return (lane < WB && p + lane < len) ? ids[p + lane] : 0u; };
 
     if (!__all_sync(0xffffffffu, done)) {
         int bf = 0;
-        uint32_t mask = stage(0, 0);
+        const uint32_t id0 = list_id(0);
+        issue_tin(0, id0);
+        uint32_t id_t = list_id(WB);
+        cp_async_wait_all();
+        __syncwarp();
+        uint32_t mask = test_stage(0, 0, id0);
+        issue_tin(WB, id_t);
+        uint32_t id_n = list_id(2 * WB);
         for (int p0 = 0; p0 < len; p0 += WB, bf ^= 1) {
             if (!ORDER && a.ck && chunk == 0) {
                 // transmittance in front of list position K, 2K, ... (a batch start)
@@ -231,9 +254,12 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
                     a.ck[(size_t)(p / a.ck_every - 1) * rays + ray] = make_float4(Tr, Ti, Gam, Ta);
                 }
             }
-            const uint32_t next = stage(bf ^ 1, p0 + WB);  // empty past the end of the list
-            cp_async_wait_prev();
+            cp_async_wait_all();  // this batch's records and the next batch's test inputs
             __syncwarp();
+            const uint32_t next = test_stage(bf ^ 1, p0 + WB, id_t);  // empty past the end of the list
+            issue_tin(p0 + 2 * WB, id_n);
+            id_t = id_n;
+            id_n = list_id(p0 + 3 * WB);
             if (!done) {
                 for (uint32_t m = mask; m; m &= m - 1) {
                     const int j = __ffs(m) - 1;
@@ -426,6 +452,7 @@ __global__ void __launch_bounds__(kThreads, NFC == 1 ? ((PATH || ORDER) ? 6 : (L
     __shared__ float4 sbuf[kWarps][2][WB][kRec];
     __shared__ uint32_t sid[kWarps][2][WB];
     __shared__ float4 spl[kWarps][kPlaneSlots];
+    __shared__ float4 stin[kWarps][WB][1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned per_rx = (unsigned)a.n_tiles * (unsigned)a.per_tile;
     for (;;) {
@@ -436,7 +463,7 @@ __global__ void __launch_bounds__(kThreads, NFC == 1 ? ((PATH || ORDER) ? 6 : (L
         const uint32_t id = order[it];
         const unsigned rem = id % per_rx;
         render_block<NFC, WB, L, PATH, ORDER>(a, (int)(id / per_rx), (int)(rem / (unsigned)a.per_tile),
-                                 (int)(rem % (unsigned)a.per_tile), sbuf[warp], sid[warp], spl[warp]);
+                                 (int)(rem % (unsigned)a.per_tile), sbuf[warp], sid[warp], spl[warp], stin[warp]);
     }
 }
 
@@ -457,6 +484,7 @@ __global__ void __launch_bounds__(kThreads, 6)
     __shared__ float4 sbuf[kWarps][2][WB][kRec];
     __shared__ uint32_t sid[kWarps][2][WB];
     __shared__ float4 spl[kWarps][kPlaneSlots];
+    __shared__ float4 stin[kWarps][WB][1];
     __shared__ RenderArgs sjob[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned long long total = item_base[n_jobs];
@@ -488,7 +516,7 @@ __global__ void __launch_bounds__(kThreads, 6)
         const unsigned long long per_rx = (unsigned long long)a.n_tiles * a.per_tile;
         const unsigned rem = (unsigned)(local % per_rx);
         render_block<1, WB, 3>(a, (int)(local / per_rx), (int)(rem / (unsigned)a.per_tile),
-                               (int)(rem % (unsigned)a.per_tile), sbuf[warp], sid[warp], spl[warp]);
+                               (int)(rem % (unsigned)a.per_tile), sbuf[warp], sid[warp], spl[warp], stin[warp]);
         if (job_done && lane == 0) atomicMax(job_done + j, global_ns());
     }
 }

@@ -115,3 +115,41 @@ def test_batch_completion_stamps_and_many_jobs():
         assert torch.equal(x, y)
     c = Bo.completion_ms()
     assert np.mean(c[:10]) < np.mean(c[-10:]), c
+
+
+def test_uneven_serving_requests_in_one_launch_match_oracle():
+    """Requests of the uneven serving workload (its scenes of 12k to 688k Gaussians, 1-32
+    receivers, 2.4 and 5.2 GHz, 360 x 90) rendered by ONE gsrf_render_batch launch in job
+    order with completion stamps; sampled rays of the first and last receiver of four
+    requests -- a 688k-Gaussian one at 5.2 GHz, a 287k one, a 101k one and a 12k one --
+    against the oracle's per-ray bars."""
+    import oracle
+    from gpu_util import compare, oracle_pair
+
+    oracle.build()
+    cfg = synthetic.config_uneven()
+    scenes = [to_device(sc) for sc in cfg["scenes"]]
+    reqs = cfg["requests"][:24]
+    jobs = []
+    for q in reqs:
+        R = Renderer(scenes[q["scene"]]["means"].shape[0], q["rx"].shape[0], make_grid(**cfg["grid"]), q["f0"],
+                     pair_capacity=1024)
+        rx, tx = torch.tensor(q["rx"], device="cuda"), torch.tensor(q["tx"], device="cuda")
+        R.ensure_capacity(scenes[q["scene"]], rx, tx)
+        jobs.append(R)
+    B = BatchRender(jobs, stamps=True, job_order=True)
+    outs = B.render()
+    torch.cuda.synchronize()
+    for R in jobs:
+        assert R.status().code == 0
+    assert np.all(B.completion_ms() > 0.0)
+    g = oracle.make_grid(**cfg["grid"])
+    rng = np.random.default_rng(41)
+    for i in (23, 12, 0, 3):  # 688k at 5.2 GHz, 287k, 101k, 12k Gaussians
+        q = reqs[i]
+        S = outs[i].cpu().numpy()
+        S = (S[..., 0] + 1j * S[..., 1]).reshape(q["rx"].shape[0], -1)
+        rays = np.sort(rng.choice(S.shape[1], 200, replace=False)).astype(np.int32)
+        for r in sorted({0, q["rx"].shape[0] - 1}):
+            ref = oracle_pair(cfg["scenes"][q["scene"]], q["rx"][r], q["tx"], q["f0"], g, rays=rays)
+            compare(S[r][rays], ref)
