@@ -101,7 +101,7 @@ typedef struct {
                                 * in front of tile-list positions K, 2K, ... (ckpt_slots of them)
                                 * and the backward re-anchors its recomputed transmittance there */
     int32_t ckpt_slots;        /* checkpoints kept per ray, 1..64 when ckpt_every > 0 */
-    int32_t variant;           /* other readings of the paper, forward only (bit mask, 0 = the
+    int32_t variant;           /* other readings of the paper (bit mask, 0 = the
                                 * default): GSRF_VARIANT_RADIANCE_AT_MEAN takes Gaussian k's
                                 * Fourier-Legendre radiance at the direction of mu_k seen from
                                 * the receiver (Sec. 4.3's v_k) for all its rays instead of at
@@ -120,7 +120,9 @@ typedef struct {
                                 * ties by list position) instead of in the list's |mu - r|
                                 * order: one frequency, L = 3, without bit 8, not batched; a ray
                                 * keeps its 512 nearest hits and must terminate on them (else
-                                * GSRF_ERR_UNSUPPORTED in the status word).  0..31 */
+                                * GSRF_ERR_UNSUPPORTED in the status word).  The backward has
+                                * bits 2 and 4 (and none); bits 1, 8 and 16 are forward-only.
+                                * 0..31 */
     int32_t fle_degree;        /* degree L of the Fourier-Legendre radiance (Sec. 4.2), 1..5;
                                 * 0 = 3, the paper's choice.  The Gaussians then carry (L + 1)^2
                                 * complex coefficients each.  L != 3 is single-frequency:
@@ -198,8 +200,10 @@ size_t gsrf_ray_state_bytes(const gsrf_plan *plan);
  *   (+=); any may be NULL.  The gradient of the opacity is taken through its sigmoid, of
  *   the rotation through the quaternion's normalisation, of the scales through exp.
  *   Hit decisions that sit on the integer steps of the method (splatting, the 3-sigma
- *   boundary, the early stop) carry no gradient.  GSRF_ERR_UNSUPPORTED for a plan with
- *   a variant reading.  With plan.ckpt_every = K > 0 the
+ *   boundary, the early stop, the paper's splatting circle) carry no gradient.  Readings:
+ *   the default, GSRF_VARIANT_NORMALISED_WEIGHT (the normalisation adds a log-scale term)
+ *   and GSRF_VARIANT_PAPER_CULLING; GSRF_ERR_UNSUPPORTED for the other variant bits.  Any
+ *   Fourier-Legendre degree (one frequency when L != 3).  With plan.ckpt_every = K > 0 the
  *   recomputed transmittance is replaced by the forward's own at every checkpoint the
  *   walk crosses, so division by (1 - alpha) never runs over more than K list positions
  *   (the per-tile checkpointing of deep scenes).  With n_f > 1 every subcarrier

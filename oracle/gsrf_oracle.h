@@ -211,8 +211,8 @@ int or_render(const or_scene *s, const float *rx, const float *tx, double f0, do
 /* Gradient of L = sum_rays sum_f Re(conj(G) S) for the given dL/dRe S, dL/dIm S
  * (G [n_f][n_rays][2]), with respect to the raw parameters, at the grid's degree L.
  * Gradient buffers are overwritten ([n,3],[n,3],[n,4],[n],[n,(L+1)^2,2],[n]); any may be
- * NULL.  Same ray selection, mode and termination rule as or_render; default reading
- * (variant 0) only. */
+ * NULL.  Same ray selection, mode and termination rule as or_render; the default reading
+ * and variants 2 (normalised weight) and 4 (the paper's splatting-circle culling) only. */
 int or_render_grad(const or_scene *s, const float *rx, const float *tx, double f0, double df,
                    int32_t n_f, const or_grid *g, int32_t mode, const int32_t *ray_idx,
                    int64_t n_rays, int32_t n_threads, const double *G,

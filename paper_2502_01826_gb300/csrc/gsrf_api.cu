@@ -293,8 +293,8 @@ gsrf_status gsrf_render_bwd(const gsrf_plan* plan, const gsrf_gaussians* g, void
     if ((s = check_gauss(plan, g)) != GSRF_OK) return s;
     if (!ray_state || !grad_rays || ((uintptr_t)ray_state & 15) != 0 || ((uintptr_t)grad_rays & 7) != 0)
         return GSRF_ERR_INVALID_ARG;
-    if (plan->variant != 0)
-        return GSRF_ERR_UNSUPPORTED;  // the adjoint of the default reading only (any degree; L != 3 has n_f = 1)
+    if ((plan->variant & ~(GSRF_VARIANT_NORMALISED_WEIGHT | GSRF_VARIANT_PAPER_CULLING)) != 0)
+        return GSRF_ERR_UNSUPPORTED;  // the default reading, normalised weight, circle culling (any degree)
     StageTimer tm(workspace, GSRF_STAGE_RENDER_BWD, (cudaStream_t)stream);
     return cuda_status(launch_render_bwd(plan, L, g, workspace, ray_state, grad_rays, g_means, g_log_scales, g_quats,
                                          g_opacity_logit, g_coeffs, g_phase_b, (cudaStream_t)stream));

@@ -90,7 +90,8 @@ gsrf_status gsrf_autotune(const gsrf_plan* plan, const gsrf_gaussians* g, const 
     if (!plan || !g || !rx_pos || !tx_pos || !workspace || !out_rays || !best || reps < 1 || reps > 100)
         return GSRF_ERR_INVALID_ARG;
     if (bwd && (!bwd->ray_state || !bwd->grad_rays)) return GSRF_ERR_INVALID_ARG;
-    if (bwd && (plan->variant != 0 || plan_degree(plan) != 3)) return GSRF_ERR_UNSUPPORTED;
+    if (bwd && (plan->variant & ~(GSRF_VARIANT_NORMALISED_WEIGHT | GSRF_VARIANT_PAPER_CULLING)) != 0)
+        return GSRF_ERR_UNSUPPORTED;  // the readings the backward has
     if (max_results < 0 || (max_results > 0 && !results)) return GSRF_ERR_INVALID_ARG;
     size_t need = 0;
     gsrf_status s = gsrf_workspace_size(plan, &need);  // validates the caller's plan

@@ -58,6 +58,8 @@ struct BwdArgs {
     int nchunk;   // subcarrier chunks of NFC
     int n_rx;
     const float4* ck;  // the forward's transmittance checkpoints [slot][ray], or null
+    int variant;       // 0, or GSRF_VARIANT_NORMALISED_WEIGHT / GSRF_VARIANT_PAPER_CULLING bits
+    const float4* circle;  // the paper's splatting circles [receiver][Gaussian] (culling variant)
     int ck_every, ck_slots;
 };
 
@@ -211,7 +213,12 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
             const float4 v1 = rec[1], s0 = rec[3], s1 = rec[4], s2 = rec[5];
             const float4 v0 = rec[0];  // c = mu - r, used by the hit path
             PairGeo pg;
-            bool hit = pos <= last && pair_hits(v1, s0, s1, s2, dx, dy, dz, r_rx, pg);
+            // the forward's hit decision: inside the splatting circle (culling variant), then
+            // the exact test
+            bool hit = pos <= last &&
+                       (!(a.variant & GSRF_VARIANT_PAPER_CULLING) ||
+                        circle_in(__ldg(a.circle + (size_t)r * a.n + sid[bf][j]), u, v)) &&
+                       pair_hits(v1, s0, s1, s2, dx, dy, dz, r_rx, pg);
             if (!__any_sync(0xffffffffu, hit)) continue;
             float go[16];
             float g_pr = 0.0f, g_pi = 0.0f;  // dL/d psi (real, imaginary) of this pair on this ray
@@ -422,10 +429,19 @@ template <int L>
 __global__ void __launch_bounds__(256) k_grad_params(gsrf_gaussians g, const GShape* __restrict__ shape,
                                                      const float* __restrict__ acc, float* g_means,
                                                      float* g_log_scales, float* g_quats, float* g_opacity_logit,
-                                                     float* g_coeffs, float* g_phase_b) {
+                                                     float* g_coeffs, float* g_phase_b, int variant) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g.n) return;
     const float* A = acc + (size_t)k * grad_floats(L);
+    // the normalised-weight variant: the opacity in alpha is o N, N = e^{-(l0 + l1 + l2)} /
+    // (2 pi)^1.5 (folded into the shape record the same way), so dL/dlogit carries N and
+    // every log-scale also gets -o N dL/d(o N)
+    const float o = 1.0f / (1.0f + expf(-g.opacity_logit[k]));
+    const float N = (variant & GSRF_VARIANT_NORMALISED_WEIGHT)
+                        ? expf(-(g.log_scales[3 * k] + g.log_scales[3 * k + 1] + g.log_scales[3 * k + 2])) *
+                              0.0634936359f
+                        : 1.0f;
+    const float gN = (variant & GSRF_VARIANT_NORMALISED_WEIGHT) ? -A[12] * o * N : 0.0f;
     // W = diag(1/s) R^T: W_ij = R_ji / s_i
     float qw = g.quats[4 * k], qx = g.quats[4 * k + 1], qy = g.quats[4 * k + 2], qz = g.quats[4 * k + 3];
     const float n2 = qw * qw + qx * qx + qy * qy + qz * qz;
@@ -444,7 +460,7 @@ __global__ void __launch_bounds__(256) k_grad_params(gsrf_gaussians g, const GSh
             GR[3 * j + i] = A[3 * i + j] * is;  // dL/dR_ji
             gis += A[3 * i + j] * R[3 * j + i];
         }
-        if (g_log_scales) g_log_scales[3 * k + i] += -gis * is;  // d(1/s)/dls = -1/s
+        if (g_log_scales) g_log_scales[3 * k + i] += -gis * is + gN;  // d(1/s)/dls = -1/s
     }
     if (g_quats) {
         const float dw[9] = {0, -2 * qz, 2 * qy, 2 * qz, 0, -2 * qx, -2 * qy, 2 * qx, 0};
@@ -467,8 +483,7 @@ __global__ void __launch_bounds__(256) k_grad_params(gsrf_gaussians g, const GSh
     if (g_means)
         for (int i = 0; i < 3; ++i) g_means[3 * k + i] += A[9 + i];
     if (g_opacity_logit) {
-        const float o = shape[k].o;
-        g_opacity_logit[k] += A[12] * o * (1.0f - o);
+        g_opacity_logit[k] += A[12] * N * o * (1.0f - o);  // through the sigmoid (and N)
     }
     if (g_phase_b) g_phase_b[k] += A[13];
     if (g_coeffs) {
@@ -546,6 +561,8 @@ cudaError_t launch_render_bwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
                : nullptr;
     a.ck_every = p->ckpt_every > 0 ? p->ckpt_every : 1;
     a.ck_slots = p->ckpt_slots;
+    a.variant = p->variant;
+    a.circle = (p->variant & GSRF_VARIANT_PAPER_CULLING) ? at<float4>(ws, L.circle) : nullptr;
     uint32_t* order = nullptr;
     unsigned long long* counter = nullptr;
     if ((e = launch_item_order(L, ws, a.per_tile, &order, &counter, st)) != cudaSuccess) return e;
@@ -578,11 +595,11 @@ cudaError_t launch_render_bwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     const unsigned nb = (unsigned)((L.n + 255) / 256);
     const GShape* sh = at<GShape>(ws, L.gshape);
     switch (deg) {
-        case 1: k_grad_params<1><<<nb, 256, 0, st>>>(*g, sh, acc, g_means, g_log_scales, g_quats, g_opacity_logit, g_coeffs, g_phase_b); break;
-        case 2: k_grad_params<2><<<nb, 256, 0, st>>>(*g, sh, acc, g_means, g_log_scales, g_quats, g_opacity_logit, g_coeffs, g_phase_b); break;
-        case 4: k_grad_params<4><<<nb, 256, 0, st>>>(*g, sh, acc, g_means, g_log_scales, g_quats, g_opacity_logit, g_coeffs, g_phase_b); break;
-        case 5: k_grad_params<5><<<nb, 256, 0, st>>>(*g, sh, acc, g_means, g_log_scales, g_quats, g_opacity_logit, g_coeffs, g_phase_b); break;
-        default: k_grad_params<3><<<nb, 256, 0, st>>>(*g, sh, acc, g_means, g_log_scales, g_quats, g_opacity_logit, g_coeffs, g_phase_b); break;
+        case 1: k_grad_params<1><<<nb, 256, 0, st>>>(*g, sh, acc, g_means, g_log_scales, g_quats, g_opacity_logit, g_coeffs, g_phase_b, p->variant); break;
+        case 2: k_grad_params<2><<<nb, 256, 0, st>>>(*g, sh, acc, g_means, g_log_scales, g_quats, g_opacity_logit, g_coeffs, g_phase_b, p->variant); break;
+        case 4: k_grad_params<4><<<nb, 256, 0, st>>>(*g, sh, acc, g_means, g_log_scales, g_quats, g_opacity_logit, g_coeffs, g_phase_b, p->variant); break;
+        case 5: k_grad_params<5><<<nb, 256, 0, st>>>(*g, sh, acc, g_means, g_log_scales, g_quats, g_opacity_logit, g_coeffs, g_phase_b, p->variant); break;
+        default: k_grad_params<3><<<nb, 256, 0, st>>>(*g, sh, acc, g_means, g_log_scales, g_quats, g_opacity_logit, g_coeffs, g_phase_b, p->variant); break;
     }
     return cudaGetLastError();
 }

@@ -195,14 +195,19 @@ def test_autotune_sizing_and_argument_checks(lib):
 
 
 def test_backward_refuses_variant_readings(lib):
-    p = plan()
-    p.variant = L.VARIANT_RADIANCE_AT_MEAN
-    sz = C.c_size_t()
-    assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_OK  # the forward takes it
+    """The backward has the default reading, the normalised weight and the paper's circle
+    culling (GPU tests); the radiance at the mean, the path through x_rep and the t_mid
+    order are refused before any launch."""
     dev = C.c_void_p(1 << 20)
     g = L.gsrf_gaussians(1000, dev, dev, dev, dev, dev, None)
-    assert lib.gsrf_render_bwd(C.byref(p), C.byref(g), dev, sz.value, dev, dev, None, None, None, None, None,
-                               None, None) == L.GSRF_ERR_UNSUPPORTED
+    for v in (L.VARIANT_RADIANCE_AT_MEAN, L.VARIANT_PATH_AT_REP, L.VARIANT_ORDER_T_MID,
+              L.VARIANT_RADIANCE_AT_MEAN | L.VARIANT_NORMALISED_WEIGHT):
+        p = plan()
+        p.variant = v
+        sz = C.c_size_t()
+        assert lib.gsrf_workspace_size(C.byref(p), C.byref(sz)) == L.GSRF_OK  # the forward takes it
+        assert lib.gsrf_render_bwd(C.byref(p), C.byref(g), dev, sz.value, dev, dev, None, None, None, None,
+                                   None, None, None) == L.GSRF_ERR_UNSUPPORTED
 
 
 def test_other_fle_degrees_are_single_frequency(lib):
@@ -251,8 +256,8 @@ def test_tmid_order_variant_limits(lib):
 
 def test_batch_and_tuned_backward_refuse_the_forward_only_readings(lib):
     """The batched render takes only the default degree and no per-pair path or t_mid
-    order; the tuner times no backward for a variant or another degree.  Both refuse
-    before touching the (fake, aligned) device pointers."""
+    order; the tuner times no backward for a reading the backward does not have.  Both
+    refuse before touching the (fake, aligned) device pointers."""
     dev = C.c_void_p(1 << 20)
     for field, value in (("fle_degree", 2), ("variant", L.VARIANT_PATH_AT_REP), ("variant", L.VARIANT_ORDER_T_MID)):
         p = plan()

@@ -274,3 +274,21 @@ def test_backward_at_other_degrees_matches_oracle(deg):
     got = gpu_grads(scene, rx, tx, 2.4e9, spec, G, fle_degree=deg)
     assert got["coeffs"].shape == ((300, (deg + 1) ** 2, 2))
     compare_grads(got, ref)
+
+
+@pytest.mark.parametrize("variant", [2, 4, 6])
+def test_backward_of_variant_readings_matches_oracle(variant):
+    """The adjoint of the normalised-weight reading (2: o N with N = 1 / ((2 pi)^1.5 s0 s1
+    s2), so the log-scales get an extra term) and of the paper's splatting-circle culling
+    (4: the hit set only), against the FP64 oracle's gradient under the same reading."""
+    scene = synthetic.tiny_scene(300, 230 + variant, box=(6.0, 5.0, 3.0), log_scale_mu=math.log(0.25))
+    rng = np.random.default_rng(50 + variant)
+    rx = (rng.uniform(0, 1, (2, 3)) * [6.0, 5.0, 3.0]).astype(np.float32)
+    tx = np.array([0.5, 4.0, 2.0], np.float32)
+    spec = dict(n_az=72, n_el=18)
+    G, _ = masked_upstream(scene, rx, tx, 2.4e9, spec, rng)
+    assert np.count_nonzero(G) > 0.5 * G.size
+    g = oracle.make_grid(**spec, eps_T=1e-4, variant=variant)
+    ref = oracle_grads(scene, rx, tx, 2.4e9, g, G)
+    got = gpu_grads(scene, rx, tx, 2.4e9, spec, G, variant=variant)
+    compare_grads(got, ref)

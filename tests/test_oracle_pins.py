@@ -800,12 +800,34 @@ def test_variant_normalised_weight(oracle_lib):
 
 
 def test_variant_gradient_refused(oracle_lib):
+    """The adjoint covers the default reading and variants 2 and 4; the radiance at the
+    mean (1), the path through x_rep (8) and the t_mid order (16) are refused."""
     s = one_gaussian((4.0, 3.0, 1.0))
     r = np.array([2.0, 2.0, 0.5], np.float32)
     G = np.ones((1, 72 * 18), complex)
     oracle_lib.render_grad(s, r, r, 2.4e9, small_grid(oracle_lib), G)  # the default reading runs
-    with pytest.raises(ValueError, match="rejected"):
-        oracle_lib.render_grad(s, r, r, 2.4e9, small_grid(oracle_lib, variant=1), G)
+    for v in (1, 8, 16, 3):
+        with pytest.raises(ValueError, match="rejected"):
+            oracle_lib.render_grad(s, r, r, 2.4e9, small_grid(oracle_lib, variant=v), G)
+
+
+@pytest.mark.parametrize("variant", [2, 4, 6])
+def test_variant_gradient_matches_finite_differences(oracle_lib, variant):
+    """The adjoint of the normalised-weight reading (2: the opacity that enters alpha is
+    o / ((2 pi)^1.5 s0 s1 s2), which adds a log-scale term) and of the paper's circle
+    culling (4: a discrete decision on top of the exact test), against central differences
+    of the forward under the same reading."""
+    s = synthetic.tiny_scene(24, 75 + variant)
+    r = np.array([2.0, 2.0, 0.6], np.float32)
+    t = np.array([3.0, 0.5, 1.5], np.float32)
+    grid = oracle_lib.make_grid(72, 18, eps_T=0.0, variant=variant)
+    rng = np.random.default_rng(30 + variant)
+    G = rng.normal(size=(1, 72 * 18)) + 1j * rng.normal(size=(1, 72 * 18))
+    _fd_check(oracle_lib, s, r, t, 2.0e8, grid, None, G, seed=20 + variant, rel_step=5e-5)
+    if variant & 2:  # the log-scale term is there: the default reading's gradient differs
+        g0 = oracle_lib.render_grad(s, r, t, 2.0e8, oracle_lib.make_grid(72, 18, eps_T=0.0), G)
+        g2 = oracle_lib.render_grad(s, r, t, 2.0e8, grid, G)
+        assert not np.allclose(g0["log_scales"], g2["log_scales"])
 
 
 # --------------------------------------------------------------------------- the paper's splatting circle
