@@ -493,14 +493,16 @@ __device__ __forceinline__ bool pair_hits(const float4& v1, const float4& s0, co
 // Radiance psi of one Gaussian along one ray (Eq. 9) from its folded coefficients q
 // (see fle_floats) and the ray's basis values: P = (P_10 .. P_L0), Y = the complex
 // Y_{l,m>0} in m-major order.  One fused multiply-add per product, accumulated in order.
-template <int L>
+template <int L, bool SHARED = false>
 __device__ __forceinline__ void fle_psi(const float4* __restrict__ q4, const float* P, const float* Y,
                                         float& pr, float& pi) {
+    // SHARED: the coefficients were staged in shared memory (plain loads)
+    auto ld = [&](int i) -> float4 { if constexpr (SHARED) return q4[i]; else return __ldg(q4 + i); };
     constexpr int kQ0 = fle_m0_floats(L) / 4;
     float m0[4 * kQ0];
 #pragma unroll
     for (int i = 0; i < kQ0; ++i) {
-        const float4 a = __ldg(q4 + i);
+        const float4 a = ld(i);
         m0[4 * i] = a.x;
         m0[4 * i + 1] = a.y;
         m0[4 * i + 2] = a.z;
@@ -515,7 +517,7 @@ __device__ __forceinline__ void fle_psi(const float4* __restrict__ q4, const flo
     }
 #pragma unroll
     for (int t = 0; t < L * (L + 1) / 2; ++t) {
-        const float4 e = __ldg(q4 + kQ0 + t);
+        const float4 e = ld(kQ0 + t);
         pr = fmaf(e.y, Y[2 * t + 1], fmaf(e.x, Y[2 * t], pr));
         pi = fmaf(e.w, Y[2 * t + 1], fmaf(e.z, Y[2 * t], pi));
     }

@@ -39,6 +39,11 @@ constexpr int kThreads = 32 * kWarps;
 // float4 per staged candidate: View floats 4..11 (w, er | ei, omd, psi at the mean) and
 // the first 48 bytes of GShape (W, o, b); the forward needs no c or D cos(theta) per ray
 constexpr int kRec = 5;
+// Per batch, the Fourier-Legendre coefficients (L = 3: 128 bytes) of the first kCoefSlots
+// candidates of the ballot mask are staged with their records, in mask order, so that
+// their radiance reads shared memory instead of a cold global line; later candidates of
+// the batch read global memory.  Seven slots (7 KB per CTA) keep 7 CTAs per SM.
+constexpr int kCoefSlots = 7;
 
 struct RenderArgs {
     const GShape* shape;
@@ -152,7 +157,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <int NFC, int WB, int L, bool PATH = false, bool ORDER = false>
 __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int tile, int k,
                                              float4 (*sbuf)[WB][kRec], uint32_t (*sid)[WB], float4* spl,
-                                             float4 (*stin)[1]) {
+                                             float4 (*stin)[1], float4 (*scoef)[kCoefSlots][8]) {
     const int lane = threadIdx.x & 31;
     const gsrf_grid& gr = a.gr;
     const int chunk = k % a.nchunk, blk = k / a.nchunk;
@@ -202,35 +207,40 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
     // on one dependent load (the M block, only where the cone test passes) instead of
     // three (id, c, M).
     auto issue_tin = [&](int p0, uint32_t id) {
-        if (lane < WB && p0 + lane < len) {
-            const float4* vw = reinterpret_cast<const float4*>(view + id);
-            const float4* sh = reinterpret_cast<const float4*>(a.shape + id);
-            cp_async16(stin[lane] + 0, vw);
-        }
+        if (lane < WB && p0 + lane < len) cp_async16(stin[lane] + 0, reinterpret_cast<const float4*>(view + id));
         cp_async_commit();
     };
     // Test the batch at p0 against the warp's cone (c from its arrived stin slot) and
-    // half-spaces, and copy the records of the candidates that may be hit into buffer bf;
+    // half-spaces, and copy the records of the candidates that may be hit into buffer bf,
+    // with the coefficients of the first kCoefSlots of them (slot = rank in the mask);
     // returns the mask of candidates that may be hit.
     auto test_stage = [&](int bf, int p0, uint32_t id) -> uint32_t {
         bool keep = false;
         if (lane < WB && p0 + lane < len) {
             const float4 c = stin[lane][0];
             keep = bundle_meets(bundle_at(spl), c) && planes_meet(spl, c, a.shape + id);
-            if (keep) {
-                sid[bf][lane] = id;
-                const float4* vw = reinterpret_cast<const float4*>(view + id);
-                const float4* sh = reinterpret_cast<const float4*>(a.shape + id);
-                float4* dst = sbuf[bf][lane];
-                cp_async16(dst + 0, vw + 1);
-                cp_async16(dst + 1, vw + 2);
-                cp_async16(dst + 2, sh + 0);
-                cp_async16(dst + 3, sh + 1);
-                cp_async16(dst + 4, sh + 2);
+        }
+        const uint32_t kmask = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            sid[bf][lane] = id;
+            const float4* vw = reinterpret_cast<const float4*>(view + id);
+            const float4* sh = reinterpret_cast<const float4*>(a.shape + id);
+            float4* dst = sbuf[bf][lane];
+            cp_async16(dst + 0, vw + 1);
+            cp_async16(dst + 1, vw + 2);
+            cp_async16(dst + 2, sh + 0);
+            cp_async16(dst + 3, sh + 1);
+            cp_async16(dst + 4, sh + 2);
+            const int slot = __popc(kmask & ((1u << lane) - 1u));
+            if (L == 3 && slot < kCoefSlots) {
+                const float4* qf = reinterpret_cast<const float4*>(a.fle + (size_t)id * kFle);
+                float4* qd = scoef[bf][slot];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) cp_async16(qd + i, qf + i);
             }
         }
         cp_async_commit();
-        return __ballot_sync(0xffffffffu, keep);
+        return kmask;
     };
     auto list_id = [&](int p) -> uint32_t { return (lane < WB && p + lane < len) ? ids[p + lane] : 0u; };
 
@@ -261,8 +271,10 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
             id_t = id_n;
             id_n = list_id(p0 + 3 * WB);
             if (!done) {
+                int slot = -1;
                 for (uint32_t m = mask; m; m &= m - 1) {
                     const int j = __ffs(m) - 1;
+                    ++slot;
                     const float4* rec = sbuf[bf][j];
                     if ((a.variant & GSRF_VARIANT_PAPER_CULLING) &&
                         !circle_in(__ldg(a.circle + (size_t)r * a.n + sid[bf][j]), u, v))
@@ -299,8 +311,11 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
                         pr = rec[1].z;
                         pi = rec[1].w;
                     } else {
-                        fle_psi<L>(reinterpret_cast<const float4*>(a.fle + (size_t)sid[bf][j] * fle_floats(L)), P, Y,
-                                   pr, pi);
+                        if (L == 3 && slot < kCoefSlots)
+                            fle_psi<L, true>(scoef[bf][slot], P, Y, pr, pi);
+                        else
+                            fle_psi<L>(reinterpret_cast<const float4*>(a.fle + (size_t)sid[bf][j] * fle_floats(L)), P,
+                                       Y, pr, pi);
                     }
                     // S += alpha psi E T, E = e^{-j phi} = (er, ei)
                     float er = v1.w, ei = rec[1].x;
@@ -453,6 +468,7 @@ __global__ void __launch_bounds__(kThreads, NFC == 1 ? ((PATH || ORDER) ? 6 : (L
     __shared__ uint32_t sid[kWarps][2][WB];
     __shared__ float4 spl[kWarps][kPlaneSlots];
     __shared__ float4 stin[kWarps][WB][1];
+    __shared__ float4 scoef[kWarps][2][kCoefSlots][8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned per_rx = (unsigned)a.n_tiles * (unsigned)a.per_tile;
     for (;;) {
@@ -463,7 +479,7 @@ __global__ void __launch_bounds__(kThreads, NFC == 1 ? ((PATH || ORDER) ? 6 : (L
         const uint32_t id = order[it];
         const unsigned rem = id % per_rx;
         render_block<NFC, WB, L, PATH, ORDER>(a, (int)(id / per_rx), (int)(rem / (unsigned)a.per_tile),
-                                 (int)(rem % (unsigned)a.per_tile), sbuf[warp], sid[warp], spl[warp], stin[warp]);
+                                 (int)(rem % (unsigned)a.per_tile), sbuf[warp], sid[warp], spl[warp], stin[warp], scoef[warp]);
     }
 }
 
@@ -485,6 +501,7 @@ __global__ void __launch_bounds__(kThreads, 6)
     __shared__ uint32_t sid[kWarps][2][WB];
     __shared__ float4 spl[kWarps][kPlaneSlots];
     __shared__ float4 stin[kWarps][WB][1];
+    __shared__ float4 scoef[kWarps][2][kCoefSlots][8];
     __shared__ RenderArgs sjob[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned long long total = item_base[n_jobs];
@@ -516,7 +533,7 @@ __global__ void __launch_bounds__(kThreads, 6)
         const unsigned long long per_rx = (unsigned long long)a.n_tiles * a.per_tile;
         const unsigned rem = (unsigned)(local % per_rx);
         render_block<1, WB, 3>(a, (int)(local / per_rx), (int)(rem / (unsigned)a.per_tile),
-                               (int)(rem % (unsigned)a.per_tile), sbuf[warp], sid[warp], spl[warp], stin[warp]);
+                               (int)(rem % (unsigned)a.per_tile), sbuf[warp], sid[warp], spl[warp], stin[warp], scoef[warp]);
         if (job_done && lane == 0) atomicMax(job_done + j, global_ns());
     }
 }
