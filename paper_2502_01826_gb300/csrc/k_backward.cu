@@ -29,6 +29,11 @@ namespace gsrf {
 constexpr int kBW = 4;           // warps per CTA
 constexpr int kBThreads = 32 * kBW;
 constexpr int kBB = 32;          // candidates per warp batch
+// Per batch, the Fourier-Legendre coefficients (L = 3) of the kBCoefSlots candidates of the
+// mask that the reverse walk meets first (the highest list positions) are staged in shared
+// memory with their records, so that their radiance reads shared memory; the others read
+// global memory.  10 slots (10 KB per CTA) keep 5 CTAs per SM.
+constexpr int kBCoefSlots = 10;
 // Accumulator floats per Gaussian: W 9, mu 3, o, b, then the coefficient gradients in
 // chunks of 32 (dL/d psi_re and dL/d psi_im times 16 basis values each) -- grad_floats(L)
 // in the internal header; 48 at L <= 3.
@@ -95,7 +100,8 @@ __device__ __forceinline__ float reduce_scatter16(float* v, int lane) {
 // Every chunk adds its share of the gradient to the same accumulators.
 template <int NFC, int L>
 __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int k, float4 (*sbuf)[kBB][6],
-                                          uint32_t (*sid)[kBB], float4* spl, float (*sbp)[32]) {
+                                          uint32_t (*sid)[kBB], float4* spl, float (*sbp)[32],
+                                          float4 (*scoef)[kBCoefSlots][8]) {
     constexpr int NB = (L + 1) * (L + 1), NCH = grad_chunks(L);
     const int lane = threadIdx.x & 31;
     const gsrf_grid& gr = a.gr;
@@ -180,20 +186,30 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
             const float4* vw = reinterpret_cast<const float4*>(view + id);
             const float4 c = __ldg(vw);
             keep = bundle_meets(bundle_at(spl), c) && planes_meet(spl, c, a.shape + id);
-            if (keep) {
-                sid[bf][lane] = id;
-                const float4* sh = reinterpret_cast<const float4*>(a.shape + id);
-                float4* dst = sbuf[bf][lane];
-                dst[0] = c;
-                cp_async16b(dst + 1, vw + 1);
-                cp_async16b(dst + 2, vw + 2);
-                cp_async16b(dst + 3, sh + 0);
-                cp_async16b(dst + 4, sh + 1);
-                cp_async16b(dst + 5, sh + 2);
+        }
+        const uint32_t kmask = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const uint32_t id = ids[p0 + lane];
+            const float4* vw = reinterpret_cast<const float4*>(view + id);
+            sid[bf][lane] = id;
+            const float4* sh = reinterpret_cast<const float4*>(a.shape + id);
+            float4* dst = sbuf[bf][lane];
+            dst[0] = __ldg(vw);
+            cp_async16b(dst + 1, vw + 1);
+            cp_async16b(dst + 2, vw + 2);
+            cp_async16b(dst + 3, sh + 0);
+            cp_async16b(dst + 4, sh + 1);
+            cp_async16b(dst + 5, sh + 2);
+            // slot = rank from the top of the mask (the walk goes from high positions down)
+            const int slot = __popc(kmask >> lane) - 1;
+            if (L == 3 && slot < kBCoefSlots) {
+                const float4* qf = reinterpret_cast<const float4*>(a.fle + (size_t)id * kFle);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) cp_async16b(scoef[bf][slot] + i, qf + i);
             }
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
-        return __ballot_sync(0xffffffffu, keep);
+        return kmask;
     };
 
     // batches that hold list positions 0 .. wlast, from the last one down
@@ -205,9 +221,11 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
         const uint32_t next = b0 - kBB >= 0 ? stage(bf ^ 1, b0 - kBB, end) : (stage(bf ^ 1, end, end), 0u);
         asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         __syncwarp();
+        int slot = -1;
         for (uint32_t m = mask; m;) {
             const int j = 31 - __clz(m);
             m &= ~(1u << j);
+            ++slot;
             const int pos = b0 + j;
             const float4* rec = sbuf[bf][j];
             const float4 v1 = rec[1], s0 = rec[3], s1 = rec[4], s2 = rec[5];
@@ -230,7 +248,11 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
                 const float alpha = pair_alpha(o, pg.m2r, amax, gw);
                 const bool clamped = o * gw >= amax;
                 float pr, pi;
-                fle_psi<L>(reinterpret_cast<const float4*>(a.fle + (size_t)sid[bf][j] * fle_floats(L)), P, Y, pr, pi);
+                if (L == 3 && slot < kBCoefSlots)
+                    fle_psi<L, true>(scoef[bf][slot], P, Y, pr, pi);
+                else
+                    fle_psi<L>(reinterpret_cast<const float4*>(a.fle + (size_t)sid[bf][j] * fle_floats(L)), P, Y, pr,
+                               pi);
                 // T before this pair: undo (1 - alpha) e^{-j theta}
                 float sn, cs;
                 phase_rot(a.om_pi * s2.z * pg.dt, sn, cs);
@@ -408,6 +430,7 @@ __global__ void __launch_bounds__(kBThreads, NFC == 1 ? (L <= 3 ? 5 : (L == 4 ? 
     __shared__ uint32_t sid[kBW][2][kBB];
     __shared__ float4 spl[kBW][kPlaneSlots];
     __shared__ float sbp[kBW][16 * grad_chunks(L)][32];
+    __shared__ float4 scoef[kBW][2][kBCoefSlots][8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned per_rx = (unsigned)a.n_tiles * (unsigned)a.per_tile;
     for (;;) {
@@ -418,7 +441,7 @@ __global__ void __launch_bounds__(kBThreads, NFC == 1 ? (L <= 3 ? 5 : (L == 4 ? 
         const uint32_t id = order[it];
         const unsigned rem = id % per_rx;
         bwd_block<NFC, L>(a, (int)(id / per_rx), (int)(rem / (unsigned)a.per_tile), (int)(rem % (unsigned)a.per_tile),
-                          sbuf[warp], sid[warp], spl[warp], sbp[warp]);
+                          sbuf[warp], sid[warp], spl[warp], sbp[warp], scoef[warp]);
         __syncwarp();
     }
 }
