@@ -59,8 +59,9 @@ struct BwdArgs {
     float dlt;    // 2 pi df / c
     int bw_log;   // log2 of the ray-block width (block height 32 / width)
     int nbx;      // ray blocks per tile along azimuth
-    int per_tile; // work items per tile: ray blocks x subcarrier chunks
-    int nchunk;   // subcarrier chunks of NFC
+    int per_tile; // work items per tile: ray blocks
+    int g_pairs;  // several frequencies: subcarrier pairs of the upstream gradient, ceil(n_f / 2)
+    int g_stride4;  // float4s per lane row of it in shared memory (g_pairs, made odd)
     int n_rx;
     const float4* ck;  // the forward's transmittance checkpoints [slot][ray], or null
     int variant;       // 0, or GSRF_VARIANT_NORMALISED_WEIGHT / GSRF_VARIANT_PAPER_CULLING bits
@@ -91,22 +92,25 @@ __device__ __forceinline__ float reduce_scatter16(float* v, int lane) {
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-// One warp's work item k of tile `tile` for receiver r: ray block k / nchunk, subcarrier
-// chunk k % nchunk.  NFC = 1: one frequency.  NFC > 1: the lanes take subcarriers
-// fs0 .. fs0 + NFC - 1 (fs0 = NFC chunk) of f0 + s df.  The pair's contribution there is
-// z_k(f0) r_k^s with r_k = e^{-j (2 pi df d_k / c + 2 pi df Gamma_k / c)} (Gamma_k = sum
-// of b dt in front of k), exactly as the forward builds it; each subcarrier keeps its own
-// suffix R, and the transmittance and path phases enter with their own 2 pi f_s / c.
-// Every chunk adds its share of the gradient to the same accumulators.
-template <int NFC, int L>
+// One warp's work item: ray block k of tile `tile` for receiver r.  MF = false: one
+// frequency.  MF = true: all n_f subcarriers f0 + s df in one walk.  There the pair's
+// contribution at subcarrier s is z_k r_k^s, r_k = e^{-j (2 pi df d_k / c + 2 pi df
+// Gamma_k / c)} (Gamma_k = sum of b dt in front of k), exactly as the forward builds it.
+// With c_s = conj(G_s), every sum over s that the gradient needs is one of
+//     H_k = sum_s c_s r_k^s,   H'_k = sum_s omega_s c_s r_k^s,
+// and the suffix sums Q_k = sum_{j>k} alpha_j psi_j w_j H_j (and Q' with H'), which
+// replace the n_f suffixes R_s: sum_s c_s R_{k,s} = Q_k.  Per pair the lane evaluates H
+// and H' by Horner's rule over the ray's n_f upstream values (held in shared memory):
+// with omega_s = omega_0 + s 2 pi df / c, H' = omega_0 H + (2 pi df / c) r dH/dr, and
+// Horner's rule gives dH/dr in the same pass.
+template <bool MF, int L>
 __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int k, float4 (*sbuf)[kBB][6],
                                           uint32_t (*sid)[kBB], float4* spl, float (*sbp)[32],
-                                          float4 (*scoef)[kBCoefSlots][8]) {
+                                          float4 (*scoef)[kBCoefSlots][8], float4* sg) {
     constexpr int NB = (L + 1) * (L + 1), NCH = grad_chunks(L);
     const int lane = threadIdx.x & 31;
     const gsrf_grid& gr = a.gr;
-    const int chunk = k % a.nchunk, blk = k / a.nchunk;
-    const int fs0 = chunk * NFC;  // first subcarrier of the chunk
+    const int blk = k;
     const int bw = 1 << a.bw_log, bh = 32 >> a.bw_log;
     const int tu = tile % a.ntu, tv = tile / a.ntu;
     const int u_lo = tu * gr.tile_w + (blk % a.nbx) * bw, v_lo = tv * gr.tile_h + (blk / a.nbx) * bh;
@@ -121,26 +125,27 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
     for (int i = 0; i < L * (L + 1); ++i) Y[i] = 0.0f;
     int last = -1;
     float Tr = 0.0f, Ti = 0.0f, Gam = 0.0f;
-    float Gs[2 * NFC], Rs[2 * NFC];  // upstream G and suffix R per subcarrier of the chunk
-#pragma unroll
-    for (int i = 0; i < 2 * NFC; ++i) Gs[i] = Rs[i] = 0.0f;
+    float Gr = 0.0f, Gi = 0.0f, Rr = 0.0f, Ri = 0.0f;  // one frequency: upstream G and suffix R
+    float Qr = 0.0f, Qi = 0.0f, Q2r = 0.0f, Q2i = 0.0f;  // several: the suffix sums Q and Q'
+    const size_t plane = (size_t)gr.n_el * gr.n_az, pix = valid ? (size_t)v * gr.n_az + u : 0;
     if (valid) {
-        load_ray<L>(a.raytab, (size_t)v * gr.n_az + u, dx, dy, dz, P, Y);
-        const size_t plane = (size_t)gr.n_el * gr.n_az, pix = (size_t)v * gr.n_az + u;
+        load_ray<L>(a.raytab, pix, dx, dy, dz, P, Y);
         const RayState s = a.rs[(size_t)r * plane + pix];
         last = s.last;
         Tr = s.Tr;
         Ti = s.Ti;
         Gam = s.Gam;
-        const float2* g2 = reinterpret_cast<const float2*>(a.grad_rays) + ((size_t)r * a.n_f + fs0) * plane + pix;
-#pragma unroll
-        for (int q = 0; q < NFC; ++q) {
-            if (fs0 + q < a.n_f) {
-                const float2 gq2 = g2[(size_t)q * plane];
-                Gs[2 * q] = gq2.x;
-                Gs[2 * q + 1] = gq2.y;
-            }
+        if constexpr (!MF) {
+            const float2 g = reinterpret_cast<const float2*>(a.grad_rays)[(size_t)r * plane + pix];
+            Gr = g.x;
+            Gi = g.y;
         }
+    }
+    if constexpr (MF) {  // this lane's row: G_0 .. G_{n_f - 1}, zero-padded to 2 g_pairs
+        float2* row = reinterpret_cast<float2*>(sg + lane * a.g_stride4);
+        const float2* g2 = reinterpret_cast<const float2*>(a.grad_rays) + (size_t)r * a.n_f * plane + pix;
+        for (int s = 0; s < 2 * a.g_pairs; ++s)
+            row[s] = (valid && s < a.n_f) ? g2[(size_t)s * plane] : make_float2(0.0f, 0.0f);
     }
     // The ray's basis in the order of the coefficient accumulators -- 1, P_10 .. P_L0,
     // then (Re, Im) of the Y_{l,m>0} in m-major order, zero-padded to chunks of 16 --
@@ -265,8 +270,7 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
                 const float er = v1.w, ei = rec[2].x;
                 const float wr = er * Tr - ei * Ti, wi = er * Ti + ei * Tr;
                 float g_alpha, Theta, Phi;
-                if constexpr (NFC == 1) {
-                    const float Gr = Gs[0], Gi = Gs[1], Rr = Rs[0], Ri = Rs[1];
+                if constexpr (!MF) {
                     const float zr = alpha * (pr * wr - pi * wi), zi = alpha * (pr * wi + pi * wr);
                     const float Xr = pr * wr - pi * wi - Rr * iom, Xi = pr * wi + pi * wr - Ri * iom;
                     g_alpha = Gr * Xr + Gi * Xi;
@@ -275,37 +279,46 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
                     const float ur = alpha * wr, ui = alpha * wi;
                     g_pr = Gr * ur + Gi * ui;
                     g_pi = Gi * ur - Gr * ui;
-                    Rs[0] = Rr + zr;
-                    Rs[1] = Ri + zi;
+                    Rr += zr;
+                    Ri += zi;
                 } else {
                     Gam -= s2.z * pg.dt;  // Gamma in front of this pair
                     const float ws = rec[2].y + a.dlt * Gam;
-                    float rs, rc, ss, sc;
-                    sincosf(ws, &rs, &rc);
-                    sincosf((float)fs0 * ws, &ss, &sc);
-                    // w and psi w at the chunk's first subcarrier, then one rotation per step
-                    float Wr = wr * sc + wi * ss, Wi = wi * sc - wr * ss;
-                    float pwr = pr * Wr - pi * Wi, pwi = pr * Wi + pi * Wr;
-                    g_alpha = Theta = Phi = g_pr = g_pi = 0.0f;
-#pragma unroll
-                    for (int q = 0; q < NFC; ++q) {
-                        const float Gr = Gs[2 * q], Gi = Gs[2 * q + 1], Rr = Rs[2 * q], Ri = Rs[2 * q + 1];
-                        const float om_s = omega + (float)(fs0 + q) * a.dlt;
-                        const float zr = alpha * pwr, zi = alpha * pwi;
-                        g_alpha += Gr * (pwr - Rr * iom) + Gi * (pwi - Ri * iom);
-                        Theta += om_s * (Gr * Ri - Gi * Rr);
-                        Phi += om_s * (Gr * zi - Gi * zr);
-                        g_pr += alpha * (Gr * Wr + Gi * Wi);
-                        g_pi += alpha * (Gi * Wr - Gr * Wi);
-                        Rs[2 * q] = Rr + zr;
-                        Rs[2 * q + 1] = Ri + zi;
-                        const float nWr = Wr * rc + Wi * rs;
-                        Wi = Wi * rc - Wr * rs;
-                        Wr = nWr;
-                        const float npr = pwr * rc + pwi * rs;
-                        pwi = pwi * rc - pwr * rs;
-                        pwr = npr;
+                    float rs, rc;
+                    sincosf(ws, &rs, &rc);  // r = e^{-j ws} = rc - j rs
+                    // Horner over s = 2 g_pairs - 1 .. 0: D <- D r + H, H <- H r + conj(G_s)
+                    const float4* row = sg + lane * a.g_stride4;
+                    float hr = 0.0f, hi = 0.0f, dr = 0.0f, di = 0.0f;
+                    for (int i = a.g_pairs - 1; i >= 0; --i) {
+                        const float4 c = row[i];  // G_{2i} (x, y), G_{2i+1} (z, w)
+                        float t = dr * rc + di * rs + hr;
+                        di = di * rc - dr * rs + hi;
+                        dr = t;
+                        t = hr * rc + hi * rs + c.z;
+                        hi = hi * rc - hr * rs - c.w;
+                        hr = t;
+                        t = dr * rc + di * rs + hr;
+                        di = di * rc - dr * rs + hi;
+                        dr = t;
+                        t = hr * rc + hi * rs + c.x;
+                        hi = hi * rc - hr * rs - c.y;
+                        hr = t;
                     }
+                    // H' = omega_0 H + dlt r dH/dr
+                    const float h2r = omega * hr + a.dlt * (dr * rc + di * rs);
+                    const float h2i = omega * hi + a.dlt * (di * rc - dr * rs);
+                    const float pwr = pr * wr - pi * wi, pwi = pr * wi + pi * wr;  // psi w at f0
+                    const float xr = pwr * hr - pwi * hi, xi = pwr * hi + pwi * hr;  // psi w H
+                    const float yr = pwr * h2r - pwi * h2i, yi = pwr * h2i + pwi * h2r;  // psi w H'
+                    g_alpha = xr - Qr * iom;
+                    Theta = Q2i;
+                    Phi = alpha * yi;
+                    g_pr = alpha * (wr * hr - wi * hi);
+                    g_pi = -alpha * (wr * hi + wi * hr);
+                    Qr += alpha * xr;
+                    Qi += alpha * xi;
+                    Q2r += alpha * yr;
+                    Q2i += alpha * yi;
                 }
                 // transmittance phase theta_s = omega_s b dt
                 const float g_b = Theta * pg.dt;
@@ -416,14 +429,13 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Persistent launch: every warp takes work items (receiver, tile, ray block, subcarrier
-// chunk) from one counter, heaviest first, until none is left.  One frequency: 5 CTAs
-// per SM up to L = 3 (at most 102 registers, no spills), 4 at L = 4, 3 at L = 5 (the
-// larger basis); chunks of 8 subcarriers (L = 3): 3 (at most 168; 4 would spill); of
-// 16: 2.  More than 8 subcarriers go in chunks of 16: half the walks of chunks of 8 for
-// 64 subcarriers, which outweighs the lower occupancy.
-template <int NFC, int L>
-__global__ void __launch_bounds__(kBThreads, NFC == 1 ? (L <= 3 ? 5 : (L == 4 ? 4 : 3)) : (NFC == 8 ? 3 : 2))
+// Persistent launch: every warp takes work items (receiver, tile, ray block) from one
+// counter, heaviest first, until none is left.  One frequency: 5 CTAs per SM up to L = 3
+// (at most 102 registers, no spills), 4 at L = 4, 3 at L = 5 (the larger basis).  Several
+// frequencies: 2, with each warp's upstream rows in dynamic shared memory (66 KB per CTA
+// at 64 subcarriers).
+template <bool MF, int L>
+__global__ void __launch_bounds__(kBThreads, MF ? 2 : (L <= 3 ? 5 : (L == 4 ? 4 : 3)))
     k_render_bwd(BwdArgs a, const uint32_t* __restrict__ order, unsigned long long* __restrict__ counter,
                  unsigned long long total) {
     __shared__ float4 sbuf[kBW][2][kBB][6];
@@ -431,6 +443,7 @@ __global__ void __launch_bounds__(kBThreads, NFC == 1 ? (L <= 3 ? 5 : (L == 4 ? 
     __shared__ float4 spl[kBW][kPlaneSlots];
     __shared__ float sbp[kBW][16 * grad_chunks(L)][32];
     __shared__ float4 scoef[kBW][2][kBCoefSlots][8];
+    extern __shared__ float4 sgrad[];  // several frequencies: [warp][lane][g_stride4]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned per_rx = (unsigned)a.n_tiles * (unsigned)a.per_tile;
     for (;;) {
@@ -440,8 +453,9 @@ __global__ void __launch_bounds__(kBThreads, NFC == 1 ? (L <= 3 ? 5 : (L == 4 ? 
         if (it >= total) break;
         const uint32_t id = order[it];
         const unsigned rem = id % per_rx;
-        bwd_block<NFC, L>(a, (int)(id / per_rx), (int)(rem / (unsigned)a.per_tile), (int)(rem % (unsigned)a.per_tile),
-                          sbuf[warp], sid[warp], spl[warp], sbp[warp], scoef[warp]);
+        bwd_block<MF, L>(a, (int)(id / per_rx), (int)(rem / (unsigned)a.per_tile), (int)(rem % (unsigned)a.per_tile),
+                         sbuf[warp], sid[warp], spl[warp], sbp[warp], scoef[warp],
+                         MF ? sgrad + (size_t)warp * 32 * a.g_stride4 : nullptr);
         __syncwarp();
     }
 }
@@ -574,9 +588,10 @@ cudaError_t launch_render_bwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     const int bw = plan_block_w(p);
     a.bw_log = __builtin_ctz((unsigned)bw);
     a.nbx = p->grid.tile_w / bw;
-    const int nfc = p->n_f == 1 ? 1 : (p->n_f <= 8 ? 8 : 16);
-    a.nchunk = (p->n_f + nfc - 1) / nfc;
-    a.per_tile = (p->grid.tile_w * p->grid.tile_h / 32) * a.nchunk;
+    a.per_tile = p->grid.tile_w * p->grid.tile_h / 32;
+    a.g_pairs = (p->n_f + 1) / 2;
+    a.g_stride4 = a.g_pairs | 1;  // an odd stride keeps the lanes' 16-byte reads conflict-free
+    const size_t dyn = p->n_f > 1 ? (size_t)kBW * 32 * a.g_stride4 * sizeof(float4) : 0;
     a.n_rx = L.n_rx;
     const size_t rays = (size_t)p->n_rx * p->grid.n_az * p->grid.n_el;
     a.ck = p->ckpt_every > 0
@@ -594,25 +609,25 @@ cudaError_t launch_render_bwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     auto run = [&](auto kernel) -> cudaError_t {
+        cudaError_t r = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (r != cudaSuccess) return r;
         int per_sm = 0;
-        cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBThreads, 0);
+        r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBThreads, dyn);
         if (r != cudaSuccess) return r;
         const int grid = (int)max(1ll, min((long long)sms * max(per_sm, 1), (n + kBW - 1) / kBW));
-        kernel<<<grid, kBThreads, 0, st>>>(a, order, counter, (unsigned long long)n);
+        kernel<<<grid, kBThreads, dyn, st>>>(a, order, counter, (unsigned long long)n);
         return cudaGetLastError();
     };
     if (p->n_f == 1) {
         switch (deg) {  // several frequencies: L = 3 only (checked with the plan)
-            case 1: e = run(k_render_bwd<1, 1>); break;
-            case 2: e = run(k_render_bwd<1, 2>); break;
-            case 4: e = run(k_render_bwd<1, 4>); break;
-            case 5: e = run(k_render_bwd<1, 5>); break;
-            default: e = run(k_render_bwd<1, 3>); break;
+            case 1: e = run(k_render_bwd<false, 1>); break;
+            case 2: e = run(k_render_bwd<false, 2>); break;
+            case 4: e = run(k_render_bwd<false, 4>); break;
+            case 5: e = run(k_render_bwd<false, 5>); break;
+            default: e = run(k_render_bwd<false, 3>); break;
         }
-    } else if (nfc == 8) {
-        e = run(k_render_bwd<8, 3>);
     } else {
-        e = run(k_render_bwd<16, 3>);
+        e = run(k_render_bwd<true, 3>);
     }
     if (e != cudaSuccess) return e;
     const unsigned nb = (unsigned)((L.n + 255) / 256);

@@ -97,10 +97,11 @@ def test_backward_matches_oracle_gradient_small():
     compare_grads(gpu_grads(scene, rx, tx, 2.4e9, spec, G), oracle_grads(scene, rx, tx, 2.4e9, g, G))
 
 
-@pytest.mark.parametrize("n_f,df", [(3, 2.0e7), (12, 2.0e6)])
+@pytest.mark.parametrize("n_f,df", [(3, 2.0e7), (12, 2.0e6), (64, 312.5e3)])
 def test_backward_multifrequency_matches_oracle(n_f, df):
-    """Subcarriers f0 + s df (12 = one chunk of 8 and a ragged one of 4): every
-    subcarrier's upstream enters with its own suffix sum and its own 2 pi f_s / c."""
+    """Subcarriers f0 + s df, all in one reverse walk (3: an odd count, whose last pair is
+    zero-padded; 64 at 312.5 kHz: the CSI workload's band): every subcarrier's upstream
+    enters with its own suffix sum and its own 2 pi f_s / c."""
     scene = synthetic.tiny_scene(300, 203, box=(6.0, 5.0, 3.0), log_scale_mu=math.log(0.25))
     rng = np.random.default_rng(4)
     rx = (rng.uniform(0, 1, (2, 3)) * [6.0, 5.0, 3.0]).astype(np.float32)
