@@ -456,10 +456,13 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
 // left; a warp that finishes early takes the next item instead of idling until the
 // other warps of its CTA are done.
 // One frequency: 7 CTAs per SM up to L = 3 (72 registers), fewer for the larger bases of
-// L = 4 and 5; chunks of subcarriers (L = 3 only): 4.  PATH: the path-through-x_rep
+// L = 4 and 5.  Several frequencies (L = 3 only) take one chunk of 8, 16, 32 or 64
+// subcarriers per walk, the smallest that holds n_f (so at most 64 subcarriers need one
+// walk; more per lane costs registers, not walks): 4 CTAs per SM for chunks of 8 and 16,
+// 3 for 32 (168 registers), 2 for 64 (242, no spills).  PATH: the path-through-x_rep
 // variant, a separate instance so that its arithmetic costs the others no registers.
 template <int NFC, int WB, int L, bool PATH = false, bool ORDER = false>
-__global__ void __launch_bounds__(kThreads, NFC == 1 ? ((PATH || ORDER) ? 6 : (L <= 3 ? 7 : (L == 4 ? 6 : 5))) : 4)
+__global__ void __launch_bounds__(kThreads, NFC == 1 ? ((PATH || ORDER) ? 6 : (L <= 3 ? 7 : (L == 4 ? 6 : 5))) : (NFC <= 16 ? 4 : (NFC == 32 ? 3 : 2)))
     k_render_queue(RenderArgs a,
                                                                             const uint32_t* __restrict__ order,
                                                                             unsigned long long* __restrict__ counter,
@@ -635,7 +638,7 @@ static RenderArgs render_args(const gsrf_plan* p, const Layout& L, void* ws, flo
     const int bw = plan_block_w(p);
     a.bw_log = __builtin_ctz((unsigned)bw);
     a.nbx = p->grid.tile_w / bw;
-    const int nfc = p->n_f == 1 ? 1 : (p->n_f <= 8 ? 8 : 16);
+    const int nfc = p->n_f == 1 ? 1 : (p->n_f <= 8 ? 8 : (p->n_f <= 16 ? 16 : (p->n_f <= 32 ? 32 : 64)));
     a.nchunk = (p->n_f + nfc - 1) / nfc;
     a.per_tile = (p->grid.tile_w * p->grid.tile_h / 32) * a.nchunk;
     const size_t rays = (size_t)p->n_rx * p->grid.n_az * p->grid.n_el;
@@ -696,7 +699,9 @@ cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_ga
         return wb16 ? launch_queue_degree<16>(plan_degree(p), a, order, counter, n, st)
                     : launch_queue_degree<32>(plan_degree(p), a, order, counter, n, st);
     if (p->n_f <= 8) return wb16 ? launch_queue<8, 16>(a, order, counter, n, st) : launch_queue<8, 32>(a, order, counter, n, st);
-    return wb16 ? launch_queue<16, 16>(a, order, counter, n, st) : launch_queue<16, 32>(a, order, counter, n, st);
+    if (p->n_f <= 16) return wb16 ? launch_queue<16, 16>(a, order, counter, n, st) : launch_queue<16, 32>(a, order, counter, n, st);
+    if (p->n_f <= 32) return wb16 ? launch_queue<32, 16>(a, order, counter, n, st) : launch_queue<32, 32>(a, order, counter, n, st);
+    return wb16 ? launch_queue<64, 16>(a, order, counter, n, st) : launch_queue<64, 32>(a, order, counter, n, st);
 }
 
 long long batch_items(int n_jobs, const gsrf_plan* plans) {

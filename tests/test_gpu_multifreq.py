@@ -38,8 +38,11 @@ def render_mf(scene, rx, tx, f0, df, n_f, spec):
     return out, R
 
 
-@pytest.mark.parametrize("n_f", [3, 8, 64])
+@pytest.mark.parametrize("n_f", [3, 8, 24, 40, 64])
 def test_subcarriers_match_oracle(n_f):
+    """Each subcarrier against the oracle, and the CSI sum per subcarrier.  The walk takes
+    the smallest chunk of 8, 16, 32 or 64 subcarriers that holds n_f (24 and 40: ragged
+    chunks of 32 and 64; 64: the CSI band in one walk, its phase recurrence 64 steps long)."""
     cfg = synthetic.config_csi(K=3000)
     rx = cfg["rx"][:4]  # one four-element array
     spec = cfg["grid"]
