@@ -20,7 +20,7 @@ bool make_layout(const gsrf_plan* p, Layout* L) {
     L->n_rx = p->n_rx;
     L->n = p->n_gauss;
     L->cap = p->pair_capacity;
-    L->dchunks = (int32_t)((p->n_gauss + kChunk - 1) / kChunk);
+    L->dchunks = (int32_t)((p->n_gauss + kDChunk - 1) / kDChunk);
     L->echunks = (int32_t)((p->n_gauss + kEChunk - 1) / kEChunk);
     L->pchunks_max = (p->pair_capacity + kChunk - 1) / kChunk + p->n_rx;
     const size_t n = (size_t)p->n_gauss, nr = (size_t)p->n_rx, cap = (size_t)p->pair_capacity;
@@ -45,6 +45,7 @@ bool make_layout(const gsrf_plan* p, Layout* L) {
     L->dval = take(nr * n * 4);
     L->dval2 = take(nr * n * 4);
     L->dhist = take(nr * (size_t)L->dchunks * 256 * 4);
+    L->dvis = take(nr * 4);
     L->dchunk_sum = take(nr * (size_t)L->echunks * 4);
     L->rx_base = take((nr + 1) * 8);
     L->rx_total = take(nr * 4);

@@ -14,10 +14,14 @@ constexpr double kC = 3.0e8;          // propagation speed (Sec. 2 worked exampl
 constexpr int kTile = 16;             // rays per tile side (App. E)
 constexpr int kRenderThreads = kTile * kTile;
 constexpr int kChunk = 4096;          // items per block in the sort passes
+constexpr int kDChunk = 2048;         // items per block in the depth passes
 constexpr int kEChunk = 1024;         // depth-sorted Gaussians per block in the emission
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kMaxTiles = 1024;       // bins of the tile counting sort
+// The depth key of a (receiver, Gaussian) that covers no tile: an FP32 NaN pattern, which
+// no distance has, so the depth sort can leave such Gaussians out.
+constexpr uint32_t kAbsentKey = 0xffffffffu;
 constexpr int kMaxNf = 64;
 
 // Per-Gaussian shape record: whitening matrix W = diag(1/s) R^T (so that
@@ -106,7 +110,7 @@ struct __align__(16) RayState {
 
 struct Layout {
     // byte offsets
-    size_t status, rxpos, txpos, gacc, raytab, fle, gshape, dpath, view, cover, dkey, dkey2, dval, dval2, dhist, dchunk_sum,
+    size_t status, rxpos, txpos, gacc, raytab, fle, gshape, dpath, view, cover, dkey, dkey2, dval, dval2, dhist, dvis, dchunk_sum,
         rx_base, rx_total, pchunk_base, pkeys, pkeys2, pids, pids2, tile_start, thist, qkeys, qkeys2, qorder, qhist,
         qcounter, circle, tbuf, total;
     int32_t ntu, ntv, n_tiles;

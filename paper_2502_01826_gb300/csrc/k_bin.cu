@@ -15,14 +15,20 @@
 
 namespace gsrf {
 
-// Which items a block owns.  Segments are receivers; either all of length eq_len or
-// given by base[] with chunk_base[] = prefix of ceil(len / kChunk).
+// Which items a block owns.  Segments are receivers; either one every eq_len items (of
+// length eq_len, or len[s] <= eq_len when len is given: the blocks past a segment's end
+// own nothing) or given by base[] with chunk_base[] = prefix of ceil(len / kChunk).
+// drop: keys equal to kAbsentKey are left out (counted by no histogram, written by no
+// scatter), so a pass that drops them compacts each segment.
 struct Segs {
     int n_seg;
-    long long eq_len;  // >= 0: equal segments
-    int eq_chunks;
+    long long eq_len;  // >= 0: segments at multiples of eq_len, in blocks of eq_chunk items
+    int eq_chunks;     // blocks per segment (ceil(eq_len / eq_chunk))
+    int eq_chunk;
     const long long* base;
     const uint32_t* chunk_base;
+    const uint32_t* len;  // equal-stride segments: their lengths (null: eq_len each)
+    int drop;
 };
 
 __device__ __forceinline__ bool block_items(const Segs& S, long long b, long long& lo, long long& hi,
@@ -32,8 +38,8 @@ __device__ __forceinline__ bool block_items(const Segs& S, long long b, long lon
         const long long c = b % S.eq_chunks;
         if (seg >= S.n_seg) return false;
         seg_lo = (long long)seg * S.eq_len;
-        lo = seg_lo + c * kChunk;
-        hi = min(lo + (long long)kChunk, seg_lo + S.eq_len);
+        lo = seg_lo + c * S.eq_chunk;
+        hi = min(lo + (long long)S.eq_chunk, seg_lo + (S.len ? (long long)S.len[seg] : S.eq_len));
         return lo < hi;
     }
     if (b >= (long long)S.chunk_base[S.n_seg]) return false;
@@ -53,7 +59,7 @@ __device__ __forceinline__ bool block_items(const Segs& S, long long b, long lon
 __device__ __forceinline__ void chunk_range(const Segs& S, int seg, long long& c0, long long& c1) {
     if (S.eq_len >= 0) {
         c0 = (long long)seg * S.eq_chunks;
-        c1 = c0 + S.eq_chunks;
+        c1 = c0 + (S.len ? (long long)((S.len[seg] + S.eq_chunk - 1) / S.eq_chunk) : S.eq_chunks);
     } else {
         c0 = S.chunk_base[seg];
         c1 = S.chunk_base[seg + 1];
@@ -80,7 +86,10 @@ __global__ void __launch_bounds__(kSortThreads) k_hist(const K* __restrict__ key
     if (!block_items(S, blockIdx.x, lo, hi, seg_lo, seg)) return;
     for (int i = threadIdx.x; i < nbins; i += kSortThreads) h[i] = 0;
     __syncthreads();
-    for (long long i = lo + threadIdx.x; i < hi; i += kSortThreads) atomicAdd(&h[digit_of(keys[i], shift, mask)], 1u);
+    for (long long i = lo + threadIdx.x; i < hi; i += kSortThreads) {
+        const K key = keys[i];
+        if (!(S.drop && key == (K)kAbsentKey)) atomicAdd(&h[digit_of(key, shift, mask)], 1u);
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < nbins; i += kSortThreads) H[(size_t)blockIdx.x * nbins + i] = h[i];
 }
@@ -109,10 +118,11 @@ __device__ __forceinline__ T block_excl_scan(T v, T* total, T* sh /* [kSortWarps
 }
 
 // One block per segment: turn per-block digit counts H[block][digit] into absolute
-// destinations inside the segment; optionally record each digit's [start, end).
+// destinations inside the segment; optionally record each digit's [start, end) and the
+// segment's item count.
 __global__ void __launch_bounds__(kSortThreads) k_scan(Segs S, int nbins, uint32_t* __restrict__ H,
                                                        uint32_t* __restrict__ bin_start,
-                                                       const DevStatus* st) {
+                                                       const DevStatus* st, uint32_t* __restrict__ seg_total = nullptr) {
     if (capacity_failed(st)) return;
     __shared__ uint32_t tot[kMaxTiles];
     __shared__ uint32_t sh[kSortWarps];
@@ -156,6 +166,7 @@ __global__ void __launch_bounds__(kSortThreads) k_scan(Segs S, int nbins, uint32
         carry += t;
     }
     if (bin_start && threadIdx.x == 0) bin_start[(size_t)seg * (nbins + 1) + nbins] = carry;
+    if (seg_total && threadIdx.x == 0) seg_total[seg] = carry;
 }
 
 // Stable scatter.  vin == nullptr: the value is the item's index inside its segment.
@@ -180,11 +191,14 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const K* __restrict__ 
     const uint32_t lt = (1u << lane) - 1u;
     for (long long r0 = lo; r0 < hi; r0 += kSortThreads) {
         const long long i = r0 + threadIdx.x;
-        const bool valid = i < hi;
+        bool valid = i < hi;
         K key = 0;
         uint32_t val = 0, d = 0xffffffffu;
         if (valid) {
             key = kin[i];
+            valid = !(S.drop && key == (K)kAbsentKey);
+        }
+        if (valid) {
             val = vin ? vin[i] : (uint32_t)(i - seg_lo);
             d = digit_of(key, shift, mask);
         }
@@ -222,8 +236,10 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const K* __restrict__ 
 // Stable scatter for at most 256 bins, four keys per thread per round: key s of thread t
 // is item r0 + 256 s + t, so the (sub-round, warp, lane) order of a round of 1024 keys is
 // the input order.  Ranks inside a warp come from ballots; a per-digit exclusive prefix
-// over the 32 (sub-round, warp) slots, in that order, places each warp's group.  Four
-// block barriers per 1024 keys, against three per 256 in k_scatter.
+// over the 32 (sub-round, warp) slots, in that order, places each warp's group.  The
+// round's keys are first gathered in shared memory in (digit, input) order and then
+// written out by consecutive threads, so that each digit's run of the round goes to
+// consecutive addresses instead of one scattered store per key.
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads) k_scatter4(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                            K* __restrict__ kout, uint32_t* __restrict__ vout,
@@ -233,7 +249,11 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter4(const K* __restrict__
     constexpr int R = 4;
     __shared__ uint32_t base[256];
     __shared__ uint32_t tot[256];
+    __shared__ uint32_t lstart[256];  // the digit's first place in the round's reordered keys
     __shared__ uint16_t cnt[R][kSortWarps][256];
+    __shared__ K skey[R * kSortThreads];
+    __shared__ uint32_t sval[R * kSortThreads];
+    __shared__ uint32_t sh[kSortWarps];
     long long lo, hi, seg_lo;
     int seg;
     if (!block_items(S, blockIdx.x, lo, hi, seg_lo, seg)) return;
@@ -254,12 +274,15 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter4(const K* __restrict__
 #pragma unroll
         for (int s = 0; s < R; ++s) {
             const long long i = r0 + (long long)s * kSortThreads + threadIdx.x;
-            const bool valid = i < hi;
+            bool valid = i < hi;
             key[s] = 0;
             val[s] = 0;
             dg[s] = 0xffffffffu;
             if (valid) {
                 key[s] = kin[i];
+                valid = !(S.drop && key[s] == (K)kAbsentKey);
+            }
+            if (valid) {
                 val[s] = vin ? vin[i] : (uint32_t)(i - seg_lo);
                 dg[s] = digit_of(key[s], shift, mask);
             }
@@ -273,9 +296,11 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter4(const K* __restrict__
             if (valid && rank[s] == 0) cnt[s][warp][dg[s]] = (uint16_t)__popc(peers);
         }
         __syncthreads();
-        // per digit, the exclusive prefix over the slots in (sub-round, warp) order
-        for (int d = threadIdx.x; d < nbins; d += kSortThreads) {
-            uint32_t run = 0;
+        // per digit (one per thread), the exclusive prefix over the slots in (sub-round,
+        // warp) order, the round's count, and the digit's start in the reordered round
+        const int d = threadIdx.x;
+        uint32_t run = 0;
+        if (d < nbins) {
 #pragma unroll
             for (int s = 0; s < R; ++s)
 #pragma unroll
@@ -286,17 +311,28 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter4(const K* __restrict__
                 }
             tot[d] = run;
         }
+        uint32_t n_round;
+        const uint32_t ls = block_excl_scan<uint32_t>(run, &n_round, sh);
+        if (d < nbins) lstart[d] = ls;
         __syncthreads();
 #pragma unroll
         for (int s = 0; s < R; ++s) {
             if (dg[s] != 0xffffffffu) {
-                const uint32_t off = base[dg[s]] + cnt[s][warp][dg[s]] + (uint32_t)rank[s];
-                kout[seg_lo + off] = key[s];
-                vout[seg_lo + off] = val[s];
+                const uint32_t lp = lstart[dg[s]] + cnt[s][warp][dg[s]] + (uint32_t)rank[s];
+                skey[lp] = key[s];
+                sval[lp] = val[s];
             }
         }
         __syncthreads();
-        for (int d = threadIdx.x; d < nbins; d += kSortThreads) {
+        for (uint32_t j = threadIdx.x; j < n_round; j += kSortThreads) {
+            const K k = skey[j];
+            const uint32_t dj = digit_of(k, shift, mask);
+            const uint32_t off = base[dj] + (j - lstart[dj]);
+            kout[seg_lo + off] = k;
+            vout[seg_lo + off] = sval[j];
+        }
+        __syncthreads();
+        if (d < nbins) {
             base[d] += tot[d];
 #pragma unroll
             for (int s = 0; s < R; ++s)
@@ -336,12 +372,14 @@ __device__ __forceinline__ int select_bit(uint32_t x, uint32_t k) {
 }
 
 // Per (receiver, emission chunk of kEChunk depth-sorted Gaussians): number of pairs.
+// A receiver's sorted Gaussians are the nvis[r] that cover some tile.
 __global__ void __launch_bounds__(kSortThreads) k_count_chunks(const uint32_t* __restrict__ dval,
                                                                const Cover* __restrict__ cover, long long n,
-                                                               int dchunks, uint32_t* __restrict__ chunk_sum) {
+                                                               const uint32_t* __restrict__ nvis, int dchunks,
+                                                               uint32_t* __restrict__ chunk_sum) {
     __shared__ uint32_t sh[kSortWarps];
     const int r = blockIdx.y, c = blockIdx.x;
-    const long long lo = (long long)c * kEChunk, hi = min(lo + (long long)kEChunk, n);
+    const long long lo = (long long)c * kEChunk, hi = min(lo + (long long)kEChunk, (long long)nvis[r]);
     uint32_t s = 0;
     for (long long i = lo + threadIdx.x; i < hi; i += kSortThreads)
         s += cover[(size_t)r * n + dval[(size_t)r * n + i]].count;
@@ -400,7 +438,8 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_pairs(uint32_t* __restric
 // Gaussian's cover (elevation rows of the set azimuth tiles, in order).
 __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restrict__ dval,
                                                        const uint32_t* __restrict__ dkey_sorted,
-                                                       const Cover* __restrict__ cover, long long n, int dchunks,
+                                                       const Cover* __restrict__ cover, long long n,
+                                                       const uint32_t* __restrict__ nvis, int dchunks,
                                                        const uint32_t* __restrict__ chunk_off,
                                                        const long long* __restrict__ rx_base,
                                                        const uint32_t* __restrict__ rx_total, int ntu,
@@ -410,8 +449,9 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
     __shared__ uint32_t offs[kEChunk];
     __shared__ uint32_t sh[kSortWarps];
     const int r = blockIdx.y, c = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long lo = (long long)c * kEChunk, hi = min(lo + (long long)kEChunk, n);
+    const int lane = threadIdx.x & 31;
+    const long long lo = (long long)c * kEChunk, hi = min(lo + (long long)kEChunk, (long long)nvis[r]);
+    if (lo >= hi) return;
     const int m = (int)(hi - lo);
     constexpr int per = kEChunk / kSortThreads;
     // exclusive scan of the pair counts over the chunk, in item order (blocked per thread)
@@ -494,7 +534,7 @@ cudaError_t launch_sort_small_keys(const uint32_t* keys, uint32_t* keys_out, uin
                                    int nbins, uint32_t* hist, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     const int chunks = (int)((n + kChunk - 1) / kChunk);
-    Segs sg{1, n, chunks, nullptr, nullptr};
+    Segs sg{1, n, chunks, kChunk, nullptr, nullptr, nullptr, 0};
     k_hist<uint32_t><<<chunks, kSortThreads, 0, st>>>(keys, sg, 0, (uint32_t)(nbins - 1), nbins, hist, nullptr);
     k_scan<<<1, kSortThreads, 0, st>>>(sg, nbins, hist, nullptr, nullptr);
     launch_scatter<uint32_t>(chunks, keys, nullptr, keys_out, vals_out, sg, 0, (uint32_t)(nbins - 1), nbins, hist,
@@ -510,7 +550,7 @@ cudaError_t launch_sort_small_keys_segmented(const uint32_t* keys, uint32_t* key
                                              const long long* seg_base, const uint32_t* chunk_base, long long chunks,
                                              int nbins, uint32_t* hist, cudaStream_t st) {
     if (chunks == 0) return cudaSuccess;
-    Segs sg{n_seg, -1, 0, seg_base, chunk_base};
+    Segs sg{n_seg, -1, 0, kChunk, seg_base, chunk_base, nullptr, 0};
     k_hist<uint32_t><<<(unsigned)chunks, kSortThreads, 0, st>>>(keys, sg, 0, (uint32_t)(nbins - 1), nbins, hist,
                                                                 nullptr);
     k_scan<<<n_seg, kSortThreads, 0, st>>>(sg, nbins, hist, nullptr, nullptr);
@@ -527,8 +567,12 @@ cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream
     if (e != cudaSuccess) return e;
     if (L.n == 0) return cudaGetLastError();
 
-    // (1) depth sort, per receiver: keys dkey -> dkey2 -> dkey ..., values likewise
-    Segs ds{L.n_rx, L.n, L.dchunks, nullptr, nullptr};
+    // (1) depth sort, per receiver: keys dkey -> dkey2 -> dkey ..., values likewise.  The
+    // first pass drops the Gaussians that cover no tile (key kAbsentKey) and records how
+    // many are left per receiver; the other passes sort only those.
+    uint32_t* nvis = at<uint32_t>(ws, L.dvis);
+    const Segs ds_all{L.n_rx, L.n, L.dchunks, kDChunk, nullptr, nullptr, nullptr, 1};
+    const Segs ds_vis{L.n_rx, L.n, L.dchunks, kDChunk, nullptr, nullptr, nvis, 0};
     const unsigned dblocks = (unsigned)(L.n_rx * L.dchunks);
     uint32_t* k_in = at<uint32_t>(ws, L.dkey);
     uint32_t* k_out = at<uint32_t>(ws, L.dkey2);
@@ -538,8 +582,9 @@ cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream
     uint32_t* H = at<uint32_t>(ws, L.dhist);
     for (int pass = 0; pass < 4; ++pass) {
         const int shift = 8 * pass;
+        const Segs& ds = pass == 0 ? ds_all : ds_vis;
         k_hist<uint32_t><<<dblocks, kSortThreads, 0, st>>>(k_in, ds, shift, 0xffu, 256, H, nullptr);
-        k_scan<<<L.n_rx, kSortThreads, 0, st>>>(ds, 256, H, nullptr, nullptr);
+        k_scan<<<L.n_rx, kSortThreads, 0, st>>>(ds, 256, H, nullptr, nullptr, pass == 0 ? nvis : nullptr);
         launch_scatter<uint32_t>(dblocks, k_in, v_in, k_out, v_out, ds, shift, 0xffu, 256, H, nullptr, st);
         uint32_t* t = k_in; k_in = k_out; k_out = t;
         v_in = v_out;
@@ -552,15 +597,15 @@ cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream
     // (2) emission in depth order
     uint32_t* chunk_sum = at<uint32_t>(ws, L.dchunk_sum);
     k_count_chunks<<<dim3(L.echunks, L.n_rx), kSortThreads, 0, st>>>(dval_sorted, at<Cover>(ws, L.cover), L.n,
-                                                                       L.echunks, chunk_sum);
+                                                                       nvis, L.echunks, chunk_sum);
     k_scan_pairs<<<1, kSortThreads, 0, st>>>(chunk_sum, L.n_rx, L.echunks, L.cap, at<long long>(ws, L.rx_base),
                                              at<uint32_t>(ws, L.rx_total), at<uint32_t>(ws, L.pchunk_base), status);
     k_emit<<<dim3(L.echunks, L.n_rx), kSortThreads, 0, st>>>(
-        dval_sorted, dkey_sorted, at<Cover>(ws, L.cover), L.n, L.echunks, chunk_sum, at<long long>(ws, L.rx_base),
+        dval_sorted, dkey_sorted, at<Cover>(ws, L.cover), L.n, nvis, L.echunks, chunk_sum, at<long long>(ws, L.rx_base),
         at<uint32_t>(ws, L.rx_total), L.ntu, at<unsigned long long>(ws, L.pkeys2), at<uint32_t>(ws, L.pids2), status);
 
     // (3) stable counting sort of each receiver's pairs by tile: pkeys2 -> pkeys
-    Segs ps{L.n_rx, -1, 0, at<long long>(ws, L.rx_base), at<uint32_t>(ws, L.pchunk_base)};
+    Segs ps{L.n_rx, -1, 0, kChunk, at<long long>(ws, L.rx_base), at<uint32_t>(ws, L.pchunk_base), nullptr, 0};
     const unsigned pblocks = (unsigned)L.pchunks_max;
     uint32_t* TH = at<uint32_t>(ws, L.thist);
     k_hist<unsigned long long><<<pblocks, kSortThreads, 0, st>>>(at<unsigned long long>(ws, L.pkeys2), ps, 32,

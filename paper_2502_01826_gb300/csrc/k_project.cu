@@ -338,11 +338,12 @@ __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __r
     // depth key and coverage: deterministic FP32 on c = mu - r
     const float cx = dsub(mx, rx), cy = dsub(my, ry), cz = dsub(mz, rz);
     const float D = dsqrt(dadd(dadd(dmul(cx, cx), dmul(cy, cy)), dmul(cz, cz)));
-    dkey[o] = __float_as_uint(D);
     const float lsm = fmaxf(fmaxf(g.log_scales[3 * k], g.log_scales[3 * k + 1]), g.log_scales[3 * k + 2]);
     float D_c, Rs;
     bool wide;
-    cover[o] = cover_of(cx, cy, cz, lsm, gr, ntu, ntv, D_c, Rs, wide);
+    const Cover cv = cover_of(cx, cy, cz, lsm, gr, ntu, ntv, D_c, Rs, wide);
+    cover[o] = cv;
+    dkey[o] = cv.count ? __float_as_uint(D) : kAbsentKey;  // no tile: left out of the depth sort
     if (variant & GSRF_VARIANT_PAPER_CULLING)
         circle[o] = circle_of(cx, cy, cz, g.log_scales + 3 * k, g.quats + 4 * k, gr);
     // direction pre-test of the render: D cos(theta) of the cover's cone less a rounding
