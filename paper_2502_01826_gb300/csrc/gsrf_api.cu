@@ -47,6 +47,8 @@ bool make_layout(const gsrf_plan* p, Layout* L) {
     L->dhist = take(nr * (size_t)L->dchunks * 256 * 4);
     L->dvis = take(nr * 4);
     L->dchunk_sum = take(nr * (size_t)L->echunks * 4);
+    L->egroup = take(nr * (size_t)L->echunks * (kEChunk / 32) * 4);
+    L->ecounter = take(8);
     L->rx_base = take((nr + 1) * 8);
     L->rx_total = take(nr * 4);
     L->pchunk_base = take((nr + 1) * 4);

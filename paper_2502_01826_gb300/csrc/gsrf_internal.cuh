@@ -110,7 +110,7 @@ struct __align__(16) RayState {
 
 struct Layout {
     // byte offsets
-    size_t status, rxpos, txpos, gacc, raytab, fle, gshape, dpath, view, cover, dkey, dkey2, dval, dval2, dhist, dvis, dchunk_sum,
+    size_t status, rxpos, txpos, gacc, raytab, fle, gshape, dpath, view, cover, dkey, dkey2, dval, dval2, dhist, dvis, dchunk_sum, egroup, ecounter,
         rx_base, rx_total, pchunk_base, pkeys, pkeys2, pids, pids2, tile_start, thist, qkeys, qkeys2, qorder, qhist,
         qcounter, circle, tbuf, total;
     int32_t ntu, ntv, n_tiles;

@@ -371,21 +371,40 @@ __device__ __forceinline__ int select_bit(uint32_t x, uint32_t k) {
     return pos;
 }
 
-// Per (receiver, emission chunk of kEChunk depth-sorted Gaussians): number of pairs.
-// A receiver's sorted Gaussians are the nvis[r] that cover some tile.
+// Per (receiver, emission chunk of kEChunk depth-sorted Gaussians): number of pairs,
+// and for each group of 32 consecutive Gaussians of the chunk (the emission's work item)
+// its first pair relative to the chunk's.  A receiver's sorted Gaussians are the
+// nvis[r] that cover some tile.
 __global__ void __launch_bounds__(kSortThreads) k_count_chunks(const uint32_t* __restrict__ dval,
                                                                const Cover* __restrict__ cover, long long n,
                                                                const uint32_t* __restrict__ nvis, int dchunks,
-                                                               uint32_t* __restrict__ chunk_sum) {
-    __shared__ uint32_t sh[kSortWarps];
+                                                               uint32_t* __restrict__ chunk_sum,
+                                                               uint32_t* __restrict__ group_off) {
+    constexpr int G = kEChunk / 32;  // groups per chunk
+    __shared__ uint32_t gs[G];
     const int r = blockIdx.y, c = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long lo = (long long)c * kEChunk, hi = min(lo + (long long)kEChunk, (long long)nvis[r]);
-    uint32_t s = 0;
-    for (long long i = lo + threadIdx.x; i < hi; i += kSortThreads)
-        s += cover[(size_t)r * n + dval[(size_t)r * n + i]].count;
-    uint32_t tot;
-    block_excl_scan<uint32_t>(s, &tot, sh);
-    if (threadIdx.x == 0) chunk_sum[(size_t)r * dchunks + c] = tot;
+    // group g = items 32 g .. 32 g + 31 of the chunk: round g / kSortWarps, warp g % kSortWarps
+    for (int k = 0; k < kEChunk / kSortThreads; ++k) {
+        const long long i = lo + (long long)k * kSortThreads + threadIdx.x;
+        uint32_t v = i < hi ? cover[(size_t)r * n + dval[(size_t)r * n + i]].count : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) gs[k * kSortWarps + warp] = v;
+    }
+    __syncthreads();
+    if (warp == 0) {  // exclusive scan over the chunk's groups (G = 32: one per lane)
+        const uint32_t v = gs[lane];
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        group_off[((size_t)r * dchunks + c) * G + lane] = x - v;
+        if (lane == 31) chunk_sum[(size_t)r * dchunks + c] = x;
+    }
 }
 
 // One block: chunk offsets per receiver, receiver bases, capacity check, and the
@@ -393,7 +412,9 @@ __global__ void __launch_bounds__(kSortThreads) k_count_chunks(const uint32_t* _
 __global__ void __launch_bounds__(kSortThreads) k_scan_pairs(uint32_t* __restrict__ chunk_sum, int n_rx, int dchunks,
                                                              long long cap, long long* __restrict__ rx_base,
                                                              uint32_t* __restrict__ rx_total,
-                                                             uint32_t* __restrict__ pchunk_base, DevStatus* st) {
+                                                             uint32_t* __restrict__ pchunk_base, DevStatus* st,
+                                                             unsigned long long* __restrict__ emit_counter) {
+    if (threadIdx.x == 0) *emit_counter = 0ull;
     for (int r = threadIdx.x; r < n_rx; r += kSortThreads) {
         uint32_t run = 0;
         uint32_t* cs = chunk_sum + (size_t)r * dchunks;
@@ -430,74 +451,60 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_pairs(uint32_t* __restric
     }
 }
 
-// Expand each chunk of depth-sorted Gaussians into its (tile, Gaussian) pairs, written
-// contiguously in depth order.  Thread t takes Gaussians t, t + 256, ... of the chunk, so
-// a warp holds 32 consecutive Gaussians whose pairs form one contiguous run; the warp
-// writes that run 32 slots at a time (coalesced), each slot finding its Gaussian by a
-// search over the warp's inclusive counts and its tile from its index inside that
-// Gaussian's cover (elevation rows of the set azimuth tiles, in order).
+// Expand the depth-sorted Gaussians into their (tile, Gaussian) pairs, written
+// contiguously in depth order.  A work item is one group of 32 consecutive Gaussians of a
+// receiver, whose pairs form one contiguous run; warps take items from one counter in
+// group-major order (group 0 of every receiver, then group 1, ...), so the nearest
+// Gaussians, whose covers are the widest and whose runs the longest, come first and
+// spread over all warps.  The warp writes its run 32 slots at a time (coalesced), each
+// slot finding its Gaussian by a search over the warp's inclusive counts and its tile
+// from its index inside that Gaussian's cover (elevation rows of the set azimuth tiles,
+// in order).
 __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restrict__ dval,
                                                        const uint32_t* __restrict__ dkey_sorted,
                                                        const Cover* __restrict__ cover, long long n,
                                                        const uint32_t* __restrict__ nvis, int dchunks,
                                                        const uint32_t* __restrict__ chunk_off,
-                                                       const long long* __restrict__ rx_base,
-                                                       const uint32_t* __restrict__ rx_total, int ntu,
+                                                       const uint32_t* __restrict__ group_off,
+                                                       const long long* __restrict__ rx_base, int n_rx, int ntu,
+                                                       unsigned long long* __restrict__ counter,
                                                        unsigned long long* __restrict__ pkeys,
                                                        uint32_t* __restrict__ pids, const DevStatus* st) {
     if (capacity_failed(st)) return;
-    __shared__ uint32_t offs[kEChunk];
-    __shared__ uint32_t sh[kSortWarps];
-    const int r = blockIdx.y, c = blockIdx.x;
+    constexpr int G = kEChunk / 32;
     const int lane = threadIdx.x & 31;
-    const long long lo = (long long)c * kEChunk, hi = min(lo + (long long)kEChunk, (long long)nvis[r]);
-    if (lo >= hi) return;
-    const int m = (int)(hi - lo);
-    constexpr int per = kEChunk / kSortThreads;
-    // exclusive scan of the pair counts over the chunk, in item order (blocked per thread)
-    uint32_t v[per];
-    uint32_t s = 0;
-#pragma unroll
-    for (int j = 0; j < per; ++j) {
-        const int idx = threadIdx.x * per + j;
-        v[j] = idx < m ? cover[(size_t)r * n + dval[(size_t)r * n + lo + idx]].count : 0u;
-        s += v[j];
-    }
-    uint32_t tot;
-    uint32_t ex = block_excl_scan<uint32_t>(s, &tot, sh);
-#pragma unroll
-    for (int j = 0; j < per; ++j) {
-        offs[threadIdx.x * per + j] = ex;
-        ex += v[j];
-    }
-    __syncthreads();
-    unsigned long long* kout = pkeys + rx_base[r] + chunk_off[(size_t)r * dchunks + c];
-    uint32_t* iout = pids + rx_base[r] + chunk_off[(size_t)r * dchunks + c];
-    for (int i0 = 0; i0 < m; i0 += kSortThreads) {
-        const int i = i0 + threadIdx.x;
-        uint32_t gid = 0, dk = 0, cnt = 0, tvw = 0, mlo = 0, mhi = 0, o = 0;
-        if (i < m) {
-            const size_t gi = (size_t)r * n + lo + i;
-            gid = dval[gi];
-            dk = dkey_sorted[gi];
+    const unsigned long long items = (unsigned long long)n_rx * dchunks * G;
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(counter, 1ull);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= items) break;
+        const int r = (int)(it % (unsigned long long)n_rx);
+        const long long g = (long long)(it / (unsigned long long)n_rx);  // group inside the receiver
+        const long long nv = nvis[r];
+        if (g * 32 >= nv) continue;  // uniform over the warp
+        const long long i = g * 32 + lane;
+        uint32_t gid = 0, dk = 0, cnt = 0, tvw = 0, mlo = 0, mhi = 0;
+        if (i < nv) {
+            gid = dval[(size_t)r * n + i];
+            dk = dkey_sorted[(size_t)r * n + i];
             const Cover cv = cover[(size_t)r * n + gid];
             cnt = cv.count;
             tvw = cv.tv;
             mlo = (uint32_t)cv.mask;
             mhi = (uint32_t)(cv.mask >> 32);
-            o = offs[i];
         }
-        // the warp's 32 consecutive items own one run of pairs from lane 0's offset; the
-        // warp writes it 32 slots at a time, each slot finding its item by a search over
-        // the inclusive counts and its (row, column) inside the item's cover
         uint32_t incl = cnt;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
             if (lane >= d) incl += t;
         }
-        const uint32_t wbase = __shfl_sync(0xffffffffu, o, 0);
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const long long c = g / G;
+        const uint32_t wbase = chunk_off[(size_t)r * dchunks + c] + group_off[(size_t)r * dchunks * G + g];
+        unsigned long long* kout = pkeys + rx_base[r] + wbase;
+        uint32_t* iout = pids + rx_base[r] + wbase;
         for (uint32_t s0 = 0; s0 < total; s0 += 32) {
             const uint32_t q = s0 + lane;
             int j = 0;  // lanes whose inclusive count is <= q: the owner of slot q
@@ -516,12 +523,11 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
                 const uint32_t row = p / nb, col = p - row * nb;
                 const int tu = col < nlo ? select_bit(olo, col) : 32 + select_bit(ohi, col - nlo);
                 const int tv = (int)(otv & 0xffffu) + (int)row;
-                kout[wbase + q] = ((unsigned long long)(uint32_t)(tv * ntu + tu) << 32) | odk;
-                iout[wbase + q] = ogid;
+                kout[q] = ((unsigned long long)(uint32_t)(tv * ntu + tu) << 32) | odk;
+                iout[q] = ogid;
             }
         }
     }
-    (void)rx_total;
 }
 
 __global__ void k_zero_tile_start(uint32_t* ts, size_t n) {
@@ -596,13 +602,25 @@ cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream
 
     // (2) emission in depth order
     uint32_t* chunk_sum = at<uint32_t>(ws, L.dchunk_sum);
+    uint32_t* group_off = at<uint32_t>(ws, L.egroup);
+    unsigned long long* ecounter = at<unsigned long long>(ws, L.ecounter);
     k_count_chunks<<<dim3(L.echunks, L.n_rx), kSortThreads, 0, st>>>(dval_sorted, at<Cover>(ws, L.cover), L.n,
-                                                                       nvis, L.echunks, chunk_sum);
+                                                                       nvis, L.echunks, chunk_sum, group_off);
     k_scan_pairs<<<1, kSortThreads, 0, st>>>(chunk_sum, L.n_rx, L.echunks, L.cap, at<long long>(ws, L.rx_base),
-                                             at<uint32_t>(ws, L.rx_total), at<uint32_t>(ws, L.pchunk_base), status);
-    k_emit<<<dim3(L.echunks, L.n_rx), kSortThreads, 0, st>>>(
-        dval_sorted, dkey_sorted, at<Cover>(ws, L.cover), L.n, nvis, L.echunks, chunk_sum, at<long long>(ws, L.rx_base),
-        at<uint32_t>(ws, L.rx_total), L.ntu, at<unsigned long long>(ws, L.pkeys2), at<uint32_t>(ws, L.pids2), status);
+                                             at<uint32_t>(ws, L.rx_total), at<uint32_t>(ws, L.pchunk_base), status,
+                                             ecounter);
+    // one resident wave of warps taking the groups from the counter
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_emit, kSortThreads, 0)) != cudaSuccess) return e;
+    const long long groups = (long long)L.n_rx * L.echunks * (kEChunk / 32);
+    const unsigned emit_grid =
+        (unsigned)max(1ll, min((long long)sms * max(per_sm, 1), (groups + kSortWarps - 1) / kSortWarps));
+    k_emit<<<emit_grid, kSortThreads, 0, st>>>(dval_sorted, dkey_sorted, at<Cover>(ws, L.cover), L.n, nvis, L.echunks,
+                                               chunk_sum, group_off, at<long long>(ws, L.rx_base), L.n_rx, L.ntu,
+                                               ecounter, at<unsigned long long>(ws, L.pkeys2), at<uint32_t>(ws, L.pids2),
+                                               status);
 
     // (3) stable counting sort of each receiver's pairs by tile: pkeys2 -> pkeys
     Segs ps{L.n_rx, -1, 0, kChunk, at<long long>(ws, L.rx_base), at<uint32_t>(ws, L.pchunk_base), nullptr, 0};
