@@ -1,6 +1,9 @@
 // k_signal.cu -- received signal from the per-ray signals (Sec. 4.4, loss paragraph):
 // the single-antenna complex sum over rays, its power in dB, the incoherent power sum,
-// and the spatial-spectrum magnitude.  FP64 accumulation in a fixed order.
+// and the spatial-spectrum magnitude.  Accumulation in a fixed order: each thread sums its
+// rays in compensated FP32 (Knuth's two-sum, an error-free transformation of each
+// addition, so the pair (sum, error) carries the exact running sum up to the error
+// term's own rounding), then the threads' partials are added in FP64.
 #include <cooperative_groups.h>
 #include <math.h>
 
@@ -14,11 +17,21 @@ constexpr int kSigThreads = 256;
 
 constexpr int kSigCluster = 8;  // CTAs per (receiver, frequency) sum
 
+// s + c += x: Knuth's two-sum of s and x (the rounded sum t and its exact error), the
+// error added to the compensation c.
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+    const float t = s + x;
+    const float z = t - s;
+    c += (s - (t - z)) + (x - z);
+    s = t;
+}
+
 // One thread-block cluster of kSigCluster CTAs per (receiver, frequency): CTA c, thread t
-// sums rays c * 256 + t + k * 256 * kSigCluster (k = 0, 1, ...) in FP64, a fixed tree in
-// shared memory gives each CTA's partial, and CTA 0 adds the partials of CTAs
-// 0 .. kSigCluster - 1, in that order, through distributed shared memory.  The order
-// never depends on timing, and all SMs share the work.
+// sums rays c * 256 + t + k * 256 * kSigCluster (k = 0, 1, ...) in compensated FP32 (the
+// power sum, of positive terms, in plain FP32) and converts its partial to FP64 once; a
+// fixed FP64 tree in shared memory gives each CTA's partial, and CTA 0 adds the partials
+// of CTAs 0 .. kSigCluster - 1, in that order, through distributed shared memory.  The
+// order never depends on timing, and all SMs share the work.
 __global__ void __cluster_dims__(kSigCluster, 1, 1) __launch_bounds__(kSigThreads)
     k_signal_sum(const float2* __restrict__ rays, int n_rays, int mode, float* __restrict__ out) {
     __shared__ double sr[kSigThreads], si[kSigThreads], sp[kSigThreads];
@@ -26,16 +39,17 @@ __global__ void __cluster_dims__(kSigCluster, 1, 1) __launch_bounds__(kSigThread
     const int c = (int)cl.block_rank();
     const int rf = blockIdx.x / kSigCluster;
     const float2* S = rays + (size_t)rf * n_rays;
-    double ar = 0.0, ai = 0.0, ap = 0.0;
+    float fr = 0.0f, cr = 0.0f, fi = 0.0f, ci = 0.0f, fp = 0.0f;
+    const bool power = mode == GSRF_SIG_POWER_SUM;
     for (int i = c * kSigThreads + threadIdx.x; i < n_rays; i += kSigThreads * kSigCluster) {
         const float2 s = S[i];
-        ar += (double)s.x;
-        ai += (double)s.y;
-        ap += (double)s.x * s.x + (double)s.y * s.y;
+        two_sum_acc(fr, cr, s.x);
+        two_sum_acc(fi, ci, s.y);
+        if (power) fp += s.x * s.x + s.y * s.y;
     }
-    sr[threadIdx.x] = ar;
-    si[threadIdx.x] = ai;
-    sp[threadIdx.x] = ap;
+    sr[threadIdx.x] = (double)fr + (double)cr;
+    si[threadIdx.x] = (double)fi + (double)ci;
+    sp[threadIdx.x] = (double)fp;
     __syncthreads();
     for (int w = kSigThreads / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w) {
