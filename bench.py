@@ -67,8 +67,8 @@ FLOP_HIT = 172
 # ncu DRAM bytes (read + write) of one full-size k_render_queue launch on the 64-receiver
 # workload, per work split (tile_w, tile_h, ray_block_w, stage); null in the output for a
 # split not measured (profiles/)
-RENDER_TRAFFIC = {(16, 16, 8, 32): 83646208 + 7084288, (32, 16, 8, 32): 78890752 + 6373120,
-                  (32, 32, 8, 32): 83668224 + 6735360}
+RENDER_TRAFFIC = {(16, 16, 8, 32): 85583104 + 7175424, (32, 16, 8, 32): 79896320 + 6626304,
+                  (32, 32, 8, 32): 84491008 + 6703104}
 # library kernels per step: project 4 (status, ray table, shape records, view records),
 # bin 19 (zero, 4 x (hist, scan, scatter), count, scan, emit, tile hist, scan, scatter),
 # render 5 (item keys, counting pass of 3, persistent render), received signal 1

@@ -232,7 +232,7 @@ __device__ __forceinline__ void render_block(const RenderArgs& a, int r, int til
             cp_async16(dst + 3, sh + 1);
             cp_async16(dst + 4, sh + 2);
             const int slot = __popc(kmask & ((1u << lane) - 1u));
-            if (L == 3 && slot < kCoefSlots) {
+            if (L == 3 && !ORDER && slot < kCoefSlots) {  // the t_mid pass composites later, from global memory
                 const float4* qf = reinterpret_cast<const float4*>(a.fle + (size_t)id * kFle);
                 float4* qd = scoef[bf][slot];
 #pragma unroll
