@@ -28,8 +28,8 @@
  * with every azimuth when rho <= Rs (the cone holds the vertical), every tile when
  * the cone is a hemisphere or wider, and no tile when D + Rc < r_rx (the sphere lies
  * inside the ray-emitting sphere).  exp, atan2 and asin are evaluated by the short
- * formulas below (textbook series after exact argument reduction), not by libm,
- * so that both sides round identically.
+ * formulas below (textbook series after exact argument reduction, and a fitted
+ * polynomial for asin), not by libm, so that both sides round identically.
  */
 #include <math.h>
 #include <stdint.h>
@@ -85,12 +85,33 @@ static float det_atan2(float y, float x)
     return a;
 }
 
+/* asin(x), x in [0, 1/2]: x + x z P(z) with z = x^2 and P of degree 4, a least-squares
+ * fit of (asin(x) - x) / (x z) on z in [0, 1/4] (FP32 coefficients; the FP32 evaluation
+ * stays within 6.6e-8 relative of asin).  For |s| > 1/2 the half-angle identity
+ * asin(a) = pi/2 - 2 asin(sqrt((1 - a) / 2)) maps the argument below 1/2. */
+static float det_asin_poly(float z)
+{
+    float p = 0.0421473645f;
+    p = p * z + 0.0241886489f;
+    p = p * z + 0.0454691872f;
+    p = p * z + 0.0749529824f;
+    return p * z + 0.166667536f;
+}
+
 static float det_asin(float s)
 {
     if (s > 1.0f) s = 1.0f;
     if (s < -1.0f) s = -1.0f;
-    float c = sqrtf((1.0f - s) * (1.0f + s));
-    return det_atan2(s, c);
+    float a = fabsf(s), r;
+    if (a <= 0.5f) {
+        float z = a * a;
+        r = a + (a * z) * det_asin_poly(z);
+    } else {
+        float z = (1.0f - a) * 0.5f;
+        float w = sqrtf(z);
+        r = 1.57079633f - 2.0f * (w + (w * z) * det_asin_poly(z));
+    }
+    return s < 0.0f ? -r : r;
 }
 
 /* exported for the pins: the same three functions, callable one value at a time */
