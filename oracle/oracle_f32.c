@@ -28,8 +28,9 @@
  * with every azimuth when rho <= Rs (the cone holds the vertical), every tile when
  * the cone is a hemisphere or wider, and no tile when D + Rc < r_rx (the sphere lies
  * inside the ray-emitting sphere).  exp, atan2 and asin are evaluated by the short
- * formulas below (textbook series after exact argument reduction, and a fitted
- * polynomial for asin), not by libm, so that both sides round identically.
+ * formulas below (a textbook series for exp after exact argument reduction; fitted
+ * polynomials for atan and asin after exact identities), not by libm, so that both
+ * sides round identically.
  */
 #include <math.h>
 #include <stdint.h>
@@ -58,20 +59,25 @@ static float det_exp(float x)
     return ldexpf(p, (int)n);
 }
 
-/* atan(t), t in [0, 1]: two half-angle reductions t <- t / (1 + sqrt(1 + t^2))
- * bring t below tan(pi/16); then the Maclaurin series to t^11. */
+/* atan(t), t in [0, 1]: above tan(pi/8) the identity atan(t) = pi/4 + atan((t - 1) /
+ * (t + 1)) maps the argument into [-tan(pi/8), 0]; there atan(u) = u + u z Q(z), z = u^2,
+ * Q of degree 4, a least-squares fit of (atan(u) - u) / (u z) on z in [0, tan^2(pi/8)]
+ * (FP32 coefficients; the FP32 evaluation stays within 6.3e-8 relative of atan). */
+static float det_atan_poly(float u)
+{
+    float z = u * u;
+    float q = -0.0607130416f;
+    q = q * z + 0.105907731f;
+    q = q * z + -0.142430648f;
+    q = q * z + 0.199984416f;
+    q = q * z + -0.333333135f;
+    return u + (u * z) * q;
+}
+
 static float det_atan_unit(float t)
 {
-    t = t / (1.0f + sqrtf(1.0f + t * t));
-    t = t / (1.0f + sqrtf(1.0f + t * t));
-    float z = t * t;
-    float p = -9.09090909e-2f;
-    p = p * z + 1.11111111e-1f;
-    p = p * z + -1.42857143e-1f;
-    p = p * z + 2.0e-1f;
-    p = p * z + -3.33333333e-1f;
-    p = p * z + 1.0f;
-    return 4.0f * (t * p);
+    if (t <= 0.414213568f) return det_atan_poly(t);
+    return 0.785398163f + det_atan_poly((t - 1.0f) / (t + 1.0f));
 }
 
 static float det_atan2(float y, float x)

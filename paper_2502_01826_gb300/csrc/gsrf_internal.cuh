@@ -160,19 +160,23 @@ __device__ __forceinline__ float det_exp(float x) {
     return ldexpf(p, (int)n);
 }
 
-// atan on [0, 1]: two half-angle steps t -> t / (1 + sqrt(1 + t^2)) reduce the
-// argument below tan(pi/16); the Maclaurin series to t^11 finishes it; times 4.
+// atan on [0, 1]: above tan(pi/8), atan(t) = pi/4 + atan((t - 1) / (t + 1)) brings the
+// argument into [-tan(pi/8), 0]; there atan(u) = u + u z Q(z), z = u^2, with Q a degree-4
+// least-squares fit of (atan(u) - u) / (u z) on z in [0, tan^2(pi/8)] (coefficients
+// rounded to FP32; the FP32 evaluation is within 6.3e-8 relative of atan).
+__device__ __forceinline__ float det_atan_poly(float u) {
+    const float z = dmul(u, u);
+    float q = -0.0607130416f;
+    q = dadd(dmul(q, z), 0.105907731f);
+    q = dadd(dmul(q, z), -0.142430648f);
+    q = dadd(dmul(q, z), 0.199984416f);
+    q = dadd(dmul(q, z), -0.333333135f);
+    return dadd(u, dmul(dmul(u, z), q));
+}
+
 __device__ __forceinline__ float det_atan_unit(float t) {
-    t = ddiv(t, dadd(1.0f, dsqrt(dadd(1.0f, dmul(t, t)))));
-    t = ddiv(t, dadd(1.0f, dsqrt(dadd(1.0f, dmul(t, t)))));
-    float z = dmul(t, t);
-    float p = -9.09090909e-2f;
-    p = dadd(dmul(p, z), 1.11111111e-1f);
-    p = dadd(dmul(p, z), -1.42857143e-1f);
-    p = dadd(dmul(p, z), 2.0e-1f);
-    p = dadd(dmul(p, z), -3.33333333e-1f);
-    p = dadd(dmul(p, z), 1.0f);
-    return dmul(4.0f, dmul(t, p));
+    if (t <= 0.414213568f) return det_atan_poly(t);
+    return dadd(0.785398163f, det_atan_poly(ddiv(dsub(t, 1.0f), dadd(t, 1.0f))));
 }
 
 __device__ __forceinline__ float det_atan2(float y, float x) {

@@ -236,6 +236,18 @@ def test_det_functions_close_to_libm(oracle_lib):
         assert abs(oracle_lib.det_atan2(y, x) - math.atan2(y, x)) < 3e-6
     for s in np.linspace(-1, 1, 41):
         assert abs(oracle_lib.det_asin(float(s)) - math.asin(float(np.float32(s)))) < 3e-6
+    # dense sweeps across the branch points (tan(pi/8) and 1 for atan, 1/2 for asin),
+    # relative to the value so that small angles are held too
+    for a in np.linspace(-math.pi, math.pi, 2003):
+        y, x = float(np.float32(3.0 * math.sin(a))), float(np.float32(3.0 * math.cos(a)))
+        assert abs(oracle_lib.det_atan2(y, x) - math.atan2(y, x)) < 3e-6
+    for s in np.concatenate([np.linspace(-1, 1, 2001), np.geomspace(1e-6, 1.0, 200)]):
+        sf = float(np.float32(s))
+        ref = math.asin(sf)
+        assert abs(oracle_lib.det_asin(sf) - ref) <= 2e-7 * abs(ref) + 2e-7
+    for t in np.geomspace(1e-6, 1.0, 300):
+        tf = float(np.float32(t))
+        assert abs(oracle_lib.det_atan2(tf, 1.0) - math.atan(tf)) <= 2e-7 * math.atan(tf) + 1e-7
 
 
 def test_depth_key_is_float32_distance(oracle_lib):
