@@ -35,6 +35,9 @@ bool make_layout(const gsrf_plan* p, Layout* L) {
     L->txpos = take(3 * sizeof(float));
     L->gacc = take(n * grad_floats(plan_degree(p)) * sizeof(float));
     L->raytab = take((size_t)g.n_az * g.n_el * raytab_floats(plan_degree(p)) * sizeof(float));
+    // the ray table's per-column and per-row FP64 factors: (cos, sin)(m az) for m = 1..5,
+    // sin el, cos el and P_l^m (m <= l <= 5)
+    L->rayfac = take(((size_t)g.n_az * 2 * kMaxDegree + (size_t)g.n_el * (2 + (kMaxDegree + 1) * (kMaxDegree + 2) / 2)) * sizeof(double));
     L->fle = take(n * fle_floats(plan_degree(p)) * sizeof(float));
     L->gshape = take(n * sizeof(GShape));
     L->dpath = take(n * sizeof(double));
@@ -190,7 +193,7 @@ static gsrf_status check_plan(const gsrf_plan* p) {
         return GSRF_ERR_UNSUPPORTED;  // its kernel instance: one frequency, L = 3
     if ((p->variant & GSRF_VARIANT_PATH_AT_REP) && (p->n_f > 1 || plan_degree(p) != 3))
         return GSRF_ERR_UNSUPPORTED;  // its kernel instance: one frequency, L = 3
-    if (p->fle_degree < 0 || p->fle_degree > 5) return GSRF_ERR_INVALID_ARG;
+    if (p->fle_degree < 0 || p->fle_degree > kMaxDegree) return GSRF_ERR_INVALID_ARG;
     if (plan_degree(p) != 3 && (p->n_f > 1 || (p->variant & GSRF_VARIANT_RADIANCE_AT_MEAN)))
         return GSRF_ERR_UNSUPPORTED;  // other degrees: one frequency, radiance per ray
     const gsrf_status s = check_grid(&p->grid);

@@ -73,6 +73,7 @@ __host__ __device__ constexpr int fle_floats(int L) { return 4 * ((L + 2) / 2) +
 __host__ __device__ constexpr int fle_m0_floats(int L) { return 4 * ((L + 2) / 2); }
 __host__ __device__ constexpr int raytab_floats(int L) { return 4 * ((L * (L + 2) + 6) / 4); }
 static_assert(fle_floats(3) == kFle && raytab_floats(3) == kRayTab, "the L = 3 layouts");
+constexpr int kMaxDegree = 5;  // the largest Fourier-Legendre degree a plan may ask for
 inline int plan_degree(const gsrf_plan* p) { return p->fle_degree > 0 ? p->fle_degree : 3; }
 // Backward accumulators per Gaussian: W 9, mu 3, opacity, b, then the coefficient
 // gradients in chunks of 16 basis values x (dL/d psi_re, dL/d psi_im), rounded to float4.
@@ -110,7 +111,7 @@ struct __align__(16) RayState {
 
 struct Layout {
     // byte offsets
-    size_t status, rxpos, txpos, gacc, raytab, fle, gshape, dpath, view, cover, dkey, dkey2, dval, dval2, dhist, dvis, dchunk_sum, egroup, ecounter,
+    size_t status, rxpos, txpos, gacc, raytab, fle, gshape, dpath, view, cover, rayfac, dkey, dkey2, dval, dval2, dhist, dvis, dchunk_sum, egroup, ecounter,
         rx_base, rx_total, pchunk_base, pkeys, pkeys2, pids, pids2, tile_start, thist, qkeys, qkeys2, qorder, qhist,
         qcounter, circle, tbuf, total;
     int32_t ntu, ntv, n_tiles;

@@ -16,14 +16,16 @@ __global__ void k_status_init(DevStatus* st) {
     }
 }
 
-// One thread per Gaussian: W = diag(1/s) R^T with R the rotation of the normalised
-// quaternion (Sec. 4.2, Sigma = R S S^T R^T, so Sigma^-1 = W^T W), opacity = sigmoid,
-// and |t - mu| in FP64 for the path phase.
-__global__ void __launch_bounds__(256) k_prepare(gsrf_gaussians g, const float* __restrict__ tx,
-                                                 GShape* __restrict__ shape, double* __restrict__ dpath_t,
-                                                 float* __restrict__ fle, DevStatus* st, int variant, int L) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= g.n) return;
+constexpr int kPrepThreads = 64;
+constexpr int kCoefMax = 2 * (kMaxDegree + 1) * (kMaxDegree + 1);  // floats of c at the largest degree
+static_assert(fle_floats(kMaxDegree) <= kCoefMax, "folded coefficients fit the staging rows");
+constexpr int kShapeFloats = (int)(sizeof(GShape) / sizeof(float));
+
+// The per-Gaussian part of k_prepare: c = its coefficients, and its shape record and
+// folded coefficients q written to the block's staging rows.
+__device__ __forceinline__ void prepare_one(const gsrf_gaussians& g, const float* __restrict__ tx, int64_t k,
+                                            const float* c, float* sgo, float* q, double* __restrict__ dpath_t,
+                                            DevStatus* st, int variant, int L) {
     const float mx = g.means[3 * k], my = g.means[3 * k + 1], mz = g.means[3 * k + 2];
     const float l0 = g.log_scales[3 * k], l1 = g.log_scales[3 * k + 1], l2 = g.log_scales[3 * k + 2];
     float qw = g.quats[4 * k], qx = g.quats[4 * k + 1], qy = g.quats[4 * k + 2], qz = g.quats[4 * k + 3];
@@ -33,7 +35,6 @@ __global__ void __launch_bounds__(256) k_prepare(gsrf_gaussians g, const float* 
                   isfinite(l2) && isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) &&
                   !isnan(ol) && isfinite(b);
     const int nb = (L + 1) * (L + 1);  // coefficients of degree L (Sec. 4.2)
-    const float* c = g.coeffs + (size_t)k * 2 * nb;
     for (int i = 0; i < 2 * nb; ++i) finite = finite && isfinite(c[i]);
     if (!finite) {
         atomicCAS(&st->code, (int)GSRF_OK, (int)GSRF_ERR_NONFINITE);
@@ -65,13 +66,13 @@ __global__ void __launch_bounds__(256) k_prepare(gsrf_gaussians g, const float* 
     if (variant & GSRF_VARIANT_NORMALISED_WEIGHT) out.o *= expf(-(l0 + l1 + l2)) * 0.0634936359f;
     out.b = b;
     out.pad = 0.0f;
-    shape[k] = out;
+    const float* of = reinterpret_cast<const float*>(&out);
+    for (int i = 0; i < kShapeFloats; ++i) sgo[i] = of[i];
     const double dx = (double)tx[0] - mx, dy = (double)tx[1] - my, dz = (double)tx[2] - mz;
     dpath_t[k] = sqrt(dx * dx + dy * dy + dz * dz);
     // folded Fourier-Legendre coefficients (see fle_floats): the m = 0 pairs, then per
     // (l, m > 0) in m-major order the four reals that fold c_{l,m} Y_{l,m} + c_{l,-m}
     // Y_{l,-m} with Y_{l,-m} = kappa conj(Y_{l,m}), kappa = (-1)^m (l-m)!/(l+m)!
-    float* q = fle + (size_t)k * fle_floats(L);
     const int m0 = fle_m0_floats(L);
     for (int l = 0; l <= L; ++l) {
         q[2 * l] = c[2 * (l * l + l)];
@@ -95,44 +96,112 @@ __global__ void __launch_bounds__(256) k_prepare(gsrf_gaussians g, const float* 
     }
 }
 
-// Per-ray table of the receiving grid, in FP64 and rounded once: the ray direction
+// One thread per Gaussian: W = diag(1/s) R^T with R the rotation of the normalised
+// quaternion (Sec. 4.2, Sigma = R S S^T R^T, so Sigma^-1 = W^T W), opacity = sigmoid,
+// and |t - mu| in FP64 for the path phase.  A block's coefficients come in, and its
+// folded coefficients and shape records go out, through shared memory (rows padded to an
+// odd stride), so that global memory is read and written in consecutive words rather
+// than one 128-byte record per thread.
+
+__global__ void __launch_bounds__(kPrepThreads) k_prepare(gsrf_gaussians g, const float* __restrict__ tx,
+                                                          GShape* __restrict__ shape, double* __restrict__ dpath_t,
+                                                          float* __restrict__ fle, DevStatus* st, int variant, int L) {
+    __shared__ float sc[kPrepThreads * (kCoefMax + 1)];
+    __shared__ float sq[kPrepThreads * (kCoefMax + 1)];
+    __shared__ float sg[kPrepThreads * (kShapeFloats + 1)];
+    const int64_t k0 = (int64_t)blockIdx.x * kPrepThreads, k = k0 + threadIdx.x;
+    const int mb = (int)min((int64_t)kPrepThreads, g.n - k0);  // Gaussians of this block
+    const int nb = (L + 1) * (L + 1);                          // coefficients of degree L (Sec. 4.2)
+    const int nc = 2 * nb, nq = fle_floats(L);
+    for (int i = threadIdx.x; i < mb * nc; i += kPrepThreads) {
+        const int gi = i / nc;
+        sc[gi * (nc + 1) + (i - gi * nc)] = g.coeffs[k0 * nc + i];
+    }
+    __syncthreads();
+    if (k < g.n) prepare_one(g, tx, k, sc + threadIdx.x * (nc + 1), sg + threadIdx.x * (kShapeFloats + 1),
+                             sq + threadIdx.x * (nq + 1), dpath_t, st, variant, L);
+    __syncthreads();
+    for (int i = threadIdx.x; i < mb * nq; i += kPrepThreads) {
+        const int gi = i / nq;
+        fle[k0 * nq + i] = sq[gi * (nq + 1) + (i - gi * nq)];
+    }
+    float* shape_f = reinterpret_cast<float*>(shape);
+    for (int i = threadIdx.x; i < mb * kShapeFloats; i += kPrepThreads) {
+        const int gi = i / kShapeFloats;
+        shape_f[k0 * kShapeFloats + i] = sg[gi * (kShapeFloats + 1) + (i - gi * kShapeFloats)];
+    }
+}
+
+
+
+// Per-ray table of the receiving grid, in FP64 and rounded once to FP32: the ray direction
 // (cos el cos az, cos el sin az, sin el) at the bin centre and the basis values the
 // folded Fourier-Legendre sum of degree L needs (see raytab_floats): P_l^m without the
 // Condon-Shortley phase at x = sin el, by the recurrences P_m^m = (2m-1)!! (1-x^2)^{m/2},
 // P_{m+1}^m = (2m+1) x P_m^m, (l-m) P_l^m = (2l-1) x P_{l-1}^m - (l+m-1) P_{l-2}^m.
-__global__ void __launch_bounds__(256) k_raytab(gsrf_grid gr, int L, float* __restrict__ tab) {
+// The table is separable: a ray's direction and basis are products of factors of its
+// azimuth bin u (cos, sin of m az, m = 0..L) and of its elevation bin v (sin and cos of el,
+// P_l^m).  k_raytab_factors computes them once per column and once per row (FP64), and
+// k_raytab forms each ray's products in FP64 and rounds them once to FP32.
+constexpr int kRayU = 2 * kMaxDegree;                                 // (cos, sin)(m az), m = 1..L
+constexpr int kRayV = 2 + (kMaxDegree + 1) * (kMaxDegree + 2) / 2;  // sin el, cos el, P_l^m (m <= l)
+
+// One item (a column or a row) per 32-thread block, lane 0 computing: FP64 runs at about
+// 1.7 operations per clock per SM on this part, so the few hundred items are spread over
+// every SM rather than packed into a handful of blocks.
+__global__ void __launch_bounds__(32) k_raytab_factors(gsrf_grid gr, int L, double* __restrict__ fu,
+                                                       double* __restrict__ fv) {
+    if (threadIdx.x != 0) return;
+    const int i = blockIdx.x;
+    const double deg = 0.017453292519943295;
+    if (i < gr.n_az) {
+        const double az = ((double)gr.az0_deg + ((double)i + 0.5) * (double)gr.daz_deg) * deg;
+        double* f = fu + (size_t)i * kRayU;
+        for (int m = 1; m <= L; ++m) sincos((double)m * az, &f[2 * m - 1], &f[2 * m - 2]);
+    } else if (i < gr.n_az + gr.n_el) {
+        const int v = i - gr.n_az;
+        const double el = ((double)gr.el0_deg + ((double)v + 0.5) * (double)gr.del_deg) * deg;
+        double se, ce;
+        sincos(el, &se, &ce);
+        const double x = se, sx = ce;
+        double P[kMaxDegree + 1][kMaxDegree + 1];
+        for (int m = 0; m <= L; ++m) {
+            double pmm = 1.0;
+            for (int j = 1; j <= m; ++j) pmm *= (double)(2 * j - 1) * sx;
+            P[m][m] = pmm;
+            if (m + 1 <= L) P[m + 1][m] = (double)(2 * m + 1) * x * pmm;
+            for (int l = m + 2; l <= L; ++l)
+                P[l][m] = ((double)(2 * l - 1) * x * P[l - 1][m] - (double)(l + m - 1) * P[l - 2][m]) / (double)(l - m);
+        }
+        double* f = fv + (size_t)v * kRayV;
+        f[0] = se;
+        f[1] = ce;
+        for (int l = 0; l <= L; ++l)
+            for (int m = 0; m <= l; ++m) f[2 + l * (l + 1) / 2 + m] = P[l][m];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_raytab(gsrf_grid gr, int L, const double* __restrict__ fu,
+                                                const double* __restrict__ fv, float* __restrict__ tab) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= gr.n_az * gr.n_el) return;
     const int u = i % gr.n_az, v = i / gr.n_az;
-    const double deg = 0.017453292519943295;
-    const double az = ((double)gr.az0_deg + ((double)u + 0.5) * (double)gr.daz_deg) * deg;
-    const double el = ((double)gr.el0_deg + ((double)v + 0.5) * (double)gr.del_deg) * deg;
-    double se, ce, s1, c1;
-    sincos(el, &se, &ce);
-    sincos(az, &s1, &c1);
-    const double x = se, sx = ce;
-    double P[6][6];
-    for (int m = 0; m <= L; ++m) {
-        double pmm = 1.0;
-        for (int j = 1; j <= m; ++j) pmm *= (double)(2 * j - 1) * sx;
-        P[m][m] = pmm;
-        if (m + 1 <= L) P[m + 1][m] = (double)(2 * m + 1) * x * pmm;
-        for (int l = m + 2; l <= L; ++l)
-            P[l][m] = ((double)(2 * l - 1) * x * P[l - 1][m] - (double)(l + m - 1) * P[l - 2][m]) / (double)(l - m);
-    }
+    const double* a = fu + (size_t)u * kRayU;
+    const double* e = fv + (size_t)v * kRayV;
+    const double c1 = a[0], s1 = a[1], se = e[0], ce = e[1];
     const int nf = raytab_floats(L);
     float* t = tab + (size_t)i * nf;
     t[0] = (float)(ce * c1);
     t[1] = (float)(ce * s1);
     t[2] = (float)se;
     int o = 3;
-    for (int l = 1; l <= L; ++l) t[o++] = (float)P[l][0];
+    for (int l = 1; l <= L; ++l) t[o++] = (float)e[2 + l * (l + 1) / 2];
     for (int m = 1; m <= L; ++m) {
-        double sm, cm;
-        sincos((double)m * az, &sm, &cm);
+        const double cm = a[2 * m - 2], sm = a[2 * m - 1];
         for (int l = m; l <= L; ++l) {
-            t[o++] = (float)(cm * P[l][m]);
-            t[o++] = (float)(sm * P[l][m]);
+            const double plm = e[2 + l * (l + 1) / 2 + m];
+            t[o++] = (float)(cm * plm);
+            t[o++] = (float)(sm * plm);
         }
     }
     while (o < nf) t[o++] = 0.0f;
@@ -366,21 +435,28 @@ __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __r
     view[o] = v;
 }
 
+static void launch_raytab(const gsrf_plan* p, const Layout& L, void* ws, cudaStream_t st) {
+    const int n_rays = p->grid.n_az * p->grid.n_el, n_fac = p->grid.n_az + p->grid.n_el;
+    double* fu = at<double>(ws, L.rayfac);
+    double* fv = fu + (size_t)p->grid.n_az * kRayU;
+    k_raytab_factors<<<n_fac, 32, 0, st>>>(p->grid, plan_degree(p), fu, fv);
+    k_raytab<<<(n_rays + 255) / 256, 256, 0, st>>>(p->grid, plan_degree(p), fu, fv, at<float>(ws, L.raytab));
+}
+
 cudaError_t launch_project(const gsrf_plan* p, const Layout& L, const gsrf_gaussians* g, const float* rx,
                            const float* tx, void* ws, cudaStream_t st) {
     DevStatus* status = at<DevStatus>(ws, L.status);
     k_status_init<<<1, 32, 0, st>>>(status);
     if (L.n == 0) {
-        const int n_rays = p->grid.n_az * p->grid.n_el;
-        k_raytab<<<(n_rays + 255) / 256, 256, 0, st>>>(p->grid, plan_degree(p), at<float>(ws, L.raytab));
+        launch_raytab(p, L, ws, st);
         cudaError_t e = cudaMemcpyAsync(at<float>(ws, L.rxpos), rx, sizeof(float) * 3 * L.n_rx,
                                         cudaMemcpyDeviceToDevice, st);
         return e != cudaSuccess ? e : cudaGetLastError();
     }
-    const int n_rays = p->grid.n_az * p->grid.n_el;
-    k_raytab<<<(n_rays + 255) / 256, 256, 0, st>>>(p->grid, plan_degree(p), at<float>(ws, L.raytab));
+    launch_raytab(p, L, ws, st);
     const unsigned nb = (unsigned)((L.n + 255) / 256);
-    k_prepare<<<nb, 256, 0, st>>>(*g, tx, at<GShape>(ws, L.gshape), at<double>(ws, L.dpath),
+    k_prepare<<<(unsigned)((L.n + kPrepThreads - 1) / kPrepThreads), kPrepThreads, 0, st>>>(
+        *g, tx, at<GShape>(ws, L.gshape), at<double>(ws, L.dpath),
                                   at<float>(ws, L.fle), status, p->variant, plan_degree(p));
     k_view<<<dim3(nb, L.n_rx), 256, 0, st>>>(*g, rx, at<GShape>(ws, L.gshape), at<double>(ws, L.dpath),
                                               p->grid, L.ntu, L.ntv, p->f0_hz / kC,
