@@ -140,10 +140,12 @@ typedef struct {
 gsrf_status gsrf_workspace_size(const gsrf_plan *plan, size_t *bytes);
 
 /* Byte offsets inside the workspace of the arrays tests and tools may inspect after
- * gsrf_project (view) and gsrf_bin (the rest): sorted 64-bit splat keys (tile << 32 | FP32 depth bits) [uint64], their
- * Gaussian ids [uint32], both over all receivers back to back; per receiver the first
- * pair (int64, [n_rx + 1]); per receiver and tile the list start relative to the
- * receiver's first pair (uint32, [n_rx][n_tiles + 1]). */
+ * gsrf_project (view) and gsrf_bin (the rest): the sorted pairs' Gaussian ids [uint32]
+ * over all receivers back to back; per receiver the first pair (int64, [n_rx + 1]); per
+ * receiver and tile the list start relative to the receiver's first pair (uint32,
+ * [n_rx][n_tiles + 1]); and the sorted 64-bit splat keys (tile << 32 | FP32 depth bits)
+ * [uint64] parallel to the ids, which gsrf_pair_keys fills on request (gsrf_bin does not:
+ * the render needs only the ids and the tile ranges). */
 typedef struct {
     size_t pair_keys, pair_ids, rx_pair_base, tile_start;
     size_t status;
@@ -175,6 +177,13 @@ gsrf_status gsrf_project(const gsrf_plan *plan, const gsrf_gaussians *g, const f
  * receivers exceed plan.pair_capacity the status word gets GSRF_ERR_CAPACITY and the
  * required count; later steps then write zeros. */
 gsrf_status gsrf_bin(const gsrf_plan *plan, void *workspace, size_t ws_bytes, void *stream);
+
+/* Inspection after gsrf_bin -- App. E, the splat keys of Alg. 1 line 4: writes the sorted
+ * 64-bit key (tile << 32 | FP32 depth bits) of every pair into the workspace array that
+ * gsrf_workspace_layout's pair_keys names, parallel to the pair ids.  The depth bits are
+ * those the depth sort used (|mu - r| in deterministic FP32).  Same arguments and errors as
+ * gsrf_bin; the workspace must hold a completed gsrf_bin of this plan. */
+gsrf_status gsrf_pair_keys(const gsrf_plan *plan, void *workspace, size_t ws_bytes, void *stream);
 
 /* Step 3 -- Alg. 1 lines 6-12, Eq. 14: every ray walks its tile's list front to back,
  * intersects the 3-sigma ellipsoid (App. D.3), weights by the Gaussian at the midpoint

@@ -22,7 +22,7 @@ VARIANT_ORDER_T_MID = 16
 
 # every exported symbol of include/gsrf.h
 EXPORTS = ["gsrf_workspace_size", "gsrf_workspace_layout", "gsrf_ray_state_bytes", "gsrf_project",
-           "gsrf_bin", "gsrf_render_fwd", "gsrf_render_bwd", "gsrf_render", "gsrf_received_signal",
+           "gsrf_bin", "gsrf_pair_keys", "gsrf_render_fwd", "gsrf_render_bwd", "gsrf_render", "gsrf_received_signal",
            "gsrf_read_status", "gsrf_render_static", "gsrf_batch_workspace_size", "gsrf_render_batch",
            "gsrf_autotune_workspace_size", "gsrf_autotune", "gsrf_stage_times", "gsrf_version"]
 STAGE_PROJECT, STAGE_BIN, STAGE_RENDER_FWD, STAGE_RENDER_BWD, STAGE_BATCH = 0, 1, 2, 3, 4
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = False):
     L.gsrf_ray_state_bytes.restype = C.c_size_t
     L.gsrf_project.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, vp, vp, sz, vp]
     L.gsrf_bin.argtypes = [P(gsrf_plan), vp, sz, vp]
+    L.gsrf_pair_keys.argtypes = [P(gsrf_plan), vp, sz, vp]
     L.gsrf_render_fwd.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, sz, vp, vp, vp]
     L.gsrf_render.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, vp, vp, sz, vp, vp, vp]
     L.gsrf_render_bwd.argtypes = [P(gsrf_plan), P(gsrf_gaussians), vp, sz, vp, vp, vp, vp, vp, vp, vp, vp, vp]

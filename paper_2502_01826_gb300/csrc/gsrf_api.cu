@@ -56,7 +56,7 @@ bool make_layout(const gsrf_plan* p, Layout* L) {
     L->rx_total = take(nr * 4);
     L->pchunk_base = take((nr + 1) * 4);
     L->pkeys = take(cap * 8);
-    L->pkeys2 = take(cap * 8);
+    L->pkeys2 = take(cap * 4);  // the pairs' tile indices in depth order (the tile sort's input)
     L->pids = take(cap * 4);
     L->pids2 = take(cap * 4);
     L->tile_start = take(nr * (size_t)(L->n_tiles + 1) * 4);
@@ -275,6 +275,13 @@ gsrf_status gsrf_bin(const gsrf_plan* plan, void* workspace, size_t ws_bytes, vo
     if (s != GSRF_OK) return s;
     StageTimer tm(workspace, GSRF_STAGE_BIN, (cudaStream_t)stream);
     return cuda_status(launch_bin(plan, L, workspace, (cudaStream_t)stream));
+}
+
+gsrf_status gsrf_pair_keys(const gsrf_plan* plan, void* workspace, size_t ws_bytes, void* stream) {
+    Layout L;
+    gsrf_status s = check_ws(plan, workspace, ws_bytes, &L);
+    if (s != GSRF_OK) return s;
+    return cuda_status(launch_pair_keys(L, workspace, (cudaStream_t)stream));
 }
 
 gsrf_status gsrf_render_fwd(const gsrf_plan* plan, const gsrf_gaussians* g, void* workspace, size_t ws_bytes,

@@ -142,6 +142,12 @@ __device__ __forceinline__ float dsub(float a, float b) { return __fsub_rn(a, b)
 __device__ __forceinline__ float ddiv(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float dsqrt(float a) { return __fsqrt_rn(a); }
 
+// |c| in deterministic FP32 (the depth sort key's value, App. E: the low 32 bits of a splat
+// key), c = mu - r.
+__device__ __forceinline__ float depth_of(float cx, float cy, float cz) {
+    return dsqrt(dadd(dadd(dmul(cx, cx), dmul(cy, cy)), dmul(cz, cz)));
+}
+
 // exp(x) for the culling radius: 2^n * e^t with n = floor(x log2 e), t = frac * ln 2,
 // e^t by its Taylor series to t^9 (error ~1e-7, far inside the 1% radius margin).
 __device__ __forceinline__ float det_exp(float x) {
@@ -302,6 +308,7 @@ __device__ __forceinline__ bool circle_in(const float4& cc, int u, int v) {
 cudaError_t launch_project(const gsrf_plan* p, const Layout& L, const gsrf_gaussians* g,
                            const float* rx, const float* tx, void* ws, cudaStream_t st);
 cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream_t st);
+cudaError_t launch_pair_keys(const Layout& L, void* ws, cudaStream_t st);
 cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_gaussians* g,
                               void* ws, float* out, void* ray_state, cudaStream_t st);
 cudaError_t launch_signal(const float* rays, int n_rx, int n_f, int n_el, int n_az, int mode,

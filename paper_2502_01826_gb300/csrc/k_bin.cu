@@ -169,7 +169,8 @@ __global__ void __launch_bounds__(kSortThreads) k_scan(Segs S, int nbins, uint32
     if (seg_total && threadIdx.x == 0) seg_total[seg] = carry;
 }
 
-// Stable scatter.  vin == nullptr: the value is the item's index inside its segment.
+// Stable scatter.  vin == nullptr: the value is the item's index inside its segment;
+// kout == nullptr: only the values are written.
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads) k_scatter(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                           K* __restrict__ kout, uint32_t* __restrict__ vout,
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const K* __restrict__ 
         if (valid) {
             uint32_t off = base[d] + rank;
             for (int w = 0; w < warp; ++w) off += cnt[w][d];
-            kout[seg_lo + off] = key;
+            if (kout) kout[seg_lo + off] = key;
             vout[seg_lo + off] = val;
         }
         __syncthreads();
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter4(const K* __restrict__
             const K k = skey[j];
             const uint32_t dj = digit_of(k, shift, mask);
             const uint32_t off = base[dj] + (j - lstart[dj]);
-            kout[seg_lo + off] = k;
+            if (kout) kout[seg_lo + off] = k;
             vout[seg_lo + off] = sval[j];
         }
         __syncthreads();
@@ -452,7 +453,7 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_pairs(uint32_t* __restric
 }
 
 // Expand the depth-sorted Gaussians into their (tile, Gaussian) pairs, written
-// contiguously in depth order.  A work item is one group of 32 consecutive Gaussians of a
+// contiguously in depth order as (tile index, Gaussian id).  A work item is one group of 32 consecutive Gaussians of a
 // receiver, whose pairs form one contiguous run; warps take items from one counter in
 // group-major order (group 0 of every receiver, then group 1, ...), so the nearest
 // Gaussians, whose covers are the widest and whose runs the longest, come first and
@@ -461,14 +462,13 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_pairs(uint32_t* __restric
 // from its index inside that Gaussian's cover (elevation rows of the set azimuth tiles,
 // in order).
 __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restrict__ dval,
-                                                       const uint32_t* __restrict__ dkey_sorted,
                                                        const Cover* __restrict__ cover, long long n,
                                                        const uint32_t* __restrict__ nvis, int dchunks,
                                                        const uint32_t* __restrict__ chunk_off,
                                                        const uint32_t* __restrict__ group_off,
                                                        const long long* __restrict__ rx_base, int n_rx, int ntu,
                                                        unsigned long long* __restrict__ counter,
-                                                       unsigned long long* __restrict__ pkeys,
+                                                       uint32_t* __restrict__ ptile,
                                                        uint32_t* __restrict__ pids, const DevStatus* st) {
     if (capacity_failed(st)) return;
     constexpr int G = kEChunk / 32;
@@ -484,10 +484,9 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
         const long long nv = nvis[r];
         if (g * 32 >= nv) continue;  // uniform over the warp
         const long long i = g * 32 + lane;
-        uint32_t gid = 0, dk = 0, cnt = 0, tvw = 0, mlo = 0, mhi = 0;
+        uint32_t gid = 0, cnt = 0, tvw = 0, mlo = 0, mhi = 0;
         if (i < nv) {
             gid = dval[(size_t)r * n + i];
-            dk = dkey_sorted[(size_t)r * n + i];
             const Cover cv = cover[(size_t)r * n + gid];
             cnt = cv.count;
             tvw = cv.tv;
@@ -503,7 +502,7 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
         const long long c = g / G;
         const uint32_t wbase = chunk_off[(size_t)r * dchunks + c] + group_off[(size_t)r * dchunks * G + g];
-        unsigned long long* kout = pkeys + rx_base[r] + wbase;
+        uint32_t* kout = ptile + rx_base[r] + wbase;
         uint32_t* iout = pids + rx_base[r] + wbase;
         for (uint32_t s0 = 0; s0 < total; s0 += 32) {
             const uint32_t q = s0 + lane;
@@ -514,7 +513,7 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
                 if (t <= q) j += b;
             }
             const uint32_t oi = __shfl_sync(0xffffffffu, incl, j), oc = __shfl_sync(0xffffffffu, cnt, j);
-            const uint32_t ogid = __shfl_sync(0xffffffffu, gid, j), odk = __shfl_sync(0xffffffffu, dk, j);
+            const uint32_t ogid = __shfl_sync(0xffffffffu, gid, j);
             const uint32_t otv = __shfl_sync(0xffffffffu, tvw, j);
             const uint32_t olo = __shfl_sync(0xffffffffu, mlo, j), ohi = __shfl_sync(0xffffffffu, mhi, j);
             if (q < total) {
@@ -523,7 +522,7 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
                 const uint32_t row = p / nb, col = p - row * nb;
                 const int tu = col < nlo ? select_bit(olo, col) : 32 + select_bit(ohi, col - nlo);
                 const int tv = (int)(otv & 0xffffu) + (int)row;
-                kout[q] = ((unsigned long long)(uint32_t)(tv * ntu + tu) << 32) | odk;
+                kout[q] = (uint32_t)(tv * ntu + tu);
                 iout[q] = ogid;
             }
         }
@@ -591,14 +590,14 @@ cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream
         const Segs& ds = pass == 0 ? ds_all : ds_vis;
         k_hist<uint32_t><<<dblocks, kSortThreads, 0, st>>>(k_in, ds, shift, 0xffu, 256, H, nullptr);
         k_scan<<<L.n_rx, kSortThreads, 0, st>>>(ds, 256, H, nullptr, nullptr, pass == 0 ? nvis : nullptr);
-        launch_scatter<uint32_t>(dblocks, k_in, v_in, k_out, v_out, ds, shift, 0xffu, 256, H, nullptr, st);
+        // the last pass writes the sorted ids only: nothing reads the sorted keys
+        launch_scatter<uint32_t>(dblocks, k_in, v_in, pass == 3 ? nullptr : k_out, v_out, ds, shift, 0xffu, 256, H,
+                                 nullptr, st);
         uint32_t* t = k_in; k_in = k_out; k_out = t;
         v_in = v_out;
         v_out = (v_out == at<uint32_t>(ws, L.dval)) ? v_alt : at<uint32_t>(ws, L.dval);
     }
-    // after 4 passes the sorted keys / values are back in dkey / dval2 ... track them:
-    const uint32_t* dkey_sorted = k_in;
-    const uint32_t* dval_sorted = v_in;
+    const uint32_t* dval_sorted = v_in;  // each receiver's ids in (depth, id) order
 
     // (2) emission in depth order
     uint32_t* chunk_sum = at<uint32_t>(ws, L.dchunk_sum);
@@ -617,22 +616,48 @@ cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream
     const long long groups = (long long)L.n_rx * L.echunks * (kEChunk / 32);
     const unsigned emit_grid =
         (unsigned)max(1ll, min((long long)sms * max(per_sm, 1), (groups + kSortWarps - 1) / kSortWarps));
-    k_emit<<<emit_grid, kSortThreads, 0, st>>>(dval_sorted, dkey_sorted, at<Cover>(ws, L.cover), L.n, nvis, L.echunks,
-                                               chunk_sum, group_off, at<long long>(ws, L.rx_base), L.n_rx, L.ntu,
-                                               ecounter, at<unsigned long long>(ws, L.pkeys2), at<uint32_t>(ws, L.pids2),
-                                               status);
+    uint32_t* ptile = at<uint32_t>(ws, L.pkeys2);  // the pairs' tile indices, in depth order
+    k_emit<<<emit_grid, kSortThreads, 0, st>>>(dval_sorted, at<Cover>(ws, L.cover), L.n, nvis, L.echunks, chunk_sum,
+                                               group_off, at<long long>(ws, L.rx_base), L.n_rx, L.ntu, ecounter, ptile,
+                                               at<uint32_t>(ws, L.pids2), status);
 
-    // (3) stable counting sort of each receiver's pairs by tile: pkeys2 -> pkeys
+    // (3) stable counting sort of each receiver's pairs by tile index: ids pids2 -> pids (the
+    // 64-bit splat keys are formed only on request, by launch_pair_keys)
     Segs ps{L.n_rx, -1, 0, kChunk, at<long long>(ws, L.rx_base), at<uint32_t>(ws, L.pchunk_base), nullptr, 0};
     const unsigned pblocks = (unsigned)L.pchunks_max;
     uint32_t* TH = at<uint32_t>(ws, L.thist);
-    k_hist<unsigned long long><<<pblocks, kSortThreads, 0, st>>>(at<unsigned long long>(ws, L.pkeys2), ps, 32,
-                                                                 0xffffffffu, L.n_tiles, TH, status);
+    k_hist<uint32_t><<<pblocks, kSortThreads, 0, st>>>(ptile, ps, 0, 0xffffffffu, L.n_tiles, TH, status);
     k_scan<<<L.n_rx, kSortThreads, 0, st>>>(ps, L.n_tiles, TH, at<uint32_t>(ws, L.tile_start), status);
-    launch_scatter<unsigned long long>(pblocks, at<unsigned long long>(ws, L.pkeys2), at<uint32_t>(ws, L.pids2),
-                                       at<unsigned long long>(ws, L.pkeys), at<uint32_t>(ws, L.pids), ps, 32,
-                                       0xffffffffu, L.n_tiles, TH, status, st);
+    launch_scatter<uint32_t>(pblocks, ptile, at<uint32_t>(ws, L.pids2), nullptr, at<uint32_t>(ws, L.pids), ps, 0,
+                             0xffffffffu, L.n_tiles, TH, status, st);
     (void)p;
+    return cudaGetLastError();
+}
+
+// The sorted 64-bit splat keys (tile << 32 | FP32 depth bits) of the last bin, for
+// inspection: the render needs only the ids and the tile ranges.  One block per (tile,
+// receiver); the depth bits are recomputed from the view record's c = mu - r by the same
+// deterministic operations as the projection's depth key.
+__global__ void __launch_bounds__(kSortThreads) k_pair_keys(const View* __restrict__ view,
+                                                            const uint32_t* __restrict__ pids,
+                                                            const long long* __restrict__ rx_base,
+                                                            const uint32_t* __restrict__ tile_start, int n_tiles,
+                                                            long long n, unsigned long long* __restrict__ keys) {
+    const int t = blockIdx.x, r = blockIdx.y;
+    const size_t ts = (size_t)r * (n_tiles + 1) + t;
+    const uint32_t b = tile_start[ts], e = tile_start[ts + 1];
+    for (uint32_t i = b + threadIdx.x; i < e; i += kSortThreads) {
+        const long long p = rx_base[r] + i;
+        const View& v = view[(size_t)r * n + pids[p]];
+        keys[p] = ((unsigned long long)(uint32_t)t << 32) | __float_as_uint(depth_of(v.c[0], v.c[1], v.c[2]));
+    }
+}
+
+cudaError_t launch_pair_keys(const Layout& L, void* ws, cudaStream_t st) {
+    if (L.n == 0 || L.n_tiles == 0) return cudaSuccess;
+    k_pair_keys<<<dim3(L.n_tiles, L.n_rx), kSortThreads, 0, st>>>(
+        at<View>(ws, L.view), at<uint32_t>(ws, L.pids), at<long long>(ws, L.rx_base), at<uint32_t>(ws, L.tile_start),
+        L.n_tiles, L.n, at<unsigned long long>(ws, L.pkeys));
     return cudaGetLastError();
 }
 

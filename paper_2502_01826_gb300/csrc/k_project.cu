@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __r
     v.w[2] = sh.W[6] * ux + sh.W[7] * uy + sh.W[8] * uz;
     // depth key and coverage: deterministic FP32 on c = mu - r
     const float cx = dsub(mx, rx), cy = dsub(my, ry), cz = dsub(mz, rz);
-    const float D = dsqrt(dadd(dadd(dmul(cx, cx), dmul(cy, cy)), dmul(cz, cz)));
+    const float D = depth_of(cx, cy, cz);
     const float lsm = fmaxf(fmaxf(g.log_scales[3 * k], g.log_scales[3 * k + 1]), g.log_scales[3 * k + 2]);
     float D_c, Rs;
     bool wide;

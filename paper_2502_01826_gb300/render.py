@@ -204,9 +204,11 @@ class Renderer:
         nr, n = self.plan.n_rx, self.plan.n_gauss
         return self.ws[lay.view: lay.view + 48 * nr * n].view(torch.float32).view(nr, n, 12)
 
-    def pairs(self):
+    def pairs(self, stream=None):
         """Views into the workspace after bin: (keys uint64 [total], ids int32 [total],
-        rx_base int64 [n_rx+1], tile_start int32 [n_rx, n_tiles+1])."""
+        rx_base int64 [n_rx+1], tile_start int32 [n_rx, n_tiles+1]); the keys are formed
+        here by gsrf_pair_keys (the bin itself writes only the ids and the ranges)."""
+        L.call("gsrf_pair_keys", C.byref(self.plan), _ptr(self.ws), self.ws_bytes, _stream(stream))
         lay = self.layout()
         nt = lay.n_tiles_u * lay.n_tiles_v
         nr = self.plan.n_rx
