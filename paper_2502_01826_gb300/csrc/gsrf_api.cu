@@ -51,7 +51,7 @@ bool make_layout(const gsrf_plan* p, Layout* L) {
     L->dvis = take(nr * 4);
     L->dchunk_sum = take(nr * (size_t)L->echunks * 4);
     L->egroup = take(nr * (size_t)L->echunks * (kEChunk / 32) * 4);
-    L->ecounter = take(8);
+    L->eslice = take(((size_t)L->n_rx + 1) * 4);
     L->rx_base = take((nr + 1) * 8);
     L->rx_total = take(nr * 4);
     L->pchunk_base = take((nr + 1) * 4);

@@ -16,6 +16,7 @@ constexpr int kRenderThreads = kTile * kTile;
 constexpr int kChunk = 4096;          // items per block in the sort passes
 constexpr int kDChunk = 2048;         // items per block in the depth passes
 constexpr int kEChunk = 1024;         // depth-sorted Gaussians per block in the emission
+constexpr int kESlice = 512;          // pairs per emission work item
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kMaxTiles = 1024;       // bins of the tile counting sort
@@ -111,7 +112,7 @@ struct __align__(16) RayState {
 
 struct Layout {
     // byte offsets
-    size_t status, rxpos, txpos, gacc, raytab, fle, gshape, dpath, view, cover, rayfac, dkey, dkey2, dval, dval2, dhist, dvis, dchunk_sum, egroup, ecounter,
+    size_t status, rxpos, txpos, gacc, raytab, fle, gshape, dpath, view, cover, rayfac, dkey, dkey2, dval, dval2, dhist, dvis, dchunk_sum, egroup, eslice,
         rx_base, rx_total, pchunk_base, pkeys, pkeys2, pids, pids2, tile_start, thist, qkeys, qkeys2, qorder, qhist,
         qcounter, circle, tbuf, total;
     int32_t ntu, ntv, n_tiles;

@@ -408,14 +408,13 @@ __global__ void __launch_bounds__(kSortThreads) k_count_chunks(const uint32_t* _
     }
 }
 
-// One block: chunk offsets per receiver, receiver bases, capacity check, and the
-// chunk table of the tile sort.
+// One block: chunk offsets per receiver, receiver bases, capacity check, the chunk
+// table of the tile sort and the slice table of the emission.
 __global__ void __launch_bounds__(kSortThreads) k_scan_pairs(uint32_t* __restrict__ chunk_sum, int n_rx, int dchunks,
                                                              long long cap, long long* __restrict__ rx_base,
                                                              uint32_t* __restrict__ rx_total,
                                                              uint32_t* __restrict__ pchunk_base, DevStatus* st,
-                                                             unsigned long long* __restrict__ emit_counter) {
-    if (threadIdx.x == 0) *emit_counter = 0ull;
+                                                             uint32_t* __restrict__ eslice_base) {
     for (int r = threadIdx.x; r < n_rx; r += kSortThreads) {
         uint32_t run = 0;
         uint32_t* cs = chunk_sum + (size_t)r * dchunks;
@@ -434,97 +433,120 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_pairs(uint32_t* __restric
     __syncthreads();
     if (threadIdx.x == 0) {
         long long b = 0;
-        uint32_t cb = 0;
+        uint32_t cb = 0, es = 0;
         for (int r = 0; r < n_rx; ++r) {
             rx_base[r] = b;
             pchunk_base[r] = cb;
+            eslice_base[r] = es;
             b += rx_total[r];
             cb += (rx_total[r] + kChunk - 1) / kChunk;
+            es += (rx_total[r] + kESlice - 1) / kESlice;
         }
         rx_base[n_rx] = b;
         pchunk_base[n_rx] = cb;
+        eslice_base[n_rx] = es;
         st->required_pairs = b;
         if (b > cap) {
             atomicCAS(&st->code, (int)GSRF_OK, (int)GSRF_ERR_CAPACITY);
             // a failed bin leaves no pairs: downstream kernels see empty lists
-            for (int r = 0; r <= n_rx; ++r) { rx_base[r] = 0; pchunk_base[r] = 0; }
+            for (int r = 0; r <= n_rx; ++r) { rx_base[r] = 0; pchunk_base[r] = 0; eslice_base[r] = 0; }
         }
     }
 }
 
 // Expand the depth-sorted Gaussians into their (tile, Gaussian) pairs, written
-// contiguously in depth order as (tile index, Gaussian id).  A work item is one group of 32 consecutive Gaussians of a
-// receiver, whose pairs form one contiguous run; warps take items from one counter in
-// group-major order (group 0 of every receiver, then group 1, ...), so the nearest
-// Gaussians, whose covers are the widest and whose runs the longest, come first and
-// spread over all warps.  The warp writes its run 32 slots at a time (coalesced), each
-// slot finding its Gaussian by a search over the warp's inclusive counts and its tile
+// contiguously in depth order as (tile index, Gaussian id).  The work is split into
+// slices of kESlice consecutive pairs of a receiver (eslice_base), one per warp at a time,
+// so that the nearest Gaussians, whose covers are the widest, spread over many warps
+// instead of one.  A slice finds the group of 32 sorted Gaussians that holds its first
+// pair by a binary search over the groups' first pairs (chunk_off + group_off), loads that
+// group and writes the slice's part of the group's run 32 slots at a time (coalesced):
+// each slot finds its Gaussian by a search over the warp's inclusive counts and its tile
 // from its index inside that Gaussian's cover (elevation rows of the set azimuth tiles,
-// in order).
+// in order); then it goes on with the next group until the slice is done.
 __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restrict__ dval,
                                                        const Cover* __restrict__ cover, long long n,
                                                        const uint32_t* __restrict__ nvis, int dchunks,
                                                        const uint32_t* __restrict__ chunk_off,
                                                        const uint32_t* __restrict__ group_off,
-                                                       const long long* __restrict__ rx_base, int n_rx, int ntu,
-                                                       unsigned long long* __restrict__ counter,
-                                                       uint32_t* __restrict__ ptile,
-                                                       uint32_t* __restrict__ pids, const DevStatus* st) {
+                                                       const long long* __restrict__ rx_base,
+                                                       const uint32_t* __restrict__ rx_total,
+                                                       const uint32_t* __restrict__ eslice_base, int n_rx, int ntu,
+                                                       uint32_t* __restrict__ ptile, uint32_t* __restrict__ pids,
+                                                       const DevStatus* st) {
     if (capacity_failed(st)) return;
     constexpr int G = kEChunk / 32;
     const int lane = threadIdx.x & 31;
-    const unsigned long long items = (unsigned long long)n_rx * dchunks * G;
-    for (;;) {
-        unsigned long long it = 0;
-        if (lane == 0) it = atomicAdd(counter, 1ull);
-        it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= items) break;
-        const int r = (int)(it % (unsigned long long)n_rx);
-        const long long g = (long long)(it / (unsigned long long)n_rx);  // group inside the receiver
+    const uint32_t slices = eslice_base[n_rx];
+    const uint32_t warps = gridDim.x * kSortWarps;
+    for (uint32_t w = blockIdx.x * kSortWarps + (threadIdx.x >> 5); w < slices; w += warps) {
+        // receiver: the last r with eslice_base[r] <= w
+        int r = 0;
+        for (int z = n_rx; r < z;) {
+            const int mid = (r + z + 1) >> 1;
+            if (eslice_base[mid] <= w) r = mid;
+            else z = mid - 1;
+        }
+        const uint32_t total_r = rx_total[r];
+        uint32_t P0 = (w - eslice_base[r]) * (uint32_t)kESlice;
+        const uint32_t P1 = min(P0 + (uint32_t)kESlice, total_r);
         const long long nv = nvis[r];
-        if (g * 32 >= nv) continue;  // uniform over the warp
-        const long long i = g * 32 + lane;
-        uint32_t gid = 0, cnt = 0, tvw = 0, mlo = 0, mhi = 0;
-        if (i < nv) {
-            gid = dval[(size_t)r * n + i];
-            const Cover cv = cover[(size_t)r * n + gid];
-            cnt = cv.count;
-            tvw = cv.tv;
-            mlo = (uint32_t)cv.mask;
-            mhi = (uint32_t)(cv.mask >> 32);
+        const int ng = (int)((nv + 31) / 32);
+        const uint32_t* co = chunk_off + (size_t)r * dchunks;
+        const uint32_t* go = group_off + (size_t)r * dchunks * G;
+        // the group that holds pair P0: the last g with first pair <= P0
+        int g = 0;
+        for (int z = ng - 1; g < z;) {
+            const int mid = (g + z + 1) >> 1;
+            if (co[mid / G] + go[mid] <= P0) g = mid;
+            else z = mid - 1;
         }
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += t;
-        }
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        const long long c = g / G;
-        const uint32_t wbase = chunk_off[(size_t)r * dchunks + c] + group_off[(size_t)r * dchunks * G + g];
-        uint32_t* kout = ptile + rx_base[r] + wbase;
-        uint32_t* iout = pids + rx_base[r] + wbase;
-        for (uint32_t s0 = 0; s0 < total; s0 += 32) {
-            const uint32_t q = s0 + lane;
-            int j = 0;  // lanes whose inclusive count is <= q: the owner of slot q
-#pragma unroll
-            for (int b = 16; b; b >>= 1) {
-                const uint32_t t = __shfl_sync(0xffffffffu, incl, j + b - 1);
-                if (t <= q) j += b;
+        uint32_t* kout = ptile + rx_base[r];
+        uint32_t* iout = pids + rx_base[r];
+        while (P0 < P1 && g < ng) {  // uniform over the warp
+            const long long i = (long long)g * 32 + lane;
+            uint32_t gid = 0, cnt = 0, tvw = 0, mlo = 0, mhi = 0;
+            if (i < nv) {
+                gid = dval[(size_t)r * n + i];
+                const Cover cv = cover[(size_t)r * n + gid];
+                cnt = cv.count;
+                tvw = cv.tv;
+                mlo = (uint32_t)cv.mask;
+                mhi = (uint32_t)(cv.mask >> 32);
             }
-            const uint32_t oi = __shfl_sync(0xffffffffu, incl, j), oc = __shfl_sync(0xffffffffu, cnt, j);
-            const uint32_t ogid = __shfl_sync(0xffffffffu, gid, j);
-            const uint32_t otv = __shfl_sync(0xffffffffu, tvw, j);
-            const uint32_t olo = __shfl_sync(0xffffffffu, mlo, j), ohi = __shfl_sync(0xffffffffu, mhi, j);
-            if (q < total) {
-                const uint32_t p = q - (oi - oc);  // pair index inside the owner's cover
-                const uint32_t nlo = __popc(olo), nb = nlo + __popc(ohi);
-                const uint32_t row = p / nb, col = p - row * nb;
-                const int tu = col < nlo ? select_bit(olo, col) : 32 + select_bit(ohi, col - nlo);
-                const int tv = (int)(otv & 0xffffu) + (int)row;
-                kout[q] = (uint32_t)(tv * ntu + tu);
-                iout[q] = ogid;
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += t;
             }
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            const uint32_t base = co[g / G] + go[g];  // the group's first pair
+            const uint32_t q1 = min(P1 - base, total);
+            for (uint32_t s0 = P0 - base; s0 < q1; s0 += 32) {
+                const uint32_t q = s0 + lane;
+                int j = 0;  // lanes whose inclusive count is <= q: the owner of slot q
+#pragma unroll
+                for (int b = 16; b; b >>= 1) {
+                    const uint32_t t = __shfl_sync(0xffffffffu, incl, j + b - 1);
+                    if (t <= q) j += b;
+                }
+                const uint32_t oi = __shfl_sync(0xffffffffu, incl, j), oc = __shfl_sync(0xffffffffu, cnt, j);
+                const uint32_t ogid = __shfl_sync(0xffffffffu, gid, j);
+                const uint32_t otv = __shfl_sync(0xffffffffu, tvw, j);
+                const uint32_t olo = __shfl_sync(0xffffffffu, mlo, j), ohi = __shfl_sync(0xffffffffu, mhi, j);
+                if (q < q1) {
+                    const uint32_t p = q - (oi - oc);  // pair index inside the owner's cover
+                    const uint32_t nlo = __popc(olo), nb = nlo + __popc(ohi);
+                    const uint32_t row = p / nb, col = p - row * nb;
+                    const int tu = col < nlo ? select_bit(olo, col) : 32 + select_bit(ohi, col - nlo);
+                    const int tv = (int)(otv & 0xffffu) + (int)row;
+                    kout[base + q] = (uint32_t)(tv * ntu + tu);
+                    iout[base + q] = ogid;
+                }
+            }
+            P0 = base + total;
+            ++g;
         }
     }
 }
@@ -602,24 +624,25 @@ cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream
     // (2) emission in depth order
     uint32_t* chunk_sum = at<uint32_t>(ws, L.dchunk_sum);
     uint32_t* group_off = at<uint32_t>(ws, L.egroup);
-    unsigned long long* ecounter = at<unsigned long long>(ws, L.ecounter);
+    uint32_t* eslice_base = at<uint32_t>(ws, L.eslice);
     k_count_chunks<<<dim3(L.echunks, L.n_rx), kSortThreads, 0, st>>>(dval_sorted, at<Cover>(ws, L.cover), L.n,
                                                                        nvis, L.echunks, chunk_sum, group_off);
     k_scan_pairs<<<1, kSortThreads, 0, st>>>(chunk_sum, L.n_rx, L.echunks, L.cap, at<long long>(ws, L.rx_base),
                                              at<uint32_t>(ws, L.rx_total), at<uint32_t>(ws, L.pchunk_base), status,
-                                             ecounter);
-    // one resident wave of warps taking the groups from the counter
+                                             eslice_base);
+    // one resident wave of warps striding over the slices
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_emit, kSortThreads, 0)) != cudaSuccess) return e;
-    const long long groups = (long long)L.n_rx * L.echunks * (kEChunk / 32);
+    const long long max_slices = ((long long)L.cap + kESlice - 1) / kESlice + L.n_rx;
     const unsigned emit_grid =
-        (unsigned)max(1ll, min((long long)sms * max(per_sm, 1), (groups + kSortWarps - 1) / kSortWarps));
+        (unsigned)max(1ll, min((long long)sms * max(per_sm, 1), (max_slices + kSortWarps - 1) / kSortWarps));
     uint32_t* ptile = at<uint32_t>(ws, L.pkeys2);  // the pairs' tile indices, in depth order
     k_emit<<<emit_grid, kSortThreads, 0, st>>>(dval_sorted, at<Cover>(ws, L.cover), L.n, nvis, L.echunks, chunk_sum,
-                                               group_off, at<long long>(ws, L.rx_base), L.n_rx, L.ntu, ecounter, ptile,
-                                               at<uint32_t>(ws, L.pids2), status);
+                                               group_off, at<long long>(ws, L.rx_base), at<uint32_t>(ws, L.rx_total),
+                                               eslice_base, L.n_rx, L.ntu, ptile, at<uint32_t>(ws, L.pids2),
+                                               status);
 
     // (3) stable counting sort of each receiver's pairs by tile index: ids pids2 -> pids (the
     // 64-bit splat keys are formed only on request, by launch_pair_keys)
