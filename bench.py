@@ -358,6 +358,11 @@ def autotune(R, p, rx, tx, args, reps, training=False):
     R.plan.pair_capacity = 3 * cap  # room for the small-tile candidates' extra pairs
     R._alloc()
     best, table = R.autotune(p, rx, tx, reps=reps, training=training)
+    # then size the workspace to the chosen split's pairs (5% slack), as a caller would for
+    # its plan: the bin launches one block per 4096 pairs of capacity, empty ones included
+    R.plan.pair_capacity = 1024
+    R._alloc()
+    R.ensure_capacity(p, rx, tx)
     dflt = [t for t in table if (t["tile_w"], t["tile_h"], t["ray_block_w"], t["stage"]) == (16, 16, 8, 32)]
     return {"best": best, "default_16x16_8x4_32": dflt[0] if dflt else None, "candidates": len(table),
             "what": "median of %d event-timed runs per candidate: project + bin per tile shape, %s per "
