@@ -70,9 +70,10 @@ FLOP_HIT = 172
 RENDER_TRAFFIC = {(16, 16, 8, 32): 85583104 + 7175424, (32, 16, 8, 32): 79896320 + 6626304,
                   (32, 32, 8, 32): 84491008 + 6703104}
 # library kernels per step: project 5 (status, ray-table factors, ray table, shape records,
-# view records), bin 19 (zero, 4 x (hist, scan, scatter), count, scan, emit, tile hist, scan,
-# scatter), render 5 (item keys, counting pass of 3, persistent render), received signal 1
-LAUNCHES_PER_STEP = 30
+# view records), bin 18 (zero, 4 x (hist, scan, scatter), count, scan, emit with the tile
+# histogram, tile scan, scatter), render 5 (item keys, counting pass of 3, persistent render),
+# received signal 1
+LAUNCHES_PER_STEP = 29
 # nominal FP32 lanes per SM (context beside the measured FP32 peak)
 SMS, FP32_LANES = 152, 128
 

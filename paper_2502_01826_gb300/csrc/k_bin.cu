@@ -472,6 +472,8 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
                                                        const long long* __restrict__ rx_base,
                                                        const uint32_t* __restrict__ rx_total,
                                                        const uint32_t* __restrict__ eslice_base, int n_rx, int ntu,
+                                                       const uint32_t* __restrict__ pchunk_base, int n_tiles,
+                                                       uint32_t* __restrict__ thist,
                                                        uint32_t* __restrict__ ptile, uint32_t* __restrict__ pids,
                                                        const DevStatus* st) {
     if (capacity_failed(st)) return;
@@ -541,7 +543,10 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
                     const uint32_t row = p / nb, col = p - row * nb;
                     const int tu = col < nlo ? select_bit(olo, col) : 32 + select_bit(ohi, col - nlo);
                     const int tv = (int)(otv & 0xffffu) + (int)row;
-                    kout[base + q] = (uint32_t)(tv * ntu + tu);
+                    const uint32_t tile = (uint32_t)(tv * ntu + tu);
+                    kout[base + q] = tile;
+                    // the tile pass's histogram: pairs per (pair chunk of kChunk, tile)
+                    atomicAdd(thist + (size_t)(pchunk_base[r] + (base + q) / (uint32_t)kChunk) * n_tiles + tile, 1u);
                     iout[base + q] = ogid;
                 }
             }
@@ -639,17 +644,17 @@ cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream
     const unsigned emit_grid =
         (unsigned)max(1ll, min((long long)sms * max(per_sm, 1), (max_slices + kSortWarps - 1) / kSortWarps));
     uint32_t* ptile = at<uint32_t>(ws, L.pkeys2);  // the pairs' tile indices, in depth order
+    uint32_t* TH = at<uint32_t>(ws, L.thist);       // filled by the emission
+    if ((e = cudaMemsetAsync(TH, 0, (size_t)L.pchunks_max * L.n_tiles * sizeof(uint32_t), st)) != cudaSuccess) return e;
     k_emit<<<emit_grid, kSortThreads, 0, st>>>(dval_sorted, at<Cover>(ws, L.cover), L.n, nvis, L.echunks, chunk_sum,
                                                group_off, at<long long>(ws, L.rx_base), at<uint32_t>(ws, L.rx_total),
-                                               eslice_base, L.n_rx, L.ntu, ptile, at<uint32_t>(ws, L.pids2),
-                                               status);
+                                               eslice_base, L.n_rx, L.ntu, at<uint32_t>(ws, L.pchunk_base), L.n_tiles,
+                                               TH, ptile, at<uint32_t>(ws, L.pids2), status);
 
     // (3) stable counting sort of each receiver's pairs by tile index: ids pids2 -> pids (the
     // 64-bit splat keys are formed only on request, by launch_pair_keys)
     Segs ps{L.n_rx, -1, 0, kChunk, at<long long>(ws, L.rx_base), at<uint32_t>(ws, L.pchunk_base), nullptr, 0};
     const unsigned pblocks = (unsigned)L.pchunks_max;
-    uint32_t* TH = at<uint32_t>(ws, L.thist);
-    k_hist<uint32_t><<<pblocks, kSortThreads, 0, st>>>(ptile, ps, 0, 0xffffffffu, L.n_tiles, TH, status);
     k_scan<<<L.n_rx, kSortThreads, 0, st>>>(ps, L.n_tiles, TH, at<uint32_t>(ws, L.tile_start), status);
     launch_scatter<uint32_t>(pblocks, ptile, at<uint32_t>(ws, L.pids2), nullptr, at<uint32_t>(ws, L.pids), ps, 0,
                              0xffffffffu, L.n_tiles, TH, status, st);
