@@ -159,6 +159,11 @@ def test_calls_reject_bad_pointers_before_launch(lib):
                             None) == L.GSRF_ERR_INVALID_ARG
     assert lib.gsrf_bin(C.byref(p), C.c_void_p(4096 + 8), sz.value, None) == L.GSRF_ERR_INVALID_ARG
     assert lib.gsrf_bin(C.byref(p), C.c_void_p(4096), sz.value - 1, None) == L.GSRF_ERR_INVALID_ARG
+    # the inspection call takes the same checks as the bin
+    assert lib.gsrf_pair_keys(C.byref(p), None, sz.value, None) == L.GSRF_ERR_INVALID_ARG
+    assert lib.gsrf_pair_keys(C.byref(p), C.c_void_p(4096 + 8), sz.value, None) == L.GSRF_ERR_INVALID_ARG
+    assert lib.gsrf_pair_keys(C.byref(p), C.c_void_p(4096), sz.value - 1, None) == L.GSRF_ERR_INVALID_ARG
+    assert lib.gsrf_pair_keys(None, C.c_void_p(4096), sz.value, None) == L.GSRF_ERR_INVALID_ARG
     assert lib.gsrf_project(C.byref(p), C.byref(g), C.c_void_p(256), C.c_void_p(256), C.c_void_p(4096),
                             sz.value, None) == L.GSRF_ERR_INVALID_ARG
     assert lib.gsrf_received_signal(None, 1, 1, 1, 1, 0, None, None) == L.GSRF_ERR_INVALID_ARG
