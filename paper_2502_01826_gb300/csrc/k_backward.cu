@@ -286,27 +286,36 @@ __device__ __forceinline__ void bwd_block(const BwdArgs& a, int r, int tile, int
                     const float ws = rec[2].y + a.dlt * Gam;
                     float rs, rc;
                     sincosf(ws, &rs, &rc);  // r = e^{-j ws} = rc - j rs
-                    // Horner over s = 2 g_pairs - 1 .. 0: D <- D r + H, H <- H r + conj(G_s)
+                    // Horner in x = r^2 on the even and odd coefficients, two independent
+                    // chains: H = E(x) + r O(x) with E = sum_k conj(G_2k) x^k, O = sum_k
+                    // conj(G_2k+1) x^k, and D = r dH/dr = 2 x E'(x) + r (O(x) + 2 x O'(x));
+                    // each chain carries its derivative (E' <- E' x + E, E <- E x + c)
                     const float4* row = sg + lane * a.g_stride4;
-                    float hr = 0.0f, hi = 0.0f, dr = 0.0f, di = 0.0f;
+                    const float c2 = rc * rc - rs * rs, s2x = 2.0f * rs * rc;  // x = c2 - j s2x
+                    float er = 0.0f, ei = 0.0f, edr = 0.0f, edi = 0.0f;  // E, E'
+                    float orr = 0.0f, oi = 0.0f, odr = 0.0f, odi = 0.0f;  // O, O'
                     for (int i = a.g_pairs - 1; i >= 0; --i) {
                         const float4 c = row[i];  // G_{2i} (x, y), G_{2i+1} (z, w)
-                        float t = dr * rc + di * rs + hr;
-                        di = di * rc - dr * rs + hi;
-                        dr = t;
-                        t = hr * rc + hi * rs + c.z;
-                        hi = hi * rc - hr * rs - c.w;
-                        hr = t;
-                        t = dr * rc + di * rs + hr;
-                        di = di * rc - dr * rs + hi;
-                        dr = t;
-                        t = hr * rc + hi * rs + c.x;
-                        hi = hi * rc - hr * rs - c.y;
-                        hr = t;
+                        float t = edr * c2 + edi * s2x + er;
+                        edi = edi * c2 - edr * s2x + ei;
+                        edr = t;
+                        t = er * c2 + ei * s2x + c.x;
+                        ei = ei * c2 - er * s2x - c.y;
+                        er = t;
+                        t = odr * c2 + odi * s2x + orr;
+                        odi = odi * c2 - odr * s2x + oi;
+                        odr = t;
+                        t = orr * c2 + oi * s2x + c.z;
+                        oi = oi * c2 - orr * s2x - c.w;
+                        orr = t;
                     }
-                    // H' = omega_0 H + dlt r dH/dr
-                    const float h2r = omega * hr + a.dlt * (dr * rc + di * rs);
-                    const float h2i = omega * hi + a.dlt * (di * rc - dr * rs);
+                    const float hr = er + (orr * rc + oi * rs), hi = ei + (oi * rc - orr * rs);
+                    const float xer = edr * c2 + edi * s2x, xei = edi * c2 - edr * s2x;  // x E'
+                    const float ur = orr + 2.0f * (odr * c2 + odi * s2x), ui = oi + 2.0f * (odi * c2 - odr * s2x);
+                    const float dr = 2.0f * xer + (ur * rc + ui * rs), di = 2.0f * xei + (ui * rc - ur * rs);
+                    // H' = omega_0 H + dlt D
+                    const float h2r = omega * hr + a.dlt * dr;
+                    const float h2i = omega * hi + a.dlt * di;
                     const float pwr = pr * wr - pi * wi, pwi = pr * wi + pi * wr;  // psi w at f0
                     const float xr = pwr * hr - pwi * hi, xi = pwr * hi + pwi * hr;  // psi w H
                     const float yr = pwr * h2r - pwi * h2i, yi = pwr * h2i + pwi * h2r;  // psi w H'
