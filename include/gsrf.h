@@ -156,7 +156,9 @@ typedef struct {
                                 * 4-6 whitened receiver offset, 7-8 e^{-j 2 pi f0 d / c}
                                 * (cos, -sin) with the phase reduced in FP64, 9 the
                                 * per-subcarrier step 2 pi df d / c, 10-11 the radiance at
-                                * the direction of mu (GSRF_VARIANT_RADIANCE_AT_MEAN), else 0 */
+                                * the direction of mu (GSRF_VARIANT_RADIANCE_AT_MEAN), else 0;
+                                * for a Gaussian that covers no tile of that receiver only
+                                * floats 0-2 and a NaN in float 3 (the rest is not written) */
 } gsrf_layout;
 gsrf_status gsrf_workspace_layout(const gsrf_plan *plan, gsrf_layout *out);
 

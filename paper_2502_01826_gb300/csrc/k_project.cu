@@ -368,7 +368,9 @@ __device__ __forceinline__ void radiance_at(const float* __restrict__ q, float c
     }
 }
 
-// One thread per (receiver, Gaussian): whitened offset, depth key, coverage, phase.
+// One thread per (receiver, Gaussian): depth key and coverage; then, for a Gaussian that
+// covers some tile, whitened offset, cone term and path phase (a Gaussian in no tile's
+// list keeps only c and a NaN cone term: nothing reads the rest).
 __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __restrict__ rxp,
                                               const GShape* __restrict__ shape,
                                               const double* __restrict__ dpath_t, gsrf_grid gr,
@@ -394,16 +396,11 @@ __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __r
     const size_t o = (size_t)r * g.n + k;
     const float rx = rxp[3 * r], ry = rxp[3 * r + 1], rz = rxp[3 * r + 2];
     const float mx = g.means[3 * k], my = g.means[3 * k + 1], mz = g.means[3 * k + 2];
-    const GShape sh = shape[k];
-    // whitened receiver offset (FP32, contraction allowed: not a decision)
     const float ux = rx - mx, uy = ry - my, uz = rz - mz;
     View v;
     v.c[0] = -ux;
     v.c[1] = -uy;
     v.c[2] = -uz;
-    v.w[0] = sh.W[0] * ux + sh.W[1] * uy + sh.W[2] * uz;
-    v.w[1] = sh.W[3] * ux + sh.W[4] * uy + sh.W[5] * uz;
-    v.w[2] = sh.W[6] * ux + sh.W[7] * uy + sh.W[8] * uz;
     // depth key and coverage: deterministic FP32 on c = mu - r
     const float cx = dsub(mx, rx), cy = dsub(my, ry), cz = dsub(mz, rz);
     const float D = depth_of(cx, cy, cz);
@@ -413,6 +410,16 @@ __global__ void __launch_bounds__(256) k_view(gsrf_gaussians g, const float* __r
     const Cover cv = cover_of(cx, cy, cz, lsm, gr, ntu, ntv, D_c, Rs, wide);
     cover[o] = cv;
     dkey[o] = cv.count ? __float_as_uint(D) : kAbsentKey;  // no tile: left out of the depth sort
+    if (!cv.count) {
+        // in no tile's list, so nothing reads the rest of the record: c and a NaN mark only
+        reinterpret_cast<float4*>(view + o)[0] = make_float4(-ux, -uy, -uz, __int_as_float(0x7fc00000));
+        return;
+    }
+    // whitened receiver offset (FP32, contraction allowed: not a decision)
+    const GShape sh = shape[k];
+    v.w[0] = sh.W[0] * ux + sh.W[1] * uy + sh.W[2] * uz;
+    v.w[1] = sh.W[3] * ux + sh.W[4] * uy + sh.W[5] * uz;
+    v.w[2] = sh.W[6] * ux + sh.W[7] * uy + sh.W[8] * uz;
     if (variant & GSRF_VARIANT_PAPER_CULLING)
         circle[o] = circle_of(cx, cy, cz, g.log_scales + 3 * k, g.quats + 4 * k, gr);
     // direction pre-test of the render: D cos(theta) of the cover's cone less a rounding

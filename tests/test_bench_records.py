@@ -56,19 +56,23 @@ def test_malformed_lines_and_no_samples():
 
 
 def test_phase_error_against_the_oracle():
-    """The bench's phase check reads the view records' phasor as (cos, -sin): phasors
-    built from the oracle's own phase give a rounding-sized error, and one phasor
-    rotated by 0.01 rad shows up as the largest error."""
+    """The bench's phase check reads the view records' (cone term, cos, -sin): phasors
+    built from the oracle's own phase give a rounding-sized error, one phasor rotated by
+    0.01 rad shows up as the largest error, and records marked by a NaN cone term (in no
+    tile's list, no phase stored) are left out, whatever their phasor floats hold."""
     import numpy as np
     import oracle
     from paper_2502_01826_gb300 import synthetic
     cfg = synthetic.config_ble(K=64, n_rx=3)
     oracle.build()
     ph = np.stack([oracle.path_phase(cfg["scene"], cfg["rx"][r], cfg["tx"], cfg["f0"]) for r in range(3)])
-    phasor = np.stack([np.cos(ph), -np.sin(ph)], axis=-1).astype(np.float32)
+    phasor = np.stack([np.zeros_like(ph), np.cos(ph), -np.sin(ph)], axis=-1).astype(np.float32)
     e = bench.oracle_phase_error(cfg, phasor)
     assert e["pairs"] == 3 * 64 and e["max"] < 1e-6
     ph[1, 5] += 0.01
-    phasor[1, 5] = np.array([np.cos(ph[1, 5]), -np.sin(ph[1, 5])], np.float32)
+    phasor[1, 5, 1:] = np.array([np.cos(ph[1, 5]), -np.sin(ph[1, 5])], np.float32)
     e = bench.oracle_phase_error(cfg, phasor)
     assert abs(e["max"] - 0.01) < 1e-5
+    phasor[1, 5] = np.array([np.nan, 123.0, -7.0], np.float32)  # a record in no list
+    e = bench.oracle_phase_error(cfg, phasor)
+    assert e["pairs"] == 3 * 64 - 1 and e["max"] < 1e-6
