@@ -162,7 +162,7 @@ typedef struct {
 } gsrf_layout;
 gsrf_status gsrf_workspace_layout(const gsrf_plan *plan, gsrf_layout *out);
 
-/* Step 1 -- Alg. 1 line 2 ("sphericalGaussian", Sec. 4.3): per Gaussian the
+/* Step 1 -- Alg. 1's splatting step, Sec. 4.3: per Gaussian the
  * whitening matrix diag(1/s) R^T and opacity; per (receiver, Gaussian) the whitened
  * receiver offset, the FP32 depth |mu - r| (sort key), the set of tiles the Gaussian
  * may touch (conservative: every ray that can hit it lies in one of them) and the
@@ -172,7 +172,7 @@ gsrf_status gsrf_workspace_layout(const gsrf_plan *plan, gsrf_layout *out);
 gsrf_status gsrf_project(const gsrf_plan *plan, const gsrf_gaussians *g, const float *rx_pos,
                          const float *tx_pos, void *workspace, size_t ws_bytes, void *stream);
 
-/* Step 2 -- Alg. 1 lines 4-5 and App. E: one 64-bit key per (tile, Gaussian) pair,
+/* Step 2 -- the key sort of Alg. 1 and App. E: one 64-bit key per (tile, Gaussian) pair,
  * high 32 bits the tile index (tv * n_tiles_u + tu), low 32 bits the FP32 depth;
  * all pairs of a receiver sorted by key, ties by Gaussian index (a stable radix sort
  * written for this library), and each tile's [start, end) range.  If the pairs of all
@@ -180,14 +180,14 @@ gsrf_status gsrf_project(const gsrf_plan *plan, const gsrf_gaussians *g, const f
  * required count; later steps then write zeros. */
 gsrf_status gsrf_bin(const gsrf_plan *plan, void *workspace, size_t ws_bytes, void *stream);
 
-/* Inspection after gsrf_bin -- App. E, the splat keys of Alg. 1 line 4: writes the sorted
+/* Inspection after gsrf_bin -- App. E, the splat keys of Alg. 1: writes the sorted
  * 64-bit key (tile << 32 | FP32 depth bits) of every pair into the workspace array that
  * gsrf_workspace_layout's pair_keys names, parallel to the pair ids.  The depth bits are
  * those the depth sort used (|mu - r| in deterministic FP32).  Same arguments and errors as
  * gsrf_bin; the workspace must hold a completed gsrf_bin of this plan. */
 gsrf_status gsrf_pair_keys(const gsrf_plan *plan, void *workspace, size_t ws_bytes, void *stream);
 
-/* Step 3 -- Alg. 1 lines 6-12, Eq. 14: every ray walks its tile's list front to back,
+/* Step 3 -- the blend loop of Alg. 1, Eq. 14: every ray walks its tile's list front to back,
  * intersects the 3-sigma ellipsoid (App. D.3), weights by the Gaussian at the midpoint
  * of the chord beyond r_rx (App. A.2), evaluates the Fourier-Legendre radiance and
  * accumulates S += alpha psi e^{-j phi} T, T *= (1 - alpha) e^{-j theta}.
@@ -225,7 +225,7 @@ gsrf_status gsrf_render_bwd(const gsrf_plan *plan, const gsrf_gaussians *g, void
                             float *g_means, float *g_log_scales, float *g_quats,
                             float *g_opacity_logit, float *g_coeffs, float *g_phase_b, void *stream);
 
-/* Batched persistent render (reading of the paper's Alg. 1 lines 6-12 for many
+/* Batched persistent render (reading of Alg. 1's blend loop for many
  * problems at once; the paper renders one query at a time).  n_jobs problems -- each a
  * plan (n_f == 1) with its own workspace that gsrf_project and gsrf_bin have filled,
  * e.g. different scenes, receiver groups, transmitters and carriers -- are rendered by

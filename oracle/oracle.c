@@ -163,7 +163,7 @@ int or_intersect(const double *Sinv, const double *mu, const double *r, const do
 }
 
 /* ------------------------------------------------------------------------- */
-/* Splatting + 64-bit key sort (Alg. 1 lines 2-5, App. E)                      */
+/* Splatting + 64-bit key sort (Alg. 1, App. E)                              */
 /* ------------------------------------------------------------------------- */
 
 typedef struct { uint64_t key; uint32_t id; } kv_t;
@@ -236,7 +236,7 @@ void or_path_phase(const or_scene *s, const float *rx, const float *tx, double f
 }
 
 /* ------------------------------------------------------------------------- */
-/* The render (Alg. 1 lines 6-12; Eq. 14; App. A.3)                             */
+/* The render (blend loop of Alg. 1; Eq. 14; App. A.3)                       */
 /* ------------------------------------------------------------------------- */
 
 typedef struct {

@@ -1,5 +1,5 @@
-// k_bin.cu -- Alg. 1 lines 4-5 and App. E: splat keys (tile << 32 | depth), one sort,
-// tile ranges.  The 64-bit sort is done as
+// k_bin.cu -- the key sort of Alg. 1 and App. E: splat keys (tile << 32 | depth), one
+// sort, tile ranges.  The 64-bit sort is done as
 //   (1) a stable LSD radix sort of each receiver's n FP32 depth keys (4 x 8-bit digits);
 //   (2) emission of the (tile, Gaussian) pairs in that depth order;
 //   (3) a stable counting sort of each receiver's pairs by tile (the high 32 bits),

@@ -1,4 +1,4 @@
-// k_project.cu -- Alg. 1 line 2 ("sphericalGaussian"): per-Gaussian shape records and
+// k_project.cu -- Alg. 1's splatting step: per-Gaussian shape records and
 // per-(receiver, Gaussian) view records, depth keys and tile coverage.
 #include <math.h>
 

@@ -1,4 +1,4 @@
-// k_render.cu -- Alg. 1 lines 6-12 ("Blend"), Eq. 14 / App. A.3: per-ray complex
+// k_render.cu -- Alg. 1's blend loop, Eq. 14 / App. A.3: per-ray complex
 // front-to-back accumulation over the tile's depth-sorted Gaussians.
 //
 // Layout of the work: a work item is one warp's block of bw x bh = 32 rays (one ray per
