@@ -15,7 +15,7 @@ BUILD = os.path.join(ROOT, "_build")
 SO = os.path.join(PKG, "libgsrf.so")
 PEAKS_SO = os.path.join(PKG, "libgsrf_peaks.so")
 PEAKS_SRC = "peaks.cu"
-SOURCES = ["gsrf_api.cu", "k_project.cu", "k_bin.cu", "k_render.cu", "k_signal.cu", "k_backward.cu", "gsrf_static.cu",
+SOURCES = ["gsrf_api.cu", "k_project.cu", "k_bin.cu", "k_dsort.cu", "k_render.cu", "k_signal.cu", "k_backward.cu", "gsrf_static.cu",
            "gsrf_tune.cu"]
 HEADERS = ["gsrf_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -310,6 +310,11 @@ cudaError_t launch_project(const gsrf_plan* p, const Layout& L, const gsrf_gauss
                            const float* rx, const float* tx, void* ws, cudaStream_t st);
 cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream_t st);
 cudaError_t launch_pair_keys(const Layout& L, void* ws, cudaStream_t st);
+// Depth sort of every receiver's n keys in one thread-block cluster per receiver
+// (k_dsort.cu): applies when n keys fit in the largest cluster that runs on the device.
+bool depth_sort_cluster_applies(long long n);
+cudaError_t launch_depth_sort_cluster(const uint32_t* dkey, long long n, int n_rx, uint32_t* dval, uint32_t* nvis,
+                                      cudaStream_t st);
 cudaError_t launch_render_fwd(const gsrf_plan* p, const Layout& L, const gsrf_gaussians* g,
                               void* ws, float* out, void* ray_state, cudaStream_t st);
 cudaError_t launch_signal(const float* rays, int n_rx, int n_f, int n_el, int n_az, int mode,

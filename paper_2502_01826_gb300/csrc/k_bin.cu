@@ -592,6 +592,7 @@ cudaError_t launch_sort_small_keys_segmented(const uint32_t* keys, uint32_t* key
 }
 
 cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream_t st) {
+    const bool on_chip = depth_sort_cluster_applies(L.n);  // before any launch of this call
     DevStatus* status = at<DevStatus>(ws, L.status);
     const size_t nts = (size_t)L.n_rx * (L.n_tiles + 1);
     k_zero_tile_start<<<(unsigned)((nts + 255) / 256), 256, 0, st>>>(at<uint32_t>(ws, L.tile_start), nts);
@@ -601,7 +602,9 @@ cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream
 
     // (1) depth sort, per receiver: keys dkey -> dkey2 -> dkey ..., values likewise.  The
     // first pass drops the Gaussians that cover no tile (key kAbsentKey) and records how
-    // many are left per receiver; the other passes sort only those.
+    // many are left per receiver; the other passes sort only those.  Receivers whose keys
+    // fit in one cluster's shared memory are sorted on chip (k_dsort.cu), the same
+    // permutation in one launch.
     uint32_t* nvis = at<uint32_t>(ws, L.dvis);
     const Segs ds_all{L.n_rx, L.n, L.dchunks, kDChunk, nullptr, nullptr, nullptr, 1};
     const Segs ds_vis{L.n_rx, L.n, L.dchunks, kDChunk, nullptr, nullptr, nvis, 0};
@@ -612,7 +615,12 @@ cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream
     uint32_t* v_out = at<uint32_t>(ws, L.dval);
     uint32_t* v_alt = at<uint32_t>(ws, L.dval2);
     uint32_t* H = at<uint32_t>(ws, L.dhist);
-    for (int pass = 0; pass < 4; ++pass) {
+    const int passes = on_chip ? 0 : 4;
+    if (passes == 0) {  // all four passes on chip, one cluster per receiver
+        if ((e = launch_depth_sort_cluster(k_in, L.n, L.n_rx, v_out, nvis, st)) != cudaSuccess) return e;
+        v_in = v_out;
+    }
+    for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
         const Segs& ds = pass == 0 ? ds_all : ds_vis;
         k_hist<uint32_t><<<dblocks, kSortThreads, 0, st>>>(k_in, ds, shift, 0xffu, 256, H, nullptr);

@@ -269,11 +269,12 @@ def test_stage_times_report_each_stage_of_the_last_call():
     assert t2["render_bwd"] > 0.0 and t2["project"] == t["project"], t2
 
 
-@pytest.mark.parametrize("K", [150_000, 260_000])
+@pytest.mark.parametrize("K", [120_000, 150_000, 260_000])
 def test_bins_bit_exact_at_large_scenes(K):
-    """Scenes larger than the benchmark's (150k and 260k Gaussians, two receivers, 360 x
-    90): keys, ids and tile ranges equal the oracle's bit for bit (dozens of sort chunks
-    per receiver in every pass)."""
+    """Scenes larger than the benchmark's (120k, 150k and 260k Gaussians, two receivers,
+    360 x 90): keys, ids and tile ranges equal the oracle's bit for bit.  Up to 131,072
+    Gaussians a receiver's depth sort runs in one cluster of up to 8 CTAs (8 at 120k);
+    above, in the four global passes (dozens of sort chunks per receiver in every pass)."""
     cfg = synthetic.config_ble(K=K, n_rx=2)
     spec = dict(cfg["grid"])
     K_ = cfg["scene"]["means"].shape[0]
