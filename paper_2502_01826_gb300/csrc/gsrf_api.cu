@@ -67,7 +67,7 @@ bool make_layout(const gsrf_plan* p, Layout* L) {
     L->qkeys = take(items * 4);
     L->qkeys2 = take(items * 4);
     L->qorder = take(items * 4);
-    L->qhist = take((items + kChunk - 1) / kChunk * 32 * 4);
+    L->qhist = take((items + kSmallChunk - 1) / kSmallChunk * 32 * 4);
     L->qcounter = take(8);
     // the paper's splatting circles, per (receiver, Gaussian), only for that variant
     L->circle = take((p->variant & GSRF_VARIANT_PAPER_CULLING) ? nr * n * sizeof(float4) : 0);

@@ -14,6 +14,7 @@ constexpr double kC = 3.0e8;          // propagation speed (Sec. 2 worked exampl
 constexpr int kTile = 16;             // rays per tile side (App. E)
 constexpr int kRenderThreads = kTile * kTile;
 constexpr int kChunk = 4096;          // items per block in the sort passes
+constexpr int kSmallChunk = 1024;     // items per block in the one-segment small-key sort (item orders)
 constexpr int kDChunk = 2048;         // items per block in the depth passes
 constexpr int kEChunk = 1024;         // depth-sorted Gaussians per block in the emission
 constexpr int kESlice = 512;          // pairs per emission work item

@@ -302,13 +302,17 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter4(const K* __restrict__
         const int d = threadIdx.x;
         uint32_t run = 0;
         if (d < nbins) {
+            uint32_t c[R][kSortWarps];  // all loads first: one latency instead of a chain of 32
+#pragma unroll
+            for (int s = 0; s < R; ++s)
+#pragma unroll
+                for (int w = 0; w < kSortWarps; ++w) c[s][w] = cnt[s][w][d];
 #pragma unroll
             for (int s = 0; s < R; ++s)
 #pragma unroll
                 for (int w = 0; w < kSortWarps; ++w) {
-                    const uint32_t c = cnt[s][w][d];
                     cnt[s][w][d] = (uint16_t)run;
-                    run += c;
+                    run += c[s][w];
                 }
             tot[d] = run;
         }
@@ -561,12 +565,14 @@ __global__ void k_zero_tile_start(uint32_t* ts, size_t n) {
 }
 
 // One stable counting pass over n 32-bit keys (digit = key & (nbins - 1), nbins <= 256):
-// vals_out gets the item indices in key order.  hist needs ceil(n / kChunk) * nbins words.
+// vals_out gets the item indices in key order.  hist needs ceil(n / kSmallChunk) * nbins
+// words.  Blocks of kSmallChunk keys (one round of k_scatter4) spread the few tens of
+// thousands of work items over many SMs.
 cudaError_t launch_sort_small_keys(const uint32_t* keys, uint32_t* keys_out, uint32_t* vals_out, long long n,
                                    int nbins, uint32_t* hist, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    const int chunks = (int)((n + kChunk - 1) / kChunk);
-    Segs sg{1, n, chunks, kChunk, nullptr, nullptr, nullptr, 0};
+    const int chunks = (int)((n + kSmallChunk - 1) / kSmallChunk);
+    Segs sg{1, n, chunks, kSmallChunk, nullptr, nullptr, nullptr, 0};
     k_hist<uint32_t><<<chunks, kSortThreads, 0, st>>>(keys, sg, 0, (uint32_t)(nbins - 1), nbins, hist, nullptr);
     k_scan<<<1, kSortThreads, 0, st>>>(sg, nbins, hist, nullptr, nullptr);
     launch_scatter<uint32_t>(chunks, keys, nullptr, keys_out, vals_out, sg, 0, (uint32_t)(nbins - 1), nbins, hist,

@@ -723,7 +723,7 @@ struct BatchLayout {
 
 static BatchLayout batch_layout(int n_jobs, long long n) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const long long chunks = (n + kChunk - 1) / kChunk + n_jobs;
+    const long long chunks = (n + kSmallChunk - 1) / kSmallChunk + n_jobs;  // either sort's chunks
     BatchLayout b;
     b.keys = 0;
     b.keys2 = b.keys + al(n * 4);
