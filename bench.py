@@ -70,10 +70,15 @@ FLOP_HIT = 172
 RENDER_TRAFFIC = {(16, 16, 8, 32): 85583104 + 7175424, (32, 16, 8, 32): 79896320 + 6626304,
                   (32, 32, 8, 32): 84491008 + 6703104}
 # library kernels per step: project 5 (status, ray-table factors, ray table, shape records,
-# view records), bin 18 (zero, 4 x (hist, scan, scatter), count, scan, emit with the tile
-# histogram, tile scan, scatter), render 5 (item keys, counting pass of 3, persistent render),
-# received signal 1
-LAUNCHES_PER_STEP = 29
+# view records), bin 7 (zero, the depth sort in one cluster per receiver, count, scan, emit
+# with the tile histogram, tile scan, scatter; receivers of more than 131,072 Gaussians sort
+# in 4 x (hist, scan, scatter) instead: 18), render 5 (item keys, counting pass of 3,
+# persistent render), received signal 1
+CLUSTER_SORT_MAX_GAUSSIANS = 131072
+
+
+def launches_per_step(n_gauss):
+    return 5 + (7 if n_gauss <= CLUSTER_SORT_MAX_GAUSSIANS else 18) + 5 + 1
 # nominal FP32 lanes per SM (context beside the measured FP32 peak)
 SMS, FP32_LANES = 152, 128
 
@@ -584,7 +589,7 @@ def run_ours(args, ws, rank):
         "fle_degree": fle_degree,
         "uneven": uneven,
         "variants": variants,
-        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "gpu_launches": launches_per_step(K) * args.steps,
         "clocks": clocks,
     }
     return result, cfg, phasor
