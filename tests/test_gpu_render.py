@@ -269,6 +269,23 @@ def test_stage_times_report_each_stage_of_the_last_call():
     assert t2["render_bwd"] > 0.0 and t2["project"] == t["project"], t2
 
 
+@pytest.mark.parametrize("K", [16_384, 16_385, 40_000])
+def test_depth_sort_cluster_sizes_and_an_empty_receiver(K):
+    """Depth sorts in clusters of 1, 2 and 3 CTAs (16,384 keys per CTA at most): a receiver
+    inside the scene, one whose 40 x 12 window points away from it (no Gaussian covers a
+    tile: an empty sort and no pairs) and one outside looking in.  Keys, ids and tile
+    ranges equal the oracle's bit for bit, and the empty receiver renders zero."""
+    scene = synthetic.tiny_scene(K, 104, box=(6.0, 5.0, 3.0), log_scale_mu=math.log(0.15))
+    rx = np.array([[3.0, 2.5, 1.5], [-40.0, 2.5, 1.5], [9.0, -3.0, 1.0]], np.float32)
+    spec = dict(n_az=40, n_el=12, az0_deg=150.0, daz_deg=1.0, el0_deg=-10.0, del_deg=2.0)
+    S, R, p, out = gpu_render(scene, rx, [0.5, 4.5, 2.5], 2.4e9, spec)
+    check_bins(R, scene, rx, spec)
+    keys, ids, rb, ts = R.pairs()
+    rb = rb.cpu().numpy()
+    assert rb[2] - rb[1] == 0 and rb[1] - rb[0] > 0 and rb[3] - rb[2] > 0
+    assert np.all(S[1] == 0)
+
+
 @pytest.mark.parametrize("K", [120_000, 150_000, 260_000])
 def test_bins_bit_exact_at_large_scenes(K):
     """Scenes larger than the benchmark's (120k, 150k and 260k Gaussians, two receivers,
