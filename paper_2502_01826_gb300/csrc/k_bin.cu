@@ -119,31 +119,46 @@ __device__ __forceinline__ T block_excl_scan(T v, T* total, T* sh /* [kSortWarps
 
 // One block per segment: turn per-block digit counts H[block][digit] into absolute
 // destinations inside the segment; optionally record each digit's [start, end) and the
-// segment's item count.
+// segment's item count.  With fewer digits than threads, each digit's chunks are split
+// over G = threads / nbins groups of threads (one pass that sums the groups' spans, one
+// that writes the destinations), so that the whole block walks the counts.
 __global__ void __launch_bounds__(kSortThreads) k_scan(Segs S, int nbins, uint32_t* __restrict__ H,
                                                        uint32_t* __restrict__ bin_start,
                                                        const DevStatus* st, uint32_t* __restrict__ seg_total = nullptr) {
     if (capacity_failed(st)) return;
     __shared__ uint32_t tot[kMaxTiles];
+    __shared__ uint32_t sstart[kMaxTiles];
+    __shared__ uint32_t part[kSortThreads];  // per (group, digit): the sum of the groups before
     __shared__ uint32_t sh[kSortWarps];
     const int seg = blockIdx.x;
     long long c0, c1;
     chunk_range(S, seg, c0, c1);
-    for (int d = threadIdx.x; d < nbins; d += kSortThreads) {
+    const int G = nbins < kSortThreads ? kSortThreads / nbins : 1;
+    const long long span = (c1 - c0 + G - 1) / G;
+    for (int t = threadIdx.x; t < G * nbins; t += kSortThreads) {
+        const int d = t % nbins, g = t / nbins;
+        const long long a = c0 + g * span, b = min(a + span, c1);
         uint32_t run = 0;
-        for (long long cb = c0; cb < c1; cb += 8) {  // 8 independent loads in flight
-            uint32_t v[8];
+        for (long long cb = a; cb < b; cb += 8) {  // 8 independent loads in flight
 #pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = cb + j < c1 ? H[(size_t)(cb + j) * nbins + d] : 0u;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                if (cb + j < c1) H[(size_t)(cb + j) * nbins + d] = run;
-                run += v[j];
-            }
+            for (int j = 0; j < 8; ++j) run += cb + j < b ? H[(size_t)(cb + j) * nbins + d] : 0u;
         }
-        tot[d] = run;
+        if (G > 1) part[t] = run;
+        else tot[d] = run;
     }
     __syncthreads();
+    if (G > 1) {
+        for (int d = threadIdx.x; d < nbins; d += kSortThreads) {
+            uint32_t p = 0;
+            for (int g = 0; g < G; ++g) {
+                const uint32_t x = part[g * nbins + d];
+                part[g * nbins + d] = p;
+                p += x;
+            }
+            tot[d] = p;
+        }
+        __syncthreads();
+    }
     // exclusive scan over digits, kSortThreads at a time
     uint32_t carry = 0;
     for (int d0 = 0; d0 < nbins; d0 += kSortThreads) {
@@ -152,18 +167,26 @@ __global__ void __launch_bounds__(kSortThreads) k_scan(Segs S, int nbins, uint32
         uint32_t t;
         const uint32_t ex = block_excl_scan<uint32_t>(v, &t, sh);
         if (d < nbins) {
-            const uint32_t start = carry + ex;
-            for (long long cb = c0; cb < c1; cb += 8) {
-                uint32_t v[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] = cb + j < c1 ? H[(size_t)(cb + j) * nbins + d] : 0u;
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (cb + j < c1) H[(size_t)(cb + j) * nbins + d] = v[j] + start;
-            }
-            if (bin_start) bin_start[(size_t)seg * (nbins + 1) + d] = start;
+            sstart[d] = carry + ex;
+            if (bin_start) bin_start[(size_t)seg * (nbins + 1) + d] = carry + ex;
         }
         carry += t;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < G * nbins; t += kSortThreads) {
+        const int d = t % nbins, g = t / nbins;
+        const long long a = c0 + g * span, b = min(a + span, c1);
+        uint32_t run = sstart[d] + (G > 1 ? part[t] : 0u);
+        for (long long cb = a; cb < b; cb += 8) {
+            uint32_t v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = cb + j < b ? H[(size_t)(cb + j) * nbins + d] : 0u;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (cb + j < b) H[(size_t)(cb + j) * nbins + d] = run;
+                run += v[j];
+            }
+        }
     }
     if (bin_start && threadIdx.x == 0) bin_start[(size_t)seg * (nbins + 1) + nbins] = carry;
     if (seg_total && threadIdx.x == 0) seg_total[seg] = carry;
@@ -413,47 +436,68 @@ __global__ void __launch_bounds__(kSortThreads) k_count_chunks(const uint32_t* _
 }
 
 // One block: chunk offsets per receiver, receiver bases, capacity check, the chunk
-// table of the tile sort and the slice table of the emission.
+// table of the tile sort and the slice table of the emission.  A warp scans one
+// receiver's chunk sums 32 at a time (shuffles); the receivers' bases are block scans,
+// kSortThreads receivers at a time.
 __global__ void __launch_bounds__(kSortThreads) k_scan_pairs(uint32_t* __restrict__ chunk_sum, int n_rx, int dchunks,
                                                              long long cap, long long* __restrict__ rx_base,
                                                              uint32_t* __restrict__ rx_total,
                                                              uint32_t* __restrict__ pchunk_base, DevStatus* st,
                                                              uint32_t* __restrict__ eslice_base) {
-    for (int r = threadIdx.x; r < n_rx; r += kSortThreads) {
-        uint32_t run = 0;
+    __shared__ long long shl[kSortWarps];
+    __shared__ uint32_t shu[kSortWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = warp; r < n_rx; r += kSortWarps) {
         uint32_t* cs = chunk_sum + (size_t)r * dchunks;
-        for (int cb = 0; cb < dchunks; cb += 8) {  // 8 independent loads in flight
-            uint32_t v[8];
+        uint32_t carry = 0;
+        for (int c0 = 0; c0 < dchunks; c0 += 32) {
+            const int c = c0 + lane;
+            const uint32_t v = c < dchunks ? cs[c] : 0u;
+            uint32_t x = v;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = cb + j < dchunks ? cs[cb + j] : 0u;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                if (cb + j < dchunks) cs[cb + j] = run;
-                run += v[j];
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
             }
+            if (c < dchunks) cs[c] = carry + x - v;
+            carry += __shfl_sync(0xffffffffu, x, 31);
         }
-        rx_total[r] = run;
+        if (lane == 0) rx_total[r] = carry;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        long long b = 0;
-        uint32_t cb = 0, es = 0;
-        for (int r = 0; r < n_rx; ++r) {
-            rx_base[r] = b;
-            pchunk_base[r] = cb;
-            eslice_base[r] = es;
-            b += rx_total[r];
-            cb += (rx_total[r] + kChunk - 1) / kChunk;
-            es += (rx_total[r] + kESlice - 1) / kESlice;
+    long long b = 0;
+    uint32_t cb = 0, es = 0;
+    for (int r0 = 0; r0 < n_rx; r0 += kSortThreads) {
+        const int r = r0 + threadIdx.x;
+        const uint32_t t = r < n_rx ? rx_total[r] : 0u;
+        long long tb;
+        uint32_t tc, te;
+        const long long xb = block_excl_scan<long long>((long long)t, &tb, shl);
+        const uint32_t xc = block_excl_scan<uint32_t>((t + kChunk - 1) / kChunk, &tc, shu);
+        const uint32_t xe = block_excl_scan<uint32_t>((t + kESlice - 1) / kESlice, &te, shu);
+        if (r < n_rx) {
+            rx_base[r] = b + xb;
+            pchunk_base[r] = cb + xc;
+            eslice_base[r] = es + xe;
         }
+        b += tb;
+        cb += tc;
+        es += te;
+    }
+    if (threadIdx.x == 0) {
         rx_base[n_rx] = b;
         pchunk_base[n_rx] = cb;
         eslice_base[n_rx] = es;
         st->required_pairs = b;
-        if (b > cap) {
-            atomicCAS(&st->code, (int)GSRF_OK, (int)GSRF_ERR_CAPACITY);
-            // a failed bin leaves no pairs: downstream kernels see empty lists
-            for (int r = 0; r <= n_rx; ++r) { rx_base[r] = 0; pchunk_base[r] = 0; eslice_base[r] = 0; }
+    }
+    if (b > cap) {  // uniform: every thread holds the same totals
+        if (threadIdx.x == 0) atomicCAS(&st->code, (int)GSRF_OK, (int)GSRF_ERR_CAPACITY);
+        __syncthreads();
+        // a failed bin leaves no pairs: downstream kernels see empty lists
+        for (int r = threadIdx.x; r <= n_rx; r += kSortThreads) {
+            rx_base[r] = 0;
+            pchunk_base[r] = 0;
+            eslice_base[r] = 0;
         }
     }
 }
