@@ -511,7 +511,9 @@ __global__ void __launch_bounds__(kSortThreads) k_scan_pairs(uint32_t* __restric
 // group and writes the slice's part of the group's run 32 slots at a time (coalesced):
 // each slot finds its Gaussian by a search over the warp's inclusive counts and its tile
 // from its index inside that Gaussian's cover (elevation rows of the set azimuth tiles,
-// in order); then it goes on with the next group until the slice is done.
+// in order); then it goes on with the next group until the slice is done.  The group
+// loads are pipelined: the sorted ids two groups ahead and the covers one group ahead are
+// in flight while a group is written.
 __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restrict__ dval,
                                                        const Cover* __restrict__ cover, long long n,
                                                        const uint32_t* __restrict__ nvis, int dchunks,
@@ -553,17 +555,23 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
         }
         uint32_t* kout = ptile + rx_base[r];
         uint32_t* iout = pids + rx_base[r];
+        // loads pipelined across groups: the ids two groups ahead, the covers one ahead
+        const uint32_t* dv = dval + (size_t)r * n;
+        const Cover* cov = cover + (size_t)r * n;
+        auto id_of = [&](int gg) -> uint32_t {
+            const long long i = (long long)gg * 32 + lane;
+            return (gg < ng && i < nv) ? dv[i] : 0xffffffffu;
+        };
+        uint32_t id_c = id_of(g), id_n = id_of(g + 1);
+        Cover cv_c = {0ull, 0u, 0u};
+        if (id_c != 0xffffffffu) cv_c = cov[id_c];
         while (P0 < P1 && g < ng) {  // uniform over the warp
-            const long long i = (long long)g * 32 + lane;
-            uint32_t gid = 0, cnt = 0, tvw = 0, mlo = 0, mhi = 0;
-            if (i < nv) {
-                gid = dval[(size_t)r * n + i];
-                const Cover cv = cover[(size_t)r * n + gid];
-                cnt = cv.count;
-                tvw = cv.tv;
-                mlo = (uint32_t)cv.mask;
-                mhi = (uint32_t)(cv.mask >> 32);
-            }
+            Cover cv_n = {0ull, 0u, 0u};
+            if (id_n != 0xffffffffu) cv_n = cov[id_n];
+            const uint32_t id_nn = id_of(g + 2);
+            const uint32_t gid = id_c != 0xffffffffu ? id_c : 0u;
+            const uint32_t cnt = cv_c.count, tvw = cv_c.tv;
+            const uint32_t mlo = (uint32_t)cv_c.mask, mhi = (uint32_t)(cv_c.mask >> 32);
             uint32_t incl = cnt;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
@@ -600,6 +608,9 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
             }
             P0 = base + total;
             ++g;
+            id_c = id_n;
+            cv_c = cv_n;
+            id_n = id_nn;
         }
     }
 }
