@@ -615,8 +615,14 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
     }
 }
 
-__global__ void k_zero_tile_start(uint32_t* ts, size_t n) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) ts[i] = 0;
+// The bin's zeroed state in one launch: tile ranges, the emission's tile histogram and
+// the receivers' first pairs (all zero: no pairs, should the bin stop early).
+__global__ void k_zero_bin(uint32_t* ts, size_t nts, uint32_t* th, size_t nth, long long* rxb, int nrxb) {
+    const size_t step = (size_t)gridDim.x * blockDim.x;
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (size_t i = t0; i < nts; i += step) ts[i] = 0;
+    for (size_t i = t0; i < nth; i += step) th[i] = 0;
+    for (size_t i = t0; i < (size_t)nrxb; i += step) rxb[i] = 0;
 }
 
 // One stable counting pass over n 32-bit keys (digit = key & (nbins - 1), nbins <= 256):
@@ -656,10 +662,13 @@ cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream
     const bool on_chip = depth_sort_cluster_applies(L.n);  // before any launch of this call
     DevStatus* status = at<DevStatus>(ws, L.status);
     const size_t nts = (size_t)L.n_rx * (L.n_tiles + 1);
-    k_zero_tile_start<<<(unsigned)((nts + 255) / 256), 256, 0, st>>>(at<uint32_t>(ws, L.tile_start), nts);
-    cudaError_t e = cudaMemsetAsync(at<long long>(ws, L.rx_base), 0, sizeof(long long) * (L.n_rx + 1), st);
+    const size_t nth = (size_t)L.pchunks_max * L.n_tiles;
+    const size_t nz = max(nts, nth);
+    k_zero_bin<<<(unsigned)min((nz + 255) / 256, (size_t)4096), 256, 0, st>>>(
+        at<uint32_t>(ws, L.tile_start), nts, at<uint32_t>(ws, L.thist), nth, at<long long>(ws, L.rx_base), L.n_rx + 1);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (L.n == 0) return cudaGetLastError();
+    if (L.n == 0) return cudaSuccess;
 
     // (1) depth sort, per receiver: keys dkey -> dkey2 -> dkey ..., values likewise.  The
     // first pass drops the Gaussians that cover no tile (key kAbsentKey) and records how
@@ -713,8 +722,7 @@ cudaError_t launch_bin(const gsrf_plan* p, const Layout& L, void* ws, cudaStream
     const unsigned emit_grid =
         (unsigned)max(1ll, min((long long)sms * max(per_sm, 1), (max_slices + kSortWarps - 1) / kSortWarps));
     uint32_t* ptile = at<uint32_t>(ws, L.pkeys2);  // the pairs' tile indices, in depth order
-    uint32_t* TH = at<uint32_t>(ws, L.thist);       // filled by the emission
-    if ((e = cudaMemsetAsync(TH, 0, (size_t)L.pchunks_max * L.n_tiles * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    uint32_t* TH = at<uint32_t>(ws, L.thist);       // zeroed by k_zero_bin, filled by the emission
     k_emit<<<emit_grid, kSortThreads, 0, st>>>(dval_sorted, at<Cover>(ws, L.cover), L.n, nvis, L.echunks, chunk_sum,
                                                group_off, at<long long>(ws, L.rx_base), at<uint32_t>(ws, L.rx_total),
                                                eslice_base, L.n_rx, L.ntu, at<uint32_t>(ws, L.pchunk_base), L.n_tiles,
