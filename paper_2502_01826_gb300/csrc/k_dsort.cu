@@ -205,37 +205,43 @@ __global__ void __launch_bounds__(kCsThreads, 1)
 // Cluster size for n keys per receiver, 0 when the cluster sort does not apply (more keys
 // than kCsMaxCluster CTAs hold, or no cluster of that size fits on the device).  Above 8
 // CTAs (13 for 200k Gaussians) only one cluster fits per GPC and the global passes are
-// faster.
+// faster.  Whether a cluster size fits is a property of the device, cached per device; the
+// kernel's shared-memory attribute is set again before every launch (a device reset clears
+// it).
+constexpr int kCsMaxDevices = 64;
 static int cluster_for(long long n) {
     if (n <= 0) return 0;
     const long long C = (n + kCsCap - 1) / kCsCap;
     if (C > kCsMaxCluster) return 0;
-    static int fits[kCsMaxCluster + 1] = {};  // 0 unknown, 1 fits, -1 does not
-    if (fits[C] == 0) {
-        if (cudaPeekAtLastError() != cudaSuccess) return 0;  // leave a pending error to its caller
+    int dev = 0;
+    if (cudaPeekAtLastError() != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess || dev < 0 ||
+        dev >= kCsMaxDevices)
+        return 0;  // leave a pending error to its caller
+    static int fits[kCsMaxDevices][kCsMaxCluster + 1] = {};  // 0 unknown, 1 fits, -1 does not
+    if (fits[dev][C] == 0) {
         int ok = -1;
         const int smem = (int)sizeof(CsShared);
         if (cudaFuncSetAttribute(k_depth_sort_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
             cudaSuccess) {
             cudaLaunchConfig_t cfg = {};
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = (unsigned)C;
-            at[0].val.clusterDim.y = 1;
-            at[0].val.clusterDim.z = 1;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = (unsigned)C;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
             cfg.gridDim = dim3((unsigned)C);
             cfg.blockDim = dim3(kCsThreads);
             cfg.dynamicSmemBytes = (size_t)smem;
-            cfg.attrs = at;
+            cfg.attrs = attr;
             cfg.numAttrs = 1;
             int clusters = 0;
             if (cudaOccupancyMaxActiveClusters(&clusters, k_depth_sort_cluster, &cfg) == cudaSuccess && clusters > 0)
                 ok = 1;
         }
         (void)cudaGetLastError();  // a refused attribute is an answer, not an error of the call
-        fits[C] = ok;
+        fits[dev][C] = ok;
     }
-    return fits[C] > 0 ? (int)C : 0;
+    return fits[dev][C] > 0 ? (int)C : 0;
 }
 
 bool depth_sort_cluster_applies(long long n) { return cluster_for(n) > 0; }
@@ -244,6 +250,9 @@ cudaError_t launch_depth_sort_cluster(const uint32_t* dkey, long long n, int n_r
                                       cudaStream_t st) {
     const int C = cluster_for(n);
     if (C == 0) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_depth_sort_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(CsShared));
+    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
