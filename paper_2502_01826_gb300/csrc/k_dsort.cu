@@ -1,12 +1,15 @@
 // k_dsort.cu -- the depth sort of the key sort (Alg. 1, App. E) for one receiver inside
-// one thread-block cluster.  The per-receiver sort is the same stable LSD radix sort as
-// the one in k_bin.cu (4 passes of 8-bit digits over the FP32 depth bits, the first pass
-// dropping the Gaussians that cover no tile, ties in input order, so ties by Gaussian
-// index), but the keys stay on chip between the passes: the cluster's CTAs hold the
-// receiver's (key, id) items in shared memory, each pass ranks them with warp peer groups
-// and stores every item straight into the shared memory of the CTA that holds its new
-// position (distributed shared memory).  The keys are read from HBM once and the sorted
-// ids written once, in one launch instead of twelve.
+// one thread-block cluster.  The per-receiver sort is a stable LSD radix sort like the
+// one in k_bin.cu (the first pass dropping the Gaussians that cover no tile, ties in input
+// order, so ties by Gaussian index), but over key - min of the receiver's visible keys:
+// the FP32 depth bits of one room span about 26 bits, so 9-bit digits need three passes
+// instead of four 8-bit ones (as many 9-bit passes as the span needs up to 27 bits, else
+// four 8-bit passes).  Subtracting the minimum keeps the order of the keys, so the
+// permutation is the same.  The keys stay on chip between the passes: the cluster's CTAs
+// hold the receiver's (key, id) items in shared memory, each pass ranks them with warp
+// peer groups and stores every item straight into the shared memory of the CTA that holds
+// its new position (distributed shared memory).  The keys are read from HBM once and the
+// sorted ids written once, in one launch instead of twelve.
 //
 // Layout: CTA c of the cluster holds positions [c * sl, (c + 1) * sl) of the current
 // order, sl = ceil(m / C) for the m items of the pass; warp w of a CTA takes a
@@ -31,31 +34,37 @@ constexpr uint32_t kCsNone = 0xffffffffu;    // an empty register slot
 static_assert((long long)kCsCap * kCsMaxCluster <= (1ll << kCsRankShift), "ids must fit below the rank");
 static_assert(kCsIpt * 32 <= (1 << (32 - kCsRankShift - 1)), "ranks must fit above the id");
 
+constexpr int kCsDigits = 512;  // 9-bit digits at most
 struct CsShared {
-    uint2 item[kCsCap];                // (depth key, Gaussian id) at the CTA's positions
-    uint32_t wcnt[256 * kCsStride];    // per (digit, warp): count, then exclusive prefix
-    uint32_t ctot[256];                // the CTA's count per digit (read by the cluster)
-    uint32_t base[256];                // the digit's first position for this CTA's items
-    uint32_t wsum[8];
+    uint2 item[kCsCap];                    // (key - min, Gaussian id) at the CTA's positions
+    uint32_t wcnt[kCsDigits * kCsStride];  // per (digit, warp): count, then exclusive prefix
+    uint32_t ctot[kCsDigits];              // the CTA's count per digit (read by the cluster)
+    uint32_t base[kCsDigits];              // the digit's first position for this CTA's items
+    uint32_t wsum[kCsDigits / 32];
     uint32_t total;
+    uint32_t kmin, kmax;                   // the CTA's visible keys (read by the cluster)
+    uint32_t gmin, gmax;                   // the receiver's
     unsigned long long inv;  // ceil(2^40 / slice): dest / slice as one multiply and shift
 };
 
 // Rank the registers' items of one pass: per warp and digit, the running count in
 // wcnt gives each item its place among the warp's items of the same digit.
 __device__ __forceinline__ void cs_rank(const uint32_t (&key)[kCsIpt], uint32_t (&val)[kCsIpt], int ipt, int shift,
-                                        uint32_t* wcnt, int warp, uint32_t lt) {
+                                        int width, uint32_t* wcnt, int warp, uint32_t lt) {
+    const uint32_t dmask = (1u << width) - 1u;
 #pragma unroll
     for (int j = 0; j < kCsIpt; ++j) {
         if (j < ipt) {  // warp-uniform
             const bool valid = val[j] != kCsNone;
-            const uint32_t dg = valid ? (key[j] >> shift) & 0xffu : kCsNone;
+            const uint32_t dg = valid ? (key[j] >> shift) & dmask : kCsNone;
             uint32_t peers = __ballot_sync(0xffffffffu, valid);
             if (!valid) peers = ~peers;
 #pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                const uint32_t bb = __ballot_sync(0xffffffffu, (dg >> b) & 1u);
-                peers &= ((dg >> b) & 1u) ? bb : ~bb;
+            for (int b = 0; b < 9; ++b) {
+                if (b < width) {  // uniform
+                    const uint32_t bb = __ballot_sync(0xffffffffu, (dg >> b) & 1u);
+                    peers &= ((dg >> b) & 1u) ? bb : ~bb;
+                }
             }
             const uint32_t r = (uint32_t)__popc(peers & lt);
             uint32_t old = 0;
@@ -85,7 +94,11 @@ __global__ void __launch_bounds__(kCsThreads, 1)
     const uint32_t lt = (1u << lane) - 1u;
     const uint32_t* keys = dkey + rx * n;
 
-    for (int i = threadIdx.x; i < 256 * kCsStride; i += kCsThreads) S.wcnt[i] = 0;
+    for (int i = threadIdx.x; i < kCsDigits * kCsStride; i += kCsThreads) S.wcnt[i] = 0;
+    if (threadIdx.x == 0) {
+        S.kmin = 0xffffffffu;
+        S.kmax = 0u;
+    }
 
     uint32_t key[kCsIpt], val[kCsIpt];
     // pass 0 reads CTA c's slice of the n keys from global memory
@@ -105,11 +118,52 @@ __global__ void __launch_bounds__(kCsThreads, 1)
             if (key[j] != kAbsentKey) val[j] = (uint32_t)(lo + p);
         }
     }
-    __syncthreads();  // wcnt cleared
+    __syncthreads();  // wcnt, kmin and kmax cleared
+    // the span of the receiver's visible keys, so that the sort runs over key - min and
+    // over as few digits as that needs
+    {
+        uint32_t mn = 0xffffffffu, mx = 0u;
+#pragma unroll
+        for (int j = 0; j < kCsIpt; ++j)
+            if (val[j] != kCsNone) {
+                mn = min(mn, key[j]);
+                mx = max(mx, key[j]);
+            }
+        mn = __reduce_min_sync(0xffffffffu, mn);
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if (lane == 0) {
+            atomicMin(&S.kmin, mn);
+            atomicMax(&S.kmax, mx);
+        }
+    }
+    cl.sync();
+    if (warp == 0) {
+        uint32_t mn = 0xffffffffu, mx = 0u;
+        if (lane < C) {
+            mn = *cl.map_shared_rank(&S.kmin, lane);
+            mx = *cl.map_shared_rank(&S.kmax, lane);
+        }
+        mn = __reduce_min_sync(0xffffffffu, mn);
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if (lane == 0) {
+            S.gmin = mn;
+            S.gmax = mx;
+        }
+    }
+    __syncthreads();
+    const uint32_t gmin = S.gmin;
+    const uint32_t span = S.gmax >= gmin ? S.gmax - gmin : 0u;
+    const int bits = 32 - __clz((int)span);
+    const int width = bits <= 27 ? 9 : 8;
+    const int npass = bits <= 27 ? max(1, (bits + 8) / 9) : 4;
+#pragma unroll
+    for (int j = 0; j < kCsIpt; ++j)
+        if (val[j] != kCsNone) key[j] -= gmin;
+    const int nb = 1 << width;
 
-    for (int pass = 0; pass < 4; ++pass) {
-        const int shift = 8 * pass;
-        const bool last = pass == 3;
+    for (int pass = 0; pass < npass; ++pass) {
+        const int shift = width * pass;
+        const bool last = pass == npass - 1;
         if (pass > 0) {
 #pragma unroll
             for (int j = 0; j < kCsIpt; ++j) {
@@ -123,10 +177,10 @@ __global__ void __launch_bounds__(kCsThreads, 1)
                 }
             }
         }
-        cs_rank(key, val, ipt, shift, S.wcnt, warp, lt);
+        cs_rank(key, val, ipt, shift, width, S.wcnt, warp, lt);
         __syncthreads();
         // per digit, the exclusive prefix over the warps and the CTA's count
-        for (int d = warp; d < 256; d += kCsWarps) {
+        for (int d = warp; d < nb; d += kCsWarps) {
             const uint32_t v = S.wcnt[d * kCsStride + lane];
             uint32_t x = v;
 #pragma unroll
@@ -139,7 +193,7 @@ __global__ void __launch_bounds__(kCsThreads, 1)
         }
         cl.sync();  // every CTA's counts are complete, and every item is in registers
         uint32_t tot = 0, before = 0, incl = 0;
-        if (threadIdx.x < 256) {
+        if (threadIdx.x < nb) {
             const int d = threadIdx.x;
             for (int q = 0; q < C; ++q) {
                 const uint32_t x = cl.map_shared_rank(S.ctot, q)[d];
@@ -155,12 +209,14 @@ __global__ void __launch_bounds__(kCsThreads, 1)
             if (lane == 31) S.wsum[warp] = incl;
         }
         __syncthreads();
-        if (threadIdx.x < 256) {
+        if (threadIdx.x < nb) {
             uint32_t wb = 0, all = 0;
 #pragma unroll
-            for (int w = 0; w < 8; ++w) {
-                if (w < warp) wb += S.wsum[w];
-                all += S.wsum[w];
+            for (int w = 0; w < kCsDigits / 32; ++w) {
+                if (w < nb / 32) {
+                    if (w < warp) wb += S.wsum[w];
+                    all += S.wsum[w];
+                }
             }
             S.base[threadIdx.x] = wb + incl - tot + before;
             if (threadIdx.x == 0) {
@@ -180,7 +236,7 @@ __global__ void __launch_bounds__(kCsThreads, 1)
 #pragma unroll
         for (int j = 0; j < kCsIpt; ++j) {
             if (j < ipt && val[j] != kCsNone) {
-                const uint32_t d = (key[j] >> shift) & 0xffu;
+                const uint32_t d = (key[j] >> shift) & (uint32_t)(nb - 1);
                 const uint32_t id = val[j] & ((1u << kCsRankShift) - 1u);
                 const uint32_t dest = S.base[d] + S.wcnt[d * kCsStride + warp] + (val[j] >> kCsRankShift);
                 if (last) {
@@ -192,7 +248,7 @@ __global__ void __launch_bounds__(kCsThreads, 1)
             }
         }
         cl.sync();  // every item is in place and every count read
-        for (int i = threadIdx.x; i < 256 * kCsStride; i += kCsThreads) S.wcnt[i] = 0;
+        for (int i = threadIdx.x; i < nb * kCsStride; i += kCsThreads) S.wcnt[i] = 0;
         sl = (int)sl_next;
         lo = min(c * sl, (int)m_next);
         m = min(sl, (int)m_next - lo);
