@@ -26,7 +26,7 @@ constexpr int kCsThreads = 1024;
 constexpr int kCsWarps = kCsThreads / 32;
 constexpr int kCsIpt = 16;                   // items a thread holds at most
 constexpr int kCsCap = kCsThreads * kCsIpt;  // items a CTA holds at most
-constexpr int kCsMaxCluster = 8;  // larger clusters measured slower than the global passes
+constexpr int kCsMaxCluster = 8;             // larger clusters measured slower than the global passes
 constexpr int kCsStride = kCsWarps + 1;      // padded digit row of the per-warp counts
 constexpr int kCsRankShift = 20;             // id in the low 20 bits, rank above
 constexpr uint32_t kCsNone = 0xffffffffu;    // an empty register slot
@@ -43,7 +43,7 @@ struct CsShared {
     uint32_t wsum[kCsDigits / 32];
     uint32_t total;
     uint32_t kmin, kmax;                   // the CTA's visible keys (read by the cluster)
-    uint32_t gmin, gmax;                   // the receiver's
+    uint32_t gmin, gmax;                   // the receiver's, over the cluster
     unsigned long long inv;  // ceil(2^40 / slice): dest / slice as one multiply and shift
 };
 
