@@ -76,3 +76,19 @@ def test_phase_error_against_the_oracle():
     phasor[1, 5] = np.array([np.nan, 123.0, -7.0], np.float32)  # a record in no list
     e = bench.oracle_phase_error(cfg, phasor)
     assert e["pairs"] == 3 * 64 - 1 and e["max"] < 1e-6
+
+
+def test_launch_count_follows_the_cluster_sort_limit():
+    """The bench's per-step launch claim (18 library kernels when a receiver's depth sort
+    runs in one cluster, 29 with the 12 global passes) uses the library's limit: CTAs of
+    kCsThreads x kCsIpt keys, at most kCsMaxCluster of them."""
+    import re
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "paper_2502_01826_gb300", "csrc", "k_dsort.cu")).read()
+    const = {k: int(re.search(r"constexpr int %s = (\d+);" % k, src).group(1))
+             for k in ("kCsThreads", "kCsIpt", "kCsMaxCluster")}
+    limit = const["kCsThreads"] * const["kCsIpt"] * const["kCsMaxCluster"]
+    assert bench.CLUSTER_SORT_MAX_GAUSSIANS == limit
+    assert bench.launches_per_step(50_000) == 18
+    assert bench.launches_per_step(limit) == 18
+    assert bench.launches_per_step(limit + 1) == 29
