@@ -286,6 +286,26 @@ def test_depth_sort_cluster_sizes_and_an_empty_receiver(K):
     assert np.all(S[1] == 0)
 
 
+def test_depth_sort_of_a_wide_depth_span():
+    """Depths from 2 cm to 20 km, each Gaussian scaled with its distance so that all stay
+    visible (about 20 binades: a key span above 2^27, so the cluster sort takes four 8-bit
+    passes instead of 9-bit ones): keys, ids and tile ranges equal the oracle's bit for
+    bit."""
+    rng = np.random.default_rng(105)
+    K = 20_000
+    scene = synthetic.tiny_scene(K, 105, box=(6.0, 5.0, 3.0), log_scale_mu=math.log(0.05))
+    rx = np.array([[0.0, 0.0, 0.0], [1.0, -2.0, 0.5]], np.float32)
+    u = rng.normal(size=(K, 3))
+    u[:, 2] = np.abs(u[:, 2])  # above the horizon of the 0..90 degree grid
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    dist = np.exp(rng.uniform(math.log(0.02), math.log(20000.0), K))
+    scene["means"] = (u * dist[:, None]).astype(np.float32)
+    scene["log_scales"] = (scene["log_scales"] + np.log(dist)[:, None]).astype(np.float32)
+    spec = dict(n_az=72, n_el=18, r_rx=0.01)
+    S, R, p, out = gpu_render(scene, rx, [5.0, 5.0, 2.0], 2.4e9, spec)
+    check_bins(R, scene, rx, spec)
+
+
 @pytest.mark.parametrize("K", [120_000, 150_000, 260_000])
 def test_bins_bit_exact_at_large_scenes(K):
     """Scenes larger than the benchmark's (120k, 150k and 260k Gaussians, two receivers,
