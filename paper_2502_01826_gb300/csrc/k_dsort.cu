@@ -16,6 +16,7 @@
 // contiguous run of ceil(sl / threads) * 32 of them, 32 per round, so the order
 // (CTA, warp, round, lane) is the position order and the ranks keep it.
 #include "gsrf_internal.cuh"
+#include <atomic>
 #include <cooperative_groups.h>
 
 namespace cg = cooperative_groups;
@@ -273,8 +274,9 @@ static int cluster_for(long long n) {
     if (cudaPeekAtLastError() != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess || dev < 0 ||
         dev >= kCsMaxDevices)
         return 0;  // leave a pending error to its caller
-    static int fits[kCsMaxDevices][kCsMaxCluster + 1] = {};  // 0 unknown, 1 fits, -1 does not
-    if (fits[dev][C] == 0) {
+    // 0 unknown, 1 fits, -1 does not
+    static std::atomic<int> fits[kCsMaxDevices][kCsMaxCluster + 1] = {};
+    if (fits[dev][C].load(std::memory_order_relaxed) == 0) {
         int ok = -1;
         const int smem = (int)sizeof(CsShared);
         if (cudaFuncSetAttribute(k_depth_sort_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
@@ -295,9 +297,9 @@ static int cluster_for(long long n) {
                 ok = 1;
         }
         (void)cudaGetLastError();  // a refused attribute is an answer, not an error of the call
-        fits[dev][C] = ok;
+        fits[dev][C].store(ok, std::memory_order_relaxed);  // racing threads store the same answer
     }
-    return fits[dev][C] > 0 ? (int)C : 0;
+    return fits[dev][C].load(std::memory_order_relaxed) > 0 ? (int)C : 0;
 }
 
 bool depth_sort_cluster_applies(long long n) { return cluster_for(n) > 0; }
